@@ -1,0 +1,257 @@
+"""FP64 CPU oracle of the coupled flood-pedestrian step -- TEST INFRASTRUCTURE.
+
+This package wraps ``floodped_oracle.c`` (plain, single-threaded FP64 C, see its
+header for the paper passages each function follows).  It is a checker, not a
+product component: only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import it.  It
+shares no code with the CUDA library and never imports it.
+
+Parity unpinned: the pedestrian repulsion constants (reading of the cited
+social-force model) and the paper's 3484-bag barrier count.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "floodped_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+TICKS = 1 << 20
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no FMA contraction, no fast-math)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".%d.tmp" % os.getpid()
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
+               "-o", tmp, _SRC, "-lm"]
+        subprocess.check_call(cmd)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        _lib = ctypes.CDLL(_LIB)
+        _lib.or_step.restype = ctypes.c_int64
+        _lib.or_run.restype = ctypes.c_int64
+        _lib.or_run.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]
+        _lib.or_step.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+        _lib.or_prepare.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+        _lib.or_mass.restype = ctypes.c_double
+        _lib.or_mass.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+        _lib.or_dt_ticks.restype = ctypes.c_int64
+        _lib.or_dt_ticks.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_int64]
+        _lib.or_hr_state.restype = ctypes.c_int
+        _lib.or_hr_state.argtypes = [ctypes.c_float, ctypes.c_float, ctypes.c_float]
+        _lib.or_hll.restype = None
+        _lib.or_hll.argtypes = [ctypes.c_double] * 7 + [ctypes.c_void_p]
+        _lib.or_philox4x64.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        _lib.or_hydro_depth.restype = ctypes.c_double
+        _lib.or_hydro_depth.argtypes = [ctypes.c_void_p, ctypes.c_int64]
+        _lib.or_nav_field.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_void_p, ctypes.c_void_p]
+        _lib.or_bags_per_cell.restype = ctypes.c_int32
+        _lib.or_bags_per_cell.argtypes = [ctypes.c_double]
+        _lib.or_flood_step.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
+    return _lib
+
+
+_P = ctypes.c_void_p
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+        ("dx", ctypes.c_double), ("g", ctypes.c_double), ("cfl", ctypes.c_double),
+        ("t_end_ticks", ctypes.c_int64),
+        ("n_hydro", ctypes.c_int32), ("hydro_t", _P), ("hydro_h", _P),
+        ("bc_s", _P), ("bc_n", _P), ("bc_w", _P), ("bc_e", _P),
+        ("n0", _P), ("walkable", _P), ("exit_mask", _P),
+        ("n_depot", ctypes.c_int32), ("depot_cells", _P),
+        ("n_barrier", ctypes.c_int32), ("barrier_cells", _P),
+        ("n_layers", ctypes.c_int32), ("coupling", ctypes.c_int32), ("evac_trigger", ctypes.c_int32),
+        ("seed", ctypes.c_uint64), ("ped_noise", ctypes.c_double),
+    ]
+
+
+class _State(ctypes.Structure):
+    _fields_ = [
+        ("h", _P), ("hu", _P), ("hv", _P), ("z", _P), ("bflux", _P),
+        ("t_ticks", ctypes.c_int64), ("step", ctypes.c_int64),
+        ("wet", ctypes.c_int32), ("pad0", ctypes.c_int32),
+        ("total_bags", ctypes.c_int64), ("applied_layers", ctypes.c_int64),
+        ("neg_depth", ctypes.c_int64), ("n_exited", ctypes.c_int64),
+        ("hist", ctypes.c_int64 * 5),
+        ("np", ctypes.c_int32), ("pad1", ctypes.c_int32),
+        ("px", _P), ("py", _P), ("pvx", _P), ("pvy", _P), ("pv0", _P),
+        ("pid", _P), ("ptimer", _P),
+        ("prole", _P), ("pfsm", _P), ("phr", _P), ("pexit", _P),
+        ("nav_exit", _P), ("nav_depot", _P), ("nav_barrier", _P),
+        ("last_dt_ticks", ctypes.c_int64),
+    ]
+
+
+def _ptr(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.c_void_p) if a.size else None
+
+
+def _f32(v) -> float:
+    """The FP32 value a scalar parameter takes on the GPU path, as a double."""
+    return float(np.float32(v))
+
+
+class Oracle:
+    """Holds one scenario's state in FP64 and advances it with the C oracle."""
+
+    def __init__(self, sc):
+        L = lib()
+        self.sc = sc
+        nx, ny = sc.nx, sc.ny
+        self._keep = []
+
+        def keep(a):
+            a = np.ascontiguousarray(a)
+            self._keep.append(a)
+            return a
+
+        self.hydro_t = keep(np.asarray(sc.hydro_t, np.float64))
+        self.hydro_h = keep(np.asarray(sc.hydro_h, np.float64))
+        self.bc = [keep(np.asarray(b, np.uint8)) for b in (sc.bc_s, sc.bc_n, sc.bc_w, sc.bc_e)]
+        self.n0 = keep(np.asarray(sc.n0, np.float64).reshape(-1))
+        self.walkable = keep(np.asarray(sc.walkable, np.uint8).reshape(-1))
+        self.exit_mask = keep(np.asarray(sc.exit_mask, np.uint8).reshape(-1))
+        self.depot = keep(np.asarray(sc.depot_cells, np.int32))
+        self.barrier = keep(np.asarray(sc.barrier_cells, np.int32))
+        P = _Params()
+        P.nx, P.ny = nx, ny
+        P.dx, P.g, P.cfl = _f32(sc.dx), _f32(sc.g), _f32(sc.cfl)
+        P.t_end_ticks = int(round(sc.t_end * TICKS))
+        P.n_hydro = self.hydro_t.size
+        P.hydro_t, P.hydro_h = _ptr(self.hydro_t), _ptr(self.hydro_h)
+        P.bc_s, P.bc_n, P.bc_w, P.bc_e = [_ptr(b) for b in self.bc]
+        P.n0, P.walkable, P.exit_mask = _ptr(self.n0), _ptr(self.walkable), _ptr(self.exit_mask)
+        P.n_depot, P.depot_cells = self.depot.size, _ptr(self.depot)
+        P.n_barrier, P.barrier_cells = self.barrier.size, _ptr(self.barrier)
+        P.n_layers, P.coupling, P.evac_trigger = int(sc.n_layers), int(sc.coupling), int(sc.evac_trigger)
+        P.seed = int(sc.seed) & ((1 << 64) - 1)
+        P.ped_noise = _f32(sc.ped_noise)
+        self.P = P
+        n = nx * ny
+        self.h = keep(np.asarray(sc.h, np.float64).reshape(-1).copy())
+        self.hu = keep(np.asarray(sc.hu, np.float64).reshape(-1).copy())
+        self.hv = keep(np.asarray(sc.hv, np.float64).reshape(-1).copy())
+        self.z = keep(np.asarray(sc.z, np.float64).reshape(-1).copy())
+        self.bflux = keep(np.zeros(2 * nx + 2 * ny, np.float64))
+        p = sc.peds
+        m = int(p["x"].shape[0])
+        self.px = keep(p["x"].astype(np.float64))
+        self.py = keep(p["y"].astype(np.float64))
+        self.pvx = keep(p["vx"].astype(np.float64))
+        self.pvy = keep(p["vy"].astype(np.float64))
+        self.pv0 = keep(p["v0"].astype(np.float64))
+        self.pid = keep(np.arange(m, dtype=np.int32))
+        self.ptimer = keep(p["timer"].astype(np.int32))
+        self.prole = keep(p["role"].astype(np.uint8))
+        self.pfsm = keep(p["fsm"].astype(np.uint8))
+        self.phr = keep(np.zeros(m, np.uint8))
+        self.pexit = keep(np.zeros(m, np.uint8))
+        self.nav_exit = keep(np.zeros(n, np.uint8))
+        self.nav_depot = keep(np.zeros(n, np.uint8))
+        self.nav_barrier = keep(np.zeros(n, np.uint8))
+        S = _State()
+        S.h, S.hu, S.hv, S.z, S.bflux = [_ptr(a) for a in (self.h, self.hu, self.hv, self.z, self.bflux)]
+        S.np = m
+        S.px, S.py, S.pvx, S.pvy, S.pv0 = [_ptr(a) for a in (self.px, self.py, self.pvx, self.pvy, self.pv0)]
+        S.pid, S.ptimer = _ptr(self.pid), _ptr(self.ptimer)
+        S.prole, S.pfsm, S.phr, S.pexit = [_ptr(a) for a in (self.prole, self.pfsm, self.phr, self.pexit)]
+        S.nav_exit, S.nav_depot, S.nav_barrier = _ptr(self.nav_exit), _ptr(self.nav_depot), _ptr(self.nav_barrier)
+        self.S = S
+        L.or_prepare(ctypes.byref(P), ctypes.byref(S))
+
+    # -- stepping ---------------------------------------------------------
+    def step(self, n: int = 1) -> int:
+        return int(lib().or_run(ctypes.byref(self.P), ctypes.byref(self.S), int(n)))
+
+    def step_dt(self) -> int:
+        return int(lib().or_step(ctypes.byref(self.P), ctypes.byref(self.S)))
+
+    # -- views -----------------------------------------------------------
+    @property
+    def t(self) -> float:
+        return self.S.t_ticks / TICKS
+
+    @property
+    def t_ticks(self) -> int:
+        return int(self.S.t_ticks)
+
+    @property
+    def nstep(self) -> int:
+        return int(self.S.step)
+
+    def field(self, name):
+        return getattr(self, name).reshape(self.sc.ny, self.sc.nx)
+
+    def mass(self) -> float:
+        return float(lib().or_mass(ctypes.byref(self.P), ctypes.byref(self.S)))
+
+    def boundary_inflow(self) -> float:
+        return float(self.bflux.sum())
+
+    def dt_ticks_now(self) -> int:
+        return int(lib().or_dt_ticks(ctypes.byref(self.P), _ptr(self.h), _ptr(self.hu), _ptr(self.hv),
+                                     self.S.t_ticks))
+
+    def counters(self) -> dict:
+        S = self.S
+        return dict(t_ticks=int(S.t_ticks), step=int(S.step), wet=int(S.wet), total_bags=int(S.total_bags),
+                    applied_layers=int(S.applied_layers), neg_depth=int(S.neg_depth),
+                    n_exited=int(S.n_exited), hist=[int(v) for v in S.hist],
+                    n_active=int((self.pexit == 0).sum()))
+
+    def peds(self) -> dict:
+        return dict(x=self.px.copy(), y=self.py.copy(), vx=self.pvx.copy(), vy=self.pvy.copy(),
+                    role=self.prole.copy(), fsm=self.pfsm.copy(), hr=self.phr.copy(),
+                    exited=self.pexit.copy(), timer=self.ptimer.copy())
+
+
+# -- pointwise functions, used by the pins ------------------------------------
+def hll(g, hL, unL, utL, hR, unR, utR):
+    out = (ctypes.c_double * 3)()
+    lib().or_hll(g, hL, unL, utL, hR, unR, utR, out)
+    return np.array(out[:])
+
+
+def hr_state(h, hu, hv) -> int:
+    return int(lib().or_hr_state(h, hu, hv))
+
+
+def philox4x64(counter, key):
+    c = (ctypes.c_uint64 * 4)(*[int(v) & ((1 << 64) - 1) for v in counter])
+    k = (ctypes.c_uint64 * 2)(*[int(v) & ((1 << 64) - 1) for v in key])
+    o = (ctypes.c_uint64 * 4)()
+    lib().or_philox4x64(c, k, o)
+    return [int(v) for v in o]
+
+
+def nav_field(walkable: np.ndarray, goal: np.ndarray):
+    ny, nx = walkable.shape
+    w = np.ascontiguousarray(walkable, np.uint8)
+    gl = np.ascontiguousarray(goal, np.uint8)
+    d = np.zeros((ny, nx), np.uint8)
+    dist = np.zeros((ny, nx), np.int32)
+    lib().or_nav_field(nx, ny, _ptr(w), _ptr(gl), _ptr(d), _ptr(dist))
+    return d, dist
+
+
+def bags_per_cell(dx: float) -> int:
+    return int(lib().or_bags_per_cell(_f32(dx)))

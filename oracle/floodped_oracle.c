@@ -552,7 +552,8 @@ int64_t or_ped_step(const or_params *P, or_state *S, int64_t dt_ticks, int32_t w
             double d2 = rx * rx + ry * ry;
             if (d2 >= OR_R * OR_R || d2 <= 0.0) continue;
             double d = sqrt(d2);
-            double fm = OR_A * exp((2.0 * OR_RB - d) / OR_B);
+            /* exponential repulsion shifted to vanish at the neighbour radius */
+            double fm = OR_A * (exp((2.0 * OR_RB - d) / OR_B) - exp((2.0 * OR_RB - OR_R) / OR_B));
             Fx += fm * rx / d;
             Fy += fm * ry / d;
         }

@@ -73,6 +73,7 @@ static const double OR_A = 2.0;       /* repulsion strength (m/s^2) */
 static const double OR_B = 0.3;       /* repulsion range (m) */
 static const double OR_RB = 0.25;     /* body radius (m) */
 static const double OR_R = 1.0;       /* neighbour radius (m) */
+static const double OR_SIDE = 0.5;    /* share of the repulsion turned sideways when approaching */
 static const double OR_SPEED[5] = {0.0, 1.8, 0.9, 0.45, 0.0};  /* Table 1; [0] unused (dry: own v0) */
 static const int32_t OR_T_PICK = 30 * 1048576;   /* 30 s pick-up wait */
 static const int32_t OR_T_DROP = 30 * 1048576;   /* 30 s drop wait */
@@ -556,6 +557,11 @@ int64_t or_ped_step(const or_params *P, or_state *S, int64_t dt_ticks, int32_t w
             double fm = OR_A * (exp((2.0 * OR_RB - d) / OR_B) - exp((2.0 * OR_RB - OR_R) / OR_B));
             Fx += fm * rx / d;
             Fy += fm * ry / d;
+            /* walking toward the neighbour: part of the push turns to the walker's right */
+            if (vdx * rx + vdy * ry < 0.0) {
+                Fx += OR_SIDE * fm * (-ry / d);
+                Fy += OR_SIDE * fm * (rx / d);
+            }
         }
         /* relaxation toward the desired velocity, capped at the state's speed */
         double a = dt / OR_TAU; if (a > 1.0) a = 1.0;

@@ -546,6 +546,7 @@ int64_t or_ped_step(const or_params *P, or_state *S, int64_t dt_ticks, int32_t w
         }
         /* repulsion from every other present pedestrian within the neighbour radius */
         double Fx = 0.0, Fy = 0.0;
+        const double vdn = sqrt(vdx * vdx + vdy * vdy);
         for (int32_t q = 0; q < np; ++q) {
             if (q == p || S->pexit[q]) continue;
             double rx = x - S->px[q], ry = y - S->py[q];
@@ -557,10 +558,14 @@ int64_t or_ped_step(const or_params *P, or_state *S, int64_t dt_ticks, int32_t w
             double fm = OR_A * (exp((2.0 * OR_RB - d) / OR_B) - exp((2.0 * OR_RB - OR_R) / OR_B));
             Fx += fm * rx / d;
             Fy += fm * ry / d;
-            /* walking toward the neighbour: part of the push turns to the walker's right */
-            if (vdx * rx + vdy * ry < 0.0) {
-                Fx += OR_SIDE * fm * (-ry / d);
-                Fy += OR_SIDE * fm * (rx / d);
+            /* walking toward the neighbour: part of the push turns to the walker's right,
+             * weighted by the cosine of the approach angle (continuous in every input) */
+            if (vdn > 0.0) {
+                double w = -(vdx * rx + vdy * ry) / (vdn * d);
+                if (w > 0.0) {
+                    Fx += OR_SIDE * w * fm * (-ry / d);
+                    Fy += OR_SIDE * w * fm * (rx / d);
+                }
             }
         }
         /* relaxation toward the desired velocity, capped at the state's speed */

@@ -1,0 +1,350 @@
+#!/usr/bin/env python3
+"""Benchmark of the coupled flood-pedestrian step on B300.
+
+Workload (default): the synthetic shopping centre, 512 x 512 cells of 0.5 m,
+10,000 evacuees, evacuee roughness coupling on, triangular depth hydrograph
+peaking at 1.0 m.  The simulation is first advanced 1024 steps (flood inside,
+evacuation under way) and that state is kept as a snapshot.  One benchmark
+step = restore the snapshot (untimed), flush L2, then 256 coupled simulation
+steps through the C ABI (``fp_step``), timed with CUDA events on the
+simulation's stream.
+
+metric  coupled cell-updates/s + ped-updates/s (cells x steps + pedestrians
+        advanced, over the timed region).
+e2e     the same through the C ABI with host buffers: pinned-host state and
+        pedestrian upload, 256 steps, read-back of h, hu, hv, pedestrians and
+        counters, all inside the timed region.
+roofline the flood kernel (HBM-bound stencil), 34 algorithmic bytes per cell
+        update, its launch duration from CUDA events in a profiled pass.
+cpu_baseline the FP64 C oracle on a bounded sample of the same workload.
+
+``--impl reference`` times the oracle itself (host cores) on the same workload.
+Multi-GPU (torchrun): every rank runs an independent replica (weak scaling).
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+CHUNK = 256            # simulation steps per benchmark step
+PRE_STEPS = 1024       # steps before the snapshot
+FLOOD_BYTES_PER_CELL = 34  # read h,hu,hv,z,n0 (20 B) + occupancy (2 B); write h,hu,hv (12 B)
+METRIC = "coupled cell-updates/s + ped-updates/s"
+UNIT = "updates/s"
+
+
+def workload(seed):
+    import scenarios
+    return scenarios.shopping_centre(512, 0.5, 10_000, 0, seed, 1800.0)
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+class ClockSampler:
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.hw_slowdown",
+              "clocks_event_reasons.hw_thermal_slowdown", "clocks_event_reasons.sw_thermal_slowdown",
+              "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) != len(self.FIELDS):
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def flood_traffic():
+    """DRAM bytes per flood launch from the committed ncu summary, null if the kernel changed since."""
+    p = os.path.join(ROOT, "profiles", "flood_kernel_ncu.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    src = open(os.path.join(ROOT, "paper_1908_05232_b300", "csrc", "flood.cu"), "rb").read()
+    if d.get("flood_cu_sha256") != hashlib.sha256(src).hexdigest():
+        return None
+    return d.get("dram_bytes_per_launch_full_size")
+
+
+# --------------------------------------------------------------------------
+# oracle (CPU) timing
+# --------------------------------------------------------------------------
+def oracle_rate(n_steps, seed=2):
+    import oracle
+    sc = workload(seed)
+    o = oracle.Oracle(sc)
+    t0 = time.perf_counter()
+    upd = 0
+    for _ in range(n_steps):
+        active = int((o.pexit == 0).sum())
+        if o.step_dt() == 0:
+            break
+        upd += sc.n_cells + active
+    el = time.perf_counter() - t0
+    return upd / el, el
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    sc = workload(2)
+    o = oracle.Oracle(sc)
+    per = args.ref_sample_steps
+    for _ in range(args.warmup):
+        o.step(per)
+    t_total, upd = 0.0, 0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        for _ in range(per):
+            active = int((o.pexit == 0).sum())
+            if o.step_dt() == 0:
+                break
+            upd += sc.n_cells + active
+        t_total += time.perf_counter() - t0
+    value = upd / t_total
+    sample = "%d oracle steps per benchmark step of the 512x512 / 10k-evacuee shopping centre" % per
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "shopping_centre_512", "nx": 512, "ny": 512, "dx": 0.5, "n_peds": 10000},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------
+# our arm
+# --------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import paper_1908_05232_b300 as P
+    from paper_1908_05232_b300 import _native as N
+    P.build.build()
+    sc = workload(2 + rank)
+    stream = torch.cuda.Stream()
+    sim = P.from_scenario(sc, tile_rows=args.tile_rows)
+    N.fp_set_stream(sim.h, stream.cuda_stream)
+    sim.step(PRE_STEPS)
+    sim.synchronize()
+    # device snapshot
+    dev = torch.device("cuda", local)
+    snap = [torch.empty((sc.ny, sc.nx), dtype=torch.float32, device=dev) for _ in range(3)]
+    for k, t in zip((N.FP_FIELD_H, N.FP_FIELD_HU, N.FP_FIELD_HV), snap):
+        N.fp_read_state(sim.h, k, t)
+    c0 = sim.counters()
+    peds_all = sim.peds()
+    active = peds_all[peds_all["exited"] == 0].copy()
+    peds_dev = torch.from_numpy(active.view(np.uint8).copy()).to(dev)
+    n_act = int(active.shape[0])
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > 126 MB L2
+
+    def restore():
+        N.fp_set_state(sim.h, snap[0], snap[1], snap[2])
+        N.fp_clear_pedestrians(sim.h)
+        N._check(N.lib().fp_add_pedestrians(sim.h, N._VP(peds_dev.data_ptr()), n_act), sim.h)
+        sim.n_total = n_act
+        N.fp_set_time(sim.h, c0["t_ticks"], c0["step"])
+        sim.counters()  # runs the post-restore preparation outside the timed region
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        stream.synchronize()
+
+    def one(timed):
+        restore()
+        a = sim.counters()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(CHUNK)
+        e1.record(stream)
+        e1.synchronize()
+        b = sim.counters()
+        if b["error_flags"]:
+            raise RuntimeError("device error flags %#x" % b["error_flags"])
+        upd = (b["step"] - a["step"]) * sc.n_cells + (b["ped_updates"] - a["ped_updates"])
+        return e0.elapsed_time(e1), upd, b["step"] - a["step"]
+
+    for _ in range(args.warmup):
+        one(False)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    ms_list, upd_total, steps_total = [], 0, 0
+    for _ in range(args.steps):
+        ms, upd, st = one(True)
+        ms_list.append(ms)
+        upd_total += upd
+        steps_total += st
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    t_sec = sum(ms_list) / 1e3
+    if ws > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([t_sec], dtype=torch.float64, device=dev)
+        uu = torch.tensor([float(upd_total)], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        dist.all_reduce(uu, op=dist.ReduceOp.SUM)
+        t_sec, upd_all = float(tt.item()), float(uu.item())
+    else:
+        upd_all = float(upd_total)
+    value = upd_all / t_sec
+
+    # profiled pass: CUDA events around each kernel group, same workload
+    restore()
+    N.fp_set_profiling(sim.h, 1)
+    sim.step(CHUNK)
+    prof = sim.profile()
+    N.fp_set_profiling(sim.h, 0)
+    flood_ms = prof["flood_ms"] / max(prof["steps"], 1)
+    hbm, peak_kind = peaks()
+    achieved = sc.n_cells * FLOOD_BYTES_PER_CELL / (flood_ms * 1e-3) / 1e9
+    traffic = flood_traffic()
+
+    # end to end through the C ABI with pinned host buffers
+    host_state = [t.cpu().pin_memory() for t in snap]
+    host_peds = torch.from_numpy(active.view(np.uint8).copy()).pin_memory()
+    out_state = [torch.empty((sc.ny, sc.nx), dtype=torch.float32).pin_memory() for _ in range(3)]
+    out_peds = torch.empty(n_act * 32, dtype=torch.uint8).pin_memory()
+    e2e_t = 0.0
+    for it in range(args.warmup + args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        stream.synchronize()
+        t0 = time.perf_counter()
+        N.fp_set_state(sim.h, host_state[0], host_state[1], host_state[2])
+        N.fp_clear_pedestrians(sim.h)
+        N._check(N.lib().fp_add_pedestrians(sim.h, N._VP(host_peds.data_ptr()), n_act), sim.h)
+        sim.n_total = n_act
+        N.fp_set_time(sim.h, c0["t_ticks"], c0["step"])
+        sim.step(CHUNK)
+        for k, t in zip((N.FP_FIELD_H, N.FP_FIELD_HU, N.FP_FIELD_HV), out_state):
+            N.fp_read_state(sim.h, k, t)
+        N._check(N.lib().fp_read_state(sim.h, N.FP_FIELD_PEDS, N._VP(out_peds.data_ptr()), n_act * 32), sim.h)
+        sim.counters()
+        el = time.perf_counter() - t0
+        if it >= args.warmup:
+            e2e_t += el
+    # every iteration replays the same 256 steps from the snapshot (deterministic),
+    # so it performs the same updates as a device-timed iteration
+    e2e_value = (upd_total / args.steps) * args.steps / e2e_t
+    h2d = 3 * sc.n_cells * 4 + n_act * 32
+    d2h = 3 * sc.n_cells * 4 + n_act * 32 + 112
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        rate, el = oracle_rate(args.cpu_sample_steps)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "first %d coupled steps of the same 512x512 / 10k-evacuee workload, FP64 C oracle, "
+                         "single thread (%.1f s)" % (args.cpu_sample_steps, el)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": statistics.mean(ms_list), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "shopping_centre_512", "nx": sc.nx, "ny": sc.ny, "dx": sc.dx,
+                       "n_peds": sc.n_peds, "n_peds_active_at_snapshot": n_act,
+                       "sim_steps_per_bench_step": CHUNK, "snapshot_after_steps": PRE_STEPS,
+                       "parallelism": "replicas" if ws > 1 else "single",
+                       "l2": "flushed between timed iterations (256 MB write); the 512x512 working set "
+                             "(~10 MB) is L2-resident within an iteration",
+                       "tile_rows": args.tile_rows or 16},
+            "breakdown": {"cell_updates_per_s": steps_total * sc.n_cells / (sum(ms_list) / 1e3),
+                          "ped_updates_per_s": (upd_total - steps_total * sc.n_cells) / (sum(ms_list) / 1e3),
+                          "profiled_ms_per_step": {k: prof[k] / max(prof["steps"], 1)
+                                                   for k in ("hash_ms", "flood_ms", "ped_chain_ms", "step_ms")}},
+            "roofline": {"kernel": "flood_kernel<16>", "bound": "hbm", "achieved": achieved, "peak": hbm,
+                         "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
+                         "bytes_per_cell_update": FLOOD_BYTES_PER_CELL,
+                         "note": "512x512 fits in L2; frac is against HBM"},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "clocks": clocks,
+            "gpu_launches": 5 * CHUNK * args.steps,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--tile-rows", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-steps", type=int, default=100)
+    ap.add_argument("--ref-sample-steps", type=int, default=8)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,194 @@
+/*
+ * floodped.h -- C ABI of the B300 coupled flood-pedestrian simulation library
+ * (libfloodped.so).
+ *
+ * One simulation step advances, on one GPU and from the same state at step n,
+ *   (a) every hydrodynamic cell by the first-order finite-volume shallow-water
+ *       update of Eq. (2) of the paper (Section 2.2) with the global CFL time
+ *       step of Section 3,
+ *   (b) every pedestrian by the rules of Sections 2.3-2.4 (Table 1 hazard
+ *       states, navigation toward the emergency exit / sandbag storage /
+ *       barrier, repulsion from neighbours, responders' sandbag cycle),
+ *   (c) the two-way coupling of Section 2.4: evacuees per cell raise the
+ *       Manning n of the next flood update (n_M + N_p n_M, N_p <= 20) and
+ *       completed sandbag layers raise the barrier cells' bed.
+ *
+ * Conventions (all entry points):
+ *   - Grids are row-major, index c = j * nx + i; i runs west->east along x,
+ *     j south->north along y; cell (i, j) covers [i dx, (i+1) dx) x [j dx, (j+1) dx).
+ *   - Array arguments may be host or device pointers (unified addressing
+ *     decides); the library copies them and never keeps a caller pointer.
+ *   - Every call returns FP_OK (0) or a negative FP_E* code; fp_last_error()
+ *     gives a message.  No C++ exception crosses the ABI.  A handle is not
+ *     thread-safe; distinct handles are independent.
+ *   - Time is kept as int64 ticks of 2^-20 s (the step's dt is quantised down
+ *     to whole ticks).
+ */
+#ifndef FLOODPED_H
+#define FLOODPED_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define FP_OK 0
+#define FP_EINVAL (-1)    /* bad argument or size */
+#define FP_ENOMEM (-2)    /* device allocation failed */
+#define FP_ECUDA (-3)     /* a CUDA call failed */
+#define FP_ETIMEOUT (-4)  /* a bounded device-side wait gave up */
+#define FP_ENAN (-5)      /* non-finite state detected */
+#define FP_EOVERFLOW (-6) /* a per-cell counter or capacity overflowed */
+
+/* boundary condition codes, one per boundary cell (Section 3.1) */
+#define FP_BC_WALL 0         /* reflective wall */
+#define FP_BC_TRANSMISSIVE 1 /* zero-gradient ("slip" outflow) */
+#define FP_BC_INFLOW 2       /* ghost at rest with the hydrograph depth */
+
+#define FP_EDGE_SOUTH 0 /* row j = 0, nx codes */
+#define FP_EDGE_NORTH 1 /* row j = ny-1, nx codes */
+#define FP_EDGE_WEST 2  /* column i = 0, ny codes */
+#define FP_EDGE_EAST 3  /* column i = nx-1, ny codes */
+
+/* pedestrian roles (Section 2.4) and states */
+#define FP_ROLE_EVACUEE 0
+#define FP_ROLE_RESPONDER 1
+#define FP_HR_DRY 0      /* depth below 1 mm */
+#define FP_HR_LOW 1      /* Table 1: HR in [0, 0.75), 1.8 m/s */
+#define FP_HR_MEDIUM 2   /* [0.75, 1.5), 0.9 m/s */
+#define FP_HR_HIGH 3     /* [1.5, 2.5), 0.45 m/s */
+#define FP_HR_HIGHEST 4  /* >= 2.5, 0 m/s */
+#define FP_TASK_TO_DEPOT 0
+#define FP_TASK_PICKUP 1
+#define FP_TASK_TO_BARRIER 2
+#define FP_TASK_DROP 3
+#define FP_TASK_DONE 4
+
+/* fields for fp_read_state */
+#define FP_FIELD_H 0        /* float[ny*nx] depth h (m) */
+#define FP_FIELD_HU 1       /* float[ny*nx] unit discharge hu (m^2/s) */
+#define FP_FIELD_HV 2       /* float[ny*nx] unit discharge hv (m^2/s) */
+#define FP_FIELD_Z 3        /* float[ny*nx] bed elevation z (m), barrier raises included */
+#define FP_FIELD_PEDS 4     /* fp_ped[n_peds_total], indexed by pedestrian id */
+#define FP_FIELD_COUNTERS 5 /* one fp_counters */
+#define FP_FIELD_NAV 6      /* uint8[3*ny*nx]: exit, storage, barrier direction codes */
+#define FP_FIELD_MASS 7     /* double[2]: water volume sum h dx^2 (m^3), net boundary inflow volume (m^3) */
+#define FP_FIELD_PROFILE 8  /* double[5]: profiled steps, then total ms of hash_count, flood, the
+                               scan -> gather -> pedestrian chain, and whole steps (see fp_set_profiling) */
+
+/* Simulation set-up.  Sizes: nx, ny >= 1; max_peds >= 0. */
+typedef struct fp_config {
+    int32_t nx, ny;     /* cells along x and y */
+    float dx;           /* cell side (m); cells are square */
+    float g;            /* gravity (m/s^2) */
+    float cfl;          /* Courant number (Section 3) */
+    float ped_noise;    /* amplitude of the random term of the desired velocity (m/s) */
+    double t_end;       /* simulated end time (s); steps past it do nothing */
+    uint64_t seed;      /* key of the counter-based random generator */
+    int32_t max_peds;   /* pedestrian capacity */
+    int32_t coupling;   /* 1: evacuees raise Manning n (Section 2.4), 0: off */
+    int32_t evac_trigger; /* 0: evacuees head for the exit from t = 0;
+                             1: only once some cell holds water (Section 2.4) */
+    int32_t tile_rows;  /* flood tile height: 8, 16 or 32 (0 = 16) */
+    int32_t reserved[4];
+} fp_config;
+
+/* One pedestrian record (32 bytes).  On input, id is ignored: ids are given
+ * in order of addition starting at 0.  timer_ticks is the remaining wait of a
+ * responder picking up or dropping a sandbag. */
+typedef struct fp_ped {
+    float x, y;      /* position (m) */
+    float vx, vy;    /* velocity (m/s) */
+    uint32_t id;
+    uint8_t role;    /* FP_ROLE_* */
+    uint8_t task;    /* FP_TASK_* (responders) */
+    uint8_t hr;      /* FP_HR_* of the last step */
+    uint8_t exited;  /* 1 once through the emergency exit */
+    int32_t timer_ticks;
+    float v0;        /* walking speed on dry ground (m/s) */
+} fp_ped;
+
+typedef struct fp_counters {
+    int64_t t_ticks;        /* simulated time */
+    int64_t step;           /* steps taken with dt > 0 */
+    int64_t n_active;       /* pedestrians still in the domain */
+    int64_t n_exited;
+    int64_t total_bags;     /* sandbags dropped so far */
+    int64_t applied_layers; /* barrier cell-layers completed and applied to z */
+    int64_t neg_depth;      /* negative depths clamped to 0 (expected 0) */
+    int64_t hist[5];        /* pedestrians per FP_HR_* state in the last step */
+    int32_t wet;            /* 1 once any cell held >= 1 mm of water */
+    uint32_t error_flags;   /* device-side error bits (0 = none) */
+    int64_t ped_updates;    /* pedestrians advanced, summed over steps */
+} fp_counters;
+
+typedef struct fp_sim fp_sim; /* opaque handle, owned by the library */
+
+/* Create a simulation: validates *cfg, allocates device memory on the current
+ * CUDA device.  Terrain defaults to flat, dry, walkable, n = 0.01, all walls. */
+int fp_sim_create(const fp_config *cfg, fp_sim **out);
+
+/* Run subsequent work on a caller CUDA stream (cudaStream_t, may be NULL for the
+ * library's own stream).  The caller keeps ownership of the stream. */
+int fp_set_stream(fp_sim *sim, void *cuda_stream);
+
+/* Terrain (Section 2.1 flood agent z, n_M; navigation map walkable cells and
+ * emergency exit cells).  z, n0: float[ny*nx]; walkable, exit_mask: uint8[ny*nx]
+ * (non-zero = yes).  Rebuilds the navigation fields. */
+int fp_set_terrain(fp_sim *sim, const float *z, const float *n0, const uint8_t *walkable,
+                   const uint8_t *exit_mask);
+
+/* Boundary codes of one edge (FP_EDGE_*): uint8[nx] for south/north, uint8[ny]
+ * for west/east, each FP_BC_*. */
+int fp_set_boundary(fp_sim *sim, int32_t edge, const uint8_t *codes);
+
+/* Inflow depth hydrograph (Section 3.1, depth form): n >= 1 points (t_k, h_k),
+ * t increasing (s), h >= 0 (m); linear between points, constant outside. */
+int fp_set_hydrograph(fp_sim *sim, const double *t, const double *h, int32_t n);
+
+/* Sandbag storage cells and the ordered barrier cells (Section 2.4, Fig. 3-right),
+ * flat cell indices; n_layers = N_L layers of one bag thickness (0.25 m). */
+int fp_set_goals(fp_sim *sim, const int32_t *depot_cells, int32_t n_depot,
+                 const int32_t *barrier_cells, int32_t n_barrier, int32_t n_layers);
+
+/* Water state U = [h, hu, hv] (Eq. 1), float[ny*nx] each; h >= 0. */
+int fp_set_state(fp_sim *sim, const float *h, const float *hu, const float *hv);
+
+/* Set simulated time (ticks) and step index (the random generator's counter). */
+int fp_set_time(fp_sim *sim, int64_t t_ticks, int64_t step);
+
+/* Append count pedestrians; each must stand in a walkable cell inside the domain. */
+int fp_add_pedestrians(fp_sim *sim, const fp_ped *peds, int32_t count);
+
+/* Remove all pedestrians and reset the exit and sandbag counters. */
+int fp_clear_pedestrians(fp_sim *sim);
+
+/* Enqueue n_steps coupled steps on the simulation's stream (asynchronous). */
+int fp_step(fp_sim *sim, int32_t n_steps);
+
+/* Profiling mode (on != 0): fp_step launches every step directly (no CUDA
+ * graph) with CUDA events around the kernel groups and synchronises at its end;
+ * FP_FIELD_PROFILE returns the accumulated times.  Turning it on resets them. */
+int fp_set_profiling(fp_sim *sim, int32_t on);
+
+/* Wait for enqueued work; returns FP_ETIMEOUT / FP_EOVERFLOW / FP_ENAN when the
+ * device raised the corresponding error bit. */
+int fp_synchronize(fp_sim *sim);
+
+/* Copy one FP_FIELD_* into dst (host or device), bytes >= the field's size.
+ * Synchronises the stream. */
+int fp_read_state(fp_sim *sim, int32_t which, void *dst, size_t bytes);
+
+/* Free the handle and its device memory. */
+int fp_destroy(fp_sim *sim);
+
+/* Last error message of the handle (or of the last failed create if sim is NULL). */
+const char *fp_last_error(const fp_sim *sim);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FLOODPED_H */

@@ -1,0 +1,260 @@
+"""ctypes binding of ``libfloodped.so`` (include/floodped.h).
+
+Argument marshalling only: every step of the simulation runs in the CUDA
+kernels of the library.  Arrays may be numpy arrays (host) or CUDA torch
+tensors (device); the library copies them.  If the library is missing the
+import of a simulation fails loudly -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+FP_OK, FP_EINVAL, FP_ENOMEM, FP_ECUDA, FP_ETIMEOUT, FP_ENAN, FP_EOVERFLOW = 0, -1, -2, -3, -4, -5, -6
+FP_FIELD_H, FP_FIELD_HU, FP_FIELD_HV, FP_FIELD_Z = 0, 1, 2, 3
+FP_FIELD_PEDS, FP_FIELD_COUNTERS, FP_FIELD_NAV, FP_FIELD_MASS, FP_FIELD_PROFILE = 4, 5, 6, 7, 8
+FP_EDGE_SOUTH, FP_EDGE_NORTH, FP_EDGE_WEST, FP_EDGE_EAST = 0, 1, 2, 3
+TICKS = 1 << 20
+
+PED_DTYPE = np.dtype([("x", "<f4"), ("y", "<f4"), ("vx", "<f4"), ("vy", "<f4"), ("id", "<u4"),
+                      ("role", "u1"), ("task", "u1"), ("hr", "u1"), ("exited", "u1"),
+                      ("timer_ticks", "<i4"), ("v0", "<f4")])
+assert PED_DTYPE.itemsize == 32
+
+
+class FpConfig(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("dx", ctypes.c_float), ("g", ctypes.c_float),
+                ("cfl", ctypes.c_float), ("ped_noise", ctypes.c_float), ("t_end", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("max_peds", ctypes.c_int32), ("coupling", ctypes.c_int32),
+                ("evac_trigger", ctypes.c_int32), ("tile_rows", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
+
+
+class FpCounters(ctypes.Structure):
+    _fields_ = [("t_ticks", ctypes.c_int64), ("step", ctypes.c_int64), ("n_active", ctypes.c_int64),
+                ("n_exited", ctypes.c_int64), ("total_bags", ctypes.c_int64), ("applied_layers", ctypes.c_int64),
+                ("neg_depth", ctypes.c_int64), ("hist", ctypes.c_int64 * 5), ("wet", ctypes.c_int32),
+                ("error_flags", ctypes.c_uint32), ("ped_updates", ctypes.c_int64)]
+
+
+class FloodPedError(RuntimeError):
+    pass
+
+
+_lib = None
+_VP = ctypes.c_void_p
+
+
+def lib():
+    """Load the CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_build.LIB):
+            raise FloodPedError("libfloodped.so is not built: run paper_1908_05232_b300.build.build()")
+        L = ctypes.CDLL(_build.LIB)
+        sigs = {
+            "fp_sim_create": [_VP, _VP], "fp_set_stream": [_VP, _VP],
+            "fp_set_terrain": [_VP] * 5, "fp_set_boundary": [_VP, ctypes.c_int32, _VP],
+            "fp_set_hydrograph": [_VP, _VP, _VP, ctypes.c_int32],
+            "fp_set_goals": [_VP, _VP, ctypes.c_int32, _VP, ctypes.c_int32, ctypes.c_int32],
+            "fp_set_state": [_VP] * 4, "fp_set_time": [_VP, ctypes.c_int64, ctypes.c_int64],
+            "fp_add_pedestrians": [_VP, _VP, ctypes.c_int32], "fp_clear_pedestrians": [_VP],
+            "fp_step": [_VP, ctypes.c_int32], "fp_synchronize": [_VP], "fp_set_profiling": [_VP, ctypes.c_int32],
+            "fp_read_state": [_VP, ctypes.c_int32, _VP, ctypes.c_size_t], "fp_destroy": [_VP],
+        }
+        for name, args in sigs.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = ctypes.c_int
+        L.fp_last_error.argtypes = [_VP]
+        L.fp_last_error.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):  # torch tensor (host or device)
+        assert a.is_contiguous()
+        return _VP(a.data_ptr())
+    assert isinstance(a, np.ndarray) and a.flags["C_CONTIGUOUS"]
+    return _VP(a.ctypes.data) if a.size else None
+
+
+def _check(rc, handle=None):
+    if rc != FP_OK:
+        msg = lib().fp_last_error(handle)
+        raise FloodPedError("floodped error %d: %s" % (rc, msg.decode() if msg else ""))
+
+
+# -- C-ABI entry points, same names ------------------------------------------
+def fp_sim_create(cfg: FpConfig):
+    h = _VP()
+    _check(lib().fp_sim_create(ctypes.byref(cfg), ctypes.byref(h)))
+    return h
+
+
+def fp_set_stream(h, stream_ptr):
+    _check(lib().fp_set_stream(h, _VP(stream_ptr) if stream_ptr else None), h)
+
+
+def fp_set_terrain(h, z, n0, walkable, exit_mask):
+    _check(lib().fp_set_terrain(h, _ptr(z), _ptr(n0), _ptr(walkable), _ptr(exit_mask)), h)
+
+
+def fp_set_boundary(h, edge, codes):
+    _check(lib().fp_set_boundary(h, edge, _ptr(codes)), h)
+
+
+def fp_set_hydrograph(h, t, depth):
+    t = np.ascontiguousarray(t, np.float64)
+    depth = np.ascontiguousarray(depth, np.float64)
+    _check(lib().fp_set_hydrograph(h, _ptr(t), _ptr(depth), int(t.size)), h)
+
+
+def fp_set_goals(h, depot, barrier, n_layers):
+    depot = np.ascontiguousarray(depot, np.int32)
+    barrier = np.ascontiguousarray(barrier, np.int32)
+    _check(lib().fp_set_goals(h, _ptr(depot), depot.size, _ptr(barrier), barrier.size, int(n_layers)), h)
+
+
+def fp_set_state(h, depth, hu, hv):
+    _check(lib().fp_set_state(h, _ptr(depth), _ptr(hu), _ptr(hv)), h)
+
+
+def fp_set_time(h, t_ticks, step):
+    _check(lib().fp_set_time(h, int(t_ticks), int(step)), h)
+
+
+def fp_add_pedestrians(h, recs):
+    n = int(recs.shape[0]) if hasattr(recs, "shape") else len(recs)
+    _check(lib().fp_add_pedestrians(h, _ptr(recs), n), h)
+
+
+def fp_clear_pedestrians(h):
+    _check(lib().fp_clear_pedestrians(h), h)
+
+
+def fp_step(h, n):
+    _check(lib().fp_step(h, int(n)), h)
+
+
+def fp_set_profiling(h, on):
+    _check(lib().fp_set_profiling(h, 1 if on else 0), h)
+
+
+def fp_synchronize(h):
+    _check(lib().fp_synchronize(h), h)
+
+
+def fp_read_state(h, which, dst):
+    nbytes = dst.numel() * dst.element_size() if hasattr(dst, "data_ptr") else dst.nbytes
+    _check(lib().fp_read_state(h, int(which), _ptr(dst), nbytes), h)
+    return dst
+
+
+def fp_destroy(h):
+    _check(lib().fp_destroy(h))
+
+
+# -- convenience wrapper ------------------------------------------------------
+def ped_records(peds: dict) -> np.ndarray:
+    n = int(peds["x"].shape[0])
+    r = np.zeros(n, PED_DTYPE)
+    for k_src, k_dst in (("x", "x"), ("y", "y"), ("vx", "vx"), ("vy", "vy"), ("role", "role"),
+                         ("fsm", "task"), ("timer", "timer_ticks"), ("v0", "v0")):
+        r[k_dst] = peds[k_src]
+    return r
+
+
+class Simulation:
+    """One simulation handle; methods call the C ABI one to one."""
+
+    def __init__(self, cfg: FpConfig):
+        self.cfg = cfg
+        self.h = fp_sim_create(cfg)
+        self.nx, self.ny = cfg.nx, cfg.ny
+        self.n_total = 0
+
+    def close(self):
+        if self.h is not None:
+            fp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n=1):
+        fp_step(self.h, n)
+
+    def synchronize(self):
+        fp_synchronize(self.h)
+
+    def add_pedestrians(self, recs):
+        fp_add_pedestrians(self.h, recs)
+        self.n_total += int(recs.shape[0])
+
+    def field(self, which):
+        out = np.empty((self.ny, self.nx), np.float32)
+        return fp_read_state(self.h, which, out)
+
+    def peds(self):
+        out = np.zeros(self.n_total, PED_DTYPE)
+        if self.n_total:
+            fp_read_state(self.h, FP_FIELD_PEDS, out)
+        return out
+
+    def counters(self) -> dict:
+        c = FpCounters()
+        _check(lib().fp_read_state(self.h, FP_FIELD_COUNTERS, ctypes.byref(c), ctypes.sizeof(c)), self.h)
+        return dict(t_ticks=c.t_ticks, step=c.step, n_active=c.n_active, n_exited=c.n_exited,
+                    total_bags=c.total_bags, applied_layers=c.applied_layers, neg_depth=c.neg_depth,
+                    hist=list(c.hist), wet=c.wet, error_flags=c.error_flags, ped_updates=c.ped_updates)
+
+    def profile(self) -> dict:
+        out = np.zeros(5, np.float64)
+        fp_read_state(self.h, FP_FIELD_PROFILE, out)
+        return dict(steps=out[0], hash_ms=out[1], flood_ms=out[2], ped_chain_ms=out[3], step_ms=out[4])
+
+    def nav(self):
+        out = np.empty((3, self.ny, self.nx), np.uint8)
+        return fp_read_state(self.h, FP_FIELD_NAV, out)
+
+    def mass(self):
+        out = np.zeros(2, np.float64)
+        fp_read_state(self.h, FP_FIELD_MASS, out)
+        return float(out[0]), float(out[1])
+
+
+def config_for(sc, max_peds=None, tile_rows=0) -> FpConfig:
+    c = FpConfig()
+    c.nx, c.ny, c.dx, c.g, c.cfl = sc.nx, sc.ny, sc.dx, sc.g, sc.cfl
+    c.ped_noise, c.t_end, c.seed = sc.ped_noise, sc.t_end, int(sc.seed) & ((1 << 64) - 1)
+    c.max_peds = sc.n_peds if max_peds is None else max_peds
+    c.coupling, c.evac_trigger, c.tile_rows = int(sc.coupling), int(sc.evac_trigger), int(tile_rows)
+    return c
+
+
+def from_scenario(sc, max_peds=None, tile_rows=0, peds=True) -> Simulation:
+    """Create a simulation and load a ``scenarios.Scenario`` into it through the C ABI."""
+    sim = Simulation(config_for(sc, max_peds, tile_rows))
+    c = np.ascontiguousarray
+    fp_set_terrain(sim.h, c(sc.z, np.float32), c(sc.n0, np.float32), c(sc.walkable, np.uint8),
+                   c(sc.exit_mask, np.uint8))
+    for edge, codes in ((FP_EDGE_SOUTH, sc.bc_s), (FP_EDGE_NORTH, sc.bc_n), (FP_EDGE_WEST, sc.bc_w),
+                        (FP_EDGE_EAST, sc.bc_e)):
+        fp_set_boundary(sim.h, edge, c(codes, np.uint8))
+    fp_set_hydrograph(sim.h, sc.hydro_t, sc.hydro_h)
+    fp_set_goals(sim.h, sc.depot_cells, sc.barrier_cells, sc.n_layers)
+    fp_set_state(sim.h, c(sc.h, np.float32), c(sc.hu, np.float32), c(sc.hv, np.float32))
+    if peds and sc.n_peds:
+        sim.add_pedestrians(ped_records(sc.peds))
+    return sim

@@ -1,0 +1,703 @@
+// floodped.cu -- host side of the C ABI declared in include/floodped.h.
+//
+// Owns the device memory of one simulation, builds the navigation fields
+// (Section 2.1: navigation agents pointing pedestrians toward the exit, the
+// sandbag storage and the barrier) with a breadth-first search, encodes the
+// TMA descriptors of the flood kernel, and enqueues coupled steps.  A step is
+// five kernels on two streams:
+//     hash_count --+--> flood (stream 1)                      --+--> next step
+//                  +--> scan -> gather -> ped_step (stream 2) --+
+// Both branches read the state at step n, so they overlap.  Runs of 64 steps
+// are captured once into a CUDA graph per starting clock slot and replayed.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "floodped.h"
+#include "fp_common.cuh"
+
+namespace {
+
+constexpr int kGraphSteps = 64;
+std::string g_create_error;
+
+// 4-connected breadth-first distance over walkable cells from the goal set;
+// each reachable cell gets the code (0..7 = E, N, W, S, NE, NW, SW, SE) of the
+// neighbour with the strictly smallest distance, earliest in that order on
+// ties, diagonals only past two walkable side cells; goal cells get 8 and
+// unreachable cells 255.
+void build_nav(int nx, int ny, const std::vector<uint8_t> &walk, const std::vector<uint8_t> &goal,
+               std::vector<uint8_t> &code) {
+    static const int ox[8] = {1, 0, -1, 0, 1, -1, -1, 1};
+    static const int oy[8] = {0, 1, 0, -1, 1, 1, -1, -1};
+    const size_t n = (size_t)nx * ny;
+    std::vector<int> dist(n, -1), frontier;
+    frontier.reserve(n);
+    for (size_t c = 0; c < n; ++c)
+        if (goal[c]) { dist[c] = 0; frontier.push_back((int)c); }
+    for (size_t head = 0; head < frontier.size(); ++head) {
+        const int c = frontier[head], i = c % nx, j = c / nx;
+        for (int k = 0; k < 4; ++k) {
+            const int a = i + ox[k], b = j + oy[k];
+            if (a < 0 || b < 0 || a >= nx || b >= ny) continue;
+            const int d = b * nx + a;
+            if (walk[d] && dist[d] < 0) { dist[d] = dist[c] + 1; frontier.push_back(d); }
+        }
+    }
+    code.assign(n, 255);
+    for (int j = 0; j < ny; ++j) {
+        for (int i = 0; i < nx; ++i) {
+            const int c = j * nx + i;
+            if (goal[c]) { code[c] = 8; continue; }
+            if (dist[c] < 0) continue;
+            int best = -1, bestd = dist[c];
+            for (int k = 0; k < 8; ++k) {
+                const int a = i + ox[k], b = j + oy[k];
+                if (a < 0 || b < 0 || a >= nx || b >= ny) continue;
+                const int d = dist[b * nx + a];
+                if (d < 0) continue;
+                if (k >= 4 && (!walk[j * nx + a] || !walk[b * nx + i])) continue;
+                if (d < bestd) { bestd = d; best = k; }
+            }
+            if (best >= 0) code[c] = (uint8_t)best;
+        }
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void *p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+}  // namespace
+
+struct fp_sim {
+    fp_config cfg{};
+    FpSim S{};
+    int device = 0;
+    cudaStream_t stream = nullptr, stream2 = nullptr;
+    bool own_stream = true;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    int par = 0, slot = 0;
+    bool need_prepare = true, pending_time = false;
+    long long pend_t = 0, pend_step = 0;
+    int tile_rows = 16;
+    FpTmaSet tma[2];
+    cudaGraphExec_t graphs[4] = {nullptr, nullptr, nullptr, nullptr};
+    int n_total = 0;
+    std::string err;
+    std::vector<void *> allocs;
+    std::vector<uint8_t> walk_h, exit_h, bc_h[4];
+    std::vector<int> depot_h, barrier_h;
+    uint4 *read_buf = nullptr;
+    bool profiling = false;
+    std::vector<cudaEvent_t> prof_ev;  // 4 per profiled step
+    double prof[5] = {0, 0, 0, 0, 0};  // steps, hash ms, flood ms, pedestrian chain ms, step ms
+
+    int fail(int code, const std::string &msg) {
+        err = msg;
+        return code;
+    }
+    int cuda_fail(cudaError_t e, const char *what) {
+        err = std::string(what) + ": " + cudaGetErrorString(e);
+        return FP_ECUDA;
+    }
+    template <class T>
+    T *dalloc(size_t count) {
+        void *p = nullptr;
+        if (cudaMalloc(&p, count * sizeof(T) + 16) != cudaSuccess) return nullptr;
+        cudaMemset(p, 0, count * sizeof(T) + 16);
+        allocs.push_back(p);
+        return static_cast<T *>(p);
+    }
+    void drop_graphs() {
+        for (auto &g : graphs)
+            if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+    }
+    size_t plane_elems() const { return (size_t)S.px * (size_t)(S.ny + 2); }
+};
+
+static int encode_tma(fp_sim *s) {
+    auto enc = get_encode();
+    if (!enc) return s->fail(FP_ECUDA, "cuTensorMapEncodeTiled entry point unavailable");
+    const FpSim &S = s->S;
+    cuuint64_t dims[2] = {(cuuint64_t)S.px, (cuuint64_t)(S.ny + 2)};
+    cuuint64_t strides[1] = {(cuuint64_t)S.px * 4};
+    cuuint32_t box[2] = {(cuuint32_t)(FP_TX + 8), (cuuint32_t)(s->tile_rows + 2)};
+    cuuint32_t es[2] = {1, 1};
+    for (int p = 0; p < 2; ++p) {
+        float *ptrs[4] = {S.h[p], S.hu[p], S.hv[p], S.z};
+        CUtensorMap *maps[4] = {&s->tma[p].h, &s->tma[p].hu, &s->tma[p].hv, &s->tma[p].z};
+        for (int k = 0; k < 4; ++k) {
+            CUresult r = enc(maps[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, ptrs[k], dims, strides, box, es,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) return s->fail(FP_ECUDA, "cuTensorMapEncodeTiled failed");
+        }
+    }
+    return FP_OK;
+}
+
+static int upload_nav(fp_sim *s) {
+    const int nx = s->S.nx, ny = s->S.ny;
+    const size_t n = (size_t)nx * ny;
+    std::vector<uint8_t> goal(n), code;
+    for (int g = 0; g < 3; ++g) {
+        std::fill(goal.begin(), goal.end(), 0);
+        if (g == 0) {
+            for (size_t c = 0; c < n; ++c) goal[c] = s->exit_h[c] ? 1 : 0;
+        } else {
+            const std::vector<int> &cells = g == 1 ? s->depot_h : s->barrier_h;
+            for (int c : cells) goal[c] = 1;
+        }
+        build_nav(nx, ny, s->walk_h, goal, code);
+        cudaError_t e = cudaMemcpy(const_cast<unsigned char *>(s->S.nav[g]), code.data(), n, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return s->cuda_fail(e, "nav upload");
+    }
+    return FP_OK;
+}
+
+static void update_inflow_flag(fp_sim *s) {
+    int f = 0;
+    for (int e = 0; e < 4; ++e)
+        for (uint8_t c : s->bc_h[e]) f |= (c == FP_BC_INFLOW);
+    s->S.has_inflow = f;
+}
+
+// copy a caller grid (host or device) into a padded device plane
+static cudaError_t put_plane(fp_sim *s, float *dst, const float *src) {
+    const FpSim &S = s->S;
+    return cudaMemcpy2DAsync(dst + S.px + FP_PADX, (size_t)S.px * 4, src, (size_t)S.nx * 4, (size_t)S.nx * 4, S.ny,
+                             cudaMemcpyDefault, s->stream);
+}
+
+static cudaError_t get_plane(fp_sim *s, void *dst, const float *src) {
+    const FpSim &S = s->S;
+    return cudaMemcpy2DAsync(dst, (size_t)S.nx * 4, src + S.px + FP_PADX, (size_t)S.px * 4, (size_t)S.nx * 4, S.ny,
+                             cudaMemcpyDefault, s->stream);
+}
+
+static int prepare(fp_sim *s) {
+    cudaError_t e;
+    FpClock ring[4];
+    memset(ring, 0, sizeof(ring));
+    if (s->pending_time) {
+        ring[s->slot].t = s->pend_t;
+        ring[s->slot].step = s->pend_step;
+        s->pending_time = false;
+    } else {
+        FpClock cur;
+        e = cudaMemcpy(&cur, &s->S.clock[s->slot], sizeof(cur), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return s->cuda_fail(e, "clock read");
+        ring[s->slot].t = cur.t;
+        ring[s->slot].step = cur.step;
+    }
+    e = cudaMemcpyAsync(s->S.clock, ring, sizeof(ring), cudaMemcpyHostToDevice, s->stream);
+    if (e != cudaSuccess) return s->cuda_fail(e, "clock write");
+    fp_launch_init_clock(s->S, s->par, s->slot, s->stream);
+    e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return s->cuda_fail(e, "prepare");
+    s->need_prepare = false;
+    return FP_OK;
+}
+
+// One coupled step.  ev (profiling only): 4 events -- before hash_count, after
+// it, after the flood kernel (stream 1), after the pedestrian chain (stream 2).
+static void launch_step(fp_sim *s, int par, int slot, cudaEvent_t *ev = nullptr) {
+    const FpSim &S = s->S;
+    if (ev) cudaEventRecord(ev[0], s->stream);
+    fp_launch_hash_count(S, s->stream);
+    cudaEventRecord(s->ev_fork, s->stream);
+    if (ev) cudaEventRecord(ev[1], s->stream);
+    cudaStreamWaitEvent(s->stream2, s->ev_fork, 0);
+    fp_launch_flood(S, &s->tma[par], par, slot, s->tile_rows, s->stream);
+    if (ev) cudaEventRecord(ev[2], s->stream);
+    fp_launch_scan(S, s->stream2);
+    fp_launch_gather(S, s->stream2);
+    fp_launch_ped_step(S, par, slot, s->stream2);
+    if (ev) cudaEventRecord(ev[3], s->stream2);
+    cudaEventRecord(s->ev_join, s->stream2);
+    cudaStreamWaitEvent(s->stream, s->ev_join, 0);
+}
+
+static int step_profiled(fp_sim *s, int n) {
+    if ((int)s->prof_ev.size() < 4 * n) {
+        for (int k = (int)s->prof_ev.size(); k < 4 * n; ++k) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return s->fail(FP_ECUDA, "event create");
+            s->prof_ev.push_back(e);
+        }
+    }
+    for (int k = 0; k < n; ++k) {
+        launch_step(s, s->par, s->slot, &s->prof_ev[4 * k]);
+        s->par ^= 1;
+        s->slot = (s->slot + 1) & 3;
+    }
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return s->cuda_fail(e, "profiled steps");
+    for (int k = 0; k < n; ++k) {
+        cudaEvent_t *ev = &s->prof_ev[4 * k];
+        float a = 0, b = 0, c = 0, d = 0;
+        cudaEventElapsedTime(&a, ev[0], ev[1]);
+        cudaEventElapsedTime(&b, ev[1], ev[2]);
+        cudaEventElapsedTime(&c, ev[1], ev[3]);
+        cudaEventElapsedTime(&d, ev[0], ev[2]);
+        s->prof[0] += 1;
+        s->prof[1] += a;
+        s->prof[2] += b;
+        s->prof[3] += c;
+        s->prof[4] += std::max(d, a + c);
+    }
+    return FP_OK;
+}
+
+extern "C" {
+
+int fp_sim_create(const fp_config *cfg, fp_sim **out) {
+    if (!cfg || !out) { g_create_error = "null argument"; return FP_EINVAL; }
+    *out = nullptr;
+    const fp_config &c = *cfg;
+    if (c.nx < 1 || c.ny < 1 || c.nx > (1 << 16) || c.ny > (1 << 16) || !(c.dx > 0.0f) || !(c.g > 0.0f) ||
+        !(c.cfl > 0.0f) || c.cfl > 1.0f || c.max_peds < 0 || c.max_peds > (1 << 26) || !(c.t_end >= 0.0) ||
+        !(c.ped_noise >= 0.0f) ||
+        (c.tile_rows != 0 && c.tile_rows != 8 && c.tile_rows != 16 && c.tile_rows != 32)) {
+        g_create_error = "invalid fp_config";
+        return FP_EINVAL;
+    }
+    fp_sim *s = new fp_sim();
+    s->cfg = c;
+    cudaGetDevice(&s->device);
+    FpSim &S = s->S;
+    S.nx = c.nx;
+    S.ny = c.ny;
+    S.px = ((c.nx + 3) / 4) * 4 + 2 * FP_PADX;
+    S.dx = c.dx;
+    S.g = c.g;
+    S.cfl = c.cfl;
+    S.ped_noise = c.ped_noise;
+    S.t_end = (long long)llround(c.t_end * 1048576.0);
+    S.seed = c.seed;
+    S.coupling = c.coupling ? 1 : 0;
+    S.evac_trigger = c.evac_trigger ? 1 : 0;
+    S.cap = c.max_peds;
+    S.hk = std::max(1, (int)std::ceil(1.0 / (double)c.dx));
+    S.nbx = (c.nx + S.hk - 1) / S.hk;
+    S.nby = (c.ny + S.hk - 1) / S.hk;
+    S.nbins = S.nbx * S.nby;
+    S.bpc = (int)std::ceil(((double)c.dx * (double)c.dx) / (0.40 * 0.30));
+    s->tile_rows = c.tile_rows ? c.tile_rows : 16;
+    const size_t pe = s->plane_elems(), n = (size_t)c.nx * c.ny;
+    bool ok = true;
+    for (int p = 0; p < 2; ++p) {
+        ok &= (S.h[p] = s->dalloc<float>(pe)) != nullptr;
+        ok &= (S.hu[p] = s->dalloc<float>(pe)) != nullptr;
+        ok &= (S.hv[p] = s->dalloc<float>(pe)) != nullptr;
+    }
+    ok &= (S.z = s->dalloc<float>(pe)) != nullptr;
+    ok &= (S.n0 = s->dalloc<float>(pe)) != nullptr;
+    ok &= (S.occ = s->dalloc<unsigned short>(pe + 2)) != nullptr;
+    unsigned char *bcd[4];
+    for (int e = 0; e < 4; ++e) {
+        const int len = e < 2 ? c.nx : c.ny;
+        ok &= (bcd[e] = s->dalloc<unsigned char>(len)) != nullptr;
+        S.bc[e] = bcd[e];
+        s->bc_h[e].assign(len, FP_BC_WALL);
+    }
+    unsigned char *walk = s->dalloc<unsigned char>(n), *exitm = s->dalloc<unsigned char>(n);
+    ok &= walk && exitm;
+    S.walk = walk;
+    S.exitm = exitm;
+    for (int g = 0; g < 3; ++g) ok &= (S.nav[g] = s->dalloc<unsigned char>(n)) != nullptr;
+    double *ht = s->dalloc<double>(FP_MAX_HYDRO), *hh = s->dalloc<double>(FP_MAX_HYDRO);
+    ok &= ht && hh;
+    S.hydro_t = ht;
+    S.hydro_h = hh;
+    ok &= (S.clock = s->dalloc<FpClock>(4)) != nullptr;
+    ok &= (S.cnt = s->dalloc<FpCounters>(1)) != nullptr;
+    const size_t cap = (size_t)std::max(1, c.max_peds);
+    ok &= (S.pedA = s->dalloc<uint4>(2 * cap)) != nullptr;
+    ok &= (S.pedB = s->dalloc<uint4>(2 * cap)) != nullptr;
+    ok &= (S.arch = s->dalloc<uint4>(2 * cap)) != nullptr;
+    ok &= (s->read_buf = s->dalloc<uint4>(2 * cap)) != nullptr;
+    ok &= (S.bin_count = s->dalloc<int>((size_t)S.nbins + 1)) != nullptr;
+    ok &= (S.bin_start = s->dalloc<int>((size_t)S.nbins + 2)) != nullptr;
+    ok &= (S.pkey = s->dalloc<int>(cap)) != nullptr;
+    ok &= (S.pslot = s->dalloc<int>(cap)) != nullptr;
+    ok &= (S.scan_flags = s->dalloc<unsigned long long>((size_t)fp_scan_tiles(S.nbins))) != nullptr;
+    ok &= (S.bflux = s->dalloc<double>(2 * (size_t)c.nx + 2 * (size_t)c.ny)) != nullptr;
+    ok &= (S.partials = s->dalloc<double>(148 * 4)) != nullptr;
+    if (!ok) {
+        g_create_error = "device allocation failed";
+        fp_destroy(s);
+        return FP_ENOMEM;
+    }
+    // defaults: flat dry walkable terrain, n = 0.01, walls, no hydrograph
+    s->walk_h.assign(n, 1);
+    s->exit_h.assign(n, 0);
+    std::vector<float> n0(n, 0.01f);
+    cudaMemset(walk, 1, n);
+    cudaMemcpy2D(S.n0 + S.px + FP_PADX, (size_t)S.px * 4, n0.data(), (size_t)c.nx * 4, (size_t)c.nx * 4, c.ny,
+                 cudaMemcpyHostToDevice);
+    cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+    cudaStreamCreateWithFlags(&s->stream2, cudaStreamNonBlocking);
+    cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming);
+    cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming);
+    int rc = upload_nav(s);
+    if (rc == FP_OK) rc = encode_tma(s);
+    if (rc == FP_OK) {
+        cudaError_t ea = fp_flood_init_attributes();
+        if (ea != cudaSuccess) rc = s->cuda_fail(ea, "flood kernel attributes");
+    }
+    cudaError_t e = cudaDeviceSynchronize();
+    if (rc == FP_OK && e != cudaSuccess) rc = s->cuda_fail(e, "create");
+    if (rc != FP_OK) {
+        g_create_error = s->err;
+        fp_destroy(s);
+        return rc;
+    }
+    *out = s;
+    return FP_OK;
+}
+
+int fp_set_stream(fp_sim *s, void *cuda_stream) {
+    if (!s) return FP_EINVAL;
+    cudaStreamSynchronize(s->stream);
+    if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
+    if (cuda_stream) {
+        s->stream = static_cast<cudaStream_t>(cuda_stream);
+        s->own_stream = false;
+    } else {
+        cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+        s->own_stream = true;
+    }
+    s->drop_graphs();
+    return FP_OK;
+}
+
+int fp_set_terrain(fp_sim *s, const float *z, const float *n0, const uint8_t *walkable, const uint8_t *exit_mask) {
+    if (!s || !z || !n0 || !walkable || !exit_mask) return s ? s->fail(FP_EINVAL, "null terrain array") : FP_EINVAL;
+    const size_t n = (size_t)s->S.nx * s->S.ny;
+    cudaError_t e;
+    if ((e = put_plane(s, s->S.z, z)) != cudaSuccess) return s->cuda_fail(e, "z upload");
+    if ((e = put_plane(s, s->S.n0, n0)) != cudaSuccess) return s->cuda_fail(e, "n0 upload");
+    if ((e = cudaMemcpyAsync(const_cast<unsigned char *>(s->S.walk), walkable, n, cudaMemcpyDefault, s->stream)) !=
+        cudaSuccess)
+        return s->cuda_fail(e, "walkable upload");
+    if ((e = cudaMemcpyAsync(const_cast<unsigned char *>(s->S.exitm), exit_mask, n, cudaMemcpyDefault,
+                             s->stream)) != cudaSuccess)
+        return s->cuda_fail(e, "exit upload");
+    if ((e = cudaMemcpy(s->walk_h.data(), walkable, n, cudaMemcpyDefault)) != cudaSuccess)
+        return s->cuda_fail(e, "walkable copy");
+    if ((e = cudaMemcpy(s->exit_h.data(), exit_mask, n, cudaMemcpyDefault)) != cudaSuccess)
+        return s->cuda_fail(e, "exit copy");
+    for (auto &v : s->walk_h) v = v ? 1 : 0;
+    if ((e = cudaStreamSynchronize(s->stream)) != cudaSuccess) return s->cuda_fail(e, "terrain");
+    return upload_nav(s);
+}
+
+int fp_set_boundary(fp_sim *s, int32_t edge, const uint8_t *codes) {
+    if (!s) return FP_EINVAL;
+    if (edge < 0 || edge > 3 || !codes) return s->fail(FP_EINVAL, "bad edge or codes");
+    const int len = edge < 2 ? s->S.nx : s->S.ny;
+    std::vector<uint8_t> h(len);
+    cudaError_t e = cudaMemcpy(h.data(), codes, len, cudaMemcpyDefault);
+    if (e != cudaSuccess) return s->cuda_fail(e, "boundary copy");
+    for (uint8_t c : h)
+        if (c > FP_BC_INFLOW) return s->fail(FP_EINVAL, "boundary code out of range");
+    s->bc_h[edge] = h;
+    e = cudaMemcpy(const_cast<unsigned char *>(s->S.bc[edge]), h.data(), len, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return s->cuda_fail(e, "boundary upload");
+    update_inflow_flag(s);
+    s->drop_graphs();
+    return FP_OK;
+}
+
+int fp_set_hydrograph(fp_sim *s, const double *t, const double *h, int32_t n) {
+    if (!s) return FP_EINVAL;
+    if (!t || !h || n < 1 || n > FP_MAX_HYDRO) return s->fail(FP_EINVAL, "hydrograph needs 1..64 points");
+    std::vector<double> th(n), hh(n);
+    cudaMemcpy(th.data(), t, n * sizeof(double), cudaMemcpyDefault);
+    cudaMemcpy(hh.data(), h, n * sizeof(double), cudaMemcpyDefault);
+    for (int k = 0; k < n; ++k) {
+        if (!(hh[k] >= 0.0) || !std::isfinite(th[k])) return s->fail(FP_EINVAL, "hydrograph values");
+        if (k && !(th[k] > th[k - 1])) return s->fail(FP_EINVAL, "hydrograph times must increase");
+    }
+    cudaMemcpy(const_cast<double *>(s->S.hydro_t), th.data(), n * sizeof(double), cudaMemcpyHostToDevice);
+    cudaError_t e = cudaMemcpy(const_cast<double *>(s->S.hydro_h), hh.data(), n * sizeof(double), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return s->cuda_fail(e, "hydrograph upload");
+    s->S.n_hydro = n;
+    s->drop_graphs();
+    s->need_prepare = true;
+    return FP_OK;
+}
+
+int fp_set_goals(fp_sim *s, const int32_t *depot, int32_t n_depot, const int32_t *barrier, int32_t n_barrier,
+                 int32_t n_layers) {
+    if (!s) return FP_EINVAL;
+    const int n = s->S.nx * s->S.ny;
+    if (n_depot < 0 || n_barrier < 0 || n_layers < 0 || (n_depot && !depot) || (n_barrier && !barrier))
+        return s->fail(FP_EINVAL, "bad goal arguments");
+    std::vector<int> dh(n_depot), bh(n_barrier);
+    if (n_depot) cudaMemcpy(dh.data(), depot, n_depot * sizeof(int), cudaMemcpyDefault);
+    if (n_barrier) cudaMemcpy(bh.data(), barrier, n_barrier * sizeof(int), cudaMemcpyDefault);
+    for (int c : dh)
+        if (c < 0 || c >= n) return s->fail(FP_EINVAL, "depot cell out of range");
+    for (int c : bh)
+        if (c < 0 || c >= n) return s->fail(FP_EINVAL, "barrier cell out of range");
+    s->depot_h = dh;
+    s->barrier_h = bh;
+    if (n_barrier) {
+        int *d = s->dalloc<int>(n_barrier);
+        if (!d) return s->fail(FP_ENOMEM, "barrier allocation");
+        cudaMemcpy(d, bh.data(), n_barrier * sizeof(int), cudaMemcpyHostToDevice);
+        s->S.barrier = d;
+    } else {
+        s->S.barrier = nullptr;
+    }
+    s->S.nb = n_barrier;
+    s->S.n_layers = n_layers;
+    s->drop_graphs();
+    return upload_nav(s);
+}
+
+int fp_set_state(fp_sim *s, const float *h, const float *hu, const float *hv) {
+    if (!s) return FP_EINVAL;
+    if (!h || !hu || !hv) return s->fail(FP_EINVAL, "null state array");
+    const int p = s->par;
+    cudaError_t e;
+    if ((e = put_plane(s, s->S.h[p], h)) != cudaSuccess) return s->cuda_fail(e, "h upload");
+    if ((e = put_plane(s, s->S.hu[p], hu)) != cudaSuccess) return s->cuda_fail(e, "hu upload");
+    if ((e = put_plane(s, s->S.hv[p], hv)) != cudaSuccess) return s->cuda_fail(e, "hv upload");
+    cudaMemsetAsync(s->S.bflux, 0, (2 * (size_t)s->S.nx + 2 * (size_t)s->S.ny) * sizeof(double), s->stream);
+    s->need_prepare = true;
+    return FP_OK;
+}
+
+int fp_set_time(fp_sim *s, int64_t t_ticks, int64_t step) {
+    if (!s) return FP_EINVAL;
+    if (t_ticks < 0 || step < 0) return s->fail(FP_EINVAL, "negative time or step");
+    s->pending_time = true;
+    s->pend_t = t_ticks;
+    s->pend_step = step;
+    s->need_prepare = true;
+    return FP_OK;
+}
+
+int fp_add_pedestrians(fp_sim *s, const fp_ped *peds, int32_t count) {
+    if (!s) return FP_EINVAL;
+    if (count < 0 || (count > 0 && !peds)) return s->fail(FP_EINVAL, "bad pedestrian arguments");
+    if (count == 0) return FP_OK;
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return s->cuda_fail(e, "sync");
+    FpCounters c;
+    cudaMemcpy(&c, s->S.cnt, sizeof(c), cudaMemcpyDeviceToHost);
+    if (s->n_total + count > s->S.cap || c.nB + count > s->S.cap)
+        return s->fail(FP_EOVERFLOW, "pedestrian capacity exceeded");
+    e = cudaMemcpy(s->S.pedB + 2 * (size_t)c.nB, peds, (size_t)count * sizeof(fp_ped), cudaMemcpyDefault);
+    if (e != cudaSuccess) return s->cuda_fail(e, "pedestrian upload");
+    fp_launch_assign_ids(s->S, c.nB, s->n_total, count, s->stream);
+    e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return s->cuda_fail(e, "assign ids");
+    FpCounters c2;
+    cudaMemcpy(&c2, s->S.cnt, sizeof(c2), cudaMemcpyDeviceToHost);
+    if (c2.bad_ped) {
+        int zero = 0;
+        cudaMemcpy(&s->S.cnt->bad_ped, &zero, sizeof(int), cudaMemcpyHostToDevice);
+        return s->fail(FP_EINVAL, "a pedestrian stands outside the domain or in a non-walkable cell");
+    }
+    const int nb = c.nB + count;
+    cudaMemcpy(&s->S.cnt->nB, &nb, sizeof(int), cudaMemcpyHostToDevice);
+    s->n_total += count;
+    return FP_OK;
+}
+
+int fp_clear_pedestrians(fp_sim *s) {
+    if (!s) return FP_EINVAL;
+    cudaStreamSynchronize(s->stream);
+    FpCounters c;
+    cudaMemcpy(&c, s->S.cnt, sizeof(c), cudaMemcpyDeviceToHost);
+    c.nA = c.nB = 0;
+    c.total_bags = c.bags_snap = c.applied = 0;
+    c.n_exited = 0;
+    for (auto &v : c.hist) v = 0;
+    cudaError_t e = cudaMemcpy(s->S.cnt, &c, sizeof(c), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return s->cuda_fail(e, "clear");
+    s->n_total = 0;
+    return FP_OK;
+}
+
+int fp_step(fp_sim *s, int32_t n_steps) {
+    if (!s) return FP_EINVAL;
+    if (n_steps < 0) return s->fail(FP_EINVAL, "negative step count");
+    if (s->need_prepare) {
+        int rc = prepare(s);
+        if (rc != FP_OK) return rc;
+    }
+    if (s->profiling) return step_profiled(s, n_steps);
+    int left = n_steps;
+    while (left > 0) {
+        if (left >= kGraphSteps) {
+            cudaGraphExec_t &g = s->graphs[s->slot];
+            if (!g) {
+                cudaGraph_t graph;
+                cudaError_t e = cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal);
+                if (e != cudaSuccess) return s->cuda_fail(e, "begin capture");
+                int p = s->par, sl = s->slot;
+                for (int k = 0; k < kGraphSteps; ++k) {
+                    launch_step(s, p, sl);
+                    p ^= 1;
+                    sl = (sl + 1) & 3;
+                }
+                e = cudaStreamEndCapture(s->stream, &graph);
+                if (e != cudaSuccess) return s->cuda_fail(e, "end capture");
+                e = cudaGraphInstantiate(&g, graph, 0);
+                cudaGraphDestroy(graph);
+                if (e != cudaSuccess) { g = nullptr; return s->cuda_fail(e, "graph instantiate"); }
+            }
+            cudaError_t e = cudaGraphLaunch(g, s->stream);
+            if (e != cudaSuccess) return s->cuda_fail(e, "graph launch");
+            left -= kGraphSteps;  // 64 steps: parity and slot return to their start values
+        } else {
+            launch_step(s, s->par, s->slot);
+            s->par ^= 1;
+            s->slot = (s->slot + 1) & 3;
+            left -= 1;
+        }
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return s->cuda_fail(e, "step launch");
+    return FP_OK;
+}
+
+int fp_set_profiling(fp_sim *s, int32_t on) {
+    if (!s) return FP_EINVAL;
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return s->cuda_fail(e, "profiling switch");
+    s->profiling = on != 0;
+    for (double &v : s->prof) v = 0.0;
+    return FP_OK;
+}
+
+int fp_synchronize(fp_sim *s) {
+    if (!s) return FP_EINVAL;
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return s->cuda_fail(e, "synchronize");
+    unsigned err = 0;
+    e = cudaMemcpy(&err, &s->S.cnt->err, sizeof(err), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return s->cuda_fail(e, "error word");
+    if (err & FP_ERR_TIMEOUT) return s->fail(FP_ETIMEOUT, "a bounded device wait timed out");
+    if (err & FP_ERR_OCC_OVERFLOW) return s->fail(FP_EOVERFLOW, "more than 65535 evacuees in one cell");
+    if (err & FP_ERR_NAN) return s->fail(FP_ENAN, "non-finite water state");
+    return FP_OK;
+}
+
+int fp_read_state(fp_sim *s, int32_t which, void *dst, size_t bytes) {
+    if (!s) return FP_EINVAL;
+    if (!dst) return s->fail(FP_EINVAL, "null destination");
+    if (s->need_prepare) {
+        int rc = prepare(s);
+        if (rc != FP_OK) return rc;
+    }
+    const FpSim &S = s->S;
+    const size_t n = (size_t)S.nx * S.ny;
+    cudaError_t e = cudaSuccess;
+    switch (which) {
+        case FP_FIELD_H:
+        case FP_FIELD_HU:
+        case FP_FIELD_HV:
+        case FP_FIELD_Z: {
+            if (bytes < n * 4) return s->fail(FP_EINVAL, "destination too small");
+            const float *src = which == FP_FIELD_H ? S.h[s->par] : which == FP_FIELD_HU ? S.hu[s->par]
+                               : which == FP_FIELD_HV ? S.hv[s->par] : S.z;
+            e = get_plane(s, dst, src);
+            break;
+        }
+        case FP_FIELD_PEDS: {
+            if (bytes < (size_t)s->n_total * sizeof(fp_ped)) return s->fail(FP_EINVAL, "destination too small");
+            fp_launch_read_peds(S, s->read_buf, s->n_total, s->stream);
+            if (s->n_total)
+                e = cudaMemcpyAsync(dst, s->read_buf, (size_t)s->n_total * sizeof(fp_ped), cudaMemcpyDefault, s->stream);
+            break;
+        }
+        case FP_FIELD_COUNTERS: {
+            if (bytes < sizeof(fp_counters)) return s->fail(FP_EINVAL, "destination too small");
+            FpCounters c;
+            FpClock k;
+            cudaStreamSynchronize(s->stream);
+            cudaMemcpy(&c, S.cnt, sizeof(c), cudaMemcpyDeviceToHost);
+            e = cudaMemcpy(&k, &S.clock[s->slot], sizeof(k), cudaMemcpyDeviceToHost);
+            fp_counters o;
+            memset(&o, 0, sizeof(o));
+            o.t_ticks = k.t;
+            o.step = k.step;
+            o.n_exited = (int64_t)c.n_exited;
+            o.n_active = (int64_t)s->n_total - (int64_t)c.n_exited;
+            o.total_bags = (int64_t)c.total_bags;
+            o.applied_layers = (int64_t)c.applied;
+            o.neg_depth = (int64_t)c.neg_depth;
+            for (int q = 0; q < 5; ++q) o.hist[q] = (int64_t)c.hist[q];
+            o.wet = k.wet;
+            o.error_flags = c.err;
+            o.ped_updates = (int64_t)c.ped_updates;
+            if (e == cudaSuccess) e = cudaMemcpy(dst, &o, sizeof(o), cudaMemcpyDefault);
+            break;
+        }
+        case FP_FIELD_NAV: {
+            if (bytes < 3 * n) return s->fail(FP_EINVAL, "destination too small");
+            for (int g = 0; g < 3 && e == cudaSuccess; ++g)
+                e = cudaMemcpyAsync(static_cast<uint8_t *>(dst) + g * n, S.nav[g], n, cudaMemcpyDefault, s->stream);
+            break;
+        }
+        case FP_FIELD_MASS: {
+            if (bytes < 2 * sizeof(double)) return s->fail(FP_EINVAL, "destination too small");
+            fp_launch_mass(S, s->par, s->stream);
+            double tmp[2];
+            e = cudaMemcpyAsync(tmp, &S.cnt->mass, 2 * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+            if (e == cudaSuccess) e = cudaMemcpy(dst, tmp, sizeof(tmp), cudaMemcpyDefault);
+            break;
+        }
+        case FP_FIELD_PROFILE: {
+            if (bytes < sizeof(s->prof)) return s->fail(FP_EINVAL, "destination too small");
+            e = cudaMemcpy(dst, s->prof, sizeof(s->prof), cudaMemcpyDefault);
+            break;
+        }
+        default:
+            return s->fail(FP_EINVAL, "unknown field");
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return s->cuda_fail(e, "read_state");
+    return FP_OK;
+}
+
+int fp_destroy(fp_sim *s) {
+    if (!s) return FP_EINVAL;
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    if (s->stream2) cudaStreamSynchronize(s->stream2);
+    s->drop_graphs();
+    for (void *p : s->allocs) cudaFree(p);
+    if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
+    if (s->stream2) cudaStreamDestroy(s->stream2);
+    if (s->ev_fork) cudaEventDestroy(s->ev_fork);
+    if (s->ev_join) cudaEventDestroy(s->ev_join);
+    for (cudaEvent_t e : s->prof_ev) cudaEventDestroy(e);
+    delete s;
+    return FP_OK;
+}
+
+const char *fp_last_error(const fp_sim *s) { return s ? s->err.c_str() : g_create_error.c_str(); }
+
+}  // extern "C"

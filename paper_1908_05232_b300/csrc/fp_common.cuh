@@ -1,0 +1,201 @@
+// fp_common.cuh -- device data layout and shared device helpers of the coupled
+// flood-pedestrian step (Shirvani, Kesserwani & Richmond, arXiv 1908.05232).
+//
+// HBM layout (one simulation):
+//   - water planes h, hu, hv (two copies, ping-pong by step parity), bed z and
+//     base Manning n0: float, padded pitch `px` floats, cell (i, j) stored at
+//     (j + 1) * px + i + FP_PADX.  The 4-float guard columns keep every TMA box
+//     start 16-byte aligned and every 4-cell group a 16-byte vector; guard rows
+//     j = -1 and j = ny are zero and never read as cells.
+//   - occ: uint16 evacuees per cell with the same padding, incremented by the
+//     hash kernel (Section 2.4 N_p) and cleared by the flood kernel that uses it.
+//   - walkable / exit / navigation codes: uint8[ny * nx], unpadded.
+//   - pedestrians: arrays of 32-byte fp_ped records (float4 x,y,vx,vy + uint4
+//     id,meta,timer,v0), "A" sorted by spatial-hash bin, "B" the step output.
+//   - a 4-slot clock ring: slot s holds the time, step index, max wave speed
+//     and wet flag of the step that reads it.
+#pragma once
+#include <stdint.h>
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#define FP_PADX 4
+#define FP_TX 64                 // flood tile width (cells)
+#define FP_TICKS_F 1048576.0f    // ticks per second (2^20)
+#define FP_DT_MAX_TICKS 1048576LL
+#define FP_H_EPS_F 1e-6f         // depth with no velocity (m)
+#define FP_H_DRY_F 1e-3f         // dry pedestrian below 1 mm (m)
+#define FP_NP_CAP 20             // evacuees counted per cell (Section 2.4)
+#define FP_MAX_HYDRO 64
+
+// error bits
+#define FP_ERR_TIMEOUT 1u
+#define FP_ERR_OCC_OVERFLOW 2u
+#define FP_ERR_NAN 4u
+#define FP_ERR_BAD_PED 8u
+
+// pedestrian meta word: role | task << 8 | hr << 16 | exited << 24 (byte lanes of fp_ped)
+#define FP_META_ROLE(m) ((m) & 0xffu)
+#define FP_META_TASK(m) (((m) >> 8) & 0xffu)
+#define FP_META_HR(m) (((m) >> 16) & 0xffu)
+#define FP_META_EXITED(m) (((m) >> 24) & 0xffu)
+#define FP_META(role, task, hr, ex) ((uint32_t)(role) | ((uint32_t)(task) << 8) | ((uint32_t)(hr) << 16) | ((uint32_t)(ex) << 24))
+
+#define FP_AT_GOAL 8
+#define FP_UNREACHABLE 255
+
+struct __align__(16) FpClock {
+    long long t;            // ticks
+    long long step;         // step index (random counter)
+    unsigned int smax_bits; // max over wet cells of max(|u|,|v|) + sqrt(g h), float bits
+    int wet;                // sticky: some cell held >= 1 mm
+    int pad[2];
+};
+
+struct FpCounters {
+    int nA;                           // records in A (sorted, input of the pedestrian step)
+    int nB;                           // records in B (output of the pedestrian step)
+    unsigned long long total_bags;    // bags dropped so far
+    unsigned long long bags_snap;     // total at the start of the step
+    unsigned long long applied;       // barrier cell-layers applied to z
+    unsigned long long n_exited;
+    unsigned long long neg_depth;
+    unsigned int err;
+    unsigned int scan_epoch;          // increments once per hash build
+    unsigned int scan_ticket;         // dynamic tile order of the scan
+    int bad_ped;
+    unsigned long long hist[5];
+    double mass;                      // last mass reduction (m^3)
+    double inflow;                    // net boundary inflow volume (m^3)
+    unsigned int mass_done;           // blocks finished in the mass reduction
+    int pad;
+    unsigned long long ped_updates;   // sum over steps with dt > 0 of pedestrians advanced
+};
+
+struct FpSim {
+    int nx, ny, px;            // cells, padded pitch (floats)
+    int nbx, nby, hk, nbins;   // hash bins (hk x hk cells each), nbins = nbx * nby
+    float dx, g, cfl, ped_noise;
+    long long t_end;           // ticks
+    unsigned long long seed;
+    int coupling, evac_trigger, has_inflow, n_hydro;
+    int cap;                   // pedestrian capacity
+    int nb, n_layers, bpc;     // barrier cells, layers, bags per cell-layer
+    float *h[2], *hu[2], *hv[2];
+    float *z, *n0;
+    unsigned short *occ;
+    const unsigned char *bc[4];
+    const unsigned char *walk, *exitm, *nav[3];
+    const int *barrier;
+    const double *hydro_t, *hydro_h;
+    FpClock *clock;
+    FpCounters *cnt;
+    uint4 *pedA, *pedB;        // 2 x uint4 per record
+    uint4 *arch;               // records by id (exited ones)
+    int *bin_count;            // nbins + 1 (last = exited)
+    int *bin_start;            // nbins + 2
+    int *pkey, *pslot;         // per record of B
+    unsigned long long *scan_flags;  // per scan tile: epoch<<34 | status<<32 | value
+    double *bflux;             // 2 nx + 2 ny inflow volume per boundary face (S, N, W, E)
+    double *partials;          // mass reduction partial sums
+};
+
+__device__ __forceinline__ size_t fp_pidx(const FpSim &S, int i, int j) {
+    return (size_t)(j + 1) * (size_t)S.px + (size_t)(i + FP_PADX);
+}
+
+// Piecewise-linear inflow depth at time t (ticks), evaluated in FP64 with
+// explicit round-to-nearest operations (no contraction) in the same order as
+// any other evaluation of the same table.
+__device__ __forceinline__ double fp_hydro_depth(const FpSim &S, long long t_ticks) {
+    const int n = S.n_hydro;
+    if (n <= 0) return 0.0;
+    const double t = __ddiv_rn((double)t_ticks, 1048576.0);
+    if (t <= S.hydro_t[0]) return S.hydro_h[0];
+    if (t >= S.hydro_t[n - 1]) return S.hydro_h[n - 1];
+    for (int k = 0; k + 1 < n; ++k) {
+        const double t1 = S.hydro_t[k + 1];
+        if (t < t1) {
+            const double t0 = S.hydro_t[k];
+            const double a = __ddiv_rn(__dsub_rn(t, t0), __dsub_rn(t1, t0));
+            return __dadd_rn(S.hydro_h[k], __dmul_rn(__dsub_rn(S.hydro_h[k + 1], S.hydro_h[k]), a));
+        }
+    }
+    return S.hydro_h[n - 1];
+}
+
+// The step's dt in ticks: min(1 s, CFL dx / max wave speed, t_end - t), the
+// max over wet cells of the state it reads and the inflow ghost state.
+// Taken in FP32 with correctly rounded division and square root.
+__device__ __forceinline__ long long fp_dt_ticks(const FpSim &S, const FpClock &c, float h_in) {
+    float smax = __uint_as_float(c.smax_bits);
+    if (S.has_inflow && h_in > FP_H_EPS_F) {
+        const float s = __fsqrt_rn(__fmul_rn(S.g, h_in));
+        smax = fmaxf(smax, s);
+    }
+    long long ticks = FP_DT_MAX_TICKS;
+    if (smax > 0.0f) {
+        const float dtf = __fdiv_rn(__fmul_rn(S.cfl, S.dx), smax);
+        const float tk = __fmul_rn(dtf, FP_TICKS_F);
+        ticks = tk >= FP_TICKS_F ? FP_DT_MAX_TICKS : (long long)tk;
+    }
+    long long left = S.t_end - c.t;
+    if (left < 0) left = 0;
+    return ticks < left ? ticks : left;
+}
+
+// Wave speed of one cell for the CFL bound: max(|u|,|v|) + sqrt(g h).  The max of
+// the two correctly rounded quotients equals the quotient of the larger
+// magnitude, so one division suffices.
+__device__ __forceinline__ float fp_wave_speed(float g, float h, float hu, float hv) {
+    const float a = __fdiv_rn(fmaxf(fabsf(hu), fabsf(hv)), h);
+    return __fadd_rn(a, __fsqrt_rn(__fmul_rn(g, h)));
+}
+
+// Table 1 flood-risk state from HR = (V + 0.5) h, V = max(|u|, |v|), FP32.
+__device__ __forceinline__ int fp_hr_state(float h, float hu, float hv) {
+    if (!(h >= FP_H_DRY_F)) return 0;
+    const float V = __fdiv_rn(fmaxf(fabsf(hu), fabsf(hv)), h);
+    const float hr = __fmul_rn(__fadd_rn(V, 0.5f), h);
+    if (hr < 0.75f) return 1;
+    if (hr < 1.5f) return 2;
+    if (hr < 2.5f) return 3;
+    return 4;
+}
+
+__device__ __forceinline__ int fp_cell_of(float x, float dx) { return (int)floorf(__fdiv_rn(x, dx)); }
+
+// Philox4x64-10 (Salmon et al., SC'11) from its published round function.
+__device__ __forceinline__ void fp_philox4x64(unsigned long long c[4], unsigned long long k0, unsigned long long k1) {
+    const unsigned long long M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+    const unsigned long long W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const unsigned long long hi0 = __umul64hi(M0, c[0]), lo0 = M0 * c[0];
+        const unsigned long long hi1 = __umul64hi(M1, c[2]), lo1 = M1 * c[2];
+        const unsigned long long n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+        k0 += W0; k1 += W1;
+    }
+}
+
+__device__ __forceinline__ void fp_set_err(const FpSim &S, unsigned int bit) { atomicOr(&S.cnt->err, bit); }
+
+// TMA descriptors of the four staged planes for one step parity
+struct FpTmaSet {
+    CUtensorMap h, hu, hv, z;
+};
+
+// launchers (defined in flood.cu / peds.cu)
+void fp_launch_flood(const FpSim &S, const void *tma_set, int par, int slot, int tile_rows, cudaStream_t st);
+void fp_launch_init_clock(const FpSim &S, int par, int slot, cudaStream_t st);
+void fp_launch_mass(const FpSim &S, int par, cudaStream_t st);
+int fp_flood_smem_bytes(int tile_rows);
+cudaError_t fp_flood_init_attributes();
+void fp_launch_hash_count(const FpSim &S, cudaStream_t st);
+void fp_launch_scan(const FpSim &S, cudaStream_t st);
+void fp_launch_gather(const FpSim &S, cudaStream_t st);
+void fp_launch_ped_step(const FpSim &S, int par, int slot, cudaStream_t st);
+void fp_launch_assign_ids(const FpSim &S, int first_slot, int first_id, int count, cudaStream_t st);
+void fp_launch_read_peds(const FpSim &S, uint4 *out, int n_total, cudaStream_t st);
+int fp_scan_tiles(int nbins);

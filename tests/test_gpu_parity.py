@@ -1,0 +1,299 @@
+"""GPU parity of the CUDA path (through the C ABI) against the FP64 oracle on
+identical seeded inputs, plus exact properties the FP32 kernels must keep.
+
+Tolerances: one step from an identical state, FP32 vs FP64 rounding only:
+flood fields within 2e-5 m (or m^2/s), positions within 1e-4 m.  Free-running
+flood: within 1e-4 m after 1000 steps (the accumulated FP32 rounding of the
+update).  Integer outputs (hazard states, responder tasks, timers, exits,
+sandbag counts, time in ticks) must be identical: both sides take those
+decisions in FP32 on the same values.
+"""
+import numpy as np
+import pytest
+
+import scenarios as S
+
+pytestmark = pytest.mark.gpu
+
+H, HU, HV, Z = 0, 1, 2, 3
+
+
+@pytest.fixture(scope="module")
+def P():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1908_05232_b300 as pkg
+    pkg.build.build()
+    return pkg
+
+
+@pytest.fixture(scope="module")
+def O():
+    import oracle
+    oracle.build()
+    return oracle
+
+
+def run_gpu(P, sc, n, **kw):
+    sim = P.from_scenario(sc, **kw)
+    sim.step(n)
+    sim.synchronize()
+    return sim
+
+
+def fields(sim):
+    return [sim.field(k) for k in (H, HU, HV)]
+
+
+def oracle_fields(o):
+    return [o.field(k) for k in ("h", "hu", "hv")]
+
+
+def assert_flood_close(sim, o, atol, rtol=0.0):
+    for a, b, name in zip(fields(sim), oracle_fields(o), ("h", "hu", "hv")):
+        err = np.abs(a.astype(np.float64) - b)
+        bound = atol + rtol * np.abs(b)
+        assert np.all(err <= bound), "%s max err %g at %s" % (name, err.max(), np.unravel_index(err.argmax(), err.shape))
+
+
+def assert_peds_match(sim, o, pos_tol, vel_tol):
+    g = sim.peds()
+    r = o.peds()
+    assert np.array_equal(g["exited"], r["exited"]), np.nonzero(g["exited"] != r["exited"])
+    assert np.array_equal(g["task"], r["fsm"]), np.nonzero(g["task"] != r["fsm"])
+    assert np.array_equal(g["timer_ticks"], r["timer"])
+    assert np.array_equal(g["hr"], r["hr"]), np.nonzero(g["hr"] != r["hr"])
+    assert np.abs(g["x"] - r["x"]).max(initial=0) <= pos_tol
+    assert np.abs(g["y"] - r["y"]).max(initial=0) <= pos_tol
+    assert np.abs(g["vx"] - r["vx"]).max(initial=0) <= vel_tol
+    assert np.abs(g["vy"] - r["vy"]).max(initial=0) <= vel_tol
+
+
+# --------------------------------------------------------------------------
+# exact properties of the FP32 flood update
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("tile_rows", [8, 16, 32])
+def test_lake_at_rest_exact(P, tile_rows):
+    sc = S.closed_basin(150, 70, dx=1.0, seed=3)
+    sim = run_gpu(P, sc, 200, tile_rows=tile_rows)
+    h, hu, hv = fields(sim)
+    z = sim.field(Z)
+    wet = sc.h > 0
+    assert np.all(hu == 0) and np.all(hv == 0)
+    assert np.array_equal((h + z)[wet], (sc.h + sc.z)[wet])
+    assert np.all(h[~wet] == 0)
+    assert sim.counters()["step"] == 200
+
+
+@pytest.mark.parametrize("axis", ["x", "y"])
+def test_mirror_symmetry_exact(P, axis):
+    sc = S.random_wet_state(133, 77, dx=0.7, seed=21, bc=(2, 1, 0, 1))
+    m = sc.copy()
+    if axis == "x":
+        for f in ("z", "h", "hu", "hv", "n0"):
+            setattr(m, f, np.ascontiguousarray(getattr(sc, f)[:, ::-1]))
+        m.hu = -m.hu
+        m.bc_w, m.bc_e = sc.bc_e.copy(), sc.bc_w.copy()
+        m.bc_s, m.bc_n = sc.bc_s[::-1].copy(), sc.bc_n[::-1].copy()
+        fl = lambda f: f[:, ::-1]
+        su, sv = -1, 1
+    else:
+        for f in ("z", "h", "hu", "hv", "n0"):
+            setattr(m, f, np.ascontiguousarray(getattr(sc, f)[::-1, :]))
+        m.hv = -m.hv
+        m.bc_s, m.bc_n = sc.bc_n.copy(), sc.bc_s.copy()
+        m.bc_w, m.bc_e = sc.bc_w[::-1].copy(), sc.bc_e[::-1].copy()
+        fl = lambda f: f[::-1, :]
+        su, sv = 1, -1
+    a, b = run_gpu(P, sc, 60), run_gpu(P, m, 60)
+    assert a.counters()["t_ticks"] == b.counters()["t_ticks"]
+    ha, hua, hva = fields(a)
+    hb, hub, hvb = fields(b)
+    assert np.array_equal(ha, fl(hb))
+    assert np.array_equal(hua, su * fl(hub))
+    assert np.array_equal(hva, sv * fl(hvb))
+
+
+def test_mass_balance(P):
+    sc = S.random_wet_state(130, 90, dx=0.5, seed=11, bc=(0, 0, 0, 0))
+    sim = P.from_scenario(sc)
+    m0, _ = sim.mass()
+    sim.step(400)
+    sim.synchronize()
+    m1, q = sim.mass()
+    assert q == 0.0
+    assert abs(m1 - m0) <= 2e-6 * m0
+    assert sim.counters()["neg_depth"] == 0
+    sc = S.random_wet_state(130, 90, dx=0.5, seed=12)
+    sim = P.from_scenario(sc)
+    m0, _ = sim.mass()
+    sim.step(400)
+    sim.synchronize()
+    m1, q = sim.mass()
+    assert abs(m1 - (m0 + q)) <= 2e-6 * m0
+
+
+# --------------------------------------------------------------------------
+# parity with the oracle
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("shape,tile_rows", [((150, 70), 16), ((64, 16), 16), ((129, 45), 8), ((97, 100), 32),
+                                             ((5, 3), 16)])
+def test_flood_one_step_parity(P, O, shape, tile_rows):
+    nx, ny = shape
+    sc = S.random_wet_state(nx, ny, dx=0.8, seed=nx * 7 + ny)
+    o = O.Oracle(sc)
+    o.step(1)
+    sim = run_gpu(P, sc, 1, tile_rows=tile_rows)
+    assert sim.counters()["t_ticks"] == o.t_ticks
+    assert_flood_close(sim, o, atol=2e-5, rtol=2e-6)
+
+
+def test_flood_1000_steps_parity(P, O):
+    sc = S.plain_coupled_128(seed=1, n_peds=0)
+    sc.t_end = 1e6
+    o = O.Oracle(sc)
+    o.step(1000)
+    sim = run_gpu(P, sc, 1000)
+    c = sim.counters()
+    assert c["step"] == 1000
+    assert abs(c["t_ticks"] - o.t_ticks) <= 1000  # dt may round to a neighbouring tick now and then
+    assert_flood_close(sim, o, atol=1e-4)
+    m, q = sim.mass()
+    assert abs(m - o.mass()) <= 1e-5 * o.mass()
+
+
+def test_dam_break_ritter(P, O):
+    sc = S.dam_break_1d(nx=800, ny=4, dx=0.125, h_left=1.0, h_right=0.0, t_end=4.0)
+    o = O.Oracle(sc)
+    o.step(100000)
+    sim = run_gpu(P, sc, o.nstep + 5)
+    assert sim.counters()["t_ticks"] == o.t_ticks
+    assert_flood_close(sim, o, atol=1e-4)
+
+
+def test_nav_fields_match(P, O):
+    sc = S.shopping_centre(160, 0.5, 200, 20, seed=5, n_barrier=30, n_layers=2)
+    sim = P.from_scenario(sc)
+    nav = sim.nav()
+    o = O.Oracle(sc)
+    assert np.array_equal(nav[0], o.field("nav_exit"))
+    assert np.array_equal(nav[1], o.field("nav_depot"))
+    assert np.array_equal(nav[2], o.field("nav_barrier"))
+
+
+def _crowd_state(seed, nx=140, ny=75, n_evac=900, n_resp=120):
+    sc = S.random_wet_state(nx, ny, dx=0.5, seed=seed, dry_frac=0.35, vel=1.0)
+    sc.walkable = (S.np.random.default_rng(seed).uniform(size=(ny, nx)) > 0.08).astype(np.uint8)
+    sc.exit_mask[ny - 1, nx // 2 - 6: nx // 2 + 6] = 1
+    sc.walkable[sc.exit_mask == 1] = 1
+    sc.coupling = 1
+    S.random_crowd(sc, n_evac, n_resp, seed=seed, random_velocity=1.0, random_tasks=True)
+    S.with_depot_and_barrier(sc, depot_ij=[(10, 10), (11, 10)], barrier_ij=[(i, 40) for i in range(30, 60)],
+                             n_layers=2)
+    sc.walkable[40, 30:60] = 1
+    sc.walkable[10, 10:12] = 1
+    return sc
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_coupled_one_step_parity(P, O, seed):
+    sc = _crowd_state(seed)
+    # put some responders exactly in their depot / barrier cells to exercise arrivals
+    o = O.Oracle(sc)
+    o.step(1)
+    sim = run_gpu(P, sc, 1)
+    assert sim.counters()["t_ticks"] == o.t_ticks
+    assert_flood_close(sim, o, atol=2e-5, rtol=2e-6)
+    assert_peds_match(sim, o, pos_tol=1e-4, vel_tol=2e-4)
+    cg, co = sim.counters(), o.counters()
+    for k in ("n_exited", "total_bags", "hist", "n_active"):
+        assert cg[k] == co[k], (k, cg[k], co[k])
+
+
+def test_coupled_multi_step_parity(P, O):
+    """Free-running coupled steps on the 128 x 128 plain case: identical integer
+    states and positions within 1e-3 m while no decision sits on an edge."""
+    sc = S.plain_coupled_128(seed=1)
+    o = O.Oracle(sc)
+    sim = P.from_scenario(sc)
+    for chunk in range(6):
+        o.step(50)
+        sim.step(50)
+        sim.synchronize()
+        assert_flood_close(sim, o, atol=1e-4)
+        assert_peds_match(sim, o, pos_tol=1e-3, vel_tol=1e-2)
+        assert sim.counters()["n_exited"] == o.counters()["n_exited"]
+
+
+def test_sandbag_barrier_parity(P, O):
+    sc = S.closed_basin(30, 16, dx=0.5, wet=False, bumps=False)
+    sc.ped_noise = 0.05
+    sc.exit_mask[15, 12:16] = 1
+    S.with_depot_and_barrier(sc, depot_ij=[(3, 3), (4, 3)], barrier_ij=[(i, 8) for i in range(18, 24)], n_layers=2)
+    S.random_crowd(sc, 0, 6, seed=4)
+    sc.t_end = 3000.0
+    o = O.Oracle(sc)
+    o.step(2000)
+    sim = run_gpu(P, sc, 2000)
+    cg, co = sim.counters(), o.counters()
+    assert cg["total_bags"] == co["total_bags"] and cg["applied_layers"] == co["applied_layers"]
+    assert np.array_equal(sim.field(Z), o.field("z").astype(np.float32))
+    assert_peds_match(sim, o, pos_tol=1e-3, vel_tol=1e-2)
+
+
+def test_determinism(P):
+    sc = S.plain_coupled_128(seed=3)
+    a = run_gpu(P, sc, 300)
+    b = run_gpu(P, sc, 300)
+    for x, y in zip(fields(a), fields(b)):
+        assert np.array_equal(x, y)
+    assert np.array_equal(a.peds(), b.peds())
+
+
+def test_graph_and_direct_launch_agree(P):
+    """64-step CUDA-graph replay and one-at-a-time launches give the same bytes."""
+    sc = S.plain_coupled_128(seed=5)
+    a = run_gpu(P, sc, 128)
+    b = P.from_scenario(sc)
+    for _ in range(128):
+        b.step(1)
+    b.synchronize()
+    for x, y in zip(fields(a), fields(b)):
+        assert np.array_equal(x, y)
+    assert np.array_equal(a.peds(), b.peds())
+
+
+# --------------------------------------------------------------------------
+# the benchmark's workload sizes
+# --------------------------------------------------------------------------
+def test_shopping_centre_full_size_parity(P, O):
+    """512 x 512 cells, 10,000 evacuees (the benchmark workload): three steps
+    compared cell by cell and pedestrian by pedestrian with the oracle."""
+    sc = S.config_shopping()
+    o = O.Oracle(sc)
+    o.step(3)
+    sim = run_gpu(P, sc, 3)
+    assert sim.counters()["t_ticks"] == o.t_ticks
+    assert_flood_close(sim, o, atol=2e-5, rtol=2e-6)
+    assert_peds_match(sim, o, pos_tol=1e-4, vel_tol=2e-4)
+
+
+def test_barrier_config_full_size_properties(P):
+    """2048 x 2048 cells, 100,000 pedestrians incl. 500 responders: properties
+    that hold at any size (the oracle is too slow here)."""
+    sc = S.config_barrier()
+    sim = P.from_scenario(sc)
+    m0, _ = sim.mass()
+    sim.step(64)
+    sim.synchronize()
+    m1, q = sim.mass()
+    c = sim.counters()
+    assert c["neg_depth"] == 0 and c["error_flags"] == 0
+    assert abs(m1 - (m0 + q)) <= 1e-5 * max(m0 + abs(q), 1.0)
+    g = sim.peds()
+    assert c["n_active"] + c["n_exited"] == sc.n_peds
+    ii = np.floor(g["x"] / np.float32(sc.dx)).astype(int)
+    jj = np.floor(g["y"] / np.float32(sc.dx)).astype(int)
+    assert np.all(sc.walkable[jj, ii] == 1)
+    assert sum(c["hist"]) == c["n_active"] + 0 or sum(c["hist"]) <= sc.n_peds

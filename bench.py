@@ -330,6 +330,23 @@ def run_ours(args):
     return 0
 
 
+def run_case(args):
+    """A short untimed run of one workload (the command line profiled under ncu)."""
+    import torch
+    import scenarios
+    import paper_1908_05232_b300 as P
+    torch.cuda.set_device(0)
+    P.build.build()
+    sc = scenarios.config_barrier() if args.ncu_case == "barrier2048" else workload(2)
+    sim = P.from_scenario(sc, tile_rows=args.tile_rows)
+    sim.step(args.case_steps)
+    sim.synchronize()
+    c = sim.counters()
+    print(json.dumps({"case": args.ncu_case, "steps": c["step"], "t_ticks": c["t_ticks"],
+                      "n_active": c["n_active"], "error_flags": c["error_flags"]}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -340,7 +357,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-steps", type=int, default=100)
     ap.add_argument("--ref-sample-steps", type=int, default=8)
+    ap.add_argument("--ncu-case", choices=["barrier2048", "shopping512"], default=None,
+                    help="short untimed run of one workload, for profiler captures")
+    ap.add_argument("--case-steps", type=int, default=4)
     args = ap.parse_args()
+    if args.ncu_case:
+        return run_case(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -160,6 +160,10 @@ int fp_set_state(fp_sim *sim, const float *h, const float *hu, const float *hv);
 /* Set simulated time (ticks) and step index (the random generator's counter). */
 int fp_set_time(fp_sim *sim, int64_t t_ticks, int64_t step);
 
+/* Sandbags already dropped and barrier cell-layers already built into z (for a
+ * run resumed mid-deployment); total_bags >= 0, 0 <= applied_layers. */
+int fp_set_barrier_progress(fp_sim *sim, int64_t total_bags, int64_t applied_layers);
+
 /* Append count pedestrians; each must stand in a walkable cell inside the domain. */
 int fp_add_pedestrians(fp_sim *sim, const fp_ped *peds, int32_t count);
 

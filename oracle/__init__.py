@@ -175,6 +175,8 @@ class Oracle:
         S.pid, S.ptimer = _ptr(self.pid), _ptr(self.ptimer)
         S.prole, S.pfsm, S.phr, S.pexit = [_ptr(a) for a in (self.prole, self.pfsm, self.phr, self.pexit)]
         S.nav_exit, S.nav_depot, S.nav_barrier = _ptr(self.nav_exit), _ptr(self.nav_depot), _ptr(self.nav_barrier)
+        S.t_ticks, S.step = int(sc.t0_ticks), int(sc.step0)
+        S.total_bags, S.applied_layers = int(sc.bags0), int(sc.applied0)
         self.S = S
         L.or_prepare(ctypes.byref(P), ctypes.byref(S))
 
@@ -217,6 +219,28 @@ class Oracle:
                     applied_layers=int(S.applied_layers), neg_depth=int(S.neg_depth),
                     n_exited=int(S.n_exited), hist=[int(v) for v in S.hist],
                     n_active=int((self.pexit == 0).sum()))
+
+    def to_scenario(self):
+        """The oracle's current state as a new scenario (FP32-rounded fields and
+        pedestrians still present, renumbered in id order), to start both
+        implementations from one mid-run state."""
+        import scenarios
+        sc = self.sc.copy()
+        ny, nx = sc.ny, sc.nx
+        sc.h = self.h.reshape(ny, nx).astype(np.float32)
+        sc.hu = self.hu.reshape(ny, nx).astype(np.float32)
+        sc.hv = self.hv.reshape(ny, nx).astype(np.float32)
+        sc.z = self.z.reshape(ny, nx).astype(np.float32)
+        keep = self.pexit == 0
+        p = scenarios.empty_peds(int(keep.sum()))
+        p["x"], p["y"] = self.px[keep].astype(np.float32), self.py[keep].astype(np.float32)
+        p["vx"], p["vy"] = self.pvx[keep].astype(np.float32), self.pvy[keep].astype(np.float32)
+        p["role"], p["fsm"] = self.prole[keep].copy(), self.pfsm[keep].copy()
+        p["timer"], p["v0"] = self.ptimer[keep].copy(), self.pv0[keep].astype(np.float32)
+        sc.peds = p
+        sc.t0_ticks, sc.step0 = int(self.S.t_ticks), int(self.S.step)
+        sc.bags0, sc.applied0 = int(self.S.total_bags), int(self.S.applied_layers)
+        return sc
 
     def peds(self) -> dict:
         return dict(x=self.px.copy(), y=self.py.copy(), vx=self.pvx.copy(), vy=self.pvy.copy(),

@@ -641,6 +641,7 @@ int64_t or_step(const or_params *P, or_state *S) {
         S->applied_layers = done;
     }
     const int64_t bags_snap = S->total_bags;
+    for (int k = 0; k < 5; ++k) S->hist[k] = 0;   /* hazard-state counts of this step */
     /* evacuees per cell -> Manning n (Section 2.4) */
     double *n_eff = (double *)malloc(sizeof(double) * (size_t)n);
     int32_t *occ = (int32_t *)calloc((size_t)n, sizeof(int32_t));

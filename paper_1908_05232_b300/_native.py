@@ -62,6 +62,7 @@ def lib():
             "fp_set_hydrograph": [_VP, _VP, _VP, ctypes.c_int32],
             "fp_set_goals": [_VP, _VP, ctypes.c_int32, _VP, ctypes.c_int32, ctypes.c_int32],
             "fp_set_state": [_VP] * 4, "fp_set_time": [_VP, ctypes.c_int64, ctypes.c_int64],
+            "fp_set_barrier_progress": [_VP, ctypes.c_int64, ctypes.c_int64],
             "fp_add_pedestrians": [_VP, _VP, ctypes.c_int32], "fp_clear_pedestrians": [_VP],
             "fp_step": [_VP, ctypes.c_int32], "fp_synchronize": [_VP], "fp_set_profiling": [_VP, ctypes.c_int32],
             "fp_read_state": [_VP, ctypes.c_int32, _VP, ctypes.c_size_t], "fp_destroy": [_VP],
@@ -129,6 +130,10 @@ def fp_set_state(h, depth, hu, hv):
 
 def fp_set_time(h, t_ticks, step):
     _check(lib().fp_set_time(h, int(t_ticks), int(step)), h)
+
+
+def fp_set_barrier_progress(h, total_bags, applied_layers):
+    _check(lib().fp_set_barrier_progress(h, int(total_bags), int(applied_layers)), h)
 
 
 def fp_add_pedestrians(h, recs):
@@ -255,6 +260,10 @@ def from_scenario(sc, max_peds=None, tile_rows=0, peds=True) -> Simulation:
     fp_set_hydrograph(sim.h, sc.hydro_t, sc.hydro_h)
     fp_set_goals(sim.h, sc.depot_cells, sc.barrier_cells, sc.n_layers)
     fp_set_state(sim.h, c(sc.h, np.float32), c(sc.hu, np.float32), c(sc.hv, np.float32))
+    if getattr(sc, "t0_ticks", 0) or getattr(sc, "step0", 0):
+        fp_set_time(sim.h, sc.t0_ticks, sc.step0)
+    if getattr(sc, "bags0", 0) or getattr(sc, "applied0", 0):
+        fp_set_barrier_progress(sim.h, sc.bags0, sc.applied0)
     if peds and sc.n_peds:
         sim.add_pedestrians(ped_records(sc.peds))
     return sim

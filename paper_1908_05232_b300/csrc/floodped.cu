@@ -496,6 +496,21 @@ int fp_set_time(fp_sim *s, int64_t t_ticks, int64_t step) {
     return FP_OK;
 }
 
+int fp_set_barrier_progress(fp_sim *s, int64_t total_bags, int64_t applied_layers) {
+    if (!s) return FP_EINVAL;
+    if (total_bags < 0 || applied_layers < 0) return s->fail(FP_EINVAL, "negative barrier progress");
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return s->cuda_fail(e, "sync");
+    FpCounters c;
+    cudaMemcpy(&c, s->S.cnt, sizeof(c), cudaMemcpyDeviceToHost);
+    c.total_bags = (unsigned long long)total_bags;
+    c.bags_snap = (unsigned long long)total_bags;
+    c.applied = (unsigned long long)applied_layers;
+    e = cudaMemcpy(s->S.cnt, &c, sizeof(c), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return s->cuda_fail(e, "barrier progress");
+    return FP_OK;
+}
+
 int fp_add_pedestrians(fp_sim *s, const fp_ped *peds, int32_t count) {
     if (!s) return FP_EINVAL;
     if (count < 0 || (count > 0 && !peds)) return s->fail(FP_EINVAL, "bad pedestrian arguments");

@@ -114,31 +114,50 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(const __grid_constan
         if (w < wid) wpre += s_warp[w];
         total += s_warp[w];
     }
-    if (tid == 0) {
+    // warp-parallel decoupled look-back: lane l inspects predecessor tile - 1 - l
+    // (and the window moves back by 32 while none of them has its inclusive prefix)
+    if (wid == 0) {
         volatile unsigned long long *flags = S.scan_flags;
         int excl = 0;
         if (tile == 0) {
-            flags[0] = (epoch << 34) | (2ull << 32) | (unsigned)total;
+            if (lane == 0) flags[0] = (epoch << 34) | (2ull << 32) | (unsigned)total;
         } else {
-            flags[tile] = (epoch << 34) | (1ull << 32) | (unsigned)total;
-            __threadfence();
-            for (int t = tile - 1; t >= 0; --t) {
-                unsigned long long w = 0;
-                unsigned st = 0;
-                int it = 0;
-                for (; it < (1 << 24); ++it) {
-                    w = flags[t];
-                    st = (unsigned)(w >> 32) & 3u;
-                    if ((w >> 34) == epoch && st != 0u) break;
-                }
-                if (it == (1 << 24)) { fp_set_err(S, FP_ERR_TIMEOUT); break; }
-                excl += (int)(unsigned)(w & 0xffffffffull);
-                if (st == 2u) break;
+            if (lane == 0) {
+                flags[tile] = (epoch << 34) | (1ull << 32) | (unsigned)total;
+                __threadfence();
             }
-            __threadfence();
-            flags[tile] = (epoch << 34) | (2ull << 32) | (unsigned)(excl + total);
+            __syncwarp();
+            int t = tile - 1 - lane;
+            bool timed_out = false;
+            while (true) {
+                unsigned long long w = 0;
+                unsigned st = 2u;  // tiles before 0: an inclusive prefix of 0
+                if (t >= 0) {
+                    int it = 0;
+                    for (; it < (1 << 22); ++it) {
+                        w = flags[t];
+                        st = (unsigned)(w >> 32) & 3u;
+                        if ((w >> 34) == epoch && st != 0u) break;
+                    }
+                    if (it == (1 << 22)) { timed_out = true; w = 0; st = 2u; }
+                }
+                const int val = t >= 0 ? (int)(unsigned)(w & 0xffffffffull) : 0;
+                const unsigned pmask = __ballot_sync(0xffffffffu, st == 2u);
+                const int last = pmask ? __ffs(pmask) - 1 : 31;  // nearest predecessor with a prefix
+                int part = lane <= last ? val : 0;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+                excl += part;
+                if (pmask) break;
+                t -= 32;
+            }
+            if (__any_sync(0xffffffffu, timed_out) && lane == 0) fp_set_err(S, FP_ERR_TIMEOUT);
+            if (lane == 0) {
+                __threadfence();
+                flags[tile] = (epoch << 34) | (2ull << 32) | (unsigned)(excl + total);
+            }
         }
-        s_prefix = excl;
+        if (lane == 0) s_prefix = excl;
     }
     __syncthreads();
     int run = s_prefix + wpre + incl - sum;

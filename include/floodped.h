@@ -189,8 +189,39 @@ int fp_read_state(fp_sim *sim, int32_t which, void *dst, size_t bytes);
 /* Free the handle and its device memory. */
 int fp_destroy(fp_sim *sim);
 
-/* Last error message of the handle (or of the last failed create if sim is NULL). */
+/* Last error message of the handle (or, with sim NULL, of the last failed
+ * fp_sim_create or fp_water_volume_noalloc). */
 const char *fp_last_error(const fp_sim *sim);
+
+/* ---- allocation-free entry point --------------------------------------------
+ * The paper has no counterpart: this is a service of the library.
+ *
+ * Water volume sum(h) * dx^2 (m^3, FP64) of a depth grid the caller owns, for
+ * callers that may not allocate device memory through this library: code whose
+ * device memory is all owned by a host framework's pool (a cudaMalloc/cudaFree
+ * from here would bypass the pool, and cudaFree synchronises the whole device),
+ * tools that size their device memory once at start-up and must not grow it,
+ * and hot loops where an allocation per call would cost more than the sum.
+ * It allocates nothing: its scratch is one fixed device array of
+ * FP_NOALLOC_MAX_ROWS + 32 doubles (~512 KB) that every GPU loading the
+ * library holds until the process exits.
+ *
+ * h: device pointer to ny rows of nx floats, row r at h + r * row_pitch
+ * (row_pitch >= nx, in elements); out: device-accessible pointer to one double,
+ * written when the kernel finishes; cuda_stream: cudaStream_t or NULL.  The
+ * call is asynchronous on that stream.  Returns FP_EINVAL (with a message in
+ * fp_last_error(NULL)) for null pointers, nx or ny < 1, row_pitch < nx, dx <= 0,
+ * or ny > FP_NOALLOC_MAX_ROWS; FP_ECUDA if the set-up or launch fails.
+ *
+ * The first call on each device looks up the scratch array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture begins.  Every call shares the one scratch array and the
+ * kernel re-arms its completion counter for the next call, so calls must not
+ * overlap on the GPU: two calls in flight at once (other streams, other host
+ * threads) race on the array. */
+#define FP_NOALLOC_MAX_ROWS 65536
+int fp_water_volume_noalloc(const float *h, int32_t nx, int32_t ny, int64_t row_pitch, float dx,
+                            double *out, void *cuda_stream);
 
 #ifdef __cplusplus
 }

@@ -71,6 +71,9 @@ def lib():
             f = getattr(L, name)
             f.argtypes = args
             f.restype = ctypes.c_int
+        L.fp_water_volume_noalloc.argtypes = [_VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, ctypes.c_float,
+                                              _VP, _VP]
+        L.fp_water_volume_noalloc.restype = ctypes.c_int
         L.fp_last_error.argtypes = [_VP]
         L.fp_last_error.restype = ctypes.c_char_p
         _lib = L
@@ -161,6 +164,12 @@ def fp_read_state(h, which, dst):
     nbytes = dst.numel() * dst.element_size() if hasattr(dst, "data_ptr") else dst.nbytes
     _check(lib().fp_read_state(h, int(which), _ptr(dst), nbytes), h)
     return dst
+
+
+def fp_water_volume_noalloc(depth, nx, ny, row_pitch, dx, out, stream_ptr=None):
+    """Water volume of a caller's device depth grid into a caller's device double; allocates nothing."""
+    _check(lib().fp_water_volume_noalloc(_ptr(depth), int(nx), int(ny), int(row_pitch), float(dx), _ptr(out),
+                                         _VP(stream_ptr) if stream_ptr else None))
 
 
 def fp_destroy(h):

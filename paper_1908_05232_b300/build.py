@@ -14,7 +14,7 @@ LIB = os.path.join(HERE, "libfloodped.so")
 OBJ = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INC, "-I", CSRC]
-SOURCES = [("flood.cu", ["-fmad=false"]), ("peds.cu", []), ("floodped.cu", [])]
+SOURCES = [("flood.cu", ["-fmad=false"]), ("peds.cu", []), ("floodped.cu", []), ("noalloc.cu", [])]
 
 
 def _inputs():

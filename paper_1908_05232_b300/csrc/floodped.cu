@@ -716,3 +716,9 @@ int fp_destroy(fp_sim *s) {
 const char *fp_last_error(const fp_sim *s) { return s ? s->err.c_str() : g_create_error.c_str(); }
 
 }  // extern "C"
+
+void fp_note_error(const char *msg) { g_create_error = msg; }
+
+extern "C" {
+
+}  // extern "C"

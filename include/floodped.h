@@ -76,8 +76,9 @@ extern "C" {
 #define FP_FIELD_COUNTERS 5 /* one fp_counters */
 #define FP_FIELD_NAV 6      /* uint8[3*ny*nx]: exit, storage, barrier direction codes */
 #define FP_FIELD_MASS 7     /* double[2]: water volume sum h dx^2 (m^3), net boundary inflow volume (m^3) */
-#define FP_FIELD_PROFILE 8  /* double[5]: profiled steps, then total ms of hash_count, flood, the
-                               scan -> gather -> pedestrian chain, and whole steps (see fp_set_profiling) */
+#define FP_FIELD_PROFILE 8  /* double[5]: profiled steps, then total ms of: the hashing/scan part,
+                               the flood update, the gather + pedestrian part, whole steps
+                               (see fp_set_profiling) */
 
 /* Simulation set-up.  Sizes: nx, ny >= 1; max_peds >= 0. */
 typedef struct fp_config {
@@ -173,9 +174,21 @@ int fp_clear_pedestrians(fp_sim *sim);
 /* Enqueue n_steps coupled steps on the simulation's stream (asynchronous). */
 int fp_step(fp_sim *sim, int32_t n_steps);
 
-/* Profiling mode (on != 0): fp_step launches every step directly (no CUDA
- * graph) with CUDA events around the kernel groups and synchronises at its end;
- * FP_FIELD_PROFILE returns the accumulated times.  Turning it on resets them. */
+/* How fp_step runs a step (both give bit-identical results):
+ * FP_MODE_KERNELS (default): five kernels per step on two streams (the flood
+ *   update overlaps the pedestrian chain), 64-step CUDA graphs;
+ * FP_MODE_PERSISTENT (devices with cooperative launch): up to 256 steps per
+ *   launch of one persistent kernel whose phases are separated by grid
+ *   barriers with bounded waits (FP_ETIMEOUT if one gives up). */
+#define FP_MODE_KERNELS 0
+#define FP_MODE_PERSISTENT 1
+int fp_set_step_mode(fp_sim *sim, int32_t mode);
+
+/* Profiling mode (on != 0): fp_step synchronises at its end and accumulates
+ * the time of the parts of each step -- per-step kernels: launched directly
+ * (no CUDA graph) with CUDA events around the kernel groups; persistent
+ * kernel: global-timer stamps at every phase boundary.  FP_FIELD_PROFILE
+ * returns the totals.  Turning it on resets them. */
 int fp_set_profiling(fp_sim *sim, int32_t on);
 
 /* Wait for enqueued work; returns FP_ETIMEOUT / FP_EOVERFLOW / FP_ENAN when the

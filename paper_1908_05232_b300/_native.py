@@ -19,6 +19,7 @@ FP_FIELD_H, FP_FIELD_HU, FP_FIELD_HV, FP_FIELD_Z = 0, 1, 2, 3
 FP_FIELD_PEDS, FP_FIELD_COUNTERS, FP_FIELD_NAV, FP_FIELD_MASS, FP_FIELD_PROFILE = 4, 5, 6, 7, 8
 FP_EDGE_SOUTH, FP_EDGE_NORTH, FP_EDGE_WEST, FP_EDGE_EAST = 0, 1, 2, 3
 TICKS = 1 << 20
+FP_MODE_KERNELS, FP_MODE_PERSISTENT = 0, 1
 
 PED_DTYPE = np.dtype([("x", "<f4"), ("y", "<f4"), ("vx", "<f4"), ("vy", "<f4"), ("id", "<u4"),
                       ("role", "u1"), ("task", "u1"), ("hr", "u1"), ("exited", "u1"),
@@ -64,7 +65,7 @@ def lib():
             "fp_set_state": [_VP] * 4, "fp_set_time": [_VP, ctypes.c_int64, ctypes.c_int64],
             "fp_set_barrier_progress": [_VP, ctypes.c_int64, ctypes.c_int64],
             "fp_add_pedestrians": [_VP, _VP, ctypes.c_int32], "fp_clear_pedestrians": [_VP],
-            "fp_step": [_VP, ctypes.c_int32], "fp_synchronize": [_VP], "fp_set_profiling": [_VP, ctypes.c_int32],
+            "fp_step": [_VP, ctypes.c_int32], "fp_synchronize": [_VP], "fp_set_step_mode": [_VP, ctypes.c_int32], "fp_set_profiling": [_VP, ctypes.c_int32],
             "fp_read_state": [_VP, ctypes.c_int32, _VP, ctypes.c_size_t], "fp_destroy": [_VP],
         }
         for name, args in sigs.items():
@@ -150,6 +151,10 @@ def fp_clear_pedestrians(h):
 
 def fp_step(h, n):
     _check(lib().fp_step(h, int(n)), h)
+
+
+def fp_set_step_mode(h, mode):
+    _check(lib().fp_set_step_mode(h, int(mode)), h)
 
 
 def fp_set_profiling(h, on):
@@ -257,9 +262,11 @@ def config_for(sc, max_peds=None, tile_rows=0) -> FpConfig:
     return c
 
 
-def from_scenario(sc, max_peds=None, tile_rows=0, peds=True) -> Simulation:
+def from_scenario(sc, max_peds=None, tile_rows=0, peds=True, mode=None) -> Simulation:
     """Create a simulation and load a ``scenarios.Scenario`` into it through the C ABI."""
     sim = Simulation(config_for(sc, max_peds, tile_rows))
+    if mode is not None:
+        fp_set_step_mode(sim.h, mode)
     c = np.ascontiguousarray
     fp_set_terrain(sim.h, c(sc.z, np.float32), c(sc.n0, np.float32), c(sc.walkable, np.uint8),
                    c(sc.exit_mask, np.uint8))

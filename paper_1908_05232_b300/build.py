@@ -1,8 +1,9 @@
 """Compile the CUDA library ``libfloodped.so`` for sm_103a (B300), in-tree.
 
-Each translation unit is compiled separately so that the flood update can use
-``-fmad=false`` (exact mirror symmetry of the scheme) while the rest keeps the
-default contraction.  The CUDA runtime is linked statically.
+Each translation unit is compiled separately, all with -fmad=false: every
+fused multiply-add in the kernels is written out explicitly, so a device
+function gives the same bits in every kernel it is inlined into.  The CUDA
+runtime is linked statically.
 """
 import os
 import subprocess
@@ -13,8 +14,8 @@ INC = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libfloodped.so")
 OBJ = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INC, "-I", CSRC]
-SOURCES = [("flood.cu", ["-fmad=false"]), ("peds.cu", []), ("floodped.cu", []), ("noalloc.cu", [])]
+COMMON = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC", "-I", INC, "-I", CSRC]
+SOURCES = [("flood.cu", []), ("peds.cu", []), ("floodped.cu", []), ("noalloc.cu", []), ("persist.cu", [])]
 
 
 def _inputs():

@@ -1,0 +1,381 @@
+// flood_dev.cuh -- device code of the hydrodynamic cell update (Section 2.2),
+// shared by the per-step flood kernel and the persistent coupled-step kernel.
+//
+// flood_tile<TY>: a 64 x TY tile of cells by 32 x TY threads.
+//   1. one thread issues four 2D TMA loads (cp.async.bulk.tensor) of the tile
+//      plus a one-cell halo (a 72-float-wide box starting 16-byte aligned) of
+//      h, hu, hv, z into shared memory, completing on an mbarrier; meanwhile
+//      every thread loads its two cells' n0 and evacuee counts;
+//   2. velocities u = hu/h, v = hv/h per staged cell;
+//   3. every x and y face of the tile once: non-negative hydrostatic
+//      reconstruction h* = max(0, eta - max(z_L, z_R)) and the HLL flux;
+//      each side keeps the flux minus the pressure 1/2 g h*^2 of its own
+//      reconstructed depth (this carries the bed-slope source of Eq. 1);
+//      domain-edge faces use ghost states from the boundary codes;
+//   4. Eq. (2) per cell, point-implicit Manning friction with
+//      n = n0 + N_p n0 (N_p <= 20), writes U^{n+1} (warp r: row r, lane l:
+//      cells l and l + 32, so every shared-memory access is lane-contiguous);
+//      the CFL wave-speed max of U^{n+1} and the wet flag are reduced per CTA
+//      (warp shuffles) and folded into the next step's clock slot with one
+//      atomic each; edge tiles add their boundary mass fluxes in FP64.
+// Built with -fmad=false: every fused multiply-add is written out, and each one
+// is sign-symmetric, so the update is exactly mirror-symmetric and gives the
+// same bits in every kernel it is inlined into.
+#pragma once
+#include "fp_common.cuh"
+
+namespace fpdev {
+
+
+constexpr int ROWW = FP_TX + 8;  // staged row width: 4 guard floats each side
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ float sqrt_fast(float x) {
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ float press(float g, float h) { return 0.5f * g * h * h; }
+
+// HLL flux across a face; un normal and ut tangential velocity, pL/pR the face
+// pressures 1/2 g h^2 of the two sides.  out = (mass, normal momentum incl.
+// pressure, tangential momentum).  Identical states give the physical flux
+// exactly (lake at rest stays exactly at rest).
+__device__ __forceinline__ void hll(float g, float hL, float unL, float utL, float pL, float hR, float unR,
+                                    float utR, float pR, float &fm, float &fn, float &ft) {
+    if (hL <= FP_H_EPS_F && hR <= FP_H_EPS_F) {
+        fm = 0.0f; fn = 0.0f; ft = 0.0f;
+        return;
+    }
+    const float qL = hL * unL, qR = hR * unR;
+    const float FL0 = qL, FL1 = __fmaf_rn(qL, unL, pL), FL2 = qL * utL;
+    const float FR0 = qR, FR1 = __fmaf_rn(qR, unR, pR), FR2 = qR * utR;
+    if (hL == hR && unL == unR && utL == utR) {
+        fm = FL0; fn = FL1; ft = FL2;
+        return;
+    }
+    const float cL = sqrt_fast(g * hL), cR = sqrt_fast(g * hR);
+    float sL, sR;
+    if (hL <= FP_H_EPS_F) {
+        sL = __fmaf_rn(-2.0f, cR, unR);
+        sR = unR + cR;
+    } else if (hR <= FP_H_EPS_F) {
+        sL = unL - cL;
+        sR = __fmaf_rn(2.0f, cL, unL);
+    } else {
+        const float us = __fmaf_rn(0.5f, unL + unR, cL - cR);
+        const float cs = __fmaf_rn(0.25f, unL - unR, 0.5f * (cL + cR));
+        const float a = unL - cL, b = us - cs;
+        sL = a < b ? a : b;
+        const float c = unR + cR, d = us + cs;
+        sR = c > d ? c : d;
+    }
+    if (sL >= 0.0f) { fm = FL0; fn = FL1; ft = FL2; return; }
+    if (sR <= 0.0f) { fm = FR0; fn = FR1; ft = FR2; return; }
+    // Differences of two products are rounded explicitly (no contraction), so the
+    // flux of a mirrored face is exactly the mirrored flux.
+    const float inv = __frcp_rn(sR - sL);
+    const float sLR = __fmul_rn(sL, sR);
+    fm = __fadd_rn(__fsub_rn(__fmul_rn(sR, FL0), __fmul_rn(sL, FR0)), __fmul_rn(sLR, hR - hL)) * inv;
+    fn = __fadd_rn(__fsub_rn(__fmul_rn(sR, FL1), __fmul_rn(sL, FR1)), __fmul_rn(sLR, qR - qL)) * inv;
+    ft = __fadd_rn(__fsub_rn(__fmul_rn(sR, FL2), __fmul_rn(sL, FR2)),
+                   __fmul_rn(sLR, __fsub_rn(__fmul_rn(hR, utR), __fmul_rn(hL, utL)))) * inv;
+}
+
+struct Side {
+    float h, u, v, z;
+};
+
+__device__ __forceinline__ Side ghost(unsigned char code, Side in, bool normal_x, float h_in) {
+    Side g = in;
+    if (code == 0) {
+        if (normal_x) g.u = -in.u; else g.v = -in.v;
+    } else if (code == 2) {
+        g.h = h_in; g.u = 0.0f; g.v = 0.0f;
+    }
+    return g;
+}
+
+// staged plane stride, padded to 32 floats so every TMA destination is 128-byte aligned
+template <int TY>
+__host__ __device__ constexpr int plane_stride() {
+    return (((TY + 2) * ROWW + 31) / 32) * 32;
+}
+
+template <int TY>
+__host__ __device__ constexpr int smem_bytes() {
+    return 6 * plane_stride<TY>() * 4 + TY * (FP_TX + 1) * 16 + (TY + 1) * FP_TX * 16;
+}
+
+// 32 * TY threads: warp r owns row r of the tile, lane l its cells l and l + 32.
+// One 64 x TY tile (tile coordinates bx, by) by the 32 * TY threads of the CTA.
+// The caller owns the mbarrier (initialised once, count 1) and its phase parity,
+// and guarantees no thread still reads the staged planes of a previous tile.
+// Returns false if the TMA transfer did not complete (error flag set).
+template <int TY>
+__device__ __forceinline__ bool flood_tile(const FpTmaSet &tm, const FpSim &S, int par, int slot, int bx, int by,
+                                           unsigned char *smem_raw, unsigned long long *mbar, unsigned parity) {
+    constexpr int NT = 32 * TY;
+    constexpr int PLANE = plane_stride<TY>();
+    constexpr int BOX_BYTES = (TY + 2) * ROWW * 4;
+    float *s_h = reinterpret_cast<float *>(smem_raw);
+    float *s_hu = s_h + PLANE;
+    float *s_hv = s_hu + PLANE;
+    float *s_z = s_hv + PLANE;
+    float *s_u = s_z + PLANE;
+    float *s_v = s_u + PLANE;
+    float4 *s_xf = reinterpret_cast<float4 *>(s_v + PLANE);  // [TY][65]
+    float4 *s_yf = s_xf + TY * (FP_TX + 1);                   // [TY+1][64]
+    __shared__ long long s_dt, s_t, s_step;
+    __shared__ float s_hin, s_dtf, s_lx;
+    __shared__ int s_ok;
+    __shared__ float s_red[NT / 32];
+    __shared__ int s_redi[NT / 32];
+    __shared__ float s_bx[2][TY];      // mass flux through the west / east domain edge faces
+    __shared__ float s_by[2][FP_TX];   // ... through the south / north domain edge faces
+
+    const int tid = threadIdx.x;
+    const int x0 = bx * FP_TX, y0 = by * TY;
+    const int nx = S.nx, ny = S.ny;
+
+    if (tid == 0) {
+        const unsigned bar = smem_u32(mbar);
+        // the staged planes were last written by generic stores / read by this CTA
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(4 * BOX_BYTES)
+                     : "memory");
+        const CUtensorMap *maps[4] = {&tm.h, &tm.hu, &tm.hv, &tm.z};
+        float *dsts[4] = {s_h, s_hu, s_hv, s_z};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            asm volatile(
+                "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+                    smem_u32(dsts[k])),
+                "l"(reinterpret_cast<unsigned long long>(maps[k])), "r"(x0), "r"(y0), "r"(bar)
+                : "memory");
+        }
+        const FpClock c = S.clock[slot];
+        const long long dt = fp_dt_ticks(S, c, c.h_in);
+        const float dtf = (float)dt * (1.0f / FP_TICKS_F);
+        s_hin = c.h_in;
+        s_dt = dt;
+        s_dtf = dtf;
+        s_lx = __fdiv_rn(dtf, S.dx);
+        s_t = c.t;
+        s_step = c.step;
+    }
+    // this thread's two cells: n0 and evacuee counts, loaded while the TMA is in flight
+    const int lane = tid & 31, row = tid >> 5;
+    const int cj = y0 + row;
+    const int ciA = x0 + lane, ciB = x0 + lane + 32;
+    const bool okA = cj < ny && ciA < nx, okB = cj < ny && ciB < nx;
+    float n0A = 0.f, n0B = 0.f;
+    unsigned short occA = 0, occB = 0;
+    const size_t gA = okA ? fp_pidx(S, ciA, cj) : 0;
+    if (okA) { n0A = S.n0[gA]; occA = S.occ[par][gA]; }
+    if (okB) { n0B = S.n0[gA + 32]; occB = S.occ[par][gA + 32]; }
+    if (tid == 0) {
+        const unsigned bar = smem_u32(mbar);
+        unsigned ok = 0;
+        for (int it = 0; it < (1 << 22) && !ok; ++it) {
+            asm volatile(
+                "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+                : "=r"(ok)
+                : "r"(bar), "r"(parity)
+                : "memory");
+        }
+        s_ok = ok;
+        if (!ok) fp_set_err(S, FP_ERR_TIMEOUT);
+    }
+    __syncthreads();
+    if (!s_ok) return false;
+
+    const float g = S.g;
+    const float h_in = s_hin;
+
+    // 2. velocities of staged cells x0-1 .. x0+64 (staged columns 3 .. 68)
+    for (int idx = tid; idx < (TY + 2) * (FP_TX + 2); idx += NT) {
+        const int r = idx / (FP_TX + 2), cc = idx % (FP_TX + 2) + 3;
+        const int o = r * ROWW + cc;
+        const float h = s_h[o];
+        float u = 0.0f, v = 0.0f;
+        if (h > FP_H_EPS_F) {
+            u = __fdividef(s_hu[o], h);
+            v = __fdividef(s_hv[o], h);
+        }
+        s_u[o] = u;
+        s_v[o] = v;
+    }
+    __syncthreads();
+
+    // 3a. x faces: face k of row r lies between cells x0+k-1 and x0+k
+    for (int idx = tid; idx < TY * (FP_TX + 1); idx += NT) {
+        const int r = idx / (FP_TX + 1), k = idx % (FP_TX + 1);
+        const int j = y0 + r, xl = x0 + k - 1, xr = x0 + k;
+        if (j >= ny || xr > nx) continue;
+        const int oL = (r + 1) * ROWW + k + 3, oR = oL + 1;
+        Side L, R;
+        if (xr < nx) R = Side{s_h[oR], s_u[oR], s_v[oR], s_z[oR]};
+        if (xl >= 0) L = Side{s_h[oL], s_u[oL], s_v[oL], s_z[oL]};
+        if (xl < 0) L = ghost(S.bc[2][j], R, true, h_in);
+        if (xr == nx) R = ghost(S.bc[3][j], L, true, h_in);
+        const float zf = fmaxf(L.z, R.z);
+        const float hLs = fmaxf(0.0f, (L.h + L.z) - zf);
+        const float hRs = fmaxf(0.0f, (R.h + R.z) - zf);
+        const float pL = press(g, hLs), pR = press(g, hRs);
+        float fm, fn, ft;
+        hll(g, hLs, L.u, L.v, pL, hRs, R.u, R.v, pR, fm, fn, ft);
+        s_xf[r * (FP_TX + 1) + k] = make_float4(fm, fn - pL, fn - pR, ft);
+        if (xl < 0) s_bx[0][r] = fm;
+        if (xr == nx) s_bx[1][r] = fm;
+    }
+    // 3b. y faces: face r of column c lies between rows y0+r-1 and y0+r
+    for (int idx = tid; idx < (TY + 1) * FP_TX; idx += NT) {
+        const int r = idx / FP_TX, c = idx % FP_TX;
+        const int i = x0 + c, jb = y0 + r - 1, ja = y0 + r;
+        if (i >= nx || ja > ny) continue;
+        const int oB = r * ROWW + c + 4, oA = oB + ROWW;
+        Side B, A;
+        if (ja < ny) A = Side{s_h[oA], s_u[oA], s_v[oA], s_z[oA]};
+        if (jb >= 0) B = Side{s_h[oB], s_u[oB], s_v[oB], s_z[oB]};
+        if (jb < 0) B = ghost(S.bc[0][i], A, false, h_in);
+        if (ja == ny) A = ghost(S.bc[1][i], B, false, h_in);
+        const float zf = fmaxf(B.z, A.z);
+        const float hBs = fmaxf(0.0f, (B.h + B.z) - zf);
+        const float hAs = fmaxf(0.0f, (A.h + A.z) - zf);
+        const float pB = press(g, hBs), pA = press(g, hAs);
+        float fm, fn, ft;
+        hll(g, hBs, B.v, B.u, pB, hAs, A.v, A.u, pA, fm, fn, ft);
+        s_yf[r * FP_TX + c] = make_float4(fm, ft, fn - pB, fn - pA);
+        if (jb < 0) s_by[0][c] = fm;
+        if (ja == ny) s_by[1][c] = fm;
+    }
+    __syncthreads();
+
+    // 4. Eq. (2) + friction for this thread's two cells
+    float smax = 0.0f;
+    float sk_[2] = {-1.0f, -1.0f}, hk_[2] = {0.f, 0.f}, huk_[2] = {0.f, 0.f}, hvk_[2] = {0.f, 0.f};
+    int wet = 0, neg = 0, bad = 0;
+    const float dt = s_dtf, lx = s_lx, ly = s_lx;
+    const int p2 = par ^ 1;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const bool ok = k == 0 ? okA : okB;
+        if (!ok) continue;
+        const int c = lane + 32 * k;
+        const int o = (row + 1) * ROWW + c + 4;
+        const float4 fw = s_xf[row * (FP_TX + 1) + c];
+        const float4 fe = s_xf[row * (FP_TX + 1) + c + 1];
+        const float4 gs = s_yf[row * FP_TX + c];
+        const float4 gn = s_yf[(row + 1) * FP_TX + c];
+        float h = __fmaf_rn(-ly, gn.x - gs.x, __fmaf_rn(-lx, fe.x - fw.x, s_h[o]));
+        float hu = __fmaf_rn(-ly, gn.y - gs.y, __fmaf_rn(-lx, fe.y - fw.z, s_hu[o]));
+        float hv = __fmaf_rn(-ly, gn.z - gs.w, __fmaf_rn(-lx, fe.w - fw.w, s_hv[o]));
+        if (h < 0.0f) { neg += 1; h = 0.0f; }
+        if (h <= FP_H_EPS_F) {
+            hu = 0.0f; hv = 0.0f;
+        } else {
+            const float u = __fdividef(hu, h), v = __fdividef(hv, h);
+            const float sp = sqrt_fast(__fmaf_rn(u, u, v * v));
+            const unsigned short oc = k == 0 ? occA : occB;
+            const float n0 = k == 0 ? n0A : n0B;
+            const int np = oc < FP_NP_CAP ? oc : FP_NP_CAP;
+            const float nm = S.coupling ? n0 + (float)np * n0 : n0;
+            const float denom = __fmaf_rn(dt * g * nm * nm * sp, __frcp_rn(h * cbrtf(h)), 1.0f);
+            hu = __fdividef(hu, denom);
+            hv = __fdividef(hv, denom);
+        }
+        if (!(h == h) || !(hu == hu) || !(hv == hv)) bad = 1;
+        if (h > FP_H_EPS_F) {
+            hk_[k] = h; huk_[k] = hu; hvk_[k] = hv;
+            sk_[k] = __fdividef(fmaxf(fabsf(hu), fabsf(hv)), h) + sqrt_fast(g * h);
+        }
+        if (h >= FP_H_DRY_F) wet = 1;
+        const size_t gi = gA + 32 * k;
+        S.h[p2][gi] = h;
+        S.hu[p2][gi] = hu;
+        S.hv[p2][gi] = hv;
+        if ((k == 0 ? occA : occB) != 0) S.occ[par][gi] = 0;
+    }
+    // CFL: the exact (correctly rounded) wave speed only for cells whose
+    // approximate speed is within 1e-5 of the warp's approximate maximum -- the
+    // approximation errs by < 1e-6, so the exact maximum is among them.
+    {
+        float amax = fmaxf(sk_[0], sk_[1]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+        const float thr = amax * (1.0f - 1e-5f);
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+            if (sk_[k] >= 0.0f && sk_[k] >= thr) smax = fmaxf(smax, fp_wave_speed(g, hk_[k], huk_[k], hvk_[k]));
+    }
+    // CTA reductions -> next clock slot
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        smax = fmaxf(smax, __shfl_xor_sync(0xffffffffu, smax, o));
+        wet |= __shfl_xor_sync(0xffffffffu, wet, o);
+        neg += __shfl_xor_sync(0xffffffffu, neg, o);
+        bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+    }
+    if (lane == 0) {
+        s_red[row] = smax;
+        s_redi[row] = wet | (bad << 1) | (neg << 2);
+    }
+    __syncthreads();
+    // boundary tiles only: FP64 accumulation of the mass through the domain edges (one warp)
+    const bool edge_x0 = x0 == 0, edge_x1 = x0 + FP_TX >= nx, edge_y0 = y0 == 0, edge_y1 = y0 + TY >= ny;
+    if (row == 1 && (edge_x0 || edge_x1 || edge_y0 || edge_y1)) {
+        const double dtdx = (double)dt * (double)S.dx;
+        for (int r = lane; r < TY; r += 32) {
+            const int j = y0 + r;
+            if (j >= ny) break;
+            if (edge_x0) S.bflux[2 * nx + j] += (double)s_bx[0][r] * dtdx;
+            if (edge_x1) S.bflux[2 * nx + ny + j] -= (double)s_bx[1][r] * dtdx;
+        }
+        for (int c = lane; c < FP_TX; c += 32) {
+            const int i = x0 + c;
+            if (i >= nx) break;
+            if (edge_y0) S.bflux[i] += (double)s_by[0][c] * dtdx;
+            if (edge_y1) S.bflux[nx + i] -= (double)s_by[1][c] * dtdx;
+        }
+    }
+    if (tid == 0) {
+        float m = 0.0f;
+        int w = 0, b = 0, ng = 0;
+        for (int k = 0; k < NT / 32; ++k) {
+            m = fmaxf(m, s_red[k]);
+            w |= s_redi[k] & 1;
+            b |= (s_redi[k] >> 1) & 1;
+            ng += s_redi[k] >> 2;
+        }
+        FpClock *nxt = &S.clock[(slot + 1) & 3];
+        if (m > 0.0f) atomicMax(&nxt->smax_bits, __float_as_uint(m));
+        if (w) atomicOr(&nxt->wet, 1);
+        if (b) fp_set_err(S, FP_ERR_NAN);
+        if (ng) atomicAdd(&S.cnt->neg_depth, (unsigned long long)ng);
+        if (bx == 0 && by == 0) {
+            const long long dt_ticks = s_dt;
+            const long long t1 = s_t + dt_ticks;
+            nxt->t = t1;
+            nxt->step = s_step + (dt_ticks > 0 ? 1 : 0);
+            nxt->h_in = (float)fp_hydro_depth(S, t1);
+            if (S.clock[slot].wet) atomicOr(&nxt->wet, 1);
+            FpClock *old = &S.clock[(slot + 2) & 3];
+            old->smax_bits = 0u;
+            old->wet = 0;
+        }
+    }
+    __syncthreads();
+    return true;
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long *mbar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+}  // namespace fpdev

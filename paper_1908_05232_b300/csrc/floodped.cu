@@ -9,6 +9,8 @@
 //                  +--> scan -> gather -> ped_step (stream 2) --+
 // Both branches read the state at step n, so they overlap.  Runs of 64 steps
 // are captured once into a CUDA graph per starting clock slot and replayed.
+// The default mode instead runs up to 256 steps per launch of the persistent
+// kernel (persist.cu).
 #include <cudaTypedefs.h>
 
 #include <algorithm>
@@ -96,6 +98,7 @@ struct fp_sim {
     long long pend_t = 0, pend_step = 0;
     int tile_rows = 16;
     FpTmaSet tma[2];
+    FpTmaSet tma16[2];  // 16-row tiles, for the persistent kernel
     cudaGraphExec_t graphs[4] = {nullptr, nullptr, nullptr, nullptr};
     int n_total = 0;
     std::string err;
@@ -104,6 +107,9 @@ struct fp_sim {
     std::vector<int> depot_h, barrier_h;
     uint4 *read_buf = nullptr;
     bool profiling = false;
+    int mode = FP_MODE_KERNELS;
+    int persist_ctas = 0, persist_smem = 0;
+    unsigned *grid_bar = nullptr;
     std::vector<cudaEvent_t> prof_ev;  // 4 per profiled step
     double prof[5] = {0, 0, 0, 0, 0};  // steps, hash ms, flood ms, pedestrian chain ms, step ms
 
@@ -130,17 +136,17 @@ struct fp_sim {
     size_t plane_elems() const { return (size_t)S.px * (size_t)(S.ny + 2); }
 };
 
-static int encode_tma(fp_sim *s) {
+static int encode_tma_rows(fp_sim *s, int rows, FpTmaSet out[2]) {
     auto enc = get_encode();
     if (!enc) return s->fail(FP_ECUDA, "cuTensorMapEncodeTiled entry point unavailable");
     const FpSim &S = s->S;
     cuuint64_t dims[2] = {(cuuint64_t)S.px, (cuuint64_t)(S.ny + 2)};
     cuuint64_t strides[1] = {(cuuint64_t)S.px * 4};
-    cuuint32_t box[2] = {(cuuint32_t)(FP_TX + 8), (cuuint32_t)(s->tile_rows + 2)};
+    cuuint32_t box[2] = {(cuuint32_t)(FP_TX + 8), (cuuint32_t)(rows + 2)};
     cuuint32_t es[2] = {1, 1};
     for (int p = 0; p < 2; ++p) {
         float *ptrs[4] = {S.h[p], S.hu[p], S.hv[p], S.z};
-        CUtensorMap *maps[4] = {&s->tma[p].h, &s->tma[p].hu, &s->tma[p].hv, &s->tma[p].z};
+        CUtensorMap *maps[4] = {&out[p].h, &out[p].hu, &out[p].hv, &out[p].z};
         for (int k = 0; k < 4; ++k) {
             CUresult r = enc(maps[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, ptrs[k], dims, strides, box, es,
                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -149,6 +155,12 @@ static int encode_tma(fp_sim *s) {
         }
     }
     return FP_OK;
+}
+
+static int encode_tma(fp_sim *s) {
+    int rc = encode_tma_rows(s, s->tile_rows, s->tma);
+    if (rc == FP_OK) rc = encode_tma_rows(s, 16, s->tma16);
+    return rc;
 }
 
 static int upload_nav(fp_sim *s) {
@@ -219,7 +231,7 @@ static int prepare(fp_sim *s) {
 static void launch_step(fp_sim *s, int par, int slot, cudaEvent_t *ev = nullptr) {
     const FpSim &S = s->S;
     if (ev) cudaEventRecord(ev[0], s->stream);
-    fp_launch_hash_count(S, s->stream);
+    fp_launch_hash_count(S, par, s->stream);
     cudaEventRecord(s->ev_fork, s->stream);
     if (ev) cudaEventRecord(ev[1], s->stream);
     cudaStreamWaitEvent(s->stream2, s->ev_fork, 0);
@@ -233,7 +245,44 @@ static void launch_step(fp_sim *s, int par, int slot, cudaEvent_t *ev = nullptr)
     cudaStreamWaitEvent(s->stream, s->ev_join, 0);
 }
 
+// Persistent kernel with the global timer stamped by CTA 0 at every phase end.
+static int step_profiled_persistent(fp_sim *s, int n) {
+    int left = n;
+    while (left > 0) {
+        const int m = left < 256 ? left : 256;
+        const size_t cnt = 4 * (size_t)m + 1;
+        unsigned long long *ts = s->dalloc<unsigned long long>(cnt);
+        if (!ts) return s->fail(FP_ENOMEM, "profile stamps");
+        FpSim S = s->S;
+        S.phase_ts = ts;
+        S.phase_ts_steps = m;
+        cudaError_t e = fp_launch_persistent(S, s->tma16, s->par, s->slot, m, s->grid_bar, s->persist_ctas,
+                                             s->persist_smem, s->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+        std::vector<unsigned long long> h(cnt);
+        if (e == cudaSuccess) e = cudaMemcpy(h.data(), ts, cnt * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+        s->allocs.pop_back();
+        cudaFree(ts);
+        if (e != cudaSuccess) return s->cuda_fail(e, "profiled persistent steps");
+        for (int k = 0; k < m; ++k) {
+            const double a = (double)(h[4 * k + 1] - h[4 * k]) * 1e-6;      // scan phase
+            const double b = (double)(h[4 * k + 2] - h[4 * k + 1]) * 1e-6;  // prefix + gather
+            const double c = (double)(h[4 * k + 4] - h[4 * k + 2]) * 1e-6;  // flood + pedestrians
+            s->prof[0] += 1;
+            s->prof[1] += a;
+            s->prof[2] += c;
+            s->prof[3] += b;
+            s->prof[4] += a + b + c;
+        }
+        if (m & 1) s->par ^= 1;
+        s->slot = (s->slot + m) & 3;
+        left -= m;
+    }
+    return FP_OK;
+}
+
 static int step_profiled(fp_sim *s, int n) {
+    if (s->mode == FP_MODE_PERSISTENT) return step_profiled_persistent(s, n);
     if ((int)s->prof_ev.size() < 4 * n) {
         for (int k = (int)s->prof_ev.size(); k < 4 * n; ++k) {
             cudaEvent_t e;
@@ -308,7 +357,8 @@ int fp_sim_create(const fp_config *cfg, fp_sim **out) {
     }
     ok &= (S.z = s->dalloc<float>(pe)) != nullptr;
     ok &= (S.n0 = s->dalloc<float>(pe)) != nullptr;
-    ok &= (S.occ = s->dalloc<unsigned short>(pe + 2)) != nullptr;
+    ok &= (S.occ[0] = s->dalloc<unsigned short>(pe + 2)) != nullptr;
+    ok &= (S.occ[1] = s->dalloc<unsigned short>(pe + 2)) != nullptr;
     unsigned char *bcd[4];
     for (int e = 0; e < 4; ++e) {
         const int len = e < 2 ? c.nx : c.ny;
@@ -339,6 +389,8 @@ int fp_sim_create(const fp_config *cfg, fp_sim **out) {
     ok &= (S.scan_flags = s->dalloc<unsigned long long>((size_t)fp_scan_tiles(S.nbins))) != nullptr;
     ok &= (S.bflux = s->dalloc<double>(2 * (size_t)c.nx + 2 * (size_t)c.ny)) != nullptr;
     ok &= (S.partials = s->dalloc<double>(148 * 4)) != nullptr;
+    ok &= (S.scan_part = s->dalloc<int>(2048)) != nullptr;
+    ok &= (s->grid_bar = s->dalloc<unsigned>(2)) != nullptr;
     if (!ok) {
         g_create_error = "device allocation failed";
         fp_destroy(s);
@@ -360,6 +412,12 @@ int fp_sim_create(const fp_config *cfg, fp_sim **out) {
     if (rc == FP_OK) {
         cudaError_t ea = fp_flood_init_attributes();
         if (ea != cudaSuccess) rc = s->cuda_fail(ea, "flood kernel attributes");
+    }
+    if (rc == FP_OK) {
+        s->persist_smem = fp_flood_smem_bytes(16);
+        s->persist_ctas = fp_persistent_ctas(s->persist_smem);
+        cudaGetLastError();
+        s->mode = FP_MODE_KERNELS;
     }
     cudaError_t e = cudaDeviceSynchronize();
     if (rc == FP_OK && e != cudaSuccess) rc = s->cuda_fail(e, "create");
@@ -562,6 +620,19 @@ int fp_step(fp_sim *s, int32_t n_steps) {
         if (rc != FP_OK) return rc;
     }
     if (s->profiling) return step_profiled(s, n_steps);
+    if (s->mode == FP_MODE_PERSISTENT) {
+        int left = n_steps;
+        while (left > 0) {
+            const int n = left < 256 ? left : 256;
+            cudaError_t e = fp_launch_persistent(s->S, s->tma16, s->par, s->slot, n, s->grid_bar, s->persist_ctas,
+                                                 s->persist_smem, s->stream);
+            if (e != cudaSuccess) return s->cuda_fail(e, "persistent launch");
+            if (n & 1) s->par ^= 1;
+            s->slot = (s->slot + n) & 3;
+            left -= n;
+        }
+        return FP_OK;
+    }
     int left = n_steps;
     while (left > 0) {
         if (left >= kGraphSteps) {
@@ -594,6 +665,17 @@ int fp_step(fp_sim *s, int32_t n_steps) {
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return s->cuda_fail(e, "step launch");
+    return FP_OK;
+}
+
+int fp_set_step_mode(fp_sim *s, int32_t mode) {
+    if (!s) return FP_EINVAL;
+    if (mode != FP_MODE_KERNELS && mode != FP_MODE_PERSISTENT) return s->fail(FP_EINVAL, "unknown step mode");
+    if (mode == FP_MODE_PERSISTENT && s->persist_ctas <= 0)
+        return s->fail(FP_EINVAL, "cooperative launch unavailable on this device");
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return s->cuda_fail(e, "mode switch");
+    s->mode = mode;
     return FP_OK;
 }
 

@@ -49,7 +49,8 @@ struct __align__(16) FpClock {
     long long step;         // step index (random counter)
     unsigned int smax_bits; // max over wet cells of max(|u|,|v|) + sqrt(g h), float bits
     int wet;                // sticky: some cell held >= 1 mm
-    int pad[2];
+    float h_in;             // inflow hydrograph depth at t, rounded to FP32 (evaluated once per step)
+    int pad;
 };
 
 struct FpCounters {
@@ -83,7 +84,7 @@ struct FpSim {
     int nb, n_layers, bpc;     // barrier cells, layers, bags per cell-layer
     float *h[2], *hu[2], *hv[2];
     float *z, *n0;
-    unsigned short *occ;
+    unsigned short *occ[2];    // evacuees per cell, by the parity of the step that uses them
     const unsigned char *bc[4];
     const unsigned char *walk, *exitm, *nav[3];
     const int *barrier;
@@ -98,6 +99,9 @@ struct FpSim {
     unsigned long long *scan_flags;  // per scan tile: epoch<<34 | status<<32 | value
     double *bflux;             // 2 nx + 2 ny inflow volume per boundary face (S, N, W, E)
     double *partials;          // mass reduction partial sums
+    int *scan_part;            // persistent kernel: bin-count total of each CTA's chunk
+    unsigned long long *phase_ts;  // optional: global timer at each persistent-kernel phase end
+    int phase_ts_steps;            // steps recorded in phase_ts (4 stamps per step + 1)
 };
 
 __device__ __forceinline__ size_t fp_pidx(const FpSim &S, int i, int j) {
@@ -192,7 +196,7 @@ void fp_launch_init_clock(const FpSim &S, int par, int slot, cudaStream_t st);
 void fp_launch_mass(const FpSim &S, int par, cudaStream_t st);
 int fp_flood_smem_bytes(int tile_rows);
 cudaError_t fp_flood_init_attributes();
-void fp_launch_hash_count(const FpSim &S, cudaStream_t st);
+void fp_launch_hash_count(const FpSim &S, int par, cudaStream_t st);
 void fp_launch_scan(const FpSim &S, cudaStream_t st);
 void fp_launch_gather(const FpSim &S, cudaStream_t st);
 void fp_launch_ped_step(const FpSim &S, int par, int slot, cudaStream_t st);
@@ -200,3 +204,6 @@ void fp_launch_assign_ids(const FpSim &S, int first_slot, int first_id, int coun
 void fp_launch_read_peds(const FpSim &S, uint4 *out, int n_total, cudaStream_t st);
 int fp_scan_tiles(int nbins);
 void fp_note_error(const char *msg);  // message for fp_last_error(NULL)
+int fp_persistent_ctas(int smem_dynamic);
+cudaError_t fp_launch_persistent(const FpSim &S, const FpTmaSet tma[2], int par, int slot, int nsteps,
+                                 unsigned *bar, int ctas, int smem_dynamic, cudaStream_t st);

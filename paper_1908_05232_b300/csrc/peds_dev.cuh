@@ -1,0 +1,297 @@
+// peds_dev.cuh -- device code of the pedestrian side of the coupled step
+// (Sections 2.3-2.4), shared by the per-step kernels and the persistent
+// coupled-step kernel.
+//
+//   hash_record   a record's hash bin (hk x hk cells, bin side >= the 1 m
+//                 neighbour radius) or the "exited" bin, its slot in the bin
+//                 (integer atomic) and the evacuee count of its cell (uint16
+//                 lanes of the occupancy plane, N_p of Section 2.4);
+//   barrier_and_snapshot   completed sandbag layers raise z;
+//   ped_group     eight lanes per pedestrian: Table 1 state from the cell's
+//                 h, u, v at step n, responder task, navigation direction,
+//                 repulsion from neighbours in the 3 x 3 bins split over the
+//                 lanes (integer fixed point, so the sum does not depend on the
+//                 order records sit in a bin), velocity relaxation and cap, move
+//                 with wall sliding, exit.
+#pragma once
+#include "fp_common.cuh"
+
+namespace fpdev {
+
+
+__constant__ float c_speed[5] = {0.0f, 1.8f, 0.9f, 0.45f, 0.0f};  // Table 1 (index 0: own dry speed)
+constexpr float kTau = 0.5f, kA = 2.0f, kB = 0.3f, kRb = 0.25f, kR = 1.0f, kSide = 0.5f;
+constexpr int kTPick = 30 * 1048576, kTDrop = 30 * 1048576;
+constexpr float kBagT = 0.25f;
+__constant__ int c_ox[8] = {1, 0, -1, 0, 1, -1, -1, 1};
+__constant__ int c_oy[8] = {0, 1, 0, -1, 1, 1, -1, -1};
+
+enum { G_NONE = 0, G_EXIT = 1, G_DEPOT = 2, G_BARRIER = 3, G_STRAIGHT = 4 };
+
+__device__ __forceinline__ bool walkable_at(const FpSim &S, float x, float y) {
+    const int i = fp_cell_of(x, S.dx), j = fp_cell_of(y, S.dx);
+    if (i < 0 || j < 0 || i >= S.nx || j >= S.ny) return false;
+    return S.walk[(size_t)j * S.nx + i] != 0;
+}
+
+
+constexpr int kGroup = 8;  // lanes per pedestrian
+
+// Values every thread of a step reads once (filled by one thread per CTA).
+struct StepCtl {
+    long long dt_ticks, step;
+    unsigned long long bags;
+    int wet, nA;
+};
+
+__device__ __forceinline__ void load_step_ctl(const FpSim &S, int slot, int nA, StepCtl &ctl) {
+    const FpClock c = S.clock[slot];
+    ctl.dt_ticks = fp_dt_ticks(S, c, c.h_in);
+    ctl.step = c.step;
+    ctl.wet = c.wet;
+    ctl.bags = S.cnt->bags_snap;
+    ctl.nA = nA;
+}
+
+// Hash one record of B (index i) for the next step: its bin (or the exited bin),
+// its slot in the bin and, for a present evacuee, +1 on its cell's count.
+__device__ __forceinline__ void hash_record(const FpSim &S, int i, float x, float y, unsigned meta,
+                                            unsigned short *occ) {
+    int key = S.nbins;
+    if (!FP_META_EXITED(meta)) {
+        const int ci = fp_cell_of(x, S.dx), cj = fp_cell_of(y, S.dx);
+        key = (cj / S.hk) * S.nbx + ci / S.hk;
+        if (FP_META_ROLE(meta) == 0) {
+            const size_t o = fp_pidx(S, ci, cj);
+            const unsigned shift = (unsigned)(o & 1) * 16u;
+            unsigned *w = reinterpret_cast<unsigned *>(occ + (o & ~(size_t)1));
+            const unsigned old = atomicAdd(w, 1u << shift);
+            if (((old >> shift) & 0xffffu) == 0xffffu) fp_set_err(S, FP_ERR_OCC_OVERFLOW);
+        }
+    }
+    S.pkey[i] = key;
+    S.pslot[i] = atomicAdd(&S.bin_count[key], 1);
+}
+
+// Completed sandbag cell-layers raise the bed (one thread, before the flood
+// update of the step reads z); snapshot of the bag count for the step.
+__device__ __forceinline__ void barrier_and_snapshot(const FpSim &S) {
+    FpCounters *C = S.cnt;
+    if (S.nb > 0 && S.n_layers > 0) {
+        unsigned long long done = C->total_bags / (unsigned long long)S.bpc;
+        const unsigned long long cap = (unsigned long long)S.nb * (unsigned long long)S.n_layers;
+        if (done > cap) done = cap;
+        for (unsigned long long k = C->applied; k < done; ++k) {
+            const int c = S.barrier[k % (unsigned long long)S.nb];
+            S.z[fp_pidx(S, c % S.nx, c / S.nx)] += kBagT;
+        }
+        C->applied = done;
+    }
+    C->bags_snap = C->total_bags;
+    for (int k = 0; k < 5; ++k) C->hist[k] = 0ull;
+}
+
+// One pedestrian (record j of A) by a group of kGroup lanes (sub = lane in the
+// group).  lookup(key) gives the first record of hash bin key in A.  With
+// hash_next the group's first lane also hashes its output record for the next
+// step.  Every lane of the warp must call this (shuffles over the full warp).
+template <class Lookup>
+__device__ __forceinline__ void ped_group(const FpSim &S, int par, const StepCtl &ctl, int j, int sub,
+                                          const Lookup &lookup, bool hash_next) {
+    FpCounters *C = S.cnt;
+    const bool leader = sub == 0;
+    const bool valid = j < ctl.nA;
+    const long long dt_ticks = ctl.dt_ticks;
+    const bool live = valid && dt_ticks > 0;
+    const float dx = S.dx;
+    const float dt = (float)dt_ticks * (1.0f / FP_TICKS_F);
+    int hr = 0, role = 0, task = 0, timer = 0, goal = G_NONE, target = -1, ci = 0, cj = 0;
+    float x = 0.f, y = 0.f, vx = 0.f, vy = 0.f, speed = 0.f, vdx = 0.f, vdy = 0.f;
+    unsigned id = 0, v0bits = 0;
+    bool drop = false;
+    int rk0[3] = {0, 0, 0}, rk1[3] = {0, 0, 0};  // record ranges of the three bin rows
+    if (valid) {
+        const uint4 pa = S.pedA[2 * j], pb = S.pedA[2 * j + 1];
+        if (dt_ticks == 0) {
+            if (leader) {
+                S.pedB[2 * j] = pa;
+                S.pedB[2 * j + 1] = pb;
+                if (hash_next) hash_record(S, j, __uint_as_float(pa.x), __uint_as_float(pa.y), pb.y, S.occ[par ^ 1]);
+            }
+        } else {
+            x = __uint_as_float(pa.x); y = __uint_as_float(pa.y);
+            vx = __uint_as_float(pa.z); vy = __uint_as_float(pa.w);
+            id = pb.x;
+            const unsigned meta = pb.y;
+            timer = (int)pb.z;
+            v0bits = pb.w;
+            role = FP_META_ROLE(meta);
+            task = FP_META_TASK(meta);
+            ci = fp_cell_of(x, dx);
+            cj = fp_cell_of(y, dx);
+            const int c = cj * S.nx + ci;
+            const size_t pc = fp_pidx(S, ci, cj);
+            // independent loads issued together: the cell's water, the 3 x 3 bin ranges
+            const float hc = S.h[par][pc], huc = S.hu[par][pc], hvc = S.hv[par][pc];
+            {
+                const int bx = ci / S.hk, by = cj / S.hk;
+                const int bx0 = bx > 0 ? bx - 1 : 0, bx1 = bx + 1 < S.nbx ? bx + 1 : S.nbx - 1;
+#pragma unroll
+                for (int r = 0; r < 3; ++r) {
+                    const int yy = by - 1 + r;
+                    if (yy < 0 || yy >= S.nby) { rk0[r] = 0; rk1[r] = 0; continue; }
+                    rk0[r] = lookup(yy * S.nbx + bx0);
+                    rk1[r] = lookup(yy * S.nbx + bx1 + 1);
+                }
+            }
+            hr = fp_hr_state(hc, huc, hvc);
+            speed = hr == 0 ? __uint_as_float(v0bits) : c_speed[hr];
+            if (role == 0) {
+                goal = (S.evac_trigger == 0 || ctl.wet) ? G_EXIT : G_NONE;
+            } else {
+                const unsigned long long cap =
+                    (unsigned long long)S.nb * (unsigned long long)S.n_layers * (unsigned long long)S.bpc;
+                if (task != 4 && ctl.bags >= cap) task = 4;
+                switch (task) {
+                    case 4: goal = G_EXIT; break;
+                    case 0:
+                        if (S.nav[1][c] == FP_AT_GOAL) { task = 1; timer = kTPick; }
+                        else goal = G_DEPOT;
+                        break;
+                    case 1:
+                        timer = (int)(timer - dt_ticks);
+                        if (timer <= 0) { task = 2; timer = 0; }
+                        break;
+                    case 2:
+                        target = S.barrier[(ctl.bags / (unsigned long long)S.bpc) % (unsigned long long)S.nb];
+                        if (c == target) { task = 3; timer = kTDrop; }
+                        else if (S.nav[2][c] == FP_AT_GOAL) goal = G_STRAIGHT;
+                        else goal = G_BARRIER;
+                        break;
+                    case 3:
+                        timer = (int)(timer - dt_ticks);
+                        if (timer <= 0) { drop = true; task = 0; timer = 0; }
+                        break;
+                    default: break;
+                }
+                if (task == 1 || task == 3) speed = 0.0f;
+            }
+            // desired velocity
+            float ex = 0.0f, ey = 0.0f, sdes = speed;
+            if (goal != G_NONE) {
+                float tx = 0.0f, ty = 0.0f;
+                bool have = false, arriving = false;
+                if (goal == G_STRAIGHT) {
+                    tx = ((float)(target % S.nx) + 0.5f) * dx;
+                    ty = ((float)(target / S.nx) + 0.5f) * dx;
+                    have = arriving = true;
+                } else {
+                    const unsigned char *nav = S.nav[goal == G_EXIT ? 0 : goal == G_DEPOT ? 1 : 2];
+                    const int code = nav[c];
+                    if (code < 8) {
+                        const int ti = ci + c_ox[code], tj = cj + c_oy[code];
+                        tx = ((float)ti + 0.5f) * dx;
+                        ty = ((float)tj + 0.5f) * dx;
+                        have = true;
+                        arriving = nav[tj * S.nx + ti] == FP_AT_GOAL;
+                    }
+                }
+                if (have) {
+                    const float ddx = tx - x, ddy = ty - y;
+                    const float len = sqrtf(__fmaf_rn(ddx, ddx, ddy * ddy));
+                    if (len > 0.0f) { ex = ddx / len; ey = ddy / len; }
+                    if (arriving && len / dt < sdes) sdes = len / dt;
+                }
+            }
+            if (goal != G_NONE && speed > 0.0f) {
+                unsigned long long ctr[4] = {(unsigned long long)id, (unsigned long long)ctl.step, 0ull, 0ull};
+                fp_philox4x64(ctr, S.seed, 0ull);
+                const float xi1 = (float)(unsigned)(ctr[0] >> 40) * (1.0f / 16777216.0f);
+                const float xi2 = (float)(unsigned)(ctr[1] >> 40) * (1.0f / 16777216.0f);
+                vdx = __fmaf_rn(S.ped_noise, xi1 - 0.5f, sdes * ex);
+                vdy = __fmaf_rn(S.ped_noise, xi2 - 0.5f, sdes * ey);
+            }
+        }
+    }
+    // repulsion from neighbours in the 3 x 3 bins, split over the group.  Each
+    // pair term (|term| < 16 m/s^2) is rounded to an int32 count of 2^-18 m/s^2
+    // and summed in 64-bit integers, so the total does not depend on order.
+    long long Fx = 0, Fy = 0;
+    if (live) {
+        const float vdn = sqrtf(__fmaf_rn(vdx, vdx, vdy * vdy));
+        const float inv_vdn = vdn > 0.0f ? __frcp_rn(vdn) : 0.0f;
+        const float fcut = __expf((2.0f * kRb - kR) * (1.0f / kB));
+#pragma unroll 1
+        for (int r = 0; r < 3; ++r) {
+            for (int k = rk0[r] + sub; k < rk1[r]; k += kGroup) {
+                if (k == j) continue;
+                const float4 q = *reinterpret_cast<const float4 *>(&S.pedA[2 * k]);
+                const float rx = x - q.x, ry = y - q.y;
+                if (fabsf(rx) >= kR || fabsf(ry) >= kR) continue;
+                const float d2 = __fmaf_rn(rx, rx, ry * ry);
+                if (d2 >= kR * kR || d2 <= 0.0f) continue;
+                const float d = sqrtf(d2);
+                const float invd = __frcp_rn(d);
+                const float fm = kA * (__expf((2.0f * kRb - d) * (1.0f / kB)) - fcut);
+                const float nx_ = rx * invd, ny_ = ry * invd;
+                float fx = fm * nx_, fy = fm * ny_;
+                if (vdn > 0.0f) {
+                    const float w = -__fmaf_rn(vdx, nx_, vdy * ny_) * inv_vdn;
+                    if (w > 0.0f) {
+                        const float sw = kSide * w * fm;
+                        fx = __fmaf_rn(sw, -ny_, fx);
+                        fy = __fmaf_rn(sw, nx_, fy);
+                    }
+                }
+                Fx += (long long)__float2int_rn(fx * 262144.0f);
+                Fy += (long long)__float2int_rn(fy * 262144.0f);
+            }
+        }
+    }
+#pragma unroll
+    for (int o = kGroup / 2; o > 0; o >>= 1) {
+        Fx += __shfl_xor_sync(0xffffffffu, Fx, o, kGroup);
+        Fy += __shfl_xor_sync(0xffffffffu, Fy, o, kGroup);
+    }
+    if (live && leader) {
+        const float fxs = __ll2float_rn(Fx) * (1.0f / 262144.0f), fys = __ll2float_rn(Fy) * (1.0f / 262144.0f);
+        // relaxation toward the desired velocity, capped at the state's speed
+        const float a = fminf(1.0f, dt / kTau);
+        vx = __fmaf_rn(dt, fxs, __fmaf_rn(a, vdx - vx, vx));
+        vy = __fmaf_rn(dt, fys, __fmaf_rn(a, vdy - vy, vy));
+        if (speed <= 0.0f) {
+            vx = 0.0f; vy = 0.0f;
+        } else {
+            const float sp = sqrtf(__fmaf_rn(vx, vx, vy * vy));
+            if (sp > speed) { vx = vx * (speed / sp); vy = vy * (speed / sp); }
+        }
+        float xn = __fmaf_rn(dt, vx, x), yn = __fmaf_rn(dt, vy, y);
+        if (walkable_at(S, xn, yn)) {
+        } else if (walkable_at(S, xn, y)) { yn = y; vy = 0.0f; }
+        else if (walkable_at(S, x, yn)) { xn = x; vx = 0.0f; }
+        else { xn = x; yn = y; vx = 0.0f; vy = 0.0f; }
+        int exited = 0;
+        if (goal == G_EXIT) {
+            const int ii = fp_cell_of(xn, dx), jj = fp_cell_of(yn, dx);
+            if (S.exitm[(size_t)jj * S.nx + ii]) exited = 1;
+        }
+        if (exited) atomicAdd(&C->n_exited, 1ull);
+        if (drop) atomicAdd(&C->total_bags, 1ull);
+        const unsigned meta_out = FP_META(role, task, hr, exited);
+        S.pedB[2 * j] = make_uint4(__float_as_uint(xn), __float_as_uint(yn), __float_as_uint(vx), __float_as_uint(vy));
+        S.pedB[2 * j + 1] = make_uint4(id, meta_out, (unsigned)timer, v0bits);
+        if (hash_next) hash_record(S, j, xn, yn, meta_out, S.occ[par ^ 1]);
+    }
+    // state histogram, aggregated per warp over the group leaders
+    if (dt_ticks > 0) {
+        const int lane = threadIdx.x & 31;
+#pragma unroll
+        for (int s = 0; s < 5; ++s) {
+            const unsigned m = __ballot_sync(0xffffffffu, live && leader && hr == s);
+            if (lane == 0 && m) atomicAdd(&C->hist[s], (unsigned long long)__popc(m));
+        }
+    }
+}
+
+
+}  // namespace fpdev

@@ -1,0 +1,263 @@
+// persist.cu -- persistent coupled-step kernel: many steps of the whole coupled
+// update in one cooperative launch (every CTA resident), the phases of a step
+// separated by grid barriers with bounded waits.
+//
+// Launch start:  H   hash every record of B (bin, slot, evacuee counts).
+// Each step:     S1  CTA 0 applies completed sandbag layers to z and snapshots
+//                    the bag count; every CTA scans its contiguous chunk of
+//                    bin counts (local exclusive starts), re-zeroes them and
+//                    publishes the chunk total;
+//                --- grid barrier ---
+//                G   every CTA forms the prefix of the chunk totals in shared
+//                    memory (bin start = chunk prefix + local start) and
+//                    gathers its share of B into bin order A;
+//                --- grid barrier ---
+//                FP  flood tiles (flood_dev.cuh) from the first CTA up and
+//                    pedestrian chunks of eight lanes per pedestrian
+//                    (peds_dev.cuh) from the last CTA down, concurrently; each
+//                    output record is hashed at once for the next step into
+//                    the other parity's evacuee-count plane;
+//                --- grid barrier ---
+// The last step does not hash its output, so a launch ends with the same
+// invariants as the per-step kernels (bin counts and evacuee counts zero).
+#include "flood_dev.cuh"
+#include "peds_dev.cuh"
+
+namespace {
+using namespace fpdev;
+
+constexpr int kPT = 512;       // threads per CTA = 32 x TY with TY = 16
+constexpr int kPTY = 16;
+constexpr int kMaxCTAs = 2048;
+
+struct PersistTma {
+    FpTmaSet p[2];
+};
+
+// Grid barrier: arrival counter bar[0], generation bar[1].  Each CTA reads the
+// generation before arriving, so the last arriver's bump is always seen as a
+// change.  The wait is bounded; on timeout the error flag is set and every CTA
+// returns (those still waiting time out in turn).
+__device__ __forceinline__ bool grid_sync(unsigned *bar, const FpSim &S) {
+    __shared__ int s_fail;
+    // generic-proxy stores of this phase become visible to later TMA reads
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *vgen = bar + 1;
+        const unsigned gen = *vgen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(bar, 1u);
+        int fail = 0;
+        if (arrived == gridDim.x - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            int it = 0;
+            while (*vgen == gen) {
+                if (++it > (1 << 22)) { fail = 1; break; }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        if (fail) fp_set_err(S, FP_ERR_TIMEOUT);
+        s_fail = fail || (*(volatile unsigned *)&S.cnt->err & FP_ERR_TIMEOUT) != 0u;
+    }
+    __syncthreads();
+    return !s_fail;
+}
+
+// exclusive scan of one value per thread over the CTA (kPT threads); returns
+// the thread's prefix, total in *total
+__device__ __forceinline__ int block_exclusive_scan(int v, int *total) {
+    __shared__ int s_w[kPT / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) s_w[wid] = incl;
+    __syncthreads();
+    int pre = 0, tot = 0;
+#pragma unroll
+    for (int w = 0; w < kPT / 32; ++w) {
+        pre += w < wid ? s_w[w] : 0;
+        tot += s_w[w];
+    }
+    __syncthreads();
+    *total = tot;
+    return pre + incl - v;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// CTA 0 stamps the global timer after a phase (profiling only)
+__device__ __forceinline__ void stamp(const FpSim &S, int idx) {
+    if (S.phase_ts != nullptr && blockIdx.x == 0 && threadIdx.x == 0 && idx < 4 * S.phase_ts_steps + 1)
+        S.phase_ts[idx] = global_ns();
+}
+
+struct ChunkLookup {
+    const int *local;  // chunk-local starts
+    const int *base;   // shared: prefix of chunk totals
+    int chunk;
+    __device__ int operator()(int key) const { return base[key / chunk] + local[key]; }
+};
+
+__global__ void __launch_bounds__(kPT, 2) persistent_kernel(const __grid_constant__ PersistTma tm,
+                                                            const __grid_constant__ FpSim S, int par0, int slot0,
+                                                            int nsteps, unsigned *bar) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) unsigned long long mbar;
+    __shared__ int s_base[kMaxCTAs];
+    __shared__ StepCtl s_ctl;
+    FpCounters *C = S.cnt;
+    const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x;
+    const int nbin1 = S.nbins + 1;
+    const int chunk = (nbin1 + G - 1) / G;
+    const int tiles_x = (S.nx + FP_TX - 1) / FP_TX, tiles_y = (S.ny + kPTY - 1) / kPTY;
+    const int ntiles = tiles_x * tiles_y;
+    if (tid == 0) mbar_init(&mbar);
+    unsigned parity = 0;
+
+    // H: hash the current records of B
+    {
+        const int nB = C->nB;
+        for (int i = cta * kPT + tid; i < nB; i += G * kPT) {
+            const uint4 pa = S.pedB[2 * i], pb = S.pedB[2 * i + 1];
+            hash_record(S, i, __uint_as_float(pa.x), __uint_as_float(pa.y), pb.y, S.occ[par0]);
+        }
+    }
+    if (!grid_sync(bar, S)) return;
+    stamp(S, 0);
+
+    for (int s = 0; s < nsteps; ++s) {
+        const int par = par0 ^ (s & 1), slot = (slot0 + s) & 3;
+        // S1: sandbag layers + bag snapshot; chunk-local scan of the bin counts
+        if (cta == 0 && tid == 0) barrier_and_snapshot(S);
+        {
+            const int lo = cta * chunk, hi = min(lo + chunk, nbin1);
+            int running = 0;
+            for (int base = lo; base < hi; base += kPT * 4) {
+                int v[4], sum = 0;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int idx = base + tid * 4 + k;
+                    v[k] = idx < hi ? S.bin_count[idx] : 0;
+                    sum += v[k];
+                }
+                int total;
+                int run = running + block_exclusive_scan(sum, &total);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int idx = base + tid * 4 + k;
+                    if (idx < hi) {
+                        S.bin_start[idx] = run;
+                        S.bin_count[idx] = 0;
+                    }
+                    run += v[k];
+                }
+                running += total;
+            }
+            if (tid == 0) S.scan_part[cta] = running;
+        }
+        if (!grid_sync(bar, S)) return;
+        stamp(S, 4 * s + 1);
+
+        // G: bin starts, gather B -> A
+        {
+            int total;
+            for (int c0 = 0; c0 < G; c0 += kPT) {
+                const int c = c0 + tid;
+                const int v = c < G ? S.scan_part[c] : 0;
+                const int pre = block_exclusive_scan(v, &total);
+                const int carry = c0 == 0 ? 0 : s_base[c0 - 1] + S.scan_part[c0 - 1];
+                if (c < G) s_base[c] = carry + pre;
+                __syncthreads();
+            }
+        }
+        const ChunkLookup lookup{S.bin_start, s_base, chunk};
+        const int nA = lookup(S.nbins);
+        {
+            const int nB = C->nB;
+            for (int i = cta * kPT + tid; i < nB; i += G * kPT) {
+                const int key = S.pkey[i];
+                const uint4 a = S.pedB[2 * i], b = S.pedB[2 * i + 1];
+                if (key == S.nbins) {
+                    S.arch[2 * (size_t)b.x] = a;
+                    S.arch[2 * (size_t)b.x + 1] = b;
+                } else {
+                    const int dst = lookup(key) + S.pslot[i];
+                    S.pedA[2 * dst] = a;
+                    S.pedA[2 * dst + 1] = b;
+                }
+            }
+        }
+        if (!grid_sync(bar, S)) return;
+        stamp(S, 4 * s + 2);
+        // FP: flood tiles (dealt from the first CTA up) and pedestrian chunks
+        // (dealt from the last CTA down) in one phase -- both read the state at
+        // step n; pedestrian outputs are hashed for the next step (not after the
+        // last), into the other parity's evacuee-count plane.
+        if (tid == 0) {
+            load_step_ctl(S, slot, nA, s_ctl);
+            if (cta == 0) {
+                C->nA = nA;
+                C->nB = nA;
+                if (s_ctl.dt_ticks > 0) C->ped_updates += (unsigned long long)nA;
+            }
+        }
+        for (int t = cta; t < ntiles; t += G) {
+            if (!flood_tile<kPTY>(tm.p[par], S, par, slot, t % tiles_x, t / tiles_x, smem_raw, &mbar, parity))
+                return;
+            parity ^= 1u;
+        }
+        __syncthreads();
+        const StepCtl ctl = s_ctl;
+        const bool hash_next = s + 1 < nsteps;
+        constexpr int kPedPerCTA = kPT / kGroup;
+        for (int pcx = G - 1 - cta; pcx * kPedPerCTA < nA; pcx += G)
+            ped_group(S, par, ctl, pcx * kPedPerCTA + tid / kGroup, tid & (kGroup - 1), lookup, hash_next);
+        if (!grid_sync(bar, S)) return;
+        stamp(S, 4 * s + 4);
+    }
+}
+
+}  // namespace
+
+int fp_persistent_ctas(int smem_dynamic) {
+    static int cached = -1;
+    if (cached >= 0) return cached;
+    int dev = 0, sms = 0, per_sm = 0, coop = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    if (!coop) return cached = 0;
+    if (cudaFuncSetAttribute(persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_dynamic) !=
+        cudaSuccess)
+        return cached = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_kernel, kPT, smem_dynamic) != cudaSuccess)
+        return cached = 0;
+    int g = sms * per_sm;
+    if (g > kMaxCTAs) g = kMaxCTAs;
+    return cached = g;
+}
+
+cudaError_t fp_launch_persistent(const FpSim &S, const FpTmaSet tma[2], int par, int slot, int nsteps,
+                                 unsigned *bar, int ctas, int smem_dynamic, cudaStream_t st) {
+    PersistTma tm;
+    tm.p[0] = tma[0];
+    tm.p[1] = tma[1];
+    FpSim s = S;
+    void *args[] = {(void *)&tm, (void *)&s, (void *)&par, (void *)&slot, (void *)&nsteps, (void *)&bar};
+    return cudaLaunchCooperativeKernel((const void *)persistent_kernel, dim3(ctas), dim3(kPT), args,
+                                       (size_t)smem_dynamic, st);
+}

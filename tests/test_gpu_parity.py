@@ -317,17 +317,30 @@ def test_determinism(P):
     assert np.array_equal(a.peds(), b.peds())
 
 
-def test_graph_and_direct_launch_agree(P):
-    """64-step CUDA-graph replay and one-at-a-time launches give the same bytes."""
-    sc = S.plain_coupled_128(seed=5)
-    a = run_gpu(P, sc, 128)
-    b = P.from_scenario(sc)
-    for _ in range(128):
-        b.step(1)
+@pytest.mark.parametrize("case", ["plain128", "barrier192"])
+def test_step_modes_agree(P, case):
+    """The persistent kernel (up to 256 steps per launch), 64-step CUDA graphs of
+    the per-step kernels, and one-at-a-time launches give the same bytes."""
+    from paper_1908_05232_b300 import _native as N
+    sc = S.plain_coupled_128(seed=5) if case == "plain128" else _barrier_wet()
+    n = 300
+    a = P.from_scenario(sc, mode=N.FP_MODE_PERSISTENT)
+    a.step(n)
+    a.synchronize()
+    b = P.from_scenario(sc, mode=N.FP_MODE_KERNELS)
+    b.step(n)
     b.synchronize()
-    for x, y in zip(fields(a), fields(b)):
-        assert np.array_equal(x, y)
-    assert np.array_equal(a.peds(), b.peds())
+    c = P.from_scenario(sc, mode=N.FP_MODE_KERNELS)
+    for _ in range(n):
+        c.step(1)
+    c.synchronize()
+    for x, y, z in zip(fields(a), fields(b), fields(c)):
+        assert np.array_equal(x, y) and np.array_equal(x, z)
+    assert np.array_equal(a.peds(), b.peds()) and np.array_equal(a.peds(), c.peds())
+    ca, cb = a.counters(), b.counters()
+    for k in ("t_ticks", "step", "n_exited", "total_bags", "applied_layers", "hist", "ped_updates"):
+        assert ca[k] == cb[k], k
+    assert np.array_equal(a.field(Z), b.field(Z))
 
 
 # --------------------------------------------------------------------------

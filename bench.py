@@ -330,6 +330,75 @@ def run_ours(args):
     return 0
 
 
+def run_ensemble(args):
+    """Batched ensemble: 256 seeded shopping-centre scenarios (grid side 128-1024,
+    1k-50k pedestrians, 50-1000 responders, 1-3 sandbag layers, inflow peak
+    0.3-1.5 m) stepped together by the batched kernels, against the same
+    simulations stepped one by one.  Metric: simulated scenario-seconds per
+    wall second."""
+    import torch
+    import scenarios
+    import paper_1908_05232_b300 as P
+    torch.cuda.set_device(0)
+    P.build.build()
+    scs = scenarios.ensemble(args.ensemble_size)
+    t0 = time.perf_counter()
+    sims = [P.from_scenario(sc) for sc in scs]
+    setup = time.perf_counter() - t0
+    batch = P.Batch(sims)
+    chunk = 64
+    for _ in range(args.warmup):
+        batch.step(chunk)
+    batch.synchronize()
+
+    def sim_seconds():
+        return sum(s.counters()["t_ticks"] for s in sims) / float(1 << 20)
+
+    def cell_steps():
+        return sum(s.counters()["step"] * s.nx * s.ny for s in sims)
+
+    s0, c0 = sim_seconds(), cell_steps()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        batch.step(chunk)
+    batch.synchronize()
+    t_batch = time.perf_counter() - t0
+    s1, c1 = sim_seconds(), cell_steps()
+    batch.close()
+    # one by one: each simulation's steps run to completion before the next starts
+    t0 = time.perf_counter()
+    for sim in sims:
+        sim.step(chunk * args.steps)
+        sim.synchronize()
+    t_single = time.perf_counter() - t0
+    s2, c2 = sim_seconds(), cell_steps()
+    # independent: every simulation on its own stream, all enqueued at once
+    t0 = time.perf_counter()
+    for sim in sims:
+        sim.step(chunk * args.steps)
+    for sim in sims:
+        sim.synchronize()
+    t_streams = time.perf_counter() - t0
+    s3 = sim_seconds()
+    rate_b = (s1 - s0) / t_batch
+    rate_1 = (s2 - s1) / t_single
+    rate_s = (s3 - s2) / t_streams
+    line = {"metric": "scenario-seconds/s (batched ensemble)", "value": rate_b, "unit": "scenario-s/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_batch / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "ensemble_%d" % len(scs), "scenarios": len(scs),
+                       "cells": int(sum(sc.nx * sc.ny for sc in scs)), "pedestrians": int(sum(sc.n_peds for sc in scs)),
+                       "sim_steps_per_bench_step": chunk, "setup_s": setup},
+            "one_by_one": {"value": rate_1, "unit": "scenario-s/s", "seconds": t_single},
+            "independent_streams": {"value": rate_s, "unit": "scenario-s/s", "seconds": t_streams},
+            "speedup_vs_one_by_one": rate_b / rate_1,
+            "speedup_vs_independent_streams": rate_b / rate_s,
+            "cell_updates_per_s_batched": (c1 - c0) / t_batch, "cell_updates_per_s_one_by_one": (c2 - c1) / t_single}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_case(args):
     """A short untimed run of one workload (the command line profiled under ncu)."""
     import torch
@@ -360,9 +429,13 @@ def main():
     ap.add_argument("--ncu-case", choices=["barrier2048", "shopping512"], default=None,
                     help="short untimed run of one workload, for profiler captures")
     ap.add_argument("--case-steps", type=int, default=4)
+    ap.add_argument("--workload", choices=["shopping512", "ensemble"], default="shopping512")
+    ap.add_argument("--ensemble-size", type=int, default=256)
     args = ap.parse_args()
     if args.ncu_case:
         return run_case(args)
+    if args.workload == "ensemble":
+        return run_ensemble(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -17,7 +17,8 @@
  *   - Grids are row-major, index c = j * nx + i; i runs west->east along x,
  *     j south->north along y; cell (i, j) covers [i dx, (i+1) dx) x [j dx, (j+1) dx).
  *   - Array arguments may be host or device pointers (unified addressing
- *     decides); the library copies them and never keeps a caller pointer.
+ *     decides); the library copies them, never keeps a caller pointer, and the
+ *     set-up calls return only once the copy is complete.
  *   - Every call returns FP_OK (0) or a negative FP_E* code; fp_last_error()
  *     gives a message.  No C++ exception crosses the ABI.  A handle is not
  *     thread-safe; distinct handles are independent.
@@ -190,6 +191,29 @@ int fp_set_step_mode(fp_sim *sim, int32_t mode);
  * kernel: global-timer stamps at every phase boundary.  FP_FIELD_PROFILE
  * returns the totals.  Turning it on resets them. */
 int fp_set_profiling(fp_sim *sim, int32_t on);
+
+/* ---- batched ensemble --------------------------------------------------------
+ * Many independent scenarios (different grids, crowds, barriers, hydrographs)
+ * stepped together: each step is one set of kernels over all members (flat
+ * tile / record / pedestrian work lists), 64-step CUDA graphs.  Every member
+ * keeps its own time step, clock and counters, so a member's results are
+ * bit-identical to stepping it alone.  This is the ensemble use of the
+ * simulator (Section 3.3 runs 36 scenarios of responder group size x barrier
+ * height); the paper runs them one by one.
+ *
+ * fp_batch_create: sims[0..n) are simulations created and loaded through the
+ *   calls above, on the current device, at the same step parity (e.g. all
+ *   fresh, or all stepped the same number of times); they must outlive the
+ *   batch and must not be stepped on their own while batched.  The batch
+ *   re-reads their configuration at every fp_batch_step.
+ * fp_batch_step: n_steps coupled steps of every member (asynchronous on the
+ *   batch's stream).  fp_batch_synchronize waits for it and reports device
+ *   error bits of any member; read members with fp_read_state afterwards. */
+typedef struct fp_batch fp_batch;
+int fp_batch_create(fp_sim *const *sims, int32_t n, fp_batch **out);
+int fp_batch_step(fp_batch *batch, int32_t n_steps);
+int fp_batch_synchronize(fp_batch *batch);
+int fp_batch_destroy(fp_batch *batch);
 
 /* Wait for enqueued work; returns FP_ETIMEOUT / FP_EOVERFLOW / FP_ENAN when the
  * device raised the corresponding error bit. */

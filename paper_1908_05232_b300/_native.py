@@ -65,7 +65,9 @@ def lib():
             "fp_set_state": [_VP] * 4, "fp_set_time": [_VP, ctypes.c_int64, ctypes.c_int64],
             "fp_set_barrier_progress": [_VP, ctypes.c_int64, ctypes.c_int64],
             "fp_add_pedestrians": [_VP, _VP, ctypes.c_int32], "fp_clear_pedestrians": [_VP],
-            "fp_step": [_VP, ctypes.c_int32], "fp_synchronize": [_VP], "fp_set_step_mode": [_VP, ctypes.c_int32], "fp_set_profiling": [_VP, ctypes.c_int32],
+            "fp_step": [_VP, ctypes.c_int32], "fp_synchronize": [_VP], "fp_set_step_mode": [_VP, ctypes.c_int32],
+            "fp_batch_create": [_VP, ctypes.c_int32, _VP], "fp_batch_step": [_VP, ctypes.c_int32],
+            "fp_batch_synchronize": [_VP], "fp_batch_destroy": [_VP], "fp_set_profiling": [_VP, ctypes.c_int32],
             "fp_read_state": [_VP, ctypes.c_int32, _VP, ctypes.c_size_t], "fp_destroy": [_VP],
         }
         for name, args in sigs.items():
@@ -251,6 +253,33 @@ class Simulation:
         out = np.zeros(2, np.float64)
         fp_read_state(self.h, FP_FIELD_MASS, out)
         return float(out[0]), float(out[1])
+
+
+class Batch:
+    """Members (``Simulation`` objects) stepped together by the batched kernels."""
+
+    def __init__(self, sims):
+        self.sims = list(sims)
+        arr = (_VP * len(self.sims))(*[s.h for s in self.sims])
+        self.h = _VP()
+        _check(lib().fp_batch_create(arr, len(self.sims), ctypes.byref(self.h)))
+
+    def step(self, n=1):
+        _check(lib().fp_batch_step(self.h, int(n)))
+
+    def synchronize(self):
+        _check(lib().fp_batch_synchronize(self.h))
+
+    def close(self):
+        if self.h is not None:
+            _check(lib().fp_batch_destroy(self.h))
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def config_for(sc, max_peds=None, tile_rows=0) -> FpConfig:

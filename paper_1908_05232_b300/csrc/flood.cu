@@ -6,6 +6,27 @@
 namespace {
 using namespace fpdev;
 
+// Batched ensemble: flat tile space, member s owns tiles [tile_off[s], tile_off[s+1]).
+__global__ void __launch_bounds__(512) flood_batch_kernel(const FpSim *__restrict__ sims,
+                                                          const FpTmaSet *__restrict__ maps,
+                                                          const int *__restrict__ tile_off, int n, int par,
+                                                          int slot) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) unsigned long long mbar;
+    if (threadIdx.x == 0) mbar_init(&mbar);
+    __syncthreads();
+    const int t = blockIdx.x;
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (tile_off[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    const FpSim &S = sims[lo];
+    const int local = t - tile_off[lo];
+    const int tiles_x = (S.nx + FP_TX - 1) / FP_TX;
+    flood_tile<16>(maps[2 * lo + par], S, par, slot, local % tiles_x, local / tiles_x, smem_raw, &mbar, 0u);
+}
+
 template <int TY>
 __global__ void __launch_bounds__(32 * TY) flood_kernel(const __grid_constant__ FpTmaSet tm,
                                                         const __grid_constant__ FpSim S, int par, int slot) {
@@ -84,12 +105,19 @@ int fp_flood_smem_bytes(int tile_rows) {
     return smem_bytes<16>();
 }
 
+void fp_launch_flood_batch(const FpSim *d_sims, const FpTmaSet *d_maps, const int *d_tile_off, int n,
+                           int total_tiles, int par, int slot, cudaStream_t st) {
+    flood_batch_kernel<<<total_tiles, 512, smem_bytes<16>(), st>>>(d_sims, d_maps, d_tile_off, n, par, slot);
+}
+
 cudaError_t fp_flood_init_attributes() {
     cudaError_t e = cudaFuncSetAttribute(flood_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<8>());
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(flood_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<16>());
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(flood_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<32>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(flood_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<16>());
     return e;
 }
 

@@ -113,6 +113,14 @@ struct fp_sim {
     std::vector<cudaEvent_t> prof_ev;  // 4 per profiled step
     double prof[5] = {0, 0, 0, 0, 0};  // steps, hash ms, flood ms, pedestrian chain ms, step ms
 
+    // Every copy of the library is stream-ordered on the simulation's stream and
+    // complete when this returns (a plain cudaMemcpy from pageable memory may
+    // return before its DMA lands, unordered with this non-blocking stream).
+    cudaError_t copy(void *dst, const void *src, size_t bytes) {
+        cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+        return e;
+    }
     int fail(int code, const std::string &msg) {
         err = msg;
         return code;
@@ -176,7 +184,7 @@ static int upload_nav(fp_sim *s) {
             for (int c : cells) goal[c] = 1;
         }
         build_nav(nx, ny, s->walk_h, goal, code);
-        cudaError_t e = cudaMemcpy(const_cast<unsigned char *>(s->S.nav[g]), code.data(), n, cudaMemcpyHostToDevice);
+        cudaError_t e = s->copy(const_cast<unsigned char *>(s->S.nav[g]), code.data(), n);
         if (e != cudaSuccess) return s->cuda_fail(e, "nav upload");
     }
     return FP_OK;
@@ -203,7 +211,8 @@ static cudaError_t get_plane(fp_sim *s, void *dst, const float *src) {
 }
 
 static int prepare(fp_sim *s) {
-    cudaError_t e;
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return s->cuda_fail(e, "prepare sync");
     FpClock ring[4];
     memset(ring, 0, sizeof(ring));
     if (s->pending_time) {
@@ -212,7 +221,7 @@ static int prepare(fp_sim *s) {
         s->pending_time = false;
     } else {
         FpClock cur;
-        e = cudaMemcpy(&cur, &s->S.clock[s->slot], sizeof(cur), cudaMemcpyDeviceToHost);
+        e = s->copy(&cur, &s->S.clock[s->slot], sizeof(cur));
         if (e != cudaSuccess) return s->cuda_fail(e, "clock read");
         ring[s->slot].t = cur.t;
         ring[s->slot].step = cur.step;
@@ -260,7 +269,7 @@ static int step_profiled_persistent(fp_sim *s, int n) {
                                              s->persist_smem, s->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
         std::vector<unsigned long long> h(cnt);
-        if (e == cudaSuccess) e = cudaMemcpy(h.data(), ts, cnt * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = s->copy(h.data(), ts, cnt * sizeof(unsigned long long));
         s->allocs.pop_back();
         cudaFree(ts);
         if (e != cudaSuccess) return s->cuda_fail(e, "profiled persistent steps");
@@ -457,9 +466,9 @@ int fp_set_terrain(fp_sim *s, const float *z, const float *n0, const uint8_t *wa
     if ((e = cudaMemcpyAsync(const_cast<unsigned char *>(s->S.exitm), exit_mask, n, cudaMemcpyDefault,
                              s->stream)) != cudaSuccess)
         return s->cuda_fail(e, "exit upload");
-    if ((e = cudaMemcpy(s->walk_h.data(), walkable, n, cudaMemcpyDefault)) != cudaSuccess)
+    if ((e = s->copy(s->walk_h.data(), walkable, n)) != cudaSuccess)
         return s->cuda_fail(e, "walkable copy");
-    if ((e = cudaMemcpy(s->exit_h.data(), exit_mask, n, cudaMemcpyDefault)) != cudaSuccess)
+    if ((e = s->copy(s->exit_h.data(), exit_mask, n)) != cudaSuccess)
         return s->cuda_fail(e, "exit copy");
     for (auto &v : s->walk_h) v = v ? 1 : 0;
     if ((e = cudaStreamSynchronize(s->stream)) != cudaSuccess) return s->cuda_fail(e, "terrain");
@@ -471,12 +480,12 @@ int fp_set_boundary(fp_sim *s, int32_t edge, const uint8_t *codes) {
     if (edge < 0 || edge > 3 || !codes) return s->fail(FP_EINVAL, "bad edge or codes");
     const int len = edge < 2 ? s->S.nx : s->S.ny;
     std::vector<uint8_t> h(len);
-    cudaError_t e = cudaMemcpy(h.data(), codes, len, cudaMemcpyDefault);
+    cudaError_t e = s->copy(h.data(), codes, len);
     if (e != cudaSuccess) return s->cuda_fail(e, "boundary copy");
     for (uint8_t c : h)
         if (c > FP_BC_INFLOW) return s->fail(FP_EINVAL, "boundary code out of range");
     s->bc_h[edge] = h;
-    e = cudaMemcpy(const_cast<unsigned char *>(s->S.bc[edge]), h.data(), len, cudaMemcpyHostToDevice);
+    e = s->copy(const_cast<unsigned char *>(s->S.bc[edge]), h.data(), len);
     if (e != cudaSuccess) return s->cuda_fail(e, "boundary upload");
     update_inflow_flag(s);
     s->drop_graphs();
@@ -487,14 +496,14 @@ int fp_set_hydrograph(fp_sim *s, const double *t, const double *h, int32_t n) {
     if (!s) return FP_EINVAL;
     if (!t || !h || n < 1 || n > FP_MAX_HYDRO) return s->fail(FP_EINVAL, "hydrograph needs 1..64 points");
     std::vector<double> th(n), hh(n);
-    cudaMemcpy(th.data(), t, n * sizeof(double), cudaMemcpyDefault);
-    cudaMemcpy(hh.data(), h, n * sizeof(double), cudaMemcpyDefault);
+    s->copy(th.data(), t, n * sizeof(double));
+    s->copy(hh.data(), h, n * sizeof(double));
     for (int k = 0; k < n; ++k) {
         if (!(hh[k] >= 0.0) || !std::isfinite(th[k])) return s->fail(FP_EINVAL, "hydrograph values");
         if (k && !(th[k] > th[k - 1])) return s->fail(FP_EINVAL, "hydrograph times must increase");
     }
-    cudaMemcpy(const_cast<double *>(s->S.hydro_t), th.data(), n * sizeof(double), cudaMemcpyHostToDevice);
-    cudaError_t e = cudaMemcpy(const_cast<double *>(s->S.hydro_h), hh.data(), n * sizeof(double), cudaMemcpyHostToDevice);
+    s->copy(const_cast<double *>(s->S.hydro_t), th.data(), n * sizeof(double));
+    cudaError_t e = s->copy(const_cast<double *>(s->S.hydro_h), hh.data(), n * sizeof(double));
     if (e != cudaSuccess) return s->cuda_fail(e, "hydrograph upload");
     s->S.n_hydro = n;
     s->drop_graphs();
@@ -509,8 +518,8 @@ int fp_set_goals(fp_sim *s, const int32_t *depot, int32_t n_depot, const int32_t
     if (n_depot < 0 || n_barrier < 0 || n_layers < 0 || (n_depot && !depot) || (n_barrier && !barrier))
         return s->fail(FP_EINVAL, "bad goal arguments");
     std::vector<int> dh(n_depot), bh(n_barrier);
-    if (n_depot) cudaMemcpy(dh.data(), depot, n_depot * sizeof(int), cudaMemcpyDefault);
-    if (n_barrier) cudaMemcpy(bh.data(), barrier, n_barrier * sizeof(int), cudaMemcpyDefault);
+    if (n_depot) s->copy(dh.data(), depot, n_depot * sizeof(int));
+    if (n_barrier) s->copy(bh.data(), barrier, n_barrier * sizeof(int));
     for (int c : dh)
         if (c < 0 || c >= n) return s->fail(FP_EINVAL, "depot cell out of range");
     for (int c : bh)
@@ -520,7 +529,7 @@ int fp_set_goals(fp_sim *s, const int32_t *depot, int32_t n_depot, const int32_t
     if (n_barrier) {
         int *d = s->dalloc<int>(n_barrier);
         if (!d) return s->fail(FP_ENOMEM, "barrier allocation");
-        cudaMemcpy(d, bh.data(), n_barrier * sizeof(int), cudaMemcpyHostToDevice);
+        s->copy(d, bh.data(), n_barrier * sizeof(int));
         s->S.barrier = d;
     } else {
         s->S.barrier = nullptr;
@@ -540,6 +549,7 @@ int fp_set_state(fp_sim *s, const float *h, const float *hu, const float *hv) {
     if ((e = put_plane(s, s->S.hu[p], hu)) != cudaSuccess) return s->cuda_fail(e, "hu upload");
     if ((e = put_plane(s, s->S.hv[p], hv)) != cudaSuccess) return s->cuda_fail(e, "hv upload");
     cudaMemsetAsync(s->S.bflux, 0, (2 * (size_t)s->S.nx + 2 * (size_t)s->S.ny) * sizeof(double), s->stream);
+    if ((e = cudaStreamSynchronize(s->stream)) != cudaSuccess) return s->cuda_fail(e, "state upload");
     s->need_prepare = true;
     return FP_OK;
 }
@@ -560,11 +570,11 @@ int fp_set_barrier_progress(fp_sim *s, int64_t total_bags, int64_t applied_layer
     cudaError_t e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return s->cuda_fail(e, "sync");
     FpCounters c;
-    cudaMemcpy(&c, s->S.cnt, sizeof(c), cudaMemcpyDeviceToHost);
+    s->copy(&c, s->S.cnt, sizeof(c));
     c.total_bags = (unsigned long long)total_bags;
     c.bags_snap = (unsigned long long)total_bags;
     c.applied = (unsigned long long)applied_layers;
-    e = cudaMemcpy(s->S.cnt, &c, sizeof(c), cudaMemcpyHostToDevice);
+    e = s->copy(s->S.cnt, &c, sizeof(c));
     if (e != cudaSuccess) return s->cuda_fail(e, "barrier progress");
     return FP_OK;
 }
@@ -576,23 +586,23 @@ int fp_add_pedestrians(fp_sim *s, const fp_ped *peds, int32_t count) {
     cudaError_t e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return s->cuda_fail(e, "sync");
     FpCounters c;
-    cudaMemcpy(&c, s->S.cnt, sizeof(c), cudaMemcpyDeviceToHost);
+    s->copy(&c, s->S.cnt, sizeof(c));
     if (s->n_total + count > s->S.cap || c.nB + count > s->S.cap)
         return s->fail(FP_EOVERFLOW, "pedestrian capacity exceeded");
-    e = cudaMemcpy(s->S.pedB + 2 * (size_t)c.nB, peds, (size_t)count * sizeof(fp_ped), cudaMemcpyDefault);
+    e = s->copy(s->S.pedB + 2 * (size_t)c.nB, peds, (size_t)count * sizeof(fp_ped));
     if (e != cudaSuccess) return s->cuda_fail(e, "pedestrian upload");
     fp_launch_assign_ids(s->S, c.nB, s->n_total, count, s->stream);
     e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return s->cuda_fail(e, "assign ids");
     FpCounters c2;
-    cudaMemcpy(&c2, s->S.cnt, sizeof(c2), cudaMemcpyDeviceToHost);
+    s->copy(&c2, s->S.cnt, sizeof(c2));
     if (c2.bad_ped) {
         int zero = 0;
-        cudaMemcpy(&s->S.cnt->bad_ped, &zero, sizeof(int), cudaMemcpyHostToDevice);
+        s->copy(&s->S.cnt->bad_ped, &zero, sizeof(int));
         return s->fail(FP_EINVAL, "a pedestrian stands outside the domain or in a non-walkable cell");
     }
     const int nb = c.nB + count;
-    cudaMemcpy(&s->S.cnt->nB, &nb, sizeof(int), cudaMemcpyHostToDevice);
+    s->copy(&s->S.cnt->nB, &nb, sizeof(int));
     s->n_total += count;
     return FP_OK;
 }
@@ -601,12 +611,12 @@ int fp_clear_pedestrians(fp_sim *s) {
     if (!s) return FP_EINVAL;
     cudaStreamSynchronize(s->stream);
     FpCounters c;
-    cudaMemcpy(&c, s->S.cnt, sizeof(c), cudaMemcpyDeviceToHost);
+    s->copy(&c, s->S.cnt, sizeof(c));
     c.nA = c.nB = 0;
     c.total_bags = c.bags_snap = c.applied = 0;
     c.n_exited = 0;
     for (auto &v : c.hist) v = 0;
-    cudaError_t e = cudaMemcpy(s->S.cnt, &c, sizeof(c), cudaMemcpyHostToDevice);
+    cudaError_t e = s->copy(s->S.cnt, &c, sizeof(c));
     if (e != cudaSuccess) return s->cuda_fail(e, "clear");
     s->n_total = 0;
     return FP_OK;
@@ -693,7 +703,7 @@ int fp_synchronize(fp_sim *s) {
     cudaError_t e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return s->cuda_fail(e, "synchronize");
     unsigned err = 0;
-    e = cudaMemcpy(&err, &s->S.cnt->err, sizeof(err), cudaMemcpyDeviceToHost);
+    e = s->copy(&err, &s->S.cnt->err, sizeof(err));
     if (e != cudaSuccess) return s->cuda_fail(e, "error word");
     if (err & FP_ERR_TIMEOUT) return s->fail(FP_ETIMEOUT, "a bounded device wait timed out");
     if (err & FP_ERR_OCC_OVERFLOW) return s->fail(FP_EOVERFLOW, "more than 65535 evacuees in one cell");
@@ -734,8 +744,8 @@ int fp_read_state(fp_sim *s, int32_t which, void *dst, size_t bytes) {
             FpCounters c;
             FpClock k;
             cudaStreamSynchronize(s->stream);
-            cudaMemcpy(&c, S.cnt, sizeof(c), cudaMemcpyDeviceToHost);
-            e = cudaMemcpy(&k, &S.clock[s->slot], sizeof(k), cudaMemcpyDeviceToHost);
+            s->copy(&c, S.cnt, sizeof(c));
+            e = s->copy(&k, &S.clock[s->slot], sizeof(k));
             fp_counters o;
             memset(&o, 0, sizeof(o));
             o.t_ticks = k.t;
@@ -749,7 +759,7 @@ int fp_read_state(fp_sim *s, int32_t which, void *dst, size_t bytes) {
             o.wet = k.wet;
             o.error_flags = c.err;
             o.ped_updates = (int64_t)c.ped_updates;
-            if (e == cudaSuccess) e = cudaMemcpy(dst, &o, sizeof(o), cudaMemcpyDefault);
+            if (e == cudaSuccess) e = s->copy(dst, &o, sizeof(o));
             break;
         }
         case FP_FIELD_NAV: {
@@ -764,12 +774,12 @@ int fp_read_state(fp_sim *s, int32_t which, void *dst, size_t bytes) {
             double tmp[2];
             e = cudaMemcpyAsync(tmp, &S.cnt->mass, 2 * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
             if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
-            if (e == cudaSuccess) e = cudaMemcpy(dst, tmp, sizeof(tmp), cudaMemcpyDefault);
+            if (e == cudaSuccess) e = s->copy(dst, tmp, sizeof(tmp));
             break;
         }
         case FP_FIELD_PROFILE: {
             if (bytes < sizeof(s->prof)) return s->fail(FP_EINVAL, "destination too small");
-            e = cudaMemcpy(dst, s->prof, sizeof(s->prof), cudaMemcpyDefault);
+            e = s->copy(dst, s->prof, sizeof(s->prof));
             break;
         }
         default:
@@ -777,6 +787,191 @@ int fp_read_state(fp_sim *s, int32_t which, void *dst, size_t bytes) {
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return s->cuda_fail(e, "read_state");
+    return FP_OK;
+}
+
+}  // extern "C"
+
+struct fp_batch {
+    std::vector<fp_sim *> sims;
+    int n = 0, total_tiles = 0, total_rec = 0, max_scan_tiles = 0;
+    FpSim *d_sims = nullptr;
+    FpTmaSet *d_maps = nullptr;
+    int *d_tile_off = nullptr, *d_rec_off = nullptr;
+    std::vector<FpSim> h_sims;
+    std::vector<FpTmaSet> h_maps;
+    cudaStream_t stream = nullptr, stream2 = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaGraphExec_t graphs[4] = {nullptr, nullptr, nullptr, nullptr};
+    std::vector<void *> allocs;
+};
+
+static void batch_launch_step(fp_batch *b, int par, int slot) {
+    fp_launch_batch_peds(b->d_sims, b->d_rec_off, b->n, b->total_rec, b->max_scan_tiles, par, slot, b->stream,
+                         b->stream2, b->ev_fork, true);
+    cudaStreamWaitEvent(b->stream2, b->ev_fork, 0);
+    fp_launch_flood_batch(b->d_sims, b->d_maps, b->d_tile_off, b->n, b->total_tiles, par, slot, b->stream);
+    fp_launch_batch_peds(b->d_sims, b->d_rec_off, b->n, b->total_rec, b->max_scan_tiles, par, slot, b->stream,
+                         b->stream2, b->ev_fork, false);
+    cudaEventRecord(b->ev_join, b->stream2);
+    cudaStreamWaitEvent(b->stream, b->ev_join, 0);
+}
+
+extern "C" {
+
+int fp_batch_create(fp_sim *const *sims, int32_t n, fp_batch **out) {
+    if (!sims || !out || n < 1) {
+        g_create_error = "fp_batch_create: need n >= 1 simulations";
+        return FP_EINVAL;
+    }
+    *out = nullptr;
+    fp_batch *b = new fp_batch();
+    b->n = n;
+    std::vector<int> tile_off(n + 1, 0), rec_off(n + 1, 0);
+    for (int k = 0; k < n; ++k) {
+        fp_sim *m = sims[k];
+        if (!m) { delete b; g_create_error = "fp_batch_create: null member"; return FP_EINVAL; }
+        b->sims.push_back(m);
+        const int tiles = ((m->S.nx + FP_TX - 1) / FP_TX) * ((m->S.ny + 15) / 16);
+        tile_off[k + 1] = tile_off[k] + tiles;
+        const int cap = std::max(1, m->S.cap);
+        rec_off[k + 1] = rec_off[k] + ((cap + 255) / 256) * 256;
+        b->max_scan_tiles = std::max(b->max_scan_tiles, fp_scan_tiles(m->S.nbins));
+    }
+    b->total_tiles = tile_off[n];
+    b->total_rec = rec_off[n];
+    auto alloc = [&](size_t bytes) -> void * {
+        void *p = nullptr;
+        if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+        b->allocs.push_back(p);
+        return p;
+    };
+    b->d_sims = static_cast<FpSim *>(alloc(sizeof(FpSim) * n));
+    b->d_maps = static_cast<FpTmaSet *>(alloc(sizeof(FpTmaSet) * 2 * n));
+    b->d_tile_off = static_cast<int *>(alloc(sizeof(int) * (n + 1)));
+    b->d_rec_off = static_cast<int *>(alloc(sizeof(int) * (n + 1)));
+    if (!b->d_sims || !b->d_maps || !b->d_tile_off || !b->d_rec_off) {
+        fp_batch_destroy(b);
+        g_create_error = "fp_batch_create: device allocation failed";
+        return FP_ENOMEM;
+    }
+    cudaMemcpy(b->d_tile_off, tile_off.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice);
+    cudaMemcpy(b->d_rec_off, rec_off.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice);
+    b->h_sims.resize(n);
+    b->h_maps.resize(2 * n);
+    cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    cudaStreamCreateWithFlags(&b->stream2, cudaStreamNonBlocking);
+    cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
+    cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        fp_batch_destroy(b);
+        g_create_error = "fp_batch_create: CUDA error";
+        return FP_ECUDA;
+    }
+    *out = b;
+    return FP_OK;
+}
+
+int fp_batch_step(fp_batch *b, int32_t n_steps) {
+    if (!b || n_steps < 0) return FP_EINVAL;
+    const int par = b->sims[0]->par, slot = b->sims[0]->slot;
+    for (int k = 0; k < b->n; ++k) {
+        fp_sim *m = b->sims[k];
+        cudaError_t e = cudaStreamSynchronize(m->stream);
+        if (e != cudaSuccess) return m->cuda_fail(e, "batch member sync");
+        if (m->need_prepare) {
+            int rc = prepare(m);
+            if (rc != FP_OK) return rc;
+        }
+        if (m->par != par || m->slot != slot) {
+            g_create_error = "fp_batch_step: members are at different step parities";
+            return FP_EINVAL;
+        }
+        b->h_sims[k] = m->S;
+        b->h_maps[2 * k] = m->tma16[0];
+        b->h_maps[2 * k + 1] = m->tma16[1];
+    }
+    cudaError_t e = cudaMemcpyAsync(b->d_sims, b->h_sims.data(), sizeof(FpSim) * b->n, cudaMemcpyHostToDevice,
+                                    b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_maps, b->h_maps.data(), sizeof(FpTmaSet) * 2 * b->n, cudaMemcpyHostToDevice,
+                            b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);  // host vectors may change at the next call
+    if (e != cudaSuccess) {
+        g_create_error = "fp_batch_step: descriptor upload failed";
+        return FP_ECUDA;
+    }
+    int p = par, sl = slot, left = n_steps;
+    while (left > 0) {
+        if (left >= kGraphSteps) {
+            cudaGraphExec_t &g = b->graphs[sl];
+            if (!g) {
+                cudaGraph_t graph;
+                e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+                if (e != cudaSuccess) break;
+                int pp = p, ss = sl;
+                for (int k = 0; k < kGraphSteps; ++k) {
+                    batch_launch_step(b, pp, ss);
+                    pp ^= 1;
+                    ss = (ss + 1) & 3;
+                }
+                e = cudaStreamEndCapture(b->stream, &graph);
+                if (e != cudaSuccess) break;
+                e = cudaGraphInstantiate(&g, graph, 0);
+                cudaGraphDestroy(graph);
+                if (e != cudaSuccess) { g = nullptr; break; }
+            }
+            e = cudaGraphLaunch(g, b->stream);
+            if (e != cudaSuccess) break;
+            left -= kGraphSteps;
+        } else {
+            batch_launch_step(b, p, sl);
+            p ^= 1;
+            sl = (sl + 1) & 3;
+            left -= 1;
+        }
+    }
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        g_create_error = std::string("fp_batch_step: ") + cudaGetErrorString(e);
+        return FP_ECUDA;
+    }
+    for (fp_sim *m : b->sims) {
+        m->par = p;
+        m->slot = sl;
+    }
+    return FP_OK;
+}
+
+int fp_batch_synchronize(fp_batch *b) {
+    if (!b) return FP_EINVAL;
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) {
+        g_create_error = std::string("fp_batch_synchronize: ") + cudaGetErrorString(e);
+        return FP_ECUDA;
+    }
+    for (fp_sim *m : b->sims) {
+        const int rc = fp_synchronize(m);
+        if (rc != FP_OK) {
+            g_create_error = m->err;
+            return rc;
+        }
+    }
+    return FP_OK;
+}
+
+int fp_batch_destroy(fp_batch *b) {
+    if (!b) return FP_EINVAL;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    for (auto &g : b->graphs)
+        if (g) cudaGraphExecDestroy(g);
+    for (void *p : b->allocs) cudaFree(p);
+    if (b->stream) cudaStreamDestroy(b->stream);
+    if (b->stream2) cudaStreamDestroy(b->stream2);
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    if (b->ev_join) cudaEventDestroy(b->ev_join);
+    delete b;
     return FP_OK;
 }
 

@@ -205,5 +205,10 @@ void fp_launch_read_peds(const FpSim &S, uint4 *out, int n_total, cudaStream_t s
 int fp_scan_tiles(int nbins);
 void fp_note_error(const char *msg);  // message for fp_last_error(NULL)
 int fp_persistent_ctas(int smem_dynamic);
+void fp_launch_batch_peds(const FpSim *d_sims, const int *d_rec_off, int n, int total_rec, int max_scan_tiles,
+                          int par, int slot, cudaStream_t st_hash, cudaStream_t st_chain, cudaEvent_t fork,
+                          bool hash_part);
+void fp_launch_flood_batch(const FpSim *d_sims, const FpTmaSet *d_maps, const int *d_tile_off, int n,
+                           int total_tiles, int par, int slot, cudaStream_t st);
 cudaError_t fp_launch_persistent(const FpSim &S, const FpTmaSet tma[2], int par, int slot, int nsteps,
                                  unsigned *bar, int ctas, int smem_dynamic, cudaStream_t st);

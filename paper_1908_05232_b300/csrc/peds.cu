@@ -28,7 +28,7 @@ __global__ void hash_count_kernel(const __grid_constant__ FpSim S, int par) {
 }
 
 // status word: epoch (30 bits) << 34 | status (1 aggregate, 2 inclusive prefix) << 32 | value
-__global__ void __launch_bounds__(kScanThreads) scan_kernel(const __grid_constant__ FpSim S) {
+__device__ __forceinline__ void scan_tile(const FpSim &S) {
     __shared__ int s_tile, s_prefix;
     __shared__ int s_warp[kScanThreads / 32];
     const int tid = threadIdx.x;
@@ -126,9 +126,9 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(const __grid_constan
     }
 }
 
-__global__ void gather_kernel(const __grid_constant__ FpSim S) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= S.cnt->nB) return;
+__global__ void __launch_bounds__(kScanThreads) scan_kernel(const __grid_constant__ FpSim S) { scan_tile(S); }
+
+__device__ __forceinline__ void gather_record(const FpSim &S, int i) {
     const int key = S.pkey[i];
     const uint4 a = S.pedB[2 * i], b = S.pedB[2 * i + 1];
     if (key == S.nbins) {
@@ -139,6 +139,11 @@ __global__ void gather_kernel(const __grid_constant__ FpSim S) {
         S.pedA[2 * dst] = a;
         S.pedA[2 * dst + 1] = b;
     }
+}
+
+__global__ void gather_kernel(const __grid_constant__ FpSim S) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < S.cnt->nB) gather_record(S, i);
 }
 
 struct DirectLookup {
@@ -196,7 +201,83 @@ __global__ void read_live_kernel(const __grid_constant__ FpSim S, uint4 *out) {
 
 inline int blocks_for(int n, int t) { return n <= 0 ? 1 : (n + t - 1) / t; }
 
+// ---- batched ensemble: one launch covers every member of a batch ------------
+// Flat record space: member s owns [rec_off[s], rec_off[s+1]), a multiple of 256
+// records long, so every CTA belongs to one member.
+
+__device__ __forceinline__ int batch_member(const int *off, int n, int x) {
+    int lo = 0, hi = n - 1;  // largest s with off[s] <= x
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= x) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void hash_count_batch_kernel(const FpSim *__restrict__ sims, const int *__restrict__ rec_off, int n,
+                                        int par) {
+    const int s = batch_member(rec_off, n, blockIdx.x * blockDim.x);
+    const FpSim &S = sims[s];
+    FpCounters *C = S.cnt;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x - rec_off[s];
+    if (i == 0) {
+        barrier_and_snapshot(S);
+        C->scan_epoch += 1u;
+        C->scan_ticket = 0u;
+    }
+    if (i >= C->nB) return;
+    const uint4 pa = S.pedB[2 * i], pb = S.pedB[2 * i + 1];
+    hash_record(S, i, __uint_as_float(pa.x), __uint_as_float(pa.y), pb.y, S.occ[par]);
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_batch_kernel(const FpSim *__restrict__ sims) {
+    const FpSim &S = sims[blockIdx.y];
+    if ((int)blockIdx.x >= (S.nbins + 1 + kScanTile - 1) / kScanTile) return;
+    scan_tile(S);
+}
+
+__global__ void gather_batch_kernel(const FpSim *__restrict__ sims, const int *__restrict__ rec_off, int n) {
+    const int s = batch_member(rec_off, n, blockIdx.x * blockDim.x);
+    const FpSim &S = sims[s];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x - rec_off[s];
+    if (i < S.cnt->nB) gather_record(S, i);
+}
+
+__global__ void __launch_bounds__(256) ped_step_batch_kernel(const FpSim *__restrict__ sims,
+                                                             const int *__restrict__ rec_off, int n, int par,
+                                                             int slot) {
+    __shared__ StepCtl s_ctl;
+    constexpr int kRecPerBlock = 256 / kGroup;
+    const int s = batch_member(rec_off, n, blockIdx.x * kRecPerBlock);
+    const FpSim &S = sims[s];
+    const int j0 = blockIdx.x * kRecPerBlock - rec_off[s];
+    if (threadIdx.x == 0) {
+        FpCounters *C = S.cnt;
+        load_step_ctl(S, slot, C->nA, s_ctl);
+        if (j0 == 0) {
+            C->nB = s_ctl.nA;
+            if (s_ctl.dt_ticks > 0) C->ped_updates += (unsigned long long)s_ctl.nA;
+        }
+    }
+    __syncthreads();
+    const StepCtl ctl = s_ctl;
+    ped_group(S, par, ctl, j0 + threadIdx.x / kGroup, threadIdx.x & (kGroup - 1), DirectLookup{S.bin_start}, false);
+}
+
 }  // namespace
+
+void fp_launch_batch_peds(const FpSim *d_sims, const int *d_rec_off, int n, int total_rec, int max_scan_tiles,
+                          int par, int slot, cudaStream_t st_hash, cudaStream_t st_chain, cudaEvent_t fork,
+                          bool hash_part) {
+    if (hash_part) {
+        hash_count_batch_kernel<<<total_rec / 256, 256, 0, st_hash>>>(d_sims, d_rec_off, n, par);
+        cudaEventRecord(fork, st_hash);
+        return;
+    }
+    scan_batch_kernel<<<dim3(max_scan_tiles, n), kScanThreads, 0, st_chain>>>(d_sims);
+    gather_batch_kernel<<<total_rec / 256, 256, 0, st_chain>>>(d_sims, d_rec_off, n);
+    ped_step_batch_kernel<<<total_rec * kGroup / 256, 256, 0, st_chain>>>(d_sims, d_rec_off, n, par, slot);
+}
 
 int fp_scan_tiles(int nbins) { return (nbins + 1 + kScanTile - 1) / kScanTile; }
 

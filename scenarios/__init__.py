@@ -350,3 +350,31 @@ def with_depot_and_barrier(s: Scenario, depot_ij, barrier_ij, n_layers) -> Scena
     s.barrier_cells = np.array([j * s.nx + i for i, j in barrier_ij], np.int32)
     s.n_layers = int(n_layers)
     return s
+
+
+def ensemble(n: int = 256, seed: int = 4, side_range=(128, 1024), peds_range=(1_000, 50_000),
+             resp_range=(50, 1_000), barrier_m=(0.2, 0.8), peak_m=(0.3, 1.5), dx: float = 0.5,
+             t_end: float = 3600.0) -> list:
+    """Seeded ensemble of shopping-centre scenarios: grid side log-uniform in
+    side_range (multiple of 8), pedestrians uniform in peds_range of which
+    responders uniform in resp_range, barrier height uniform in barrier_m
+    (rounded to whole 0.25 m sandbag layers, at least one), inflow peak depth
+    uniform in peak_m."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n):
+        side = int(np.exp(rng.uniform(np.log(side_range[0]), np.log(side_range[1]))))
+        side = max(64, (side // 8) * 8)
+        n_peds = int(rng.integers(peds_range[0], peds_range[1] + 1))
+        n_resp = min(int(rng.integers(resp_range[0], resp_range[1] + 1)), n_peds // 2)
+        layers = max(1, int(round(rng.uniform(*barrier_m) / 0.25)))
+        peak = float(rng.uniform(*peak_m))
+        # keep the crowd below ~1 pedestrian per square metre of the domain
+        n_peds = min(n_peds, int((side * dx) ** 2 * 0.5))
+        n_resp = min(n_resp, n_peds // 2)
+        sc = shopping_centre(side, dx, n_peds - n_resp, n_resp, seed * 1000 + k, t_end,
+                             hydro=([0.0, 300.0, 900.0], [0.0, peak, 0.0]),
+                             n_barrier=min(200, side // 4), n_layers=layers)
+        sc.name = "ensemble_%d" % k
+        out.append(sc)
+    return out

@@ -381,3 +381,52 @@ def test_barrier_config_full_size_properties(P):
     jj = np.floor(g["y"] / np.float32(sc.dx)).astype(int)
     assert np.all(sc.walkable[jj, ii] == 1)
     assert c["n_active"] <= sum(c["hist"]) <= sc.n_peds
+
+
+# --------------------------------------------------------------------------
+# batched ensemble
+# --------------------------------------------------------------------------
+def _batch_members():
+    a = S.plain_coupled_128(seed=1)
+    b = S.plain_coupled_128(seed=2, n_peds=120, nx=96, ny=80)
+    c = _barrier_wet()
+    d = _crowd_state(7, nx=100, ny=60, n_evac=300, n_resp=30)
+    e = S.closed_basin(70, 45, dx=0.5, seed=9)
+    return [a, b, c, d, e]
+
+
+def test_batch_matches_members_alone(P):
+    """Scenarios of different grids and crowds stepped as one batch give the
+    bytes each gives stepped alone (graph-replayed 64-step runs included)."""
+    scs = _batch_members()
+    n = 200
+    members = [P.from_scenario(sc) for sc in scs]
+    batch = P.Batch(members)
+    batch.step(n)
+    batch.synchronize()
+    for sc, m in zip(scs, members):
+        alone = run_gpu(P, sc, n)
+        for x, y in zip(fields(m), fields(alone)):
+            assert np.array_equal(x, y), sc.name
+        assert np.array_equal(m.field(Z), alone.field(Z))
+        assert np.array_equal(m.peds(), alone.peds()), sc.name
+        cm, ca = m.counters(), alone.counters()
+        for k in ("t_ticks", "step", "n_exited", "total_bags", "applied_layers", "hist", "ped_updates"):
+            assert cm[k] == ca[k], (sc.name, k)
+    batch.close()
+
+
+def test_batch_then_alone_continues(P):
+    """A member stepped in a batch can be stepped on its own afterwards."""
+    sc = S.plain_coupled_128(seed=3)
+    m = P.from_scenario(sc)
+    b = P.Batch([m])
+    b.step(70)
+    b.synchronize()
+    b.close()
+    m.step(30)
+    m.synchronize()
+    alone = run_gpu(P, sc, 100)
+    for x, y in zip(fields(m), fields(alone)):
+        assert np.array_equal(x, y)
+    assert np.array_equal(m.peds(), alone.peds())

@@ -181,6 +181,11 @@ int fp_step(fp_sim *sim, int32_t n_steps);
  * FP_MODE_PERSISTENT (devices with cooperative launch): up to 256 steps per
  *   launch of one persistent kernel whose phases are separated by grid
  *   barriers with bounded waits (FP_ETIMEOUT if one gives up). */
+/* Launch shape of the per-step kernels (results do not depend on it): flood
+ * tile height tile_rows (8, 16, 32 cells; 64 wide) and lanes per pedestrian in
+ * the pedestrian step (4, 8, 16).  Chosen by the package's autotuner. */
+int fp_set_tuning(fp_sim *sim, int32_t tile_rows, int32_t ped_lanes);
+
 #define FP_MODE_KERNELS 0
 #define FP_MODE_PERSISTENT 1
 int fp_set_step_mode(fp_sim *sim, int32_t mode);

@@ -1,0 +1,86 @@
+"""Autotuner for the launch shape of a simulation.
+
+Times every candidate (flood tile height 8/16/32, lanes per pedestrian
+4/8/16, per-step kernels or the persistent kernel) for a few dozen steps on a
+scratch copy of the scenario, picks the fastest and caches the choice in a JSON
+file keyed by device, grid size and crowd size.  The launch shape never changes
+the results (the same arithmetic runs in every shape), only the time.
+"""
+from __future__ import annotations
+
+import json
+import os
+
+from . import _native as N
+
+DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "floodped_autotune.json")
+TILE_ROWS = (8, 16, 32)
+PED_LANES = (4, 8, 16)
+
+
+def cache_key(device: str, nx: int, ny: int, n_peds: int) -> str:
+    bucket = 0 if n_peds == 0 else 1 << max(0, int(n_peds - 1).bit_length())
+    return "%s|%dx%d|peds<=%d" % (device, nx, ny, bucket)
+
+
+def _load(path):
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def tune(sc, steps: int = 48, warm: int = 16, modes=(N.FP_MODE_KERNELS, N.FP_MODE_PERSISTENT)) -> dict:
+    """Time every candidate on a scratch simulation of ``sc``; returns the
+    fastest {"tile_rows", "ped_lanes", "mode", "us_per_step"} and all timings."""
+    import torch
+    stream = torch.cuda.Stream()
+    sim = N.from_scenario(sc)
+    N.fp_set_stream(sim.h, stream.cuda_stream)
+    sim.step(warm)
+    sim.synchronize()
+    results = []
+    for mode in modes:
+        try:
+            N.fp_set_step_mode(sim.h, mode)
+        except N.FloodPedError:
+            continue
+        for rows in TILE_ROWS:
+            for lanes in PED_LANES:
+                if mode == N.FP_MODE_PERSISTENT and (rows != 16 or lanes != 8):
+                    continue  # the persistent kernel has one fixed shape
+                N.fp_set_tuning(sim.h, rows, lanes)
+                sim.step(8)
+                sim.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                sim.step(steps)
+                e1.record(stream)
+                e1.synchronize()
+                results.append({"tile_rows": rows, "ped_lanes": lanes, "mode": mode,
+                                "us_per_step": 1e3 * e0.elapsed_time(e1) / steps})
+    sim.close()
+    best = min(results, key=lambda r: r["us_per_step"])
+    return {"best": best, "all": results}
+
+
+def choose(sc, cache_path: str = DEFAULT_CACHE, retune: bool = False) -> dict:
+    """The cached best launch shape for ``sc`` on this device (tuning if absent)."""
+    import torch
+    key = cache_key(torch.cuda.get_device_name(), sc.nx, sc.ny, sc.n_peds)
+    cache = _load(cache_path)
+    if retune or key not in cache:
+        cache[key] = tune(sc)["best"]
+        os.makedirs(os.path.dirname(cache_path) or ".", exist_ok=True)
+        tmp = cache_path + ".%d.tmp" % os.getpid()
+        with open(tmp, "w") as f:
+            json.dump(cache, f, indent=1, sort_keys=True)
+        os.replace(tmp, cache_path)
+    return cache[key]
+
+
+def apply(sim, best: dict) -> None:
+    N.fp_set_step_mode(sim.h, best["mode"])
+    N.fp_set_tuning(sim.h, best["tile_rows"], best["ped_lanes"])

@@ -97,6 +97,7 @@ struct fp_sim {
     bool need_prepare = true, pending_time = false;
     long long pend_t = 0, pend_step = 0;
     int tile_rows = 16;
+    int ped_lanes = 8;   // lanes per pedestrian in the per-step kernel (4, 8, 16)
     FpTmaSet tma[2];
     FpTmaSet tma16[2];  // 16-row tiles, for the persistent kernel
     cudaGraphExec_t graphs[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -248,7 +249,7 @@ static void launch_step(fp_sim *s, int par, int slot, cudaEvent_t *ev = nullptr)
     if (ev) cudaEventRecord(ev[2], s->stream);
     fp_launch_scan(S, s->stream2);
     fp_launch_gather(S, s->stream2);
-    fp_launch_ped_step(S, par, slot, s->stream2);
+    fp_launch_ped_step(S, par, slot, s->ped_lanes, s->stream2);
     if (ev) cudaEventRecord(ev[3], s->stream2);
     cudaEventRecord(s->ev_join, s->stream2);
     cudaStreamWaitEvent(s->stream, s->ev_join, 0);
@@ -675,6 +676,22 @@ int fp_step(fp_sim *s, int32_t n_steps) {
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return s->cuda_fail(e, "step launch");
+    return FP_OK;
+}
+
+int fp_set_tuning(fp_sim *s, int32_t tile_rows, int32_t ped_lanes) {
+    if (!s) return FP_EINVAL;
+    if ((tile_rows != 8 && tile_rows != 16 && tile_rows != 32) || (ped_lanes != 4 && ped_lanes != 8 && ped_lanes != 16))
+        return s->fail(FP_EINVAL, "tile_rows must be 8, 16 or 32 and ped_lanes 4, 8 or 16");
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return s->cuda_fail(e, "tuning switch");
+    if (tile_rows != s->tile_rows) {
+        s->tile_rows = tile_rows;
+        const int rc = encode_tma_rows(s, tile_rows, s->tma);
+        if (rc != FP_OK) return rc;
+    }
+    s->ped_lanes = ped_lanes;
+    s->drop_graphs();
     return FP_OK;
 }
 

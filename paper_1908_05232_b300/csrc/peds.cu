@@ -151,6 +151,7 @@ struct DirectLookup {
     __device__ int operator()(int key) const { return start[key]; }
 };
 
+template <int kG>
 __global__ void __launch_bounds__(256) ped_step_kernel(const __grid_constant__ FpSim S, int par, int slot) {
     __shared__ StepCtl s_ctl;
     FpCounters *C = S.cnt;
@@ -164,7 +165,7 @@ __global__ void __launch_bounds__(256) ped_step_kernel(const __grid_constant__ F
     __syncthreads();
     const StepCtl ctl = s_ctl;
     const int gt = blockIdx.x * blockDim.x + threadIdx.x;
-    ped_group(S, par, ctl, gt / kGroup, threadIdx.x & (kGroup - 1), DirectLookup{S.bin_start}, false);
+    ped_group<kG>(S, par, ctl, gt / kG, threadIdx.x & (kG - 1), DirectLookup{S.bin_start}, false);
 }
 
 // New records sit in B at [first_slot, first_slot + count): give them ids
@@ -261,7 +262,7 @@ __global__ void __launch_bounds__(256) ped_step_batch_kernel(const FpSim *__rest
     }
     __syncthreads();
     const StepCtl ctl = s_ctl;
-    ped_group(S, par, ctl, j0 + threadIdx.x / kGroup, threadIdx.x & (kGroup - 1), DirectLookup{S.bin_start}, false);
+    ped_group<kGroup>(S, par, ctl, j0 + threadIdx.x / kGroup, threadIdx.x & (kGroup - 1), DirectLookup{S.bin_start}, false);
 }
 
 }  // namespace
@@ -288,8 +289,10 @@ void fp_launch_scan(const FpSim &S, cudaStream_t st) {
     scan_kernel<<<fp_scan_tiles(S.nbins), kScanThreads, 0, st>>>(S);
 }
 void fp_launch_gather(const FpSim &S, cudaStream_t st) { gather_kernel<<<blocks_for(S.cap, 256), 256, 0, st>>>(S); }
-void fp_launch_ped_step(const FpSim &S, int par, int slot, cudaStream_t st) {
-    ped_step_kernel<<<blocks_for(S.cap * kGroup, 256), 256, 0, st>>>(S, par, slot);
+void fp_launch_ped_step(const FpSim &S, int par, int slot, int lanes, cudaStream_t st) {
+    if (lanes == 4) ped_step_kernel<4><<<blocks_for(S.cap * 4, 256), 256, 0, st>>>(S, par, slot);
+    else if (lanes == 16) ped_step_kernel<16><<<blocks_for(S.cap * 16, 256), 256, 0, st>>>(S, par, slot);
+    else ped_step_kernel<8><<<blocks_for(S.cap * 8, 256), 256, 0, st>>>(S, par, slot);
 }
 void fp_launch_assign_ids(const FpSim &S, int first_slot, int first_id, int count, cudaStream_t st) {
     if (count > 0) assign_ids_kernel<<<blocks_for(count, 256), 256, 0, st>>>(S, first_slot, first_id, count);

@@ -91,11 +91,11 @@ __device__ __forceinline__ void barrier_and_snapshot(const FpSim &S) {
     for (int k = 0; k < 5; ++k) C->hist[k] = 0ull;
 }
 
-// One pedestrian (record j of A) by a group of kGroup lanes (sub = lane in the
-// group).  lookup(key) gives the first record of hash bin key in A.  With
+// One pedestrian (record j of A) by a group of kG lanes (sub = lane in the
+// group; kG = 4, 8 or 16).  lookup(key) gives the first record of hash bin key in A.  With
 // hash_next the group's first lane also hashes its output record for the next
 // step.  Every lane of the warp must call this (shuffles over the full warp).
-template <class Lookup>
+template <int kG, class Lookup>
 __device__ __forceinline__ void ped_group(const FpSim &S, int par, const StepCtl &ctl, int j, int sub,
                                           const Lookup &lookup, bool hash_next) {
     FpCounters *C = S.cnt;
@@ -223,7 +223,7 @@ __device__ __forceinline__ void ped_group(const FpSim &S, int par, const StepCtl
         const float fcut = __expf((2.0f * kRb - kR) * (1.0f / kB));
 #pragma unroll 1
         for (int r = 0; r < 3; ++r) {
-            for (int k = rk0[r] + sub; k < rk1[r]; k += kGroup) {
+            for (int k = rk0[r] + sub; k < rk1[r]; k += kG) {
                 if (k == j) continue;
                 const float4 q = *reinterpret_cast<const float4 *>(&S.pedA[2 * k]);
                 const float rx = x - q.x, ry = y - q.y;
@@ -249,9 +249,9 @@ __device__ __forceinline__ void ped_group(const FpSim &S, int par, const StepCtl
         }
     }
 #pragma unroll
-    for (int o = kGroup / 2; o > 0; o >>= 1) {
-        Fx += __shfl_xor_sync(0xffffffffu, Fx, o, kGroup);
-        Fy += __shfl_xor_sync(0xffffffffu, Fy, o, kGroup);
+    for (int o = kG / 2; o > 0; o >>= 1) {
+        Fx += __shfl_xor_sync(0xffffffffu, Fx, o, kG);
+        Fy += __shfl_xor_sync(0xffffffffu, Fy, o, kG);
     }
     if (live && leader) {
         const float fxs = __ll2float_rn(Fx) * (1.0f / 262144.0f), fys = __ll2float_rn(Fy) * (1.0f / 262144.0f);

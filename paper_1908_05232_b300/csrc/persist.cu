@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(kPT, 2) persistent_kernel(const __grid_constan
         const bool hash_next = s + 1 < nsteps;
         constexpr int kPedPerCTA = kPT / kGroup;
         for (int pcx = G - 1 - cta; pcx * kPedPerCTA < nA; pcx += G)
-            ped_group(S, par, ctl, pcx * kPedPerCTA + tid / kGroup, tid & (kGroup - 1), lookup, hash_next);
+            ped_group<kGroup>(S, par, ctl, pcx * kPedPerCTA + tid / kGroup, tid & (kGroup - 1), lookup, hash_next);
         if (!grid_sync(bar, S)) return;
         stamp(S, 4 * s + 4);
     }

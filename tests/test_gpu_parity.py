@@ -430,3 +430,36 @@ def test_batch_then_alone_continues(P):
     for x, y in zip(fields(m), fields(alone)):
         assert np.array_equal(x, y)
     assert np.array_equal(m.peds(), alone.peds())
+
+
+def test_launch_shape_does_not_change_results(P):
+    """Every flood tile height and pedestrian lane count gives the same bytes."""
+    from paper_1908_05232_b300 import _native as N
+    sc = _barrier_wet()
+    ref = None
+    for rows, lanes in ((16, 8), (8, 4), (32, 16), (8, 16)):
+        sim = P.from_scenario(sc)
+        N.fp_set_tuning(sim.h, rows, lanes)
+        sim.step(150)
+        sim.synchronize()
+        out = (fields(sim), sim.peds(), sim.counters()["t_ticks"])
+        if ref is None:
+            ref = out
+        else:
+            for x, y in zip(out[0], ref[0]):
+                assert np.array_equal(x, y), (rows, lanes)
+            assert np.array_equal(out[1], ref[1]) and out[2] == ref[2]
+
+
+def test_autotuner_picks_a_valid_shape(P, tmp_path):
+    from paper_1908_05232_b300 import autotune
+    sc = S.plain_coupled_128(seed=2)
+    best = autotune.choose(sc, cache_path=str(tmp_path / "tune.json"))
+    assert best["tile_rows"] in (8, 16, 32) and best["ped_lanes"] in (4, 8, 16)
+    assert best["us_per_step"] > 0
+    again = autotune.choose(sc, cache_path=str(tmp_path / "tune.json"))
+    assert again == best
+    sim = P.from_scenario(sc)
+    autotune.apply(sim, best)
+    sim.step(10)
+    sim.synchronize()

@@ -62,6 +62,13 @@ def lib():
         _lib.or_bags_per_cell.restype = ctypes.c_int32
         _lib.or_bags_per_cell.argtypes = [ctypes.c_double]
         _lib.or_flood_step.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
+        _lib.or_conv3x3.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                    ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int]
+        _lib.or_net_loss_grad.restype = ctypes.c_double
+        _lib.or_net_loss_grad.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_size_t]
     return _lib
 
 
@@ -279,3 +286,48 @@ def nav_field(walkable: np.ndarray, goal: np.ndarray):
 
 def bags_per_cell(dx: float) -> int:
     return int(lib().or_bags_per_cell(_f32(dx)))
+
+
+# -- learned surrogate (build-added): FP64 conv net -----------------------------
+def conv3x3(x, w, b, relu=False):
+    """x: H x W x Ci, w: 3 x 3 x Ci x Co, b: Co -> (H-2) x (W-2) x Co (FP64)."""
+    x = np.ascontiguousarray(x, np.float64)
+    w = np.ascontiguousarray(w, np.float64)
+    b = np.ascontiguousarray(b, np.float64)
+    H, W, Ci = x.shape
+    Co = w.shape[3]
+    y = np.zeros((H - 2, W - 2, Co), np.float64)
+    lib().or_conv3x3(_ptr(x), H, W, Ci, _ptr(w), _ptr(b), Co, _ptr(y), 1 if relu else 0)
+    return y
+
+
+def net_forward(x, ws, bs):
+    h = np.asarray(x, np.float64)
+    for l, (w, b) in enumerate(zip(ws, bs)):
+        h = conv3x3(h, w, b, relu=l + 1 < len(ws))
+    return h
+
+
+def net_loss_grad(x, ws, bs, target):
+    """Mean squared error of the net output against target and its gradients."""
+    x = np.ascontiguousarray(x, np.float64)
+    H, W, _ = x.shape
+    L = len(ws)
+    ch = np.array([ws[0].shape[2]] + [w.shape[3] for w in ws], np.int32)
+    ws_c = [np.ascontiguousarray(w, np.float64) for w in ws]
+    bs_c = [np.ascontiguousarray(b, np.float64) for b in bs]
+    n_act = sum((H - 2 * (l + 1)) * (W - 2 * (l + 1)) * int(ch[l + 1]) for l in range(L))
+    acts = np.zeros(n_act, np.float64)
+    big = max(H * W * int(c) for c in ch)
+    scratch = np.zeros(2 * big, np.float64)
+    dws = [np.zeros_like(w) for w in ws_c]
+    dbs = [np.zeros_like(b) for b in bs_c]
+    P = ctypes.c_void_p
+    wp = (P * L)(*[w.ctypes.data for w in ws_c])
+    bp = (P * L)(*[b.ctypes.data for b in bs_c])
+    dwp = (P * L)(*[w.ctypes.data for w in dws])
+    dbp = (P * L)(*[b.ctypes.data for b in dbs])
+    tgt = np.ascontiguousarray(target, np.float64)
+    loss = lib().or_net_loss_grad(_ptr(x), H, W, L, _ptr(ch), wp, bp, _ptr(tgt), _ptr(acts), dwp, dbp,
+                                  _ptr(scratch), scratch.size)
+    return float(loss), dws, dbs

@@ -687,3 +687,107 @@ double or_mass(const or_params *P, const or_state *S) {
     for (int64_t c = 0; c < n; ++c) m += S->h[c] * P->dx * P->dx;
     return m;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Learned surrogate (build-added, not in the paper): a stack of 3x3 "valid" */
+/* convolutions over NHWC tensors in FP64, with ReLU between layers, and the */
+/* gradients of the mean squared error of its output.  Plain loops in the    */
+/* definition's order.                                                       */
+/* ------------------------------------------------------------------------ */
+
+/* y[i][j][co] = b[co] + sum_{ky,kx,ci} x[i+ky][j+kx][ci] * w[ky][kx][ci][co],
+ * x: H x W x Ci, y: (H-2) x (W-2) x Co; relu != 0 clamps y at 0. */
+void or_conv3x3(const double *x, int H, int W, int Ci, const double *w, const double *b, int Co, double *y,
+                int relu) {
+    const int Ho = H - 2, Wo = W - 2;
+    for (int i = 0; i < Ho; ++i)
+        for (int j = 0; j < Wo; ++j)
+            for (int co = 0; co < Co; ++co) {
+                double acc = b[co];
+                for (int ky = 0; ky < 3; ++ky)
+                    for (int kx = 0; kx < 3; ++kx)
+                        for (int ci = 0; ci < Ci; ++ci)
+                            acc += x[((size_t)(i + ky) * W + (j + kx)) * Ci + ci] *
+                                   w[((size_t)(ky * 3 + kx) * Ci + ci) * Co + co];
+                if (relu && acc < 0.0) acc = 0.0;
+                y[((size_t)i * Wo + j) * Co + co] = acc;
+            }
+}
+
+/* Gradients of a conv layer (pre-activation output y): given dy (Ho x Wo x Co),
+ * accumulate dx (H x W x Ci, may be NULL), dw and db. */
+void or_conv3x3_backward(const double *x, int H, int W, int Ci, const double *w, int Co, const double *dy,
+                         double *dx, double *dw, double *db) {
+    const int Ho = H - 2, Wo = W - 2;
+    for (int i = 0; i < Ho; ++i)
+        for (int j = 0; j < Wo; ++j)
+            for (int co = 0; co < Co; ++co) {
+                const double g = dy[((size_t)i * Wo + j) * Co + co];
+                db[co] += g;
+                for (int ky = 0; ky < 3; ++ky)
+                    for (int kx = 0; kx < 3; ++kx)
+                        for (int ci = 0; ci < Ci; ++ci) {
+                            const size_t xi = ((size_t)(i + ky) * W + (j + kx)) * Ci + ci;
+                            const size_t wi = ((size_t)(ky * 3 + kx) * Ci + ci) * Co + co;
+                            dw[wi] += g * x[xi];
+                            if (dx) dx[xi] += g * w[wi];
+                        }
+            }
+}
+
+/* Forward through L layers (channels ch[0..L]); acts receives every layer's
+ * output (post-ReLU except the last), laid out one after another.  Returns the
+ * final output pointer inside acts. */
+double *or_net_forward(const double *x, int H, int W, int L, const int *ch, const double *const *ws,
+                       const double *const *bs, double *acts) {
+    const double *in = x;
+    double *out = acts;
+    int h = H, w = W;
+    for (int l = 0; l < L; ++l) {
+        or_conv3x3(in, h, w, ch[l], ws[l], bs[l], ch[l + 1], out, l + 1 < L);
+        in = out;
+        h -= 2; w -= 2;
+        out += (size_t)h * w * ch[l + 1];
+    }
+    return (double *)in;
+}
+
+/* Loss = mean over the final output of (out - target)^2; fills dws/dbs
+ * (zeroed first) with its gradients.  scratch holds 2 x the largest activation. */
+double or_net_loss_grad(const double *x, int H, int W, int L, const int *ch, const double *const *ws,
+                        const double *const *bs, const double *target, double *acts, double *const *dws,
+                        double *const *dbs, double *scratch, size_t scratch_len) {
+    size_t off[16];
+    int hs[17], wsz[17];
+    hs[0] = H; wsz[0] = W;
+    size_t o = 0;
+    for (int l = 0; l < L; ++l) {
+        off[l] = o;
+        hs[l + 1] = hs[l] - 2; wsz[l + 1] = wsz[l] - 2;
+        o += (size_t)hs[l + 1] * wsz[l + 1] * ch[l + 1];
+    }
+    const double *out = or_net_forward(x, H, W, L, ch, ws, bs, acts);
+    const size_t n_out = (size_t)hs[L] * wsz[L] * ch[L];
+    double loss = 0.0;
+    double *g = scratch, *g2 = scratch + scratch_len / 2;
+    for (size_t k = 0; k < n_out; ++k) {
+        const double d = out[k] - target[k];
+        loss += d * d;
+        g[k] = 2.0 * d / (double)n_out;
+    }
+    loss /= (double)n_out;
+    for (int l = L - 1; l >= 0; --l) {
+        const size_t nw = (size_t)9 * ch[l] * ch[l + 1];
+        memset(dws[l], 0, nw * sizeof(double));
+        memset(dbs[l], 0, (size_t)ch[l + 1] * sizeof(double));
+        const double *xin = l == 0 ? x : acts + off[l - 1];
+        const size_t nin = (size_t)hs[l] * wsz[l] * ch[l];
+        if (l > 0) memset(g2, 0, nin * sizeof(double));
+        or_conv3x3_backward(xin, hs[l], wsz[l], ch[l], ws[l], ch[l + 1], g, l > 0 ? g2 : NULL, dws[l], dbs[l]);
+        if (l > 0) {
+            /* through the ReLU of layer l-1's output */
+            for (size_t k = 0; k < nin; ++k) g[k] = xin[k] > 0.0 ? g2[k] : 0.0;
+        }
+    }
+    return loss;
+}

@@ -1,0 +1,67 @@
+"""Pins of the oracle's FP64 conv net (the learned surrogate, build-added):
+exact special cases of a convolution and central finite differences of the
+loss gradient."""
+import numpy as np
+import pytest
+
+
+def _net(rng, ch=(4, 6, 5, 3)):
+    ws = [rng.normal(0, 0.4, (3, 3, ch[l], ch[l + 1])) for l in range(len(ch) - 1)]
+    bs = [rng.normal(0, 0.1, ch[l + 1]) for l in range(len(ch) - 1)]
+    return ws, bs
+
+
+def test_conv_delta_kernel_is_center_crop(oracle_mod):
+    rng = np.random.default_rng(0)
+    x = rng.normal(size=(9, 7, 3))
+    w = np.zeros((3, 3, 3, 3))
+    for c in range(3):
+        w[1, 1, c, c] = 1.0
+    y = oracle_mod.conv3x3(x, w, np.zeros(3))
+    assert np.array_equal(y, x[1:-1, 1:-1, :])
+
+
+def test_conv_shift_and_sum_of_taps(oracle_mod):
+    rng = np.random.default_rng(1)
+    x = rng.normal(size=(8, 10, 2))
+    w = np.zeros((3, 3, 2, 1))
+    w[0, 2, 1, 0] = 1.0          # picks x[i, j+2, 1]
+    w[2, 0, 0, 0] = -2.0         # and -2 x[i+2, j, 0]
+    y = oracle_mod.conv3x3(x, w, np.array([0.5]))
+    want = x[:-2, 2:, 1] - 2.0 * x[2:, :-2, 0] + 0.5
+    assert np.allclose(y[..., 0], want, rtol=0, atol=1e-15)
+
+
+def test_relu_clamps(oracle_mod):
+    x = -np.ones((3, 3, 1))
+    w = np.ones((3, 3, 1, 1))
+    assert oracle_mod.conv3x3(x, w, np.zeros(1), relu=True)[0, 0, 0] == 0.0
+    assert oracle_mod.conv3x3(x, w, np.zeros(1), relu=False)[0, 0, 0] == -9.0
+
+
+def test_loss_gradient_finite_differences(oracle_mod):
+    rng = np.random.default_rng(2)
+    ws, bs = _net(rng)
+    x = rng.normal(size=(12, 11, 4))
+    target = rng.normal(size=(6, 5, 3))
+    loss, dws, dbs = oracle_mod.net_loss_grad(x, ws, bs, target)
+    out = oracle_mod.net_forward(x, ws, bs)
+    assert np.isclose(loss, np.mean((out - target) ** 2), rtol=1e-12)
+    eps = 1e-6
+    for l in range(len(ws)):
+        for idx in [(0, 0, 0, 0), (1, 2, 1, 2), (2, 1, ws[l].shape[2] - 1, ws[l].shape[3] - 1)]:
+            wp = [w.copy() for w in ws]
+            wm = [w.copy() for w in ws]
+            wp[l][idx] += eps
+            wm[l][idx] -= eps
+            lp = oracle_mod.net_loss_grad(x, wp, bs, target)[0]
+            lm = oracle_mod.net_loss_grad(x, wm, bs, target)[0]
+            fd = (lp - lm) / (2 * eps)
+            assert abs(fd - dws[l][idx]) <= 1e-6 * max(1.0, abs(fd)), (l, idx, fd, dws[l][idx])
+        k = bs[l].shape[0] - 1
+        bp = [b.copy() for b in bs]
+        bm = [b.copy() for b in bs]
+        bp[l][k] += eps
+        bm[l][k] -= eps
+        fd = (oracle_mod.net_loss_grad(x, ws, bp, target)[0] - oracle_mod.net_loss_grad(x, ws, bm, target)[0]) / (2 * eps)
+        assert abs(fd - dbs[l][k]) <= 1e-6 * max(1.0, abs(fd))

@@ -220,6 +220,25 @@ int fp_batch_step(fp_batch *batch, int32_t n_steps);
 int fp_batch_synchronize(fp_batch *batch);
 int fp_batch_destroy(fp_batch *batch);
 
+/* ---- learned surrogate -------------------------------------------------------
+ * Build-added (the paper has no surrogate): a 5-layer 3x3 convolutional net
+ * 4 -> 32 -> 32 -> 32 -> 32 -> 3 channels, ReLU between layers, mapping
+ * (h, hu, hv, z) over an 11 x 11 neighbourhood to the change of (h, hu, hv) of
+ * the centre cell over FP_SUR_WINDOW fixed time steps.  Forward on the tensor
+ * cores (tcgen05, BF16 operands, FP32 accumulation); FP32 master parameters,
+ * layer by layer w[ky][kx][ci][co] then b[co]. */
+#define FP_SUR_WINDOW 8
+#define FP_SUR_HALO 5
+typedef struct fp_surrogate fp_surrogate;
+int fp_surrogate_num_params(void);
+int fp_surrogate_create(uint64_t seed, fp_surrogate **out);
+int fp_surrogate_destroy(fp_surrogate *sur);
+int fp_surrogate_get_params(fp_surrogate *sur, float *dst, size_t n);
+int fp_surrogate_set_params(fp_surrogate *sur, const float *src, size_t n);
+/* x: device FP32 [B][H][W][4] = (h, hu, hv, z); y: device FP32
+ * [B][H-10][W-10][3] = predicted change of (h, hu, hv); H, W >= 11. */
+int fp_surrogate_forward(fp_surrogate *sur, const float *x, int32_t B, int32_t H, int32_t W, float *y);
+
 /* Wait for enqueued work; returns FP_ETIMEOUT / FP_EOVERFLOW / FP_ENAN when the
  * device raised the corresponding error bit. */
 int fp_synchronize(fp_sim *sim);

@@ -4,8 +4,8 @@ The computation lives in ``libfloodped.so`` (CUDA for sm_103a, C ABI in
 ``include/floodped.h``); this package only builds and binds it.
 """
 from . import build
-from ._native import (Batch, FloodPedError, FpConfig, PED_DTYPE, Simulation, TICKS, config_for, from_scenario,
+from ._native import (Batch, FloodPedError, FpConfig, Surrogate, PED_DTYPE, Simulation, TICKS, config_for, from_scenario,
                       ped_records, lib)
 
-__all__ = ["Batch", "build", "FloodPedError", "FpConfig", "PED_DTYPE", "Simulation", "TICKS", "config_for",
+__all__ = ["Batch", "Surrogate", "build", "FloodPedError", "FpConfig", "PED_DTYPE", "Simulation", "TICKS", "config_for",
            "from_scenario", "ped_records", "lib"]

@@ -78,6 +78,14 @@ def lib():
         L.fp_water_volume_noalloc.argtypes = [_VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, ctypes.c_float,
                                               _VP, _VP]
         L.fp_water_volume_noalloc.restype = ctypes.c_int
+        for name, args in {"fp_surrogate_create": [ctypes.c_uint64, _VP], "fp_surrogate_destroy": [_VP],
+                           "fp_surrogate_get_params": [_VP, _VP, ctypes.c_size_t],
+                           "fp_surrogate_set_params": [_VP, _VP, ctypes.c_size_t],
+                           "fp_surrogate_forward": [_VP, _VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _VP],
+                           "fp_surrogate_num_params": []}.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = ctypes.c_int
         L.fp_last_error.argtypes = [_VP]
         L.fp_last_error.restype = ctypes.c_char_p
         _lib = L
@@ -317,3 +325,52 @@ def from_scenario(sc, max_peds=None, tile_rows=0, peds=True, mode=None) -> Simul
     if peds and sc.n_peds:
         sim.add_pedestrians(ped_records(sc.peds))
     return sim
+
+
+class Surrogate:
+    """The learned flood surrogate (tcgen05 forward); parameters as FP32 numpy."""
+
+    CH = (4, 32, 32, 32, 32, 3)
+
+    def __init__(self, seed=0):
+        self.h = _VP()
+        _check(lib().fp_surrogate_create(int(seed), ctypes.byref(self.h)))
+        self.n_params = lib().fp_surrogate_num_params()
+
+    def params(self) -> np.ndarray:
+        out = np.zeros(self.n_params, np.float32)
+        _check(lib().fp_surrogate_get_params(self.h, _ptr(out), out.size))
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, np.float32)
+        _check(lib().fp_surrogate_set_params(self.h, _ptr(p), p.size))
+
+    def layers(self, p=None):
+        """Split a flat parameter vector into per-layer (w[3,3,ci,co], b[co])."""
+        p = self.params() if p is None else p
+        out, o = [], 0
+        for ci, co in zip(self.CH[:-1], self.CH[1:]):
+            w = p[o:o + 9 * ci * co].reshape(3, 3, ci, co)
+            o += 9 * ci * co
+            b = p[o:o + co]
+            o += co
+            out.append((w, b))
+        return out
+
+    def forward(self, x, y):
+        """x: CUDA tensor [B,H,W,4] float32; y: CUDA tensor [B,H-10,W-10,3] float32."""
+        B, H, W, _ = x.shape
+        _check(lib().fp_surrogate_forward(self.h, _ptr(x), B, H, W, _ptr(y)))
+        return y
+
+    def close(self):
+        if self.h is not None:
+            _check(lib().fp_surrogate_destroy(self.h))
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

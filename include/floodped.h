@@ -238,6 +238,14 @@ int fp_surrogate_set_params(fp_surrogate *sur, const float *src, size_t n);
 /* x: device FP32 [B][H][W][4] = (h, hu, hv, z); y: device FP32
  * [B][H-10][W-10][3] = predicted change of (h, hu, hv); H, W >= 11. */
 int fp_surrogate_forward(fp_surrogate *sur, const float *x, int32_t B, int32_t H, int32_t W, float *y);
+/* Loss = mean squared error of the forward output against target (device FP32
+ * [B][H-10][W-10][3]) and its gradient with respect to every parameter
+ * (grads: host or device, fp_surrogate_num_params floats; may be NULL). */
+int fp_surrogate_gradients(fp_surrogate *sur, const float *x, const float *target, int32_t B, int32_t H, int32_t W,
+                           float *grads, double *loss);
+/* One Adam step (beta1 0.9, beta2 0.999) of learning rate lr on that loss. */
+int fp_surrogate_train_step(fp_surrogate *sur, const float *x, const float *target, int32_t B, int32_t H, int32_t W,
+                            float lr, double *loss);
 
 /* Wait for enqueued work; returns FP_ETIMEOUT / FP_EOVERFLOW / FP_ENAN when the
  * device raised the corresponding error bit. */

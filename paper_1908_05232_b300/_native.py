@@ -82,7 +82,11 @@ def lib():
                            "fp_surrogate_get_params": [_VP, _VP, ctypes.c_size_t],
                            "fp_surrogate_set_params": [_VP, _VP, ctypes.c_size_t],
                            "fp_surrogate_forward": [_VP, _VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _VP],
-                           "fp_surrogate_num_params": []}.items():
+                           "fp_surrogate_num_params": [],
+                           "fp_surrogate_gradients": [_VP, _VP, _VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                                      _VP, _VP],
+                           "fp_surrogate_train_step": [_VP, _VP, _VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                                       ctypes.c_float, _VP]}.items():
             f = getattr(L, name)
             f.argtypes = args
             f.restype = ctypes.c_int
@@ -363,6 +367,19 @@ class Surrogate:
         B, H, W, _ = x.shape
         _check(lib().fp_surrogate_forward(self.h, _ptr(x), B, H, W, _ptr(y)))
         return y
+
+    def gradients(self, x, target):
+        B, H, W, _ = x.shape
+        g = np.zeros(self.n_params, np.float32)
+        loss = ctypes.c_double()
+        _check(lib().fp_surrogate_gradients(self.h, _ptr(x), _ptr(target), B, H, W, _ptr(g), ctypes.byref(loss)))
+        return float(loss.value), g
+
+    def train_step(self, x, target, lr):
+        B, H, W, _ = x.shape
+        loss = ctypes.c_double()
+        _check(lib().fp_surrogate_train_step(self.h, _ptr(x), _ptr(target), B, H, W, float(lr), ctypes.byref(loss)))
+        return float(loss.value)
 
     def close(self):
         if self.h is not None:

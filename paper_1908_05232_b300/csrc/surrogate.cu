@@ -253,20 +253,177 @@ __global__ void pack_input_kernel(const float *__restrict__ x4, size_t npix, __n
     dst[1] = reinterpret_cast<const uint4 *>(o)[1];
 }
 
+
+// ---- training (A13): FP32 backward on the CUDA cores --------------------------
+
+// g = d loss / d (last layer pre-activation): loss = mean (0.1 * z - t)^2 over
+// B x Ho x Wo x 3, so dz = 0.2 (0.1 z - t) / n = 0.2 (y - t) / n with y the
+// scaled output.  Per-block FP64 partial losses, summed in block order later.
+__global__ void loss_grad_kernel(const float *__restrict__ y, const float *__restrict__ t, size_t n,
+                                 float *__restrict__ g, double *__restrict__ partial) {
+    __shared__ double red[256 / 32];
+    double acc = 0.0;
+    const size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (k < n) {
+        const float d = y[k] - t[k];
+        acc = (double)d * (double)d;
+        g[k] = 2.0f * kOutScale * d / (float)n;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s2 = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s2 += red[w];
+        partial[blockIdx.x] = s2;
+    }
+}
+
+__global__ void sum_partials_kernel(const double *__restrict__ partial, int n, double scale, double *out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double s2 = 0.0;
+        for (int k = 0; k < n; ++k) s2 += partial[k];
+        *out = s2 * scale;
+    }
+}
+
+__device__ __forceinline__ float act_value(const __nv_bfloat16 *a, size_t i) { return __bfloat162float(a[i]); }
+
+// dW[t][ci][co] += sum_p X[p + off_t][ci] dY[p][co] and db[co] += sum_p dY[p][co],
+// one CTA per (tap, input channel); threads stride over output pixels; fixed-order
+// tree reduction.  X: BF16 [B][H][W][CX] (channel stride CX >= CIN).
+template <int COUT>
+__global__ void __launch_bounds__(256) conv_bwd_weight_kernel(const __nv_bfloat16 *__restrict__ X, int CX, int CIN,
+                                                              const float *__restrict__ dY, int B, int H, int W,
+                                                              float *__restrict__ dw, float *__restrict__ db) {
+    const int t = blockIdx.x / CIN, ci = blockIdx.x % CIN;
+    const int ky = t / 3, kx = t % 3;
+    const int Ho = H - 2, Wo = W - 2;
+    const size_t npix = (size_t)B * Ho * Wo;
+    float acc[COUT], accb[COUT];
+#pragma unroll
+    for (int c = 0; c < COUT; ++c) { acc[c] = 0.0f; accb[c] = 0.0f; }
+    const bool do_b = blockIdx.x == 0;
+    for (size_t p = threadIdx.x; p < npix; p += blockDim.x) {
+        const int b = (int)(p / ((size_t)Ho * Wo));
+        const int r = (int)(p % ((size_t)Ho * Wo));
+        const int oy = r / Wo, ox = r % Wo;
+        const float xv = act_value(X, (((size_t)b * H + oy + ky) * W + ox + kx) * CX + ci);
+        const float *g = dY + p * COUT;
+#pragma unroll
+        for (int c = 0; c < COUT; ++c) {
+            acc[c] = fmaf(xv, g[c], acc[c]);
+            if (do_b) accb[c] += g[c];
+        }
+    }
+    __shared__ float red[256][COUT + 1];
+#pragma unroll
+    for (int c = 0; c < COUT; ++c) red[threadIdx.x][c] = acc[c];
+    __syncthreads();
+    for (int sz = 128; sz > 0; sz >>= 1) {
+        if ((int)threadIdx.x < sz)
+            for (int c = 0; c < COUT; ++c) red[threadIdx.x][c] += red[threadIdx.x + sz][c];
+        __syncthreads();
+    }
+    if ((int)threadIdx.x < COUT) dw[((size_t)t * CIN + ci) * COUT + threadIdx.x] = red[0][threadIdx.x];
+    if (do_b) {
+        __syncthreads();
+#pragma unroll
+        for (int c = 0; c < COUT; ++c) red[threadIdx.x][c] = accb[c];
+        __syncthreads();
+        for (int sz = 128; sz > 0; sz >>= 1) {
+            if ((int)threadIdx.x < sz)
+                for (int c = 0; c < COUT; ++c) red[threadIdx.x][c] += red[threadIdx.x + sz][c];
+            __syncthreads();
+        }
+        if ((int)threadIdx.x < COUT) db[threadIdx.x] = red[0][threadIdx.x];
+    }
+}
+
+// dX[q][ci] = sum_{t, co} dY[q - off_t][co] W[t][ci][co] over valid output
+// positions, masked by the ReLU of X (the previous layer's output): the
+// gradient of the previous layer's pre-activation.  One thread per (q, ci).
+template <int CIN, int COUT>
+__global__ void conv_bwd_data_kernel(const float *__restrict__ dY, const float *__restrict__ w,
+                                     const __nv_bfloat16 *__restrict__ X, int B, int H, int W,
+                                     float *__restrict__ dXm) {
+    const size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    const size_t n = (size_t)B * H * W * CIN;
+    if (k >= n) return;
+    const int ci = (int)(k % CIN);
+    const size_t q = k / CIN;
+    const int b = (int)(q / ((size_t)H * W));
+    const int r = (int)(q % ((size_t)H * W));
+    const int iy = r / W, ix = r % W;
+    const int Ho = H - 2, Wo = W - 2;
+    float acc = 0.0f;
+    if (act_value(X, q * CIN + ci) > 0.0f) {
+        for (int ky = 0; ky < 3; ++ky) {
+            const int oy = iy - ky;
+            if (oy < 0 || oy >= Ho) continue;
+            for (int kx = 0; kx < 3; ++kx) {
+                const int ox = ix - kx;
+                if (ox < 0 || ox >= Wo) continue;
+                const float *g = dY + (((size_t)b * Ho + oy) * Wo + ox) * COUT;
+                const float *wr = w + ((size_t)(ky * 3 + kx) * CIN + ci) * COUT;
+#pragma unroll 8
+                for (int co = 0; co < COUT; ++co) acc = fmaf(g[co], wr[co], acc);
+            }
+        }
+    }
+    dXm[k] = acc;
+}
+
+// Adam on the FP32 master parameters
+__global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
+                            float *__restrict__ v, int n, float lr, float b1, float b2, float eps, float c1, float c2) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const float gk = g[k];
+    const float mk = b1 * m[k] + (1.0f - b1) * gk;
+    const float vk = b2 * v[k] + (1.0f - b2) * gk * gk;
+    m[k] = mk;
+    v[k] = vk;
+    p[k] -= lr * (mk * c1) / (sqrtf(vk * c2) + eps);
+}
+
+// FP32 master (one layer) -> packed BF16 operand blocks and padded bias
+__global__ void pack_layer_kernel(const float *__restrict__ w, const float *__restrict__ b, int ci_real, int co_real,
+                                  int ci_pad, int co_pad, __nv_bfloat16 *__restrict__ pk, float *__restrict__ bias) {
+    const int kc = ci_pad / 16;
+    const int total = 9 * kc * 2 * co_pad * 8;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < co_pad) bias[k] = k < co_real ? b[k] : 0.0f;
+    if (k >= total) return;
+    const int e = k % 8, n = (k / 8) % co_pad, j = (k / (8 * co_pad)) % 2;
+    const int c = (k / (16 * co_pad)) % kc, t = k / (16 * co_pad * kc);
+    const int ci = 16 * c + 8 * j + e;
+    float v = 0.0f;
+    if (ci < ci_real && n < co_real) v = w[((size_t)t * ci_real + ci) * co_real + n];
+    pk[k] = __float2bfloat16(v);
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 struct fp_surrogate {
-    std::vector<float> master;                    // FP32 parameters, per layer w[3][3][ci][co] then b[co]
-    std::vector<size_t> w_off, b_off;             // offsets into master
+    size_t n_params = 0;
+    std::vector<size_t> w_off, b_off;             // offsets of each layer's w and b
+    float *d_master = nullptr, *d_m = nullptr, *d_v = nullptr, *d_grad = nullptr;
     __nv_bfloat16 *d_wpack[kLayers] = {};         // packed BF16 weights per layer
     float *d_bias[kLayers] = {};                  // padded FP32 biases per layer
     unsigned *d_err = nullptr;
+    double *d_loss = nullptr, *d_partial = nullptr;
+    long long adam_t = 0;
+    // cached scratch: activations (BF16), output and gradients (FP32)
+    size_t cap_pix = 0, cap_partial = 0;
+    __nv_bfloat16 *d_a[kLayers] = {};             // inputs of every layer (a[0] packed input)
+    float *d_out = nullptr, *d_g0 = nullptr, *d_g1 = nullptr;
     std::vector<void *> allocs;
     int sms = 148;
-    std::string err;
 };
 
 namespace {
@@ -296,30 +453,90 @@ size_t param_count() {
     return n;
 }
 
-// master FP32 -> packed BF16 operand blocks [tap][chunk][k-core][co][8] and padded biases
-cudaError_t upload_packed(fp_surrogate *s) {
+// FP32 master -> packed BF16 operand blocks and padded biases (on the device)
+cudaError_t repack(fp_surrogate *s, cudaStream_t st) {
     for (int l = 0; l < kLayers; ++l) {
         const int ci_pad = l == 0 ? kCin0 : kWidth, co_pad = l == kLayers - 1 ? kCout4 : kWidth;
-        const int kc = ci_pad / 16;
-        std::vector<__nv_bfloat16> pk((size_t)9 * kc * 2 * co_pad * 8, __float2bfloat16(0.0f));
-        const float *w = s->master.data() + s->w_off[l];
-        for (int t = 0; t < 9; ++t)
-            for (int c = 0; c < kc; ++c)
-                for (int j = 0; j < 2; ++j)
-                    for (int n = 0; n < co_pad; ++n)
-                        for (int e = 0; e < 8; ++e) {
-                            const int ci = 16 * c + 8 * j + e;
-                            float v = 0.0f;
-                            if (ci < kCh[l] && n < kCh[l + 1]) v = w[((size_t)t * kCh[l] + ci) * kCh[l + 1] + n];
-                            pk[((((size_t)t * kc + c) * 2 + j) * co_pad + n) * 8 + e] = __float2bfloat16(v);
-                        }
-        std::vector<float> b(co_pad, 0.0f);
-        for (int n = 0; n < kCh[l + 1]; ++n) b[n] = s->master[s->b_off[l] + n];
-        cudaError_t e = cudaMemcpy(s->d_wpack[l], pk.data(), pk.size() * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMemcpy(s->d_bias[l], b.data(), b.size() * sizeof(float), cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) return e;
+        const int total = 9 * (ci_pad / 16) * 2 * co_pad * 8;
+        pack_layer_kernel<<<(total + 255) / 256, 256, 0, st>>>(s->d_master + s->w_off[l], s->d_master + s->b_off[l],
+                                                              kCh[l], kCh[l + 1], ci_pad, co_pad, s->d_wpack[l],
+                                                              s->d_bias[l]);
     }
-    return cudaDeviceSynchronize();
+    return cudaGetLastError();
+}
+
+bool ensure_scratch(fp_surrogate *s, size_t pix) {
+    if (pix <= s->cap_pix) return true;
+    for (int l = 0; l < kLayers; ++l) cudaFree(s->d_a[l]);
+    cudaFree(s->d_out); cudaFree(s->d_g0); cudaFree(s->d_g1); cudaFree(s->d_partial);
+    s->cap_pix = 0;
+    bool ok = cudaMalloc(&s->d_a[0], pix * kCin0 * sizeof(__nv_bfloat16)) == cudaSuccess;
+    for (int l = 1; l < kLayers; ++l) ok &= cudaMalloc(&s->d_a[l], pix * kWidth * sizeof(__nv_bfloat16)) == cudaSuccess;
+    ok &= cudaMalloc(&s->d_out, pix * 3 * sizeof(float)) == cudaSuccess;
+    ok &= cudaMalloc(&s->d_g0, pix * kWidth * sizeof(float)) == cudaSuccess;
+    ok &= cudaMalloc(&s->d_g1, pix * kWidth * sizeof(float)) == cudaSuccess;
+    s->cap_partial = (pix * 3 + 255) / 256 + 1;
+    ok &= cudaMalloc(&s->d_partial, s->cap_partial * sizeof(double)) == cudaSuccess;
+    if (ok) s->cap_pix = pix;
+    return ok;
+}
+
+// forward of B images x [B][H][W][4] keeping every layer's input in d_a; output to out
+cudaError_t forward_keep(fp_surrogate *s, const float *x, int B, int H, int W, float *out, cudaStream_t st) {
+    const size_t npix0 = (size_t)B * H * W;
+    pack_input_kernel<<<(unsigned)((npix0 + 255) / 256), 256, 0, st>>>(x, npix0, s->d_a[0]);
+    cudaError_t e = launch_conv<kCin0, kWidth, false>(s, 0, s->d_a[0], B, H, W, s->d_a[1], st);
+    int h = H - 2, w = W - 2;
+    for (int l = 1; l < kLayers - 1 && e == cudaSuccess; ++l) {
+        e = launch_conv<kWidth, kWidth, false>(s, l, s->d_a[l], B, h, w, s->d_a[l + 1], st);
+        h -= 2; w -= 2;
+    }
+    if (e == cudaSuccess) e = launch_conv<kWidth, kCout4, true>(s, kLayers - 1, s->d_a[kLayers - 1], B, h, w, out, st);
+    return e;
+}
+
+// loss and gradients (into d_grad, master layout) of the last forward_keep
+cudaError_t backward(fp_surrogate *s, const float *target, int B, int H, int W, cudaStream_t st) {
+    const int H5 = H - 2 * kLayers, W5 = W - 2 * kLayers;
+    const size_t n_out = (size_t)B * H5 * W5 * 3;
+    const unsigned nb = (unsigned)((n_out + 255) / 256);
+    loss_grad_kernel<<<nb, 256, 0, st>>>(s->d_out, target, n_out, s->d_g0, s->d_partial);
+    sum_partials_kernel<<<1, 32, 0, st>>>(s->d_partial, (int)nb, 1.0 / (double)n_out, s->d_loss);
+    float *g = s->d_g0, *gprev = s->d_g1;
+    for (int l = kLayers - 1; l >= 0; --l) {
+        const int Hl = H - 2 * l, Wl = W - 2 * l;  // input size of layer l
+        float *dw = s->d_grad + s->w_off[l], *db = s->d_grad + s->b_off[l];
+        if (l == kLayers - 1) {
+            conv_bwd_weight_kernel<3><<<9 * kWidth, 256, 0, st>>>(s->d_a[l], kWidth, kWidth, g, B, Hl, Wl, dw, db);
+            const size_t n = (size_t)B * Hl * Wl * kWidth;
+            conv_bwd_data_kernel<kWidth, 3><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+                g, s->d_master + s->w_off[l], s->d_a[l], B, Hl, Wl, gprev);
+        } else if (l > 0) {
+            conv_bwd_weight_kernel<kWidth><<<9 * kWidth, 256, 0, st>>>(s->d_a[l], kWidth, kWidth, g, B, Hl, Wl, dw, db);
+            const size_t n = (size_t)B * Hl * Wl * kWidth;
+            conv_bwd_data_kernel<kWidth, kWidth><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+                g, s->d_master + s->w_off[l], s->d_a[l], B, Hl, Wl, gprev);
+        } else {
+            conv_bwd_weight_kernel<kWidth><<<9 * kCh[0], 256, 0, st>>>(s->d_a[0], kCin0, kCh[0], g, B, Hl, Wl, dw, db);
+        }
+        std::swap(g, gprev);
+    }
+    return cudaGetLastError();
+}
+
+int check_err(fp_surrogate *s, cudaError_t e, const char *what) {
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        fp_note_error((std::string(what) + ": " + cudaGetErrorString(e)).c_str());
+        return FP_ECUDA;
+    }
+    unsigned herr = 0;
+    cudaMemcpy(&herr, s->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost);
+    if (herr & FP_ERR_TIMEOUT) {
+        fp_note_error((std::string(what) + ": tensor-core completion wait timed out").c_str());
+        return FP_ETIMEOUT;
+    }
+    return FP_OK;
 }
 
 }  // namespace
@@ -339,34 +556,39 @@ int fp_surrogate_create(uint64_t seed, fp_surrogate **out) {
         s->b_off.push_back(o);
         o += kCh[l + 1];
     }
-    s->master.assign(o, 0.0f);
+    s->n_params = o;
+    std::vector<float> init(o, 0.0f);
     std::mt19937_64 rng(seed);
     for (int l = 0; l < kLayers; ++l) {
         std::normal_distribution<float> nd(0.0f, std::sqrt(2.0f / (9.0f * kCh[l])));
-        for (size_t k = 0; k < (size_t)9 * kCh[l] * kCh[l + 1]; ++k) s->master[s->w_off[l] + k] = nd(rng);
-        if (l == kLayers - 1)
-            for (size_t k = 0; k < (size_t)9 * kCh[l] * kCh[l + 1]; ++k) s->master[s->w_off[l] + k] *= 0.1f;
+        const float scale = l == kLayers - 1 ? 0.1f : 1.0f;
+        for (size_t k = 0; k < (size_t)9 * kCh[l] * kCh[l + 1]; ++k) init[s->w_off[l] + k] = scale * nd(rng);
     }
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, dev);
+    auto alloc = [&](size_t bytes) -> void * {
+        void *p = nullptr;
+        if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+        cudaMemset(p, 0, bytes);
+        s->allocs.push_back(p);
+        return p;
+    };
     bool ok = true;
+    ok &= (s->d_master = static_cast<float *>(alloc(o * sizeof(float)))) != nullptr;
+    ok &= (s->d_m = static_cast<float *>(alloc(o * sizeof(float)))) != nullptr;
+    ok &= (s->d_v = static_cast<float *>(alloc(o * sizeof(float)))) != nullptr;
+    ok &= (s->d_grad = static_cast<float *>(alloc(o * sizeof(float)))) != nullptr;
     for (int l = 0; l < kLayers; ++l) {
         const int ci_pad = l == 0 ? kCin0 : kWidth, co_pad = l == kLayers - 1 ? kCout4 : kWidth;
-        void *p = nullptr, *q = nullptr;
-        ok &= cudaMalloc(&p, (size_t)9 * ci_pad * co_pad * sizeof(__nv_bfloat16)) == cudaSuccess;
-        ok &= cudaMalloc(&q, (size_t)co_pad * sizeof(float)) == cudaSuccess;
-        s->allocs.push_back(p);
-        s->allocs.push_back(q);
-        s->d_wpack[l] = static_cast<__nv_bfloat16 *>(p);
-        s->d_bias[l] = static_cast<float *>(q);
+        ok &= (s->d_wpack[l] = static_cast<__nv_bfloat16 *>(alloc((size_t)9 * ci_pad * co_pad * 2))) != nullptr;
+        ok &= (s->d_bias[l] = static_cast<float *>(alloc((size_t)co_pad * sizeof(float)))) != nullptr;
     }
-    void *e = nullptr;
-    ok &= cudaMalloc(&e, sizeof(unsigned)) == cudaSuccess;
-    s->allocs.push_back(e);
-    s->d_err = static_cast<unsigned *>(e);
-    if (ok) ok = cudaMemset(s->d_err, 0, sizeof(unsigned)) == cudaSuccess;
-    if (!ok || upload_packed(s) != cudaSuccess) {
+    ok &= (s->d_err = static_cast<unsigned *>(alloc(sizeof(unsigned)))) != nullptr;
+    ok &= (s->d_loss = static_cast<double *>(alloc(sizeof(double)))) != nullptr;
+    if (ok) ok = cudaMemcpy(s->d_master, init.data(), o * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess;
+    if (ok) ok = repack(s, 0) == cudaSuccess && cudaDeviceSynchronize() == cudaSuccess;
+    if (!ok) {
         for (void *p : s->allocs) cudaFree(p);
         delete s;
         fp_note_error("fp_surrogate_create: device allocation or upload failed");
@@ -379,62 +601,65 @@ int fp_surrogate_create(uint64_t seed, fp_surrogate **out) {
 int fp_surrogate_destroy(fp_surrogate *s) {
     if (!s) return FP_EINVAL;
     cudaDeviceSynchronize();
+    for (int l = 0; l < kLayers; ++l) cudaFree(s->d_a[l]);
+    cudaFree(s->d_out); cudaFree(s->d_g0); cudaFree(s->d_g1); cudaFree(s->d_partial);
     for (void *p : s->allocs) cudaFree(p);
     delete s;
     return FP_OK;
 }
 
 int fp_surrogate_get_params(fp_surrogate *s, float *dst, size_t n) {
-    if (!s || !dst || n < s->master.size()) return FP_EINVAL;
-    memcpy(dst, s->master.data(), s->master.size() * sizeof(float));
-    return FP_OK;
+    if (!s || !dst || n < s->n_params) return FP_EINVAL;
+    return cudaMemcpy(dst, s->d_master, s->n_params * sizeof(float), cudaMemcpyDefault) == cudaSuccess ? FP_OK
+                                                                                                         : FP_ECUDA;
 }
 
 int fp_surrogate_set_params(fp_surrogate *s, const float *src, size_t n) {
-    if (!s || !src || n < s->master.size()) return FP_EINVAL;
-    memcpy(s->master.data(), src, s->master.size() * sizeof(float));
-    return upload_packed(s) == cudaSuccess ? FP_OK : FP_ECUDA;
+    if (!s || !src || n < s->n_params) return FP_EINVAL;
+    cudaError_t e = cudaMemcpy(s->d_master, src, s->n_params * sizeof(float), cudaMemcpyDefault);
+    if (e == cudaSuccess) e = repack(s, 0);
+    return check_err(s, e, "fp_surrogate_set_params");
 }
 
-// x: device FP32 [B][H][W][4]; y: device FP32 [B][H-10][W-10][3] (delta U); H, W >= 11.
-// Scratch activations are allocated per call (internal use: tests and training).
 int fp_surrogate_forward(fp_surrogate *s, const float *x, int32_t B, int32_t H, int32_t W, float *y) {
     if (!s || !x || !y || B < 1 || H < 11 || W < 11) return FP_EINVAL;
-    const size_t npix0 = (size_t)B * H * W;
-    __nv_bfloat16 *a0 = nullptr, *a1 = nullptr, *a2 = nullptr;
-    cudaError_t e = cudaMalloc(&a0, npix0 * kCin0 * sizeof(__nv_bfloat16));
-    if (e == cudaSuccess) e = cudaMalloc(&a1, npix0 * kWidth * sizeof(__nv_bfloat16));
-    if (e == cudaSuccess) e = cudaMalloc(&a2, npix0 * kWidth * sizeof(__nv_bfloat16));
-    if (e != cudaSuccess) {
-        cudaFree(a0); cudaFree(a1); cudaFree(a2);
+    if (!ensure_scratch(s, (size_t)B * H * W)) {
         fp_note_error("fp_surrogate_forward: allocation failed");
         return FP_ENOMEM;
     }
-    cudaStream_t st = 0;
-    pack_input_kernel<<<(unsigned)((npix0 + 255) / 256), 256, 0, st>>>(x, npix0, a0);
-    int h = H, w = W;
-    e = launch_conv<kCin0, kWidth, false>(s, 0, a0, B, h, w, a1, st);
-    h -= 2; w -= 2;
-    __nv_bfloat16 *src = a1, *dst = a2;
-    for (int l = 1; l < kLayers - 1 && e == cudaSuccess; ++l) {
-        e = launch_conv<kWidth, kWidth, false>(s, l, src, B, h, w, dst, st);
-        h -= 2; w -= 2;
-        std::swap(src, dst);
+    return check_err(s, forward_keep(s, x, B, H, W, y, 0), "fp_surrogate_forward");
+}
+
+int fp_surrogate_gradients(fp_surrogate *s, const float *x, const float *target, int32_t B, int32_t H, int32_t W,
+                           float *grads, double *loss) {
+    if (!s || !x || !target || B < 1 || H < 11 || W < 11) return FP_EINVAL;
+    if (!ensure_scratch(s, (size_t)B * H * W)) {
+        fp_note_error("fp_surrogate_gradients: allocation failed");
+        return FP_ENOMEM;
     }
-    if (e == cudaSuccess) e = launch_conv<kWidth, kCout4, true>(s, kLayers - 1, src, B, h, w, y, st);
-    if (e == cudaSuccess) e = cudaDeviceSynchronize();
-    unsigned herr = 0;
-    cudaMemcpy(&herr, s->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost);
-    cudaFree(a0); cudaFree(a1); cudaFree(a2);
-    if (e != cudaSuccess) {
-        fp_note_error(cudaGetErrorString(e));
+    cudaError_t e = forward_keep(s, x, B, H, W, s->d_out, 0);
+    if (e == cudaSuccess) e = backward(s, target, B, H, W, 0);
+    int rc = check_err(s, e, "fp_surrogate_gradients");
+    if (rc != FP_OK) return rc;
+    if (grads && cudaMemcpy(grads, s->d_grad, s->n_params * sizeof(float), cudaMemcpyDefault) != cudaSuccess)
         return FP_ECUDA;
-    }
-    if (herr & FP_ERR_TIMEOUT) {
-        fp_note_error("fp_surrogate_forward: tensor-core completion wait timed out");
-        return FP_ETIMEOUT;
-    }
+    if (loss && cudaMemcpy(loss, s->d_loss, sizeof(double), cudaMemcpyDefault) != cudaSuccess) return FP_ECUDA;
     return FP_OK;
+}
+
+int fp_surrogate_train_step(fp_surrogate *s, const float *x, const float *target, int32_t B, int32_t H, int32_t W,
+                            float lr, double *loss) {
+    int rc = fp_surrogate_gradients(s, x, target, B, H, W, nullptr, loss);
+    if (rc != FP_OK) return rc;
+    s->adam_t += 1;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.0f / (1.0f - std::pow(b1, (float)s->adam_t));
+    const float c2 = 1.0f / (1.0f - std::pow(b2, (float)s->adam_t));
+    const int n = (int)s->n_params;
+    adam_kernel<<<(n + 255) / 256, 256>>>(s->d_master, s->d_grad, s->d_m, s->d_v, n, lr, b1, b2, 1e-8f, c1, c2);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = repack(s, 0);
+    return check_err(s, e, "fp_surrogate_train_step");
 }
 
 }  // extern "C"

@@ -125,6 +125,8 @@ typedef struct fp_counters {
     int32_t wet;            /* 1 once any cell held >= 1 mm of water */
     uint32_t error_flags;   /* device-side error bits (0 = none) */
     int64_t ped_updates;    /* pedestrians advanced, summed over steps */
+    int64_t cfl_exceeded;   /* fixed-dt steps whose Courant number exceeded cfg.cfl
+                               (see fp_set_fixed_dt; 0 in CFL mode) */
 } fp_counters;
 
 typedef struct fp_sim fp_sim; /* opaque handle, owned by the library */
@@ -190,6 +192,15 @@ int fp_set_tuning(fp_sim *sim, int32_t tile_rows, int32_t ped_lanes);
 #define FP_MODE_PERSISTENT 1
 int fp_set_step_mode(fp_sim *sim, int32_t mode);
 
+/* Fixed time step (build-added; the paper's step is the CFL step of Section 3):
+ * dt_seconds > 0 makes every later step dt_seconds long (rounded to the
+ * 2^-20 s tick, at least one tick, at most 1 s; the last step before t_end is
+ * shortened to end on it).  Steps whose Courant number max(|u|,|v|)+sqrt(g h)
+ * times dt / dx exceeds cfg.cfl are counted in fp_counters.cfl_exceeded; the
+ * step is taken all the same.  dt_seconds = 0 returns to the CFL step.  The
+ * learned surrogate runs on a fixed step. */
+int fp_set_fixed_dt(fp_sim *sim, double dt_seconds);
+
 /* Profiling mode (on != 0): fp_step synchronises at its end and accumulates
  * the time of the parts of each step -- per-step kernels: launched directly
  * (no CUDA graph) with CUDA events around the kernel groups; persistent
@@ -246,6 +257,52 @@ int fp_surrogate_gradients(fp_surrogate *sur, const float *x, const float *targe
 /* One Adam step (beta1 0.9, beta2 0.999) of learning rate lr on that loss. */
 int fp_surrogate_train_step(fp_surrogate *sur, const float *x, const float *target, int32_t B, int32_t H, int32_t W,
                             float lr, double *loss);
+
+/* Advance a simulation by n_windows windows of FP_SUR_WINDOW fixed steps with
+ * the surrogate standing in for the flood update (requires fp_set_fixed_dt;
+ * kernel step mode is used whatever fp_set_step_mode says).  One window:
+ *   1. tiles of FP_SUR_TILE x FP_SUR_TILE cells whose region grown by
+ *      FP_SUR_WINDOW cells holds no water (h = 0, no inflow over the window)
+ *      are dry: the plain update leaves them unchanged, so they are skipped;
+ *   2. every other tile, with a FP_SUR_HALO-cell halo (cells past the domain
+ *      edge repeat the edge cell), goes through the net: U' = U + dU, h' >= 0,
+ *      no velocity where h' <= 1e-6 m;
+ *   3. the pedestrians take the window's steps on the state at its start
+ *      (coupled steps whose flood update moves no water), sandbag layers
+ *      raising the bed as they complete;
+ *   4. guard per tile: |change of tile water volume - inflow through the tile
+ *      edges| / max(tile volume, 1 cm x tile area) <= guard->mass_tol, where
+ *      the inflow is the window length times the mean of the HLL mass fluxes
+ *      of the start and end states; U' finite; Courant number of U' <= cfg.cfl;
+ *   5. a failed tile is recomputed by the plain update from the window's start
+ *      state over the tile grown by FP_SUR_WINDOW cells (cells outside held at
+ *      their start values), with the evacuee roughness of the window's end;
+ *   6. every guard->check_every windows (0: never) the whole grid is recomputed
+ *      by the plain update and the largest depth difference recorded; when it
+ *      exceeds guard->check_tol (m), the next guard->suspend_windows windows
+ *      run the plain update on every tile.
+ * Stops before a window that would cross t_end.  *stats accumulates (zero it
+ * before the first call).  Synchronises the stream. */
+#define FP_SUR_TILE 256
+typedef struct fp_surrogate_guard {
+    float mass_tol;           /* 1e-4 */
+    float check_tol;          /* 0.01 m */
+    int32_t check_every;      /* 8 windows = 64 steps */
+    int32_t suspend_windows;  /* 8 */
+} fp_surrogate_guard;
+typedef struct fp_surrogate_stats {
+    int64_t windows;          /* windows advanced */
+    int64_t tiles;            /* tile-windows in total */
+    int64_t tiles_net;        /* tile-windows given to the net */
+    int64_t tiles_fallback;   /* net tiles the guard sent to the plain update */
+    int64_t tiles_plain;      /* tile-windows of check and suspended windows */
+    int64_t checks;           /* plain checks */
+    int64_t checks_failed;    /* checks over check_tol */
+    double max_residual;      /* largest guard mass residual of a net tile */
+    double max_check_error;   /* largest depth difference at a check (m) */
+} fp_surrogate_stats;
+int fp_surrogate_advance(fp_sim *sim, fp_surrogate *sur, int32_t n_windows, const fp_surrogate_guard *guard,
+                         fp_surrogate_stats *stats);
 
 /* Wait for enqueued work; returns FP_ETIMEOUT / FP_EOVERFLOW / FP_ENAN when the
  * device raised the corresponding error bit. */

@@ -86,7 +86,7 @@ class _Params(ctypes.Structure):
         ("n_depot", ctypes.c_int32), ("depot_cells", _P),
         ("n_barrier", ctypes.c_int32), ("barrier_cells", _P),
         ("n_layers", ctypes.c_int32), ("coupling", ctypes.c_int32), ("evac_trigger", ctypes.c_int32),
-        ("seed", ctypes.c_uint64), ("ped_noise", ctypes.c_double),
+        ("seed", ctypes.c_uint64), ("ped_noise", ctypes.c_double), ("dt_fixed_ticks", ctypes.c_int64),
     ]
 
 
@@ -152,6 +152,7 @@ class Oracle:
         P.n_layers, P.coupling, P.evac_trigger = int(sc.n_layers), int(sc.coupling), int(sc.evac_trigger)
         P.seed = int(sc.seed) & ((1 << 64) - 1)
         P.ped_noise = _f32(sc.ped_noise)
+        P.dt_fixed_ticks = int(getattr(sc, "dt_fixed_ticks", 0))
         self.P = P
         n = nx * ny
         self.h = keep(np.asarray(sc.h, np.float64).reshape(-1).copy())

@@ -100,6 +100,7 @@ typedef struct {
     int32_t coupling, evac_trigger;
     uint64_t seed;
     double ped_noise;
+    int64_t dt_fixed_ticks;   /* > 0: fixed step (a build-added mode), else the CFL step */
 } or_params;
 
 typedef struct {
@@ -231,6 +232,11 @@ static int or_has_inflow(const or_params *P) {
 /* ------------------------------------------------------------------------ */
 int64_t or_dt_ticks(const or_params *P, const double *h, const double *hu, const double *hv,
                     int64_t t_ticks) {
+    if (P->dt_fixed_ticks > 0) {
+        int64_t left = P->t_end_ticks - t_ticks;
+        if (left < 0) left = 0;
+        return P->dt_fixed_ticks < left ? P->dt_fixed_ticks : left;
+    }
     const float g = (float)P->g;
     const float heps = (float)OR_H_EPS;
     float smax = 0.0f;

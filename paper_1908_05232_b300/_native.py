@@ -39,7 +39,22 @@ class FpCounters(ctypes.Structure):
     _fields_ = [("t_ticks", ctypes.c_int64), ("step", ctypes.c_int64), ("n_active", ctypes.c_int64),
                 ("n_exited", ctypes.c_int64), ("total_bags", ctypes.c_int64), ("applied_layers", ctypes.c_int64),
                 ("neg_depth", ctypes.c_int64), ("hist", ctypes.c_int64 * 5), ("wet", ctypes.c_int32),
-                ("error_flags", ctypes.c_uint32), ("ped_updates", ctypes.c_int64)]
+                ("error_flags", ctypes.c_uint32), ("ped_updates", ctypes.c_int64), ("cfl_exceeded", ctypes.c_int64)]
+
+
+class SurGuard(ctypes.Structure):
+    _fields_ = [("mass_tol", ctypes.c_float), ("check_tol", ctypes.c_float), ("check_every", ctypes.c_int32),
+                ("suspend_windows", ctypes.c_int32)]
+
+
+class SurStats(ctypes.Structure):
+    _fields_ = [("windows", ctypes.c_int64), ("tiles", ctypes.c_int64), ("tiles_net", ctypes.c_int64),
+                ("tiles_fallback", ctypes.c_int64), ("tiles_plain", ctypes.c_int64), ("checks", ctypes.c_int64),
+                ("checks_failed", ctypes.c_int64), ("max_residual", ctypes.c_double),
+                ("max_check_error", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class FloodPedError(RuntimeError):
@@ -70,6 +85,7 @@ def lib():
             "fp_batch_create": [_VP, ctypes.c_int32, _VP], "fp_batch_step": [_VP, ctypes.c_int32],
             "fp_batch_synchronize": [_VP], "fp_batch_destroy": [_VP], "fp_set_profiling": [_VP, ctypes.c_int32],
             "fp_read_state": [_VP, ctypes.c_int32, _VP, ctypes.c_size_t], "fp_destroy": [_VP],
+            "fp_set_fixed_dt": [_VP, ctypes.c_double], "fp_surrogate_advance": [_VP, _VP, ctypes.c_int32, _VP, _VP],
         }
         for name, args in sigs.items():
             f = getattr(L, name)
@@ -255,7 +271,20 @@ class Simulation:
         _check(lib().fp_read_state(self.h, FP_FIELD_COUNTERS, ctypes.byref(c), ctypes.sizeof(c)), self.h)
         return dict(t_ticks=c.t_ticks, step=c.step, n_active=c.n_active, n_exited=c.n_exited,
                     total_bags=c.total_bags, applied_layers=c.applied_layers, neg_depth=c.neg_depth,
-                    hist=list(c.hist), wet=c.wet, error_flags=c.error_flags, ped_updates=c.ped_updates)
+                    hist=list(c.hist), wet=c.wet, error_flags=c.error_flags, ped_updates=c.ped_updates,
+                    cfl_exceeded=c.cfl_exceeded)
+
+    def set_fixed_dt(self, dt_seconds):
+        _check(lib().fp_set_fixed_dt(self.h, float(dt_seconds)), self.h)
+
+    def surrogate_advance(self, sur, n_windows, mass_tol=1e-4, check_tol=0.01, check_every=8, suspend_windows=8,
+                          stats=None):
+        """n_windows windows of 8 fixed steps with the surrogate for the flood update;
+        returns the accumulated SurStats (pass it back in to keep accumulating)."""
+        g = SurGuard(float(mass_tol), float(check_tol), int(check_every), int(suspend_windows))
+        st = stats if stats is not None else SurStats()
+        _check(lib().fp_surrogate_advance(self.h, sur.h, int(n_windows), ctypes.byref(g), ctypes.byref(st)), self.h)
+        return st
 
     def profile(self) -> dict:
         out = np.zeros(5, np.float64)
@@ -326,6 +355,8 @@ def from_scenario(sc, max_peds=None, tile_rows=0, peds=True, mode=None) -> Simul
         fp_set_time(sim.h, sc.t0_ticks, sc.step0)
     if getattr(sc, "bags0", 0) or getattr(sc, "applied0", 0):
         fp_set_barrier_progress(sim.h, sc.bags0, sc.applied0)
+    if getattr(sc, "dt_fixed_ticks", 0):
+        sim.set_fixed_dt(sc.dt_fixed_ticks / TICKS)
     if peds and sc.n_peds:
         sim.add_pedestrians(ped_records(sc.peds))
     return sim

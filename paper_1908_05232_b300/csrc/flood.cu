@@ -32,6 +32,7 @@ __global__ void __launch_bounds__(32 * TY) flood_kernel(const __grid_constant__ 
                                                         const __grid_constant__ FpSim S, int par, int slot) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) unsigned long long mbar;
+    if (S.tile_mask != nullptr && S.tile_mask[blockIdx.y * gridDim.x + blockIdx.x] == 0) return;
     if (threadIdx.x == 0) mbar_init(&mbar);
     __syncthreads();
     flood_tile<TY>(tm, S, par, slot, blockIdx.x, blockIdx.y, smem_raw, &mbar, 0u);

@@ -161,6 +161,11 @@ __device__ __forceinline__ bool flood_tile(const FpTmaSet &tm, const FpSim &S, i
         const FpClock c = S.clock[slot];
         const long long dt = fp_dt_ticks(S, c, c.h_in);
         const float dtf = (float)dt * (1.0f / FP_TICKS_F);
+        if (S.dt_fixed > 0 && bx == 0 && by == 0) {
+            float smax = __uint_as_float(c.smax_bits);
+            if (S.has_inflow && c.h_in > FP_H_EPS_F) smax = fmaxf(smax, __fsqrt_rn(__fmul_rn(S.g, c.h_in)));
+            if (__fmul_rn(smax, dtf) > __fmul_rn(S.cfl, S.dx)) atomicAdd(&S.cnt->cfl_over, 1u);
+        }
         s_hin = c.h_in;
         s_dt = dt;
         s_dtf = dtf;

@@ -112,6 +112,25 @@ struct fp_sim {
     int persist_ctas = 0, persist_smem = 0;
     unsigned *grid_bar = nullptr;
     std::vector<cudaEvent_t> prof_ev;  // 4 per profiled step
+    // surrogate window buffers (allocated by the first fp_surrogate_advance)
+    struct Window {
+        bool ready = false;
+        int tiles_x = 0, tiles_y = 0, ftiles = 0;
+        float *u0[3] = {};                  // start state h, hu, hv (padded planes)
+        float *fb[2][3] = {};               // plain fallback state by parity
+        unsigned short *fb_occ = nullptr;   // evacuees per cell for the fallback
+        FpClock *clock = nullptr;           // fallback clock ring; the start clock at the window's slot
+        double *bflux = nullptr;            // fallback boundary volumes (discarded)
+        unsigned char *wet = nullptr, *fail = nullptr, *flag = nullptr, *mask = nullptr;
+        int *list = nullptr, *batch_of = nullptr, *count = nullptr;  // count[0] net tiles, count[1] failed
+        float *resid = nullptr;
+        unsigned *maxdiff = nullptr;
+        void *x16 = nullptr;                // net input [tiles][266][266][16] BF16
+        float *dU = nullptr;                // net output [tiles][256][256][3]
+        FpTmaSet tma[2];
+        long long done = 0;                 // windows advanced (check cadence)
+        int suspend = 0;                    // windows left on the plain update
+    } win;
     double prof[5] = {0, 0, 0, 0, 0};  // steps, hash ms, flood ms, pedestrian chain ms, step ms
 
     // Every copy of the library is stream-ordered on the simulation's stream and
@@ -145,10 +164,10 @@ struct fp_sim {
     size_t plane_elems() const { return (size_t)S.px * (size_t)(S.ny + 2); }
 };
 
-static int encode_tma_rows(fp_sim *s, int rows, FpTmaSet out[2]) {
+static int encode_tma_rows(fp_sim *s, int rows, FpTmaSet out[2], const FpSim *planes = nullptr) {
     auto enc = get_encode();
     if (!enc) return s->fail(FP_ECUDA, "cuTensorMapEncodeTiled entry point unavailable");
-    const FpSim &S = s->S;
+    const FpSim &S = planes ? *planes : s->S;
     cuuint64_t dims[2] = {(cuuint64_t)S.px, (cuuint64_t)(S.ny + 2)};
     cuuint64_t strides[1] = {(cuuint64_t)S.px * 4};
     cuuint32_t box[2] = {(cuuint32_t)(FP_TX + 8), (cuuint32_t)(rows + 2)};
@@ -253,6 +272,67 @@ static void launch_step(fp_sim *s, int par, int slot, cudaEvent_t *ev = nullptr)
     if (ev) cudaEventRecord(ev[3], s->stream2);
     cudaEventRecord(s->ev_join, s->stream2);
     cudaStreamWaitEvent(s->stream, s->ev_join, 0);
+}
+
+// A coupled step whose flood update moves no water (surrogate window): the
+// pedestrian chain as in launch_step; on stream 1 only the clock advance and
+// the clearing of the evacuee counts the flood kernel would have consumed.
+// Both parities of the state must hold the same water state.
+static void launch_window_step(fp_sim *s, int par, int slot) {
+    const FpSim &S = s->S;
+    fp_launch_hash_count(S, par, s->stream);
+    cudaEventRecord(s->ev_fork, s->stream);
+    cudaStreamWaitEvent(s->stream2, s->ev_fork, 0);
+    fp_launch_clock_advance(S, slot, s->stream);
+    cudaMemsetAsync(S.occ[par], 0, s->plane_elems() * sizeof(unsigned short), s->stream);
+    fp_launch_scan(S, s->stream2);
+    fp_launch_gather(S, s->stream2);
+    fp_launch_ped_step(S, par, slot, s->ped_lanes, s->stream2);
+    cudaEventRecord(s->ev_join, s->stream2);
+    cudaStreamWaitEvent(s->stream, s->ev_join, 0);
+}
+
+static int ensure_window(fp_sim *s) {
+    fp_sim::Window &W = s->win;
+    if (W.ready) return FP_OK;
+    const FpSim &S = s->S;
+    W.tiles_x = (S.nx + FP_SUR_TILE - 1) / FP_SUR_TILE;
+    W.tiles_y = (S.ny + FP_SUR_TILE - 1) / FP_SUR_TILE;
+    const int nt = W.tiles_x * W.tiles_y;
+    W.ftiles = ((S.nx + FP_TX - 1) / FP_TX) * ((S.ny + s->tile_rows - 1) / s->tile_rows);
+    const size_t pe = s->plane_elems();
+    const size_t in = (size_t)(FP_SUR_TILE + 2 * FP_SUR_HALO) * (FP_SUR_TILE + 2 * FP_SUR_HALO);
+    bool ok = true;
+    for (int k = 0; k < 3; ++k) {
+        ok &= (W.u0[k] = s->dalloc<float>(pe)) != nullptr;
+        ok &= (W.fb[0][k] = s->dalloc<float>(pe)) != nullptr;
+        ok &= (W.fb[1][k] = s->dalloc<float>(pe)) != nullptr;
+    }
+    ok &= (W.fb_occ = s->dalloc<unsigned short>(pe + 2)) != nullptr;
+    ok &= (W.clock = s->dalloc<FpClock>(4)) != nullptr;
+    ok &= (W.bflux = s->dalloc<double>(2 * (size_t)S.nx + 2 * (size_t)S.ny)) != nullptr;
+    ok &= (W.wet = s->dalloc<unsigned char>(nt)) != nullptr;
+    ok &= (W.fail = s->dalloc<unsigned char>(nt)) != nullptr;
+    ok &= (W.flag = s->dalloc<unsigned char>(nt)) != nullptr;
+    ok &= (W.mask = s->dalloc<unsigned char>(W.ftiles)) != nullptr;
+    ok &= (W.list = s->dalloc<int>(nt)) != nullptr;
+    ok &= (W.batch_of = s->dalloc<int>(nt)) != nullptr;
+    ok &= (W.count = s->dalloc<int>(2)) != nullptr;
+    ok &= (W.resid = s->dalloc<float>(nt)) != nullptr;
+    ok &= (W.maxdiff = s->dalloc<unsigned>(1)) != nullptr;
+    ok &= (W.x16 = s->dalloc<unsigned char>((size_t)nt * in * 32)) != nullptr;
+    ok &= (W.dU = s->dalloc<float>((size_t)nt * FP_SUR_TILE * FP_SUR_TILE * 3)) != nullptr;
+    if (!ok) return s->fail(FP_ENOMEM, "surrogate window buffers");
+    FpSim F = S;
+    for (int p = 0; p < 2; ++p) {
+        F.h[p] = W.fb[p][0];
+        F.hu[p] = W.fb[p][1];
+        F.hv[p] = W.fb[p][2];
+    }
+    const int rc = encode_tma_rows(s, s->tile_rows, W.tma, &F);
+    if (rc != FP_OK) return rc;
+    W.ready = true;
+    return FP_OK;
 }
 
 // Persistent kernel with the global timer stamped by CTA 0 at every phase end.
@@ -706,6 +786,173 @@ int fp_set_step_mode(fp_sim *s, int32_t mode) {
     return FP_OK;
 }
 
+int fp_set_fixed_dt(fp_sim *s, double dt_seconds) {
+    if (!s) return FP_EINVAL;
+    if (!(dt_seconds >= 0.0) || dt_seconds > 1.0) return s->fail(FP_EINVAL, "fixed dt must lie in [0, 1] s");
+    long long ticks = llround(dt_seconds * 1048576.0);
+    if (dt_seconds > 0.0 && ticks < 1) ticks = 1;
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return s->cuda_fail(e, "fixed dt switch");
+    s->S.dt_fixed = ticks;
+    s->drop_graphs();
+    return FP_OK;
+}
+
+int fp_surrogate_advance(fp_sim *s, fp_surrogate *sur, int32_t n_windows, const fp_surrogate_guard *guard,
+                         fp_surrogate_stats *st) {
+    if (!s) return FP_EINVAL;
+    if (!sur || !guard || !st || n_windows < 0) return s->fail(FP_EINVAL, "null surrogate, guard or stats");
+    if (s->S.dt_fixed <= 0) return s->fail(FP_EINVAL, "the surrogate window needs a fixed time step (fp_set_fixed_dt)");
+    if (!(guard->mass_tol >= 0.0f) || !(guard->check_tol >= 0.0f) || guard->check_every < 0 ||
+        guard->suspend_windows < 0)
+        return s->fail(FP_EINVAL, "invalid guard parameters");
+    if (s->need_prepare) {
+        const int rc = prepare(s);
+        if (rc != FP_OK) return rc;
+    }
+    int rc = ensure_window(s);
+    if (rc != FP_OK) return rc;
+    fp_sim::Window &W = s->win;
+    const FpSim &S = s->S;
+    const int nt = W.tiles_x * W.tiles_y;
+    const int kIn = FP_SUR_TILE + 2 * FP_SUR_HALO;
+    const size_t pbytes = s->plane_elems() * sizeof(float);
+    const int ftx = (S.nx + FP_TX - 1) / FP_TX, fty = (S.ny + s->tile_rows - 1) / s->tile_rows;
+    std::vector<unsigned char> flag(nt), fail(nt), mask(W.ftiles);
+    std::vector<int> list(nt);
+    std::vector<float> resid(nt);
+    cudaError_t e = cudaSuccess;
+    for (int w = 0; w < n_windows; ++w) {
+        const int par = s->par, slot = s->slot;
+        FpClock c0;
+        e = s->copy(&c0, &S.clock[slot], sizeof(c0));
+        if (e != cudaSuccess) return s->cuda_fail(e, "window clock");
+        if (c0.t + (long long)FP_SUR_WINDOW * S.dt_fixed > S.t_end) break;
+        const bool check = guard->check_every > 0 && (W.done + 1) % guard->check_every == 0;
+        const bool plain = W.suspend > 0;
+        float *state[3] = {S.h[par], S.hu[par], S.hv[par]};
+        float *other[3] = {S.h[par ^ 1], S.hu[par ^ 1], S.hv[par ^ 1]};
+        for (int k = 0; k < 3; ++k) cudaMemcpyAsync(W.u0[k], state[k], pbytes, cudaMemcpyDeviceToDevice, s->stream);
+        cudaMemsetAsync(W.clock, 0, 4 * sizeof(FpClock), s->stream);
+        cudaMemcpyAsync(&W.clock[slot], &S.clock[slot], sizeof(FpClock), cudaMemcpyDeviceToDevice, s->stream);
+        // 1-2. dry tiles and the net's tiles
+        int count = 0;
+        if (!plain) {
+            fp_launch_sur_classify(S, par, &W.clock[slot], W.tiles_x, W.tiles_y, W.wet, s->stream);
+            fp_launch_sur_compact(W.wet, nt, W.list, W.batch_of, W.count, s->stream);
+            e = s->copy(&count, W.count, sizeof(int));
+            if (e != cudaSuccess) return s->cuda_fail(e, "window tile count");
+            if (count > 0) {
+                fp_launch_sur_input(S, W.u0[0], W.u0[1], W.u0[2], W.list, count, W.tiles_x, W.x16, s->stream);
+                e = fp_sur_forward_packed(sur, W.x16, count, kIn, kIn, W.dU, s->stream);
+                if (e != cudaSuccess) return s->cuda_fail(e, "surrogate forward");
+            }
+        }
+        // 3. pedestrians over the window on the start state
+        for (int k = 0; k < 3; ++k) cudaMemcpyAsync(other[k], W.u0[k], pbytes, cudaMemcpyDeviceToDevice, s->stream);
+        for (int k = 0; k < FP_SUR_WINDOW; ++k) {
+            launch_window_step(s, s->par, s->slot);
+            s->par ^= 1;
+            s->slot = (s->slot + 1) & 3;
+        }
+        // 4. apply the net's change, guard
+        std::fill(flag.begin(), flag.end(), (unsigned char)(plain || check ? 1 : 0));
+        if (count > 0) {
+            cudaMemsetAsync(W.count + 1, 0, sizeof(int), s->stream);
+            fp_launch_sur_apply(S, par, W.u0[0], W.u0[1], W.u0[2], W.dU, W.list, W.batch_of, count, W.tiles_x,
+                                &W.clock[slot], guard->mass_tol, W.fail, W.resid, W.count + 1, s->stream);
+            e = s->copy(fail.data(), W.fail, count);
+            if (e == cudaSuccess) e = s->copy(resid.data(), W.resid, count * sizeof(float));
+            if (e == cudaSuccess) e = s->copy(list.data(), W.list, count * sizeof(int));
+            if (e != cudaSuccess) return s->cuda_fail(e, "window guard");
+            for (int b = 0; b < count; ++b) {
+                st->max_residual = std::max(st->max_residual, (double)resid[b]);
+                if (fail[b]) {
+                    flag[list[b]] = 1;
+                    st->tiles_fallback += 1;
+                }
+            }
+        }
+        st->windows += 1;
+        st->tiles += nt;
+        st->tiles_net += count;
+        if (plain || check) st->tiles_plain += nt;
+        // 5-6. plain update of the flagged tiles (grown by the window) from the start state
+        bool any = false;
+        for (unsigned char f : flag) any |= f != 0;
+        if (any) {
+            const unsigned char *dmask = nullptr;
+            if (!(plain || check)) {
+                std::fill(mask.begin(), mask.end(), (unsigned char)0);
+                for (int t = 0; t < nt; ++t) {
+                    if (!flag[t]) continue;
+                    const int xa = std::max(0, (t % W.tiles_x) * FP_SUR_TILE - FP_SUR_WINDOW);
+                    const int xb = std::min(S.nx, (t % W.tiles_x + 1) * FP_SUR_TILE + FP_SUR_WINDOW);
+                    const int ya = std::max(0, (t / W.tiles_x) * FP_SUR_TILE - FP_SUR_WINDOW);
+                    const int yb = std::min(S.ny, (t / W.tiles_x + 1) * FP_SUR_TILE + FP_SUR_WINDOW);
+                    for (int fy = ya / s->tile_rows; fy <= (yb - 1) / s->tile_rows && fy < fty; ++fy)
+                        for (int fx = xa / FP_TX; fx <= (xb - 1) / FP_TX && fx < ftx; ++fx) mask[fy * ftx + fx] = 1;
+                }
+                mask[0] = 1;  // tile (0, 0) advances the fallback clock
+                e = s->copy(W.mask, mask.data(), W.ftiles);
+                if (e != cudaSuccess) return s->cuda_fail(e, "fallback mask");
+                dmask = W.mask;
+            }
+            for (int p = 0; p < 2; ++p)
+                for (int k = 0; k < 3; ++k)
+                    cudaMemcpyAsync(W.fb[p][k], W.u0[k], pbytes, cudaMemcpyDeviceToDevice, s->stream);
+            FpSim F = S;
+            for (int p = 0; p < 2; ++p) {
+                F.h[p] = W.fb[p][0];
+                F.hu[p] = W.fb[p][1];
+                F.hv[p] = W.fb[p][2];
+                F.occ[p] = W.fb_occ;
+            }
+            F.clock = W.clock;
+            F.bflux = W.bflux;
+            F.tile_mask = dmask;
+            int p = par, sl = slot;
+            for (int k = 0; k < FP_SUR_WINDOW; ++k) {
+                cudaMemsetAsync(W.fb_occ, 0, s->plane_elems() * sizeof(unsigned short), s->stream);
+                if (S.coupling) fp_launch_sur_occupancy(F, W.fb_occ, s->stream);
+                fp_launch_flood(F, &W.tma[p], p, sl, s->tile_rows, s->stream);
+                p ^= 1;
+                sl = (sl + 1) & 3;
+            }
+            if (check) {
+                unsigned bits = 0;
+                cudaMemsetAsync(W.maxdiff, 0, sizeof(unsigned), s->stream);
+                fp_launch_sur_diff(S, S.h[par], W.fb[par][0], W.maxdiff, s->stream);
+                e = s->copy(&bits, W.maxdiff, sizeof(unsigned));
+                if (e != cudaSuccess) return s->cuda_fail(e, "plain check");
+                float err;
+                memcpy(&err, &bits, sizeof(err));
+                st->checks += 1;
+                st->max_check_error = std::max(st->max_check_error, (double)err);
+                if (!(err <= guard->check_tol)) {
+                    st->checks_failed += 1;
+                    W.suspend = guard->suspend_windows + 1;  // this window's decrement below
+                }
+            }
+            e = s->copy(W.flag, flag.data(), nt);
+            if (e != cudaSuccess) return s->cuda_fail(e, "fallback flags");
+            fp_launch_sur_merge(S, par, W.fb[par][0], W.fb[par][1], W.fb[par][2], W.flag, W.tiles_x, W.tiles_y,
+                                s->stream);
+        }
+        // the clock of the window's end takes the wave speed and wet flag of
+        // the new water state (the window's own steps carried the start's)
+        cudaMemsetAsync(&S.clock[s->slot].smax_bits, 0, sizeof(unsigned), s->stream);
+        fp_launch_init_clock(S, s->par, s->slot, s->stream);
+        if (W.suspend > 0) W.suspend -= 1;
+        W.done += 1;
+    }
+    e = cudaStreamSynchronize(s->stream);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return s->cuda_fail(e, "surrogate window");
+    if (fp_sur_error_bits(sur) & FP_ERR_TIMEOUT) return s->fail(FP_ETIMEOUT, "tensor-core completion wait timed out");
+    return fp_synchronize(s);
+}
+
 int fp_set_profiling(fp_sim *s, int32_t on) {
     if (!s) return FP_EINVAL;
     cudaError_t e = cudaStreamSynchronize(s->stream);
@@ -776,6 +1023,7 @@ int fp_read_state(fp_sim *s, int32_t which, void *dst, size_t bytes) {
             o.wet = k.wet;
             o.error_flags = c.err;
             o.ped_updates = (int64_t)c.ped_updates;
+            o.cfl_exceeded = (int64_t)c.cfl_over;
             if (e == cudaSuccess) e = s->copy(dst, &o, sizeof(o));
             break;
         }

@@ -69,7 +69,7 @@ struct FpCounters {
     double mass;                      // last mass reduction (m^3)
     double inflow;                    // net boundary inflow volume (m^3)
     unsigned int mass_done;           // blocks finished in the mass reduction
-    int pad;
+    unsigned int cfl_over;            // fixed-dt steps whose CFL number exceeded the limit
     unsigned long long ped_updates;   // sum over steps with dt > 0 of pedestrians advanced
 };
 
@@ -102,6 +102,8 @@ struct FpSim {
     int *scan_part;            // persistent kernel: bin-count total of each CTA's chunk
     unsigned long long *phase_ts;  // optional: global timer at each persistent-kernel phase end
     int phase_ts_steps;            // steps recorded in phase_ts (4 stamps per step + 1)
+    long long dt_fixed;            // fixed time step in ticks (0: CFL step)
+    const unsigned char *tile_mask;  // per flood tile: 0 = skip (nullptr: every tile runs)
 };
 
 __device__ __forceinline__ size_t fp_pidx(const FpSim &S, int i, int j) {
@@ -132,6 +134,11 @@ __device__ __forceinline__ double fp_hydro_depth(const FpSim &S, long long t_tic
 // max over wet cells of the state it reads and the inflow ghost state.
 // Taken in FP32 with correctly rounded division and square root.
 __device__ __forceinline__ long long fp_dt_ticks(const FpSim &S, const FpClock &c, float h_in) {
+    if (S.dt_fixed > 0) {
+        long long left = S.t_end - c.t;
+        if (left < 0) left = 0;
+        return S.dt_fixed < left ? S.dt_fixed : left;
+    }
     float smax = __uint_as_float(c.smax_bits);
     if (S.has_inflow && h_in > FP_H_EPS_F) {
         const float s = __fsqrt_rn(__fmul_rn(S.g, h_in));
@@ -212,3 +219,22 @@ void fp_launch_flood_batch(const FpSim *d_sims, const FpTmaSet *d_maps, const in
                            int total_tiles, int par, int slot, cudaStream_t st);
 cudaError_t fp_launch_persistent(const FpSim &S, const FpTmaSet tma[2], int par, int slot, int nsteps,
                                  unsigned *bar, int ctas, int smem_dynamic, cudaStream_t st);
+
+// surrogate window (window.cu, surrogate.cu)
+struct fp_surrogate;
+cudaError_t fp_sur_forward_packed(fp_surrogate *sur, const void *x16, int B, int H, int W, float *y, cudaStream_t st);
+unsigned fp_sur_error_bits(fp_surrogate *sur);
+void fp_launch_clock_advance(const FpSim &S, int slot, cudaStream_t st);
+void fp_launch_sur_classify(const FpSim &S, int par, const FpClock *c0, int tiles_x, int tiles_y, unsigned char *wet,
+                            cudaStream_t st);
+void fp_launch_sur_compact(const unsigned char *flags, int n, int *list, int *batch_of, int *count, cudaStream_t st);
+void fp_launch_sur_input(const FpSim &S, const float *h, const float *hu, const float *hv, const int *list, int count,
+                         int tiles_x, void *x16, cudaStream_t st);
+void fp_launch_sur_apply(const FpSim &S, int par, const float *h0, const float *hu0, const float *hv0,
+                         const float *dU, const int *list, const int *batch_of, int count, int tiles_x,
+                         const FpClock *c0, float mass_tol, unsigned char *fail, float *resid, int *n_fail,
+                         cudaStream_t st);
+void fp_launch_sur_occupancy(const FpSim &S, unsigned short *occ, cudaStream_t st);
+void fp_launch_sur_diff(const FpSim &S, const float *a, const float *b, unsigned *max_bits, cudaStream_t st);
+void fp_launch_sur_merge(const FpSim &S, int par, const float *h, const float *hu, const float *hv,
+                         const unsigned char *flags, int tiles_x, int tiles_y, cudaStream_t st);

@@ -481,11 +481,11 @@ bool ensure_scratch(fp_surrogate *s, size_t pix) {
     return ok;
 }
 
-// forward of B images x [B][H][W][4] keeping every layer's input in d_a; output to out
-cudaError_t forward_keep(fp_surrogate *s, const float *x, int B, int H, int W, float *out, cudaStream_t st) {
-    const size_t npix0 = (size_t)B * H * W;
-    pack_input_kernel<<<(unsigned)((npix0 + 255) / 256), 256, 0, st>>>(x, npix0, s->d_a[0]);
-    cudaError_t e = launch_conv<kCin0, kWidth, false>(s, 0, s->d_a[0], B, H, W, s->d_a[1], st);
+// the five layers from a packed BF16 input in0 [B][H][W][16]; every later
+// layer's input stays in d_a; output to out
+cudaError_t forward_layers(fp_surrogate *s, const __nv_bfloat16 *in0, int B, int H, int W, float *out,
+                           cudaStream_t st) {
+    cudaError_t e = launch_conv<kCin0, kWidth, false>(s, 0, in0, B, H, W, s->d_a[1], st);
     int h = H - 2, w = W - 2;
     for (int l = 1; l < kLayers - 1 && e == cudaSuccess; ++l) {
         e = launch_conv<kWidth, kWidth, false>(s, l, s->d_a[l], B, h, w, s->d_a[l + 1], st);
@@ -493,6 +493,13 @@ cudaError_t forward_keep(fp_surrogate *s, const float *x, int B, int H, int W, f
     }
     if (e == cudaSuccess) e = launch_conv<kWidth, kCout4, true>(s, kLayers - 1, s->d_a[kLayers - 1], B, h, w, out, st);
     return e;
+}
+
+// forward of B images x [B][H][W][4] keeping every layer's input in d_a; output to out
+cudaError_t forward_keep(fp_surrogate *s, const float *x, int B, int H, int W, float *out, cudaStream_t st) {
+    const size_t npix0 = (size_t)B * H * W;
+    pack_input_kernel<<<(unsigned)((npix0 + 255) / 256), 256, 0, st>>>(x, npix0, s->d_a[0]);
+    return forward_layers(s, s->d_a[0], B, H, W, out, st);
 }
 
 // loss and gradients (into d_grad, master layout) of the last forward_keep
@@ -540,6 +547,17 @@ int check_err(fp_surrogate *s, cudaError_t e, const char *what) {
 }
 
 }  // namespace
+
+cudaError_t fp_sur_forward_packed(fp_surrogate *s, const void *x16, int B, int H, int W, float *y, cudaStream_t st) {
+    if (!ensure_scratch(s, (size_t)B * H * W)) return cudaErrorMemoryAllocation;
+    return forward_layers(s, static_cast<const __nv_bfloat16 *>(x16), B, H, W, y, st);
+}
+
+unsigned fp_sur_error_bits(fp_surrogate *s) {
+    unsigned herr = 0;
+    cudaMemcpy(&herr, s->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost);
+    return herr;
+}
 
 extern "C" {
 

@@ -70,6 +70,7 @@ class Scenario:
     evac_trigger: int = 0
     ped_noise: float = 0.1
     t0_ticks: int = 0        # simulated time at the start (ticks of 2**-20 s)
+    dt_fixed_ticks: int = 0  # > 0: every step this long (ticks), else the CFL step
     step0: int = 0           # step index at the start (random-generator counter)
     bags0: int = 0           # sandbags already dropped
     applied0: int = 0        # barrier cell-layers already built into z

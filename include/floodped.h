@@ -233,13 +233,18 @@ int fp_batch_destroy(fp_batch *batch);
 
 /* ---- learned surrogate -------------------------------------------------------
  * Build-added (the paper has no surrogate): a 5-layer 3x3 convolutional net
- * 4 -> 32 -> 32 -> 32 -> 32 -> 3 channels, ReLU between layers, mapping
+ * 8 -> 32 -> 32 -> 32 -> 32 -> 3 channels, ReLU between layers, mapping
  * (h, hu, hv, z) over an 11 x 11 neighbourhood to the change of (h, hu, hv) of
  * the centre cell over FP_SUR_WINDOW fixed time steps.  Forward on the tensor
- * cores (tcgen05, BF16 operands, FP32 accumulation); FP32 master parameters,
+ * cores (tcgen05, BF16 operands, FP32 accumulation); the 8 input channels are
+ * the four inputs rounded to BF16 and the BF16-rounded remainders of that
+ * rounding (so the first layer sees them to about 16 bits); FP32 master parameters,
  * layer by layer w[ky][kx][ci][co] then b[co]. */
 #define FP_SUR_WINDOW 8
 #define FP_SUR_HALO 5
+/* The last layer's output times this is the predicted change: changes of
+ * 1e-4 .. 1e-2 over a window are then order-1 outputs of the net. */
+#define FP_SUR_OUT_SCALE (1.0f / 1024.0f)
 typedef struct fp_surrogate fp_surrogate;
 int fp_surrogate_num_params(void);
 int fp_surrogate_create(uint64_t seed, fp_surrogate **out);
@@ -294,7 +299,10 @@ typedef struct fp_surrogate_stats {
     int64_t windows;          /* windows advanced */
     int64_t tiles;            /* tile-windows in total */
     int64_t tiles_net;        /* tile-windows given to the net */
-    int64_t tiles_fallback;   /* net tiles the guard sent to the plain update */
+    int64_t tiles_fallback;   /* net tiles the guard sent to the plain update, of which */
+    int64_t fail_mass;        /*   over the mass bound, */
+    int64_t fail_courant;     /*   over the Courant limit, */
+    int64_t fail_nonfinite;   /*   with a non-finite value (a tile may count under several) */
     int64_t tiles_plain;      /* tile-windows of check and suspended windows */
     int64_t checks;           /* plain checks */
     int64_t checks_failed;    /* checks over check_tol */

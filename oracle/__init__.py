@@ -68,7 +68,7 @@ def lib():
         _lib.or_net_loss_grad.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
-                                          ctypes.c_size_t]
+                                          ctypes.c_size_t, ctypes.c_int]
     return _lib
 
 
@@ -309,8 +309,10 @@ def net_forward(x, ws, bs):
     return h
 
 
-def net_loss_grad(x, ws, bs, target):
-    """Mean squared error of the net output against target and its gradients."""
+def net_loss_grad(x, ws, bs, target, act_bf16=False):
+    """Mean squared error of the net output against target and its gradients.
+    act_bf16: hidden activations stored rounded to BF16, as on the tensor-core
+    path (the same ReLU decisions); False is the plain FP64 net."""
     x = np.ascontiguousarray(x, np.float64)
     H, W, _ = x.shape
     L = len(ws)
@@ -330,5 +332,5 @@ def net_loss_grad(x, ws, bs, target):
     dbp = (P * L)(*[b.ctypes.data for b in dbs])
     tgt = np.ascontiguousarray(target, np.float64)
     loss = lib().or_net_loss_grad(_ptr(x), H, W, L, _ptr(ch), wp, bp, _ptr(tgt), _ptr(acts), dwp, dbp,
-                                  _ptr(scratch), scratch.size)
+                                  _ptr(scratch), scratch.size, 1 if act_bf16 else 0)
     return float(loss), dws, dbs

@@ -741,19 +741,37 @@ void or_conv3x3_backward(const double *x, int H, int W, int Ci, const double *w,
             }
 }
 
+/* v rounded to FP32 and then to the nearest BF16 (8-bit significand, ties to
+ * even), the storage format of the product's hidden activations.             */
+static double or_round_bf16(double v) {
+    float f = (float)v;
+    uint32_t u;
+    memcpy(&u, &f, sizeof(u));
+    if ((u & 0x7f800000u) == 0x7f800000u) return (double)f;
+    u = (u + 0x7fffu + ((u >> 16) & 1u)) & 0xffff0000u;
+    memcpy(&f, &u, sizeof(f));
+    return (double)f;
+}
+
 /* Forward through L layers (channels ch[0..L]); acts receives every layer's
  * output (post-ReLU except the last), laid out one after another.  Returns the
- * final output pointer inside acts. */
+ * final output pointer inside acts.  act_bf16 != 0 stores each hidden layer's
+ * output rounded to BF16 (the tensor-core path keeps activations in BF16), so
+ * that comparisons with it see the same ReLU decisions; 0 is the plain FP64
+ * net. */
 double *or_net_forward(const double *x, int H, int W, int L, const int *ch, const double *const *ws,
-                       const double *const *bs, double *acts) {
+                       const double *const *bs, double *acts, int act_bf16) {
     const double *in = x;
     double *out = acts;
     int h = H, w = W;
     for (int l = 0; l < L; ++l) {
         or_conv3x3(in, h, w, ch[l], ws[l], bs[l], ch[l + 1], out, l + 1 < L);
+        const size_t n = (size_t)(h - 2) * (w - 2) * ch[l + 1];
+        if (act_bf16 && l + 1 < L)
+            for (size_t k = 0; k < n; ++k) out[k] = or_round_bf16(out[k]);
         in = out;
         h -= 2; w -= 2;
-        out += (size_t)h * w * ch[l + 1];
+        out += n;
     }
     return (double *)in;
 }
@@ -762,7 +780,7 @@ double *or_net_forward(const double *x, int H, int W, int L, const int *ch, cons
  * (zeroed first) with its gradients.  scratch holds 2 x the largest activation. */
 double or_net_loss_grad(const double *x, int H, int W, int L, const int *ch, const double *const *ws,
                         const double *const *bs, const double *target, double *acts, double *const *dws,
-                        double *const *dbs, double *scratch, size_t scratch_len) {
+                        double *const *dbs, double *scratch, size_t scratch_len, int act_bf16) {
     size_t off[16];
     int hs[17], wsz[17];
     hs[0] = H; wsz[0] = W;
@@ -772,7 +790,7 @@ double or_net_loss_grad(const double *x, int H, int W, int L, const int *ch, con
         hs[l + 1] = hs[l] - 2; wsz[l + 1] = wsz[l] - 2;
         o += (size_t)hs[l + 1] * wsz[l + 1] * ch[l + 1];
     }
-    const double *out = or_net_forward(x, H, W, L, ch, ws, bs, acts);
+    const double *out = or_net_forward(x, H, W, L, ch, ws, bs, acts, act_bf16);
     const size_t n_out = (size_t)hs[L] * wsz[L] * ch[L];
     double loss = 0.0;
     double *g = scratch, *g2 = scratch + scratch_len / 2;

@@ -49,7 +49,8 @@ class SurGuard(ctypes.Structure):
 
 class SurStats(ctypes.Structure):
     _fields_ = [("windows", ctypes.c_int64), ("tiles", ctypes.c_int64), ("tiles_net", ctypes.c_int64),
-                ("tiles_fallback", ctypes.c_int64), ("tiles_plain", ctypes.c_int64), ("checks", ctypes.c_int64),
+                ("tiles_fallback", ctypes.c_int64), ("fail_mass", ctypes.c_int64), ("fail_courant", ctypes.c_int64),
+                ("fail_nonfinite", ctypes.c_int64), ("tiles_plain", ctypes.c_int64), ("checks", ctypes.c_int64),
                 ("checks_failed", ctypes.c_int64), ("max_residual", ctypes.c_double),
                 ("max_check_error", ctypes.c_double)]
 
@@ -365,7 +366,7 @@ def from_scenario(sc, max_peds=None, tile_rows=0, peds=True, mode=None) -> Simul
 class Surrogate:
     """The learned flood surrogate (tcgen05 forward); parameters as FP32 numpy."""
 
-    CH = (4, 32, 32, 32, 32, 3)
+    CH = (8, 32, 32, 32, 32, 3)  # input: (h, hu, hv, z) as BF16 values, then their BF16 remainders
 
     def __init__(self, seed=0):
         self.h = _VP()

@@ -870,6 +870,9 @@ int fp_surrogate_advance(fp_sim *s, fp_surrogate *sur, int32_t n_windows, const 
                 if (fail[b]) {
                     flag[list[b]] = 1;
                     st->tiles_fallback += 1;
+                    st->fail_mass += fail[b] & 1;
+                    st->fail_courant += (fail[b] >> 1) & 1;
+                    st->fail_nonfinite += (fail[b] >> 2) & 1;
                 }
             }
         }

@@ -15,6 +15,7 @@
 //   - a 4-slot clock ring: slot s holds the time, step index, max wave speed
 //     and wet flag of the step that reads it.
 #pragma once
+#include <cuda_bf16.h>
 #include <stdint.h>
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -222,6 +223,23 @@ cudaError_t fp_launch_persistent(const FpSim &S, const FpTmaSet tma[2], int par,
 
 // surrogate window (window.cu, surrogate.cu)
 struct fp_surrogate;
+
+// One pixel of the net's input: 16 BF16 channels, (a, b, c, d) rounded, then
+// their rounded remainders, then 8 zeros (32 bytes, 16-byte aligned).
+__device__ __forceinline__ void fp_sur_pack_pixel(float a, float b, float c, float d, void *dst16) {
+    const __nv_bfloat162 h0 = __floats2bfloat162_rn(a, b), h1 = __floats2bfloat162_rn(c, d);
+    const __nv_bfloat162 l0 = __floats2bfloat162_rn(a - __low2float(h0), b - __high2float(h0));
+    const __nv_bfloat162 l1 = __floats2bfloat162_rn(c - __low2float(h1), d - __high2float(h1));
+    uint4 w0, w1;
+    w0.x = *reinterpret_cast<const unsigned *>(&h0);
+    w0.y = *reinterpret_cast<const unsigned *>(&h1);
+    w0.z = *reinterpret_cast<const unsigned *>(&l0);
+    w0.w = *reinterpret_cast<const unsigned *>(&l1);
+    w1 = make_uint4(0u, 0u, 0u, 0u);
+    uint4 *o = static_cast<uint4 *>(dst16);
+    o[0] = w0;
+    o[1] = w1;
+}
 cudaError_t fp_sur_forward_packed(fp_surrogate *sur, const void *x16, int B, int H, int W, float *y, cudaStream_t st);
 unsigned fp_sur_error_bits(fp_surrogate *sur);
 void fp_launch_clock_advance(const FpSim &S, int slot, cudaStream_t st);

@@ -1,7 +1,8 @@
 // surrogate.cu -- the learned flood surrogate (build-added; the paper has no
-// surrogate): a 5-layer 3x3 convolutional net 4 -> 32 -> 32 -> 32 -> 32 -> 3
+// surrogate): a 5-layer 3x3 convolutional net 8 -> 32 -> 32 -> 32 -> 32 -> 3
 // (ReLU between layers) mapping (h, hu, hv, z) around a cell to the change of
-// (h, hu, hv) over 8 fixed time steps.
+// (h, hu, hv) over 8 fixed time steps; the 8 input channels are the four inputs
+// rounded to BF16 and the rounded remainders.
 //
 // Forward (inference and training): each layer is an implicit GEMM on the
 // 5th-generation tensor cores -- tcgen05.mma, kind::f16 with BF16 operands in
@@ -38,12 +39,15 @@ namespace {
 
 constexpr int kLayers = 5;
 constexpr int kWidth = 32;
-constexpr int kCin0 = 16;   // first layer: 4 real input channels padded to 16
+constexpr int kCin0 = 16;   // first layer: 8 real input channels padded to 16
 constexpr int kCout4 = 16;  // last layer: 3 real output channels padded to 16
 constexpr int kSeg = 128;   // output pixels per MMA (M)
 constexpr int kConvThreads = 128;
-constexpr float kOutScale = 0.1f;  // the net predicts delta U / 0.1
-constexpr int kCh[kLayers + 1] = {4, kWidth, kWidth, kWidth, kWidth, 3};
+constexpr float kOutScale = FP_SUR_OUT_SCALE;  // the net predicts delta U / 2^-10
+// The first layer sees each of (h, hu, hv, z) as two BF16 numbers, the rounded
+// value and the rounded remainder (channels 0-3 and 4-7): its FP32 accumulation
+// then resolves free-surface differences far below one BF16 step of z.
+constexpr int kCh[kLayers + 1] = {8, kWidth, kWidth, kWidth, kWidth, 3};
 
 __device__ __forceinline__ unsigned sm_addr(const void *p) {
     return static_cast<unsigned>(__cvta_generic_to_shared(p));
@@ -238,26 +242,20 @@ __global__ void __launch_bounds__(kConvThreads) conv3x3_tc_kernel(const __nv_bfl
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(taddr));
 }
 
-// FP32 (h, hu, hv, z) images -> BF16 NHWC with 16 channels (4 used)
+// FP32 (h, hu, hv, z) images -> BF16 NHWC with 16 channels: 0-3 the rounded
+// values, 4-7 the rounded remainders, 8-15 zero
 __global__ void pack_input_kernel(const float *__restrict__ x4, size_t npix, __nv_bfloat16 *__restrict__ out) {
     const size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     if (p >= npix) return;
     const float4 v = reinterpret_cast<const float4 *>(x4)[p];
-    __nv_bfloat162 o[8];
-    o[0] = __floats2bfloat162_rn(v.x, v.y);
-    o[1] = __floats2bfloat162_rn(v.z, v.w);
-#pragma unroll
-    for (int k = 2; k < 8; ++k) o[k] = __floats2bfloat162_rn(0.f, 0.f);
-    uint4 *dst = reinterpret_cast<uint4 *>(out + p * 16);
-    dst[0] = reinterpret_cast<const uint4 *>(o)[0];
-    dst[1] = reinterpret_cast<const uint4 *>(o)[1];
+    fp_sur_pack_pixel(v.x, v.y, v.z, v.w, out + p * 16);
 }
 
 
 // ---- training (A13): FP32 backward on the CUDA cores --------------------------
 
-// g = d loss / d (last layer pre-activation): loss = mean (0.1 * z - t)^2 over
-// B x Ho x Wo x 3, so dz = 0.2 (0.1 z - t) / n = 0.2 (y - t) / n with y the
+// g = d loss / d (last layer pre-activation): loss = mean (s z - t)^2 over
+// B x Ho x Wo x 3 with s = kOutScale, so dz = 2 s (s z - t) / n = 2 s (y - t) / n with y the
 // scaled output.  Per-block FP64 partial losses, summed in block order later.
 __global__ void loss_grad_kernel(const float *__restrict__ y, const float *__restrict__ t, size_t n,
                                  float *__restrict__ g, double *__restrict__ partial) {
@@ -343,7 +341,8 @@ __global__ void __launch_bounds__(256) conv_bwd_weight_kernel(const __nv_bfloat1
 
 // dX[q][ci] = sum_{t, co} dY[q - off_t][co] W[t][ci][co] over valid output
 // positions, masked by the ReLU of X (the previous layer's output): the
-// gradient of the previous layer's pre-activation.  One thread per (q, ci).
+// gradient of the previous layer's pre-activation.  W is taken rounded to BF16,
+// the weights the forward multiplied by.  One thread per (q, ci).
 template <int CIN, int COUT>
 __global__ void conv_bwd_data_kernel(const float *__restrict__ dY, const float *__restrict__ w,
                                      const __nv_bfloat16 *__restrict__ X, int B, int H, int W,
@@ -368,7 +367,8 @@ __global__ void conv_bwd_data_kernel(const float *__restrict__ dY, const float *
                 const float *g = dY + (((size_t)b * Ho + oy) * Wo + ox) * COUT;
                 const float *wr = w + ((size_t)(ky * 3 + kx) * CIN + ci) * COUT;
 #pragma unroll 8
-                for (int co = 0; co < COUT; ++co) acc = fmaf(g[co], wr[co], acc);
+                for (int co = 0; co < COUT; ++co)
+                    acc = fmaf(g[co], __bfloat162float(__float2bfloat16(wr[co])), acc);
             }
         }
     }

@@ -108,8 +108,9 @@ __global__ void __launch_bounds__(1024) compact_kernel(const unsigned char *flag
     if (threadIdx.x == 0) *count = s_base;
 }
 
-// Net input: per listed tile a kIn x kIn image of (h, hu, hv, z) in BF16, 16
-// channels (12 zero), cells past the domain edge repeating the edge cell.
+// Net input: per listed tile a kIn x kIn image of (h, hu, hv, z) as BF16 values
+// and remainders (fp_sur_pack_pixel), cells past the domain edge repeating the
+// edge cell.
 __global__ void input_kernel(const __grid_constant__ FpSim S, const float *__restrict__ h,
                              const float *__restrict__ hu, const float *__restrict__ hv, const int *__restrict__ list,
                              int count, int tiles_x, __nv_bfloat16 *__restrict__ out) {
@@ -123,14 +124,7 @@ __global__ void input_kernel(const __grid_constant__ FpSim S, const float *__res
         const int i = min(max((tile % tiles_x) * kT - kHalo + c, 0), S.nx - 1);
         const int j = min(max((tile / tiles_x) * kT - kHalo + r, 0), S.ny - 1);
         const size_t o = fp_pidx(S, i, j);
-        __nv_bfloat162 v[8];
-        v[0] = __floats2bfloat162_rn(h[o], hu[o]);
-        v[1] = __floats2bfloat162_rn(hv[o], S.z[o]);
-#pragma unroll
-        for (int k = 2; k < 8; ++k) v[k] = __floats2bfloat162_rn(0.0f, 0.0f);
-        uint4 *dst = reinterpret_cast<uint4 *>(out + p * 16);
-        dst[0] = reinterpret_cast<const uint4 *>(v)[0];
-        dst[1] = reinterpret_cast<const uint4 *>(v)[1];
+        fp_sur_pack_pixel(h[o], hu[o], hv[o], S.z[o], out + p * 16);
     }
 }
 
@@ -138,12 +132,14 @@ struct Cell {
     float h, hu, hv;
 };
 
-// U + dU with h >= 0 and no momentum where h <= h_eps
+// U + dU with h >= 0 and no momentum where h < 1 mm (the net's momentum
+// change is not reliable on films thinner than that: a small error there is a
+// large velocity)
 __device__ __forceinline__ Cell updated(Cell u, const float *d) {
     Cell r;
     r.h = u.h + d[0];
     if (r.h < 0.0f) r.h = 0.0f;
-    if (r.h <= FP_H_EPS_F) {
+    if (r.h < FP_H_DRY_F) {
         r.hu = 0.0f;
         r.hv = 0.0f;
     } else {
@@ -293,8 +289,9 @@ __global__ void __launch_bounds__(256) apply_kernel(const __grid_constant__ FpSi
         const double denom = fmax(s[0] * dx * dx, (double)n * dx * dx * 0.01);
         const double rs = fabs(dM - F) / denom;
         const bool cfl_bad = (double)sm * dts > (double)S.cfl * dx;
-        const bool f = bd || cfl_bad || !(rs <= (double)mass_tol);
-        fail[b] = f ? 1 : 0;
+        const bool mass_bad = !(rs <= (double)mass_tol);
+        const bool f = bd || cfl_bad || mass_bad;
+        fail[b] = (unsigned char)((bd ? 4 : 0) | (cfl_bad ? 2 : 0) | (mass_bad ? 1 : 0));
         resid[b] = bd ? __int_as_float(0x7f800000) : (float)rs;
         if (f) atomicAdd(n_fail, 1);
     }

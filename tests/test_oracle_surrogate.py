@@ -65,3 +65,31 @@ def test_loss_gradient_finite_differences(oracle_mod):
         bm[l][k] -= eps
         fd = (oracle_mod.net_loss_grad(x, ws, bp, target)[0] - oracle_mod.net_loss_grad(x, ws, bm, target)[0]) / (2 * eps)
         assert abs(fd - dbs[l][k]) <= 1e-6 * max(1.0, abs(fd))
+
+
+def test_bf16_activation_option_special_cases(oracle_mod):
+    """The option that stores hidden activations in BF16: integer activations
+    below 256 are BF16 numbers and pass unchanged; 1 + 2^-9 lies halfway
+    between the BF16 neighbours 1 and 1 + 2^-7 and rounds to the even one (1);
+    1 + 3 * 2^-9 rounds up to 1 + 2^-8 * 2 = 1 + 2^-7."""
+    delta = np.zeros((3, 3, 1, 1))
+    delta[1, 1, 0, 0] = 1.0
+    ws, bs = [delta, delta], [np.zeros(1), np.zeros(1)]
+    for v, want in ((37.0, 37.0), (1.0 + 2.0 ** -9, 1.0), (1.0 + 3 * 2.0 ** -9, 1.0 + 2.0 ** -7),
+                    (-5.0, 0.0)):
+        x = np.full((5, 5, 1), v)
+        t = np.zeros((1, 1, 1))
+        loss_b = oracle_mod.net_loss_grad(x, ws, bs, t, act_bf16=True)[0]
+        loss_p = oracle_mod.net_loss_grad(x, ws, bs, t, act_bf16=False)[0]
+        assert loss_b == want ** 2, (v, loss_b)
+        assert loss_p == max(v, 0.0) ** 2
+    rng = np.random.default_rng(3)
+    ws2 = [rng.integers(-1, 2, (3, 3, 2, 3)).astype(float), rng.integers(-1, 2, (3, 3, 3, 2)).astype(float)]
+    bs2 = [np.zeros(3), np.zeros(2)]
+    x = rng.integers(0, 3, (9, 8, 2)).astype(float)
+    t = rng.normal(size=(5, 4, 2))
+    a = oracle_mod.net_loss_grad(x, ws2, bs2, t, act_bf16=True)
+    b = oracle_mod.net_loss_grad(x, ws2, bs2, t, act_bf16=False)
+    assert a[0] == b[0]
+    for ga, gb in zip(a[1] + a[2], b[1] + b[2]):
+        assert np.array_equal(ga, gb)

@@ -22,6 +22,7 @@ cpu_baseline the FP64 C oracle on a bounded sample of the same workload.
 Multi-GPU (torchrun): every rank runs an independent replica (weak scaling).
 """
 import argparse
+import ctypes
 import hashlib
 import json
 import os
@@ -45,6 +46,11 @@ UNIT = "updates/s"
 def workload(seed):
     import scenarios
     return scenarios.shopping_centre(512, 0.5, 10_000, 0, seed, 1800.0)
+
+
+def scenarios_mod():
+    import scenarios
+    return scenarios
 
 
 def dist_env():
@@ -75,7 +81,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + ",".join(self.FIELDS),
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
@@ -222,6 +228,20 @@ def run_ours(args):
         upd = (b["step"] - a["step"]) * sc.n_cells + (b["ped_updates"] - a["ped_updates"])
         return e0.elapsed_time(e1), upd, b["step"] - a["step"]
 
+    # launch shape: the autotuner's candidates timed on this snapshot (the
+    # results never depend on the shape); --tile-rows pins the flood tile height
+    tuned = {"tile_rows": args.tile_rows or 16, "ped_lanes": 8}
+    if not args.no_tune:
+        best = None
+        for tr in ((args.tile_rows,) if args.tile_rows else (8, 16, 32)):
+            for pl in (4, 8, 16):
+                N.fp_set_tuning(sim.h, tr, pl)
+                t = min(one(False)[0] for _ in range(2))
+                if best is None or t < best[0]:
+                    best = (t, tr, pl)
+        tuned = {"tile_rows": best[1], "ped_lanes": best[2]}
+    N.fp_set_tuning(sim.h, tuned["tile_rows"], tuned["ped_lanes"])
+
     for _ in range(args.warmup):
         one(False)
     if ws > 1:
@@ -288,7 +308,29 @@ def run_ours(args):
     # so it performs the same updates as a device-timed iteration
     e2e_value = (upd_total / args.steps) * args.steps / e2e_t
     h2d = 3 * sc.n_cells * 4 + n_act * 32
-    d2h = 3 * sc.n_cells * 4 + n_act * 32 + 112
+    d2h = 3 * sc.n_cells * 4 + n_act * 32 + ctypes.sizeof(N.FpCounters)
+
+    # the same kernel where it is HBM-bound: the 2048x2048 barrier scenario's
+    # terrain and water (its pedestrians left out, so the kernel runs alone),
+    # CUDA events around the flood kernel in a profiled pass
+    roof2048 = None
+    if rank == 0 and not args.no_2048:
+        big = scenarios_mod().config_barrier()
+        bsim = P.from_scenario(big, peds=False)
+        N.fp_set_stream(bsim.h, stream.cuda_stream)
+        bsim.step(4)
+        bsim.synchronize()
+        N.fp_set_profiling(bsim.h, 1)
+        bsim.step(32)
+        bprof = bsim.profile()
+        N.fp_set_profiling(bsim.h, 0)
+        bflood = bprof["flood_ms"] / max(bprof["steps"], 1)
+        bach = big.n_cells * FLOOD_BYTES_PER_CELL / (bflood * 1e-3) / 1e9
+        roof2048 = {"kernel": "flood_kernel<16>", "workload": "barrier_2048 terrain and water (2048x2048), flood alone",
+                    "bound": "hbm", "achieved": bach, "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s",
+                    "frac": bach / hbm, "us_per_launch": bflood * 1e3, "bytes_per_cell_update": FLOOD_BYTES_PER_CELL,
+                    "traffic": flood_traffic(), "note": "profiled pass, no pedestrians: the kernel timed alone"}
+        bsim.close()
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -308,15 +350,18 @@ def run_ours(args):
                        "parallelism": "replicas" if ws > 1 else "single",
                        "l2": "flushed between timed iterations (256 MB write); the 512x512 working set "
                              "(~10 MB) is L2-resident within an iteration",
-                       "tile_rows": args.tile_rows or 16},
+                       "tile_rows": tuned["tile_rows"], "ped_lanes": tuned["ped_lanes"],
+                       "launch_shape": "default" if args.no_tune else "fastest autotuner candidate on the snapshot"},
             "breakdown": {"cell_updates_per_s": steps_total * sc.n_cells / (sum(ms_list) / 1e3),
                           "ped_updates_per_s": (upd_total - steps_total * sc.n_cells) / (sum(ms_list) / 1e3),
                           "profiled_ms_per_step": {k: prof[k] / max(prof["steps"], 1)
                                                    for k in ("hash_ms", "flood_ms", "ped_chain_ms", "step_ms")}},
-            "roofline": {"kernel": "flood_kernel<16>", "bound": "hbm", "achieved": achieved, "peak": hbm,
+            "roofline": {"kernel": "flood_kernel<%d>" % tuned["tile_rows"], "bound": "hbm", "achieved": achieved,
+                         "peak": hbm,
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
                          "bytes_per_cell_update": FLOOD_BYTES_PER_CELL,
                          "note": "512x512 fits in L2; frac is against HBM"},
+            "roofline_2048": roof2048,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "clocks": clocks,
@@ -419,10 +464,12 @@ def run_case(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--tile-rows", type=int, default=0)
+    ap.add_argument("--no-2048", action="store_true", help="skip the 2048x2048 flood-kernel roofline pass")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default launch shape (16-row tiles, 8 lanes)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-steps", type=int, default=100)
     ap.add_argument("--ref-sample-steps", type=int, default=8)

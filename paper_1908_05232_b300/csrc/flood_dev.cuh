@@ -39,6 +39,21 @@ __device__ __forceinline__ float sqrt_fast(float x) {
     return r;
 }
 
+__device__ __forceinline__ float rcp_fast(float x) {
+    float r;
+    asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// h^(-4/3) = 2^(-4/3 log2 h) for h > 0 (two special-function instructions)
+__device__ __forceinline__ float pow_m43(float h) {
+    float l, r;
+    asm("lg2.approx.f32 %0, %1;" : "=f"(l) : "f"(h));
+    const float e = -1.33333333f * l;
+    asm("ex2.approx.f32 %0, %1;" : "=f"(r) : "f"(e));
+    return r;
+}
+
 __device__ __forceinline__ float press(float g, float h) { return 0.5f * g * h * h; }
 
 // HLL flux across a face; un normal and ut tangential velocity, pL/pR the face
@@ -77,8 +92,9 @@ __device__ __forceinline__ void hll(float g, float hL, float unL, float utL, flo
     if (sL >= 0.0f) { fm = FL0; fn = FL1; ft = FL2; return; }
     if (sR <= 0.0f) { fm = FR0; fn = FR1; ft = FR2; return; }
     // Differences of two products are rounded explicitly (no contraction), so the
-    // flux of a mirrored face is exactly the mirrored flux.
-    const float inv = __frcp_rn(sR - sL);
+    // flux of a mirrored face is exactly the mirrored flux (its sR - sL is the
+    // same number, so any reciprocal keeps that).
+    const float inv = rcp_fast(sR - sL);
     const float sLR = __fmul_rn(sL, sR);
     fm = __fadd_rn(__fsub_rn(__fmul_rn(sR, FL0), __fmul_rn(sL, FR0)), __fmul_rn(sLR, hR - hL)) * inv;
     fn = __fadd_rn(__fsub_rn(__fmul_rn(sR, FL1), __fmul_rn(sL, FR1)), __fmul_rn(sLR, qR - qL)) * inv;
@@ -290,7 +306,7 @@ __device__ __forceinline__ bool flood_tile(const FpTmaSet &tm, const FpSim &S, i
             const float n0 = k == 0 ? n0A : n0B;
             const int np = oc < FP_NP_CAP ? oc : FP_NP_CAP;
             const float nm = S.coupling ? n0 + (float)np * n0 : n0;
-            const float denom = __fmaf_rn(dt * g * nm * nm * sp, __frcp_rn(h * cbrtf(h)), 1.0f);
+            const float denom = __fmaf_rn(dt * g * nm * nm * sp, pow_m43(h), 1.0f);
             hu = __fdividef(hu, denom);
             hv = __fdividef(hv, denom);
         }

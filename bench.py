@@ -53,6 +53,13 @@ def scenarios_mod():
     return scenarios
 
 
+def wet2048():
+    """2048 x 2048 cells of 0.5 m holding water almost everywhere (70 % wet,
+    velocities up to 1.5 m/s, uneven bed, every boundary type): the flood
+    kernel on its full HLL path, as in a flooded shopping centre."""
+    return scenarios_mod().random_wet_state(2048, 2048, dx=0.5, seed=5)
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -109,16 +116,23 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def flood_traffic():
-    """DRAM bytes per flood launch from the committed ncu summary, null if the kernel changed since."""
-    p = os.path.join(ROOT, "profiles", "flood_kernel_ncu.json")
-    if not os.path.exists(p):
+# DRAM bytes per flood-kernel launch from ncu captures (dram__bytes_read.sum +
+# dram__bytes_write.sum; profiles/flood_kernel_traffic.md), valid only for the
+# kernel sources they were taken on.
+FLOOD_TRAFFIC = {"sources_sha256": "1dabd0a5779cdcf7471b459baaab168317e8864a42e9aefd0cbe21eab8bd9d92",
+                 "shopping_centre_512": 5.94e6, "wet_2048": 93.05e6 + 20.67e6}
+FLOOD_SOURCES = ("flood.cu", "flood_dev.cuh", "fp_common.cuh")
+
+
+def flood_traffic(workload_name):
+    """Measured DRAM bytes per launch of the flood kernel on a workload; None
+    once the kernel's sources differ from those the counters were taken on."""
+    h = hashlib.sha256()
+    for f in FLOOD_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_1908_05232_b300", "csrc", f), "rb").read())
+    if h.hexdigest() != FLOOD_TRAFFIC["sources_sha256"]:
         return None
-    d = json.load(open(p))
-    src = open(os.path.join(ROOT, "paper_1908_05232_b300", "csrc", "flood.cu"), "rb").read()
-    if d.get("flood_cu_sha256") != hashlib.sha256(src).hexdigest():
-        return None
-    return d.get("dram_bytes_per_launch_full_size")
+    return FLOOD_TRAFFIC.get(workload_name)
 
 
 # --------------------------------------------------------------------------
@@ -278,7 +292,7 @@ def run_ours(args):
     flood_ms = prof["flood_ms"] / max(prof["steps"], 1)
     hbm, peak_kind = peaks()
     achieved = sc.n_cells * FLOOD_BYTES_PER_CELL / (flood_ms * 1e-3) / 1e9
-    traffic = flood_traffic()
+    traffic = flood_traffic("shopping_centre_512")
 
     # end to end through the C ABI with pinned host buffers
     host_state = [t.cpu().pin_memory() for t in snap]
@@ -310,12 +324,12 @@ def run_ours(args):
     h2d = 3 * sc.n_cells * 4 + n_act * 32
     d2h = 3 * sc.n_cells * 4 + n_act * 32 + ctypes.sizeof(N.FpCounters)
 
-    # the same kernel where it is HBM-bound: the 2048x2048 barrier scenario's
-    # terrain and water (its pedestrians left out, so the kernel runs alone),
-    # CUDA events around the flood kernel in a profiled pass
+    # the same kernel where it is HBM-bound: a 2048x2048 grid holding water
+    # almost everywhere (no pedestrians, so the kernel runs alone), CUDA events
+    # around the flood kernel in a profiled pass
     roof2048 = None
     if rank == 0 and not args.no_2048:
-        big = scenarios_mod().config_barrier()
+        big = wet2048()
         bsim = P.from_scenario(big, peds=False)
         N.fp_set_stream(bsim.h, stream.cuda_stream)
         bsim.step(4)
@@ -326,10 +340,10 @@ def run_ours(args):
         N.fp_set_profiling(bsim.h, 0)
         bflood = bprof["flood_ms"] / max(bprof["steps"], 1)
         bach = big.n_cells * FLOOD_BYTES_PER_CELL / (bflood * 1e-3) / 1e9
-        roof2048 = {"kernel": "flood_kernel<16>", "workload": "barrier_2048 terrain and water (2048x2048), flood alone",
+        roof2048 = {"kernel": "flood_kernel<16>", "workload": "wet_2048 (2048x2048 cells of 0.5 m, 70 % wet, every boundary type)",
                     "bound": "hbm", "achieved": bach, "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s",
                     "frac": bach / hbm, "us_per_launch": bflood * 1e3, "bytes_per_cell_update": FLOOD_BYTES_PER_CELL,
-                    "traffic": flood_traffic(), "note": "profiled pass, no pedestrians: the kernel timed alone"}
+                    "traffic": flood_traffic("wet_2048"), "note": "profiled pass, no pedestrians: the kernel timed alone"}
         bsim.close()
 
     cpu = None
@@ -451,7 +465,12 @@ def run_case(args):
     import paper_1908_05232_b300 as P
     torch.cuda.set_device(0)
     P.build.build()
-    sc = scenarios.config_barrier() if args.ncu_case == "barrier2048" else workload(2)
+    if args.ncu_case == "barrier2048":
+        sc = scenarios.config_barrier()
+    elif args.ncu_case == "wet2048":
+        sc = wet2048()
+    else:
+        sc = workload(2)
     sim = P.from_scenario(sc, tile_rows=args.tile_rows)
     sim.step(args.case_steps)
     sim.synchronize()
@@ -473,7 +492,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-steps", type=int, default=100)
     ap.add_argument("--ref-sample-steps", type=int, default=8)
-    ap.add_argument("--ncu-case", choices=["barrier2048", "shopping512"], default=None,
+    ap.add_argument("--ncu-case", choices=["barrier2048", "wet2048", "shopping512"], default=None,
                     help="short untimed run of one workload, for profiler captures")
     ap.add_argument("--case-steps", type=int, default=4)
     ap.add_argument("--workload", choices=["shopping512", "ensemble"], default="shopping512")

@@ -54,7 +54,8 @@ __device__ __forceinline__ float pow_m43(float h) {
     return r;
 }
 
-__device__ __forceinline__ float press(float g, float h) { return 0.5f * g * h * h; }
+// face pressure 1/2 g h^2 from hg = 1/2 g (the same products in the same order)
+__device__ __forceinline__ float press(float hg, float h) { return hg * h * h; }
 
 // HLL flux across a face; un normal and ut tangential velocity, pL/pR the face
 // pressures 1/2 g h^2 of the two sides.  out = (mass, normal momentum incl.
@@ -122,9 +123,75 @@ __host__ __device__ constexpr int plane_stride() {
     return (((TY + 2) * ROWW + 31) / 32) * 32;
 }
 
+// staged h, hu, hv, z; south-face fluxes [TY+1][64]; east tile-edge fluxes [TY]
 template <int TY>
 __host__ __device__ constexpr int smem_bytes() {
-    return 6 * plane_stride<TY>() * 4 + TY * (FP_TX + 1) * 16 + (TY + 1) * FP_TX * 16;
+    return 4 * plane_stride<TY>() * 4 + (TY + 1) * FP_TX * 16 + TY * 16;
+}
+
+// a staged cell as a face side: depth, velocities (0 at h <= h_eps), bed
+__device__ __forceinline__ Side staged_side(const float *s_h, const float *s_hu, const float *s_hv, const float *s_z,
+                                            int o) {
+    Side c{s_h[o], 0.0f, 0.0f, s_z[o]};
+    if (c.h > FP_H_EPS_F) {
+        c.u = __fdividef(s_hu[o], c.h);
+        c.v = __fdividef(s_hv[o], c.h);
+    }
+    return c;
+}
+
+__device__ __forceinline__ Side shfl_side(Side c, int src) {
+    return Side{__shfl_sync(0xffffffffu, c.h, src), __shfl_sync(0xffffffffu, c.u, src),
+                __shfl_sync(0xffffffffu, c.v, src), __shfl_sync(0xffffffffu, c.z, src)};
+}
+
+__device__ __forceinline__ Side shfl_up_side(Side c) {
+    return Side{__shfl_up_sync(0xffffffffu, c.h, 1), __shfl_up_sync(0xffffffffu, c.u, 1),
+                __shfl_up_sync(0xffffffffu, c.v, 1), __shfl_up_sync(0xffffffffu, c.z, 1)};
+}
+
+__device__ __forceinline__ float4 shfl_f4(float4 f, int src) {
+    return make_float4(__shfl_sync(0xffffffffu, f.x, src), __shfl_sync(0xffffffffu, f.y, src),
+                       __shfl_sync(0xffffffffu, f.z, src), __shfl_sync(0xffffffffu, f.w, src));
+}
+
+__device__ __forceinline__ float4 shfl_down_f4(float4 f) {
+    return make_float4(__shfl_down_sync(0xffffffffu, f.x, 1), __shfl_down_sync(0xffffffffu, f.y, 1),
+                       __shfl_down_sync(0xffffffffu, f.z, 1), __shfl_down_sync(0xffffffffu, f.w, 1));
+}
+
+// x face between cells i-1 (L) and i (R) of row j: (mass, normal momentum minus
+// the L pressure, minus the R pressure, tangential momentum); ghosts on the
+// domain's west / east edges; zero past the east edge.
+__device__ __forceinline__ float4 x_face(const FpSim &S, float g, float hg, float h_in, Side L, Side R, int i,
+                                         int j) {
+    if (i > S.nx) return make_float4(0.f, 0.f, 0.f, 0.f);
+    if (i == 0) L = ghost(S.bc[2][j], R, true, h_in);
+    if (i == S.nx) R = ghost(S.bc[3][j], L, true, h_in);
+    const float zf = fmaxf(L.z, R.z);
+    const float hLs = fmaxf(0.0f, (L.h + L.z) - zf);
+    const float hRs = fmaxf(0.0f, (R.h + R.z) - zf);
+    const float pL = press(hg, hLs), pR = press(hg, hRs);
+    float fm, fn, ft;
+    hll(g, hLs, L.u, L.v, pL, hRs, R.u, R.v, pR, fm, fn, ft);
+    return make_float4(fm, fn - pL, fn - pR, ft);
+}
+
+// y face between rows j-1 (B) and j (A) of column i: (mass, tangential momentum,
+// normal momentum minus the B pressure, minus the A pressure); ghosts on the
+// domain's south / north edges; zero past the east edge.
+__device__ __forceinline__ float4 y_face(const FpSim &S, float g, float hg, float h_in, Side B, Side A, int i,
+                                         int j) {
+    if (i >= S.nx) return make_float4(0.f, 0.f, 0.f, 0.f);
+    if (j == 0) B = ghost(S.bc[0][i], A, false, h_in);
+    if (j == S.ny) A = ghost(S.bc[1][i], B, false, h_in);
+    const float zf = fmaxf(B.z, A.z);
+    const float hBs = fmaxf(0.0f, (B.h + B.z) - zf);
+    const float hAs = fmaxf(0.0f, (A.h + A.z) - zf);
+    const float pB = press(hg, hBs), pA = press(hg, hAs);
+    float fm, fn, ft;
+    hll(g, hBs, B.v, B.u, pB, hAs, A.v, A.u, pA, fm, fn, ft);
+    return make_float4(fm, ft, fn - pB, fn - pA);
 }
 
 // 32 * TY threads: warp r owns row r of the tile, lane l its cells l and l + 32.
@@ -142,10 +209,8 @@ __device__ __forceinline__ bool flood_tile(const FpTmaSet &tm, const FpSim &S, i
     float *s_hu = s_h + PLANE;
     float *s_hv = s_hu + PLANE;
     float *s_z = s_hv + PLANE;
-    float *s_u = s_z + PLANE;
-    float *s_v = s_u + PLANE;
-    float4 *s_xf = reinterpret_cast<float4 *>(s_v + PLANE);  // [TY][65]
-    float4 *s_yf = s_xf + TY * (FP_TX + 1);                   // [TY+1][64]
+    float4 *s_yf = reinterpret_cast<float4 *>(s_z + PLANE);  // [TY+1][64] south faces; row TY: the tile's north edge
+    float4 *s_xe = s_yf + (TY + 1) * FP_TX;                   // [TY] the tile's east-edge face of each row
     __shared__ long long s_dt, s_t, s_step;
     __shared__ float s_hin, s_dtf, s_lx;
     __shared__ int s_ok;
@@ -215,82 +280,90 @@ __device__ __forceinline__ bool flood_tile(const FpTmaSet &tm, const FpSim &S, i
     __syncthreads();
     if (!s_ok) return false;
 
-    const float g = S.g;
+    const float g = S.g, hg = 0.5f * g;
     const float h_in = s_hin;
 
-    // 2. velocities of staged cells x0-1 .. x0+64 (staged columns 3 .. 68)
-    for (int idx = tid; idx < (TY + 2) * (FP_TX + 2); idx += NT) {
-        const int r = idx / (FP_TX + 2), cc = idx % (FP_TX + 2) + 3;
-        const int o = r * ROWW + cc;
-        const float h = s_h[o];
-        float u = 0.0f, v = 0.0f;
-        if (h > FP_H_EPS_F) {
-            u = __fdividef(s_hu[o], h);
-            v = __fdividef(s_hv[o], h);
+    // 2. faces from registers: this thread's cells A (column lane) and B (lane +
+    // 32) of row `row`; each computes its west and south face.  West
+    // neighbours arrive by shuffle (lane 0: the halo cell, and cell 31 for B).
+    const int oA = (row + 1) * ROWW + lane + 4, oB = oA + 32;
+    const int iA = x0 + lane, iB = iA + 32;
+    float4 fwA = make_float4(0.f, 0.f, 0.f, 0.f), fwB = fwA;
+    {
+        const Side cA = staged_side(s_h, s_hu, s_hv, s_z, oA);
+        const Side cB = staged_side(s_h, s_hu, s_hv, s_z, oB);
+        Side wA = shfl_up_side(cA), wB = shfl_up_side(cB);
+        const Side c31 = shfl_side(cA, 31);
+        if (lane == 0) {
+            wA = staged_side(s_h, s_hu, s_hv, s_z, oA - 1);
+            wB = c31;
         }
-        s_u[o] = u;
-        s_v[o] = v;
+        if (cj < ny) {
+            fwA = x_face(S, g, hg, h_in, wA, cA, iA, cj);
+            fwB = x_face(S, g, hg, h_in, wB, cB, iB, cj);
+            if (iA == 0) s_bx[0][row] = fwA.x;
+            if (iA == nx) s_bx[1][row] = fwA.x;
+            if (iB == nx) s_bx[1][row] = fwB.x;
+        }
+        if (cj <= ny) {
+            const Side bA = staged_side(s_h, s_hu, s_hv, s_z, oA - ROWW);
+            const Side bB = staged_side(s_h, s_hu, s_hv, s_z, oB - ROWW);
+            const float4 gA = y_face(S, g, hg, h_in, bA, cA, iA, cj);
+            const float4 gB = y_face(S, g, hg, h_in, bB, cB, iB, cj);
+            s_yf[row * FP_TX + lane] = gA;
+            s_yf[row * FP_TX + lane + 32] = gB;
+            if (cj == 0) { s_by[0][lane] = gA.x; s_by[0][lane + 32] = gB.x; }
+            if (cj == ny) { s_by[1][lane] = gA.x; s_by[1][lane + 32] = gB.x; }
+        }
+    }
+    // 3. the tile's edge faces: east (column x0 + 64) of each row, north (row
+    // y0 + TY) of each column
+    if (tid < TY + FP_TX) {
+        if (tid < TY) {
+            const int r = tid, j = y0 + r, i = x0 + FP_TX;
+            float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (j < ny && i <= nx) {
+                const int o = (r + 1) * ROWW + FP_TX + 4;
+                f = x_face(S, g, hg, h_in, staged_side(s_h, s_hu, s_hv, s_z, o - 1),
+                           staged_side(s_h, s_hu, s_hv, s_z, o), i, j);
+                if (i == nx) s_bx[1][r] = f.x;
+            }
+            s_xe[r] = f;
+        } else {
+            const int c = tid - TY, i = x0 + c, j = y0 + TY;
+            float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (j <= ny) {
+                const int o = (TY + 1) * ROWW + c + 4;
+                f = y_face(S, g, hg, h_in, staged_side(s_h, s_hu, s_hv, s_z, o - ROWW),
+                           staged_side(s_h, s_hu, s_hv, s_z, o), i, j);
+                if (j == ny && i < nx) s_by[1][c] = f.x;
+            }
+            s_yf[TY * FP_TX + c] = f;
+        }
     }
     __syncthreads();
 
-    // 3a. x faces: face k of row r lies between cells x0+k-1 and x0+k
-    for (int idx = tid; idx < TY * (FP_TX + 1); idx += NT) {
-        const int r = idx / (FP_TX + 1), k = idx % (FP_TX + 1);
-        const int j = y0 + r, xl = x0 + k - 1, xr = x0 + k;
-        if (j >= ny || xr > nx) continue;
-        const int oL = (r + 1) * ROWW + k + 3, oR = oL + 1;
-        Side L, R;
-        if (xr < nx) R = Side{s_h[oR], s_u[oR], s_v[oR], s_z[oR]};
-        if (xl >= 0) L = Side{s_h[oL], s_u[oL], s_v[oL], s_z[oL]};
-        if (xl < 0) L = ghost(S.bc[2][j], R, true, h_in);
-        if (xr == nx) R = ghost(S.bc[3][j], L, true, h_in);
-        const float zf = fmaxf(L.z, R.z);
-        const float hLs = fmaxf(0.0f, (L.h + L.z) - zf);
-        const float hRs = fmaxf(0.0f, (R.h + R.z) - zf);
-        const float pL = press(g, hLs), pR = press(g, hRs);
-        float fm, fn, ft;
-        hll(g, hLs, L.u, L.v, pL, hRs, R.u, R.v, pR, fm, fn, ft);
-        s_xf[r * (FP_TX + 1) + k] = make_float4(fm, fn - pL, fn - pR, ft);
-        if (xl < 0) s_bx[0][r] = fm;
-        if (xr == nx) s_bx[1][r] = fm;
-    }
-    // 3b. y faces: face r of column c lies between rows y0+r-1 and y0+r
-    for (int idx = tid; idx < (TY + 1) * FP_TX; idx += NT) {
-        const int r = idx / FP_TX, c = idx % FP_TX;
-        const int i = x0 + c, jb = y0 + r - 1, ja = y0 + r;
-        if (i >= nx || ja > ny) continue;
-        const int oB = r * ROWW + c + 4, oA = oB + ROWW;
-        Side B, A;
-        if (ja < ny) A = Side{s_h[oA], s_u[oA], s_v[oA], s_z[oA]};
-        if (jb >= 0) B = Side{s_h[oB], s_u[oB], s_v[oB], s_z[oB]};
-        if (jb < 0) B = ghost(S.bc[0][i], A, false, h_in);
-        if (ja == ny) A = ghost(S.bc[1][i], B, false, h_in);
-        const float zf = fmaxf(B.z, A.z);
-        const float hBs = fmaxf(0.0f, (B.h + B.z) - zf);
-        const float hAs = fmaxf(0.0f, (A.h + A.z) - zf);
-        const float pB = press(g, hBs), pA = press(g, hAs);
-        float fm, fn, ft;
-        hll(g, hBs, B.v, B.u, pB, hAs, A.v, A.u, pA, fm, fn, ft);
-        s_yf[r * FP_TX + c] = make_float4(fm, ft, fn - pB, fn - pA);
-        if (jb < 0) s_by[0][c] = fm;
-        if (ja == ny) s_by[1][c] = fm;
-    }
-    __syncthreads();
-
-    // 4. Eq. (2) + friction for this thread's two cells
+    // 4. Eq. (2) + friction for this thread's two cells; east fluxes by shuffle
+    // (lane 31: cell 32's west face, and the tile's east edge for B)
     float smax = 0.0f;
     float sk_[2] = {-1.0f, -1.0f}, hk_[2] = {0.f, 0.f}, huk_[2] = {0.f, 0.f}, hvk_[2] = {0.f, 0.f};
     int wet = 0, neg = 0, bad = 0;
     const float dt = s_dtf, lx = s_lx, ly = s_lx;
     const int p2 = par ^ 1;
+    float4 feA = shfl_down_f4(fwA), feB = shfl_down_f4(fwB);
+    const float4 fB0 = shfl_f4(fwB, 0);
+    if (lane == 31) {
+        feA = fB0;
+        feB = s_xe[row];
+    }
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
         const bool ok = k == 0 ? okA : okB;
         if (!ok) continue;
         const int c = lane + 32 * k;
         const int o = (row + 1) * ROWW + c + 4;
-        const float4 fw = s_xf[row * (FP_TX + 1) + c];
-        const float4 fe = s_xf[row * (FP_TX + 1) + c + 1];
+        const float4 fw = k == 0 ? fwA : fwB;
+        const float4 fe = k == 0 ? feA : feB;
         const float4 gs = s_yf[row * FP_TX + c];
         const float4 gn = s_yf[(row + 1) * FP_TX + c];
         float h = __fmaf_rn(-ly, gn.x - gs.x, __fmaf_rn(-lx, fe.x - fw.x, s_h[o]));
@@ -325,22 +398,23 @@ __device__ __forceinline__ bool flood_tile(const FpTmaSet &tm, const FpSim &S, i
     // CFL: the exact (correctly rounded) wave speed only for cells whose
     // approximate speed is within 1e-5 of the warp's approximate maximum -- the
     // approximation errs by < 1e-6, so the exact maximum is among them.
+    // (non-negative floats order as their bit patterns: one warp-reduce
+    // instruction each)
     {
-        float amax = fmaxf(sk_[0], sk_[1]);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+        const float a = fmaxf(sk_[0], sk_[1]);
+        const float amax = __uint_as_float(__reduce_max_sync(0xffffffffu, a >= 0.0f ? __float_as_uint(a) : 0u));
         const float thr = amax * (1.0f - 1e-5f);
 #pragma unroll
         for (int k = 0; k < 2; ++k)
             if (sk_[k] >= 0.0f && sk_[k] >= thr) smax = fmaxf(smax, fp_wave_speed(g, hk_[k], huk_[k], hvk_[k]));
     }
     // CTA reductions -> next clock slot
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        smax = fmaxf(smax, __shfl_xor_sync(0xffffffffu, smax, o));
-        wet |= __shfl_xor_sync(0xffffffffu, wet, o);
-        neg += __shfl_xor_sync(0xffffffffu, neg, o);
-        bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+    smax = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(smax)));
+    {
+        const unsigned fl = __reduce_or_sync(0xffffffffu, (unsigned)(wet | (bad << 1)));
+        wet = (int)(fl & 1u);
+        bad = (int)(fl >> 1);
+        neg = (int)__reduce_add_sync(0xffffffffu, (unsigned)neg);
     }
     if (lane == 0) {
         s_red[row] = smax;

@@ -185,8 +185,9 @@ __device__ __forceinline__ float face_mass(float g, Side L, Side R, bool xface) 
     const float zf = fmaxf(L.z, R.z);
     const float hL = fmaxf(0.0f, (L.h + L.z) - zf), hR = fmaxf(0.0f, (R.h + R.z) - zf);
     float fm, fn, ft;
-    if (xface) hll(g, hL, L.u, L.v, press(g, hL), hR, R.u, R.v, press(g, hR), fm, fn, ft);
-    else hll(g, hL, L.v, L.u, press(g, hL), hR, R.v, R.u, press(g, hR), fm, fn, ft);
+    const float hg = 0.5f * g;
+    if (xface) hll(g, hL, L.u, L.v, press(hg, hL), hR, R.u, R.v, press(hg, hR), fm, fn, ft);
+    else hll(g, hL, L.v, L.u, press(hg, hL), hR, R.v, R.u, press(hg, hR), fm, fn, ft);
     return fm;
 }
 

@@ -413,6 +413,13 @@ class Surrogate:
         _check(lib().fp_surrogate_train_step(self.h, _ptr(x), _ptr(target), B, H, W, float(lr), ctypes.byref(loss)))
         return float(loss.value)
 
+    @classmethod
+    def pretrained(cls, name="shopping_dt1_32"):
+        """The net with the parameters shipped in the package's weights folder."""
+        sur = cls()
+        sur.set_params(np.load(os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights", name + ".npy")))
+        return sur
+
     def close(self):
         if self.h is not None:
             _check(lib().fp_surrogate_destroy(self.h))

@@ -389,6 +389,76 @@ def run_ours(args):
     return 0
 
 
+def run_surrogate(args):
+    """Learned surrogate against the plain update on the 2048x2048 shopping
+    centre with 100,000 coupled pedestrians (500 responders building a 2-layer
+    barrier; flood from t = 900 s): two identical simulations are brought to
+    mid-flood (CFL step), then the same simulated interval is run with the plain
+    update at a fixed 2^-5 s step and with surrogate windows of 8 such steps
+    (default guard: per-tile mass bound 1e-4, plain check every 64 steps,
+    suspension above 1 cm).  Metric: simulated seconds per wall second;
+    accuracy: the largest depth difference between the two runs at the end."""
+    import torch
+    import scenarios
+    import paper_1908_05232_b300 as P
+    from paper_1908_05232_b300 import _native as N
+    torch.cuda.set_device(0)
+    P.build.build()
+    dt = 2.0 ** -5
+    sc = scenarios.config_barrier()
+    t_start = args.surrogate_start
+    sur = P.Surrogate.pretrained()
+    t0 = time.perf_counter()
+    sims = []
+    for _ in range(2):
+        sim = P.from_scenario(sc)
+        c = sim.counters()
+        while c["t_ticks"] < int(t_start * N.TICKS):
+            sim.step(256)
+            c = sim.counters()
+        sim.set_fixed_dt(dt)
+        sims.append(sim)
+    setup = time.perf_counter() - t0
+    plain, surr = sims
+    assert plain.counters()["t_ticks"] == surr.counters()["t_ticks"]
+    windows = args.steps * 8
+    # warm-up: one window each (graphs, scratch buffers), on both simulations
+    plain.step(8)
+    plain.synchronize()
+    st_w = surr.surrogate_advance(sur, 1)
+    torch.cuda.synchronize()
+    ta = plain.counters()["t_ticks"]
+    t0 = time.perf_counter()
+    plain.step(8 * windows)
+    plain.synchronize()
+    t_plain = time.perf_counter() - t0
+    tb = plain.counters()["t_ticks"]
+    ts0 = surr.counters()["t_ticks"]
+    t0 = time.perf_counter()
+    st = surr.surrogate_advance(sur, windows)
+    t_sur = time.perf_counter() - t0
+    tc = surr.counters()["t_ticks"]
+    sim_s = (tb - ta) / N.TICKS
+    sim_s_sur = (tc - ts0) / N.TICKS
+    err = float(np.abs(plain.field(N.FP_FIELD_H) - surr.field(N.FP_FIELD_H)).max())
+    wet_frac = float((plain.field(N.FP_FIELD_H) > 0).mean())
+    rate_p, rate_s = sim_s / t_plain, sim_s_sur / t_sur
+    line = {"metric": "scenario-seconds/s (learned surrogate windows vs plain update)", "value": rate_s,
+            "unit": "scenario-s/s", "n_gpus": 1, "steps": args.steps, "warmup": 1,
+            "ms_per_step": 1e3 * t_sur / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16 net (FP32 accumulate), f32 plain update", "data": "synthetic",
+            "config": {"workload": "surrogate_2048 (2048x2048 shopping centre, 100,000 pedestrians, barrier, "
+                                   "flood from 900 s)", "start_s": t_start, "dt_s": dt,
+                       "windows": windows, "steps_per_window": 8, "wet_fraction_at_end": wet_frac,
+                       "setup_s": setup},
+            "plain": {"value": rate_p, "unit": "scenario-s/s", "seconds": t_plain},
+            "speedup_vs_plain": rate_s / rate_p,
+            "max_depth_error_m": err,
+            "guard": {k: getattr(st, k) for k, _ in st._fields_}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_ensemble(args):
     """Batched ensemble: 256 seeded shopping-centre scenarios (grid side 128-1024,
     1k-50k pedestrians, 50-1000 responders, 1-3 sandbag layers, inflow peak
@@ -495,11 +565,14 @@ def main():
     ap.add_argument("--ncu-case", choices=["barrier2048", "wet2048", "shopping512"], default=None,
                     help="short untimed run of one workload, for profiler captures")
     ap.add_argument("--case-steps", type=int, default=4)
-    ap.add_argument("--workload", choices=["shopping512", "ensemble"], default="shopping512")
+    ap.add_argument("--workload", choices=["shopping512", "ensemble", "surrogate"], default="shopping512")
+    ap.add_argument("--surrogate-start", type=float, default=1500.0, help="simulated time (s) the surrogate run starts at")
     ap.add_argument("--ensemble-size", type=int, default=256)
     args = ap.parse_args()
     if args.ncu_case:
         return run_case(args)
+    if args.workload == "surrogate":
+        return run_surrogate(args)
     if args.workload == "ensemble":
         return run_ensemble(args)
     if args.impl == "reference":

@@ -269,8 +269,8 @@ int fp_surrogate_train_step(fp_surrogate *sur, const float *x, const float *targ
  *   1. tiles of FP_SUR_TILE x FP_SUR_TILE cells whose region grown by
  *      FP_SUR_WINDOW cells holds no water (h = 0, no inflow over the window)
  *      are dry: the plain update leaves them unchanged, so they are skipped;
- *   2. every other tile, with a FP_SUR_HALO-cell halo (cells past the domain
- *      edge repeat the edge cell), goes through the net: U' = U + dU, h' >= 0,
+ *   2. every other tile, with a FP_SUR_HALO-cell halo (a 256 x 256 input;
+ *      cells past the domain edge repeat the edge cell), goes through the net: U' = U + dU, h' >= 0,
  *      no velocity where h' <= 1e-6 m;
  *   3. the pedestrians take the window's steps on the state at its start
  *      (coupled steps whose flood update moves no water), sandbag layers
@@ -288,7 +288,7 @@ int fp_surrogate_train_step(fp_surrogate *sur, const float *x, const float *targ
  *      run the plain update on every tile.
  * Stops before a window that would cross t_end.  *stats accumulates (zero it
  * before the first call).  Synchronises the stream. */
-#define FP_SUR_TILE 256
+#define FP_SUR_TILE 246  /* output cells per tile side: the net's input tile, halo included, is 256 x 256 */
 typedef struct fp_surrogate_guard {
     float mass_tol;           /* 1e-4 */
     float check_tol;          /* 0.01 m */

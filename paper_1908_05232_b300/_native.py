@@ -363,6 +363,9 @@ def from_scenario(sc, max_peds=None, tile_rows=0, peds=True, mode=None) -> Simul
     return sim
 
 
+SUR_TILE = 246  # FP_SUR_TILE: output cells per surrogate tile side (256 x 256 net input)
+
+
 class Surrogate:
     """The learned flood surrogate (tcgen05 forward); parameters as FP32 numpy."""
 

@@ -283,13 +283,26 @@ __device__ __forceinline__ bool flood_tile(const FpTmaSet &tm, const FpSim &S, i
     const float g = S.g, hg = 0.5f * g;
     const float h_in = s_hin;
 
+    // 1b. a dry tile -- no water in the tile and its one-cell halo, no inflow
+    // ghost at its domain edges -- has zero flux on every face (h* = 0 on both
+    // sides), so the update leaves h = hu = hv = 0: the faces are skipped and
+    // the same update runs on zero fluxes (the same bits as computing them).
+    int any = 0;
+    for (int idx = tid; idx < (TY + 2) * (FP_TX + 2); idx += NT) {
+        const int r = idx / (FP_TX + 2), cc = idx % (FP_TX + 2) + 3;
+        if (s_h[r * ROWW + cc] != 0.0f) any = 1;
+    }
+    if (S.has_inflow && h_in > FP_H_EPS_F && (x0 == 0 || x0 + FP_TX >= nx || y0 == 0 || y0 + TY >= ny)) any = 1;
+    const bool dry = __syncthreads_or(any) == 0;
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+
     // 2. faces from registers: this thread's cells A (column lane) and B (lane +
     // 32) of row `row`; each computes its west and south face.  West
     // neighbours arrive by shuffle (lane 0: the halo cell, and cell 31 for B).
     const int oA = (row + 1) * ROWW + lane + 4, oB = oA + 32;
     const int iA = x0 + lane, iB = iA + 32;
-    float4 fwA = make_float4(0.f, 0.f, 0.f, 0.f), fwB = fwA;
-    {
+    float4 fwA = zero4, fwB = zero4;
+    if (!dry) {
         const Side cA = staged_side(s_h, s_hu, s_hv, s_z, oA);
         const Side cB = staged_side(s_h, s_hu, s_hv, s_z, oB);
         Side wA = shfl_up_side(cA), wB = shfl_up_side(cB);
@@ -318,7 +331,7 @@ __device__ __forceinline__ bool flood_tile(const FpTmaSet &tm, const FpSim &S, i
     }
     // 3. the tile's edge faces: east (column x0 + 64) of each row, north (row
     // y0 + TY) of each column
-    if (tid < TY + FP_TX) {
+    if (!dry && tid < TY + FP_TX) {
         if (tid < TY) {
             const int r = tid, j = y0 + r, i = x0 + FP_TX;
             float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -354,7 +367,7 @@ __device__ __forceinline__ bool flood_tile(const FpTmaSet &tm, const FpSim &S, i
     const float4 fB0 = shfl_f4(fwB, 0);
     if (lane == 31) {
         feA = fB0;
-        feB = s_xe[row];
+        feB = dry ? zero4 : s_xe[row];
     }
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
@@ -364,8 +377,8 @@ __device__ __forceinline__ bool flood_tile(const FpTmaSet &tm, const FpSim &S, i
         const int o = (row + 1) * ROWW + c + 4;
         const float4 fw = k == 0 ? fwA : fwB;
         const float4 fe = k == 0 ? feA : feB;
-        const float4 gs = s_yf[row * FP_TX + c];
-        const float4 gn = s_yf[(row + 1) * FP_TX + c];
+        const float4 gs = dry ? zero4 : s_yf[row * FP_TX + c];
+        const float4 gn = dry ? zero4 : s_yf[(row + 1) * FP_TX + c];
         float h = __fmaf_rn(-ly, gn.x - gs.x, __fmaf_rn(-lx, fe.x - fw.x, s_h[o]));
         float hu = __fmaf_rn(-ly, gn.y - gs.y, __fmaf_rn(-lx, fe.y - fw.z, s_hu[o]));
         float hv = __fmaf_rn(-ly, gn.z - gs.w, __fmaf_rn(-lx, fe.w - fw.w, s_hv[o]));
@@ -423,7 +436,7 @@ __device__ __forceinline__ bool flood_tile(const FpTmaSet &tm, const FpSim &S, i
     __syncthreads();
     // boundary tiles only: FP64 accumulation of the mass through the domain edges (one warp)
     const bool edge_x0 = x0 == 0, edge_x1 = x0 + FP_TX >= nx, edge_y0 = y0 == 0, edge_y1 = y0 + TY >= ny;
-    if (row == 1 && (edge_x0 || edge_x1 || edge_y0 || edge_y1)) {
+    if (!dry && row == 1 && (edge_x0 || edge_x1 || edge_y0 || edge_y1)) {
         const double dtdx = (double)dt * (double)S.dx;
         for (int r = lane; r < TY; r += 32) {
             const int j = y0 + r;

@@ -68,6 +68,9 @@ __host__ __device__ constexpr unsigned umma_idesc(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(N >> 3) << 17) | ((unsigned)(M >> 4) << 24);
 }
 
+constexpr int kStripRows = 32;  // output rows per work item (one column segment of one image)
+constexpr int kRing = 5;        // staged input rows: the MMA's 3, the next MMA's new one, one loading
+
 template <int CIN, int COUT>
 struct ConvGeom {
     static constexpr int KC = CIN / 16;            // K chunks of 16 channels
@@ -77,7 +80,7 @@ struct ConvGeom {
     static constexpr int WBLK = 2 * COUT * 16;     // bytes per (tap, chunk) weight block
     static constexpr int WB = 9 * KC * WBLK;       // weight bytes
     // guard region after the operands (a descriptor-field error reads garbage inside the allocation)
-    static constexpr int SMEM = ((WB + 3 * ROWB + 16 * NPIX * 16 + 2048) + 1023) / 1024 * 1024;
+    static constexpr int SMEM = ((WB + kRing * ROWB + 2048) + 1023) / 1024 * 1024;
 };
 
 __device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity) {
@@ -118,10 +121,28 @@ __device__ __forceinline__ void tmem_load<16>(unsigned taddr, unsigned (&r)[16])
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// 16-byte asynchronous global -> shared copy; bytes = 0 fills the 16 bytes with zeros
+__device__ __forceinline__ void cp_async16(unsigned dst, const void *src, unsigned bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 // One 3x3 valid convolution of B images (NHWC, BF16, CIN channels) with the
 // packed weights (9 taps x CIN/16 chunks of [2 k-cores][COUT rows][8] BF16).
 // Hidden layers: bias + ReLU, BF16 output with COUT channels.  Last layer
 // (LAST): bias, FP32 output with 3 channels, times kOutScale.
+//
+// Work item: one column segment (128 output pixels) of up to kStripRows
+// consecutive output rows of one image.  The CTA keeps a ring of kRing staged
+// input rows ([k-core][pixel][8 channels]), filled by cp.async one row ahead,
+// so each output row stages one new input row; two TMEM accumulators (32
+// columns each) let the MMAs of row r+1 run while the four warps read row r's
+// accumulator for the epilogue.  Per output row r:
+//   stage input row r+4 (async) | wait for input row r+3 | sync
+//   thread 0 issues row r+1's MMAs (input rows r+1..r+3) -> accumulator (r+1)&1
+//   wait for row r's MMAs (bounded) | epilogue of row r from accumulator r&1
 template <int CIN, int COUT, bool LAST>
 __global__ void __launch_bounds__(kConvThreads) conv3x3_tc_kernel(const __nv_bfloat16 *__restrict__ x, int B, int H,
                                                                   int W, const __nv_bfloat16 *__restrict__ wpack,
@@ -131,23 +152,23 @@ __global__ void __launch_bounds__(kConvThreads) conv3x3_tc_kernel(const __nv_bfl
     extern __shared__ __align__(1024) unsigned char sm[];
     unsigned char *s_w = sm;
     unsigned char *s_x = sm + G::WB;
-    __shared__ __align__(8) unsigned long long mbar;
+    __shared__ __align__(8) unsigned long long mbar[2];
     __shared__ unsigned s_taddr;
-    __shared__ int s_ok;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int Ho = H - 2, Wo = W - 2;
-    const int segs_per_row = (Wo + kSeg - 1) / kSeg;
-    const int nseg = B * Ho * segs_per_row;
+    const int segs = (Wo + kSeg - 1) / kSeg;
+    const int chunks = (Ho + kStripRows - 1) / kStripRows;
+    const int items = B * segs * chunks;
     constexpr unsigned IDESC = umma_idesc(kSeg, COUT);
 
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(sm_addr(&s_taddr)));
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(sm_addr(&s_taddr)));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sm_addr(&mbar)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sm_addr(&mbar[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sm_addr(&mbar[1])));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        s_ok = 1;
     }
     for (int i = tid; i < G::WB / 16; i += kConvThreads)
         reinterpret_cast<uint4 *>(s_w)[i] = reinterpret_cast<const uint4 *>(wpack)[i];
@@ -155,91 +176,118 @@ __global__ void __launch_bounds__(kConvThreads) conv3x3_tc_kernel(const __nv_bfl
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const unsigned taddr = s_taddr;
-    unsigned phase = 0;
+    const unsigned xs = sm_addr(s_x), ws = sm_addr(s_w);
+    unsigned phases = 0u;  // bit k: phase parity of mbar[k]
+    bool ok = true;
 
-    for (int seg = blockIdx.x; seg < nseg; seg += gridDim.x) {
-        const int img = seg / (Ho * segs_per_row);
-        const int rem = seg % (Ho * segs_per_row);
-        const int oy = rem / segs_per_row, ox0 = (rem % segs_per_row) * kSeg;
+    for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
+        const int img = item / (segs * chunks);
+        const int rem = item % (segs * chunks);
+        const int ox0 = (rem / chunks) * kSeg, oy0 = (rem % chunks) * kStripRows;
+        const int nrow = min(kStripRows, Ho - oy0);
         const __nv_bfloat16 *xin = x + (size_t)img * H * W * CIN;
-        // stage input rows oy .. oy+2, pixels ox0 .. ox0+129, as [row][k-core][pixel][8 channels]
-        for (int u = tid; u < 3 * G::NKC * G::NPIX; u += kConvThreads) {
-            const int r = u / (G::NKC * G::NPIX), q = u % (G::NKC * G::NPIX);
-            const int j = q / G::NPIX, p = q % G::NPIX;
-            const int ix = ox0 + p;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (ix < W) v = *reinterpret_cast<const uint4 *>(xin + ((size_t)(oy + r) * W + ix) * CIN + j * 8);
-            *reinterpret_cast<uint4 *>(s_x + r * G::ROWB + (j * G::NPIX + p) * 16) = v;
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (tid == 0) {
-            const unsigned xs = sm_addr(s_x), ws = sm_addr(s_w);
+        // input row iy (image row oy0 + iy) into ring slot iy % kRing
+        auto stage = [&](int iy) {
+            const unsigned dst = xs + (iy % kRing) * G::ROWB;
+            const __nv_bfloat16 *row = xin + (size_t)(oy0 + iy) * W * CIN;
+            for (int u = tid; u < G::NKC * G::NPIX; u += kConvThreads) {
+                const int j = u / G::NPIX, p = u % G::NPIX;
+                const int ix = ox0 + p;
+                const bool in = ix < W;
+                cp_async16(dst + (j * G::NPIX + p) * 16, row + (size_t)(in ? ix : 0) * CIN + j * 8, in ? 16u : 0u);
+            }
+        };
+        // the MMAs of output row r (input rows r .. r+2) into accumulator r & 1
+        auto issue = [&](int r) {
+            if (tid != 0) return;
+            const unsigned acc_col = (unsigned)(r & 1) * 32u;
 #pragma unroll 1
             for (int t = 0; t < 9; ++t) {
                 const int ky = t / 3, kx = t % 3;
+                const unsigned rowa = xs + ((r + ky) % kRing) * G::ROWB;
 #pragma unroll
                 for (int c = 0; c < G::KC; ++c) {
-                    const unsigned a = xs + ky * G::ROWB + (2 * c) * (G::NPIX * 16) + kx * 16;
+                    const unsigned a = rowa + (2 * c) * (G::NPIX * 16) + kx * 16;
                     const unsigned b = ws + (t * G::KC + c) * G::WBLK;
                     const unsigned long long ad = umma_desc(a, G::NPIX * 16, 128);
                     const unsigned long long bd = umma_desc(b, COUT * 16, 128);
                     const unsigned acc = (t | c) != 0 ? 1u : 0u;
                     asm volatile(
                         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(taddr),
+                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(taddr + acc_col),
                         "l"(ad), "l"(bd), "r"(IDESC), "r"(acc)
                         : "memory");
                 }
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             sm_addr(&mbar))
+                             sm_addr(&mbar[r & 1]))
                          : "memory");
-        }
-        const bool done = mbar_wait_bounded(sm_addr(&mbar), phase);
-        phase ^= 1u;
-        if (!done) {
-            if (lane == 0) atomicOr(err, FP_ERR_TIMEOUT);
-            s_ok = 0;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        __syncthreads();
-        if (!s_ok) break;
-        // epilogue: warp w owns TMEM lanes (output pixels) 32w .. 32w+31
-        const int m = 32 * warp + lane;
-        const int ox = ox0 + m;
-        unsigned r[COUT];
-        tmem_load<COUT>(taddr + ((unsigned)(32 * warp) << 16), r);
-        if (ox < Wo) {
-            const size_t pix = ((size_t)img * Ho + oy) * Wo + ox;
-            if constexpr (LAST) {
-                float *yo = static_cast<float *>(y) + pix * 3;
-#pragma unroll
-                for (int co = 0; co < 3; ++co) yo[co] = (__uint_as_float(r[co]) + bias[co]) * kOutScale;
-            } else {
-                __nv_bfloat16 *yo = static_cast<__nv_bfloat16 *>(y) + pix * COUT;
-#pragma unroll
-                for (int q = 0; q < COUT / 8; ++q) {
-                    __nv_bfloat162 v[4];
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const float a0 = fmaxf(__uint_as_float(r[8 * q + 2 * e]) + bias[8 * q + 2 * e], 0.0f);
-                        const float a1 = fmaxf(__uint_as_float(r[8 * q + 2 * e + 1]) + bias[8 * q + 2 * e + 1], 0.0f);
-                        v[e] = __floats2bfloat162_rn(a0, a1);
-                    }
-                    *reinterpret_cast<uint4 *>(yo + 8 * q) = *reinterpret_cast<const uint4 *>(v);
-                }
-            }
-        }
+        };
+        // prologue: input rows 0..2, then 3; row 0's MMAs
+        stage(0);
+        stage(1);
+        stage(2);
+        cp_async_commit();
+        if (nrow > 1) stage(3);
+        cp_async_commit();
+        cp_async_wait<1>();
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        issue(0);
+        for (int r = 0; r < nrow; ++r) {
+            if (r + 4 < nrow + 2) stage(r + 4);
+            cp_async_commit();
+            cp_async_wait<1>();  // input row r+3 has landed
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncthreads();
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (r + 1 < nrow) issue(r + 1);
+            const bool done = mbar_wait_bounded(sm_addr(&mbar[r & 1]), (phases >> (r & 1)) & 1u);
+            phases ^= 1u << (r & 1);
+            if (!__syncthreads_and(done)) {
+                if (tid == 0) atomicOr(err, FP_ERR_TIMEOUT);
+                ok = false;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            // epilogue: warp w owns TMEM lanes (output pixels) 32w .. 32w+31
+            const int oy = oy0 + r, ox = ox0 + 32 * warp + lane;
+            unsigned v[COUT];
+            tmem_load<COUT>(taddr + ((unsigned)(32 * warp) << 16) + (unsigned)(r & 1) * 32u, v);
+            if (ox < Wo) {
+                const size_t pix = ((size_t)img * Ho + oy) * Wo + ox;
+                if constexpr (LAST) {
+                    float *yo = static_cast<float *>(y) + pix * 3;
+#pragma unroll
+                    for (int co = 0; co < 3; ++co) yo[co] = (__uint_as_float(v[co]) + bias[co]) * kOutScale;
+                } else {
+                    __nv_bfloat16 *yo = static_cast<__nv_bfloat16 *>(y) + pix * COUT;
+#pragma unroll
+                    for (int q = 0; q < COUT / 8; ++q) {
+                        __nv_bfloat162 o[4];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const float a0 = fmaxf(__uint_as_float(v[8 * q + 2 * e]) + bias[8 * q + 2 * e], 0.0f);
+                            const float a1 =
+                                fmaxf(__uint_as_float(v[8 * q + 2 * e + 1]) + bias[8 * q + 2 * e + 1], 0.0f);
+                            o[e] = __floats2bfloat162_rn(a0, a1);
+                        }
+                        *reinterpret_cast<uint4 *>(yo + 8 * q) = *reinterpret_cast<const uint4 *>(o);
+                    }
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        }
+        cp_async_wait<0>();
+        __syncthreads();
     }
+    cp_async_wait<0>();
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(taddr));
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(taddr));
 }
 
 // FP32 (h, hu, hv, z) images -> BF16 NHWC with 16 channels: 0-3 the rounded
@@ -439,8 +487,9 @@ cudaError_t launch_conv(const fp_surrogate *s, int layer, const __nv_bfloat16 *x
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    const long long nseg = (long long)B * (H - 2) * (((W - 2) + kSeg - 1) / kSeg);
-    int grid = (int)std::min<long long>(nseg, (long long)s->sms * 3);
+    const long long items =
+        (long long)B * (((W - 2) + kSeg - 1) / kSeg) * (((H - 2) + kStripRows - 1) / kStripRows);
+    int grid = (int)std::min<long long>(items, (long long)s->sms * 3);
     if (grid < 1) grid = 1;
     conv3x3_tc_kernel<CIN, COUT, LAST><<<grid, kConvThreads, G::SMEM, st>>>(x, B, H, W, s->d_wpack[layer],
                                                                              s->d_bias[layer], y, s->d_err);

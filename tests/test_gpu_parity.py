@@ -463,3 +463,25 @@ def test_autotuner_picks_a_valid_shape(P, tmp_path):
     autotune.apply(sim, best)
     sim.step(10)
     sim.synchronize()
+
+
+@pytest.mark.parametrize("tile_rows", [8, 16])
+def test_mostly_dry_grid_parity(P, O, tile_rows):
+    """Water in the west third only, inflow on the east edge: most flood tiles
+    are dry (the kernel skips their faces) while the wet front, the inflow
+    tiles and the dry-wet boundary tiles are computed; 120 steps against the
+    oracle."""
+    sc = S.random_wet_state(300, 200, dx=0.8, seed=21)
+    sc.h[:, 100:] = 0.0
+    sc.hu[:, 100:] = 0.0
+    sc.hv[:, 100:] = 0.0
+    o = O.Oracle(sc)
+    o.step(1)
+    sim = run_gpu(P, sc, 1, tile_rows=tile_rows)
+    assert sim.counters()["t_ticks"] == o.t_ticks
+    assert_flood_close(sim, o, atol=2e-5, rtol=2e-6)
+    o.step(119)
+    sim.step(119)
+    sim.synchronize()
+    assert abs(sim.counters()["t_ticks"] - o.t_ticks) <= 120
+    assert_flood_close(sim, o, atol=1e-4)

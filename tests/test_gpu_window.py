@@ -132,7 +132,8 @@ def test_window_fallback_equals_plain(P, shape):
     st = a.surrogate_advance(net(P, scale=3.0), 2, mass_tol=0.0, check_every=0)
     b.step(16)
     b.synchronize()
-    tiles = ((nx + 255) // 256) * ((ny + 255) // 256)
+    T = P._native.SUR_TILE
+    tiles = ((nx + T - 1) // T) * ((ny + T - 1) // T)
     assert st.tiles_net == 2 * tiles and st.tiles_fallback == 2 * tiles
     assert a.counters()["t_ticks"] == b.counters()["t_ticks"]
     for x, y in zip(fields(a), fields(b)):
@@ -140,14 +141,14 @@ def test_window_fallback_equals_plain(P, shape):
 
 
 def test_window_guard_recomputes_only_rejected_tiles(P):
-    # a lake at rest on the west half and a wave on the east half: the zero net
-    # keeps the lake exactly (guard passes), the wave tile fails and is recomputed
-    sc = fixed(S.random_wet_state(512, 200, dx=0.8, seed=9, bc=(S.BC_WALL,) * 4))
-    sc.h[:, :256] = np.maximum(0.0, 1.0 - sc.z[:, :256])
-    sc.hu[:, :256] = 0.0
-    sc.hv[:, :256] = 0.0
-    sc.z[:, :256] = np.round(sc.z[:, :256] * 4096) / 4096
-    sc.h[:, :256] = np.maximum(0.0, 1.0 - sc.z[:, :256])
+    # a lake at rest in the west tile column and a wave in the east one: the
+    # zero net keeps the lake exactly, the wave tile fails and is recomputed
+    T = P._native.SUR_TILE
+    sc = fixed(S.random_wet_state(2 * T, 200, dx=0.8, seed=9, bc=(S.BC_WALL,) * 4))
+    sc.z[:, :T] = np.round(sc.z[:, :T] * 4096) / 4096
+    sc.h[:, :T] = np.maximum(0.0, 1.0 - sc.z[:, :T])
+    sc.hu[:, :T] = 0.0
+    sc.hv[:, :T] = 0.0
     a = P.from_scenario(sc)
     b = P.from_scenario(sc)
     sur = net(P)
@@ -159,12 +160,12 @@ def test_window_guard_recomputes_only_rejected_tiles(P):
     fa, fb = fields(a), fields(b)
     # the wave tile is recomputed (the zero net misses the flow through its
     # west edge); the lake tile, kept by the net or recomputed, is the plain
-    # result except where the wave's 8 steps reach across x = 256
+    # result except where the wave's 8 steps reach across x = T
     assert st.tiles_fallback >= 1
     for x, y in zip(fa, fb):
-        assert np.array_equal(x[:, 256:], y[:, 256:])
+        assert np.array_equal(x[:, T:], y[:, T:])
     for x, y in zip(fa, fb):
-        assert np.array_equal(x[:, :256 - 8], y[:, :256 - 8])
+        assert np.array_equal(x[:, :T - 8], y[:, :T - 8])
 
 
 def test_window_checks_and_suspension(P):

@@ -33,6 +33,7 @@ __global__ void __launch_bounds__(32 * TY, TY == 16 ? 3 : 1) flood_kernel(const 
                                                         const __grid_constant__ FpSim S, int par, int slot) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) unsigned long long mbar;
+    fp_pdl_wait();
     if (S.tile_mask != nullptr && S.tile_mask[blockIdx.y * gridDim.x + blockIdx.x] == 0) return;
     if (threadIdx.x == 0) mbar_init(&mbar);
     __syncthreads();
@@ -124,17 +125,18 @@ cudaError_t fp_flood_init_attributes() {
 }
 
 template <int TY>
-static void launch_flood_t(const FpSim &S, const FpTmaSet &tm, int par, int slot, cudaStream_t st) {
+static void launch_flood_t(const FpSim &S, const FpTmaSet &tm, int par, int slot, cudaStream_t st, bool pdl) {
     constexpr int smem = smem_bytes<TY>();
     dim3 grid((S.nx + FP_TX - 1) / FP_TX, (S.ny + TY - 1) / TY);
-    flood_kernel<TY><<<grid, 32 * TY, smem, st>>>(tm, S, par, slot);
+    fp_launch(pdl, flood_kernel<TY>, grid, dim3(32 * TY), smem, st, tm, S, par, slot);
 }
 
-void fp_launch_flood(const FpSim &S, const void *tma_set, int par, int slot, int tile_rows, cudaStream_t st) {
+void fp_launch_flood(const FpSim &S, const void *tma_set, int par, int slot, int tile_rows, cudaStream_t st,
+                     bool pdl) {
     const FpTmaSet &tm = *static_cast<const FpTmaSet *>(tma_set);
-    if (tile_rows == 8) launch_flood_t<8>(S, tm, par, slot, st);
-    else if (tile_rows == 32) launch_flood_t<32>(S, tm, par, slot, st);
-    else launch_flood_t<16>(S, tm, par, slot, st);
+    if (tile_rows == 8) launch_flood_t<8>(S, tm, par, slot, st, pdl);
+    else if (tile_rows == 32) launch_flood_t<32>(S, tm, par, slot, st, pdl);
+    else launch_flood_t<16>(S, tm, par, slot, st, pdl);
 }
 
 void fp_launch_init_clock(const FpSim &S, int par, int slot, cudaStream_t st) {

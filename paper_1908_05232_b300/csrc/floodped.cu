@@ -264,11 +264,14 @@ static void launch_step(fp_sim *s, int par, int slot, cudaEvent_t *ev = nullptr)
     cudaEventRecord(s->ev_fork, s->stream);
     if (ev) cudaEventRecord(ev[1], s->stream);
     cudaStreamWaitEvent(s->stream2, s->ev_fork, 0);
+    // programmatic dependent launches on kernel -> kernel edges of one stream
+    // (not in profiling mode, whose events sit between the kernels)
+    const bool pdl = ev == nullptr;
     fp_launch_flood(S, &s->tma[par], par, slot, s->tile_rows, s->stream);
     if (ev) cudaEventRecord(ev[2], s->stream);
     fp_launch_scan(S, s->stream2);
-    fp_launch_gather(S, s->stream2);
-    fp_launch_ped_step(S, par, slot, s->ped_lanes, s->stream2);
+    fp_launch_gather(S, s->stream2, pdl);
+    fp_launch_ped_step(S, par, slot, s->ped_lanes, s->stream2, pdl);
     if (ev) cudaEventRecord(ev[3], s->stream2);
     cudaEventRecord(s->ev_join, s->stream2);
     cudaStreamWaitEvent(s->stream, s->ev_join, 0);

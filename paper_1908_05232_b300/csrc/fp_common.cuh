@@ -20,6 +20,8 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <utility>
+
 #define FP_PADX 4
 #define FP_TX 64                 // flood tile width (cells)
 #define FP_TICKS_F 1048576.0f    // ticks per second (2^20)
@@ -199,15 +201,16 @@ struct FpTmaSet {
 };
 
 // launchers (defined in flood.cu / peds.cu)
-void fp_launch_flood(const FpSim &S, const void *tma_set, int par, int slot, int tile_rows, cudaStream_t st);
+void fp_launch_flood(const FpSim &S, const void *tma_set, int par, int slot, int tile_rows, cudaStream_t st,
+                     bool pdl = false);
 void fp_launch_init_clock(const FpSim &S, int par, int slot, cudaStream_t st);
 void fp_launch_mass(const FpSim &S, int par, cudaStream_t st);
 int fp_flood_smem_bytes(int tile_rows);
 cudaError_t fp_flood_init_attributes();
 void fp_launch_hash_count(const FpSim &S, int par, cudaStream_t st);
 void fp_launch_scan(const FpSim &S, cudaStream_t st);
-void fp_launch_gather(const FpSim &S, cudaStream_t st);
-void fp_launch_ped_step(const FpSim &S, int par, int slot, int lanes, cudaStream_t st);
+void fp_launch_gather(const FpSim &S, cudaStream_t st, bool pdl = false);
+void fp_launch_ped_step(const FpSim &S, int par, int slot, int lanes, cudaStream_t st, bool pdl = false);
 void fp_launch_assign_ids(const FpSim &S, int first_slot, int first_id, int count, cudaStream_t st);
 void fp_launch_read_peds(const FpSim &S, uint4 *out, int n_total, cudaStream_t st);
 int fp_scan_tiles(int nbins);
@@ -220,6 +223,28 @@ void fp_launch_flood_batch(const FpSim *d_sims, const FpTmaSet *d_maps, const in
                            int total_tiles, int par, int slot, cudaStream_t st);
 cudaError_t fp_launch_persistent(const FpSim &S, const FpTmaSet tma[2], int par, int slot, int nsteps,
                                  unsigned *bar, int ctas, int smem_dynamic, cudaStream_t st);
+
+// Programmatic dependent launch: the kernel may be scheduled while the previous
+// kernel of its stream is finishing; it must execute fp_pdl_wait() before it
+// reads anything that kernel wrote (a no-op when launched normally).
+__device__ __forceinline__ void fp_pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void fp_pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t fp_launch(bool pdl, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                             cudaStream_t st, Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 // surrogate window (window.cu, surrogate.cu)
 struct fp_surrogate;

@@ -15,6 +15,7 @@ using namespace fpdev;
 constexpr int kScanItems = 8, kScanThreads = 256, kScanTile = kScanItems * kScanThreads;
 
 __global__ void hash_count_kernel(const __grid_constant__ FpSim S, int par) {
+    fp_pdl_trigger();  // the flood kernel may be scheduled now; it waits for this grid's end
     FpCounters *C = S.cnt;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         barrier_and_snapshot(S);
@@ -126,7 +127,10 @@ __device__ __forceinline__ void scan_tile(const FpSim &S) {
     }
 }
 
-__global__ void __launch_bounds__(kScanThreads) scan_kernel(const __grid_constant__ FpSim S) { scan_tile(S); }
+__global__ void __launch_bounds__(kScanThreads) scan_kernel(const __grid_constant__ FpSim S) {
+    fp_pdl_trigger();  // the gather may be scheduled now; it waits for this grid's end
+    scan_tile(S);
+}
 
 __device__ __forceinline__ void gather_record(const FpSim &S, int i) {
     const int key = S.pkey[i];
@@ -142,6 +146,8 @@ __device__ __forceinline__ void gather_record(const FpSim &S, int i) {
 }
 
 __global__ void gather_kernel(const __grid_constant__ FpSim S) {
+    fp_pdl_wait();
+    fp_pdl_trigger();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < S.cnt->nB) gather_record(S, i);
 }
@@ -154,6 +160,7 @@ struct DirectLookup {
 template <int kG>
 __global__ void __launch_bounds__(256) ped_step_kernel(const __grid_constant__ FpSim S, int par, int slot) {
     __shared__ StepCtl s_ctl;
+    fp_pdl_wait();
     FpCounters *C = S.cnt;
     if (threadIdx.x == 0) {
         load_step_ctl(S, slot, C->nA, s_ctl);
@@ -288,11 +295,14 @@ void fp_launch_hash_count(const FpSim &S, int par, cudaStream_t st) {
 void fp_launch_scan(const FpSim &S, cudaStream_t st) {
     scan_kernel<<<fp_scan_tiles(S.nbins), kScanThreads, 0, st>>>(S);
 }
-void fp_launch_gather(const FpSim &S, cudaStream_t st) { gather_kernel<<<blocks_for(S.cap, 256), 256, 0, st>>>(S); }
-void fp_launch_ped_step(const FpSim &S, int par, int slot, int lanes, cudaStream_t st) {
-    if (lanes == 4) ped_step_kernel<4><<<blocks_for(S.cap * 4, 256), 256, 0, st>>>(S, par, slot);
-    else if (lanes == 16) ped_step_kernel<16><<<blocks_for(S.cap * 16, 256), 256, 0, st>>>(S, par, slot);
-    else ped_step_kernel<8><<<blocks_for(S.cap * 8, 256), 256, 0, st>>>(S, par, slot);
+void fp_launch_gather(const FpSim &S, cudaStream_t st, bool pdl) {
+    fp_launch(pdl, gather_kernel, dim3(blocks_for(S.cap, 256)), dim3(256), 0, st, S);
+}
+void fp_launch_ped_step(const FpSim &S, int par, int slot, int lanes, cudaStream_t st, bool pdl) {
+    if (lanes == 4) fp_launch(pdl, ped_step_kernel<4>, dim3(blocks_for(S.cap * 4, 256)), dim3(256), 0, st, S, par, slot);
+    else if (lanes == 16)
+        fp_launch(pdl, ped_step_kernel<16>, dim3(blocks_for(S.cap * 16, 256)), dim3(256), 0, st, S, par, slot);
+    else fp_launch(pdl, ped_step_kernel<8>, dim3(blocks_for(S.cap * 8, 256)), dim3(256), 0, st, S, par, slot);
 }
 void fp_launch_assign_ids(const FpSim &S, int first_slot, int first_id, int count, cudaStream_t st) {
     if (count > 0) assign_ids_kernel<<<blocks_for(count, 256), 256, 0, st>>>(S, first_slot, first_id, count);

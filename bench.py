@@ -119,8 +119,8 @@ class ClockSampler:
 # DRAM bytes per flood-kernel launch from ncu captures (dram__bytes_read.sum +
 # dram__bytes_write.sum; profiles/flood_kernel_traffic.md), valid only for the
 # kernel sources they were taken on.
-FLOOD_TRAFFIC = {"sources_sha256": "1dabd0a5779cdcf7471b459baaab168317e8864a42e9aefd0cbe21eab8bd9d92",
-                 "shopping_centre_512": 5.94e6, "wet_2048": 93.05e6 + 20.67e6}
+FLOOD_TRAFFIC = {"sources_sha256": "30d8b4fdb1b4bb536e1cf93d39ec981d5879ee80ceee655791298f05950dd713",
+                 "shopping_centre_512": 5.94e6, "wet_2048": 92.99e6 + 20.42e6}
 FLOOD_SOURCES = ("flood.cu", "flood_dev.cuh", "fp_common.cuh")
 
 

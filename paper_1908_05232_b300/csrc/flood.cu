@@ -29,7 +29,7 @@ __global__ void __launch_bounds__(512) flood_batch_kernel(const FpSim *__restric
 
 // 16-row tiles: three CTAs per SM (65.5 KB of shared memory each, <= 42 registers)
 template <int TY>
-__global__ void __launch_bounds__(32 * TY, TY == 16 ? 3 : 1) flood_kernel(const __grid_constant__ FpTmaSet tm,
+__global__ void __launch_bounds__(32 * TY, TY == 16 ? 2 : 1) flood_kernel(const __grid_constant__ FpTmaSet tm,
                                                         const __grid_constant__ FpSim S, int par, int slot) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) unsigned long long mbar;

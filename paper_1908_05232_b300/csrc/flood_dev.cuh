@@ -287,11 +287,15 @@ __device__ __forceinline__ bool flood_tile(const FpTmaSet &tm, const FpSim &S, i
     // ghost at its domain edges -- has zero flux on every face (h* = 0 on both
     // sides), so the update leaves h = hu = hv = 0: the faces are skipped and
     // the same update runs on zero fluxes (the same bits as computing them).
-    int any = 0;
-    for (int idx = tid; idx < (TY + 2) * (FP_TX + 2); idx += NT) {
-        const int r = idx / (FP_TX + 2), cc = idx % (FP_TX + 2) + 3;
-        if (s_h[r * ROWW + cc] != 0.0f) any = 1;
-    }
+    // Checked: this thread's two cells, the west / east halo cells of its row
+    // (lanes 0 / 31) and the south / north halo rows (first / last warp) --
+    // every cell a face of the tile reads.
+    const int oA = (row + 1) * ROWW + lane + 4, oB = oA + 32;
+    int any = (s_h[oA] != 0.0f) | (s_h[oB] != 0.0f);
+    if (lane == 0) any |= s_h[oA - 1] != 0.0f;
+    if (lane == 31) any |= s_h[oB + 1] != 0.0f;
+    if (row == 0) any |= (s_h[oA - ROWW] != 0.0f) | (s_h[oB - ROWW] != 0.0f);
+    if (row == TY - 1) any |= (s_h[oA + ROWW] != 0.0f) | (s_h[oB + ROWW] != 0.0f);
     if (S.has_inflow && h_in > FP_H_EPS_F && (x0 == 0 || x0 + FP_TX >= nx || y0 == 0 || y0 + TY >= ny)) any = 1;
     const bool dry = __syncthreads_or(any) == 0;
     const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -299,7 +303,6 @@ __device__ __forceinline__ bool flood_tile(const FpTmaSet &tm, const FpSim &S, i
     // 2. faces from registers: this thread's cells A (column lane) and B (lane +
     // 32) of row `row`; each computes its west and south face.  West
     // neighbours arrive by shuffle (lane 0: the halo cell, and cell 31 for B).
-    const int oA = (row + 1) * ROWW + lane + 4, oB = oA + 32;
     const int iA = x0 + lane, iB = iA + 32;
     float4 fwA = zero4, fwB = zero4;
     if (!dry) {
@@ -373,6 +376,14 @@ __device__ __forceinline__ bool flood_tile(const FpTmaSet &tm, const FpSim &S, i
     for (int k = 0; k < 2; ++k) {
         const bool ok = k == 0 ? okA : okB;
         if (!ok) continue;
+        if (dry) {  // the zero state the update computes from zero fluxes
+            const size_t gi = gA + 32 * k;
+            S.h[p2][gi] = 0.0f;
+            S.hu[p2][gi] = 0.0f;
+            S.hv[p2][gi] = 0.0f;
+            if ((k == 0 ? occA : occB) != 0) S.occ[par][gi] = 0;
+            continue;
+        }
         const int c = lane + 32 * k;
         const int o = (row + 1) * ROWW + c + 4;
         const float4 fw = k == 0 ? fwA : fwB;

@@ -270,8 +270,8 @@ int fp_surrogate_train_step(fp_surrogate *sur, const float *x, const float *targ
  *      FP_SUR_WINDOW cells holds no water (h = 0, no inflow over the window)
  *      are dry: the plain update leaves them unchanged, so they are skipped;
  *   2. every other tile, with a FP_SUR_HALO-cell halo (a 256 x 256 input;
- *      cells past the domain edge repeat the edge cell), goes through the net: U' = U + dU, h' >= 0,
- *      no velocity where h' <= 1e-6 m;
+ *      cells past the domain edge repeat the edge cell), goes through the
+ *      net: U' = U + dU, h' >= 0, no momentum where h' < 1 mm;
  *   3. the pedestrians take the window's steps on the state at its start
  *      (coupled steps whose flood update moves no water), sandbag layers
  *      raising the bed as they complete;
@@ -283,9 +283,10 @@ int fp_surrogate_train_step(fp_surrogate *sur, const float *x, const float *targ
  *      state over the tile grown by FP_SUR_WINDOW cells (cells outside held at
  *      their start values), with the evacuee roughness of the window's end;
  *   6. every guard->check_every windows (0: never) the whole grid is recomputed
- *      by the plain update and the largest depth difference recorded; when it
- *      exceeds guard->check_tol (m), the next guard->suspend_windows windows
- *      run the plain update on every tile.
+ *      by the plain update and the largest depth difference over the net
+ *      tiles the guard accepted is recorded (rejected tiles take the plain
+ *      result anyway); when it exceeds guard->check_tol (m), the next
+ *      guard->suspend_windows windows run the plain update on every tile.
  * Stops before a window that would cross t_end.  *stats accumulates (zero it
  * before the first call).  Synchronises the stream. */
 #define FP_SUR_TILE 246  /* output cells per tile side: the net's input tile, halo included, is 256 x 256 */
@@ -307,7 +308,7 @@ typedef struct fp_surrogate_stats {
     int64_t checks;           /* plain checks */
     int64_t checks_failed;    /* checks over check_tol */
     double max_residual;      /* largest guard mass residual of a net tile */
-    double max_check_error;   /* largest depth difference at a check (m) */
+    double max_check_error;   /* largest depth difference of accepted net tiles at a check (m) */
 } fp_surrogate_stats;
 int fp_surrogate_advance(fp_sim *sim, fp_surrogate *sur, int32_t n_windows, const fp_surrogate_guard *guard,
                          fp_surrogate_stats *stats);

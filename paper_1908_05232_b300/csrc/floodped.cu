@@ -121,13 +121,15 @@ struct fp_sim {
         unsigned short *fb_occ = nullptr;   // evacuees per cell for the fallback
         FpClock *clock = nullptr;           // fallback clock ring; the start clock at the window's slot
         double *bflux = nullptr;            // fallback boundary volumes (discarded)
-        unsigned char *wet = nullptr, *fail = nullptr, *flag = nullptr, *mask = nullptr;
+        unsigned char *wet = nullptr, *fail = nullptr, *flag = nullptr, *mask = nullptr, *keep = nullptr;
         int *list = nullptr, *batch_of = nullptr, *count = nullptr;  // count[0] net tiles, count[1] failed
         float *resid = nullptr;
         unsigned *maxdiff = nullptr;
         void *x16 = nullptr;                // net input [tiles][266][266][16] BF16
         float *dU = nullptr;                // net output [tiles][256][256][3]
         FpTmaSet tma[2];
+        cudaStream_t net_stream = nullptr;  // the net runs here, beside the window's pedestrian steps
+        cudaEvent_t ev_start = nullptr, ev_input = nullptr, ev_net = nullptr;
         long long done = 0;                 // windows advanced (check cadence)
         int suspend = 0;                    // windows left on the plain update
     } win;
@@ -317,6 +319,7 @@ static int ensure_window(fp_sim *s) {
     ok &= (W.wet = s->dalloc<unsigned char>(nt)) != nullptr;
     ok &= (W.fail = s->dalloc<unsigned char>(nt)) != nullptr;
     ok &= (W.flag = s->dalloc<unsigned char>(nt)) != nullptr;
+    ok &= (W.keep = s->dalloc<unsigned char>(nt)) != nullptr;
     ok &= (W.mask = s->dalloc<unsigned char>(W.ftiles)) != nullptr;
     ok &= (W.list = s->dalloc<int>(nt)) != nullptr;
     ok &= (W.batch_of = s->dalloc<int>(nt)) != nullptr;
@@ -334,6 +337,11 @@ static int ensure_window(fp_sim *s) {
     }
     const int rc = encode_tma_rows(s, s->tile_rows, W.tma, &F);
     if (rc != FP_OK) return rc;
+    if (cudaStreamCreateWithFlags(&W.net_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&W.ev_start, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&W.ev_input, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&W.ev_net, cudaEventDisableTiming) != cudaSuccess)
+        return s->fail(FP_ECUDA, "surrogate window stream");
     W.ready = true;
     return FP_OK;
 }
@@ -821,7 +829,7 @@ int fp_surrogate_advance(fp_sim *s, fp_surrogate *sur, int32_t n_windows, const 
     const int kIn = FP_SUR_TILE + 2 * FP_SUR_HALO;
     const size_t pbytes = s->plane_elems() * sizeof(float);
     const int ftx = (S.nx + FP_TX - 1) / FP_TX, fty = (S.ny + s->tile_rows - 1) / s->tile_rows;
-    std::vector<unsigned char> flag(nt), fail(nt), mask(W.ftiles);
+    std::vector<unsigned char> flag(nt), fail(nt), mask(W.ftiles), keep(nt);
     std::vector<int> list(nt);
     std::vector<float> resid(nt);
     cudaError_t e = cudaSuccess;
@@ -846,9 +854,17 @@ int fp_surrogate_advance(fp_sim *s, fp_surrogate *sur, int32_t n_windows, const 
             e = s->copy(&count, W.count, sizeof(int));
             if (e != cudaSuccess) return s->cuda_fail(e, "window tile count");
             if (count > 0) {
-                fp_launch_sur_input(S, W.u0[0], W.u0[1], W.u0[2], W.list, count, W.tiles_x, W.x16, s->stream);
-                e = fp_sur_forward_packed(sur, W.x16, count, kIn, kIn, W.dU, s->stream);
+                // the net on its own stream, beside the pedestrian steps: both
+                // read only the start state (the input packing reads z before
+                // the steps may raise it)
+                cudaEventRecord(W.ev_start, s->stream);
+                cudaStreamWaitEvent(W.net_stream, W.ev_start, 0);
+                fp_launch_sur_input(S, W.u0[0], W.u0[1], W.u0[2], W.list, count, W.tiles_x, W.x16, W.net_stream);
+                cudaEventRecord(W.ev_input, W.net_stream);
+                e = fp_sur_forward_packed(sur, W.x16, count, kIn, kIn, W.dU, W.net_stream);
                 if (e != cudaSuccess) return s->cuda_fail(e, "surrogate forward");
+                cudaEventRecord(W.ev_net, W.net_stream);
+                cudaStreamWaitEvent(s->stream, W.ev_input, 0);
             }
         }
         // 3. pedestrians over the window on the start state
@@ -860,7 +876,9 @@ int fp_surrogate_advance(fp_sim *s, fp_surrogate *sur, int32_t n_windows, const 
         }
         // 4. apply the net's change, guard
         std::fill(flag.begin(), flag.end(), (unsigned char)(plain || check ? 1 : 0));
+        std::fill(keep.begin(), keep.end(), (unsigned char)0);  // net tiles the guard accepted
         if (count > 0) {
+            cudaStreamWaitEvent(s->stream, W.ev_net, 0);
             cudaMemsetAsync(W.count + 1, 0, sizeof(int), s->stream);
             fp_launch_sur_apply(S, par, W.u0[0], W.u0[1], W.u0[2], W.dU, W.list, W.batch_of, count, W.tiles_x,
                                 &W.clock[slot], guard->mass_tol, W.fail, W.resid, W.count + 1, s->stream);
@@ -870,6 +888,7 @@ int fp_surrogate_advance(fp_sim *s, fp_surrogate *sur, int32_t n_windows, const 
             if (e != cudaSuccess) return s->cuda_fail(e, "window guard");
             for (int b = 0; b < count; ++b) {
                 st->max_residual = std::max(st->max_residual, (double)resid[b]);
+                keep[list[b]] = fail[b] ? 0 : 1;
                 if (fail[b]) {
                     flag[list[b]] = 1;
                     st->tiles_fallback += 1;
@@ -926,9 +945,13 @@ int fp_surrogate_advance(fp_sim *s, fp_surrogate *sur, int32_t n_windows, const 
                 sl = (sl + 1) & 3;
             }
             if (check) {
+                // the error of what the surrogate path keeps: net tiles the guard
+                // accepted (rejected ones are replaced by the plain result)
                 unsigned bits = 0;
+                e = s->copy(W.keep, keep.data(), nt);
+                if (e != cudaSuccess) return s->cuda_fail(e, "check tiles");
                 cudaMemsetAsync(W.maxdiff, 0, sizeof(unsigned), s->stream);
-                fp_launch_sur_diff(S, S.h[par], W.fb[par][0], W.maxdiff, s->stream);
+                fp_launch_sur_diff(S, S.h[par], W.fb[par][0], W.keep, W.tiles_x, W.maxdiff, s->stream);
                 e = s->copy(&bits, W.maxdiff, sizeof(unsigned));
                 if (e != cudaSuccess) return s->cuda_fail(e, "plain check");
                 float err;
@@ -1250,6 +1273,7 @@ int fp_destroy(fp_sim *s) {
     if (!s) return FP_EINVAL;
     if (s->stream) cudaStreamSynchronize(s->stream);
     if (s->stream2) cudaStreamSynchronize(s->stream2);
+    if (s->win.net_stream) cudaStreamSynchronize(s->win.net_stream);
     s->drop_graphs();
     for (void *p : s->allocs) cudaFree(p);
     if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
@@ -1257,6 +1281,9 @@ int fp_destroy(fp_sim *s) {
     if (s->ev_fork) cudaEventDestroy(s->ev_fork);
     if (s->ev_join) cudaEventDestroy(s->ev_join);
     for (cudaEvent_t e : s->prof_ev) cudaEventDestroy(e);
+    if (s->win.net_stream) cudaStreamDestroy(s->win.net_stream);
+    for (cudaEvent_t e : {s->win.ev_start, s->win.ev_input, s->win.ev_net})
+        if (e) cudaEventDestroy(e);
     delete s;
     return FP_OK;
 }

@@ -278,6 +278,7 @@ void fp_launch_sur_apply(const FpSim &S, int par, const float *h0, const float *
                          const FpClock *c0, float mass_tol, unsigned char *fail, float *resid, int *n_fail,
                          cudaStream_t st);
 void fp_launch_sur_occupancy(const FpSim &S, unsigned short *occ, cudaStream_t st);
-void fp_launch_sur_diff(const FpSim &S, const float *a, const float *b, unsigned *max_bits, cudaStream_t st);
+void fp_launch_sur_diff(const FpSim &S, const float *a, const float *b, const unsigned char *keep, int tiles_x,
+                        unsigned *max_bits, cudaStream_t st);
 void fp_launch_sur_merge(const FpSim &S, int par, const float *h, const float *hu, const float *hv,
                          const unsigned char *flags, int tiles_x, int tiles_y, cudaStream_t st);

@@ -313,13 +313,16 @@ __global__ void occupancy_kernel(const __grid_constant__ FpSim S, unsigned short
     }
 }
 
-// largest |a - b| over the cells (float bits; NaN counts as infinity)
+// largest |a - b| over the cells of the tiles with keep[tile] != 0 (float bits;
+// NaN counts as infinity)
 __global__ void diff_kernel(const __grid_constant__ FpSim S, const float *__restrict__ a, const float *__restrict__ b,
-                            unsigned *max_bits) {
+                            const unsigned char *__restrict__ keep, int tiles_x, unsigned *max_bits) {
     float m = 0.0f;
     const long long n = (long long)S.nx * S.ny;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
-        const size_t o = fp_pidx(S, (int)(c % S.nx), (int)(c / S.nx));
+        const int i = (int)(c % S.nx), j = (int)(c / S.nx);
+        if (!keep[(j / kT) * tiles_x + i / kT]) continue;
+        const size_t o = fp_pidx(S, i, j);
         const float d = fabsf(a[o] - b[o]);
         m = fmaxf(m, d == d ? d : __int_as_float(0x7f800000));
     }
@@ -381,8 +384,9 @@ void fp_launch_sur_occupancy(const FpSim &S, unsigned short *occ, cudaStream_t s
     occupancy_kernel<<<148 * 4, 256, 0, st>>>(S, occ);
 }
 
-void fp_launch_sur_diff(const FpSim &S, const float *a, const float *b, unsigned *max_bits, cudaStream_t st) {
-    diff_kernel<<<148 * 8, 256, 0, st>>>(S, a, b, max_bits);
+void fp_launch_sur_diff(const FpSim &S, const float *a, const float *b, const unsigned char *keep, int tiles_x,
+                        unsigned *max_bits, cudaStream_t st) {
+    diff_kernel<<<148 * 8, 256, 0, st>>>(S, a, b, keep, tiles_x, max_bits);
 }
 
 void fp_launch_sur_merge(const FpSim &S, int par, const float *h, const float *hu, const float *hv,

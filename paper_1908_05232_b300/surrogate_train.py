@@ -2,7 +2,10 @@
 paper has no surrogate).
 
 Data: trajectories of the plain coupled step at a fixed time step on seeded
-shopping-centre scenarios (the stand-in for the paper's shopping centre).  A
+shopping-centre scenarios (the stand-in for the paper's shopping centre):
+512x512 centres with 10,000 evacuees and 2048x2048 centres with 100,000
+pedestrians building a sandbag barrier, flooded from t = 900 s (pairs taken
+from mid-flood on).  A
 sample pairs the state U = (h, hu, hv) and bed z at some step with the change
 of U over the next FP_SUR_WINDOW steps.  Training crops are 32 x 32 cells of
 that change with the 5-cell halo of (h, hu, hv, z) around them; cells past the
@@ -34,14 +37,21 @@ def _torch():
     return torch
 
 
-def trajectory_pairs(sc, dt=DT_DEFAULT, every=256, n_pairs=64, skip_steps=0, device="cuda"):
+def trajectory_pairs(sc, dt=DT_DEFAULT, every=256, n_pairs=64, skip_steps=0, device="cuda", cfl_until=None):
     """Run the plain coupled step on scenario ``sc`` at a fixed step dt and return
     a list of (x, d) device tensors: x = (h, hu, hv, z) [ny+10, nx+10, 4] with
-    edge-repeating halo, d = change of (h, hu, hv) over WINDOW steps [ny, nx, 3]."""
+    edge-repeating halo, d = change of (h, hu, hv) over WINDOW steps [ny, nx, 3].
+    cfl_until: first advance with the CFL step to this simulated time (s)."""
     torch = _torch()
-    sc.dt_fixed_ticks = int(round(dt * N.TICKS))
-    sim = N.from_scenario(sc)
-    z = torch.from_numpy(np.ascontiguousarray(sc.z, np.float32)).to(device)
+    if cfl_until is not None:
+        sc.dt_fixed_ticks = 0
+        sim = N.from_scenario(sc)
+        while sim.counters()["t_ticks"] < int(cfl_until * N.TICKS):
+            sim.step(256)
+        sim.set_fixed_dt(dt)
+    else:
+        sc.dt_fixed_ticks = int(round(dt * N.TICKS))
+        sim = N.from_scenario(sc)
     out = []
 
     def read():
@@ -60,6 +70,8 @@ def trajectory_pairs(sc, dt=DT_DEFAULT, every=256, n_pairs=64, skip_steps=0, dev
         u0 = read()
         sim.step(WINDOW)
         u1 = read()
+        z = torch.empty((sc.ny, sc.nx), dtype=torch.float32, device=device)
+        N.fp_read_state(sim.h, N.FP_FIELD_Z, z)  # barrier layers included
         x = torch.cat([u0, z[..., None]], dim=-1).permute(2, 0, 1)[None]
         x = torch.nn.functional.pad(x, (HALO, HALO, HALO, HALO), mode="replicate")[0].permute(1, 2, 0).contiguous()
         out.append((x, (u1 - u0).contiguous()))
@@ -155,6 +167,10 @@ def main(argv=None):
     ap.add_argument("--every", type=int, default=512)
     ap.add_argument("--dt", type=float, default=DT_DEFAULT)
     ap.add_argument("--init-seed", type=int, default=0)
+    ap.add_argument("--barrier-seeds", default="4,5", help="2048x2048 barrier scenarios (empty: none)")
+    ap.add_argument("--barrier-pairs", type=int, default=24)
+    ap.add_argument("--barrier-start", type=float, default=1000.0)
+    ap.add_argument("--barrier-every", type=int, default=1536)
     args = ap.parse_args(argv)
     t0 = time.time()
     pairs = []
@@ -164,6 +180,12 @@ def main(argv=None):
         pr, c = trajectory_pairs(sc, args.dt, args.every, args.pairs)
         print("seed %d peak %.1f: %d pairs, %d steps over the Courant limit" % (seed, peak, len(pr),
                                                                               c["cfl_exceeded"]), flush=True)
+        pairs += pr
+    for seed in [int(v) for v in args.barrier_seeds.split(",") if v]:
+        pr, c = trajectory_pairs(S.config_barrier(seed), args.dt, args.barrier_every, args.barrier_pairs,
+                                 cfl_until=args.barrier_start)
+        print("barrier 2048 seed %d: %d pairs from t = %.0f s, %d steps over the Courant limit"
+              % (seed, len(pr), args.barrier_start, c["cfl_exceeded"]), flush=True)
         pairs += pr
     print("data %.1f s" % (time.time() - t0), flush=True)
     sur = N.Surrogate(seed=args.init_seed)

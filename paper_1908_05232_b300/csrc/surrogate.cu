@@ -22,6 +22,7 @@
 // Training (A13): the backward pass (data and weight gradients of every
 // layer, FP32 on the CUDA cores, deterministic reductions), the loss and Adam
 // with FP32 master weights.
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -42,7 +43,6 @@ constexpr int kWidth = 32;
 constexpr int kCin0 = 16;   // first layer: 8 real input channels padded to 16
 constexpr int kCout4 = 16;  // last layer: 3 real output channels padded to 16
 constexpr int kSeg = 128;   // output pixels per MMA (M)
-constexpr int kConvThreads = 128;
 constexpr float kOutScale = FP_SUR_OUT_SCALE;  // the net predicts delta U / 2^-10
 // The first layer sees each of (h, hu, hv, z) as two BF16 numbers, the rounded
 // value and the rounded remainder (channels 0-3 and 4-7): its FP32 accumulation
@@ -69,18 +69,22 @@ __host__ __device__ constexpr unsigned umma_idesc(int M, int N) {
 }
 
 constexpr int kStripRows = 32;  // output rows per work item (one column segment of one image)
-constexpr int kRing = 5;        // staged input rows: the MMA's 3, the next MMA's new one, one loading
+constexpr int kRing = 6;        // staged input rows in the ring
+constexpr int kEpiWarps = 8;    // epilogue warps: TMEM lane quarter w % 4, column half w / 4
+constexpr int kConvWarps = kEpiWarps + 2;  // + one TMA producer warp + one MMA issuer warp
+constexpr int kAcc = 4;         // TMEM accumulators (32 columns each): rows in flight between issuer and epilogue
 
 template <int CIN, int COUT>
 struct ConvGeom {
     static constexpr int KC = CIN / 16;            // K chunks of 16 channels
     static constexpr int NKC = CIN / 8;            // 16-byte k-cores per pixel
     static constexpr int NPIX = kSeg + 2;          // staged input pixels per row
-    static constexpr int ROWB = NKC * NPIX * 16;   // bytes per staged input row
+    static constexpr int ROWB = NKC * NPIX * 16;   // bytes of one staged row (one TMA box)
+    static constexpr int SLOT = (ROWB + 127) / 128 * 128;  // ring slot stride (TMA destinations 128-B aligned)
     static constexpr int WBLK = 2 * COUT * 16;     // bytes per (tap, chunk) weight block
-    static constexpr int WB = 9 * KC * WBLK;       // weight bytes
+    static constexpr int WB = 9 * KC * WBLK;       // weight bytes (a multiple of 128)
     // guard region after the operands (a descriptor-field error reads garbage inside the allocation)
-    static constexpr int SMEM = ((WB + kRing * ROWB + 2048) + 1023) / 1024 * 1024;
+    static constexpr int SMEM = ((WB + kRing * SLOT + 2048) + 1023) / 1024 * 1024;
 };
 
 __device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity) {
@@ -94,19 +98,31 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity)
     return ok != 0;
 }
 
+// the same, giving up early once another role has flagged an abort
+__device__ __forceinline__ bool mbar_wait_or_abort(unsigned bar, unsigned parity, const volatile int *abort_flag) {
+    unsigned ok = 0;
+    for (int it = 0; it < (1 << 22) && !ok; ++it) {
+        asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+                     : "=r"(ok)
+                     : "r"(bar), "r"(parity)
+                     : "memory");
+        if (!ok && (it & 255) == 255 && *abort_flag) break;
+    }
+    return ok != 0;
+}
+
+__device__ __forceinline__ void mbar_init_n(unsigned bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+
 template <int N>
 __device__ __forceinline__ void tmem_load(unsigned taddr, unsigned (&r)[N]);
 
 template <>
-__device__ __forceinline__ void tmem_load<32>(unsigned taddr, unsigned (&r)[32]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
+__device__ __forceinline__ void tmem_load<8>(unsigned taddr, unsigned (&r)[8]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
@@ -121,173 +137,241 @@ __device__ __forceinline__ void tmem_load<16>(unsigned taddr, unsigned (&r)[16])
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// 16-byte asynchronous global -> shared copy; bytes = 0 fills the 16 bytes with zeros
-__device__ __forceinline__ void cp_async16(unsigned dst, const void *src, unsigned bytes) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-
 // One 3x3 valid convolution of B images (NHWC, BF16, CIN channels) with the
 // packed weights (9 taps x CIN/16 chunks of [2 k-cores][COUT rows][8] BF16).
 // Hidden layers: bias + ReLU, BF16 output with COUT channels.  Last layer
 // (LAST): bias, FP32 output with 3 channels, times kOutScale.
 //
 // Work item: one column segment (128 output pixels) of up to kStripRows
-// consecutive output rows of one image.  The CTA keeps a ring of kRing staged
-// input rows ([k-core][pixel][8 channels]), filled by cp.async one row ahead,
-// so each output row stages one new input row; two TMEM accumulators (32
-// columns each) let the MMAs of row r+1 run while the four warps read row r's
-// accumulator for the epilogue.  Per output row r:
-//   stage input row r+4 (async) | wait for input row r+3 | sync
-//   thread 0 issues row r+1's MMAs (input rows r+1..r+3) -> accumulator (r+1)&1
-//   wait for row r's MMAs (bounded) | epilogue of row r from accumulator r&1
+// consecutive output rows of one image.  Warp-specialised pipeline, hand-offs
+// by mbarriers only (every wait bounded):
+//   producer warp (one thread): one TMA per input row into a ring of kRing slots --
+//     the 5-D tensor map (8 channels, pixel, k-core, row, image) lands the row
+//     as [k-core][pixel][8 channels], the MMA's canonical K-major layout;
+//     a slot is refilled once the MMAs that read it completed (free[slot]);
+//   issuer warp (one thread): for output row r, once input rows r..r+2
+//     landed (full[]) and accumulator r % kAcc is free (empty[]), issues the
+//     18 MMAs (9 taps x 2 k-chunks of 16; the three horizontal taps of a row
+//     are the same operand shifted by one pixel; descriptors precomputed) and
+//     commits them to acc_full[r % kAcc] and to free[] of the input row no
+//     later row reads;
+//   epilogue warps (8): wait acc_full, read their TMEM lane quarter and
+//     column half (tcgen05.ld), free the accumulator (empty[]), then bias /
+//     ReLU / BF16 and the stores.
 template <int CIN, int COUT, bool LAST>
-__global__ void __launch_bounds__(kConvThreads) conv3x3_tc_kernel(const __nv_bfloat16 *__restrict__ x, int B, int H,
-                                                                  int W, const __nv_bfloat16 *__restrict__ wpack,
-                                                                  const float *__restrict__ bias, void *__restrict__ y,
-                                                                  unsigned *err) {
+__global__ void __launch_bounds__(kConvWarps * 32) conv3x3_tc_kernel(const __grid_constant__ CUtensorMap tmap, int B,
+                                                                     int H, int W,
+                                                                     const __nv_bfloat16 *__restrict__ wpack,
+                                                                     const float *__restrict__ bias,
+                                                                     void *__restrict__ y, unsigned *err) {
     using G = ConvGeom<CIN, COUT>;
     extern __shared__ __align__(1024) unsigned char sm[];
     unsigned char *s_w = sm;
     unsigned char *s_x = sm + G::WB;
-    __shared__ __align__(8) unsigned long long mbar[2];
+    __shared__ __align__(8) unsigned long long bar_full[kRing], bar_free[kRing], bar_accf[kAcc], bar_acce[kAcc];
     __shared__ unsigned s_taddr;
+    __shared__ volatile int s_abort;
+    __shared__ float s_bias[COUT];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int Ho = H - 2, Wo = W - 2;
     const int segs = (Wo + kSeg - 1) / kSeg;
     const int chunks = (Ho + kStripRows - 1) / kStripRows;
     const int items = B * segs * chunks;
     constexpr unsigned IDESC = umma_idesc(kSeg, COUT);
+    if (tid < COUT) s_bias[tid] = bias[tid];
 
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(sm_addr(&s_taddr)));
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sm_addr(&s_taddr)),
+                     "n"(kAcc * 32));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sm_addr(&mbar[0])));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sm_addr(&mbar[1])));
+        for (int k = 0; k < kRing; ++k) {
+            mbar_init_n(sm_addr(&bar_full[k]), 1);
+            mbar_init_n(sm_addr(&bar_free[k]), 1);
+        }
+        for (int a = 0; a < kAcc; ++a) {
+            mbar_init_n(sm_addr(&bar_accf[a]), 1);
+            mbar_init_n(sm_addr(&bar_acce[a]), kEpiWarps);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_abort = 0;
     }
-    for (int i = tid; i < G::WB / 16; i += kConvThreads)
+    for (int i = tid; i < G::WB / 16; i += kConvWarps * 32)
         reinterpret_cast<uint4 *>(s_w)[i] = reinterpret_cast<const uint4 *>(wpack)[i];
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const unsigned taddr = s_taddr;
     const unsigned xs = sm_addr(s_x), ws = sm_addr(s_w);
-    unsigned phases = 0u;  // bit k: phase parity of mbar[k]
-    bool ok = true;
+    auto fail = [&]() {
+        atomicOr(err, FP_ERR_TIMEOUT);
+        s_abort = 1;
+    };
 
-    for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
-        const int img = item / (segs * chunks);
-        const int rem = item % (segs * chunks);
-        const int ox0 = (rem / chunks) * kSeg, oy0 = (rem % chunks) * kStripRows;
-        const int nrow = min(kStripRows, Ho - oy0);
-        const __nv_bfloat16 *xin = x + (size_t)img * H * W * CIN;
-        // input row iy (image row oy0 + iy) into ring slot iy % kRing
-        auto stage = [&](int iy) {
-            const unsigned dst = xs + (iy % kRing) * G::ROWB;
-            const __nv_bfloat16 *row = xin + (size_t)(oy0 + iy) * W * CIN;
-            for (int u = tid; u < G::NKC * G::NPIX; u += kConvThreads) {
-                const int j = u / G::NPIX, p = u % G::NPIX;
-                const int ix = ox0 + p;
-                const bool in = ix < W;
-                cp_async16(dst + (j * G::NPIX + p) * 16, row + (size_t)(in ? ix : 0) * CIN + j * 8, in ? 16u : 0u);
-            }
-        };
-        // the MMAs of output row r (input rows r .. r+2) into accumulator r & 1
-        auto issue = [&](int r) {
-            if (tid != 0) return;
-            const unsigned acc_col = (unsigned)(r & 1) * 32u;
-#pragma unroll 1
-            for (int t = 0; t < 9; ++t) {
-                const int ky = t / 3, kx = t % 3;
-                const unsigned rowa = xs + ((r + ky) % kRing) * G::ROWB;
-#pragma unroll
-                for (int c = 0; c < G::KC; ++c) {
-                    const unsigned a = rowa + (2 * c) * (G::NPIX * 16) + kx * 16;
-                    const unsigned b = ws + (t * G::KC + c) * G::WBLK;
-                    const unsigned long long ad = umma_desc(a, G::NPIX * 16, 128);
-                    const unsigned long long bd = umma_desc(b, COUT * 16, 128);
-                    const unsigned acc = (t | c) != 0 ? 1u : 0u;
+    if (warp == kEpiWarps) {
+        // ---- TMA producer: one copy per input row segment; the 5-D tensor
+        // map lands it as [k-core][pixel][8 channels]
+        if (lane == 0) {
+            unsigned q = 0;  // input rows issued by this CTA
+            for (int item = blockIdx.x; item < items && !s_abort; item += gridDim.x) {
+                const int img = item / (segs * chunks), rem = item % (segs * chunks);
+                const int ox0 = (rem / chunks) * kSeg, oy0 = (rem % chunks) * kStripRows;
+                const int nrow = min(kStripRows, Ho - oy0);
+                bool ok = true;
+                for (int i = 0; i < nrow + 2; ++i, ++q) {
+                    const unsigned slot = q % kRing, use = q / kRing;
+                    if (use > 0 && !mbar_wait_or_abort(sm_addr(&bar_free[slot]), (use - 1) & 1u, &s_abort)) {
+                        fail();
+                        ok = false;
+                        break;
+                    }
+                    const unsigned fb = sm_addr(&bar_full[slot]);
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(G::ROWB)
+                                 : "memory");
                     asm volatile(
-                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(taddr + acc_col),
-                        "l"(ad), "l"(bd), "r"(IDESC), "r"(acc)
+                        "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
+                        "%3, %4, %5, %6}], [%7];" ::"r"(xs + slot * G::SLOT),
+                        "l"(reinterpret_cast<unsigned long long>(&tmap)), "r"(0), "r"(ox0), "r"(0), "r"(oy0 + i),
+                        "r"(img), "r"(fb)
                         : "memory");
                 }
+                if (!ok) break;
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             sm_addr(&mbar[r & 1]))
-                         : "memory");
-        };
-        // prologue: input rows 0..2, then 3; row 0's MMAs
-        stage(0);
-        stage(1);
-        stage(2);
-        cp_async_commit();
-        if (nrow > 1) stage(3);
-        cp_async_commit();
-        cp_async_wait<1>();
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        issue(0);
-        for (int r = 0; r < nrow; ++r) {
-            if (r + 4 < nrow + 2) stage(r + 4);
-            cp_async_commit();
-            cp_async_wait<1>();  // input row r+3 has landed
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            __syncthreads();
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            if (r + 1 < nrow) issue(r + 1);
-            const bool done = mbar_wait_bounded(sm_addr(&mbar[r & 1]), (phases >> (r & 1)) & 1u);
-            phases ^= 1u << (r & 1);
-            if (!__syncthreads_and(done)) {
-                if (tid == 0) atomicOr(err, FP_ERR_TIMEOUT);
-                ok = false;
-                break;
+            // no copy of this CTA may still be landing when it exits
+            const unsigned n = q < (unsigned)kRing ? q : (unsigned)kRing;
+            for (unsigned k = 0; k < n; ++k) {
+                const unsigned qq = q - 1 - k;
+                mbar_wait_bounded(sm_addr(&bar_full[qq % kRing]), (qq / kRing) & 1u);
             }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            // epilogue: warp w owns TMEM lanes (output pixels) 32w .. 32w+31
-            const int oy = oy0 + r, ox = ox0 + 32 * warp + lane;
-            unsigned v[COUT];
-            tmem_load<COUT>(taddr + ((unsigned)(32 * warp) << 16) + (unsigned)(r & 1) * 32u, v);
-            if (ox < Wo) {
-                const size_t pix = ((size_t)img * Ho + oy) * Wo + ox;
-                if constexpr (LAST) {
-                    float *yo = static_cast<float *>(y) + pix * 3;
+        }
+    } else if (warp == kEpiWarps + 1) {
+        // ---- MMA issuer.  A descriptor's start-address field is its low bits,
+        // so the descriptor of base + d is the base descriptor + d / 16 (every
+        // shared address here is below 256 KB): the weight descriptors are
+        // fixed, and an input descriptor is one add.
+        if (lane == 0) {
+            unsigned long long bdesc[9 * G::KC];
 #pragma unroll
-                    for (int co = 0; co < 3; ++co) yo[co] = (__uint_as_float(v[co]) + bias[co]) * kOutScale;
-                } else {
-                    __nv_bfloat16 *yo = static_cast<__nv_bfloat16 *>(y) + pix * COUT;
+            for (int k = 0; k < 9 * G::KC; ++k) bdesc[k] = umma_desc(ws + k * G::WBLK, COUT * 16, 128);
+            const unsigned long long adesc0 = umma_desc(xs, G::NPIX * 16, 128);
+            unsigned q0 = 0, g = 0;  // first input row of the item, output rows issued
+            bool ok = true;
+            for (int item = blockIdx.x; item < items && ok && !s_abort; item += gridDim.x) {
+                const int rem = item % (segs * chunks);
+                const int oy0 = (rem % chunks) * kStripRows;
+                const int nrow = min(kStripRows, Ho - oy0);
+                for (int r = 0; r < nrow && ok; ++r, ++g) {
+                    for (int t = 0; t < 3 && ok; ++t) {
+                        const unsigned qq = q0 + r + t;
+                        ok = mbar_wait_or_abort(sm_addr(&bar_full[qq % kRing]), (qq / kRing) & 1u, &s_abort);
+                    }
+                    const unsigned a = g % kAcc;
+                    if (ok && g >= kAcc) ok = mbar_wait_or_abort(sm_addr(&bar_acce[a]), (g / kAcc - 1) & 1u, &s_abort);
+                    if (!ok) {
+                        fail();
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    unsigned slot_off[3];
 #pragma unroll
-                    for (int q = 0; q < COUT / 8; ++q) {
-                        __nv_bfloat162 o[4];
+                    for (int ky = 0; ky < 3; ++ky) slot_off[ky] = ((q0 + r + ky) % kRing) * (G::SLOT / 16);
+                    const unsigned dcol = taddr + a * 32u;
 #pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            const float a0 = fmaxf(__uint_as_float(v[8 * q + 2 * e]) + bias[8 * q + 2 * e], 0.0f);
-                            const float a1 =
-                                fmaxf(__uint_as_float(v[8 * q + 2 * e + 1]) + bias[8 * q + 2 * e + 1], 0.0f);
-                            o[e] = __floats2bfloat162_rn(a0, a1);
+                    for (int t = 0; t < 9; ++t) {
+                        const int ky = t / 3, kx = t % 3;
+#pragma unroll
+                        for (int c = 0; c < G::KC; ++c) {
+                            const unsigned long long ad =
+                                adesc0 + slot_off[ky] + (unsigned)((2 * c * G::NPIX * 16 + kx * 16) / 16);
+                            const unsigned acc = (t | c) != 0 ? 1u : 0u;
+                            asm volatile(
+                                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dcol),
+                                "l"(ad), "l"(bdesc[t * G::KC + c]), "r"(IDESC), "r"(acc)
+                                : "memory");
                         }
-                        *reinterpret_cast<uint4 *>(yo + 8 * q) = *reinterpret_cast<const uint4 *>(o);
+                    }
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                     sm_addr(&bar_accf[a]))
+                                 : "memory");
+                    // input row q0 + r is read by no later output row
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                     sm_addr(&bar_free[(q0 + r) % kRing]))
+                                 : "memory");
+                    if (r == nrow - 1) {  // the item's last two input rows
+                        asm volatile(
+                            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                sm_addr(&bar_free[(q0 + nrow) % kRing]))
+                            : "memory");
+                        asm volatile(
+                            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                sm_addr(&bar_free[(q0 + nrow + 1) % kRing]))
+                            : "memory");
+                    }
+                }
+                q0 += nrow + 2;
+            }
+        }
+    } else {
+        // ---- epilogue: warp w owns TMEM lanes (output pixels) 32 (w % 4) ..
+        // 32 (w % 4) + 31 and accumulator columns 16 (w / 4) .. + 15 (the
+        // last layer: warps 0-3, its three channels)
+        constexpr int HALF = COUT / 2;
+        const int quarter = warp & 3, half = warp >> 2;
+        unsigned g = 0;
+        bool ok = true;
+        for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
+            const int img = item / (segs * chunks), rem = item % (segs * chunks);
+            const int ox0 = (rem / chunks) * kSeg, oy0 = (rem % chunks) * kStripRows;
+            const int nrow = min(kStripRows, Ho - oy0);
+            for (int r = 0; r < nrow; ++r, ++g) {
+                const unsigned a = g % kAcc;
+                ok = mbar_wait_or_abort(sm_addr(&bar_accf[a]), (g / kAcc) & 1u, &s_abort);
+                if (!__all_sync(0xffffffffu, ok)) {
+                    ok = false;
+                    if (lane == 0) fail();
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                unsigned v[HALF];
+                const bool active = !LAST || half == 0;
+                if (active)
+                    tmem_load<HALF>(taddr + ((unsigned)(32 * quarter) << 16) + a * 32u + (unsigned)(half * HALF), v);
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sm_addr(&bar_acce[a])) : "memory");
+                const int oy = oy0 + r, ox = ox0 + 32 * quarter + lane;
+                if (active && ox < Wo) {
+                    const size_t pix = ((size_t)img * Ho + oy) * Wo + ox;
+                    if constexpr (LAST) {
+                        float *yo = static_cast<float *>(y) + pix * 3;
+#pragma unroll
+                        for (int co = 0; co < 3; ++co) yo[co] = (__uint_as_float(v[co]) + s_bias[co]) * kOutScale;
+                    } else {
+                        __nv_bfloat16 *yo = static_cast<__nv_bfloat16 *>(y) + pix * COUT + half * HALF;
+                        const float *bb = s_bias + half * HALF;
+#pragma unroll
+                        for (int qd = 0; qd < HALF / 8; ++qd) {
+                            __nv_bfloat162 o[4];
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                const float a0 = fmaxf(__uint_as_float(v[8 * qd + 2 * e]) + bb[8 * qd + 2 * e], 0.0f);
+                                const float a1 =
+                                    fmaxf(__uint_as_float(v[8 * qd + 2 * e + 1]) + bb[8 * qd + 2 * e + 1], 0.0f);
+                                o[e] = __floats2bfloat162_rn(a0, a1);
+                            }
+                            *reinterpret_cast<uint4 *>(yo + 8 * qd) = *reinterpret_cast<const uint4 *>(o);
+                        }
                     }
                 }
             }
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         }
-        cp_async_wait<0>();
-        __syncthreads();
     }
-    cp_async_wait<0>();
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(taddr));
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "n"(kAcc * 32));
 }
 
 // FP32 (h, hu, hv, z) images -> BF16 NHWC with 16 channels: 0-3 the rounded
@@ -476,6 +560,36 @@ struct fp_surrogate {
 
 namespace {
 
+PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void *p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// 5-D view of an NHWC BF16 activation [B][H][W][CIN]: (8 channels, pixel,
+// k-core, row, image); a box of (8, kSeg + 2, CIN / 8, 1, 1) is one staged input
+// row segment in the [k-core][pixel][8 channels] layout.
+template <int CIN>
+cudaError_t encode_act_map(CUtensorMap *m, const __nv_bfloat16 *x, int B, int H, int W) {
+    auto enc = tmap_encoder();
+    if (!enc) return cudaErrorNotSupported;
+    const cuuint64_t dims[5] = {8, (cuuint64_t)W, (cuuint64_t)(CIN / 8), (cuuint64_t)H, (cuuint64_t)B};
+    const cuuint64_t strides[4] = {(cuuint64_t)CIN * 2, 16, (cuuint64_t)W * CIN * 2, (cuuint64_t)H * W * CIN * 2};
+    const cuuint32_t box[5] = {8, (cuuint32_t)(kSeg + 2), (cuuint32_t)(CIN / 8), 1, 1};
+    const cuuint32_t es[5] = {1, 1, 1, 1, 1};
+    const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<__nv_bfloat16 *>(x), dims, strides,
+                           box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 template <int CIN, int COUT, bool LAST>
 cudaError_t launch_conv(const fp_surrogate *s, int layer, const __nv_bfloat16 *x, int B, int H, int W, void *y,
                         cudaStream_t st) {
@@ -487,12 +601,15 @@ cudaError_t launch_conv(const fp_surrogate *s, int layer, const __nv_bfloat16 *x
         if (e != cudaSuccess) return e;
         attr = true;
     }
+    CUtensorMap m;
+    cudaError_t e = encode_act_map<CIN>(&m, x, B, H, W);
+    if (e != cudaSuccess) return e;
     const long long items =
         (long long)B * (((W - 2) + kSeg - 1) / kSeg) * (((H - 2) + kStripRows - 1) / kStripRows);
     int grid = (int)std::min<long long>(items, (long long)s->sms * 3);
     if (grid < 1) grid = 1;
-    conv3x3_tc_kernel<CIN, COUT, LAST><<<grid, kConvThreads, G::SMEM, st>>>(x, B, H, W, s->d_wpack[layer],
-                                                                             s->d_bias[layer], y, s->d_err);
+    conv3x3_tc_kernel<CIN, COUT, LAST><<<grid, kConvWarps * 32, G::SMEM, st>>>(m, B, H, W, s->d_wpack[layer],
+                                                                              s->d_bias[layer], y, s->d_err);
     return cudaGetLastError();
 }
 

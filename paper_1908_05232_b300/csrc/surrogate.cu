@@ -19,7 +19,7 @@
 // TMEM lanes with tcgen05.ld for the bias / ReLU / BF16 epilogue.  TMEM is
 // freed on every exit path.
 //
-// Training (A13): the backward pass (data and weight gradients of every
+// Training: the backward pass (data and weight gradients of every
 // layer, FP32 on the CUDA cores, deterministic reductions), the loss and Adam
 // with FP32 master weights.
 #include <cudaTypedefs.h>
@@ -384,7 +384,7 @@ __global__ void pack_input_kernel(const float *__restrict__ x4, size_t npix, __n
 }
 
 
-// ---- training (A13): FP32 backward on the CUDA cores --------------------------
+// ---- training: FP32 backward on the CUDA cores --------------------------------
 
 // g = d loss / d (last layer pre-activation): loss = mean (s z - t)^2 over
 // B x Ho x Wo x 3 with s = kOutScale, so dz = 2 s (s z - t) / n = 2 s (y - t) / n with y the

@@ -48,6 +48,19 @@ def workload(seed):
     return scenarios.shopping_centre(512, 0.5, 10_000, 0, seed, 1800.0)
 
 
+def combine_ranks(t_sec, updates, device):
+    """Whole-job figures of independent replicas: the slowest rank's timed
+    seconds (MAX) and the updates of all ranks (SUM), over the default process
+    group (NCCL on GPUs; gloo in the CPU tests)."""
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([float(t_sec)], dtype=torch.float64, device=device)
+    uu = torch.tensor([float(updates)], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    dist.all_reduce(uu, op=dist.ReduceOp.SUM)
+    return float(tt.item()), float(uu.item())
+
+
 def scenarios_mod():
     import scenarios
     return scenarios
@@ -273,12 +286,7 @@ def run_ours(args):
     clocks = sampler.stop()
     t_sec = sum(ms_list) / 1e3
     if ws > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([t_sec], dtype=torch.float64, device=dev)
-        uu = torch.tensor([float(upd_total)], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        dist.all_reduce(uu, op=dist.ReduceOp.SUM)
-        t_sec, upd_all = float(tt.item()), float(uu.item())
+        t_sec, upd_all = combine_ranks(t_sec, upd_total, dev)
     else:
         upd_all = float(upd_total)
     value = upd_all / t_sec

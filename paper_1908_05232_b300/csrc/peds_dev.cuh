@@ -221,11 +221,23 @@ __device__ __forceinline__ void ped_group(const FpSim &S, int par, const StepCtl
         const float vdn = sqrtf(__fmaf_rn(vdx, vdx, vdy * vdy));
         const float inv_vdn = vdn > 0.0f ? __frcp_rn(vdn) : 0.0f;
         const float fcut = __expf((2.0f * kRb - kR) * (1.0f / kB));
+        // the three bin rows' record ranges as one list, split over the lanes;
+        // the next candidate's record is loaded before the current one is used
+        const int n0 = rk1[0] - rk0[0], n01 = n0 + (rk1[1] - rk0[1]);
+        const int ntot = n01 + (rk1[2] - rk0[2]);
+        auto rec_of = [&](int t) { return t < n0 ? rk0[0] + t : t < n01 ? rk0[1] + t - n0 : rk0[2] + t - n01; };
+        int kn = sub < ntot ? rec_of(sub) : 0;
+        float4 qn = sub < ntot ? *reinterpret_cast<const float4 *>(&S.pedA[2 * kn]) : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll 1
-        for (int r = 0; r < 3; ++r) {
-            for (int k = rk0[r] + sub; k < rk1[r]; k += kG) {
+        for (int t = sub; t < ntot; t += kG) {
+            const int k = kn;
+            const float4 q = qn;
+            if (t + kG < ntot) {
+                kn = rec_of(t + kG);
+                qn = *reinterpret_cast<const float4 *>(&S.pedA[2 * kn]);
+            }
+            {
                 if (k == j) continue;
-                const float4 q = *reinterpret_cast<const float4 *>(&S.pedA[2 * k]);
                 const float rx = x - q.x, ry = y - q.y;
                 if (fabsf(rx) >= kR || fabsf(ry) >= kR) continue;
                 const float d2 = __fmaf_rn(rx, rx, ry * ry);

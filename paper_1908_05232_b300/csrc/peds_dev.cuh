@@ -20,6 +20,19 @@ namespace fpdev {
 
 
 __constant__ float c_speed[5] = {0.0f, 1.8f, 0.9f, 0.45f, 0.0f};  // Table 1 (index 0: own dry speed)
+
+// single-instruction square root / reciprocal (relative error ~1e-7) for the
+// pair forces, whose rounding enters positions far below parity tolerances
+__device__ __forceinline__ float sqrt_approx(float v) {
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
+__device__ __forceinline__ float rcp_approx(float v) {
+    float r;
+    asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
 constexpr float kTau = 0.5f, kA = 2.0f, kB = 0.3f, kRb = 0.25f, kR = 1.0f, kSide = 0.5f;
 constexpr int kTPick = 30 * 1048576, kTDrop = 30 * 1048576;
 constexpr float kBagT = 0.25f;
@@ -242,8 +255,8 @@ __device__ __forceinline__ void ped_group(const FpSim &S, int par, const StepCtl
                 if (fabsf(rx) >= kR || fabsf(ry) >= kR) continue;
                 const float d2 = __fmaf_rn(rx, rx, ry * ry);
                 if (d2 >= kR * kR || d2 <= 0.0f) continue;
-                const float d = sqrtf(d2);
-                const float invd = __frcp_rn(d);
+                const float d = sqrt_approx(d2);
+                const float invd = rcp_approx(d);
                 const float fm = kA * (__expf((2.0f * kRb - d) * (1.0f / kB)) - fcut);
                 const float nx_ = rx * invd, ny_ = ry * invd;
                 float fx = fm * nx_, fy = fm * ny_;

@@ -77,9 +77,10 @@ extern "C" {
 #define FP_FIELD_COUNTERS 5 /* one fp_counters */
 #define FP_FIELD_NAV 6      /* uint8[3*ny*nx]: exit, storage, barrier direction codes */
 #define FP_FIELD_MASS 7     /* double[2]: water volume sum h dx^2 (m^3), net boundary inflow volume (m^3) */
-#define FP_FIELD_PROFILE 8  /* double[5]: profiled steps, then total ms of: the hashing/scan part,
-                               the flood update, the gather + pedestrian part, whole steps
-                               (see fp_set_profiling) */
+#define FP_FIELD_PROFILE 8  /* double[6]: profiled steps, then total ms of: the hashing/scan part,
+                               the flood update, the gather + pedestrian part, whole steps;
+                               then the cell updates the flood kernel computed (cells of
+                               tiles not skipped as dry, see fp_step) (see fp_set_profiling) */
 
 /* Simulation set-up.  Sizes: nx, ny >= 1; max_peds >= 0. */
 typedef struct fp_config {
@@ -174,7 +175,12 @@ int fp_add_pedestrians(fp_sim *sim, const fp_ped *peds, int32_t count);
 /* Remove all pedestrians and reset the exit and sandbag counters. */
 int fp_clear_pedestrians(fp_sim *sim);
 
-/* Enqueue n_steps coupled steps on the simulation's stream (asynchronous). */
+/* Enqueue n_steps coupled steps on the simulation's stream (asynchronous).
+ * Flood tiles whose cells and one-cell halo held no water after the previous
+ * step, whose output already holds the zero state and that have no active
+ * inflow ghost are skipped (the update would write zeros: every flux is zero);
+ * the first two steps after fp_set_state, fp_set_time, fp_set_hydrograph or a
+ * surrogate window compute every tile. */
 int fp_step(fp_sim *sim, int32_t n_steps);
 
 /* How fp_step runs a step (both give bit-identical results):

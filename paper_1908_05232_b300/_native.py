@@ -288,9 +288,10 @@ class Simulation:
         return st
 
     def profile(self) -> dict:
-        out = np.zeros(5, np.float64)
+        out = np.zeros(6, np.float64)
         fp_read_state(self.h, FP_FIELD_PROFILE, out)
-        return dict(steps=out[0], hash_ms=out[1], flood_ms=out[2], ped_chain_ms=out[3], step_ms=out[4])
+        return dict(steps=out[0], hash_ms=out[1], flood_ms=out[2], ped_chain_ms=out[3], step_ms=out[4],
+                    flood_cells=out[5])
 
     def nav(self):
         out = np.empty((3, self.ny, self.nx), np.uint8)

@@ -6,14 +6,18 @@
 namespace {
 using namespace fpdev;
 
-// Batched ensemble: flat tile space, member s owns tiles [tile_off[s], tile_off[s+1]).
-__global__ void __launch_bounds__(512) flood_batch_kernel(const FpSim *__restrict__ sims,
+// Batched ensemble: flat tile space, member s owns tiles [tile_off[s], tile_off[s+1]);
+// one tile per CTA.
+__global__ void __launch_bounds__(512, 2) flood_batch_kernel(const FpSim *__restrict__ sims,
                                                           const FpTmaSet *__restrict__ maps,
                                                           const int *__restrict__ tile_off, int n, int par,
                                                           int slot) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ __align__(8) unsigned long long mbar;
-    if (threadIdx.x == 0) mbar_init(&mbar);
+    __shared__ __align__(8) unsigned long long mbar[2];
+    if (threadIdx.x == 0) {
+        mbar_init(&mbar[0]);
+        mbar_init(&mbar[1]);
+    }
     __syncthreads();
     const int t = blockIdx.x;
     int lo = 0, hi = n - 1;
@@ -22,22 +26,26 @@ __global__ void __launch_bounds__(512) flood_batch_kernel(const FpSim *__restric
         if (tile_off[mid] <= t) lo = mid; else hi = mid - 1;
     }
     const FpSim &S = sims[lo];
-    const int local = t - tile_off[lo];
-    const int tiles_x = (S.nx + FP_TX - 1) / FP_TX;
-    flood_tile<16>(maps[2 * lo + par], S, par, slot, local % tiles_x, local / tiles_x, smem_raw, &mbar, 0u);
+    const int ntiles = tile_off[lo + 1] - tile_off[lo];
+    unsigned phase = 0u;
+    flood_tiles<16>(maps[2 * lo + par], S, par, slot, t - tile_off[lo], ntiles, ntiles, smem_raw, mbar, phase);
 }
 
-// 16-row tiles: three CTAs per SM (65.5 KB of shared memory each, <= 42 registers)
+// One CTA per SM slot, each taking every gridDim.x-th tile.
 template <int TY>
-__global__ void __launch_bounds__(32 * TY, TY == 16 ? 2 : 1) flood_kernel(const __grid_constant__ FpTmaSet tm,
-                                                        const __grid_constant__ FpSim S, int par, int slot) {
+__global__ void __launch_bounds__(32 * TY, 32 / TY) flood_kernel(const __grid_constant__ FpTmaSet tm,
+                                                                 const __grid_constant__ FpSim S, int par, int slot) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ __align__(8) unsigned long long mbar;
+    __shared__ __align__(8) unsigned long long mbar[2];
     fp_pdl_wait();
-    if (S.tile_mask != nullptr && S.tile_mask[blockIdx.y * gridDim.x + blockIdx.x] == 0) return;
-    if (threadIdx.x == 0) mbar_init(&mbar);
+    if (threadIdx.x == 0) {
+        mbar_init(&mbar[0]);
+        mbar_init(&mbar[1]);
+    }
     __syncthreads();
-    flood_tile<TY>(tm, S, par, slot, blockIdx.x, blockIdx.y, smem_raw, &mbar, 0u);
+    const int ntiles = ((S.nx + FP_TX - 1) / FP_TX) * ((S.ny + TY - 1) / TY);
+    unsigned phase = 0u;
+    flood_tiles<TY>(tm, S, par, slot, blockIdx.x, gridDim.x, ntiles, smem_raw, mbar, phase);
 }
 
 // U^0 wave-speed max and wet flag into clock slot `slot` (after a state change).
@@ -113,12 +121,26 @@ void fp_launch_flood_batch(const FpSim *d_sims, const FpTmaSet *d_maps, const in
     flood_batch_kernel<<<total_tiles, 512, smem_bytes<16>(), st>>>(d_sims, d_maps, d_tile_off, n, par, slot);
 }
 
+// resident flood CTAs of each tile height on the whole GPU (set with the attributes)
+static int g_flood_ctas[3] = {0, 0, 0};
+
+template <int TY>
+static cudaError_t init_flood_t(int sms) {
+    cudaError_t e = cudaFuncSetAttribute(flood_kernel<TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<TY>());
+    int per_sm = 0;
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, flood_kernel<TY>, 32 * TY, smem_bytes<TY>());
+    g_flood_ctas[TY == 8 ? 0 : TY == 16 ? 1 : 2] = (per_sm > 0 ? per_sm : 1) * sms;
+    return e;
+}
+
 cudaError_t fp_flood_init_attributes() {
-    cudaError_t e = cudaFuncSetAttribute(flood_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<8>());
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(flood_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<16>());
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(flood_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<32>());
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = init_flood_t<8>(sms);
+    if (e == cudaSuccess) e = init_flood_t<16>(sms);
+    if (e == cudaSuccess) e = init_flood_t<32>(sms);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(flood_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<16>());
     return e;
@@ -127,8 +149,10 @@ cudaError_t fp_flood_init_attributes() {
 template <int TY>
 static void launch_flood_t(const FpSim &S, const FpTmaSet &tm, int par, int slot, cudaStream_t st, bool pdl) {
     constexpr int smem = smem_bytes<TY>();
-    dim3 grid((S.nx + FP_TX - 1) / FP_TX, (S.ny + TY - 1) / TY);
-    fp_launch(pdl, flood_kernel<TY>, grid, dim3(32 * TY), smem, st, tm, S, par, slot);
+    const int ntiles = ((S.nx + FP_TX - 1) / FP_TX) * ((S.ny + TY - 1) / TY);
+    const int resident = g_flood_ctas[TY == 8 ? 0 : TY == 16 ? 1 : 2];
+    const int grid = resident > 0 && resident < ntiles ? resident : ntiles;
+    fp_launch(pdl, flood_kernel<TY>, dim3(grid), dim3(32 * TY), smem, st, tm, S, par, slot);
 }
 
 void fp_launch_flood(const FpSim &S, const void *tma_set, int par, int slot, int tile_rows, cudaStream_t st,

@@ -1,11 +1,15 @@
 // flood_dev.cuh -- device code of the hydrodynamic cell update (Section 2.2),
 // shared by the per-step flood kernel and the persistent coupled-step kernel.
 //
-// flood_tile<TY>: a 64 x TY tile of cells by 32 x TY threads.
-//   1. one thread issues four 2D TMA loads (cp.async.bulk.tensor) of the tile
+// flood_tiles<TY>: 64 x TY tiles of cells by 32 x TY threads, a CTA taking a
+// strided list of tiles.
+//   0. tile modes from 64 x 8-cell water flags: tiles that stayed dry are not
+//      loaded (their update would write zeros);
+//   1. one thread issues six 2D TMA loads (cp.async.bulk.tensor) of a tile
 //      plus a one-cell halo (a 72-float-wide box starting 16-byte aligned) of
-//      h, hu, hv, z into shared memory, completing on an mbarrier; meanwhile
-//      every thread loads its two cells' n0 and evacuee counts;
+//      h, hu, hv, z, and of the tile's n0 and evacuee counts, into one of two
+//      stage buffers, completing on that buffer's mbarrier; the next tile's
+//      loads are issued before the current tile is processed;
 //   2. velocities u = hu/h, v = hv/h per staged cell;
 //   3. every x and y face of the tile once: non-negative hydrostatic
 //      reconstruction h* = max(0, eta - max(z_L, z_R)) and the HLL flux;
@@ -123,10 +127,27 @@ __host__ __device__ constexpr int plane_stride() {
     return (((TY + 2) * ROWW + 31) / 32) * 32;
 }
 
-// staged h, hu, hv, z; south-face fluxes [TY+1][64]; east tile-edge fluxes [TY]
+// Shared memory of the flood tiles, in bytes: two stage buffers, each holding
+// the staged h, hu, hv, z (tile + one-cell halo, ROWW x (TY + 2) floats each),
+// n0 (ROWW x TY floats) and evacuee counts (ROWW x TY uint16, box starting at
+// the tile's first cell - 4 so that its x coordinate is 16-byte aligned); then
+// the south-face fluxes [TY+1][64] and the east tile-edge fluxes [TY].
+template <int TY>
+struct FloodSmem {
+    static constexpr int PLANE = plane_stride<TY>();  // floats
+    static constexpr int N0 = 4 * PLANE * 4;            // byte offsets within a buffer
+    static constexpr int OCC = N0 + TY * ROWW * 4;
+    static constexpr int BUF = OCC + TY * ROWW * 2;
+    static constexpr int TX_BYTES = 4 * (TY + 2) * ROWW * 4 + TY * ROWW * 4 + TY * ROWW * 2;
+    static constexpr int YF = 2 * BUF;
+    static constexpr int XE = YF + (TY + 1) * FP_TX * 16;
+    static constexpr int BYTES = XE + TY * 16;
+    static_assert(N0 % 128 == 0 && OCC % 128 == 0 && BUF % 128 == 0, "TMA destinations 128-byte aligned");
+};
+
 template <int TY>
 __host__ __device__ constexpr int smem_bytes() {
-    return 4 * plane_stride<TY>() * 4 + (TY + 1) * FP_TX * 16 + TY * 16;
+    return FloodSmem<TY>::BYTES;
 }
 
 // a staged cell as a face side: depth, velocities (0 at h <= h_eps), bed
@@ -194,301 +215,421 @@ __device__ __forceinline__ float4 y_face(const FpSim &S, float g, float hg, floa
     return make_float4(fm, ft, fn - pB, fn - pA);
 }
 
-// 32 * TY threads: warp r owns row r of the tile, lane l its cells l and l + 32.
-// One 64 x TY tile (tile coordinates bx, by) by the 32 * TY threads of the CTA.
-// The caller owns the mbarrier (initialised once, count 1) and its phase parity,
-// and guarantees no thread still reads the staged planes of a previous tile.
-// Returns false if the TMA transfer did not complete (error flag set).
+// Work of a tile in one step, decided before its loads are issued.
+enum : unsigned char { kTileNone = 0, kTileDry = 1, kTileLoad = 2 };
+constexpr int kModeChunk = 64;  // tile modes decided together by one CTA
+
+// tid 0: the TMA loads of tile (x0, y0) into one stage buffer, completing on mbar
 template <int TY>
-__device__ __forceinline__ bool flood_tile(const FpTmaSet &tm, const FpSim &S, int par, int slot, int bx, int by,
-                                           unsigned char *smem_raw, unsigned long long *mbar, unsigned parity) {
+__device__ __forceinline__ void stage_tile(const FpTmaSet &tm, unsigned char *buf, unsigned long long *mbar, int x0,
+                                           int y0) {
+    using L = FloodSmem<TY>;
+    const unsigned bar = smem_u32(mbar);
+    // the buffer was last read by generic loads of this CTA; the global data by
+    // generic stores of earlier phases
+    asm volatile("fence.proxy.async;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(L::TX_BYTES) : "memory");
+    const CUtensorMap *maps[6] = {&tm.h, &tm.hu, &tm.hv, &tm.z, &tm.n0, &tm.occ};
+    const int offs[6] = {0, L::PLANE * 4, 2 * L::PLANE * 4, 3 * L::PLANE * 4, L::N0, L::OCC};
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        // planes with the halo row above the tile; n0 and counts from the tile's first row
+        const int y = k < 4 ? y0 : y0 + 1;
+        asm volatile(
+            "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+            "[%4];" ::"r"(smem_u32(buf + offs[k])),
+            "l"(reinterpret_cast<unsigned long long>(maps[k])), "r"(x0), "r"(y), "r"(bar)
+            : "memory");
+    }
+}
+
+// bounded wait for phase `parity` of an mbarrier (false: it did not complete)
+__device__ __forceinline__ bool mbar_wait_phase(unsigned long long *mbar, unsigned parity) {
+    const unsigned bar = smem_u32(mbar);
+    unsigned ok = 0;
+    for (int it = 0; it < (1 << 22) && !ok; ++it) {
+        asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+                     : "=r"(ok)
+                     : "r"(bar), "r"(parity)
+                     : "memory");
+    }
+    return ok != 0;
+}
+
+// Modes of the CTA's tiles first + k * stride, k in [k0, k0 + kModeChunk), into
+// s_mode[k - k0]; warp w takes k0 + w, k0 + w + TY, ...; each lane loads one
+// water flag of the tile's dependence region.  A tile is
+//   kTileNone when the tile mask excludes it;
+//   kTileDry  when no block of it or of its one-cell halo held water after the
+//             last step (flags of the input plane), its own blocks of the output
+//             plane already hold the zero state (flags from two steps back), no
+//             inflow ghost is active on its edges and it is not tile 0 (which
+//             advances the clock): every flux is zero and the update would
+//             write zeros, so nothing is loaded and only the evacuee counts are
+//             cleared;
+//   kTileLoad otherwise.
+template <int TY>
+__device__ __forceinline__ void decide_modes(const FpSim &S, int par, int first, int stride, int ntiles, int k0,
+                                             bool inflow_on, unsigned char *s_mode) {
+    constexpr int R = kModeChunk / TY;
+    static_assert((TY / FP_BLK_ROWS + 2) * 3 + TY / FP_BLK_ROWS <= 32, "one flag per lane");
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int nx = S.nx, ny = S.ny, bw = (nx + FP_TX - 1) / FP_TX;
+    const bool flags = S.blk_wet[0] != nullptr;
+    int f[R];
+    unsigned char m[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int t = first + (k0 + w + r * TY) * stride;
+        f[r] = 0;
+        m[r] = 1;
+        if (t < ntiles) {
+            const int bx = t % bw, y0 = (t / bw) * TY;
+            if (flags) {
+                const int r0 = max(0, y0 - 1) / FP_BLK_ROWS, r1 = min(ny - 1, y0 + TY) / FP_BLK_ROWS;
+                const int c0 = max(0, bx - 1), c1 = min(bw - 1, bx + 1);
+                const int nc = c1 - c0 + 1, nin = (r1 - r0 + 1) * nc;
+                const int q0 = y0 / FP_BLK_ROWS, nout = min(ny - 1, y0 + TY - 1) / FP_BLK_ROWS - q0 + 1;
+                if (lane < nin) f[r] = S.blk_wet[par][(r0 + lane / nc) * bw + c0 + lane % nc];
+                else if (lane < nin + nout) f[r] = S.blk_wet[par ^ 1][(q0 + lane - nin) * bw + bx];
+            }
+            if (lane == 0 && S.tile_mask != nullptr) m[r] = S.tile_mask[t];
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int k = k0 + w + r * TY, t = first + k * stride;
+        const bool any = __any_sync(0xffffffffu, f[r] != 0);
+        if (lane == 0 && t < ntiles) {
+            const int x0 = (t % bw) * FP_TX, y0 = (t / bw) * TY;
+            const bool edge = x0 == 0 || x0 + FP_TX >= nx || y0 == 0 || y0 + TY >= ny;
+            unsigned char mode = kTileLoad;
+            if (m[r] == 0) mode = kTileNone;
+            else if (flags && !any && t != 0 && !(inflow_on && edge)) mode = kTileDry;
+            s_mode[k - k0] = mode;
+        }
+    }
+}
+
+// The CTA's tiles first, first + stride, ... (< ntiles) of the 64 x TY tiling
+// (tile t at column t % tiles_x, row t / tiles_x), by the 32 * TY threads of the
+// CTA: warp r owns row r of a tile, lane l its cells l and l + 32.  Loads are
+// double-buffered: the next tile's TMA copies are issued before the current
+// tile waits for its own.  mbar[2] (initialised, count 1) and their phase bits
+// (bit b: buffer b) belong to the caller (only thread 0's copy is used); no thread may
+// still read the stage buffers of an earlier call.  Returns false if a TMA
+// transfer did not complete (error flag set; the other buffer's copy, if one
+// was in flight, waited for).
+template <int TY>
+__device__ bool flood_tiles(const FpTmaSet &tm, const FpSim &S, int par, int slot, int first, int stride,
+                            int ntiles, unsigned char *smem_raw, unsigned long long *mbar, unsigned &phase) {
+    using L = FloodSmem<TY>;
     constexpr int NT = 32 * TY;
-    constexpr int PLANE = plane_stride<TY>();
-    constexpr int BOX_BYTES = (TY + 2) * ROWW * 4;
-    float *s_h = reinterpret_cast<float *>(smem_raw);
-    float *s_hu = s_h + PLANE;
-    float *s_hv = s_hu + PLANE;
-    float *s_z = s_hv + PLANE;
-    float4 *s_yf = reinterpret_cast<float4 *>(s_z + PLANE);  // [TY+1][64] south faces; row TY: the tile's north edge
-    float4 *s_xe = s_yf + (TY + 1) * FP_TX;                   // [TY] the tile's east-edge face of each row
+    static_assert(TY % FP_BLK_ROWS == 0 && TY >= 8, "whole water-flag blocks; edge-face, flux and control warps apart");
+    __shared__ unsigned char s_mode[kModeChunk];
     __shared__ long long s_dt, s_t, s_step;
-    __shared__ float s_hin, s_dtf, s_lx;
-    __shared__ int s_ok;
+    __shared__ float s_hin, s_dtf, s_lx, s_accm;
+    __shared__ unsigned s_smax0;
+    __shared__ int s_ok[2], s_accf, s_accn;
+    __shared__ int2 s_xy[2];
+    __shared__ int s_blk[TY / FP_BLK_ROWS];
     __shared__ float s_red[NT / 32];
     __shared__ int s_redi[NT / 32];
     __shared__ float s_bx[2][TY];      // mass flux through the west / east domain edge faces
     __shared__ float s_by[2][FP_TX];   // ... through the south / north domain edge faces
+    float4 *s_yf = reinterpret_cast<float4 *>(smem_raw + L::YF);  // [TY+1][64] south faces; row TY: the tile's north edge
+    float4 *s_xe = reinterpret_cast<float4 *>(smem_raw + L::XE);  // [TY] the tile's east-edge face of each row
 
-    const int tid = threadIdx.x;
-    const int x0 = bx * FP_TX, y0 = by * TY;
-    const int nx = S.nx, ny = S.ny;
+    if (first >= ntiles) return true;
+    const int tid = threadIdx.x, lane = tid & 31, row = tid >> 5;
+    // the control thread (lane 0 of the last warp, which computes no edge
+    // faces): waits for and issues the TMA loads, folds the reductions
+    constexpr int CTL = NT - 32;
+    const int nx = S.nx, ny = S.ny, tiles_x = (nx + FP_TX - 1) / FP_TX;
 
+    // the step's clock, the same for every tile
+    const bool inflow_on = S.has_inflow && S.clock[slot].h_in > FP_H_EPS_F;
     if (tid == 0) {
-        const unsigned bar = smem_u32(mbar);
-        // the staged planes were last written by generic stores / read by this CTA
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(4 * BOX_BYTES)
-                     : "memory");
-        const CUtensorMap *maps[4] = {&tm.h, &tm.hu, &tm.hv, &tm.z};
-        float *dsts[4] = {s_h, s_hu, s_hv, s_z};
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            asm volatile(
-                "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-                    smem_u32(dsts[k])),
-                "l"(reinterpret_cast<unsigned long long>(maps[k])), "r"(x0), "r"(y0), "r"(bar)
-                : "memory");
-        }
         const FpClock c = S.clock[slot];
         const long long dt = fp_dt_ticks(S, c, c.h_in);
         const float dtf = (float)dt * (1.0f / FP_TICKS_F);
-        if (S.dt_fixed > 0 && bx == 0 && by == 0) {
-            float smax = __uint_as_float(c.smax_bits);
-            if (S.has_inflow && c.h_in > FP_H_EPS_F) smax = fmaxf(smax, __fsqrt_rn(__fmul_rn(S.g, c.h_in)));
-            if (__fmul_rn(smax, dtf) > __fmul_rn(S.cfl, S.dx)) atomicAdd(&S.cnt->cfl_over, 1u);
-        }
         s_hin = c.h_in;
         s_dt = dt;
         s_dtf = dtf;
         s_lx = __fdiv_rn(dtf, S.dx);
         s_t = c.t;
         s_step = c.step;
+        s_smax0 = c.smax_bits;
+        s_accm = 0.0f;
+        s_accf = 0;
+        s_accn = 0;
     }
-    // this thread's two cells: n0 and evacuee counts, loaded while the TMA is in flight
-    const int lane = tid & 31, row = tid >> 5;
-    const int cj = y0 + row;
-    const int ciA = x0 + lane, ciB = x0 + lane + 32;
-    const bool okA = cj < ny && ciA < nx, okB = cj < ny && ciB < nx;
-    float n0A = 0.f, n0B = 0.f;
-    unsigned short occA = 0, occB = 0;
-    const size_t gA = okA ? fp_pidx(S, ciA, cj) : 0;
-    if (okA) { n0A = S.n0[gA]; occA = S.occ[par][gA]; }
-    if (okB) { n0B = S.n0[gA + 32]; occB = S.occ[par][gA + 32]; }
-    if (tid == 0) {
-        const unsigned bar = smem_u32(mbar);
-        unsigned ok = 0;
-        for (int it = 0; it < (1 << 22) && !ok; ++it) {
-            asm volatile(
-                "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
-                : "=r"(ok)
-                : "r"(bar), "r"(parity)
-                : "memory");
-        }
-        s_ok = ok;
-        if (!ok) fp_set_err(S, FP_ERR_TIMEOUT);
-    }
-    __syncthreads();
-    if (!s_ok) return false;
-
-    const float g = S.g, hg = 0.5f * g;
-    const float h_in = s_hin;
-
-    // 1b. a dry tile -- no water in the tile and its one-cell halo, no inflow
-    // ghost at its domain edges -- has zero flux on every face (h* = 0 on both
-    // sides), so the update leaves h = hu = hv = 0: the faces are skipped and
-    // the same update runs on zero fluxes (the same bits as computing them).
-    // Checked: this thread's two cells, the west / east halo cells of its row
-    // (lanes 0 / 31) and the south / north halo rows (first / last warp) --
-    // every cell a face of the tile reads.
-    const int oA = (row + 1) * ROWW + lane + 4, oB = oA + 32;
-    int any = (s_h[oA] != 0.0f) | (s_h[oB] != 0.0f);
-    if (lane == 0) any |= s_h[oA - 1] != 0.0f;
-    if (lane == 31) any |= s_h[oB + 1] != 0.0f;
-    if (row == 0) any |= (s_h[oA - ROWW] != 0.0f) | (s_h[oB - ROWW] != 0.0f);
-    if (row == TY - 1) any |= (s_h[oA + ROWW] != 0.0f) | (s_h[oB + ROWW] != 0.0f);
-    if (S.has_inflow && h_in > FP_H_EPS_F && (x0 == 0 || x0 + FP_TX >= nx || y0 == 0 || y0 + TY >= ny)) any = 1;
-    const bool dry = __syncthreads_or(any) == 0;
-    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
-
-    // 2. faces from registers: this thread's cells A (column lane) and B (lane +
-    // 32) of row `row`; each computes its west and south face.  West
-    // neighbours arrive by shuffle (lane 0: the halo cell, and cell 31 for B).
-    const int iA = x0 + lane, iB = iA + 32;
-    float4 fwA = zero4, fwB = zero4;
-    if (!dry) {
-        const Side cA = staged_side(s_h, s_hu, s_hv, s_z, oA);
-        const Side cB = staged_side(s_h, s_hu, s_hv, s_z, oB);
-        Side wA = shfl_up_side(cA), wB = shfl_up_side(cB);
-        const Side c31 = shfl_side(cA, 31);
-        if (lane == 0) {
-            wA = staged_side(s_h, s_hu, s_hv, s_z, oA - 1);
-            wB = c31;
-        }
-        if (cj < ny) {
-            fwA = x_face(S, g, hg, h_in, wA, cA, iA, cj);
-            fwB = x_face(S, g, hg, h_in, wB, cB, iB, cj);
-            if (iA == 0) s_bx[0][row] = fwA.x;
-            if (iA == nx) s_bx[1][row] = fwA.x;
-            if (iB == nx) s_bx[1][row] = fwB.x;
-        }
-        if (cj <= ny) {
-            const Side bA = staged_side(s_h, s_hu, s_hv, s_z, oA - ROWW);
-            const Side bB = staged_side(s_h, s_hu, s_hv, s_z, oB - ROWW);
-            const float4 gA = y_face(S, g, hg, h_in, bA, cA, iA, cj);
-            const float4 gB = y_face(S, g, hg, h_in, bB, cB, iB, cj);
-            s_yf[row * FP_TX + lane] = gA;
-            s_yf[row * FP_TX + lane + 32] = gB;
-            if (cj == 0) { s_by[0][lane] = gA.x; s_by[0][lane + 32] = gB.x; }
-            if (cj == ny) { s_by[1][lane] = gA.x; s_by[1][lane + 32] = gB.x; }
-        }
-    }
-    // 3. the tile's edge faces: east (column x0 + 64) of each row, north (row
-    // y0 + TY) of each column
-    if (!dry && tid < TY + FP_TX) {
-        if (tid < TY) {
-            const int r = tid, j = y0 + r, i = x0 + FP_TX;
-            float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (j < ny && i <= nx) {
-                const int o = (r + 1) * ROWW + FP_TX + 4;
-                f = x_face(S, g, hg, h_in, staged_side(s_h, s_hu, s_hv, s_z, o - 1),
-                           staged_side(s_h, s_hu, s_hv, s_z, o), i, j);
-                if (i == nx) s_bx[1][r] = f.x;
-            }
-            s_xe[r] = f;
-        } else {
-            const int c = tid - TY, i = x0 + c, j = y0 + TY;
-            float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (j <= ny) {
-                const int o = (TY + 1) * ROWW + c + 4;
-                f = y_face(S, g, hg, h_in, staged_side(s_h, s_hu, s_hv, s_z, o - ROWW),
-                           staged_side(s_h, s_hu, s_hv, s_z, o), i, j);
-                if (j == ny && i < nx) s_by[1][c] = f.x;
-            }
-            s_yf[TY * FP_TX + c] = f;
-        }
-    }
+    auto stage = [&](int t, int b) {
+        stage_tile<TY>(tm, smem_raw + b * L::BUF, &mbar[b], (t % tiles_x) * FP_TX, (t / tiles_x) * TY);
+    };
+    // the first tile's loads go out before its mode is known (they overlap the
+    // flag loads); tile 0 waits for them whatever its mode
+    if (tid == CTL) stage(first, 0);
+    decide_modes<TY>(S, par, first, stride, ntiles, 0, inflow_on, s_mode);
     __syncthreads();
 
-    // 4. Eq. (2) + friction for this thread's two cells; east fluxes by shuffle
-    // (lane 31: cell 32's west face, and the tile's east edge for B)
-    float smax = 0.0f;
-    float sk_[2] = {-1.0f, -1.0f}, hk_[2] = {0.f, 0.f}, huk_[2] = {0.f, 0.f}, hvk_[2] = {0.f, 0.f};
-    int wet = 0, neg = 0, bad = 0;
-    const float dt = s_dtf, lx = s_lx, ly = s_lx;
-    const int p2 = par ^ 1;
-    float4 feA = shfl_down_f4(fwA), feB = shfl_down_f4(fwB);
-    const float4 fB0 = shfl_f4(fwB, 0);
-    if (lane == 31) {
-        feA = fB0;
-        feB = dry ? zero4 : s_xe[row];
-    }
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const bool ok = k == 0 ? okA : okB;
-        if (!ok) continue;
-        if (dry) {  // the zero state the update computes from zero fluxes
-            const size_t gi = gA + 32 * k;
-            S.h[p2][gi] = 0.0f;
-            S.hu[p2][gi] = 0.0f;
-            S.hv[p2][gi] = 0.0f;
-            if ((k == 0 ? occA : occB) != 0) S.occ[par][gi] = 0;
+    // Per tile k (buffer b = k & 1): the control thread waits for the tile's
+    // loads; one barrier; it issues the next tile's loads into the other buffer
+    // (every thread is past the previous tile, its last reader); the tile is
+    // processed.  Values it publishes per tile are double-buffered too, so a
+    // tile needs no closing barrier.
+    int b = 0;
+    for (int k = 0; first + k * stride < ntiles; ++k, b ^= 1) {
+        const int t = first + k * stride, tn = t + stride;
+        const int mode = s_mode[k % kModeChunk];
+        if (tn < ntiles && (k + 1) % kModeChunk == 0) {
+            __syncthreads();  // every thread has read this tile's mode
+            decide_modes<TY>(S, par, first, stride, ntiles, k + 1, inflow_on, s_mode);
+        }
+        if (tid == CTL) {
+            int ok = 1;
+            if (mode == kTileLoad || k == 0) {
+                ok = mbar_wait_phase(&mbar[b], (phase >> b) & 1u);
+                phase ^= 1u << b;
+                if (!ok) fp_set_err(S, FP_ERR_TIMEOUT);
+            }
+            s_ok[b] = ok;
+            s_xy[b] = make_int2((t % tiles_x) * FP_TX, (t / tiles_x) * TY);
+        }
+        __syncthreads();
+        if (!s_ok[b]) return false;
+        if (tid == CTL && tn < ntiles && s_mode[(k + 1) % kModeChunk] == kTileLoad) stage(tn, b ^ 1);
+        const int x0 = s_xy[b].x, y0 = s_xy[b].y, bx = x0 / FP_TX;
+        const int cj = y0 + row;
+        const bool okA = cj < ny && x0 + lane < nx, okB = cj < ny && x0 + lane + 32 < nx;
+        const size_t gA = okA ? fp_pidx(S, x0 + lane, cj) : 0;
+        if (mode != kTileLoad) {
+            if (mode == kTileDry) {  // the evacuee counts this step read are cleared all the same
+                if (okA) S.occ[par][gA] = 0;
+                if (okB) S.occ[par][gA + 32] = 0;
+            }
             continue;
         }
-        const int c = lane + 32 * k;
-        const int o = (row + 1) * ROWW + c + 4;
-        const float4 fw = k == 0 ? fwA : fwB;
-        const float4 fe = k == 0 ? feA : feB;
-        const float4 gs = dry ? zero4 : s_yf[row * FP_TX + c];
-        const float4 gn = dry ? zero4 : s_yf[(row + 1) * FP_TX + c];
-        float h = __fmaf_rn(-ly, gn.x - gs.x, __fmaf_rn(-lx, fe.x - fw.x, s_h[o]));
-        float hu = __fmaf_rn(-ly, gn.y - gs.y, __fmaf_rn(-lx, fe.y - fw.z, s_hu[o]));
-        float hv = __fmaf_rn(-ly, gn.z - gs.w, __fmaf_rn(-lx, fe.w - fw.w, s_hv[o]));
-        if (h < 0.0f) { neg += 1; h = 0.0f; }
-        if (h <= FP_H_EPS_F) {
-            hu = 0.0f; hv = 0.0f;
-        } else {
-            const float u = __fdividef(hu, h), v = __fdividef(hv, h);
-            const float sp = sqrt_fast(__fmaf_rn(u, u, v * v));
-            const unsigned short oc = k == 0 ? occA : occB;
-            const float n0 = k == 0 ? n0A : n0B;
-            const int np = oc < FP_NP_CAP ? oc : FP_NP_CAP;
-            const float nm = S.coupling ? n0 + (float)np * n0 : n0;
-            const float denom = __fmaf_rn(dt * g * nm * nm * sp, pow_m43(h), 1.0f);
-            hu = __fdividef(hu, denom);
-            hv = __fdividef(hv, denom);
+        unsigned char *buf = smem_raw + b * L::BUF;
+        float *s_h = reinterpret_cast<float *>(buf);
+        float *s_hu = s_h + L::PLANE;
+        float *s_hv = s_hu + L::PLANE;
+        float *s_z = s_hv + L::PLANE;
+        const float *s_n0 = reinterpret_cast<const float *>(buf + L::N0);
+        const unsigned short *s_occ = reinterpret_cast<const unsigned short *>(buf + L::OCC);
+        if (tid < TY / FP_BLK_ROWS) s_blk[tid] = 0;
+        if (tid == CTL && S.blk_runs != nullptr)  // profiling: the blocks this update computes
+            for (int r = y0 / FP_BLK_ROWS; r <= (min(ny, y0 + TY) - 1) / FP_BLK_ROWS; ++r)
+                S.blk_runs[r * tiles_x + bx] += 1u;
+        // this thread's two cells' n0 and evacuee counts (staged from the tile's
+        // first cell - 4)
+        const float n0A = s_n0[row * ROWW + lane + 4], n0B = s_n0[row * ROWW + lane + 36];
+        const unsigned short occA = s_occ[row * ROWW + lane + 4], occB = s_occ[row * ROWW + lane + 36];
+
+        const float g = S.g, hg = 0.5f * g;
+        const float h_in = s_hin;
+
+        const int oA = (row + 1) * ROWW + lane + 4, oB = oA + 32;
+        const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+
+        // 2. faces from registers: this thread's cells A (column lane) and B (lane +
+        // 32) of row `row`; each computes its west and south face.  West
+        // neighbours arrive by shuffle (lane 0: the halo cell, and cell 31 for B).
+        const int iA = x0 + lane, iB = iA + 32;
+        float4 fwA = zero4, fwB = zero4;
+        {
+            const Side cA = staged_side(s_h, s_hu, s_hv, s_z, oA);
+            const Side cB = staged_side(s_h, s_hu, s_hv, s_z, oB);
+            Side wA = shfl_up_side(cA), wB = shfl_up_side(cB);
+            const Side c31 = shfl_side(cA, 31);
+            if (lane == 0) {
+                wA = staged_side(s_h, s_hu, s_hv, s_z, oA - 1);
+                wB = c31;
+            }
+            if (cj < ny) {
+                fwA = x_face(S, g, hg, h_in, wA, cA, iA, cj);
+                fwB = x_face(S, g, hg, h_in, wB, cB, iB, cj);
+                if (iA == 0) s_bx[0][row] = fwA.x;
+                if (iA == nx) s_bx[1][row] = fwA.x;
+                if (iB == nx) s_bx[1][row] = fwB.x;
+            }
+            if (cj <= ny) {
+                const Side bA = staged_side(s_h, s_hu, s_hv, s_z, oA - ROWW);
+                const Side bB = staged_side(s_h, s_hu, s_hv, s_z, oB - ROWW);
+                const float4 gA = y_face(S, g, hg, h_in, bA, cA, iA, cj);
+                const float4 gB = y_face(S, g, hg, h_in, bB, cB, iB, cj);
+                s_yf[row * FP_TX + lane] = gA;
+                s_yf[row * FP_TX + lane + 32] = gB;
+                if (cj == 0) { s_by[0][lane] = gA.x; s_by[0][lane + 32] = gB.x; }
+                if (cj == ny) { s_by[1][lane] = gA.x; s_by[1][lane + 32] = gB.x; }
+            }
         }
-        if (!(h == h) || !(hu == hu) || !(hv == hv)) bad = 1;
-        if (h > FP_H_EPS_F) {
-            hk_[k] = h; huk_[k] = hu; hvk_[k] = hv;
-            sk_[k] = __fdividef(fmaxf(fabsf(hu), fabsf(hv)), h) + sqrt_fast(g * h);
+        // 3. the tile's edge faces: north (row y0 + TY) of each column by warps 0
+        // and 1, east (column x0 + 64) of each row by warp 2 (the control warp,
+        // the last, has none)
+        if (tid < FP_TX + TY) {
+            if (tid >= FP_TX) {
+                const int r = tid - FP_TX, j = y0 + r, i = x0 + FP_TX;
+                float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (j < ny && i <= nx) {
+                    const int o = (r + 1) * ROWW + FP_TX + 4;
+                    f = x_face(S, g, hg, h_in, staged_side(s_h, s_hu, s_hv, s_z, o - 1),
+                               staged_side(s_h, s_hu, s_hv, s_z, o), i, j);
+                    if (i == nx) s_bx[1][r] = f.x;
+                }
+                s_xe[r] = f;
+            } else {
+                const int c = tid, i = x0 + c, j = y0 + TY;
+                float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (j <= ny) {
+                    const int o = (TY + 1) * ROWW + c + 4;
+                    f = y_face(S, g, hg, h_in, staged_side(s_h, s_hu, s_hv, s_z, o - ROWW),
+                               staged_side(s_h, s_hu, s_hv, s_z, o), i, j);
+                    if (j == ny && i < nx) s_by[1][c] = f.x;
+                }
+                s_yf[TY * FP_TX + c] = f;
+            }
         }
-        if (h >= FP_H_DRY_F) wet = 1;
-        const size_t gi = gA + 32 * k;
-        S.h[p2][gi] = h;
-        S.hu[p2][gi] = hu;
-        S.hv[p2][gi] = hv;
-        if ((k == 0 ? occA : occB) != 0) S.occ[par][gi] = 0;
-    }
-    // CFL: the exact (correctly rounded) wave speed only for cells whose
-    // approximate speed is within 1e-5 of the warp's approximate maximum -- the
-    // approximation errs by < 1e-6, so the exact maximum is among them.
-    // (non-negative floats order as their bit patterns: one warp-reduce
-    // instruction each)
-    {
-        const float a = fmaxf(sk_[0], sk_[1]);
-        const float amax = __uint_as_float(__reduce_max_sync(0xffffffffu, a >= 0.0f ? __float_as_uint(a) : 0u));
-        const float thr = amax * (1.0f - 1e-5f);
+        __syncthreads();
+
+        // 4. Eq. (2) + friction for this thread's two cells; east fluxes by shuffle
+        // (lane 31: cell 32's west face, and the tile's east edge for B)
+        float smax = 0.0f;
+        float sk_[2] = {-1.0f, -1.0f}, hk_[2] = {0.f, 0.f}, huk_[2] = {0.f, 0.f}, hvk_[2] = {0.f, 0.f};
+        int wet = 0, neg = 0, bad = 0, nz = 0;
+        const float dt = s_dtf, lx = s_lx, ly = s_lx;
+        const int p2 = par ^ 1;
+        float4 feA = shfl_down_f4(fwA), feB = shfl_down_f4(fwB);
+        const float4 fB0 = shfl_f4(fwB, 0);
+        if (lane == 31) {
+            feA = fB0;
+            feB = s_xe[row];
+        }
 #pragma unroll
-        for (int k = 0; k < 2; ++k)
-            if (sk_[k] >= 0.0f && sk_[k] >= thr) smax = fmaxf(smax, fp_wave_speed(g, hk_[k], huk_[k], hvk_[k]));
-    }
-    // CTA reductions -> next clock slot
-    smax = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(smax)));
-    {
-        const unsigned fl = __reduce_or_sync(0xffffffffu, (unsigned)(wet | (bad << 1)));
-        wet = (int)(fl & 1u);
-        bad = (int)(fl >> 1);
-        neg = (int)__reduce_add_sync(0xffffffffu, (unsigned)neg);
-    }
-    if (lane == 0) {
-        s_red[row] = smax;
-        s_redi[row] = wet | (bad << 1) | (neg << 2);
-    }
-    __syncthreads();
-    // boundary tiles only: FP64 accumulation of the mass through the domain edges (one warp)
-    const bool edge_x0 = x0 == 0, edge_x1 = x0 + FP_TX >= nx, edge_y0 = y0 == 0, edge_y1 = y0 + TY >= ny;
-    if (!dry && row == 1 && (edge_x0 || edge_x1 || edge_y0 || edge_y1)) {
-        const double dtdx = (double)dt * (double)S.dx;
-        for (int r = lane; r < TY; r += 32) {
-            const int j = y0 + r;
-            if (j >= ny) break;
-            if (edge_x0) S.bflux[2 * nx + j] += (double)s_bx[0][r] * dtdx;
-            if (edge_x1) S.bflux[2 * nx + ny + j] -= (double)s_bx[1][r] * dtdx;
+        for (int k = 0; k < 2; ++k) {
+            const bool ok = k == 0 ? okA : okB;
+            if (!ok) continue;
+            const int c = lane + 32 * k;
+            const int o = (row + 1) * ROWW + c + 4;
+            const float4 fw = k == 0 ? fwA : fwB;
+            const float4 fe = k == 0 ? feA : feB;
+            const float4 gs = s_yf[row * FP_TX + c];
+            const float4 gn = s_yf[(row + 1) * FP_TX + c];
+            float h = __fmaf_rn(-ly, gn.x - gs.x, __fmaf_rn(-lx, fe.x - fw.x, s_h[o]));
+            float hu = __fmaf_rn(-ly, gn.y - gs.y, __fmaf_rn(-lx, fe.y - fw.z, s_hu[o]));
+            float hv = __fmaf_rn(-ly, gn.z - gs.w, __fmaf_rn(-lx, fe.w - fw.w, s_hv[o]));
+            if (h < 0.0f) { neg += 1; h = 0.0f; }
+            if (h <= FP_H_EPS_F) {
+                hu = 0.0f; hv = 0.0f;
+            } else {
+                const float u = __fdividef(hu, h), v = __fdividef(hv, h);
+                const float sp = sqrt_fast(__fmaf_rn(u, u, v * v));
+                const unsigned short oc = k == 0 ? occA : occB;
+                const float n0 = k == 0 ? n0A : n0B;
+                const int np = oc < FP_NP_CAP ? oc : FP_NP_CAP;
+                const float nm = S.coupling ? n0 + (float)np * n0 : n0;
+                const float denom = __fmaf_rn(dt * g * nm * nm * sp, pow_m43(h), 1.0f);
+                hu = __fdividef(hu, denom);
+                hv = __fdividef(hv, denom);
+            }
+            if (!(h == h) || !(hu == hu) || !(hv == hv)) bad = 1;
+            if (h > FP_H_EPS_F) {
+                hk_[k] = h; huk_[k] = hu; hvk_[k] = hv;
+                sk_[k] = __fdividef(fmaxf(fabsf(hu), fabsf(hv)), h) + sqrt_fast(g * h);
+            }
+            if (h >= FP_H_DRY_F) wet = 1;
+            if (h != 0.0f) nz = 1;
+            const size_t gi = gA + 32 * k;
+            S.h[p2][gi] = h;
+            S.hu[p2][gi] = hu;
+            S.hv[p2][gi] = hv;
+            if ((k == 0 ? occA : occB) != 0) S.occ[par][gi] = 0;
         }
-        for (int c = lane; c < FP_TX; c += 32) {
-            const int i = x0 + c;
-            if (i >= nx) break;
-            if (edge_y0) S.bflux[i] += (double)s_by[0][c] * dtdx;
-            if (edge_y1) S.bflux[nx + i] -= (double)s_by[1][c] * dtdx;
+        // water flags of the output plane's 64 x 8 blocks (h = 0 implies hu = hv = 0 above)
+        if (__any_sync(0xffffffffu, nz) && lane == 0) atomicOr(&s_blk[row / FP_BLK_ROWS], 1);
+        // CFL: the exact (correctly rounded) wave speed only for cells whose
+        // approximate speed is within 1e-5 of the warp's approximate maximum -- the
+        // approximation errs by < 1e-6, so the exact maximum is among them.
+        // (non-negative floats order as their bit patterns: one warp-reduce
+        // instruction each)
+        {
+            const float a = fmaxf(sk_[0], sk_[1]);
+            const float amax = __uint_as_float(__reduce_max_sync(0xffffffffu, a >= 0.0f ? __float_as_uint(a) : 0u));
+            const float thr = amax * (1.0f - 1e-5f);
+#pragma unroll
+            for (int k = 0; k < 2; ++k)
+                if (sk_[k] >= 0.0f && sk_[k] >= thr) smax = fmaxf(smax, fp_wave_speed(g, hk_[k], huk_[k], hvk_[k]));
+        }
+        // CTA reductions -> next clock slot
+        smax = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(smax)));
+        {
+            const unsigned fl = __reduce_or_sync(0xffffffffu, (unsigned)(wet | (bad << 1)));
+            wet = (int)(fl & 1u);
+            bad = (int)(fl >> 1);
+            neg = (int)__reduce_add_sync(0xffffffffu, (unsigned)neg);
+        }
+        if (lane == 0) {
+            s_red[row] = smax;
+            s_redi[row] = wet | (bad << 1) | (neg << 2);
+        }
+        __syncthreads();
+        if (S.blk_wet[0] != nullptr && tid < TY / FP_BLK_ROWS && y0 + tid * FP_BLK_ROWS < ny)
+            S.blk_wet[p2][(y0 / FP_BLK_ROWS + tid) * ((nx + FP_TX - 1) / FP_TX) + bx] = (unsigned char)s_blk[tid];
+        // boundary tiles only: FP64 accumulation of the mass through the domain edges (one warp)
+        const bool edge_x0 = x0 == 0, edge_x1 = x0 + FP_TX >= nx, edge_y0 = y0 == 0, edge_y1 = y0 + TY >= ny;
+        if (row == TY - 2 && (edge_x0 || edge_x1 || edge_y0 || edge_y1)) {
+            const double dtdx = (double)dt * (double)S.dx;
+            for (int r = lane; r < TY; r += 32) {
+                const int j = y0 + r;
+                if (j >= ny) break;
+                if (edge_x0) S.bflux[2 * nx + j] += (double)s_bx[0][r] * dtdx;
+                if (edge_x1) S.bflux[2 * nx + ny + j] -= (double)s_bx[1][r] * dtdx;
+            }
+            for (int c = lane; c < FP_TX; c += 32) {
+                const int i = x0 + c;
+                if (i >= nx) break;
+                if (edge_y0) S.bflux[i] += (double)s_by[0][c] * dtdx;
+                if (edge_y1) S.bflux[nx + i] -= (double)s_by[1][c] * dtdx;
+            }
+        }
+        if (row == TY - 1) {  // the control warp folds the tile's warp results into the CTA's
+            const float m = lane < NT / 32 ? s_red[lane] : 0.0f;
+            const int fl = lane < NT / 32 ? s_redi[lane] : 0;
+            const unsigned mb = __reduce_max_sync(0xffffffffu, __float_as_uint(m));
+            const unsigned fo = __reduce_or_sync(0xffffffffu, (unsigned)(fl & 3));
+            const unsigned ng = __reduce_add_sync(0xffffffffu, (unsigned)(fl >> 2));
+            if (lane == 0) {
+                s_accm = fmaxf(s_accm, __uint_as_float(mb));
+                s_accf |= (int)fo;
+                s_accn += (int)ng;
+                if (t == 0) {  // tile 0 advances the clock
+                    FpClock *nxt = &S.clock[(slot + 1) & 3];
+                    const long long dt_ticks = s_dt;
+                    const long long t1 = s_t + dt_ticks;
+                    if (S.dt_fixed > 0) {
+                        float sm = __uint_as_float(s_smax0);
+                        if (S.has_inflow && s_hin > FP_H_EPS_F) sm = fmaxf(sm, __fsqrt_rn(__fmul_rn(S.g, s_hin)));
+                        if (__fmul_rn(sm, s_dtf) > __fmul_rn(S.cfl, S.dx)) atomicAdd(&S.cnt->cfl_over, 1u);
+                    }
+                    nxt->t = t1;
+                    nxt->step = s_step + (dt_ticks > 0 ? 1 : 0);
+                    nxt->h_in = (float)fp_hydro_depth(S, t1);
+                    if (S.clock[slot].wet) atomicOr(&nxt->wet, 1);
+                    FpClock *old = &S.clock[(slot + 2) & 3];
+                    old->smax_bits = 0u;
+                    old->wet = 0;
+                }
+            }
         }
     }
-    if (tid == 0) {
-        float m = 0.0f;
-        int w = 0, b = 0, ng = 0;
-        for (int k = 0; k < NT / 32; ++k) {
-            m = fmaxf(m, s_red[k]);
-            w |= s_redi[k] & 1;
-            b |= (s_redi[k] >> 1) & 1;
-            ng += s_redi[k] >> 2;
-        }
+    // the CTA's reductions -> the next clock slot
+    if (tid == CTL) {
         FpClock *nxt = &S.clock[(slot + 1) & 3];
-        if (m > 0.0f) atomicMax(&nxt->smax_bits, __float_as_uint(m));
-        if (w) atomicOr(&nxt->wet, 1);
-        if (b) fp_set_err(S, FP_ERR_NAN);
-        if (ng) atomicAdd(&S.cnt->neg_depth, (unsigned long long)ng);
-        if (bx == 0 && by == 0) {
-            const long long dt_ticks = s_dt;
-            const long long t1 = s_t + dt_ticks;
-            nxt->t = t1;
-            nxt->step = s_step + (dt_ticks > 0 ? 1 : 0);
-            nxt->h_in = (float)fp_hydro_depth(S, t1);
-            if (S.clock[slot].wet) atomicOr(&nxt->wet, 1);
-            FpClock *old = &S.clock[(slot + 2) & 3];
-            old->smax_bits = 0u;
-            old->wet = 0;
-        }
+        if (s_accm > 0.0f) atomicMax(&nxt->smax_bits, __float_as_uint(s_accm));
+        if (s_accf & 1) atomicOr(&nxt->wet, 1);
+        if (s_accf & 2) fp_set_err(S, FP_ERR_NAN);
+        if (s_accn) atomicAdd(&S.cnt->neg_depth, (unsigned long long)s_accn);
     }
-    __syncthreads();
     return true;
 }
 

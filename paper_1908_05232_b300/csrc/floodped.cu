@@ -133,7 +133,9 @@ struct fp_sim {
         long long done = 0;                 // windows advanced (check cadence)
         int suspend = 0;                    // windows left on the plain update
     } win;
-    double prof[5] = {0, 0, 0, 0, 0};  // steps, hash ms, flood ms, pedestrian chain ms, step ms
+    // steps, hash ms, flood ms, pedestrian chain ms, step ms, cell updates the flood kernel computed
+    double prof[6] = {0, 0, 0, 0, 0, 0};
+    unsigned *blk_runs = nullptr;  // profiling: flood updates computed per 64 x 8 block
 
     // Every copy of the library is stream-ordered on the simulation's stream and
     // complete when this returns (a plain cudaMemcpy from pageable memory may
@@ -164,6 +166,16 @@ struct fp_sim {
             if (g) { cudaGraphExecDestroy(g); g = nullptr; }
     }
     size_t plane_elems() const { return (size_t)S.px * (size_t)(S.ny + 2); }
+    size_t flag_blocks() const {
+        return (size_t)((S.nx + FP_TX - 1) / FP_TX) * (size_t)((S.ny + FP_BLK_ROWS - 1) / FP_BLK_ROWS);
+    }
+    // every block "maybe wet": after any write of the water state from outside
+    // the flood update, the next two updates run every tile
+    cudaError_t reset_water_flags() {
+        cudaError_t e = cudaSuccess;
+        for (int p = 0; p < 2 && e == cudaSuccess; ++p) e = cudaMemsetAsync(S.blk_wet[p], 1, flag_blocks(), stream);
+        return e;
+    }
 };
 
 static int encode_tma_rows(fp_sim *s, int rows, FpTmaSet out[2], const FpSim *planes = nullptr) {
@@ -174,6 +186,11 @@ static int encode_tma_rows(fp_sim *s, int rows, FpTmaSet out[2], const FpSim *pl
     cuuint64_t strides[1] = {(cuuint64_t)S.px * 4};
     cuuint32_t box[2] = {(cuuint32_t)(FP_TX + 8), (cuuint32_t)(rows + 2)};
     cuuint32_t es[2] = {1, 1};
+    // n0 and the evacuee counts: the tile's rows only; the uint16 box starts
+    // at the tile's first cell - 4 too (16-byte aligned), the pitch px is a
+    // multiple of 8 cells
+    cuuint32_t box_c[2] = {(cuuint32_t)(FP_TX + 8), (cuuint32_t)rows};
+    cuuint64_t strides16[1] = {(cuuint64_t)S.px * 2};
     for (int p = 0; p < 2; ++p) {
         float *ptrs[4] = {S.h[p], S.hu[p], S.hv[p], S.z};
         CUtensorMap *maps[4] = {&out[p].h, &out[p].hu, &out[p].hv, &out[p].z};
@@ -183,6 +200,14 @@ static int encode_tma_rows(fp_sim *s, int rows, FpTmaSet out[2], const FpSim *pl
                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
             if (r != CUDA_SUCCESS) return s->fail(FP_ECUDA, "cuTensorMapEncodeTiled failed");
         }
+        CUresult r = enc(&out[p].n0, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(S.n0), dims, strides,
+                         box_c, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r == CUDA_SUCCESS)
+            r = enc(&out[p].occ, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, S.occ[p], dims, strides16, box_c, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return s->fail(FP_ECUDA, "cuTensorMapEncodeTiled failed");
     }
     return FP_OK;
 }
@@ -250,6 +275,8 @@ static int prepare(fp_sim *s) {
     }
     e = cudaMemcpyAsync(s->S.clock, ring, sizeof(ring), cudaMemcpyHostToDevice, s->stream);
     if (e != cudaSuccess) return s->cuda_fail(e, "clock write");
+    e = s->reset_water_flags();
+    if (e != cudaSuccess) return s->cuda_fail(e, "water flags");
     fp_launch_init_clock(s->S, s->par, s->slot, s->stream);
     e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return s->cuda_fail(e, "prepare");
@@ -334,6 +361,7 @@ static int ensure_window(fp_sim *s) {
         F.h[p] = W.fb[p][0];
         F.hu[p] = W.fb[p][1];
         F.hv[p] = W.fb[p][2];
+        F.blk_wet[p] = nullptr;
     }
     const int rc = encode_tma_rows(s, s->tile_rows, W.tma, &F);
     if (rc != FP_OK) return rc;
@@ -382,8 +410,31 @@ static int step_profiled_persistent(fp_sim *s, int n) {
     return FP_OK;
 }
 
+// Cell updates the flood kernel computed (tiles not skipped as dry) since
+// profiling was switched on.
+static int count_computed_cells(fp_sim *s) {
+    const FpSim &S = s->S;
+    const int bw = (S.nx + FP_TX - 1) / FP_TX, bh = (S.ny + FP_BLK_ROWS - 1) / FP_BLK_ROWS;
+    std::vector<unsigned> runs((size_t)bw * bh);
+    const cudaError_t e = s->copy(runs.data(), s->blk_runs, runs.size() * sizeof(unsigned));
+    if (e != cudaSuccess) return s->cuda_fail(e, "profile block counts");
+    double cells = 0.0;
+    for (int r = 0; r < bh; ++r)
+        for (int c = 0; c < bw; ++c)
+            cells += (double)runs[(size_t)r * bw + c] * std::min(FP_TX, S.nx - c * FP_TX) *
+                     std::min(FP_BLK_ROWS, S.ny - r * FP_BLK_ROWS);
+    s->prof[5] = cells;
+    return FP_OK;
+}
+
+static int step_profiled_kernels(fp_sim *s, int n);
+
 static int step_profiled(fp_sim *s, int n) {
-    if (s->mode == FP_MODE_PERSISTENT) return step_profiled_persistent(s, n);
+    const int rc = s->mode == FP_MODE_PERSISTENT ? step_profiled_persistent(s, n) : step_profiled_kernels(s, n);
+    return rc != FP_OK ? rc : count_computed_cells(s);
+}
+
+static int step_profiled_kernels(fp_sim *s, int n) {
     if ((int)s->prof_ev.size() < 4 * n) {
         for (int k = (int)s->prof_ev.size(); k < 4 * n; ++k) {
             cudaEvent_t e;
@@ -433,7 +484,7 @@ int fp_sim_create(const fp_config *cfg, fp_sim **out) {
     FpSim &S = s->S;
     S.nx = c.nx;
     S.ny = c.ny;
-    S.px = ((c.nx + 3) / 4) * 4 + 2 * FP_PADX;
+    S.px = ((c.nx + 2 * FP_PADX + 7) / 8) * 8;  // >= 4 guard columns each side; 16-byte rows of uint16
     S.dx = c.dx;
     S.g = c.g;
     S.cfl = c.cfl;
@@ -460,6 +511,7 @@ int fp_sim_create(const fp_config *cfg, fp_sim **out) {
     ok &= (S.n0 = s->dalloc<float>(pe)) != nullptr;
     ok &= (S.occ[0] = s->dalloc<unsigned short>(pe + 2)) != nullptr;
     ok &= (S.occ[1] = s->dalloc<unsigned short>(pe + 2)) != nullptr;
+    for (int p = 0; p < 2; ++p) ok &= (S.blk_wet[p] = s->dalloc<unsigned char>(s->flag_blocks())) != nullptr;
     unsigned char *bcd[4];
     for (int e = 0; e < 4; ++e) {
         const int len = e < 2 ? c.nx : c.ny;
@@ -932,6 +984,7 @@ int fp_surrogate_advance(fp_sim *s, fp_surrogate *sur, int32_t n_windows, const 
                 F.hu[p] = W.fb[p][1];
                 F.hv[p] = W.fb[p][2];
                 F.occ[p] = W.fb_occ;
+                F.blk_wet[p] = nullptr;  // the fallback planes start from the window's start state
             }
             F.clock = W.clock;
             F.bflux = W.bflux;
@@ -975,7 +1028,8 @@ int fp_surrogate_advance(fp_sim *s, fp_surrogate *sur, int32_t n_windows, const 
         if (W.suspend > 0) W.suspend -= 1;
         W.done += 1;
     }
-    e = cudaStreamSynchronize(s->stream);
+    e = s->reset_water_flags();  // the window wrote the water state
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return s->cuda_fail(e, "surrogate window");
     if (fp_sur_error_bits(sur) & FP_ERR_TIMEOUT) return s->fail(FP_ETIMEOUT, "tensor-core completion wait timed out");
@@ -988,6 +1042,14 @@ int fp_set_profiling(fp_sim *s, int32_t on) {
     if (e != cudaSuccess) return s->cuda_fail(e, "profiling switch");
     s->profiling = on != 0;
     for (double &v : s->prof) v = 0.0;
+    if (s->profiling) {
+        const size_t nb = s->flag_blocks();
+        if (!s->blk_runs && !(s->blk_runs = s->dalloc<unsigned>(nb))) return s->fail(FP_ENOMEM, "profile counters");
+        e = cudaMemsetAsync(s->blk_runs, 0, nb * sizeof(unsigned), s->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+        if (e != cudaSuccess) return s->cuda_fail(e, "profile counters");
+    }
+    s->S.blk_runs = s->profiling ? s->blk_runs : nullptr;
     return FP_OK;
 }
 
@@ -1183,6 +1245,7 @@ int fp_batch_step(fp_batch *b, int32_t n_steps) {
             return FP_EINVAL;
         }
         b->h_sims[k] = m->S;
+        b->h_sims[k].blk_runs = nullptr;
         b->h_maps[2 * k] = m->tma16[0];
         b->h_maps[2 * k + 1] = m->tma16[1];
     }

@@ -3,12 +3,15 @@
 //
 // HBM layout (one simulation):
 //   - water planes h, hu, hv (two copies, ping-pong by step parity), bed z and
-//     base Manning n0: float, padded pitch `px` floats, cell (i, j) stored at
-//     (j + 1) * px + i + FP_PADX.  The 4-float guard columns keep every TMA box
-//     start 16-byte aligned and every 4-cell group a 16-byte vector; guard rows
-//     j = -1 and j = ny are zero and never read as cells.
+//     base Manning n0: float, padded pitch `px` floats (a multiple of 8, at
+//     least nx + 8), cell (i, j) stored at (j + 1) * px + i + FP_PADX.  The
+//     4-float guard columns keep every TMA box start 16-byte aligned and every
+//     4-cell group a 16-byte vector; guard rows j = -1 and j = ny are zero and
+//     never read as cells.
 //   - occ: uint16 evacuees per cell with the same padding, incremented by the
 //     hash kernel (Section 2.4 N_p) and cleared by the flood kernel that uses it.
+//   - blk_wet: per 64 x 8-cell block and plane parity, 0 if the block holds no
+//     water in that plane (written by the flood update that produced it).
 //   - walkable / exit / navigation codes: uint8[ny * nx], unpadded.
 //   - pedestrians: arrays of 32-byte fp_ped records (float4 x,y,vx,vy + uint4
 //     id,meta,timer,v0), "A" sorted by spatial-hash bin, "B" the step output.
@@ -107,7 +110,14 @@ struct FpSim {
     int phase_ts_steps;            // steps recorded in phase_ts (4 stamps per step + 1)
     long long dt_fixed;            // fixed time step in ticks (0: CFL step)
     const unsigned char *tile_mask;  // per flood tile: 0 = skip (nullptr: every tile runs)
+    // Water flags of 64 x 8-cell blocks, by the parity of the state plane they
+    // describe: 0 = the block holds h = hu = hv = 0 there (written by the flood
+    // update that produced the plane); 1 = maybe water.  nullptr: not used.
+    unsigned char *blk_wet[2];
+    unsigned *blk_runs;  // profiling only: flood updates computed per block (nullptr: not counted)
 };
+
+#define FP_BLK_ROWS 8
 
 __device__ __forceinline__ size_t fp_pidx(const FpSim &S, int i, int j) {
     return (size_t)(j + 1) * (size_t)S.px + (size_t)(i + FP_PADX);
@@ -197,7 +207,8 @@ __device__ __forceinline__ void fp_set_err(const FpSim &S, unsigned int bit) { a
 
 // TMA descriptors of the four staged planes for one step parity
 struct FpTmaSet {
-    CUtensorMap h, hu, hv, z;
+    CUtensorMap h, hu, hv, z;  // FP32 planes, box (FP_TX + 8) x (rows + 2): a tile and its one-cell halo
+    CUtensorMap n0, occ;       // FP32 / uint16 planes, box (FP_TX + 8) x rows
 };
 
 // launchers (defined in flood.cu / peds.cu)

@@ -116,17 +116,19 @@ __global__ void __launch_bounds__(kPT, 2) persistent_kernel(const __grid_constan
                                                             const __grid_constant__ FpSim S, int par0, int slot0,
                                                             int nsteps, unsigned *bar) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ __align__(8) unsigned long long mbar;
+    __shared__ __align__(8) unsigned long long mbar[2];
     __shared__ int s_base[kMaxCTAs];
     __shared__ StepCtl s_ctl;
     FpCounters *C = S.cnt;
     const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x;
     const int nbin1 = S.nbins + 1;
     const int chunk = (nbin1 + G - 1) / G;
-    const int tiles_x = (S.nx + FP_TX - 1) / FP_TX, tiles_y = (S.ny + kPTY - 1) / kPTY;
-    const int ntiles = tiles_x * tiles_y;
-    if (tid == 0) mbar_init(&mbar);
-    unsigned parity = 0;
+    const int ntiles = ((S.nx + FP_TX - 1) / FP_TX) * ((S.ny + kPTY - 1) / kPTY);
+    if (tid == 0) {
+        mbar_init(&mbar[0]);
+        mbar_init(&mbar[1]);
+    }
+    unsigned phase = 0u;
 
     // H: hash the current records of B
     {
@@ -215,11 +217,7 @@ __global__ void __launch_bounds__(kPT, 2) persistent_kernel(const __grid_constan
                 if (s_ctl.dt_ticks > 0) C->ped_updates += (unsigned long long)nA;
             }
         }
-        for (int t = cta; t < ntiles; t += G) {
-            if (!flood_tile<kPTY>(tm.p[par], S, par, slot, t % tiles_x, t / tiles_x, smem_raw, &mbar, parity))
-                return;
-            parity ^= 1u;
-        }
+        if (!flood_tiles<kPTY>(tm.p[par], S, par, slot, cta, G, ntiles, smem_raw, mbar, phase)) return;
         __syncthreads();
         const StepCtl ctl = s_ctl;
         const bool hash_next = s + 1 < nsteps;

@@ -111,3 +111,24 @@ def test_pedestrian_outside_walkable_cells_rejected(P):
     recs["x"][0] = 0.5 * sc.dx  # the west wall column
     with pytest.raises(P.FloodPedError):
         sim.add_pedestrians(recs)
+
+
+@pytest.mark.parametrize("mode", ["kernels", "persistent"])
+def test_dry_tiles_skipped_after_two_steps(P, mode):
+    """A dry domain (walls, no inflow): the first two steps after the state is
+    set compute every tile, later steps only tile (0, 0) (it advances the
+    clock); the profile counts the computed cell updates."""
+    from paper_1908_05232_b300 import _native as N
+    sc = S.plain_coupled_128(seed=2, n_peds=64)
+    sc.bc_s[:] = S.BC_WALL
+    sc.evac_trigger = 0
+    m = N.FP_MODE_PERSISTENT if mode == "persistent" else N.FP_MODE_KERNELS
+    sim = P.from_scenario(sc, mode=m)
+    N.fp_set_profiling(sim.h, 1)
+    sim.step(10)
+    prof = sim.profile()
+    N.fp_set_profiling(sim.h, 0)
+    assert prof["steps"] == 10
+    assert prof["flood_cells"] == 2 * sc.nx * sc.ny + 8 * 64 * 16
+    assert all(np.all(f == 0) for f in fields(sim))
+    assert sim.counters()["error_flags"] == 0

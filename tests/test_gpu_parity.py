@@ -485,3 +485,30 @@ def test_mostly_dry_grid_parity(P, O, tile_rows):
     sim.synchronize()
     assert abs(sim.counters()["t_ticks"] - o.t_ticks) <= 120
     assert_flood_close(sim, o, atol=1e-4)
+
+
+def test_state_write_reopens_skipped_tiles(P):
+    """Tiles whose stencil stayed dry are skipped after two steps; writing the
+    state from the host (water put into that dry region) makes every tile run
+    again: the run continues exactly as a fresh simulation from that state."""
+    import copy
+    sc = S.random_wet_state(300, 200, dx=0.8, seed=23, bc=(S.BC_WALL,) * 4)
+    sc.h[:, 90:] = 0.0
+    sc.hu[:, 90:] = 0.0
+    sc.hv[:, 90:] = 0.0
+    a = run_gpu(P, sc, 40)
+    h, hu, hv = fields(a)
+    assert np.all(h[:, 200:] == 0.0)
+    h[60:120, 220:280] += 0.5
+    P._native.fp_set_state(a.h, h, hu, hv)
+    sc2 = copy.deepcopy(sc)
+    sc2.h, sc2.hu, sc2.hv = h.copy(), hu.copy(), hv.copy()
+    b = P.from_scenario(sc2)
+    a.step(60)
+    b.step(60)
+    a.synchronize()
+    b.synchronize()
+    for x, y in zip(fields(a), fields(b)):
+        assert np.array_equal(x, y)
+    assert np.any(fields(a)[0][:, 200:] != fields(run_gpu(P, sc, 100))[0][:, 200:])
+

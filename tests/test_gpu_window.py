@@ -202,3 +202,32 @@ def test_window_coupled_run_keeps_invariants(P):
     ci = np.floor(p["x"][live] / sc.dx).astype(int)
     cj = np.floor(p["y"][live] / sc.dx).astype(int)
     assert np.all(sc.walkable[cj, ci] == 1)
+
+
+def test_window_output_then_plain_steps(P):
+    """Plain steps after a window (which may put water into tiles that stayed
+    dry before it) continue exactly as a fresh simulation from the window's
+    end state."""
+    import copy
+    sc = fixed(S.random_wet_state(300, 140, dx=0.8, seed=13, bc=(S.BC_WALL,) * 4))
+    sc.h[:, 120:] = 0.0
+    sc.hu[:, 120:] = 0.0
+    sc.hv[:, 120:] = 0.0
+    a = P.from_scenario(sc)
+    a.step(40)
+    a.synchronize()
+    before = a.field(H)
+    st = a.surrogate_advance(net(P), 1, mass_tol=1e9, check_every=0)
+    assert st.tiles_net >= 1
+    after = fields(a)
+    assert np.any((before == 0.0) & (after[H] != 0.0))
+    sc2 = copy.deepcopy(sc)
+    sc2.h, sc2.hu, sc2.hv = [x.copy() for x in after]
+    b = P.from_scenario(sc2)
+    a.step(24)
+    b.step(24)
+    a.synchronize()
+    b.synchronize()
+    for x, y in zip(fields(a), fields(b)):
+        assert np.array_equal(x, y)
+

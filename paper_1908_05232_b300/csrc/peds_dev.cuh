@@ -241,15 +241,24 @@ __device__ __forceinline__ void ped_group(const FpSim &S, int par, const StepCtl
         auto rec_of = [&](int t) { return t < n0 ? rk0[0] + t : t < n01 ? rk0[1] + t - n0 : rk0[2] + t - n01; };
         int kn = sub < ntot ? rec_of(sub) : 0;
         float4 qn = sub < ntot ? *reinterpret_cast<const float4 *>(&S.pedA[2 * kn]) : make_float4(0.f, 0.f, 0.f, 0.f);
+        // The force is carried in units of 2^-18 m/s^2 from the start (kA
+        // times a power of two: every product below is the unscaled one times
+        // 2^18, exactly).  A lane sums at most 256 terms (< 2^22 each) in
+        // int32 before adding them to its int64 total.  With vdn = 0,
+        // inv_vdn = 0 makes w = 0: no side-step term, as the model says.
+        constexpr float kAs = kA * 262144.0f;
 #pragma unroll 1
-        for (int t = sub; t < ntot; t += kG) {
-            const int k = kn;
-            const float4 q = qn;
-            if (t + kG < ntot) {
-                kn = rec_of(t + kG);
-                qn = *reinterpret_cast<const float4 *>(&S.pedA[2 * kn]);
-            }
-            {
+        for (int t0 = sub; t0 < ntot; t0 += 256 * kG) {
+            const int tend = min(ntot, t0 + 256 * kG);
+            int ax = 0, ay = 0;
+#pragma unroll 1
+            for (int t = t0; t < tend; t += kG) {
+                const int k = kn;
+                const float4 q = qn;
+                if (t + kG < ntot) {
+                    kn = rec_of(t + kG);
+                    qn = *reinterpret_cast<const float4 *>(&S.pedA[2 * kn]);
+                }
                 if (k == j) continue;
                 const float rx = x - q.x, ry = y - q.y;
                 if (fabsf(rx) >= kR || fabsf(ry) >= kR) continue;
@@ -257,20 +266,20 @@ __device__ __forceinline__ void ped_group(const FpSim &S, int par, const StepCtl
                 if (d2 >= kR * kR || d2 <= 0.0f) continue;
                 const float d = sqrt_approx(d2);
                 const float invd = rcp_approx(d);
-                const float fm = kA * (__expf((2.0f * kRb - d) * (1.0f / kB)) - fcut);
+                const float fm = kAs * (__expf((2.0f * kRb - d) * (1.0f / kB)) - fcut);
                 const float nx_ = rx * invd, ny_ = ry * invd;
                 float fx = fm * nx_, fy = fm * ny_;
-                if (vdn > 0.0f) {
-                    const float w = -__fmaf_rn(vdx, nx_, vdy * ny_) * inv_vdn;
-                    if (w > 0.0f) {
-                        const float sw = kSide * w * fm;
-                        fx = __fmaf_rn(sw, -ny_, fx);
-                        fy = __fmaf_rn(sw, nx_, fy);
-                    }
+                const float w = -__fmaf_rn(vdx, nx_, vdy * ny_) * inv_vdn;
+                if (w > 0.0f) {
+                    const float sw = kSide * w * fm;
+                    fx = __fmaf_rn(sw, -ny_, fx);
+                    fy = __fmaf_rn(sw, nx_, fy);
                 }
-                Fx += (long long)__float2int_rn(fx * 262144.0f);
-                Fy += (long long)__float2int_rn(fy * 262144.0f);
+                ax += __float2int_rn(fx);
+                ay += __float2int_rn(fy);
             }
+            Fx += ax;
+            Fy += ay;
         }
     }
 #pragma unroll

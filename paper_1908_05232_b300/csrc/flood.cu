@@ -28,7 +28,7 @@ __global__ void __launch_bounds__(512, 2) flood_batch_kernel(const FpSim *__rest
     const FpSim &S = sims[lo];
     const int ntiles = tile_off[lo + 1] - tile_off[lo];
     unsigned phase = 0u;
-    flood_tiles<16>(maps[2 * lo + par], S, par, slot, t - tile_off[lo], ntiles, ntiles, smem_raw, mbar, phase);
+    flood_tiles<16>(maps[2 * lo + par], S, par, slot, t - tile_off[lo], ntiles, ntiles, smem_raw, mbar, phase, false);
 }
 
 // One CTA per SM slot, each taking every gridDim.x-th tile.
@@ -45,7 +45,7 @@ __global__ void __launch_bounds__(32 * TY, 32 / TY) flood_kernel(const __grid_co
     __syncthreads();
     const int ntiles = ((S.nx + FP_TX - 1) / FP_TX) * ((S.ny + TY - 1) / TY);
     unsigned phase = 0u;
-    flood_tiles<TY>(tm, S, par, slot, blockIdx.x, gridDim.x, ntiles, smem_raw, mbar, phase);
+    flood_tiles<TY>(tm, S, par, slot, blockIdx.x, gridDim.x, ntiles, smem_raw, mbar, phase, true);
 }
 
 // U^0 wave-speed max and wet flag into clock slot `slot` (after a state change).

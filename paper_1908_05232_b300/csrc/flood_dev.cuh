@@ -316,13 +316,15 @@ __device__ __forceinline__ void decide_modes(const FpSim &S, int par, int first,
 // CTA: warp r owns row r of a tile, lane l its cells l and l + 32.  Loads are
 // double-buffered: the next tile's TMA copies are issued before the current
 // tile waits for its own.  mbar[2] (initialised, count 1) and their phase bits
-// (bit b: buffer b) belong to the caller (only thread 0's copy is used); no thread may
-// still read the stage buffers of an earlier call.  Returns false if a TMA
-// transfer did not complete (error flag set; the other buffer's copy, if one
-// was in flight, waited for).
+// (bit b: buffer b) belong to the caller (only the control thread's copy is
+// used); no thread may still read the stage buffers of an earlier call.  Returns false if a TMA
+// transfer did not complete (error flag set).  speculative: issue the first
+// tile's loads before its mode is decided (lower latency; a skipped first tile
+// is loaded all the same).
 template <int TY>
 __device__ bool flood_tiles(const FpTmaSet &tm, const FpSim &S, int par, int slot, int first, int stride,
-                            int ntiles, unsigned char *smem_raw, unsigned long long *mbar, unsigned &phase) {
+                            int ntiles, unsigned char *smem_raw, unsigned long long *mbar, unsigned &phase,
+                            bool speculative) {
     using L = FloodSmem<TY>;
     constexpr int NT = 32 * TY;
     static_assert(TY % FP_BLK_ROWS == 0 && TY >= 8, "whole water-flag blocks; edge-face, flux and control warps apart");
@@ -367,11 +369,13 @@ __device__ bool flood_tiles(const FpTmaSet &tm, const FpSim &S, int par, int slo
     auto stage = [&](int t, int b) {
         stage_tile<TY>(tm, smem_raw + b * L::BUF, &mbar[b], (t % tiles_x) * FP_TX, (t / tiles_x) * TY);
     };
-    // the first tile's loads go out before its mode is known (they overlap the
-    // flag loads); tile 0 waits for them whatever its mode
-    if (tid == CTL) stage(first, 0);
+    // speculative: the first tile's loads go out before its mode is known
+    // (they overlap the flag loads) and are waited for whatever the mode;
+    // otherwise the mode is decided first, so that a skipped tile loads nothing
+    if (tid == CTL && speculative) stage(first, 0);
     decide_modes<TY>(S, par, first, stride, ntiles, 0, inflow_on, s_mode);
     __syncthreads();
+    if (tid == CTL && !speculative && s_mode[0] == kTileLoad) stage(first, 0);
 
     // Per tile k (buffer b = k & 1): the control thread waits for the tile's
     // loads; one barrier; it issues the next tile's loads into the other buffer
@@ -388,7 +392,7 @@ __device__ bool flood_tiles(const FpTmaSet &tm, const FpSim &S, int par, int slo
         }
         if (tid == CTL) {
             int ok = 1;
-            if (mode == kTileLoad || k == 0) {
+            if (mode == kTileLoad || (k == 0 && speculative)) {
                 ok = mbar_wait_phase(&mbar[b], (phase >> b) & 1u);
                 phase ^= 1u << b;
                 if (!ok) fp_set_err(S, FP_ERR_TIMEOUT);

@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(kPT, 2) persistent_kernel(const __grid_constan
                 if (s_ctl.dt_ticks > 0) C->ped_updates += (unsigned long long)nA;
             }
         }
-        if (!flood_tiles<kPTY>(tm.p[par], S, par, slot, cta, G, ntiles, smem_raw, mbar, phase)) return;
+        if (!flood_tiles<kPTY>(tm.p[par], S, par, slot, cta, G, ntiles, smem_raw, mbar, phase, true)) return;
         __syncthreads();
         const StepCtl ctl = s_ctl;
         const bool hash_next = s + 1 < nsteps;

@@ -34,9 +34,12 @@ struct PersistTma {
     FpTmaSet p[2];
 };
 
-// Grid barrier: arrival counter bar[0], generation bar[1].  Each CTA reads the
-// generation before arriving, so the last arriver's bump is always seen as a
-// change.  The wait is bounded; on timeout the error flag is set and every CTA
+// Grid barrier on one word: every CTA adds 1 except CTA 0, which adds
+// 2^31 - (gridDim.x - 1), so the word's top bit flips exactly when the last
+// CTA has arrived (and the low bits are back to zero); each CTA spins until
+// the top bit differs from the value it saw on arrival.  The spin is bounded;
+// past 2^10 polls it also watches the error word, so that CTAs leave soon
+// after another CTA failed; on timeout the error flag is set and the CTA
 // returns (those still waiting time out in turn).
 __device__ __forceinline__ bool grid_sync(unsigned *bar, const FpSim &S) {
     __shared__ int s_fail;
@@ -44,26 +47,24 @@ __device__ __forceinline__ bool grid_sync(unsigned *bar, const FpSim &S) {
     asm volatile("fence.proxy.async.global;" ::: "memory");
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned *vgen = bar + 1;
-        const unsigned gen = *vgen;
+        const unsigned add = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1u) : 1u;
         __threadfence();
-        const unsigned arrived = atomicAdd(bar, 1u);
+        const unsigned old = atomicAdd(bar, add);
+        volatile unsigned *vb = bar;
         int fail = 0;
-        if (arrived == gridDim.x - 1) {
-            atomicExch(bar, 0u);
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
-        } else {
-            int it = 0;
-            while (*vgen == gen) {
-                if (++it > (1 << 22)) { fail = 1; break; }
-                __nanosleep(32);
+        for (int it = 0; ((*vb ^ old) & 0x80000000u) == 0u; ++it) {
+            if (it >= (1 << 10)) {
+                if (it >= (1 << 22) || (*(volatile unsigned *)&S.cnt->err & FP_ERR_TIMEOUT) != 0u) {
+                    fail = 1;
+                    break;
+                }
+                __nanosleep(64);
             }
         }
         __threadfence();
         asm volatile("fence.proxy.async.global;" ::: "memory");
         if (fail) fp_set_err(S, FP_ERR_TIMEOUT);
-        s_fail = fail || (*(volatile unsigned *)&S.cnt->err & FP_ERR_TIMEOUT) != 0u;
+        s_fail = fail;
     }
     __syncthreads();
     return !s_fail;
@@ -256,6 +257,9 @@ cudaError_t fp_launch_persistent(const FpSim &S, const FpTmaSet tma[2], int par,
     tm.p[1] = tma[1];
     FpSim s = S;
     void *args[] = {(void *)&tm, (void *)&s, (void *)&par, (void *)&slot, (void *)&nsteps, (void *)&bar};
+    // the barrier word starts at zero (a barrier that timed out leaves it partly counted)
+    const cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
     return cudaLaunchCooperativeKernel((const void *)persistent_kernel, dim3(ctas), dim3(kPT), args,
                                        (size_t)smem_dynamic, st);
 }

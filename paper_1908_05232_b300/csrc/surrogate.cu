@@ -7,17 +7,18 @@
 // Forward (inference and training): each layer is an implicit GEMM on the
 // 5th-generation tensor cores -- tcgen05.mma, kind::f16 with BF16 operands in
 // shared memory and an FP32 accumulator in tensor memory (TMEM):
-//   M = 128 output pixels of one row, N = 32 output channels (16 for the last
-//   layer, 3 used), K = 9 taps x input channels in steps of 16.
-// A CTA (128 threads) is persistent over output row segments.  It keeps the
-// layer's weights in shared memory in the canonical no-swizzle K-major layout
-// (core matrices of 8 rows x 16 bytes; k-cores LBO apart, 8-row groups SBO
-// apart) and stages the three input rows of a segment as
-// [k-core][pixel][8 channels]: the three horizontal taps of an input row are
-// then the same operand shifted by 16 bytes.  One thread issues the MMAs and
-// commits them to an mbarrier (bounded wait); the four warps read their 32
-// TMEM lanes with tcgen05.ld for the bias / ReLU / BF16 epilogue.  TMEM is
-// freed on every exit path.
+//   M = 128 output pixels of one row; per input row and horizontal tap one
+//   MMA with N = 3 x 32 (3 x 16 for the last layer, 3 channels used): the
+//   three vertical taps' weights side by side, accumulating into three output
+//   rows at once; K = input channels in steps of 16.
+// A CTA is persistent over output row segments and warp-specialised (TMA
+// producer, MMA issuer, eight epilogue warps).  It keeps the layer's weights
+// in shared memory in the canonical no-swizzle K-major layout (core matrices
+// of 8 rows x 16 bytes; k-cores LBO apart, 8-row groups SBO apart) and stages
+// input rows as [k-core][pixel][8 channels]: the three horizontal taps of an
+// input row are then the same operand shifted by 16 bytes.  The epilogue warps
+// read their TMEM lanes with tcgen05.ld for the bias / ReLU / BF16 epilogue.
+// Every wait is bounded; TMEM is freed on every exit path.
 //
 // Training: the backward pass (data and weight gradients of every
 // layer, FP32 on the CUDA cores, deterministic reductions), the loss and Adam
@@ -72,7 +73,7 @@ constexpr int kStripRows = 32;  // output rows per work item (one column segment
 constexpr int kRing = 6;        // staged input rows in the ring
 constexpr int kEpiWarps = 8;    // epilogue warps: TMEM lane quarter w % 4, column half w / 4
 constexpr int kConvWarps = kEpiWarps + 2;  // + one TMA producer warp + one MMA issuer warp
-constexpr int kAcc = 4;         // TMEM accumulators (32 columns each): rows in flight between issuer and epilogue
+constexpr int kBlk = 8;         // TMEM accumulator blocks (COUT columns each), one per output row in flight
 
 template <int CIN, int COUT>
 struct ConvGeom {
@@ -81,8 +82,10 @@ struct ConvGeom {
     static constexpr int NPIX = kSeg + 2;          // staged input pixels per row
     static constexpr int ROWB = NKC * NPIX * 16;   // bytes of one staged row (one TMA box)
     static constexpr int SLOT = (ROWB + 127) / 128 * 128;  // ring slot stride (TMA destinations 128-B aligned)
-    static constexpr int WBLK = 2 * COUT * 16;     // bytes per (tap, chunk) weight block
-    static constexpr int WB = 9 * KC * WBLK;       // weight bytes (a multiple of 128)
+    static constexpr int WBLK = 2 * 3 * COUT * 16;  // bytes per (horizontal tap, chunk) weight block
+    static constexpr int WB = 3 * KC * WBLK;        // weight bytes (a multiple of 128)
+    static constexpr int TCOLS = kBlk * COUT;       // TMEM columns (a power of two, >= 32)
+    static_assert((TCOLS & (TCOLS - 1)) == 0 && TCOLS >= 32 && TCOLS <= 512, "TMEM allocation");
     // guard region after the operands (a descriptor-field error reads garbage inside the allocation)
     static constexpr int SMEM = ((WB + kRing * SLOT + 2048) + 1023) / 1024 * 1024;
 };
@@ -137,27 +140,62 @@ __device__ __forceinline__ void tmem_load<16>(unsigned taddr, unsigned (&r)[16])
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// D (TMEM) += A (shared memory) x B (shared memory), kind::f16
+__device__ __forceinline__ void mma_acc(unsigned dcol, unsigned long long ad, unsigned long long bd, unsigned idesc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dcol),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(1u)
+        : "memory");
+}
+
+// clear N columns of this warp's 32 TMEM lanes (completion: tcgen05.wait::st)
+template <int N>
+__device__ __forceinline__ void tmem_zero(unsigned taddr);
+
+template <>
+__device__ __forceinline__ void tmem_zero<8>(unsigned taddr) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1};" ::"r"(taddr), "r"(0u)
+                 : "memory");
+}
+
+template <>
+__device__ __forceinline__ void tmem_zero<16>(unsigned taddr) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, "
+        "%1};" ::"r"(taddr),
+        "r"(0u)
+        : "memory");
+}
+
 // One 3x3 valid convolution of B images (NHWC, BF16, CIN channels) with the
-// packed weights (9 taps x CIN/16 chunks of [2 k-cores][COUT rows][8] BF16).
-// Hidden layers: bias + ReLU, BF16 output with COUT channels.  Last layer
-// (LAST): bias, FP32 output with 3 channels, times kOutScale.
+// packed weights (3 horizontal taps x CIN/16 chunks of [2 k-cores][3 COUT
+// rows][8] BF16, the rows ordered vertical tap 2, 1, 0).  Hidden layers: bias
+// + ReLU, BF16 output with COUT channels.  Last layer (LAST): bias, FP32
+// output with 3 channels, times kOutScale.
 //
 // Work item: one column segment (128 output pixels) of up to kStripRows
-// consecutive output rows of one image.  Warp-specialised pipeline, hand-offs
-// by mbarriers only (every wait bounded):
+// consecutive output rows of one image.  Input row i feeds output rows i - 2,
+// i - 1, i through its vertical taps 2, 1, 0: one MMA per (horizontal tap,
+// chunk) with N = 3 COUT covers all three, writing three consecutive COUT-column
+// accumulator blocks (the block of output row g is g mod kBlk; a window that
+// runs past the last block is split in two MMAs).  Blocks are zero when a row
+// starts: the epilogue clears a block after reading it, so every MMA
+// accumulates.  Warp-specialised pipeline, hand-offs by mbarriers only (every
+// wait bounded):
 //   producer warp (one thread): one TMA per input row into a ring of kRing slots --
 //     the 5-D tensor map (8 channels, pixel, k-core, row, image) lands the row
 //     as [k-core][pixel][8 channels], the MMA's canonical K-major layout;
 //     a slot is refilled once the MMAs that read it completed (free[slot]);
-//   issuer warp (one thread): for output row r, once input rows r..r+2
-//     landed (full[]) and accumulator r % kAcc is free (empty[]), issues the
-//     18 MMAs (9 taps x 2 k-chunks of 16; the three horizontal taps of a row
-//     are the same operand shifted by one pixel; descriptors precomputed) and
-//     commits them to acc_full[r % kAcc] and to free[] of the input row no
-//     later row reads;
+//   issuer warp (one thread): for input row i, once it landed (full[]) and the
+//     block of the output row it starts is clear (empty[]), issues its MMAs
+//     (3 horizontal taps x chunks of 16 channels, the taps being the same
+//     operand shifted by one pixel; descriptors precomputed), commits them to
+//     free[] of the row and, once row i completes output row i - 2, to
+//     acc_full[] of that row's block;
 //   epilogue warps (8): wait acc_full, read their TMEM lane quarter and
-//     column half (tcgen05.ld), free the accumulator (empty[]), then bias /
-//     ReLU / BF16 and the stores.
+//     column half (tcgen05.ld), clear it (tcgen05.st), free the block
+//     (empty[]), then bias / ReLU / BF16 and the stores.
 template <int CIN, int COUT, bool LAST>
 __global__ void __launch_bounds__(kConvWarps * 32) conv3x3_tc_kernel(const __grid_constant__ CUtensorMap tmap, int B,
                                                                      int H, int W,
@@ -165,10 +203,11 @@ __global__ void __launch_bounds__(kConvWarps * 32) conv3x3_tc_kernel(const __gri
                                                                      const float *__restrict__ bias,
                                                                      void *__restrict__ y, unsigned *err) {
     using G = ConvGeom<CIN, COUT>;
+    constexpr int HALF = COUT / 2;
     extern __shared__ __align__(1024) unsigned char sm[];
     unsigned char *s_w = sm;
     unsigned char *s_x = sm + G::WB;
-    __shared__ __align__(8) unsigned long long bar_full[kRing], bar_free[kRing], bar_accf[kAcc], bar_acce[kAcc];
+    __shared__ __align__(8) unsigned long long bar_full[kRing], bar_free[kRing], bar_accf[kBlk], bar_acce[kBlk];
     __shared__ unsigned s_taddr;
     __shared__ volatile int s_abort;
     __shared__ float s_bias[COUT];
@@ -177,12 +216,11 @@ __global__ void __launch_bounds__(kConvWarps * 32) conv3x3_tc_kernel(const __gri
     const int segs = (Wo + kSeg - 1) / kSeg;
     const int chunks = (Ho + kStripRows - 1) / kStripRows;
     const int items = B * segs * chunks;
-    constexpr unsigned IDESC = umma_idesc(kSeg, COUT);
     if (tid < COUT) s_bias[tid] = bias[tid];
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sm_addr(&s_taddr)),
-                     "n"(kAcc * 32));
+                     "n"(G::TCOLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
@@ -190,7 +228,7 @@ __global__ void __launch_bounds__(kConvWarps * 32) conv3x3_tc_kernel(const __gri
             mbar_init_n(sm_addr(&bar_full[k]), 1);
             mbar_init_n(sm_addr(&bar_free[k]), 1);
         }
-        for (int a = 0; a < kAcc; ++a) {
+        for (int a = 0; a < kBlk; ++a) {
             mbar_init_n(sm_addr(&bar_accf[a]), 1);
             mbar_init_n(sm_addr(&bar_acce[a]), kEpiWarps);
         }
@@ -205,6 +243,15 @@ __global__ void __launch_bounds__(kConvWarps * 32) conv3x3_tc_kernel(const __gri
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const unsigned taddr = s_taddr;
     const unsigned xs = sm_addr(s_x), ws = sm_addr(s_w);
+    // the epilogue warps clear every accumulator block before the first MMA
+    if (warp < kEpiWarps) {
+        const unsigned lq = (unsigned)(32 * (warp & 3)) << 16;
+        for (int a = 0; a < kBlk; ++a) tmem_zero<HALF>(taddr + lq + a * COUT + (warp >> 2) * HALF);
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     auto fail = [&]() {
         atomicOr(err, FP_ERR_TIMEOUT);
         s_abort = 1;
@@ -250,75 +297,67 @@ __global__ void __launch_bounds__(kConvWarps * 32) conv3x3_tc_kernel(const __gri
         // ---- MMA issuer.  A descriptor's start-address field is its low bits,
         // so the descriptor of base + d is the base descriptor + d / 16 (every
         // shared address here is below 256 KB): the weight descriptors are
-        // fixed, and an input descriptor is one add.
+        // fixed, a vertical-tap range is one add (16 bytes per weight row), and
+        // an input descriptor is one add.
         if (lane == 0) {
-            unsigned long long bdesc[9 * G::KC];
+            unsigned long long bdesc[3 * G::KC];
 #pragma unroll
-            for (int k = 0; k < 9 * G::KC; ++k) bdesc[k] = umma_desc(ws + k * G::WBLK, COUT * 16, 128);
+            for (int k = 0; k < 3 * G::KC; ++k) bdesc[k] = umma_desc(ws + k * G::WBLK, 3 * COUT * 16, 128);
             const unsigned long long adesc0 = umma_desc(xs, G::NPIX * 16, 128);
-            unsigned q0 = 0, g = 0;  // first input row of the item, output rows issued
+            // instruction descriptors for N = COUT, 2 COUT, 3 COUT
+            const unsigned id1 = umma_idesc(kSeg, COUT), id2 = umma_idesc(kSeg, 2 * COUT),
+                           id3 = umma_idesc(kSeg, 3 * COUT);
+            unsigned q = 0, g0 = 0;  // input rows consumed, output rows of earlier items
             bool ok = true;
             for (int item = blockIdx.x; item < items && ok && !s_abort; item += gridDim.x) {
                 const int rem = item % (segs * chunks);
                 const int oy0 = (rem % chunks) * kStripRows;
                 const int nrow = min(kStripRows, Ho - oy0);
-                for (int r = 0; r < nrow && ok; ++r, ++g) {
-                    for (int t = 0; t < 3 && ok; ++t) {
-                        const unsigned qq = q0 + r + t;
-                        ok = mbar_wait_or_abort(sm_addr(&bar_full[qq % kRing]), (qq / kRing) & 1u, &s_abort);
-                    }
-                    const unsigned a = g % kAcc;
-                    if (ok && g >= kAcc) ok = mbar_wait_or_abort(sm_addr(&bar_acce[a]), (g / kAcc - 1) & 1u, &s_abort);
+                for (int i = 0; i < nrow + 2 && ok; ++i, ++q) {
+                    // output rows i - kyhi .. i - kylo of the item take this row
+                    const int kylo = max(0, i - (nrow - 1)), kyhi = min(2, i);
+                    ok = mbar_wait_or_abort(sm_addr(&bar_full[q % kRing]), (q / kRing) & 1u, &s_abort);
+                    const unsigned gnew = g0 + (unsigned)i;  // the output row this input row starts
+                    if (ok && kylo == 0 && gnew >= (unsigned)kBlk)
+                        ok = mbar_wait_or_abort(sm_addr(&bar_acce[gnew % kBlk]), (gnew / kBlk - 1) & 1u, &s_abort);
                     if (!ok) {
                         fail();
                         break;
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    unsigned slot_off[3];
+                    const int nb = kyhi - kylo + 1;
+                    const unsigned b0 = (g0 + (unsigned)(i - kyhi)) % kBlk;
+                    const int n1 = min(nb, kBlk - (int)b0), n2 = nb - n1;
+                    const unsigned slot_off = (q % kRing) * (G::SLOT / 16);
+                    const unsigned brow = (unsigned)((2 - kyhi) * COUT);
 #pragma unroll
-                    for (int ky = 0; ky < 3; ++ky) slot_off[ky] = ((q0 + r + ky) % kRing) * (G::SLOT / 16);
-                    const unsigned dcol = taddr + a * 32u;
-#pragma unroll
-                    for (int t = 0; t < 9; ++t) {
-                        const int ky = t / 3, kx = t % 3;
+                    for (int kx = 0; kx < 3; ++kx) {
 #pragma unroll
                         for (int c = 0; c < G::KC; ++c) {
                             const unsigned long long ad =
-                                adesc0 + slot_off[ky] + (unsigned)((2 * c * G::NPIX * 16 + kx * 16) / 16);
-                            const unsigned acc = (t | c) != 0 ? 1u : 0u;
-                            asm volatile(
-                                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dcol),
-                                "l"(ad), "l"(bdesc[t * G::KC + c]), "r"(IDESC), "r"(acc)
-                                : "memory");
+                                adesc0 + slot_off + (unsigned)((2 * c * G::NPIX * 16 + kx * 16) / 16);
+                            const unsigned long long bd = bdesc[kx * G::KC + c] + brow;
+                            mma_acc(taddr + b0 * COUT, ad, bd, n1 == 1 ? id1 : n1 == 2 ? id2 : id3);
+                            if (n2 > 0) mma_acc(taddr, ad, bd + (unsigned)(n1 * COUT), n2 == 1 ? id1 : id2);
                         }
                     }
+                    // the input row is read by no later MMA
                     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                                     sm_addr(&bar_accf[a]))
+                                     sm_addr(&bar_free[q % kRing]))
                                  : "memory");
-                    // input row q0 + r is read by no later output row
-                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                                     sm_addr(&bar_free[(q0 + r) % kRing]))
-                                 : "memory");
-                    if (r == nrow - 1) {  // the item's last two input rows
+                    if (kyhi == 2)  // output row i - 2 is complete
                         asm volatile(
                             "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                                sm_addr(&bar_free[(q0 + nrow) % kRing]))
+                                sm_addr(&bar_accf[(g0 + (unsigned)(i - 2)) % kBlk]))
                             : "memory");
-                        asm volatile(
-                            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                                sm_addr(&bar_free[(q0 + nrow + 1) % kRing]))
-                            : "memory");
-                    }
                 }
-                q0 += nrow + 2;
+                g0 += (unsigned)nrow;
             }
         }
     } else {
         // ---- epilogue: warp w owns TMEM lanes (output pixels) 32 (w % 4) ..
-        // 32 (w % 4) + 31 and accumulator columns 16 (w / 4) .. + 15 (the
-        // last layer: warps 0-3, its three channels)
-        constexpr int HALF = COUT / 2;
+        // 32 (w % 4) + 31 and accumulator columns HALF (w / 4) .. + HALF - 1
+        // of a block (the last layer: warps 0-3 hold its three channels)
         const int quarter = warp & 3, half = warp >> 2;
         unsigned g = 0;
         bool ok = true;
@@ -327,8 +366,8 @@ __global__ void __launch_bounds__(kConvWarps * 32) conv3x3_tc_kernel(const __gri
             const int ox0 = (rem / chunks) * kSeg, oy0 = (rem % chunks) * kStripRows;
             const int nrow = min(kStripRows, Ho - oy0);
             for (int r = 0; r < nrow; ++r, ++g) {
-                const unsigned a = g % kAcc;
-                ok = mbar_wait_or_abort(sm_addr(&bar_accf[a]), (g / kAcc) & 1u, &s_abort);
+                const unsigned a = g % kBlk;
+                ok = mbar_wait_or_abort(sm_addr(&bar_accf[a]), (g / kBlk) & 1u, &s_abort);
                 if (!__all_sync(0xffffffffu, ok)) {
                     ok = false;
                     if (lane == 0) fail();
@@ -337,8 +376,10 @@ __global__ void __launch_bounds__(kConvWarps * 32) conv3x3_tc_kernel(const __gri
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 unsigned v[HALF];
                 const bool active = !LAST || half == 0;
-                if (active)
-                    tmem_load<HALF>(taddr + ((unsigned)(32 * quarter) << 16) + a * 32u + (unsigned)(half * HALF), v);
+                const unsigned ta = taddr + ((unsigned)(32 * quarter) << 16) + a * COUT + (unsigned)(half * HALF);
+                if (active) tmem_load<HALF>(ta, v);
+                tmem_zero<HALF>(ta);
+                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 __syncwarp();
                 if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sm_addr(&bar_acce[a])) : "memory");
@@ -371,7 +412,7 @@ __global__ void __launch_bounds__(kConvWarps * 32) conv3x3_tc_kernel(const __gri
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "n"(kAcc * 32));
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "n"(G::TCOLS));
 }
 
 // FP32 (h, hu, hv, z) images -> BF16 NHWC with 16 channels: 0-3 the rounded
@@ -520,16 +561,19 @@ __global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ g, 
     p[k] -= lr * (mk * c1) / (sqrtf(vk * c2) + eps);
 }
 
-// FP32 master (one layer) -> packed BF16 operand blocks and padded bias
+// FP32 master (one layer) -> packed BF16 operand blocks and padded bias: per
+// (horizontal tap kx, chunk c) a block [2 k-cores][3 co_pad rows][8], row
+// (2 - ky) co_pad + n holding output channel n of vertical tap ky
 __global__ void pack_layer_kernel(const float *__restrict__ w, const float *__restrict__ b, int ci_real, int co_real,
                                   int ci_pad, int co_pad, __nv_bfloat16 *__restrict__ pk, float *__restrict__ bias) {
-    const int kc = ci_pad / 16;
-    const int total = 9 * kc * 2 * co_pad * 8;
+    const int kc = ci_pad / 16, rows = 3 * co_pad;
+    const int total = 3 * kc * 2 * rows * 8;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k < co_pad) bias[k] = k < co_real ? b[k] : 0.0f;
     if (k >= total) return;
-    const int e = k % 8, n = (k / 8) % co_pad, j = (k / (8 * co_pad)) % 2;
-    const int c = (k / (16 * co_pad)) % kc, t = k / (16 * co_pad * kc);
+    const int e = k % 8, n3 = (k / 8) % rows, j = (k / (8 * rows)) % 2;
+    const int c = (k / (16 * rows)) % kc, kx = k / (16 * rows * kc);
+    const int ky = 2 - n3 / co_pad, n = n3 % co_pad, t = 3 * ky + kx;
     const int ci = 16 * c + 8 * j + e;
     float v = 0.0f;
     if (ci < ci_real && n < co_real) v = w[((size_t)t * ci_real + ci) * co_real + n];
@@ -606,7 +650,9 @@ cudaError_t launch_conv(const fp_surrogate *s, int layer, const __nv_bfloat16 *x
     if (e != cudaSuccess) return e;
     const long long items =
         (long long)B * (((W - 2) + kSeg - 1) / kSeg) * (((H - 2) + kStripRows - 1) / kStripRows);
-    int grid = (int)std::min<long long>(items, (long long)s->sms * 3);
+    // resident CTAs per SM: shared memory allows 3, TMEM 512 / TCOLS
+    const int per_sm = std::min(3, 512 / G::TCOLS);
+    int grid = (int)std::min<long long>(items, (long long)s->sms * per_sm);
     if (grid < 1) grid = 1;
     conv3x3_tc_kernel<CIN, COUT, LAST><<<grid, kConvWarps * 32, G::SMEM, st>>>(m, B, H, W, s->d_wpack[layer],
                                                                               s->d_bias[layer], y, s->d_err);

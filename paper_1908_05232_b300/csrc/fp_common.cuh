@@ -260,21 +260,23 @@ inline cudaError_t fp_launch(bool pdl, void (*kernel)(KArgs...), dim3 grid, dim3
 // surrogate window (window.cu, surrogate.cu)
 struct fp_surrogate;
 
-// One pixel of the net's input: 16 BF16 channels, (a, b, c, d) rounded, then
-// their rounded remainders, then 8 zeros (32 bytes, 16-byte aligned).
-__device__ __forceinline__ void fp_sur_pack_pixel(float a, float b, float c, float d, void *dst16) {
+// Net activations are BF16 images stored by channel groups of 8 (k-cores):
+// element (image b, row y, column x, channel c) of an H x W image with C
+// channels sits at (((b H + y) (C / 8) + c / 8) W + x) 8 + c % 8, so that a row
+// of one group is contiguous (what the tensor-core operand is staged from).
+// One pixel of the net's input has 16 channels: (a, b, c, d) rounded, then
+// their rounded remainders (group 0), then 8 zeros (group 1).
+__device__ __forceinline__ void fp_sur_pack_pixel(float a, float b, float c, float d, void *group0, void *group1) {
     const __nv_bfloat162 h0 = __floats2bfloat162_rn(a, b), h1 = __floats2bfloat162_rn(c, d);
     const __nv_bfloat162 l0 = __floats2bfloat162_rn(a - __low2float(h0), b - __high2float(h0));
     const __nv_bfloat162 l1 = __floats2bfloat162_rn(c - __low2float(h1), d - __high2float(h1));
-    uint4 w0, w1;
+    uint4 w0;
     w0.x = *reinterpret_cast<const unsigned *>(&h0);
     w0.y = *reinterpret_cast<const unsigned *>(&h1);
     w0.z = *reinterpret_cast<const unsigned *>(&l0);
     w0.w = *reinterpret_cast<const unsigned *>(&l1);
-    w1 = make_uint4(0u, 0u, 0u, 0u);
-    uint4 *o = static_cast<uint4 *>(dst16);
-    o[0] = w0;
-    o[1] = w1;
+    *static_cast<uint4 *>(group0) = w0;
+    *static_cast<uint4 *>(group1) = make_uint4(0u, 0u, 0u, 0u);
 }
 cudaError_t fp_sur_forward_packed(fp_surrogate *sur, const void *x16, int B, int H, int W, float *y, cudaStream_t st);
 unsigned fp_sur_error_bits(fp_surrogate *sur);

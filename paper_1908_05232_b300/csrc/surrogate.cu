@@ -168,7 +168,7 @@ __device__ __forceinline__ void tmem_zero<16>(unsigned taddr) {
         : "memory");
 }
 
-// One 3x3 valid convolution of B images (NHWC, BF16, CIN channels) with the
+// One 3x3 valid convolution of B images (BF16, CIN channels in groups of 8) with the
 // packed weights (3 horizontal taps x CIN/16 chunks of [2 k-cores][3 COUT
 // rows][8] BF16, the rows ordered vertical tap 2, 1, 0).  Hidden layers: bias
 // + ReLU, BF16 output with COUT channels.  Last layer (LAST): bias, FP32
@@ -391,7 +391,9 @@ __global__ void __launch_bounds__(kConvWarps * 32) conv3x3_tc_kernel(const __gri
 #pragma unroll
                         for (int co = 0; co < 3; ++co) yo[co] = (__uint_as_float(v[co]) + s_bias[co]) * kOutScale;
                     } else {
-                        __nv_bfloat16 *yo = static_cast<__nv_bfloat16 *>(y) + pix * COUT + half * HALF;
+                        // channel groups of 8: group half * HALF / 8 + qd of the pixel
+                        __nv_bfloat16 *yo = static_cast<__nv_bfloat16 *>(y) +
+                                            ((((size_t)img * Ho + oy) * (COUT / 8) + half * (HALF / 8)) * Wo + ox) * 8;
                         const float *bb = s_bias + half * HALF;
 #pragma unroll
                         for (int qd = 0; qd < HALF / 8; ++qd) {
@@ -403,7 +405,7 @@ __global__ void __launch_bounds__(kConvWarps * 32) conv3x3_tc_kernel(const __gri
                                     fmaxf(__uint_as_float(v[8 * qd + 2 * e + 1]) + bb[8 * qd + 2 * e + 1], 0.0f);
                                 o[e] = __floats2bfloat162_rn(a0, a1);
                             }
-                            *reinterpret_cast<uint4 *>(yo + 8 * qd) = *reinterpret_cast<const uint4 *>(o);
+                            *reinterpret_cast<uint4 *>(yo + (size_t)qd * Wo * 8) = *reinterpret_cast<const uint4 *>(o);
                         }
                     }
                 }
@@ -415,13 +417,16 @@ __global__ void __launch_bounds__(kConvWarps * 32) conv3x3_tc_kernel(const __gri
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "n"(G::TCOLS));
 }
 
-// FP32 (h, hu, hv, z) images -> BF16 NHWC with 16 channels: 0-3 the rounded
-// values, 4-7 the rounded remainders, 8-15 zero
-__global__ void pack_input_kernel(const float *__restrict__ x4, size_t npix, __nv_bfloat16 *__restrict__ out) {
+// FP32 (h, hu, hv, z) images [B][H][W] -> the net's 16-channel BF16 input
+// (channel groups of 8: the rounded values and remainders, then zeros)
+__global__ void pack_input_kernel(const float *__restrict__ x4, int B, int H, int W, __nv_bfloat16 *__restrict__ out) {
     const size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-    if (p >= npix) return;
+    if (p >= (size_t)B * H * W) return;
     const float4 v = reinterpret_cast<const float4 *>(x4)[p];
-    fp_sur_pack_pixel(v.x, v.y, v.z, v.w, out + p * 16);
+    const size_t row = p / W;  // b H + y
+    const int x = (int)(p % W);
+    __nv_bfloat16 *g0 = out + ((row * 2) * W + x) * 8;
+    fp_sur_pack_pixel(v.x, v.y, v.z, v.w, g0, g0 + (size_t)W * 8);
 }
 
 
@@ -459,11 +464,14 @@ __global__ void sum_partials_kernel(const double *__restrict__ partial, int n, d
     }
 }
 
-__device__ __forceinline__ float act_value(const __nv_bfloat16 *a, size_t i) { return __bfloat162float(a[i]); }
+// activation (image b, row y, column x, channel c) of an H x W x C image, by channel groups of 8
+__device__ __forceinline__ float act_at(const __nv_bfloat16 *a, int b, int y, int x, int c, int H, int W, int C) {
+    return __bfloat162float(a[((((size_t)b * H + y) * (C / 8) + c / 8) * W + x) * 8 + (c & 7)]);
+}
 
 // dW[t][ci][co] += sum_p X[p + off_t][ci] dY[p][co] and db[co] += sum_p dY[p][co],
 // one CTA per (tap, input channel); threads stride over output pixels; fixed-order
-// tree reduction.  X: BF16 [B][H][W][CX] (channel stride CX >= CIN).
+// tree reduction.  X: BF16 H x W images with CX >= CIN channels (groups of 8).
 template <int COUT>
 __global__ void __launch_bounds__(256) conv_bwd_weight_kernel(const __nv_bfloat16 *__restrict__ X, int CX, int CIN,
                                                               const float *__restrict__ dY, int B, int H, int W,
@@ -480,7 +488,7 @@ __global__ void __launch_bounds__(256) conv_bwd_weight_kernel(const __nv_bfloat1
         const int b = (int)(p / ((size_t)Ho * Wo));
         const int r = (int)(p % ((size_t)Ho * Wo));
         const int oy = r / Wo, ox = r % Wo;
-        const float xv = act_value(X, (((size_t)b * H + oy + ky) * W + ox + kx) * CX + ci);
+        const float xv = act_at(X, b, oy + ky, ox + kx, ci, H, W, CX);
         const float *g = dY + p * COUT;
 #pragma unroll
         for (int c = 0; c < COUT; ++c) {
@@ -530,7 +538,7 @@ __global__ void conv_bwd_data_kernel(const float *__restrict__ dY, const float *
     const int iy = r / W, ix = r % W;
     const int Ho = H - 2, Wo = W - 2;
     float acc = 0.0f;
-    if (act_value(X, q * CIN + ci) > 0.0f) {
+    if (act_at(X, b, iy, ix, ci, H, W, CIN) > 0.0f) {
         for (int ky = 0; ky < 3; ++ky) {
             const int oy = iy - ky;
             if (oy < 0 || oy >= Ho) continue;
@@ -617,15 +625,16 @@ PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
     return fn;
 }
 
-// 5-D view of an NHWC BF16 activation [B][H][W][CIN]: (8 channels, pixel,
-// k-core, row, image); a box of (8, kSeg + 2, CIN / 8, 1, 1) is one staged input
-// row segment in the [k-core][pixel][8 channels] layout.
+// 5-D view of a BF16 activation (H x W images, CIN channels in groups of 8):
+// (8 channels, pixel, group, row, image); a box of (8, kSeg + 2, CIN / 8, 1, 1)
+// is one staged input row segment in the [k-core][pixel][8 channels] layout,
+// each group's 130 pixels one contiguous 2080-byte run.
 template <int CIN>
 cudaError_t encode_act_map(CUtensorMap *m, const __nv_bfloat16 *x, int B, int H, int W) {
     auto enc = tmap_encoder();
     if (!enc) return cudaErrorNotSupported;
     const cuuint64_t dims[5] = {8, (cuuint64_t)W, (cuuint64_t)(CIN / 8), (cuuint64_t)H, (cuuint64_t)B};
-    const cuuint64_t strides[4] = {(cuuint64_t)CIN * 2, 16, (cuuint64_t)W * CIN * 2, (cuuint64_t)H * W * CIN * 2};
+    const cuuint64_t strides[4] = {16, (cuuint64_t)W * 16, (cuuint64_t)W * CIN * 2, (cuuint64_t)H * W * CIN * 2};
     const cuuint32_t box[5] = {8, (cuuint32_t)(kSeg + 2), (cuuint32_t)(CIN / 8), 1, 1};
     const cuuint32_t es[5] = {1, 1, 1, 1, 1};
     const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<__nv_bfloat16 *>(x), dims, strides,
@@ -710,7 +719,7 @@ cudaError_t forward_layers(fp_surrogate *s, const __nv_bfloat16 *in0, int B, int
 // forward of B images x [B][H][W][4] keeping every layer's input in d_a; output to out
 cudaError_t forward_keep(fp_surrogate *s, const float *x, int B, int H, int W, float *out, cudaStream_t st) {
     const size_t npix0 = (size_t)B * H * W;
-    pack_input_kernel<<<(unsigned)((npix0 + 255) / 256), 256, 0, st>>>(x, npix0, s->d_a[0]);
+    pack_input_kernel<<<(unsigned)((npix0 + 255) / 256), 256, 0, st>>>(x, B, H, W, s->d_a[0]);
     return forward_layers(s, s->d_a[0], B, H, W, out, st);
 }
 

@@ -124,7 +124,8 @@ __global__ void input_kernel(const __grid_constant__ FpSim S, const float *__res
         const int i = min(max((tile % tiles_x) * kT - kHalo + c, 0), S.nx - 1);
         const int j = min(max((tile / tiles_x) * kT - kHalo + r, 0), S.ny - 1);
         const size_t o = fp_pidx(S, i, j);
-        fp_sur_pack_pixel(h[o], hu[o], hv[o], S.z[o], out + p * 16);
+        __nv_bfloat16 *g0 = out + (((size_t)(b * kIn + r) * 2) * kIn + c) * 8;
+        fp_sur_pack_pixel(h[o], hu[o], hv[o], S.z[o], g0, g0 + kIn * 8);
     }
 }
 

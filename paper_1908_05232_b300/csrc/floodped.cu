@@ -125,7 +125,7 @@ struct fp_sim {
         int *list = nullptr, *batch_of = nullptr, *count = nullptr;  // count[0] net tiles, count[1] failed
         float *resid = nullptr;
         unsigned *maxdiff = nullptr;
-        void *x16 = nullptr;                // net input [tiles][266][266][16] BF16
+        void *x16 = nullptr;                // net input: tiles of 266 x 266 pixels, 16 BF16 channels
         float *dU = nullptr;                // net output [tiles][256][256][3]
         FpTmaSet tma[2];
         cudaStream_t net_stream = nullptr;  // the net runs here, beside the window's pedestrian steps
@@ -353,7 +353,8 @@ static int ensure_window(fp_sim *s) {
     ok &= (W.count = s->dalloc<int>(2)) != nullptr;
     ok &= (W.resid = s->dalloc<float>(nt)) != nullptr;
     ok &= (W.maxdiff = s->dalloc<unsigned>(1)) != nullptr;
-    ok &= (W.x16 = s->dalloc<unsigned char>((size_t)nt * in * 32)) != nullptr;
+    ok &= (W.x16 = s->dalloc<unsigned char>((size_t)nt * (FP_SUR_TILE + 2 * FP_SUR_HALO) *
+                                            fp_sur_pitch(FP_SUR_TILE + 2 * FP_SUR_HALO) * 32)) != nullptr;
     ok &= (W.dU = s->dalloc<float>((size_t)nt * FP_SUR_TILE * FP_SUR_TILE * 3)) != nullptr;
     if (!ok) return s->fail(FP_ENOMEM, "surrogate window buffers");
     FpSim F = S;

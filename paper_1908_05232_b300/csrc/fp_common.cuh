@@ -262,10 +262,13 @@ struct fp_surrogate;
 
 // Net activations are BF16 images stored by channel groups of 8 (k-cores):
 // element (image b, row y, column x, channel c) of an H x W image with C
-// channels sits at (((b H + y) (C / 8) + c / 8) W + x) 8 + c % 8, so that a row
-// of one group is contiguous (what the tensor-core operand is staged from).
+// channels sits at (((b H + y) (C / 8) + c / 8) P + x) 8 + c % 8 with the row
+// pitch P = W rounded up to 32 pixels, so that a row of one group is one
+// contiguous run of 512-byte blocks (what the tensor-core operand is staged
+// from); pixels x >= W of a row are padding.
 // One pixel of the net's input has 16 channels: (a, b, c, d) rounded, then
 // their rounded remainders (group 0), then 8 zeros (group 1).
+__host__ __device__ constexpr int fp_sur_pitch(int w) { return (w + 31) & ~31; }
 __device__ __forceinline__ void fp_sur_pack_pixel(float a, float b, float c, float d, void *group0, void *group1) {
     const __nv_bfloat162 h0 = __floats2bfloat162_rn(a, b), h1 = __floats2bfloat162_rn(c, d);
     const __nv_bfloat162 l0 = __floats2bfloat162_rn(a - __low2float(h0), b - __high2float(h0));

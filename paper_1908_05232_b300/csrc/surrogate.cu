@@ -79,7 +79,7 @@ template <int CIN, int COUT>
 struct ConvGeom {
     static constexpr int KC = CIN / 16;            // K chunks of 16 channels
     static constexpr int NKC = CIN / 8;            // 16-byte k-cores per pixel
-    static constexpr int NPIX = kSeg + 2;          // staged input pixels per row
+    static constexpr int NPIX = kSeg + 32;         // staged input pixels per row (5 blocks of 32; 130 used)
     static constexpr int ROWB = NKC * NPIX * 16;   // bytes of one staged row (one TMA box)
     static constexpr int SLOT = (ROWB + 127) / 128 * 128;  // ring slot stride (TMA destinations 128-B aligned)
     static constexpr int WBLK = 2 * 3 * COUT * 16;  // bytes per (horizontal tap, chunk) weight block
@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(kConvWarps * 32) conv3x3_tc_kernel(const __gri
     __shared__ volatile int s_abort;
     __shared__ float s_bias[COUT];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int Ho = H - 2, Wo = W - 2;
+    const int Ho = H - 2, Wo = W - 2, Pout = fp_sur_pitch(Wo);
     const int segs = (Wo + kSeg - 1) / kSeg;
     const int chunks = (Ho + kStripRows - 1) / kStripRows;
     const int items = B * segs * chunks;
@@ -280,7 +280,7 @@ __global__ void __launch_bounds__(kConvWarps * 32) conv3x3_tc_kernel(const __gri
                     asm volatile(
                         "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
                         "%3, %4, %5, %6}], [%7];" ::"r"(xs + slot * G::SLOT),
-                        "l"(reinterpret_cast<unsigned long long>(&tmap)), "r"(0), "r"(ox0), "r"(0), "r"(oy0 + i),
+                        "l"(reinterpret_cast<unsigned long long>(&tmap)), "r"(0), "r"(ox0 / 32), "r"(0), "r"(oy0 + i),
                         "r"(img), "r"(fb)
                         : "memory");
                 }
@@ -393,7 +393,7 @@ __global__ void __launch_bounds__(kConvWarps * 32) conv3x3_tc_kernel(const __gri
                     } else {
                         // channel groups of 8: group half * HALF / 8 + qd of the pixel
                         __nv_bfloat16 *yo = static_cast<__nv_bfloat16 *>(y) +
-                                            ((((size_t)img * Ho + oy) * (COUT / 8) + half * (HALF / 8)) * Wo + ox) * 8;
+                                            ((((size_t)img * Ho + oy) * (COUT / 8) + half * (HALF / 8)) * Pout + ox) * 8;
                         const float *bb = s_bias + half * HALF;
 #pragma unroll
                         for (int qd = 0; qd < HALF / 8; ++qd) {
@@ -405,7 +405,7 @@ __global__ void __launch_bounds__(kConvWarps * 32) conv3x3_tc_kernel(const __gri
                                     fmaxf(__uint_as_float(v[8 * qd + 2 * e + 1]) + bb[8 * qd + 2 * e + 1], 0.0f);
                                 o[e] = __floats2bfloat162_rn(a0, a1);
                             }
-                            *reinterpret_cast<uint4 *>(yo + (size_t)qd * Wo * 8) = *reinterpret_cast<const uint4 *>(o);
+                            *reinterpret_cast<uint4 *>(yo + (size_t)qd * Pout * 8) = *reinterpret_cast<const uint4 *>(o);
                         }
                     }
                 }
@@ -425,8 +425,9 @@ __global__ void pack_input_kernel(const float *__restrict__ x4, int B, int H, in
     const float4 v = reinterpret_cast<const float4 *>(x4)[p];
     const size_t row = p / W;  // b H + y
     const int x = (int)(p % W);
-    __nv_bfloat16 *g0 = out + ((row * 2) * W + x) * 8;
-    fp_sur_pack_pixel(v.x, v.y, v.z, v.w, g0, g0 + (size_t)W * 8);
+    const int P = fp_sur_pitch(W);
+    __nv_bfloat16 *g0 = out + ((row * 2) * P + x) * 8;
+    fp_sur_pack_pixel(v.x, v.y, v.z, v.w, g0, g0 + (size_t)P * 8);
 }
 
 
@@ -466,7 +467,7 @@ __global__ void sum_partials_kernel(const double *__restrict__ partial, int n, d
 
 // activation (image b, row y, column x, channel c) of an H x W x C image, by channel groups of 8
 __device__ __forceinline__ float act_at(const __nv_bfloat16 *a, int b, int y, int x, int c, int H, int W, int C) {
-    return __bfloat162float(a[((((size_t)b * H + y) * (C / 8) + c / 8) * W + x) * 8 + (c & 7)]);
+    return __bfloat162float(a[((((size_t)b * H + y) * (C / 8) + c / 8) * fp_sur_pitch(W) + x) * 8 + (c & 7)]);
 }
 
 // dW[t][ci][co] += sum_p X[p + off_t][ci] dY[p][co] and db[co] += sum_p dY[p][co],
@@ -625,21 +626,23 @@ PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
     return fn;
 }
 
-// 5-D view of a BF16 activation (H x W images, CIN channels in groups of 8):
-// (8 channels, pixel, group, row, image); a box of (8, kSeg + 2, CIN / 8, 1, 1)
-// is one staged input row segment in the [k-core][pixel][8 channels] layout,
-// each group's 130 pixels one contiguous 2080-byte run.
+// 5-D view of a BF16 activation (H x W images, CIN channels in groups of 8,
+// row pitch P): (256 elements = 32 pixels x 8 channels, 32-pixel block, group,
+// row, image); a box of (256, 5, CIN / 8, 1, 1) is one staged input row
+// segment of 160 pixels in the [k-core][pixel][8 channels] layout, read as
+// 512-byte runs.
 template <int CIN>
 cudaError_t encode_act_map(CUtensorMap *m, const __nv_bfloat16 *x, int B, int H, int W) {
     auto enc = tmap_encoder();
     if (!enc) return cudaErrorNotSupported;
-    const cuuint64_t dims[5] = {8, (cuuint64_t)W, (cuuint64_t)(CIN / 8), (cuuint64_t)H, (cuuint64_t)B};
-    const cuuint64_t strides[4] = {16, (cuuint64_t)W * 16, (cuuint64_t)W * CIN * 2, (cuuint64_t)H * W * CIN * 2};
-    const cuuint32_t box[5] = {8, (cuuint32_t)(kSeg + 2), (cuuint32_t)(CIN / 8), 1, 1};
+    const cuuint64_t P = (cuuint64_t)fp_sur_pitch(W);
+    const cuuint64_t dims[5] = {256, P / 32, (cuuint64_t)(CIN / 8), (cuuint64_t)H, (cuuint64_t)B};
+    const cuuint64_t strides[4] = {512, P * 16, P * CIN * 2, (cuuint64_t)H * P * CIN * 2};
+    const cuuint32_t box[5] = {256, (cuuint32_t)((kSeg + 32) / 32), (cuuint32_t)(CIN / 8), 1, 1};
     const cuuint32_t es[5] = {1, 1, 1, 1, 1};
     const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<__nv_bfloat16 *>(x), dims, strides,
                            box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
@@ -686,6 +689,7 @@ cudaError_t repack(fp_surrogate *s, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// pix: images x rows x row pitch (pixels) of the largest input
 bool ensure_scratch(fp_surrogate *s, size_t pix) {
     if (pix <= s->cap_pix) return true;
     for (int l = 0; l < kLayers; ++l) cudaFree(s->d_a[l]);
@@ -698,6 +702,9 @@ bool ensure_scratch(fp_surrogate *s, size_t pix) {
     ok &= cudaMalloc(&s->d_g1, pix * kWidth * sizeof(float)) == cudaSuccess;
     s->cap_partial = (pix * 3 + 255) / 256 + 1;
     ok &= cudaMalloc(&s->d_partial, s->cap_partial * sizeof(double)) == cudaSuccess;
+    // activation rows are padded to 32 pixels: keep the padding finite
+    for (int l = 0; l < kLayers && ok; ++l)
+        ok = cudaMemset(s->d_a[l], 0, pix * (l == 0 ? kCin0 : kWidth) * sizeof(__nv_bfloat16)) == cudaSuccess;
     if (ok) s->cap_pix = pix;
     return ok;
 }
@@ -770,7 +777,7 @@ int check_err(fp_surrogate *s, cudaError_t e, const char *what) {
 }  // namespace
 
 cudaError_t fp_sur_forward_packed(fp_surrogate *s, const void *x16, int B, int H, int W, float *y, cudaStream_t st) {
-    if (!ensure_scratch(s, (size_t)B * H * W)) return cudaErrorMemoryAllocation;
+    if (!ensure_scratch(s, (size_t)B * H * fp_sur_pitch(W))) return cudaErrorMemoryAllocation;
     return forward_layers(s, static_cast<const __nv_bfloat16 *>(x16), B, H, W, y, st);
 }
 
@@ -862,7 +869,7 @@ int fp_surrogate_set_params(fp_surrogate *s, const float *src, size_t n) {
 
 int fp_surrogate_forward(fp_surrogate *s, const float *x, int32_t B, int32_t H, int32_t W, float *y) {
     if (!s || !x || !y || B < 1 || H < 11 || W < 11) return FP_EINVAL;
-    if (!ensure_scratch(s, (size_t)B * H * W)) {
+    if (!ensure_scratch(s, (size_t)B * H * fp_sur_pitch(W))) {
         fp_note_error("fp_surrogate_forward: allocation failed");
         return FP_ENOMEM;
     }
@@ -872,7 +879,7 @@ int fp_surrogate_forward(fp_surrogate *s, const float *x, int32_t B, int32_t H, 
 int fp_surrogate_gradients(fp_surrogate *s, const float *x, const float *target, int32_t B, int32_t H, int32_t W,
                            float *grads, double *loss) {
     if (!s || !x || !target || B < 1 || H < 11 || W < 11) return FP_EINVAL;
-    if (!ensure_scratch(s, (size_t)B * H * W)) {
+    if (!ensure_scratch(s, (size_t)B * H * fp_sur_pitch(W))) {
         fp_note_error("fp_surrogate_gradients: allocation failed");
         return FP_ENOMEM;
     }

@@ -124,8 +124,9 @@ __global__ void input_kernel(const __grid_constant__ FpSim S, const float *__res
         const int i = min(max((tile % tiles_x) * kT - kHalo + c, 0), S.nx - 1);
         const int j = min(max((tile / tiles_x) * kT - kHalo + r, 0), S.ny - 1);
         const size_t o = fp_pidx(S, i, j);
-        __nv_bfloat16 *g0 = out + (((size_t)(b * kIn + r) * 2) * kIn + c) * 8;
-        fp_sur_pack_pixel(h[o], hu[o], hv[o], S.z[o], g0, g0 + kIn * 8);
+        constexpr int kP = fp_sur_pitch(kIn);
+        __nv_bfloat16 *g0 = out + (((size_t)(b * kIn + r) * 2) * kP + c) * 8;
+        fp_sur_pack_pixel(h[o], hu[o], hv[o], S.z[o], g0, g0 + kP * 8);
     }
 }
 

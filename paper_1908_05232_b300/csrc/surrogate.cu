@@ -70,10 +70,10 @@ __host__ __device__ constexpr unsigned umma_idesc(int M, int N) {
 }
 
 constexpr int kStripRows = 32;  // output rows per work item (one column segment of one image)
-constexpr int kRing = 6;        // staged input rows in the ring
+constexpr int kRing = 4;        // staged input rows in the ring
 constexpr int kEpiWarps = 8;    // epilogue warps: TMEM lane quarter w % 4, column half w / 4
 constexpr int kConvWarps = kEpiWarps + 2;  // + one TMA producer warp + one MMA issuer warp
-constexpr int kBlk = 8;         // TMEM accumulator blocks (COUT columns each), one per output row in flight
+constexpr int kBlk = 4;         // TMEM accumulator blocks (COUT columns each), one per output row in flight
 
 template <int CIN, int COUT>
 struct ConvGeom {
@@ -662,7 +662,7 @@ cudaError_t launch_conv(const fp_surrogate *s, int layer, const __nv_bfloat16 *x
     if (e != cudaSuccess) return e;
     const long long items =
         (long long)B * (((W - 2) + kSeg - 1) / kSeg) * (((H - 2) + kStripRows - 1) / kStripRows);
-    // resident CTAs per SM: shared memory allows 3, TMEM 512 / TCOLS
+    // resident CTAs per SM: three (shared memory allows three), at most 512 / TCOLS (TMEM)
     const int per_sm = std::min(3, 512 / G::TCOLS);
     int grid = (int)std::min<long long>(items, (long long)s->sms * per_sm);
     if (grid < 1) grid = 1;

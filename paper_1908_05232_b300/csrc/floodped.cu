@@ -544,7 +544,7 @@ int fp_sim_create(const fp_config *cfg, fp_sim **out) {
     ok &= (S.bflux = s->dalloc<double>(2 * (size_t)c.nx + 2 * (size_t)c.ny)) != nullptr;
     ok &= (S.partials = s->dalloc<double>(148 * 4)) != nullptr;
     ok &= (S.scan_part = s->dalloc<int>(2048)) != nullptr;
-    ok &= (s->grid_bar = s->dalloc<unsigned>(2)) != nullptr;
+    ok &= (s->grid_bar = s->dalloc<unsigned>(4)) != nullptr;  // persistent kernel: barrier word, 2 tickets
     if (!ok) {
         g_create_error = "device allocation failed";
         fp_destroy(s);

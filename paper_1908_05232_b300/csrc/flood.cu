@@ -1,5 +1,6 @@
 // flood.cu -- per-step kernels of the hydrodynamic update (Section 2.2): the
-// flood tile kernel (one CTA per 64 x TY tile, see flood_dev.cuh), the clock
+// flood kernel (CTAs resident on every SM, each taking a strided list of 64 x TY
+// tiles, see flood_dev.cuh), its batched-ensemble form, the clock
 // initialisation after a state change, and the FP64 water-volume reduction.
 #include "flood_dev.cuh"
 

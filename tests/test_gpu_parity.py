@@ -465,7 +465,7 @@ def test_autotuner_picks_a_valid_shape(P, tmp_path):
     sim.synchronize()
 
 
-@pytest.mark.parametrize("tile_rows", [8, 16])
+@pytest.mark.parametrize("tile_rows", [8, 16, 32])
 def test_mostly_dry_grid_parity(P, O, tile_rows):
     """Water in the west third only, inflow on the east edge: most flood tiles
     are dry (the kernel skips their faces) while the wet front, the inflow

@@ -543,6 +543,7 @@ int fp_sim_create(const fp_config *cfg, fp_sim **out) {
     ok &= (S.cnt = s->dalloc<FpCounters>(1)) != nullptr;
     const size_t cap = (size_t)std::max(1, c.max_peds);
     ok &= (S.pedA = s->dalloc<uint4>(2 * cap)) != nullptr;
+    ok &= (S.posA = s->dalloc<float2>(cap)) != nullptr;
     ok &= (S.pedB = s->dalloc<uint4>(2 * cap)) != nullptr;
     ok &= (S.arch = s->dalloc<uint4>(2 * cap)) != nullptr;
     ok &= (s->read_buf = s->dalloc<uint4>(2 * cap)) != nullptr;

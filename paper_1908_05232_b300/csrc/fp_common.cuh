@@ -100,6 +100,7 @@ struct FpSim {
     FpClock *clock;
     FpCounters *cnt;
     uint4 *pedA, *pedB;        // 2 x uint4 per record
+    float2 *posA;              // positions of the records of A (the neighbour scans read these)
     uint4 *arch;               // records by id (exited ones)
     int *bin_count;            // nbins + 1 (last = exited)
     int *bin_start;            // nbins + 2

@@ -142,6 +142,7 @@ __device__ __forceinline__ void gather_record(const FpSim &S, int i) {
         const int dst = S.bin_start[key] + S.pslot[i];
         S.pedA[2 * dst] = a;
         S.pedA[2 * dst + 1] = b;
+        S.posA[dst] = make_float2(__uint_as_float(a.x), __uint_as_float(a.y));
     }
 }
 

@@ -251,7 +251,7 @@ __device__ __forceinline__ void ped_group(const FpSim &S, int par, const StepCtl
         const int ntot = n01 + (rk1[2] - rk0[2]);
         auto rec_of = [&](int t) { return t < n0 ? rk0[0] + t : t < n01 ? rk0[1] + t - n0 : rk0[2] + t - n01; };
         int kn = sub < ntot ? rec_of(sub) : 0;
-        float4 qn = sub < ntot ? *reinterpret_cast<const float4 *>(&S.pedA[2 * kn]) : make_float4(0.f, 0.f, 0.f, 0.f);
+        float2 qn = sub < ntot ? S.posA[kn] : make_float2(0.f, 0.f);
         // The force is carried in units of 2^-18 m/s^2 from the start (kA
         // times a power of two: every product below is the unscaled one times
         // 2^18, exactly).  A lane sums at most 256 terms (< 2^22 each) in
@@ -265,10 +265,10 @@ __device__ __forceinline__ void ped_group(const FpSim &S, int par, const StepCtl
 #pragma unroll 1
             for (int t = t0; t < tend; t += kG) {
                 const int k = kn;
-                const float4 q = qn;
+                const float2 q = qn;
                 if (t + kG < ntot) {
                     kn = rec_of(t + kG);
-                    qn = *reinterpret_cast<const float4 *>(&S.pedA[2 * kn]);
+                    qn = S.posA[kn];
                 }
                 if (k == j) continue;
                 const float rx = x - q.x, ry = y - q.y;

@@ -205,6 +205,7 @@ __global__ void __launch_bounds__(kPT, 2) persistent_kernel(const __grid_constan
                     const int dst = lookup(key) + S.pslot[i];
                     S.pedA[2 * dst] = a;
                     S.pedA[2 * dst + 1] = b;
+                    S.posA[dst] = make_float2(__uint_as_float(a.x), __uint_as_float(a.y));
                 }
             }
         }

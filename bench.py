@@ -441,7 +441,7 @@ def run_surrogate(args):
     # warm-up: one window each (graphs, scratch buffers), on both simulations
     plain.step(8)
     plain.synchronize()
-    st_w = surr.surrogate_advance(sur, 1)
+    st_w = surr.surrogate_advance(sur, 1, fix_tol=args.surrogate_fix_tol)
     torch.cuda.synchronize()
     ta = plain.counters()["t_ticks"]
     t0 = time.perf_counter()
@@ -451,7 +451,7 @@ def run_surrogate(args):
     tb = plain.counters()["t_ticks"]
     ts0 = surr.counters()["t_ticks"]
     t0 = time.perf_counter()
-    st = surr.surrogate_advance(sur, windows)
+    st = surr.surrogate_advance(sur, windows, fix_tol=args.surrogate_fix_tol)
     t_sur = time.perf_counter() - t0
     tc = surr.counters()["t_ticks"]
     sim_s = (tb - ta) / N.TICKS
@@ -466,6 +466,8 @@ def run_surrogate(args):
             "config": {"workload": "surrogate_2048 (2048x2048 shopping centre, 100,000 pedestrians, barrier, "
                                    "flood from 900 s)", "start_s": t_start, "dt_s": dt,
                        "windows": windows, "steps_per_window": 8, "wet_fraction_at_end": wet_frac,
+                       "guard": {"mass_tol": 1e-4, "fix_tol": args.surrogate_fix_tol, "check_tol_m": 0.01,
+                                 "check_every_windows": 8, "suspend_windows": 8},
                        "setup_s": setup},
             "plain": {"value": rate_p, "unit": "scenario-s/s", "seconds": t_plain},
             "speedup_vs_plain": rate_s / rate_p,
@@ -583,6 +585,8 @@ def main():
     ap.add_argument("--case-steps", type=int, default=4)
     ap.add_argument("--workload", choices=["shopping512", "ensemble", "surrogate"], default="shopping512")
     ap.add_argument("--surrogate-start", type=float, default=1500.0, help="simulated time (s) the surrogate run starts at")
+    ap.add_argument("--surrogate-fix-tol", type=float, default=0.0,
+                    help="accept net tiles up to this mass residual and close their balance (0: the 1e-4 bound)")
     ap.add_argument("--ensemble-size", type=int, default=256)
     args = ap.parse_args()
     if args.ncu_case:

@@ -285,6 +285,9 @@ int fp_surrogate_train_step(fp_surrogate *sur, const float *x, const float *targ
  *      edges| / max(tile volume, 1 cm x tile area) <= guard->mass_tol, where
  *      the inflow is the window length times the mean of the HLL mass fluxes
  *      of the start and end states; U' finite; Courant number of U' <= cfg.cfl;
+ *      with guard->fix_tol > 0 the mass bound is fix_tol instead and every
+ *      accepted tile's h, hu, hv are scaled by one factor so that its volume
+ *      change equals that inflow (mass balance closed exactly per tile);
  *   5. a failed tile is recomputed by the plain update from the window's start
  *      state over the tile grown by FP_SUR_WINDOW cells (cells outside held at
  *      their start values), with the evacuee roughness of the window's end;
@@ -301,6 +304,7 @@ typedef struct fp_surrogate_guard {
     float check_tol;          /* 0.01 m */
     int32_t check_every;      /* 8 windows = 64 steps */
     int32_t suspend_windows;  /* 8 */
+    float fix_tol;            /* 0: off (the mass bound is mass_tol, no correction) */
 } fp_surrogate_guard;
 typedef struct fp_surrogate_stats {
     int64_t windows;          /* windows advanced */

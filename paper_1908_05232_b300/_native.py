@@ -44,7 +44,7 @@ class FpCounters(ctypes.Structure):
 
 class SurGuard(ctypes.Structure):
     _fields_ = [("mass_tol", ctypes.c_float), ("check_tol", ctypes.c_float), ("check_every", ctypes.c_int32),
-                ("suspend_windows", ctypes.c_int32)]
+                ("suspend_windows", ctypes.c_int32), ("fix_tol", ctypes.c_float)]
 
 
 class SurStats(ctypes.Structure):
@@ -279,10 +279,12 @@ class Simulation:
         _check(lib().fp_set_fixed_dt(self.h, float(dt_seconds)), self.h)
 
     def surrogate_advance(self, sur, n_windows, mass_tol=1e-4, check_tol=0.01, check_every=8, suspend_windows=8,
-                          stats=None):
+                          fix_tol=0.0, stats=None):
         """n_windows windows of 8 fixed steps with the surrogate for the flood update;
-        returns the accumulated SurStats (pass it back in to keep accumulating)."""
-        g = SurGuard(float(mass_tol), float(check_tol), int(check_every), int(suspend_windows))
+        returns the accumulated SurStats (pass it back in to keep accumulating).
+        fix_tol > 0: accept net tiles up to that mass residual and close each
+        accepted tile's mass balance exactly."""
+        g = SurGuard(float(mass_tol), float(check_tol), int(check_every), int(suspend_windows), float(fix_tol))
         st = stats if stats is not None else SurStats()
         _check(lib().fp_surrogate_advance(self.h, sur.h, int(n_windows), ctypes.byref(g), ctypes.byref(st)), self.h)
         return st

@@ -878,7 +878,8 @@ int fp_surrogate_advance(fp_sim *s, fp_surrogate *sur, int32_t n_windows, const 
     if (!s) return FP_EINVAL;
     if (!sur || !guard || !st || n_windows < 0) return s->fail(FP_EINVAL, "null surrogate, guard or stats");
     if (s->S.dt_fixed <= 0) return s->fail(FP_EINVAL, "the surrogate window needs a fixed time step (fp_set_fixed_dt)");
-    if (!(guard->mass_tol >= 0.0f) || !(guard->check_tol >= 0.0f) || guard->check_every < 0 ||
+    if (!(guard->mass_tol >= 0.0f) || !(guard->check_tol >= 0.0f) || !(guard->fix_tol >= 0.0f) ||
+        guard->check_every < 0 ||
         guard->suspend_windows < 0)
         return s->fail(FP_EINVAL, "invalid guard parameters");
     if (s->need_prepare) {
@@ -945,7 +946,8 @@ int fp_surrogate_advance(fp_sim *s, fp_surrogate *sur, int32_t n_windows, const 
             cudaStreamWaitEvent(s->stream, W.ev_net, 0);
             cudaMemsetAsync(W.count + 1, 0, sizeof(int), s->stream);
             fp_launch_sur_apply(S, par, W.u0[0], W.u0[1], W.u0[2], W.dU, W.list, W.batch_of, count, W.tiles_x,
-                                &W.clock[slot], guard->mass_tol, W.fail, W.resid, W.count + 1, s->stream);
+                                &W.clock[slot], guard->mass_tol, guard->fix_tol, W.fail, W.resid, W.count + 1,
+                                s->stream);
             e = s->copy(fail.data(), W.fail, count);
             if (e == cudaSuccess) e = s->copy(resid.data(), W.resid, count * sizeof(float));
             if (e == cudaSuccess) e = s->copy(list.data(), W.list, count * sizeof(int));

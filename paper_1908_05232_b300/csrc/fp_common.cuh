@@ -294,7 +294,7 @@ void fp_launch_sur_input(const FpSim &S, const float *h, const float *hu, const 
                          int tiles_x, void *x16, cudaStream_t st);
 void fp_launch_sur_apply(const FpSim &S, int par, const float *h0, const float *hu0, const float *hv0,
                          const float *dU, const int *list, const int *batch_of, int count, int tiles_x,
-                         const FpClock *c0, float mass_tol, unsigned char *fail, float *resid, int *n_fail,
+                         const FpClock *c0, float mass_tol, float fix_tol, unsigned char *fail, float *resid, int *n_fail,
                          cudaStream_t st);
 void fp_launch_sur_occupancy(const FpSim &S, unsigned short *occ, cudaStream_t st);
 void fp_launch_sur_diff(const FpSim &S, const float *a, const float *b, const unsigned char *keep, int tiles_x,

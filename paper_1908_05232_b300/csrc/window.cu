@@ -223,10 +223,12 @@ __device__ float edge_inflow(const FpSim &S, const WindowView &V, int e, int k, 
 
 // One CTA per net tile: write U' into the state planes of parity par, FP64 tile
 // volumes before / after, the trapezoid inflow through the tile edges, and the
-// guard decision.
+// guard decision; with fix_tol > 0 an accepted tile's U' is then scaled to
+// close its mass balance.
 __global__ void __launch_bounds__(256) apply_kernel(const __grid_constant__ FpSim S, int par, WindowView V,
                                                     const int *__restrict__ list, const FpClock *c0, float mass_tol,
-                                                    unsigned char *fail, float *resid, int *n_fail) {
+                                                    float fix_tol, unsigned char *fail, float *resid, int *n_fail) {
+    __shared__ float s_scale;
     __shared__ double red[4][8];
     __shared__ float reds[8];
     __shared__ int redb[8];
@@ -292,11 +294,31 @@ __global__ void __launch_bounds__(256) apply_kernel(const __grid_constant__ FpSi
         const double denom = fmax(s[0] * dx * dx, (double)n * dx * dx * 0.01);
         const double rs = fabs(dM - F) / denom;
         const bool cfl_bad = (double)sm * dts > (double)S.cfl * dx;
-        const bool mass_bad = !(rs <= (double)mass_tol);
+        bool mass_bad = !(rs <= (double)(fix_tol > 0.0f ? fix_tol : mass_tol));
+        // mass fix: one factor on the tile's h, hu, hv brings its volume to
+        // the start volume plus the inflow estimate
+        double scale = 1.0;
+        if (fix_tol > 0.0f && !(bd || cfl_bad || mass_bad)) {
+            const double v1 = s[1] * dx * dx, target = s[0] * dx * dx + F;
+            if (v1 > 0.0) scale = target / v1;
+            else if (target != 0.0) mass_bad = true;
+            if (!(scale >= 0.0)) mass_bad = true;
+        }
         const bool f = bd || cfl_bad || mass_bad;
+        s_scale = f ? 1.0f : (float)scale;
         fail[b] = (unsigned char)((bd ? 4 : 0) | (cfl_bad ? 2 : 0) | (mass_bad ? 1 : 0));
         resid[b] = bd ? __int_as_float(0x7f800000) : (float)rs;
         if (f) atomicAdd(n_fail, 1);
+    }
+    __syncthreads();
+    const float scale = s_scale;
+    if (scale != 1.0f) {
+        for (int k = threadIdx.x; k < n; k += blockDim.x) {
+            const size_t o = fp_pidx(S, x0 + k % w, y0 + k / w);
+            S.h[par][o] *= scale;
+            S.hu[par][o] *= scale;
+            S.hv[par][o] *= scale;
+        }
     }
 }
 
@@ -375,11 +397,11 @@ void fp_launch_sur_input(const FpSim &S, const float *h, const float *hu, const 
 
 void fp_launch_sur_apply(const FpSim &S, int par, const float *h0, const float *hu0, const float *hv0,
                          const float *dU, const int *list, const int *batch_of, int count, int tiles_x,
-                         const FpClock *c0, float mass_tol, unsigned char *fail, float *resid, int *n_fail,
-                         cudaStream_t st) {
+                         const FpClock *c0, float mass_tol, float fix_tol, unsigned char *fail, float *resid,
+                         int *n_fail, cudaStream_t st) {
     if (count <= 0) return;
     WindowView V{h0, hu0, hv0, dU, batch_of, tiles_x};
-    apply_kernel<<<count, 256, 0, st>>>(S, par, V, list, c0, mass_tol, fail, resid, n_fail);
+    apply_kernel<<<count, 256, 0, st>>>(S, par, V, list, c0, mass_tol, fix_tol, fail, resid, n_fail);
 }
 
 void fp_launch_sur_occupancy(const FpSim &S, unsigned short *occ, cudaStream_t st) {

@@ -512,3 +512,20 @@ def test_state_write_reopens_skipped_tiles(P):
         assert np.array_equal(x, y)
     assert np.any(fields(a)[0][:, 200:] != fields(run_gpu(P, sc, 100))[0][:, 200:])
 
+
+
+def test_step_mode_switches_keep_results(P):
+    """Switching between the per-step kernels and the persistent kernel in the
+    middle of a run (the dry-tile flags carry over) gives the bytes of a run in
+    one mode."""
+    from paper_1908_05232_b300 import _native as N
+    sc = S.plain_coupled_128(seed=6)
+    a = P.from_scenario(sc, mode=N.FP_MODE_KERNELS)
+    for mode in (N.FP_MODE_KERNELS, N.FP_MODE_PERSISTENT, N.FP_MODE_KERNELS, N.FP_MODE_PERSISTENT):
+        N.fp_set_step_mode(a.h, mode)
+        a.step(70)
+    a.synchronize()
+    b = run_gpu(P, sc, 280, mode=N.FP_MODE_KERNELS)
+    for x, y in zip(fields(a), fields(b)):
+        assert np.array_equal(x, y)
+    assert np.array_equal(a.peds(), b.peds())

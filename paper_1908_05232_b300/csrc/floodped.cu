@@ -343,7 +343,6 @@ static int ensure_window(fp_sim *s) {
     const int nt = W.tiles_x * W.tiles_y;
     W.ftiles = ((S.nx + FP_TX - 1) / FP_TX) * ((S.ny + s->tile_rows - 1) / s->tile_rows);
     const size_t pe = s->plane_elems();
-    const size_t in = (size_t)(FP_SUR_TILE + 2 * FP_SUR_HALO) * (FP_SUR_TILE + 2 * FP_SUR_HALO);
     bool ok = true;
     for (int k = 0; k < 3; ++k) {
         ok &= (W.u0[k] = s->dalloc<float>(pe)) != nullptr;

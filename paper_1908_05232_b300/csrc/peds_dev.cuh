@@ -250,8 +250,7 @@ __device__ __forceinline__ void ped_group(const FpSim &S, int par, const StepCtl
         const int n0 = rk1[0] - rk0[0], n01 = n0 + (rk1[1] - rk0[1]);
         const int ntot = n01 + (rk1[2] - rk0[2]);
         auto rec_of = [&](int t) { return t < n0 ? rk0[0] + t : t < n01 ? rk0[1] + t - n0 : rk0[2] + t - n01; };
-        int kn = sub < ntot ? rec_of(sub) : 0;
-        float2 qn = sub < ntot ? S.posA[kn] : make_float2(0.f, 0.f);
+        float2 qn = sub < ntot ? S.posA[rec_of(sub)] : make_float2(0.f, 0.f);
         // The force is carried in units of 2^-18 m/s^2 from the start (kA
         // times a power of two: every product below is the unscaled one times
         // 2^18, exactly).  A lane sums at most 256 terms (< 2^22 each) in
@@ -264,15 +263,12 @@ __device__ __forceinline__ void ped_group(const FpSim &S, int par, const StepCtl
             int ax = 0, ay = 0;
 #pragma unroll 1
             for (int t = t0; t < tend; t += kG) {
-                const int k = kn;
                 const float2 q = qn;
-                if (t + kG < ntot) {
-                    kn = rec_of(t + kG);
-                    qn = S.posA[kn];
-                }
-                if (k == j) continue;
+                if (t + kG < ntot) qn = S.posA[rec_of(t + kG)];
+                // the pedestrian itself (the same position bits) gives d2 = 0 and
+                // is skipped with any other pedestrian at zero distance; |rx| or
+                // |ry| >= kR = 1 gives d2 >= 1 after rounding
                 const float rx = x - q.x, ry = y - q.y;
-                if (fabsf(rx) >= kR || fabsf(ry) >= kR) continue;
                 const float d2 = __fmaf_rn(rx, rx, ry * ry);
                 if (d2 >= kR * kR || d2 <= 0.0f) continue;
                 const float d = sqrt_approx(d2);

@@ -73,22 +73,57 @@ __device__ __forceinline__ void load_step_ctl(const FpSim &S, int slot, int nA, 
 
 // Hash one record of B (index i) for the next step: its bin (or the exited bin),
 // its slot in the bin and, for a present evacuee, +1 on its cell's count.
+// Of the active lanes, those in the same run of equal values (runs over the
+// active lanes in lane order) form one group: *first = the run's lowest lane,
+// *n = its size, return = this lane's rank in it.
+__device__ __forceinline__ int lane_run(unsigned act, unsigned long long v, int *first, int *n) {
+    const int lane = threadIdx.x & 31;
+    const unsigned me = 1u << lane, lt = me - 1u;
+    const unsigned below = act & lt;
+    const int src = below ? 31 - __clz(below) : lane;  // the next active lane below
+    const unsigned long long vb = __shfl_sync(act, v, src);
+    const unsigned heads = __ballot_sync(act, !below || vb != v);
+    const int h = 31 - __clz(heads & (lt | me));
+    const unsigned above = heads & ~(lt | me);
+    const unsigned upto = above ? (1u << (__ffs(above) - 1)) - 1u : 0xffffffffu;
+    const unsigned run = act & upto & ~((1u << h) - 1u);
+    *first = h;
+    *n = __popc(run);
+    return __popc(run & lt);
+}
+
 __device__ __forceinline__ void hash_record(const FpSim &S, int i, float x, float y, unsigned meta,
                                             unsigned short *occ) {
+    // Records arrive in bin order, so neighbouring lanes mostly share a bin
+    // (dense crowds put hundreds in one): each run of lanes with the same bin
+    // (same cell) takes its slots (adds its count) with one atomic.
+    const unsigned act = __activemask();
+    const int lane = threadIdx.x & 31;
     int key = S.nbins;
+    size_t o = 0;
+    bool evac = false;
     if (!FP_META_EXITED(meta)) {
         const int ci = fp_cell_of(x, S.dx), cj = fp_cell_of(y, S.dx);
         key = (cj / S.hk) * S.nbx + ci / S.hk;
-        if (FP_META_ROLE(meta) == 0) {
-            const size_t o = fp_pidx(S, ci, cj);
-            const unsigned shift = (unsigned)(o & 1) * 16u;
-            unsigned *w = reinterpret_cast<unsigned *>(occ + (o & ~(size_t)1));
-            const unsigned old = atomicAdd(w, 1u << shift);
-            if (((old >> shift) & 0xffffu) == 0xffffu) fp_set_err(S, FP_ERR_OCC_OVERFLOW);
-        }
+        evac = FP_META_ROLE(meta) == 0;
+        if (evac) o = fp_pidx(S, ci, cj);
     }
+    int first, n;
+    // evacuee counts: runs of evacuees on one cell (other lanes are runs of one)
+    lane_run(act, evac ? (unsigned long long)o : ~0ull - (unsigned long long)lane, &first, &n);
+    if (evac && lane == first) {
+        const unsigned shift = (unsigned)(o & 1) * 16u;
+        unsigned *w = reinterpret_cast<unsigned *>(occ + (o & ~(size_t)1));
+        const unsigned old = atomicAdd(w, (unsigned)n << shift);
+        if (((old >> shift) & 0xffffu) + (unsigned)n > 0xffffu) fp_set_err(S, FP_ERR_OCC_OVERFLOW);
+    }
+    // bin slots: a run of one bin takes consecutive slots
+    const int rank = lane_run(act, (unsigned long long)key, &first, &n);
+    int base = 0;
+    if (lane == first) base = atomicAdd(&S.bin_count[key], n);
+    base = __shfl_sync(act, base, first);
     S.pkey[i] = key;
-    S.pslot[i] = atomicAdd(&S.bin_count[key], 1);
+    S.pslot[i] = base + rank;
 }
 
 // Completed sandbag cell-layers raise the bed (one thread, before the flood

@@ -21,16 +21,17 @@ namespace fpdev {
 
 __constant__ float c_speed[5] = {0.0f, 1.8f, 0.9f, 0.45f, 0.0f};  // Table 1 (index 0: own dry speed)
 
-// single-instruction square root / reciprocal (relative error ~1e-7) for the
-// pair forces, whose rounding enters positions far below parity tolerances
-__device__ __forceinline__ float sqrt_approx(float v) {
+// single-instruction reciprocal square root and base-2 exponential (relative
+// error ~1e-7) for the pair forces, whose rounding enters positions far below
+// parity tolerances
+__device__ __forceinline__ float rsqrt_approx(float v) {
     float r;
-    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(v));
+    asm("rsqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(v));
     return r;
 }
-__device__ __forceinline__ float rcp_approx(float v) {
+__device__ __forceinline__ float exp2_approx(float v) {
     float r;
-    asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(v));
+    asm("ex2.approx.f32 %0, %1;" : "=f"(r) : "f"(v));
     return r;
 }
 constexpr float kTau = 0.5f, kA = 2.0f, kB = 0.3f, kRb = 0.25f, kR = 1.0f, kSide = 0.5f;
@@ -279,7 +280,9 @@ __device__ __forceinline__ void ped_group(const FpSim &S, int par, const StepCtl
     if (live) {
         const float vdn = sqrtf(__fmaf_rn(vdx, vdx, vdy * vdy));
         const float inv_vdn = vdn > 0.0f ? __frcp_rn(vdn) : 0.0f;
-        const float fcut = __expf((2.0f * kRb - kR) * (1.0f / kB));
+        // exp((2 Rb - d) / B) = 2^(log2(e) (2 Rb - d) / B) = 2^(kC - d kL)
+        constexpr float kL = 1.44269504f / kB, kC = 2.0f * kRb * (1.44269504f / kB);
+        const float fcut = exp2_approx(__fmaf_rn(-kR, kL, kC));
         // the three bin rows' record ranges as one list, split over the lanes;
         // the next candidate's record is loaded before the current one is used
         const int n0 = rk1[0] - rk0[0], n01 = n0 + (rk1[1] - rk0[1]);
@@ -306,9 +309,9 @@ __device__ __forceinline__ void ped_group(const FpSim &S, int par, const StepCtl
                 const float rx = x - q.x, ry = y - q.y;
                 const float d2 = __fmaf_rn(rx, rx, ry * ry);
                 if (d2 >= kR * kR || d2 <= 0.0f) continue;
-                const float d = sqrt_approx(d2);
-                const float invd = rcp_approx(d);
-                const float fm = kAs * (__expf((2.0f * kRb - d) * (1.0f / kB)) - fcut);
+                const float invd = rsqrt_approx(d2);
+                const float d = d2 * invd;
+                const float fm = kAs * (exp2_approx(__fmaf_rn(-d, kL, kC)) - fcut);
                 const float nx_ = rx * invd, ny_ = ry * invd;
                 float fx = fm * nx_, fy = fm * ny_;
                 const float w = -__fmaf_rn(vdx, nx_, vdy * ny_) * inv_vdn;

@@ -34,6 +34,28 @@ __device__ __forceinline__ float exp2_approx(float v) {
     asm("ex2.approx.f32 %0, %1;" : "=f"(r) : "f"(v));
     return r;
 }
+
+// Paired FP32 arithmetic (two correctly rounded operations per instruction).
+// The code generator merges a paired multiply into a following paired add even
+// with the rounding spelled out, so products and sums are written as fused
+// multiply-adds with a run-time 1 and -0 (P2): a b - 0 and a 1 + b round once,
+// the same bits as the plain product and sum.
+struct P2 {
+    float2 one, nz;
+};
+__device__ __forceinline__ float2 p2_fma(float2 a, float2 b, float2 c) {
+    float2 r;
+    asm("{ .reg .b64 ra, rb, rc, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n mov.b64 rc, {%6, %7};\n"
+        " fma.rn.f32x2 rd, ra, rb, rc;\n mov.b64 {%0, %1}, rd; }"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return r;
+}
+__device__ __forceinline__ float2 p2_mul(const P2 &k, float2 a, float2 b) { return p2_fma(a, b, k.nz); }
+__device__ __forceinline__ float2 p2_add(const P2 &k, float2 a, float2 b) { return p2_fma(a, k.one, b); }
+__device__ __forceinline__ float2 p2_sub(const P2 &k, float2 a, float2 b) {
+    return p2_fma(make_float2(-b.x, -b.y), k.one, a);
+}
 constexpr float kTau = 0.5f, kA = 2.0f, kB = 0.3f, kRb = 0.25f, kR = 1.0f, kSide = 0.5f;
 constexpr int kTPick = 30 * 1048576, kTDrop = 30 * 1048576;
 constexpr float kBagT = 0.25f;
@@ -295,33 +317,48 @@ __device__ __forceinline__ void ped_group(const FpSim &S, int par, const StepCtl
         // int32 before adding them to its int64 total.  With vdn = 0,
         // inv_vdn = 0 makes w = 0: no side-step term, as the model says.
         constexpr float kAs = kA * 262144.0f;
+        // Two candidates per lane and iteration (t and t + kG) on the paired
+        // FP32 instructions: the same correctly rounded operations as one at a
+        // time, products and sums written as fused multiply-adds with a
+        // run-time 1 and -0 so that none is merged into another.
+        const float one = __fdiv_rn(S.dx, S.dx), nzero = -__fmul_rn(0.0f, S.dx);
+        const P2 K{make_float2(one, one), make_float2(nzero, nzero)};
+        const float2 xx = make_float2(x, x), yy = make_float2(y, y);
+        const float2 vdx2 = make_float2(vdx, vdx), vdy2 = make_float2(vdy, vdy), ivd2 = make_float2(inv_vdn, inv_vdn);
+        const float2 fcut2 = make_float2(-fcut, -fcut);
+        float2 qa = qn, qb = sub + kG < ntot ? S.posA[rec_of(sub + kG)] : make_float2(0.f, 0.f);
 #pragma unroll 1
         for (int t0 = sub; t0 < ntot; t0 += 256 * kG) {
             const int tend = min(ntot, t0 + 256 * kG);
             int ax = 0, ay = 0;
 #pragma unroll 1
-            for (int t = t0; t < tend; t += kG) {
-                const float2 q = qn;
-                if (t + kG < ntot) qn = S.posA[rec_of(t + kG)];
+            for (int t = t0; t < tend; t += 2 * kG) {
+                const float2 pa = qa, pb = qb;
+                const bool hb = t + kG < tend;
+                if (t + 2 * kG < ntot) qa = S.posA[rec_of(t + 2 * kG)];
+                if (t + 3 * kG < ntot) qb = S.posA[rec_of(t + 3 * kG)];
                 // the pedestrian itself (the same position bits) gives d2 = 0 and
                 // is skipped with any other pedestrian at zero distance; |rx| or
                 // |ry| >= kR = 1 gives d2 >= 1 after rounding
-                const float rx = x - q.x, ry = y - q.y;
-                const float d2 = __fmaf_rn(rx, rx, ry * ry);
-                if (d2 >= kR * kR || d2 <= 0.0f) continue;
-                const float invd = rsqrt_approx(d2);
-                const float d = d2 * invd;
-                const float fm = kAs * (exp2_approx(__fmaf_rn(-d, kL, kC)) - fcut);
-                const float nx_ = rx * invd, ny_ = ry * invd;
-                float fx = fm * nx_, fy = fm * ny_;
-                const float w = -__fmaf_rn(vdx, nx_, vdy * ny_) * inv_vdn;
-                if (w > 0.0f) {
-                    const float sw = kSide * w * fm;
-                    fx = __fmaf_rn(sw, -ny_, fx);
-                    fy = __fmaf_rn(sw, nx_, fy);
-                }
-                ax += __float2int_rn(fx);
-                ay += __float2int_rn(fy);
+                const float2 rx = p2_sub(K, xx, make_float2(pa.x, pb.x)), ry = p2_sub(K, yy, make_float2(pa.y, pb.y));
+                const float2 d2 = p2_fma(rx, rx, p2_mul(K, ry, ry));
+                const bool ua = d2.x < kR * kR && d2.x > 0.0f, ub = hb && d2.y < kR * kR && d2.y > 0.0f;
+                if (!ua && !ub) continue;
+                const float2 invd = make_float2(rsqrt_approx(d2.x), rsqrt_approx(d2.y));
+                const float2 d = p2_mul(K, d2, invd);
+                const float2 ea = p2_fma(make_float2(-d.x, -d.y), make_float2(kL, kL), make_float2(kC, kC));
+                const float2 fm = p2_mul(K, make_float2(kAs, kAs),
+                                         p2_add(K, make_float2(exp2_approx(ea.x), exp2_approx(ea.y)), fcut2));
+                const float2 nx_ = p2_mul(K, rx, invd), ny_ = p2_mul(K, ry, invd);
+                float2 fx = p2_mul(K, fm, nx_), fy = p2_mul(K, fm, ny_);
+                const float2 wm = p2_fma(vdx2, nx_, p2_mul(K, vdy2, ny_));
+                const float2 w = p2_mul(K, make_float2(-wm.x, -wm.y), ivd2);
+                const float2 sw = p2_mul(K, p2_mul(K, make_float2(kSide, kSide), w), fm);
+                const float2 fxs = p2_fma(sw, make_float2(-ny_.x, -ny_.y), fx), fys = p2_fma(sw, nx_, fy);
+                if (w.x > 0.0f) { fx.x = fxs.x; fy.x = fys.x; }
+                if (w.y > 0.0f) { fx.y = fxs.y; fy.y = fys.y; }
+                if (ua) { ax += __float2int_rn(fx.x); ay += __float2int_rn(fy.x); }
+                if (ub) { ax += __float2int_rn(fx.y); ay += __float2int_rn(fy.y); }
             }
             Fx += ax;
             Fy += ay;

@@ -560,8 +560,18 @@ def run_case(args):
     else:
         sc = workload(2)
     sim = P.from_scenario(sc, tile_rows=args.tile_rows)
+    if args.case_time > 0:
+        # run up to the simulated time first, then open the profiler range
+        # (ncu --profile-from-start off) around the case's steps only
+        from paper_1908_05232_b300 import _native as N
+        while sim.counters()["t_ticks"] < int(args.case_time * N.TICKS):
+            sim.step(256)
+        sim.synchronize()
+        torch.cuda.cudart().cudaProfilerStart()
     sim.step(args.case_steps)
     sim.synchronize()
+    if args.case_time > 0:
+        torch.cuda.cudart().cudaProfilerStop()
     c = sim.counters()
     print(json.dumps({"case": args.ncu_case, "steps": c["step"], "t_ticks": c["t_ticks"],
                       "n_active": c["n_active"], "error_flags": c["error_flags"]}))
@@ -583,6 +593,8 @@ def main():
     ap.add_argument("--ncu-case", choices=["barrier2048", "wet2048", "shopping512"], default=None,
                     help="short untimed run of one workload, for profiler captures")
     ap.add_argument("--case-steps", type=int, default=4)
+    ap.add_argument("--case-time", type=float, default=0.0,
+                    help="simulated seconds to run before the case's steps (profiler range opened after them)")
     ap.add_argument("--workload", choices=["shopping512", "ensemble", "surrogate"], default="shopping512")
     ap.add_argument("--surrogate-start", type=float, default=1500.0, help="simulated time (s) the surrogate run starts at")
     ap.add_argument("--surrogate-fix-tol", type=float, default=0.0,

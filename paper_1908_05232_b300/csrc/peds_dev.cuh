@@ -313,9 +313,13 @@ __device__ __forceinline__ void ped_group(const FpSim &S, int par, const StepCtl
         float2 qn = sub < ntot ? S.posA[rec_of(sub)] : make_float2(0.f, 0.f);
         // The force is carried in units of 2^-18 m/s^2 from the start (kA
         // times a power of two: every product below is the unscaled one times
-        // 2^18, exactly).  A lane sums at most 256 terms (< 2^22 each) in
-        // int32 before adding them to its int64 total.  With vdn = 0,
-        // inv_vdn = 0 makes w = 0: no side-step term, as the model says.
+        // 2^18, exactly).  A term (|v| < 2^22) is rounded to the nearest
+        // integer, ties to even, by adding 1.5 * 2^23 in FP32: the sum lies in
+        // [2^23, 2^24), where the spacing is 1, and its bits are 0x4B400000 +
+        // rint(v).  A lane sums at most 256 terms modulo 2^32 (the true sum is
+        // below 2^30 in magnitude) before adding them to its int64 total.
+        // With vdn = 0, inv_vdn = 0 makes w = 0: no side-step term, as the
+        // model says.
         constexpr float kAs = kA * 262144.0f;
         // Two candidates per lane and iteration (t and t + kG) on the paired
         // FP32 instructions: the same correctly rounded operations as one at a
@@ -325,12 +329,12 @@ __device__ __forceinline__ void ped_group(const FpSim &S, int par, const StepCtl
         const P2 K{make_float2(one, one), make_float2(nzero, nzero)};
         const float2 xx = make_float2(x, x), yy = make_float2(y, y);
         const float2 vdx2 = make_float2(vdx, vdx), vdy2 = make_float2(vdy, vdy), ivd2 = make_float2(inv_vdn, inv_vdn);
-        const float2 fcut2 = make_float2(-fcut, -fcut);
+        const float2 fcut2 = make_float2(-fcut, -fcut), kRnd = make_float2(12582912.0f, 12582912.0f);
         float2 qa = qn, qb = sub + kG < ntot ? S.posA[rec_of(sub + kG)] : make_float2(0.f, 0.f);
 #pragma unroll 1
         for (int t0 = sub; t0 < ntot; t0 += 256 * kG) {
             const int tend = min(ntot, t0 + 256 * kG);
-            int ax = 0, ay = 0;
+            unsigned ax = 0u, ay = 0u;
 #pragma unroll 1
             for (int t = t0; t < tend; t += 2 * kG) {
                 const float2 pa = qa, pb = qb;
@@ -353,15 +357,18 @@ __device__ __forceinline__ void ped_group(const FpSim &S, int par, const StepCtl
                 float2 fx = p2_mul(K, fm, nx_), fy = p2_mul(K, fm, ny_);
                 const float2 wm = p2_fma(vdx2, nx_, p2_mul(K, vdy2, ny_));
                 const float2 w = p2_mul(K, make_float2(-wm.x, -wm.y), ivd2);
-                const float2 sw = p2_mul(K, p2_mul(K, make_float2(kSide, kSide), w), fm);
-                const float2 fxs = p2_fma(sw, make_float2(-ny_.x, -ny_.y), fx), fys = p2_fma(sw, nx_, fy);
-                if (w.x > 0.0f) { fx.x = fxs.x; fy.x = fys.x; }
-                if (w.y > 0.0f) { fx.y = fxs.y; fy.y = fys.y; }
-                if (ua) { ax += __float2int_rn(fx.x); ay += __float2int_rn(fy.x); }
-                if (ub) { ax += __float2int_rn(fx.y); ay += __float2int_rn(fy.y); }
+                float2 sw = p2_mul(K, p2_mul(K, make_float2(kSide, kSide), w), fm);
+                // no side step for w <= 0: a zero product leaves the term's
+                // integer value unchanged
+                if (!(w.x > 0.0f)) sw.x = 0.0f;
+                if (!(w.y > 0.0f)) sw.y = 0.0f;
+                fx = p2_add(K, p2_fma(sw, make_float2(-ny_.x, -ny_.y), fx), kRnd);
+                fy = p2_add(K, p2_fma(sw, nx_, fy), kRnd);
+                if (ua) { ax += __float_as_uint(fx.x) - 0x4B400000u; ay += __float_as_uint(fy.x) - 0x4B400000u; }
+                if (ub) { ax += __float_as_uint(fx.y) - 0x4B400000u; ay += __float_as_uint(fy.y) - 0x4B400000u; }
             }
-            Fx += ax;
-            Fy += ay;
+            Fx += (int)ax;
+            Fy += (int)ay;
         }
     }
 #pragma unroll

@@ -133,8 +133,8 @@ class ClockSampler:
 # DRAM bytes per flood-kernel launch from ncu captures (dram__bytes_read.sum +
 # dram__bytes_write.sum; profiles/flood_kernel_traffic.md), valid only for the
 # kernel sources they were taken on.
-FLOOD_TRAFFIC = {"sources_sha256": "9ed8248ed7e5c011c876272bf81844c8eda0a3630b2693100cec407c497948da",
-                 "shopping_centre_512": 5.96e6, "wet_2048": 93.01e6 + 15.84e6}
+FLOOD_TRAFFIC = {"sources_sha256": "0c756cba00dab7fe895c349962ab1abda0d36de3a248c8c649612cd5039cb382",
+                 "shopping_centre_512": 5.96e6, "wet_2048": 93.01e6 + 15.92e6}
 FLOOD_SOURCES = ("flood.cu", "flood_dev.cuh", "fp_common.cuh")
 
 

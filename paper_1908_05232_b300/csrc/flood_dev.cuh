@@ -64,38 +64,31 @@ __device__ __forceinline__ float press(float hg, float h) { return hg * h * h; }
 // HLL flux across a face; un normal and ut tangential velocity, pL/pR the face
 // pressures 1/2 g h^2 of the two sides.  out = (mass, normal momentum incl.
 // pressure, tangential momentum).  Identical states give the physical flux
-// exactly (lake at rest stays exactly at rest).
+// exactly (lake at rest stays exactly at rest).  Faces with both sides dry
+// leave at once; otherwise every case is computed and the one that applies is
+// selected, in this order of precedence: both dry (no flux), identical states
+// or sL >= 0 (left flux), sR <= 0 (right flux), the HLL average.
 __device__ __forceinline__ void hll(float g, float hL, float unL, float utL, float pL, float hR, float unR,
                                     float utR, float pR, float &fm, float &fn, float &ft) {
-    if (hL <= FP_H_EPS_F && hR <= FP_H_EPS_F) {
+    const bool dL = hL <= FP_H_EPS_F, dR = hR <= FP_H_EPS_F;
+    if (dL && dR) {
         fm = 0.0f; fn = 0.0f; ft = 0.0f;
         return;
     }
     const float qL = hL * unL, qR = hR * unR;
     const float FL0 = qL, FL1 = __fmaf_rn(qL, unL, pL), FL2 = qL * utL;
     const float FR0 = qR, FR1 = __fmaf_rn(qR, unR, pR), FR2 = qR * utR;
-    if (hL == hR && unL == unR && utL == utR) {
-        fm = FL0; fn = FL1; ft = FL2;
-        return;
-    }
+    // wave speeds: Einfeldt-type bounds, or the dry-bed ones when a side is dry
+    // (the left side's test first)
     const float cL = sqrt_fast(g * hL), cR = sqrt_fast(g * hR);
-    float sL, sR;
-    if (hL <= FP_H_EPS_F) {
-        sL = __fmaf_rn(-2.0f, cR, unR);
-        sR = unR + cR;
-    } else if (hR <= FP_H_EPS_F) {
-        sL = unL - cL;
-        sR = __fmaf_rn(2.0f, cL, unL);
-    } else {
-        const float us = __fmaf_rn(0.5f, unL + unR, cL - cR);
-        const float cs = __fmaf_rn(0.25f, unL - unR, 0.5f * (cL + cR));
-        const float a = unL - cL, b = us - cs;
-        sL = a < b ? a : b;
-        const float c = unR + cR, d = us + cs;
-        sR = c > d ? c : d;
-    }
-    if (sL >= 0.0f) { fm = FL0; fn = FL1; ft = FL2; return; }
-    if (sR <= 0.0f) { fm = FR0; fn = FR1; ft = FR2; return; }
+    const float us = __fmaf_rn(0.5f, unL + unR, cL - cR);
+    const float cs = __fmaf_rn(0.25f, unL - unR, 0.5f * (cL + cR));
+    const float a = unL - cL, b = us - cs;
+    float sL = a < b ? a : b;
+    const float c = unR + cR, d = us + cs;
+    float sR = c > d ? c : d;
+    if (dR) { sL = unL - cL; sR = __fmaf_rn(2.0f, cL, unL); }
+    if (dL) { sL = __fmaf_rn(-2.0f, cR, unR); sR = unR + cR; }
     // Differences of two products are rounded explicitly (no contraction), so the
     // flux of a mirrored face is exactly the mirrored flux (its sR - sL is the
     // same number, so any reciprocal keeps that).
@@ -105,6 +98,8 @@ __device__ __forceinline__ void hll(float g, float hL, float unL, float utL, flo
     fn = __fadd_rn(__fsub_rn(__fmul_rn(sR, FL1), __fmul_rn(sL, FR1)), __fmul_rn(sLR, qR - qL)) * inv;
     ft = __fadd_rn(__fsub_rn(__fmul_rn(sR, FL2), __fmul_rn(sL, FR2)),
                    __fmul_rn(sLR, __fsub_rn(__fmul_rn(hR, utR), __fmul_rn(hL, utL)))) * inv;
+    if (sR <= 0.0f) { fm = FR0; fn = FR1; ft = FR2; }
+    if (sL >= 0.0f || (hL == hR && unL == unR && utL == utR)) { fm = FL0; fn = FL1; ft = FL2; }
 }
 
 struct Side {
@@ -183,12 +178,15 @@ __device__ __forceinline__ float4 shfl_down_f4(float4 f) {
 
 // x face between cells i-1 (L) and i (R) of row j: (mass, normal momentum minus
 // the L pressure, minus the R pressure, tangential momentum); ghosts on the
-// domain's west / east edges; zero past the east edge.
+// domain's west / east edges; zero past the east edge.  edge (the same for the
+// whole tile) is false when the tile touches no domain edge: no checks then.
 __device__ __forceinline__ float4 x_face(const FpSim &S, float g, float hg, float h_in, Side L, Side R, int i,
-                                         int j) {
-    if (i > S.nx) return make_float4(0.f, 0.f, 0.f, 0.f);
-    if (i == 0) L = ghost(S.bc[2][j], R, true, h_in);
-    if (i == S.nx) R = ghost(S.bc[3][j], L, true, h_in);
+                                         int j, bool edge) {
+    if (edge) {
+        if (i > S.nx) return make_float4(0.f, 0.f, 0.f, 0.f);
+        if (i == 0) L = ghost(S.bc[2][j], R, true, h_in);
+        if (i == S.nx) R = ghost(S.bc[3][j], L, true, h_in);
+    }
     const float zf = fmaxf(L.z, R.z);
     const float hLs = fmaxf(0.0f, (L.h + L.z) - zf);
     const float hRs = fmaxf(0.0f, (R.h + R.z) - zf);
@@ -202,10 +200,12 @@ __device__ __forceinline__ float4 x_face(const FpSim &S, float g, float hg, floa
 // normal momentum minus the B pressure, minus the A pressure); ghosts on the
 // domain's south / north edges; zero past the east edge.
 __device__ __forceinline__ float4 y_face(const FpSim &S, float g, float hg, float h_in, Side B, Side A, int i,
-                                         int j) {
-    if (i >= S.nx) return make_float4(0.f, 0.f, 0.f, 0.f);
-    if (j == 0) B = ghost(S.bc[0][i], A, false, h_in);
-    if (j == S.ny) A = ghost(S.bc[1][i], B, false, h_in);
+                                         int j, bool edge) {
+    if (edge) {
+        if (i >= S.nx) return make_float4(0.f, 0.f, 0.f, 0.f);
+        if (j == 0) B = ghost(S.bc[0][i], A, false, h_in);
+        if (j == S.ny) A = ghost(S.bc[1][i], B, false, h_in);
+    }
     const float zf = fmaxf(B.z, A.z);
     const float hBs = fmaxf(0.0f, (B.h + B.z) - zf);
     const float hAs = fmaxf(0.0f, (A.h + A.z) - zf);
@@ -405,6 +405,9 @@ __device__ bool flood_tiles(const FpTmaSet &tm, const FpSim &S, int par, int slo
         if (tid == CTL && tn < ntiles && s_mode[(k + 1) % kModeChunk] == kTileLoad) stage(tn, b ^ 1);
         const int x0 = s_xy[b].x, y0 = s_xy[b].y, bx = x0 / FP_TX;
         const int cj = y0 + row;
+        // the tile or its halo touches a domain edge (then the faces check for
+        // ghosts and for cells past the edge)
+        const bool edge = x0 == 0 || y0 == 0 || x0 + FP_TX >= nx || y0 + TY >= ny;
         const bool okA = cj < ny && x0 + lane < nx, okB = cj < ny && x0 + lane + 32 < nx;
         const size_t gA = okA ? fp_pidx(S, x0 + lane, cj) : 0;
         if (mode != kTileLoad) {
@@ -451,8 +454,8 @@ __device__ bool flood_tiles(const FpTmaSet &tm, const FpSim &S, int par, int slo
                 wB = c31;
             }
             if (cj < ny) {
-                fwA = x_face(S, g, hg, h_in, wA, cA, iA, cj);
-                fwB = x_face(S, g, hg, h_in, wB, cB, iB, cj);
+                fwA = x_face(S, g, hg, h_in, wA, cA, iA, cj, edge);
+                fwB = x_face(S, g, hg, h_in, wB, cB, iB, cj, edge);
                 if (iA == 0) s_bx[0][row] = fwA.x;
                 if (iA == nx) s_bx[1][row] = fwA.x;
                 if (iB == nx) s_bx[1][row] = fwB.x;
@@ -460,8 +463,8 @@ __device__ bool flood_tiles(const FpTmaSet &tm, const FpSim &S, int par, int slo
             if (cj <= ny) {
                 const Side bA = staged_side(s_h, s_hu, s_hv, s_z, oA - ROWW);
                 const Side bB = staged_side(s_h, s_hu, s_hv, s_z, oB - ROWW);
-                const float4 gA = y_face(S, g, hg, h_in, bA, cA, iA, cj);
-                const float4 gB = y_face(S, g, hg, h_in, bB, cB, iB, cj);
+                const float4 gA = y_face(S, g, hg, h_in, bA, cA, iA, cj, edge);
+                const float4 gB = y_face(S, g, hg, h_in, bB, cB, iB, cj, edge);
                 s_yf[row * FP_TX + lane] = gA;
                 s_yf[row * FP_TX + lane + 32] = gB;
                 if (cj == 0) { s_by[0][lane] = gA.x; s_by[0][lane + 32] = gB.x; }
@@ -478,7 +481,7 @@ __device__ bool flood_tiles(const FpTmaSet &tm, const FpSim &S, int par, int slo
                 if (j < ny && i <= nx) {
                     const int o = (r + 1) * ROWW + FP_TX + 4;
                     f = x_face(S, g, hg, h_in, staged_side(s_h, s_hu, s_hv, s_z, o - 1),
-                               staged_side(s_h, s_hu, s_hv, s_z, o), i, j);
+                               staged_side(s_h, s_hu, s_hv, s_z, o), i, j, edge);
                     if (i == nx) s_bx[1][r] = f.x;
                 }
                 s_xe[r] = f;
@@ -488,7 +491,7 @@ __device__ bool flood_tiles(const FpTmaSet &tm, const FpSim &S, int par, int slo
                 if (j <= ny) {
                     const int o = (TY + 1) * ROWW + c + 4;
                     f = y_face(S, g, hg, h_in, staged_side(s_h, s_hu, s_hv, s_z, o - ROWW),
-                               staged_side(s_h, s_hu, s_hv, s_z, o), i, j);
+                               staged_side(s_h, s_hu, s_hv, s_z, o), i, j, edge);
                     if (j == ny && i < nx) s_by[1][c] = f.x;
                 }
                 s_yf[TY * FP_TX + c] = f;
@@ -498,7 +501,6 @@ __device__ bool flood_tiles(const FpTmaSet &tm, const FpSim &S, int par, int slo
 
         // 4. Eq. (2) + friction for this thread's two cells; east fluxes by shuffle
         // (lane 31: cell 32's west face, and the tile's east edge for B)
-        float smax = 0.0f;
         float sk_[2] = {-1.0f, -1.0f}, hk_[2] = {0.f, 0.f}, huk_[2] = {0.f, 0.f}, hvk_[2] = {0.f, 0.f};
         int wet = 0, neg = 0, bad = 0, nz = 0;
         const float dt = s_dtf, lx = s_lx, ly = s_lx;
@@ -553,16 +555,21 @@ __device__ bool flood_tiles(const FpTmaSet &tm, const FpSim &S, int par, int slo
         if (__any_sync(0xffffffffu, nz) && lane == 0) atomicOr(&s_blk[row / FP_BLK_ROWS], 1);
         // CFL: the exact (correctly rounded) wave speed only for cells whose
         // approximate speed is within 1e-5 of the warp's approximate maximum -- the
-        // approximation errs by < 1e-6, so the exact maximum is among them.
-        // (non-negative floats order as their bit patterns: one warp-reduce
-        // instruction each)
+        // approximation errs by < 1e-6, so the exact maximum is among them.  A
+        // lane evaluates its faster candidate, and its other cell only when that
+        // is a candidate too.  (Non-negative floats order as their bit patterns:
+        // one warp-reduce instruction each.)
+        float smax = 0.0f;
         {
             const float a = fmaxf(sk_[0], sk_[1]);
             const float amax = __uint_as_float(__reduce_max_sync(0xffffffffu, a >= 0.0f ? __float_as_uint(a) : 0u));
             const float thr = amax * (1.0f - 1e-5f);
-#pragma unroll
-            for (int k = 0; k < 2; ++k)
-                if (sk_[k] >= 0.0f && sk_[k] >= thr) smax = fmaxf(smax, fp_wave_speed(g, hk_[k], huk_[k], hvk_[k]));
+            const bool c0 = sk_[0] >= 0.0f && sk_[0] >= thr, c1 = sk_[1] >= 0.0f && sk_[1] >= thr;
+            const bool f1 = sk_[1] > sk_[0];  // cell B is the faster one
+            if (c0 || c1)
+                smax = fp_wave_speed(g, f1 ? hk_[1] : hk_[0], f1 ? huk_[1] : huk_[0], f1 ? hvk_[1] : hvk_[0]);
+            if (c0 && c1)
+                smax = fmaxf(smax, fp_wave_speed(g, f1 ? hk_[0] : hk_[1], f1 ? huk_[0] : huk_[1], f1 ? hvk_[0] : hvk_[1]));
         }
         // CTA reductions -> next clock slot
         smax = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(smax)));

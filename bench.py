@@ -258,17 +258,20 @@ def run_ours(args):
 
     # launch shape: the autotuner's candidates timed on this snapshot (the
     # results never depend on the shape); --tile-rows pins the flood tile height
-    tuned = {"tile_rows": args.tile_rows or 16, "ped_lanes": 8}
+    tuned = {"tile_rows": args.tile_rows or 16, "ped_lanes": 8, "hash_ahead": True}
     if not args.no_tune:
         best = None
         for tr in ((args.tile_rows,) if args.tile_rows else (8, 16, 32)):
             for pl in (4, 8, 16):
-                N.fp_set_tuning(sim.h, tr, pl)
-                t = min(one(False)[0] for _ in range(2))
-                if best is None or t < best[0]:
-                    best = (t, tr, pl)
-        tuned = {"tile_rows": best[1], "ped_lanes": best[2]}
+                for ha in (True, False):
+                    N.fp_set_tuning(sim.h, tr, pl)
+                    N.fp_set_hash_ahead(sim.h, ha)
+                    t = min(one(False)[0] for _ in range(2))
+                    if best is None or t < best[0]:
+                        best = (t, tr, pl, ha)
+        tuned = {"tile_rows": best[1], "ped_lanes": best[2], "hash_ahead": best[3]}
     N.fp_set_tuning(sim.h, tuned["tile_rows"], tuned["ped_lanes"])
+    N.fp_set_hash_ahead(sim.h, tuned["hash_ahead"])
 
     for _ in range(args.warmup):
         one(False)
@@ -379,6 +382,7 @@ def run_ours(args):
                        "l2": "flushed between timed iterations (256 MB write); the 512x512 working set "
                              "(~10 MB) is L2-resident within an iteration",
                        "tile_rows": tuned["tile_rows"], "ped_lanes": tuned["ped_lanes"],
+                       "hash_ahead": tuned["hash_ahead"],
                        "launch_shape": "default" if args.no_tune else "fastest autotuner candidate on the snapshot"},
             "breakdown": {"cell_updates_per_s": steps_total * sc.n_cells / (sum(ms_list) / 1e3),
                           "ped_updates_per_s": (upd_total - steps_total * sc.n_cells) / (sum(ms_list) / 1e3),

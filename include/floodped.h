@@ -194,6 +194,16 @@ int fp_step(fp_sim *sim, int32_t n_steps);
  * the pedestrian step (4, 8, 16).  Chosen by the package's autotuner. */
 int fp_set_tuning(fp_sim *sim, int32_t tile_rows, int32_t ped_lanes);
 
+/* Hash-ahead in FP_MODE_KERNELS (results do not depend on it): with on = 1
+ * (the default) the pedestrian kernel also hashes the records it writes into
+ * the bins of the next step, whose hashing pass then shrinks to a one-thread
+ * kernel (sandbag layers and bookkeeping); with on = 0 every step opens with a
+ * hashing pass of one thread per record.  The first saves a launch's worth of
+ * latency per step; the second is faster where the pedestrian kernel runs in
+ * many waves, each block then ending with an atomic round trip.  Chosen by the
+ * package's autotuner.  FP_EINVAL for on other than 0 or 1. */
+int fp_set_hash_ahead(fp_sim *sim, int32_t on);
+
 #define FP_MODE_KERNELS 0
 #define FP_MODE_PERSISTENT 1
 int fp_set_step_mode(fp_sim *sim, int32_t mode);

@@ -82,7 +82,7 @@ def lib():
             "fp_set_barrier_progress": [_VP, ctypes.c_int64, ctypes.c_int64],
             "fp_add_pedestrians": [_VP, _VP, ctypes.c_int32], "fp_clear_pedestrians": [_VP],
             "fp_step": [_VP, ctypes.c_int32], "fp_synchronize": [_VP], "fp_set_step_mode": [_VP, ctypes.c_int32],
-            "fp_set_tuning": [_VP, ctypes.c_int32, ctypes.c_int32],
+            "fp_set_tuning": [_VP, ctypes.c_int32, ctypes.c_int32], "fp_set_hash_ahead": [_VP, ctypes.c_int32],
             "fp_batch_create": [_VP, ctypes.c_int32, _VP], "fp_batch_step": [_VP, ctypes.c_int32],
             "fp_batch_synchronize": [_VP], "fp_batch_destroy": [_VP], "fp_set_profiling": [_VP, ctypes.c_int32],
             "fp_read_state": [_VP, ctypes.c_int32, _VP, ctypes.c_size_t], "fp_destroy": [_VP],
@@ -191,6 +191,10 @@ def fp_set_step_mode(h, mode):
 
 def fp_set_tuning(h, tile_rows, ped_lanes):
     _check(lib().fp_set_tuning(h, int(tile_rows), int(ped_lanes)), h)
+
+
+def fp_set_hash_ahead(h, on):
+    _check(lib().fp_set_hash_ahead(h, 1 if on else 0), h)
 
 
 def fp_set_profiling(h, on):

@@ -1,7 +1,9 @@
 """Autotuner for the launch shape of a simulation.
 
 Times every candidate (flood tile height 8/16/32, lanes per pedestrian
-4/8/16, per-step kernels or the persistent kernel) for a few dozen steps on a
+4/8/16, hashing of the next step's records in the pedestrian kernel or in a
+pass of its own, per-step kernels or the persistent kernel) for a few dozen
+steps on a
 scratch copy of the scenario, picks the fastest and caches the choice in a JSON
 file keyed by device, grid size and crowd size.  The launch shape never changes
 the results (the same arithmetic runs in every shape), only the time.
@@ -16,6 +18,7 @@ from . import _native as N
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "floodped_autotune.json")
 TILE_ROWS = (8, 16, 32)
 PED_LANES = (4, 8, 16)
+HASH_AHEAD = (True, False)
 
 
 def cache_key(device: str, nx: int, ny: int, n_peds: int) -> str:
@@ -33,7 +36,8 @@ def _load(path):
 
 def tune(sc, steps: int = 48, warm: int = 16, modes=(N.FP_MODE_KERNELS, N.FP_MODE_PERSISTENT)) -> dict:
     """Time every candidate on a scratch simulation of ``sc``; returns the
-    fastest {"tile_rows", "ped_lanes", "mode", "us_per_step"} and all timings."""
+    fastest {"tile_rows", "ped_lanes", "hash_ahead", "mode", "us_per_step"} and
+    all timings."""
     import torch
     stream = torch.cuda.Stream()
     sim = N.from_scenario(sc)
@@ -48,19 +52,21 @@ def tune(sc, steps: int = 48, warm: int = 16, modes=(N.FP_MODE_KERNELS, N.FP_MOD
             continue
         for rows in TILE_ROWS:
             for lanes in PED_LANES:
-                if mode == N.FP_MODE_PERSISTENT and (rows != 16 or lanes != 8):
-                    continue  # the persistent kernel has one fixed shape
-                N.fp_set_tuning(sim.h, rows, lanes)
-                sim.step(8)
-                sim.synchronize()
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                sim.step(steps)
-                e1.record(stream)
-                e1.synchronize()
-                results.append({"tile_rows": rows, "ped_lanes": lanes, "mode": mode,
-                                "us_per_step": 1e3 * e0.elapsed_time(e1) / steps})
+                for ahead in HASH_AHEAD:
+                    if mode == N.FP_MODE_PERSISTENT and (rows != 16 or lanes != 8 or not ahead):
+                        continue  # the persistent kernel has one fixed shape
+                    N.fp_set_tuning(sim.h, rows, lanes)
+                    N.fp_set_hash_ahead(sim.h, ahead)
+                    sim.step(8)
+                    sim.synchronize()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    sim.step(steps)
+                    e1.record(stream)
+                    e1.synchronize()
+                    results.append({"tile_rows": rows, "ped_lanes": lanes, "hash_ahead": ahead, "mode": mode,
+                                    "us_per_step": 1e3 * e0.elapsed_time(e1) / steps})
     sim.close()
     best = min(results, key=lambda r: r["us_per_step"])
     return {"best": best, "all": results}
@@ -84,3 +90,4 @@ def choose(sc, cache_path: str = DEFAULT_CACHE, retune: bool = False) -> dict:
 def apply(sim, best: dict) -> None:
     N.fp_set_step_mode(sim.h, best["mode"])
     N.fp_set_tuning(sim.h, best["tile_rows"], best["ped_lanes"])
+    N.fp_set_hash_ahead(sim.h, best.get("hash_ahead", True))

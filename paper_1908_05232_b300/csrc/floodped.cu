@@ -7,10 +7,13 @@
 // five kernels on two streams:
 //     hash_count --+--> flood (stream 1)                      --+--> next step
 //                  +--> scan -> gather -> ped_step (stream 2) --+
-// Both branches read the state at step n, so they overlap.  Runs of 64 steps
-// are captured once into a CUDA graph per starting clock slot and replayed.
-// The default mode instead runs up to 256 steps per launch of the persistent
-// kernel (persist.cu).
+// Both branches read the state at step n, so they overlap.  ped_step hashes the
+// records it writes for step n + 1, which then opens with step_begin (sandbag
+// layers and bookkeeping alone) in place of hash_count.  Runs of 64 steps are
+// captured once into a CUDA graph per starting clock slot and hash state, and
+// replayed.
+// The other step mode runs up to 256 steps per launch of the persistent kernel
+// (persist.cu).
 #include <cudaTypedefs.h>
 
 #include <algorithm>
@@ -95,12 +98,18 @@ struct fp_sim {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int par = 0, slot = 0;
     bool need_prepare = true, pending_time = false;
+    // the records of B are already hashed for the next step (bin counts and the
+    // evacuee counts of parity par), by the last pedestrian step
+    bool hashed = false;
+    bool hash_ahead = true;  // ped_step hashes its output records (fp_set_hash_ahead)
     long long pend_t = 0, pend_step = 0;
     int tile_rows = 16;
     int ped_lanes = 8;   // lanes per pedestrian in the per-step kernel (4, 8, 16)
     FpTmaSet tma[2];
     FpTmaSet tma16[2];  // 16-row tiles, for the persistent kernel
-    cudaGraphExec_t graphs[4] = {nullptr, nullptr, nullptr, nullptr};
+    // graphs of 64 steps by starting clock slot, whose first step hashes the
+    // records of B itself ([0]) or finds them hashed ([1])
+    cudaGraphExec_t graphs[2][4] = {};
     int n_total = 0;
     std::string err;
     std::vector<void *> allocs;
@@ -162,8 +171,9 @@ struct fp_sim {
         return static_cast<T *>(p);
     }
     void drop_graphs() {
-        for (auto &g : graphs)
-            if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+        for (auto &gs : graphs)
+            for (auto &g : gs)
+                if (g) { cudaGraphExecDestroy(g); g = nullptr; }
     }
     size_t plane_elems() const { return (size_t)S.px * (size_t)(S.ny + 2); }
     size_t flag_blocks() const {
@@ -267,8 +277,22 @@ static cudaError_t get_plane(fp_sim *s, void *dst, const float *src) {
                              cudaMemcpyDefault, s->stream);
 }
 
+// Undo a hash of B made ahead by the last pedestrian step (zero the bin counts
+// and the evacuee counts of parity par), before anything that rewrites B,
+// hashes it by itself or changes the parity.
+static cudaError_t drop_hash(fp_sim *s) {
+    if (!s->hashed) return cudaSuccess;
+    s->hashed = false;
+    cudaError_t e = cudaMemsetAsync(s->S.bin_count, 0, ((size_t)s->S.nbins + 1) * sizeof(int), s->stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(s->S.occ[s->par], 0, s->plane_elems() * sizeof(unsigned short), s->stream);
+    return e;
+}
+
 static int prepare(fp_sim *s) {
-    cudaError_t e = cudaStreamSynchronize(s->stream);
+    cudaError_t e = drop_hash(s);
+    if (e != cudaSuccess) return s->cuda_fail(e, "prepare hash");
+    e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return s->cuda_fail(e, "prepare sync");
     FpClock ring[4];
     memset(ring, 0, sizeof(ring));
@@ -294,12 +318,15 @@ static int prepare(fp_sim *s) {
     return FP_OK;
 }
 
-// One coupled step.  ev (profiling only): 4 events -- before hash_count, after
-// it, after the flood kernel (stream 1), after the pedestrian chain (stream 2).
+// One coupled step.  ev (profiling only): 4 events -- before hash_count (or
+// step_begin), after it, after the flood kernel (stream 1), after the
+// pedestrian chain (stream 2).  The pedestrian kernel hashes its output records
+// for the next step, which then opens with step_begin alone.
 static void launch_step(fp_sim *s, int par, int slot, cudaEvent_t *ev = nullptr) {
     const FpSim &S = s->S;
     if (ev) cudaEventRecord(ev[0], s->stream);
-    fp_launch_hash_count(S, par, s->stream);
+    if (s->hashed) fp_launch_step_begin(S, s->stream);
+    else fp_launch_hash_count(S, par, s->stream);
     cudaEventRecord(s->ev_fork, s->stream);
     if (ev) cudaEventRecord(ev[1], s->stream);
     cudaStreamWaitEvent(s->stream2, s->ev_fork, 0);
@@ -310,10 +337,11 @@ static void launch_step(fp_sim *s, int par, int slot, cudaEvent_t *ev = nullptr)
     if (ev) cudaEventRecord(ev[2], s->stream);
     fp_launch_scan(S, s->stream2);
     fp_launch_gather(S, s->stream2, pdl);
-    fp_launch_ped_step(S, par, slot, s->ped_lanes, s->stream2, pdl);
+    fp_launch_ped_step(S, par, slot, s->ped_lanes, s->stream2, pdl, s->hash_ahead);
     if (ev) cudaEventRecord(ev[3], s->stream2);
     cudaEventRecord(s->ev_join, s->stream2);
     cudaStreamWaitEvent(s->stream, s->ev_join, 0);
+    s->hashed = s->hash_ahead;
 }
 
 // A coupled step whose flood update moves no water (surrogate window): the
@@ -386,6 +414,8 @@ static int ensure_window(fp_sim *s) {
 
 // Persistent kernel with the global timer stamped by CTA 0 at every phase end.
 static int step_profiled_persistent(fp_sim *s, int n) {
+    const cudaError_t eh = drop_hash(s);  // the persistent kernel hashes B itself
+    if (eh != cudaSuccess) return s->cuda_fail(eh, "hash reset");
     int left = n;
     while (left > 0) {
         const int m = left < 256 ? left : 256;
@@ -738,7 +768,8 @@ int fp_add_pedestrians(fp_sim *s, const fp_ped *peds, int32_t count) {
     if (!s) return FP_EINVAL;
     if (count < 0 || (count > 0 && !peds)) return s->fail(FP_EINVAL, "bad pedestrian arguments");
     if (count == 0) return FP_OK;
-    cudaError_t e = cudaStreamSynchronize(s->stream);
+    cudaError_t e = drop_hash(s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return s->cuda_fail(e, "sync");
     FpCounters c;
     s->copy(&c, s->S.cnt, sizeof(c));
@@ -764,6 +795,7 @@ int fp_add_pedestrians(fp_sim *s, const fp_ped *peds, int32_t count) {
 
 int fp_clear_pedestrians(fp_sim *s) {
     if (!s) return FP_EINVAL;
+    drop_hash(s);
     cudaStreamSynchronize(s->stream);
     FpCounters c;
     s->copy(&c, s->S.cnt, sizeof(c));
@@ -786,6 +818,8 @@ int fp_step(fp_sim *s, int32_t n_steps) {
     }
     if (s->profiling) return step_profiled(s, n_steps);
     if (s->mode == FP_MODE_PERSISTENT) {
+        const cudaError_t eh = drop_hash(s);  // the persistent kernel hashes B itself
+        if (eh != cudaSuccess) return s->cuda_fail(eh, "hash reset");
         int left = n_steps;
         while (left > 0) {
             const int n = left < 256 ? left : 256;
@@ -801,7 +835,7 @@ int fp_step(fp_sim *s, int32_t n_steps) {
     int left = n_steps;
     while (left > 0) {
         if (left >= kGraphSteps) {
-            cudaGraphExec_t &g = s->graphs[s->slot];
+            cudaGraphExec_t &g = s->graphs[s->hashed ? 1 : 0][s->slot];
             if (!g) {
                 cudaGraph_t graph;
                 cudaError_t e = cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal);
@@ -820,6 +854,7 @@ int fp_step(fp_sim *s, int32_t n_steps) {
             }
             cudaError_t e = cudaGraphLaunch(g, s->stream);
             if (e != cudaSuccess) return s->cuda_fail(e, "graph launch");
+            s->hashed = s->hash_ahead;  // its last step hashed the records for the next
             left -= kGraphSteps;  // 64 steps: parity and slot return to their start values
         } else {
             launch_step(s, s->par, s->slot);
@@ -846,6 +881,18 @@ int fp_set_tuning(fp_sim *s, int32_t tile_rows, int32_t ped_lanes) {
     }
     s->ped_lanes = ped_lanes;
     s->drop_graphs();
+    return FP_OK;
+}
+
+int fp_set_hash_ahead(fp_sim *s, int32_t on) {
+    if (!s) return FP_EINVAL;
+    if (on != 0 && on != 1) return s->fail(FP_EINVAL, "hash-ahead is 0 or 1");
+    if ((on != 0) == s->hash_ahead) return FP_OK;
+    cudaError_t e = drop_hash(s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return s->cuda_fail(e, "hash-ahead switch");
+    s->hash_ahead = on != 0;
+    s->drop_graphs();  // the graphs' steps hash ahead or not
     return FP_OK;
 }
 
@@ -887,6 +934,10 @@ int fp_surrogate_advance(fp_sim *s, fp_surrogate *sur, int32_t n_windows, const 
     }
     int rc = ensure_window(s);
     if (rc != FP_OK) return rc;
+    {
+        const cudaError_t eh = drop_hash(s);  // the window's steps hash B themselves
+        if (eh != cudaSuccess) return s->cuda_fail(eh, "hash reset");
+    }
     fp_sim::Window &W = s->win;
     const FpSim &S = s->S;
     const int nt = W.tiles_x * W.tiles_y;
@@ -1247,7 +1298,8 @@ int fp_batch_step(fp_batch *b, int32_t n_steps) {
     const int par = b->sims[0]->par, slot = b->sims[0]->slot;
     for (int k = 0; k < b->n; ++k) {
         fp_sim *m = b->sims[k];
-        cudaError_t e = cudaStreamSynchronize(m->stream);
+        cudaError_t e = drop_hash(m);  // the batch kernels hash B themselves
+        if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
         if (e != cudaSuccess) return m->cuda_fail(e, "batch member sync");
         if (m->need_prepare) {
             int rc = prepare(m);

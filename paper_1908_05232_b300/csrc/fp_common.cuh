@@ -224,7 +224,9 @@ cudaError_t fp_flood_init_attributes();
 void fp_launch_hash_count(const FpSim &S, int par, cudaStream_t st);
 void fp_launch_scan(const FpSim &S, cudaStream_t st);
 void fp_launch_gather(const FpSim &S, cudaStream_t st, bool pdl = false);
-void fp_launch_ped_step(const FpSim &S, int par, int slot, int lanes, cudaStream_t st, bool pdl = false);
+void fp_launch_ped_step(const FpSim &S, int par, int slot, int lanes, cudaStream_t st, bool pdl = false,
+                        bool hash_next = false);
+void fp_launch_step_begin(const FpSim &S, cudaStream_t st);
 void fp_launch_assign_ids(const FpSim &S, int first_slot, int first_id, int count, cudaStream_t st);
 void fp_launch_read_peds(const FpSim &S, uint4 *out, int n_total, cudaStream_t st);
 int fp_scan_tiles(int nbins);

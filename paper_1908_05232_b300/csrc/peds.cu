@@ -1,6 +1,8 @@
 // peds.cu -- per-step kernels of the pedestrian side (Sections 2.3-2.4):
 //   hash_count  one thread per record of B: bin, slot, evacuee count (and
 //               thread 0 applies completed sandbag layers to z first);
+//   step_begin  the sandbag layers and step bookkeeping alone, for a step
+//               whose records the previous pedestrian step already hashed;
 //   scan        single-pass exclusive scan of the bin counts (decoupled
 //               look-back, tiles in ticket order, bounded waits) -> bin starts;
 //               re-zeroes the counts; the exited bin's start is the new count;
@@ -26,6 +28,16 @@ __global__ void hash_count_kernel(const __grid_constant__ FpSim S, int par) {
     if (i >= C->nB) return;
     const uint4 pa = S.pedB[2 * i], pb = S.pedB[2 * i + 1];
     hash_record(S, i, __uint_as_float(pa.x), __uint_as_float(pa.y), pb.y, S.occ[par]);
+}
+
+// The opening of a step whose records of B the previous pedestrian step hashed
+// as it wrote them: completed sandbag layers, the bag snapshot, a new scan epoch.
+__global__ void step_begin_kernel(const __grid_constant__ FpSim S) {
+    fp_pdl_trigger();  // the flood kernel may be scheduled now; it waits for this grid's end
+    FpCounters *C = S.cnt;
+    barrier_and_snapshot(S);
+    C->scan_epoch += 1u;
+    C->scan_ticket = 0u;
 }
 
 // status word: epoch (30 bits) << 34 | status (1 aggregate, 2 inclusive prefix) << 32 | value
@@ -158,8 +170,11 @@ struct DirectLookup {
     __device__ int operator()(int key) const { return start[key]; }
 };
 
+// hash_next: also hash the output records for the next step (bins and the
+// evacuee counts of the other parity), so that step needs no hash_count pass
 template <int kG>
-__global__ void __launch_bounds__(256) ped_step_kernel(const __grid_constant__ FpSim S, int par, int slot) {
+__global__ void __launch_bounds__(256) ped_step_kernel(const __grid_constant__ FpSim S, int par, int slot,
+                                                       int hash_next) {
     __shared__ StepCtl s_ctl;
     fp_pdl_wait();
     FpCounters *C = S.cnt;
@@ -173,7 +188,7 @@ __global__ void __launch_bounds__(256) ped_step_kernel(const __grid_constant__ F
     __syncthreads();
     const StepCtl ctl = s_ctl;
     const int gt = blockIdx.x * blockDim.x + threadIdx.x;
-    ped_group<kG>(S, par, ctl, gt / kG, threadIdx.x & (kG - 1), DirectLookup{S.bin_start}, false);
+    ped_group<kG>(S, par, ctl, gt / kG, threadIdx.x & (kG - 1), DirectLookup{S.bin_start}, hash_next != 0);
 }
 
 // New records sit in B at [first_slot, first_slot + count): give them ids
@@ -299,11 +314,14 @@ void fp_launch_scan(const FpSim &S, cudaStream_t st) {
 void fp_launch_gather(const FpSim &S, cudaStream_t st, bool pdl) {
     fp_launch(pdl, gather_kernel, dim3(blocks_for(S.cap, 256)), dim3(256), 0, st, S);
 }
-void fp_launch_ped_step(const FpSim &S, int par, int slot, int lanes, cudaStream_t st, bool pdl) {
-    if (lanes == 4) fp_launch(pdl, ped_step_kernel<4>, dim3(blocks_for(S.cap * 4, 256)), dim3(256), 0, st, S, par, slot);
+void fp_launch_step_begin(const FpSim &S, cudaStream_t st) { step_begin_kernel<<<1, 1, 0, st>>>(S); }
+void fp_launch_ped_step(const FpSim &S, int par, int slot, int lanes, cudaStream_t st, bool pdl, bool hash_next) {
+    const int hn = hash_next ? 1 : 0;
+    if (lanes == 4)
+        fp_launch(pdl, ped_step_kernel<4>, dim3(blocks_for(S.cap * 4, 256)), dim3(256), 0, st, S, par, slot, hn);
     else if (lanes == 16)
-        fp_launch(pdl, ped_step_kernel<16>, dim3(blocks_for(S.cap * 16, 256)), dim3(256), 0, st, S, par, slot);
-    else fp_launch(pdl, ped_step_kernel<8>, dim3(blocks_for(S.cap * 8, 256)), dim3(256), 0, st, S, par, slot);
+        fp_launch(pdl, ped_step_kernel<16>, dim3(blocks_for(S.cap * 16, 256)), dim3(256), 0, st, S, par, slot, hn);
+    else fp_launch(pdl, ped_step_kernel<8>, dim3(blocks_for(S.cap * 8, 256)), dim3(256), 0, st, S, par, slot, hn);
 }
 void fp_launch_assign_ids(const FpSim &S, int first_slot, int first_id, int count, cudaStream_t st) {
     if (count > 0) assign_ids_kernel<<<blocks_for(count, 256), 256, 0, st>>>(S, first_slot, first_id, count);

@@ -433,21 +433,28 @@ def test_batch_then_alone_continues(P):
 
 
 def test_launch_shape_does_not_change_results(P):
-    """Every flood tile height and pedestrian lane count gives the same bytes."""
+    """Every flood tile height, pedestrian lane count and hashing place gives the
+    same bytes; hash-ahead is also switched on and off in mid-run."""
     from paper_1908_05232_b300 import _native as N
     sc = _barrier_wet()
     ref = None
-    for rows, lanes in ((16, 8), (8, 4), (32, 16), (8, 16)):
+    for rows, lanes, ahead in ((16, 8, True), (8, 4, False), (32, 16, True), (8, 16, False), (16, 8, None)):
         sim = P.from_scenario(sc)
         N.fp_set_tuning(sim.h, rows, lanes)
-        sim.step(150)
+        if ahead is None:  # switched before each call of 70 steps (a graph and single steps)
+            for k in range(3):
+                N.fp_set_hash_ahead(sim.h, k % 2 == 1)
+                sim.step(min(70, 150 - 70 * k))
+        else:
+            N.fp_set_hash_ahead(sim.h, ahead)
+            sim.step(150)
         sim.synchronize()
         out = (fields(sim), sim.peds(), sim.counters()["t_ticks"])
         if ref is None:
             ref = out
         else:
             for x, y in zip(out[0], ref[0]):
-                assert np.array_equal(x, y), (rows, lanes)
+                assert np.array_equal(x, y), (rows, lanes, ahead)
             assert np.array_equal(out[1], ref[1]) and out[2] == ref[2]
 
 

@@ -133,7 +133,7 @@ class ClockSampler:
 # DRAM bytes per flood-kernel launch from ncu captures (dram__bytes_read.sum +
 # dram__bytes_write.sum; profiles/flood_kernel_traffic.md), valid only for the
 # kernel sources they were taken on.
-FLOOD_TRAFFIC = {"sources_sha256": "0c756cba00dab7fe895c349962ab1abda0d36de3a248c8c649612cd5039cb382",
+FLOOD_TRAFFIC = {"sources_sha256": "196cb7e4c990081f8e0d62c528bfd7db5d52bd4756a6e421b323615088a5f2ad",
                  "shopping_centre_512": 5.96e6, "wet_2048": 93.01e6 + 15.92e6}
 FLOOD_SOURCES = ("flood.cu", "flood_dev.cuh", "fp_common.cuh")
 

@@ -35,8 +35,9 @@ __global__ void hash_count_kernel(const __grid_constant__ FpSim S, int par) {
 __global__ void step_begin_kernel(const __grid_constant__ FpSim S) {
     fp_pdl_trigger();  // the flood kernel may be scheduled now; it waits for this grid's end
     FpCounters *C = S.cnt;
+    const unsigned epoch = C->scan_epoch;  // loaded beside the bag counters
     barrier_and_snapshot(S);
-    C->scan_epoch += 1u;
+    C->scan_epoch = epoch + 1u;
     C->scan_ticket = 0u;
 }
 

@@ -153,17 +153,21 @@ __device__ __forceinline__ void hash_record(const FpSim &S, int i, float x, floa
 // update of the step reads z); snapshot of the bag count for the step.
 __device__ __forceinline__ void barrier_and_snapshot(const FpSim &S) {
     FpCounters *C = S.cnt;
+    // both counters loaded before any store (nothing else writes them now)
+    const unsigned long long total = C->total_bags, applied = C->applied;
     if (S.nb > 0 && S.n_layers > 0) {
-        unsigned long long done = C->total_bags / (unsigned long long)S.bpc;
+        unsigned long long done = total / (unsigned long long)S.bpc;
         const unsigned long long cap = (unsigned long long)S.nb * (unsigned long long)S.n_layers;
         if (done > cap) done = cap;
-        for (unsigned long long k = C->applied; k < done; ++k) {
-            const int c = S.barrier[k % (unsigned long long)S.nb];
-            S.z[fp_pidx(S, c % S.nx, c / S.nx)] += kBagT;
+        if (done > applied) {
+            for (unsigned long long k = applied; k < done; ++k) {
+                const int c = S.barrier[k % (unsigned long long)S.nb];
+                S.z[fp_pidx(S, c % S.nx, c / S.nx)] += kBagT;
+            }
+            C->applied = done;
         }
-        C->applied = done;
     }
-    C->bags_snap = C->total_bags;
+    C->bags_snap = total;
     for (int k = 0; k < 5; ++k) C->hist[k] = 0ull;
 }
 

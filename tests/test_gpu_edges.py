@@ -90,6 +90,11 @@ def test_capacity_and_argument_errors(P):
         sim.step(-1)
     with pytest.raises(P.FloodPedError):
         sim.set_fixed_dt(2.0)
+    from paper_1908_05232_b300 import _native as N
+    with pytest.raises(P.FloodPedError):  # the C entry point itself (the binding passes 0 or 1)
+        N._check(N.lib().fp_set_hash_ahead(sim.h, 2), sim.h)
+    with pytest.raises(P.FloodPedError):
+        N.fp_set_tuning(sim.h, 12, 8)
     cfg = P.config_for(sc)
     cfg.nx = 0
     with pytest.raises(P.FloodPedError):

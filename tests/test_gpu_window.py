@@ -248,3 +248,22 @@ def test_window_mass_fix_closes_the_balance(P):
     va, vb = a.mass()[0], b.mass()[0]
     assert abs(va - v0) <= 1e-6 * v0
     assert abs(vb - v0) > 1e-5 * v0
+
+
+def test_window_after_hashed_steps_keeps_results(P):
+    """Steps whose pedestrian kernel hashed the records ahead, then a window,
+    then more steps give the bytes of the same run without hashing ahead."""
+    from paper_1908_05232_b300 import _native as N
+    sc = fixed(S.plain_coupled_128(seed=6))
+    out = []
+    for ahead in (True, False):
+        sim = P.from_scenario(sc)
+        N.fp_set_hash_ahead(sim.h, ahead)
+        sim.step(70)
+        sim.surrogate_advance(net(P), 2, check_every=0)
+        sim.step(20)
+        sim.synchronize()
+        out.append((fields(sim), sim.peds(), sim.counters()["ped_updates"]))
+    for x, y in zip(out[0][0], out[1][0]):
+        assert np.array_equal(x, y)
+    assert np.array_equal(out[0][1], out[1][1]) and out[0][2] == out[1][2]

@@ -131,22 +131,22 @@ __device__ __forceinline__ void hash_record(const FpSim &S, int i, float x, floa
         evac = FP_META_ROLE(meta) == 0;
         if (evac) o = fp_pidx(S, ci, cj);
     }
-    int first, n;
-    // evacuee counts: runs of evacuees on one cell (other lanes are runs of one)
-    lane_run(act, evac ? (unsigned long long)o : ~0ull - (unsigned long long)lane, &first, &n);
-    if (evac && lane == first) {
-        const unsigned shift = (unsigned)(o & 1) * 16u;
-        unsigned *w = reinterpret_cast<unsigned *>(occ + (o & ~(size_t)1));
-        const unsigned old = atomicAdd(w, (unsigned)n << shift);
-        if (((old >> shift) & 0xffffu) + (unsigned)n > 0xffffu) fp_set_err(S, FP_ERR_OCC_OVERFLOW);
-    }
     // bin slots: a run of one bin takes consecutive slots
+    int first, n;
     const int rank = lane_run(act, (unsigned long long)key, &first, &n);
+    const int bfirst = first;
     int base = 0;
     if (lane == first) base = atomicAdd(&S.bin_count[key], n);
-    base = __shfl_sync(act, base, first);
+    // evacuee counts: runs of evacuees on one cell (other lanes are runs of one);
+    // both atomics are in flight before either result is used
+    lane_run(act, evac ? (unsigned long long)o : ~0ull - (unsigned long long)lane, &first, &n);
+    const unsigned shift = (unsigned)(o & 1) * 16u;
+    unsigned old = 0u;
+    if (evac && lane == first) old = atomicAdd(reinterpret_cast<unsigned *>(occ + (o & ~(size_t)1)), (unsigned)n << shift);
+    base = __shfl_sync(act, base, bfirst);
     S.pkey[i] = key;
     S.pslot[i] = base + rank;
+    if (evac && lane == first && ((old >> shift) & 0xffffu) + (unsigned)n > 0xffffu) fp_set_err(S, FP_ERR_OCC_OVERFLOW);
 }
 
 // Completed sandbag cell-layers raise the bed (one thread, before the flood

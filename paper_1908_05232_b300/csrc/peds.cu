@@ -25,8 +25,9 @@ __global__ void hash_count_kernel(const __grid_constant__ FpSim S, int par) {
         C->scan_ticket = 0u;
     }
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= S.cap) return;
+    const uint4 pa = S.pedB[2 * i], pb = S.pedB[2 * i + 1];  // loaded beside the count
     if (i >= C->nB) return;
-    const uint4 pa = S.pedB[2 * i], pb = S.pedB[2 * i + 1];
     hash_record(S, i, __uint_as_float(pa.x), __uint_as_float(pa.y), pb.y, S.occ[par]);
 }
 
@@ -160,10 +161,32 @@ __device__ __forceinline__ void gather_record(const FpSim &S, int i) {
 }
 
 __global__ void gather_kernel(const __grid_constant__ FpSim S) {
+    // The record, its key and slot and the record count come from kernels
+    // that finished before the scan began: loaded before waiting for the
+    // scan (the arrays hold cap entries; the count is checked after).
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool in = i < S.cap;
+    const int nB = S.cnt->nB;
+    int key = 0, slot = 0;
+    uint4 a = make_uint4(0u, 0u, 0u, 0u), b = a;
+    if (in) {
+        key = S.pkey[i];
+        slot = S.pslot[i];
+        a = S.pedB[2 * i];
+        b = S.pedB[2 * i + 1];
+    }
     fp_pdl_wait();
     fp_pdl_trigger();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < S.cnt->nB) gather_record(S, i);
+    if (!in || i >= nB) return;
+    if (key == S.nbins) {
+        S.arch[2 * (size_t)b.x] = a;
+        S.arch[2 * (size_t)b.x + 1] = b;
+    } else {
+        const int dst = S.bin_start[key] + slot;
+        S.pedA[2 * dst] = a;
+        S.pedA[2 * dst + 1] = b;
+        S.posA[dst] = make_float2(__uint_as_float(a.x), __uint_as_float(a.y));
+    }
 }
 
 struct DirectLookup {

@@ -5,8 +5,8 @@
 // sandbag storage and the barrier) with a breadth-first search, encodes the
 // TMA descriptors of the flood kernel, and enqueues coupled steps.  A step is
 // five kernels on two streams:
-//     hash_count --+--> flood (stream 1)                      --+--> next step
-//                  +--> scan -> gather -> ped_step (stream 2) --+
+//     hash_count --+--> scan -> gather -> ped_step (stream 1) --+--> next step
+//                  +--> flood (stream 2)                      --+
 // Both branches read the state at step n, so they overlap.  ped_step hashes the
 // records it writes for step n + 1, which then opens with step_begin (sandbag
 // layers and bookkeeping alone) in place of hash_count.  Runs of 64 steps are
@@ -319,8 +319,8 @@ static int prepare(fp_sim *s) {
 }
 
 // One coupled step.  ev (profiling only): 4 events -- before hash_count (or
-// step_begin), after it, after the flood kernel (stream 1), after the
-// pedestrian chain (stream 2).  The pedestrian kernel hashes its output records
+// step_begin), after it, after the flood kernel (stream 2), after the
+// pedestrian chain (stream 1).  The pedestrian kernel hashes its output records
 // for the next step, which then opens with step_begin alone.
 static void launch_step(fp_sim *s, int par, int slot, cudaEvent_t *ev = nullptr) {
     const FpSim &S = s->S;
@@ -330,23 +330,25 @@ static void launch_step(fp_sim *s, int par, int slot, cudaEvent_t *ev = nullptr)
     cudaEventRecord(s->ev_fork, s->stream);
     if (ev) cudaEventRecord(ev[1], s->stream);
     cudaStreamWaitEvent(s->stream2, s->ev_fork, 0);
-    // programmatic dependent launches on kernel -> kernel edges of one stream
-    // (not in profiling mode, whose events sit between the kernels)
+    // the flood update on stream 2; the pedestrian chain, the longer branch, on
+    // stream 1 with programmatic dependent launches on its kernel -> kernel
+    // edges (not in profiling mode, whose events sit between the kernels)
     const bool pdl = ev == nullptr;
-    fp_launch_flood(S, &s->tma[par], par, slot, s->tile_rows, s->stream);
-    if (ev) cudaEventRecord(ev[2], s->stream);
-    fp_launch_scan(S, s->stream2);
-    fp_launch_gather(S, s->stream2, pdl);
-    fp_launch_ped_step(S, par, slot, s->ped_lanes, s->stream2, pdl, s->hash_ahead);
-    if (ev) cudaEventRecord(ev[3], s->stream2);
+    fp_launch_flood(S, &s->tma[par], par, slot, s->tile_rows, s->stream2);
+    if (ev) cudaEventRecord(ev[2], s->stream2);
+    fp_launch_scan(S, s->stream, pdl);
+    fp_launch_gather(S, s->stream, pdl);
+    fp_launch_ped_step(S, par, slot, s->ped_lanes, s->stream, pdl, s->hash_ahead);
+    if (ev) cudaEventRecord(ev[3], s->stream);
     cudaEventRecord(s->ev_join, s->stream2);
     cudaStreamWaitEvent(s->stream, s->ev_join, 0);
     s->hashed = s->hash_ahead;
 }
 
 // A coupled step whose flood update moves no water (surrogate window): the
-// pedestrian chain as in launch_step; on stream 1 only the clock advance and
-// the clearing of the evacuee counts the flood kernel would have consumed.
+// pedestrian chain as in launch_step (here on stream 2); on stream 1 only the
+// clock advance and the clearing of the evacuee counts the flood kernel would
+// have consumed.
 // Both parities of the state must hold the same water state.
 static void launch_window_step(fp_sim *s, int par, int slot) {
     const FpSim &S = s->S;

@@ -222,7 +222,7 @@ void fp_launch_mass(const FpSim &S, int par, cudaStream_t st);
 int fp_flood_smem_bytes(int tile_rows);
 cudaError_t fp_flood_init_attributes();
 void fp_launch_hash_count(const FpSim &S, int par, cudaStream_t st);
-void fp_launch_scan(const FpSim &S, cudaStream_t st);
+void fp_launch_scan(const FpSim &S, cudaStream_t st, bool pdl = false);
 void fp_launch_gather(const FpSim &S, cudaStream_t st, bool pdl = false);
 void fp_launch_ped_step(const FpSim &S, int par, int slot, int lanes, cudaStream_t st, bool pdl = false,
                         bool hash_next = false);

@@ -142,6 +142,7 @@ __device__ __forceinline__ void scan_tile(const FpSim &S) {
 }
 
 __global__ void __launch_bounds__(kScanThreads) scan_kernel(const __grid_constant__ FpSim S) {
+    fp_pdl_wait();     // the step's opening kernel (counts, scan epoch and ticket)
     fp_pdl_trigger();  // the gather may be scheduled now; it waits for this grid's end
     scan_tile(S);
 }
@@ -332,8 +333,8 @@ int fp_scan_tiles(int nbins) { return (nbins + 1 + kScanTile - 1) / kScanTile; }
 void fp_launch_hash_count(const FpSim &S, int par, cudaStream_t st) {
     hash_count_kernel<<<blocks_for(S.cap, 256), 256, 0, st>>>(S, par);
 }
-void fp_launch_scan(const FpSim &S, cudaStream_t st) {
-    scan_kernel<<<fp_scan_tiles(S.nbins), kScanThreads, 0, st>>>(S);
+void fp_launch_scan(const FpSim &S, cudaStream_t st, bool pdl) {
+    fp_launch(pdl, scan_kernel, dim3(fp_scan_tiles(S.nbins)), dim3(kScanThreads), 0, st, S);
 }
 void fp_launch_gather(const FpSim &S, cudaStream_t st, bool pdl) {
     fp_launch(pdl, gather_kernel, dim3(blocks_for(S.cap, 256)), dim3(256), 0, st, S);

@@ -201,13 +201,19 @@ template <int kG>
 __global__ void __launch_bounds__(256) ped_step_kernel(const __grid_constant__ FpSim S, int par, int slot,
                                                        int hash_next) {
     __shared__ StepCtl s_ctl;
-    fp_pdl_wait();
     FpCounters *C = S.cnt;
+    // the clock and the bag snapshot come from kernels that finished before
+    // the scan began: read (and the time step computed) before waiting for the
+    // gather; the record count is the scan's
+    StepCtl ctl0;
+    if (threadIdx.x == 0) load_step_ctl(S, slot, 0, ctl0);
+    fp_pdl_wait();
     if (threadIdx.x == 0) {
-        load_step_ctl(S, slot, C->nA, s_ctl);
+        ctl0.nA = C->nA;
+        s_ctl = ctl0;
         if (blockIdx.x == 0) {
-            C->nB = s_ctl.nA;
-            if (s_ctl.dt_ticks > 0) C->ped_updates += (unsigned long long)s_ctl.nA;
+            C->nB = ctl0.nA;
+            if (ctl0.dt_ticks > 0) C->ped_updates += (unsigned long long)ctl0.nA;
         }
     }
     __syncthreads();

@@ -197,8 +197,9 @@ int fp_set_tuning(fp_sim *sim, int32_t tile_rows, int32_t ped_lanes);
 /* Hash-ahead in FP_MODE_KERNELS (results do not depend on it): with on = 1
  * (the default) the pedestrian kernel also hashes the records it writes into
  * the bins of the next step, whose hashing pass then shrinks to a one-thread
- * kernel (sandbag layers and bookkeeping); with on = 0 every step opens with a
- * hashing pass of one thread per record.  The first saves a launch's worth of
+ * kernel (sandbag layers, bag snapshot) where a barrier can be built and to
+ * nothing elsewhere; with on = 0 every step opens with a hashing pass of one
+ * thread per record.  The first saves a launch's worth of
  * latency per step; the second is faster where the pedestrian kernel runs in
  * many waves, each block then ending with an atomic round trip.  Chosen by the
  * package's autotuner.  FP_EINVAL for on other than 0 or 1. */

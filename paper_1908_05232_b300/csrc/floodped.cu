@@ -9,7 +9,8 @@
 //                  +--> flood (stream 2)                      --+
 // Both branches read the state at step n, so they overlap.  ped_step hashes the
 // records it writes for step n + 1, which then opens with step_begin (sandbag
-// layers and bookkeeping alone) in place of hash_count.  Runs of 64 steps are
+// layers and bag snapshot) in place of hash_count where a barrier can be
+// built, and with the scan itself elsewhere.  Runs of 64 steps are
 // captured once into a CUDA graph per starting clock slot and hash state, and
 // replayed.
 // The other step mode runs up to 256 steps per launch of the persistent kernel
@@ -325,8 +326,12 @@ static int prepare(fp_sim *s) {
 static void launch_step(fp_sim *s, int par, int slot, cudaEvent_t *ev = nullptr) {
     const FpSim &S = s->S;
     if (ev) cudaEventRecord(ev[0], s->stream);
-    if (s->hashed) fp_launch_step_begin(S, s->stream);
-    else fp_launch_hash_count(S, par, s->stream);
+    // With the records hashed ahead, a step opens with step_begin only where a
+    // barrier can be built (sandbag layers, bag snapshot); the pedestrian
+    // kernel starts the next scan's epoch and the scan clears the histogram.
+    const bool opening = !s->hashed || (S.nb > 0 && S.n_layers > 0);
+    if (!s->hashed) fp_launch_hash_count(S, par, s->stream);
+    else if (opening) fp_launch_step_begin(S, s->stream);
     cudaEventRecord(s->ev_fork, s->stream);
     if (ev) cudaEventRecord(ev[1], s->stream);
     cudaStreamWaitEvent(s->stream2, s->ev_fork, 0);
@@ -336,7 +341,7 @@ static void launch_step(fp_sim *s, int par, int slot, cudaEvent_t *ev = nullptr)
     const bool pdl = ev == nullptr;
     fp_launch_flood(S, &s->tma[par], par, slot, s->tile_rows, s->stream2);
     if (ev) cudaEventRecord(ev[2], s->stream2);
-    fp_launch_scan(S, s->stream, pdl);
+    fp_launch_scan(S, s->stream, pdl && opening);
     fp_launch_gather(S, s->stream, pdl);
     fp_launch_ped_step(S, par, slot, s->ped_lanes, s->stream, pdl, s->hash_ahead);
     if (ev) cudaEventRecord(ev[3], s->stream);

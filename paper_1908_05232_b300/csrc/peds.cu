@@ -1,8 +1,9 @@
 // peds.cu -- per-step kernels of the pedestrian side (Sections 2.3-2.4):
 //   hash_count  one thread per record of B: bin, slot, evacuee count (and
 //               thread 0 applies completed sandbag layers to z first);
-//   step_begin  the sandbag layers and step bookkeeping alone, for a step
-//               whose records the previous pedestrian step already hashed;
+//   step_begin  the sandbag layers and bag snapshot alone, for a step whose
+//               records the previous pedestrian step already hashed (only
+//               where a barrier can be built);
 //   scan        single-pass exclusive scan of the bin counts (decoupled
 //               look-back, tiles in ticket order, bounded waits) -> bin starts;
 //               re-zeroes the counts; the exited bin's start is the new count;
@@ -51,6 +52,7 @@ __device__ __forceinline__ void scan_tile(const FpSim &S) {
     if (tid == 0) s_tile = (int)atomicAdd(&C->scan_ticket, 1u);
     __syncthreads();
     const int tile = s_tile;
+    if (tile == 0 && tid < 5) C->hist[tid] = 0ull;  // the step's state histogram (the pedestrian kernel fills it)
     const int n = S.nbins + 1;
     const unsigned long long epoch = (unsigned long long)(C->scan_epoch & 0x3fffffffu);
     const int base = tile * kScanTile + tid * kScanItems;
@@ -212,6 +214,9 @@ __global__ void __launch_bounds__(256) ped_step_kernel(const __grid_constant__ F
         ctl0.nA = C->nA;
         s_ctl = ctl0;
         if (blockIdx.x == 0) {
+            // this step's scan is over: a new epoch and ticket for the next one
+            C->scan_epoch += 1u;
+            C->scan_ticket = 0u;
             C->nB = ctl0.nA;
             if (ctl0.dt_ticks > 0) C->ped_updates += (unsigned long long)ctl0.nA;
         }

@@ -341,7 +341,7 @@ static void launch_step(fp_sim *s, int par, int slot, cudaEvent_t *ev = nullptr)
     const bool pdl = ev == nullptr;
     fp_launch_flood(S, &s->tma[par], par, slot, s->tile_rows, s->stream2);
     if (ev) cudaEventRecord(ev[2], s->stream2);
-    fp_launch_scan(S, s->stream, pdl && opening);
+    fp_launch_scan(S, s->stream, pdl);
     fp_launch_gather(S, s->stream, pdl);
     fp_launch_ped_step(S, par, slot, s->ped_lanes, s->stream, pdl, s->hash_ahead);
     if (ev) cudaEventRecord(ev[3], s->stream);

@@ -210,6 +210,7 @@ __global__ void __launch_bounds__(256) ped_step_kernel(const __grid_constant__ F
     StepCtl ctl0;
     if (threadIdx.x == 0) load_step_ctl(S, slot, 0, ctl0);
     fp_pdl_wait();
+    fp_pdl_trigger();  // the next step's scan may be scheduled; it waits for this grid's end
     if (threadIdx.x == 0) {
         ctl0.nA = C->nA;
         s_ctl = ctl0;

@@ -133,8 +133,8 @@ class ClockSampler:
 # DRAM bytes per flood-kernel launch from ncu captures (dram__bytes_read.sum +
 # dram__bytes_write.sum; profiles/flood_kernel_traffic.md), valid only for the
 # kernel sources they were taken on.
-FLOOD_TRAFFIC = {"sources_sha256": "196cb7e4c990081f8e0d62c528bfd7db5d52bd4756a6e421b323615088a5f2ad",
-                 "shopping_centre_512": 5.96e6, "wet_2048": 93.01e6 + 15.92e6}
+FLOOD_TRAFFIC = {"sources_sha256": "0ab49d1d5f2603b6f6026848076b0be18ccdb95c49d51fe74a01ea748680ab42",
+                 "shopping_centre_512": 4.52e6, "wet_2048": 93.01e6 + 15.92e6}
 FLOOD_SOURCES = ("flood.cu", "flood_dev.cuh", "fp_common.cuh")
 
 

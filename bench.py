@@ -517,6 +517,13 @@ def run_ensemble(args):
     t_batch = time.perf_counter() - t0
     s1, c1 = sim_seconds(), cell_steps()
     batch.close()
+    # the simulations' own step graphs (a step whose records are not yet hashed
+    # ahead, then one whose are) captured before the timed arms, as the batch's
+    # were in its warm-up
+    for sim in sims:
+        sim.step(2 * chunk)
+        sim.synchronize()
+    s1w, c1w = sim_seconds(), cell_steps()
     # one by one: each simulation's steps run to completion before the next starts
     t0 = time.perf_counter()
     for sim in sims:
@@ -533,7 +540,7 @@ def run_ensemble(args):
     t_streams = time.perf_counter() - t0
     s3 = sim_seconds()
     rate_b = (s1 - s0) / t_batch
-    rate_1 = (s2 - s1) / t_single
+    rate_1 = (s2 - s1w) / t_single
     rate_s = (s3 - s2) / t_streams
     line = {"metric": "scenario-seconds/s (batched ensemble)", "value": rate_b, "unit": "scenario-s/s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_batch / args.steps,
@@ -545,7 +552,7 @@ def run_ensemble(args):
             "independent_streams": {"value": rate_s, "unit": "scenario-s/s", "seconds": t_streams},
             "speedup_vs_one_by_one": rate_b / rate_1,
             "speedup_vs_independent_streams": rate_b / rate_s,
-            "cell_updates_per_s_batched": (c1 - c0) / t_batch, "cell_updates_per_s_one_by_one": (c2 - c1) / t_single}
+            "cell_updates_per_s_batched": (c1 - c0) / t_batch, "cell_updates_per_s_one_by_one": (c2 - c1w) / t_single}
     print(json.dumps(line), flush=True)
     return 0
 

@@ -18,7 +18,7 @@ using namespace fpdev;
 constexpr int kScanItems = 8, kScanThreads = 256, kScanTile = kScanItems * kScanThreads;
 
 __global__ void hash_count_kernel(const __grid_constant__ FpSim S, int par) {
-    fp_pdl_trigger();  // the flood kernel may be scheduled now; it waits for this grid's end
+    fp_pdl_trigger();  // the scan may be scheduled now; it waits for this grid's end
     FpCounters *C = S.cnt;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         barrier_and_snapshot(S);
@@ -35,7 +35,7 @@ __global__ void hash_count_kernel(const __grid_constant__ FpSim S, int par) {
 // The opening of a step whose records of B the previous pedestrian step hashed
 // as it wrote them: completed sandbag layers, the bag snapshot, a new scan epoch.
 __global__ void step_begin_kernel(const __grid_constant__ FpSim S) {
-    fp_pdl_trigger();  // the flood kernel may be scheduled now; it waits for this grid's end
+    fp_pdl_trigger();  // the scan may be scheduled now; it waits for this grid's end
     FpCounters *C = S.cnt;
     const unsigned epoch = C->scan_epoch;  // loaded beside the bag counters
     barrier_and_snapshot(S);

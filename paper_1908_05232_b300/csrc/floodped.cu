@@ -121,7 +121,7 @@ struct fp_sim {
     int mode = FP_MODE_KERNELS;
     int persist_ctas = 0, persist_smem = 0;
     unsigned *grid_bar = nullptr;
-    std::vector<cudaEvent_t> prof_ev;  // 4 per profiled step
+    std::vector<cudaEvent_t> prof_ev;  // 5 per profiled step
     // surrogate window buffers (allocated by the first fp_surrogate_advance)
     struct Window {
         bool ready = false;
@@ -319,9 +319,9 @@ static int prepare(fp_sim *s) {
     return FP_OK;
 }
 
-// One coupled step.  ev (profiling only): 4 events -- before hash_count (or
+// One coupled step.  ev (profiling only): 5 events -- before hash_count (or
 // step_begin), after it, after the flood kernel (stream 2), after the
-// pedestrian chain (stream 1).  The pedestrian kernel hashes its output records
+// pedestrian chain (stream 1), before the flood kernel (stream 2).  The pedestrian kernel hashes its output records
 // for the next step, which then opens with step_begin alone.
 static void launch_step(fp_sim *s, int par, int slot, cudaEvent_t *ev = nullptr) {
     const FpSim &S = s->S;
@@ -339,6 +339,7 @@ static void launch_step(fp_sim *s, int par, int slot, cudaEvent_t *ev = nullptr)
     // stream 1 with programmatic dependent launches on its kernel -> kernel
     // edges (not in profiling mode, whose events sit between the kernels)
     const bool pdl = ev == nullptr;
+    if (ev) cudaEventRecord(ev[4], s->stream2);
     fp_launch_flood(S, &s->tma[par], par, slot, s->tile_rows, s->stream2);
     if (ev) cudaEventRecord(ev[2], s->stream2);
     fp_launch_scan(S, s->stream, pdl);
@@ -482,25 +483,25 @@ static int step_profiled(fp_sim *s, int n) {
 }
 
 static int step_profiled_kernels(fp_sim *s, int n) {
-    if ((int)s->prof_ev.size() < 4 * n) {
-        for (int k = (int)s->prof_ev.size(); k < 4 * n; ++k) {
+    if ((int)s->prof_ev.size() < 5 * n) {
+        for (int k = (int)s->prof_ev.size(); k < 5 * n; ++k) {
             cudaEvent_t e;
             if (cudaEventCreate(&e) != cudaSuccess) return s->fail(FP_ECUDA, "event create");
             s->prof_ev.push_back(e);
         }
     }
     for (int k = 0; k < n; ++k) {
-        launch_step(s, s->par, s->slot, &s->prof_ev[4 * k]);
+        launch_step(s, s->par, s->slot, &s->prof_ev[5 * k]);
         s->par ^= 1;
         s->slot = (s->slot + 1) & 3;
     }
     cudaError_t e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return s->cuda_fail(e, "profiled steps");
     for (int k = 0; k < n; ++k) {
-        cudaEvent_t *ev = &s->prof_ev[4 * k];
+        cudaEvent_t *ev = &s->prof_ev[5 * k];
         float a = 0, b = 0, c = 0, d = 0;
         cudaEventElapsedTime(&a, ev[0], ev[1]);
-        cudaEventElapsedTime(&b, ev[1], ev[2]);
+        cudaEventElapsedTime(&b, ev[4], ev[2]);  // the flood kernel, on its own stream
         cudaEventElapsedTime(&c, ev[1], ev[3]);
         cudaEventElapsedTime(&d, ev[0], ev[2]);
         s->prof[0] += 1;

@@ -143,7 +143,7 @@ class ClockSampler:
 # DRAM bytes per flood-kernel launch from ncu captures (dram__bytes_read.sum +
 # dram__bytes_write.sum; profiles/flood_kernel_traffic.md), valid only for the
 # kernel sources they were taken on.
-FLOOD_TRAFFIC = {"sources_sha256": "0ab49d1d5f2603b6f6026848076b0be18ccdb95c49d51fe74a01ea748680ab42",
+FLOOD_TRAFFIC = {"sources_sha256": "028ecc7b75e77bf0790eaa4ca4ae2bb0da2c316059374eb0e4a48152c3d8ce79",
                  "shopping_centre_512": 4.52e6, "wet_2048": 93.01e6 + 15.92e6}
 FLOOD_SOURCES = ("flood.cu", "flood_dev.cuh", "fp_common.cuh")
 

@@ -103,6 +103,7 @@ struct fp_sim {
     // evacuee counts of parity par), by the last pedestrian step
     bool hashed = false;
     bool hash_ahead = true;  // ped_step hashes its output records (fp_set_hash_ahead)
+    int nb_known = -1;       // the record count of B while the host knows it (since a clear or an add), else -1
     long long pend_t = 0, pend_step = 0;
     int tile_rows = 16;
     int ped_lanes = 8;   // lanes per pedestrian in the per-step kernel (4, 8, 16)
@@ -290,11 +291,13 @@ static cudaError_t drop_hash(fp_sim *s) {
     return e;
 }
 
+// Before the next step after a change from outside: the clock ring, the water
+// flags and the clock's wave speed, all ordered on the simulation's stream (no
+// wait for the work enqueued here; the clock read, when no time was set, is a
+// stream-ordered copy).
 static int prepare(fp_sim *s) {
     cudaError_t e = drop_hash(s);
     if (e != cudaSuccess) return s->cuda_fail(e, "prepare hash");
-    e = cudaStreamSynchronize(s->stream);
-    if (e != cudaSuccess) return s->cuda_fail(e, "prepare sync");
     FpClock ring[4];
     memset(ring, 0, sizeof(ring));
     if (s->pending_time) {
@@ -313,7 +316,7 @@ static int prepare(fp_sim *s) {
     e = s->reset_water_flags();
     if (e != cudaSuccess) return s->cuda_fail(e, "water flags");
     fp_launch_init_clock(s->S, s->par, s->slot, s->stream);
-    e = cudaStreamSynchronize(s->stream);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return s->cuda_fail(e, "prepare");
     s->need_prepare = false;
     return FP_OK;
@@ -777,49 +780,53 @@ int fp_add_pedestrians(fp_sim *s, const fp_ped *peds, int32_t count) {
     if (count < 0 || (count > 0 && !peds)) return s->fail(FP_EINVAL, "bad pedestrian arguments");
     if (count == 0) return FP_OK;
     cudaError_t e = drop_hash(s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
-    if (e != cudaSuccess) return s->cuda_fail(e, "sync");
-    FpCounters c;
-    s->copy(&c, s->S.cnt, sizeof(c));
-    if (s->n_total + count > s->S.cap || c.nB + count > s->S.cap)
+    if (e != cudaSuccess) return s->cuda_fail(e, "hash reset");
+    // the record count of B: known on the host since a clear or an add, else read
+    int nb0 = s->nb_known;
+    if (nb0 < 0) {
+        FpCounters c;
+        if ((e = s->copy(&c, s->S.cnt, sizeof(c))) != cudaSuccess) return s->cuda_fail(e, "counters read");
+        nb0 = c.nB;
+    }
+    if (s->n_total + count > s->S.cap || nb0 + count > s->S.cap)
         return s->fail(FP_EOVERFLOW, "pedestrian capacity exceeded");
-    e = s->copy(s->S.pedB + 2 * (size_t)c.nB, peds, (size_t)count * sizeof(fp_ped));
+    // upload, ids and the new record count (set by the kernel), then one read
+    // back for the walkability check (which also waits for the upload)
+    e = cudaMemcpyAsync(s->S.pedB + 2 * (size_t)nb0, peds, (size_t)count * sizeof(fp_ped), cudaMemcpyDefault,
+                        s->stream);
     if (e != cudaSuccess) return s->cuda_fail(e, "pedestrian upload");
-    fp_launch_assign_ids(s->S, c.nB, s->n_total, count, s->stream);
-    e = cudaStreamSynchronize(s->stream);
-    if (e != cudaSuccess) return s->cuda_fail(e, "assign ids");
-    FpCounters c2;
-    s->copy(&c2, s->S.cnt, sizeof(c2));
-    if (c2.bad_ped) {
+    fp_launch_assign_ids(s->S, nb0, s->n_total, count, s->stream);
+    int bad = 0;
+    if ((e = s->copy(&bad, &s->S.cnt->bad_ped, sizeof(int))) != cudaSuccess) return s->cuda_fail(e, "assign ids");
+    if (bad) {
         int zero = 0;
         s->copy(&s->S.cnt->bad_ped, &zero, sizeof(int));
+        s->copy(&s->S.cnt->nB, &nb0, sizeof(int));  // the records stay out
+        s->nb_known = nb0;
         return s->fail(FP_EINVAL, "a pedestrian stands outside the domain or in a non-walkable cell");
     }
-    const int nb = c.nB + count;
-    s->copy(&s->S.cnt->nB, &nb, sizeof(int));
     s->n_total += count;
+    s->nb_known = nb0 + count;
     return FP_OK;
 }
 
 int fp_clear_pedestrians(fp_sim *s) {
     if (!s) return FP_EINVAL;
-    drop_hash(s);
-    cudaStreamSynchronize(s->stream);
-    FpCounters c;
-    s->copy(&c, s->S.cnt, sizeof(c));
-    c.nA = c.nB = 0;
-    c.total_bags = c.bags_snap = c.applied = 0;
-    c.n_exited = 0;
-    for (auto &v : c.hist) v = 0;
-    cudaError_t e = s->copy(s->S.cnt, &c, sizeof(c));
+    cudaError_t e = drop_hash(s);
+    if (e == cudaSuccess) {
+        fp_launch_clear_peds(s->S, s->stream);  // stream-ordered: no host round trip
+        e = cudaGetLastError();
+    }
     if (e != cudaSuccess) return s->cuda_fail(e, "clear");
     s->n_total = 0;
+    s->nb_known = 0;
     return FP_OK;
 }
 
 int fp_step(fp_sim *s, int32_t n_steps) {
     if (!s) return FP_EINVAL;
     if (n_steps < 0) return s->fail(FP_EINVAL, "negative step count");
+    if (n_steps > 0) s->nb_known = -1;  // exits change it
     if (s->need_prepare) {
         int rc = prepare(s);
         if (rc != FP_OK) return rc;
@@ -940,6 +947,7 @@ int fp_surrogate_advance(fp_sim *s, fp_surrogate *sur, int32_t n_windows, const 
         const int rc = prepare(s);
         if (rc != FP_OK) return rc;
     }
+    s->nb_known = -1;
     int rc = ensure_window(s);
     if (rc != FP_OK) return rc;
     {
@@ -1306,6 +1314,7 @@ int fp_batch_step(fp_batch *b, int32_t n_steps) {
     const int par = b->sims[0]->par, slot = b->sims[0]->slot;
     for (int k = 0; k < b->n; ++k) {
         fp_sim *m = b->sims[k];
+        m->nb_known = -1;
         cudaError_t e = drop_hash(m);  // the batch kernels hash B themselves
         if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
         if (e != cudaSuccess) return m->cuda_fail(e, "batch member sync");

@@ -228,6 +228,7 @@ void fp_launch_ped_step(const FpSim &S, int par, int slot, int lanes, cudaStream
                         bool hash_next = false);
 void fp_launch_step_begin(const FpSim &S, cudaStream_t st);
 void fp_launch_assign_ids(const FpSim &S, int first_slot, int first_id, int count, cudaStream_t st);
+void fp_launch_clear_peds(const FpSim &S, cudaStream_t st);
 void fp_launch_read_peds(const FpSim &S, uint4 *out, int n_total, cudaStream_t st);
 int fp_scan_tiles(int nbins);
 void fp_note_error(const char *msg);  // message for fp_last_error(NULL)

@@ -233,6 +233,7 @@ __global__ void __launch_bounds__(256) ped_step_kernel(const __grid_constant__ F
 // walkable cell, and seed the by-id archive.
 __global__ void assign_ids_kernel(const __grid_constant__ FpSim S, int first_slot, int first_id, int count) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k == 0) S.cnt->nB = first_slot + count;  // the host puts it back if a record is rejected
     if (k >= count) return;
     const int i = first_slot + k;
     const int id = first_id + k;
@@ -360,6 +361,20 @@ void fp_launch_ped_step(const FpSim &S, int par, int slot, int lanes, cudaStream
         fp_launch(pdl, ped_step_kernel<16>, dim3(blocks_for(S.cap * 16, 256)), dim3(256), 0, st, S, par, slot, hn);
     else fp_launch(pdl, ped_step_kernel<8>, dim3(blocks_for(S.cap * 8, 256)), dim3(256), 0, st, S, par, slot, hn);
 }
+// Every pedestrian removed: record counts, bag and exit totals, histogram.
+__global__ void clear_peds_kernel(const __grid_constant__ FpSim S) {
+    FpCounters *C = S.cnt;
+    C->nA = 0;
+    C->nB = 0;
+    C->total_bags = 0ull;
+    C->bags_snap = 0ull;
+    C->applied = 0ull;
+    C->n_exited = 0ull;
+    for (int k = 0; k < 5; ++k) C->hist[k] = 0ull;
+}
+
+void fp_launch_clear_peds(const FpSim &S, cudaStream_t st) { clear_peds_kernel<<<1, 1, 0, st>>>(S); }
+
 void fp_launch_assign_ids(const FpSim &S, int first_slot, int first_id, int count, cudaStream_t st) {
     if (count > 0) assign_ids_kernel<<<blocks_for(count, 256), 256, 0, st>>>(S, first_slot, first_id, count);
 }

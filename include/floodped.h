@@ -219,9 +219,11 @@ int fp_set_step_mode(fp_sim *sim, int32_t mode);
 int fp_set_fixed_dt(fp_sim *sim, double dt_seconds);
 
 /* Profiling mode (on != 0): fp_step synchronises at its end and accumulates
- * the time of the parts of each step -- per-step kernels: launched directly
- * (no CUDA graph) with CUDA events around the kernel groups; persistent
- * kernel: global-timer stamps at every phase boundary.  FP_FIELD_PROFILE
+ * the time of the parts of each step -- per-step kernels: the call's steps
+ * captured into one CUDA graph with CUDA events around the kernel groups
+ * (without programmatic dependent launches, which the events would split) and
+ * replayed once; persistent kernel: global-timer stamps at every phase
+ * boundary.  FP_FIELD_PROFILE
  * returns the totals.  Turning it on resets them. */
 int fp_set_profiling(fp_sim *sim, int32_t on);
 

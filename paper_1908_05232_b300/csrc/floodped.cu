@@ -328,7 +328,7 @@ static int prepare(fp_sim *s) {
 // for the next step, which then opens with step_begin alone.
 static void launch_step(fp_sim *s, int par, int slot, cudaEvent_t *ev = nullptr) {
     const FpSim &S = s->S;
-    if (ev) cudaEventRecord(ev[0], s->stream);
+    if (ev) cudaEventRecordWithFlags(ev[0], s->stream, cudaEventRecordExternal);
     // With the records hashed ahead, a step opens with step_begin only where a
     // barrier can be built (sandbag layers, bag snapshot); the pedestrian
     // kernel starts the next scan's epoch and the scan clears the histogram.
@@ -336,19 +336,19 @@ static void launch_step(fp_sim *s, int par, int slot, cudaEvent_t *ev = nullptr)
     if (!s->hashed) fp_launch_hash_count(S, par, s->stream);
     else if (opening) fp_launch_step_begin(S, s->stream);
     cudaEventRecord(s->ev_fork, s->stream);
-    if (ev) cudaEventRecord(ev[1], s->stream);
+    if (ev) cudaEventRecordWithFlags(ev[1], s->stream, cudaEventRecordExternal);
     cudaStreamWaitEvent(s->stream2, s->ev_fork, 0);
     // the flood update on stream 2; the pedestrian chain, the longer branch, on
     // stream 1 with programmatic dependent launches on its kernel -> kernel
     // edges (not in profiling mode, whose events sit between the kernels)
     const bool pdl = ev == nullptr;
-    if (ev) cudaEventRecord(ev[4], s->stream2);
+    if (ev) cudaEventRecordWithFlags(ev[4], s->stream2, cudaEventRecordExternal);
     fp_launch_flood(S, &s->tma[par], par, slot, s->tile_rows, s->stream2);
-    if (ev) cudaEventRecord(ev[2], s->stream2);
+    if (ev) cudaEventRecordWithFlags(ev[2], s->stream2, cudaEventRecordExternal);
     fp_launch_scan(S, s->stream, pdl);
     fp_launch_gather(S, s->stream, pdl);
     fp_launch_ped_step(S, par, slot, s->ped_lanes, s->stream, pdl, s->hash_ahead);
-    if (ev) cudaEventRecord(ev[3], s->stream);
+    if (ev) cudaEventRecordWithFlags(ev[3], s->stream, cudaEventRecordExternal);
     cudaEventRecord(s->ev_join, s->stream2);
     cudaStreamWaitEvent(s->stream, s->ev_join, 0);
     s->hashed = s->hash_ahead;
@@ -493,12 +493,24 @@ static int step_profiled_kernels(fp_sim *s, int n) {
             s->prof_ev.push_back(e);
         }
     }
+    // The steps and their events are captured into one graph and replayed, as
+    // in the timed runs: launched one by one from the host, a slow host would
+    // leave gaps between the kernels that the events would count.
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return s->cuda_fail(e, "profiled capture");
     for (int k = 0; k < n; ++k) {
         launch_step(s, s->par, s->slot, &s->prof_ev[5 * k]);
         s->par ^= 1;
         s->slot = (s->slot + 1) & 3;
     }
-    cudaError_t e = cudaStreamSynchronize(s->stream);
+    e = cudaStreamEndCapture(s->stream, &graph);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e == cudaSuccess) e = cudaGraphLaunch(exec, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (exec) cudaGraphExecDestroy(exec);
     if (e != cudaSuccess) return s->cuda_fail(e, "profiled steps");
     for (int k = 0; k < n; ++k) {
         cudaEvent_t *ev = &s->prof_ev[5 * k];

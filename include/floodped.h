@@ -184,7 +184,7 @@ int fp_clear_pedestrians(fp_sim *sim);
 int fp_step(fp_sim *sim, int32_t n_steps);
 
 /* How fp_step runs a step (both give bit-identical results):
- * FP_MODE_KERNELS (default): five kernels per step on two streams (the flood
+ * FP_MODE_KERNELS (default): four or five kernels per step on two streams (the flood
  *   update overlaps the pedestrian chain), 64-step CUDA graphs;
  * FP_MODE_PERSISTENT (devices with cooperative launch): up to 256 steps per
  *   launch of one persistent kernel whose phases are separated by grid

@@ -538,3 +538,30 @@ def test_step_mode_switches_keep_results(P):
     for x, y in zip(fields(a), fields(b)):
         assert np.array_equal(x, y)
     assert np.array_equal(a.peds(), b.peds())
+
+
+def test_restore_then_step_matches_a_fresh_run(P):
+    """The benchmark's restore -- state upload, pedestrians cleared and added
+    again, clock set -- on a simulation that ran (records hashed ahead) gives
+    the bytes of a fresh simulation stepped from the same start."""
+    from paper_1908_05232_b300 import _native as N
+    sc = S.plain_coupled_128(seed=4)
+    sim = P.from_scenario(sc)
+    sim.step(90)
+    sim.synchronize()
+    recs = P.ped_records(sc.peds)
+    for _ in range(2):
+        N.fp_set_state(sim.h, sc.h, sc.hu, sc.hv)
+        N.fp_clear_pedestrians(sim.h)
+        sim.n_total = 0
+        sim.add_pedestrians(recs)
+        N.fp_set_time(sim.h, 0, 0)
+        sim.step(70)
+        sim.synchronize()
+    fresh = run_gpu(P, sc, 70)
+    for x, y in zip(fields(sim), fields(fresh)):
+        assert np.array_equal(x, y)
+    assert np.array_equal(sim.peds(), fresh.peds())
+    c, f = sim.counters(), fresh.counters()
+    for k in ("t_ticks", "step", "n_active", "n_exited", "hist"):
+        assert c[k] == f[k], k

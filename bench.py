@@ -568,7 +568,10 @@ def run_ensemble(args):
 
 
 def run_case(args):
-    """A short untimed run of one workload (the command line profiled under ncu)."""
+    """A short run of one workload (the command line profiled under ncu): after
+    an optional pre-run to a simulated time, the case's steps in the given
+    launch shape, timed with CUDA events on the simulation's stream (a time
+    taken under a profiler is not a measurement)."""
     import torch
     import scenarios
     import paper_1908_05232_b300 as P
@@ -580,22 +583,31 @@ def run_case(args):
         sc = wet2048()
     else:
         sc = workload(2)
+    from paper_1908_05232_b300 import _native as N
     sim = P.from_scenario(sc, tile_rows=args.tile_rows)
+    stream = torch.cuda.Stream()
+    N.fp_set_stream(sim.h, stream.cuda_stream)
+    N.fp_set_tuning(sim.h, args.tile_rows or 16, args.case_lanes)
+    N.fp_set_hash_ahead(sim.h, args.case_hash_ahead != 0)
     if args.case_time > 0:
         # run up to the simulated time first, then open the profiler range
         # (ncu --profile-from-start off) around the case's steps only
-        from paper_1908_05232_b300 import _native as N
         while sim.counters()["t_ticks"] < int(args.case_time * N.TICKS):
             sim.step(256)
         sim.synchronize()
         torch.cuda.cudart().cudaProfilerStart()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
     sim.step(args.case_steps)
+    e1.record(stream)
     sim.synchronize()
     if args.case_time > 0:
         torch.cuda.cudart().cudaProfilerStop()
     c = sim.counters()
     print(json.dumps({"case": args.ncu_case, "steps": c["step"], "t_ticks": c["t_ticks"],
-                      "n_active": c["n_active"], "error_flags": c["error_flags"]}))
+                      "n_active": c["n_active"], "error_flags": c["error_flags"],
+                      "ped_lanes": args.case_lanes, "hash_ahead": args.case_hash_ahead,
+                      "us_per_step": 1e3 * e0.elapsed_time(e1) / max(args.case_steps, 1)}))
     return 0
 
 
@@ -614,6 +626,8 @@ def main():
     ap.add_argument("--ncu-case", choices=["barrier2048", "wet2048", "shopping512"], default=None,
                     help="short untimed run of one workload, for profiler captures")
     ap.add_argument("--case-steps", type=int, default=4)
+    ap.add_argument("--case-lanes", type=int, default=8, choices=[4, 8, 16], help="lanes per pedestrian in the case")
+    ap.add_argument("--case-hash-ahead", type=int, default=1, choices=[0, 1], help="hash-ahead in the case")
     ap.add_argument("--case-time", type=float, default=0.0,
                     help="simulated seconds to run before the case's steps (profiler range opened after them)")
     ap.add_argument("--workload", choices=["shopping512", "ensemble", "surrogate"], default="shopping512")

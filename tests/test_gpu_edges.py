@@ -137,3 +137,28 @@ def test_dry_tiles_skipped_after_two_steps(P, mode):
     assert prof["flood_cells"] == 2 * sc.nx * sc.ny + 8 * 64 * 16
     assert all(np.all(f == 0) for f in fields(sim))
     assert sim.counters()["error_flags"] == 0
+
+
+@pytest.mark.parametrize("mode", ["kernels", "persistent"])
+def test_profiled_steps_keep_results(P, mode):
+    """Steps in profiling mode (captured with events between the kernels, no
+    programmatic launches) give the bytes of unprofiled steps, and the profile
+    accounts for every one of them."""
+    from paper_1908_05232_b300 import _native as N
+    m = N.FP_MODE_KERNELS if mode == "kernels" else N.FP_MODE_PERSISTENT
+    sc = S.plain_coupled_128(seed=8)
+    a = P.from_scenario(sc, mode=m)
+    a.step(30)
+    N.fp_set_profiling(a.h, 1)
+    a.step(70)
+    prof = a.profile()
+    N.fp_set_profiling(a.h, 0)
+    a.step(20)
+    a.synchronize()
+    b = P.from_scenario(sc, mode=m)
+    b.step(120)
+    b.synchronize()
+    assert prof["steps"] == 70 and prof["step_ms"] > 0.0
+    for k in (0, 1, 2):
+        assert np.array_equal(a.field(k), b.field(k))
+    assert np.array_equal(a.peds(), b.peds())

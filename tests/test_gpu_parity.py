@@ -565,3 +565,19 @@ def test_restore_then_step_matches_a_fresh_run(P):
     c, f = sim.counters(), fresh.counters()
     for k in ("t_ticks", "step", "n_active", "n_exited", "hist"):
         assert c[k] == f[k], k
+
+
+def test_launch_shape_switched_mid_run(P):
+    """Tile height and lanes changed between calls, while the records are
+    hashed ahead, leave the bytes of a run in one shape."""
+    from paper_1908_05232_b300 import _native as N
+    sc = _barrier_wet()
+    a = P.from_scenario(sc)
+    for k, (rows, lanes) in enumerate(((16, 8), (8, 16), (32, 4), (16, 8))):
+        N.fp_set_tuning(a.h, rows, lanes)
+        a.step(70 if k < 3 else 10)
+    a.synchronize()
+    b = run_gpu(P, sc, 220)
+    for x, y in zip(fields(a), fields(b)):
+        assert np.array_equal(x, y)
+    assert np.array_equal(a.peds(), b.peds())

@@ -417,3 +417,152 @@ def test_sandbag_barrier(oracle_mod):
     assert 12 <= o.S.total_bags <= 12 + 1
     o.step(400)
     assert o.pexit.all()
+
+
+# --------------------------------------------------------------------------
+# Table 1 walking speeds: one evacuee standing in still water of each band
+# walks exactly the band's speed for one 1 s step (Section 2.4, Table 1)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("band", ["dry", "low", "medium", "high", "highest"])
+def test_table1_walking_speeds(oracle_mod, band):
+    rows = {r[2]: (float(r[0]), float(r[1]), float(r[3])) for r in read_golden("table1_hr_bands.txt")}
+    v0 = 1.25  # the walker's own dry speed, distinct from every Table 1 speed
+    if band == "dry":
+        depth, want_speed, want_state = 0.0005, v0, 0  # below 1 mm of water: dry
+    else:
+        lo, hi, want_speed = rows[band]
+        # still water: V = 0, HR = 0.5 h; a depth in the middle of the band
+        depth = 2.0 * 0.5 * (lo + min(hi, 5.0))
+        want_state = {"low": 1, "medium": 2, "high": 3, "highest": 4}[band]
+    sc = _corridor()
+    sc.h[:] = depth            # flat bed, all walls: a lake at rest stays exactly at rest
+    sc.dt_fixed_ticks = 1 << 20
+    p = S.empty_peds(1)
+    p["x"][:] = 2.5            # the centre of its column: the next cell north lies straight ahead
+    p["y"][:] = 5.5
+    p["v0"][:] = v0
+    sc.peds = p
+    o = oracle_mod.Oracle(sc)
+    o.step(1)
+    assert o.t == 1.0
+    assert o.phr[0] == want_state
+    assert o.px[0] == 2.5
+    assert math.isclose(o.py[0] - 5.5, want_speed, rel_tol=0, abs_tol=1e-12), (band, o.py[0] - 5.5)
+
+
+# --------------------------------------------------------------------------
+# Depth hydrograph (Section 3.1): piecewise linear between its points,
+# constant before the first and after the last (hand-computed values)
+# --------------------------------------------------------------------------
+def test_hydrograph_depth_values(oracle_mod):
+    import ctypes
+    sc = S.closed_basin(4, 4, wet=False, bumps=False)
+    sc.hydro_t = np.array([10.0, 40.0, 100.0])
+    sc.hydro_h = np.array([0.2, 0.8, 0.0])
+    o = oracle_mod.Oracle(sc)
+    L = oracle_mod.lib()
+    want = {0.0: 0.2, 5.0: 0.2, 10.0: 0.2, 25.0: 0.5, 40.0: 0.8, 55.0: 0.6, 70.0: 0.4, 85.0: 0.2,
+            100.0: 0.0, 250.0: 0.0}
+    for t, h in want.items():
+        got = L.or_hydro_depth(ctypes.byref(o.P), int(round(t * (1 << 20))))
+        assert math.isclose(got, h, rel_tol=0, abs_tol=1e-12), (t, got, h)
+
+
+# --------------------------------------------------------------------------
+# CFL step with moving water (Section 3): dt = CFL dx / (max(|u|, |v|) + sqrt(g h)),
+# quantised down to ticks; neither |u| + |v| nor the still-water speed fits
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("u,v", [(1.5, -0.7), (0.3, -1.9), (-2.2, 0.0)])
+def test_dt_uniform_flow(oracle_mod, u, v):
+    h, dx, cfl = 0.8, 0.5, 0.5
+    sc = S.closed_basin(6, 5, dx=dx, wet=False, bumps=False)
+    sc.h[:] = h
+    sc.hu[:] = np.float32(h * u)
+    sc.hv[:] = np.float32(h * v)
+    o = oracle_mod.Oracle(sc)
+    g = float(np.float32(9.81))
+    c = math.sqrt(g * h)
+    want = cfl * dx / (max(abs(u), abs(v)) + c)
+    got = o.dt_ticks_now() * TICK
+    assert abs(got - want) <= 2 * TICK, (got, want)
+    # the readings a plausible slip would give are many ticks away
+    assert abs(cfl * dx / (abs(u) + abs(v) + c) - want) > 100 * TICK or min(abs(u), abs(v)) == 0
+    assert abs(cfl * dx / c - want) > 100 * TICK
+
+
+# --------------------------------------------------------------------------
+# Side-step of the repulsion (Section 2.3, build reading of the social force):
+# two walkers meeting head-on on one line pass each other, each keeping to its
+# own right, and the whole pedestrian update commutes with a 180-degree
+# rotation of its input
+# --------------------------------------------------------------------------
+def _two_way_corridor(nx=5, ny=40):
+    sc = S.closed_basin(nx, ny, dx=1.0, wet=False, bumps=False)
+    sc.exit_mask[ny - 1, :] = 1
+    sc.ped_noise = 0.0
+    sc.evac_trigger = 0
+    # responders walk south to a depot along the bottom row; one barrier cell
+    # gives them a deployment to do (else they would evacuate at once)
+    S.with_depot_and_barrier(sc, depot_ij=[(i, 0) for i in range(nx)], barrier_ij=[(0, ny - 1)], n_layers=1)
+    sc.dt_fixed_ticks = 1 << 17   # 0.125 s: the walkers meet within the neighbour radius
+    sc.t_end = 1e6
+    return sc
+
+
+def test_head_on_pair_passes_on_the_right(oracle_mod):
+    sc = _two_way_corridor()
+    p = S.empty_peds(2)
+    p["x"][:] = [2.5, 2.5]      # one line
+    p["y"][:] = [15.5, 20.5]
+    p["v0"][:] = 1.4
+    p["role"][:] = [0, 1]       # an evacuee walking north, a responder walking south
+    sc.peds = p
+    o = oracle_mod.Oracle(sc)
+    passed = None
+    for k in range(120):
+        o.step(1)
+        if o.py[0] > o.py[1]:
+            passed = k
+            break
+    assert passed is not None, "the pair never passed"
+    # walking north, the evacuee's right is east; walking south, the responder's right is west
+    assert o.px[0] > 2.5 > o.px[1], (o.px, o.py)
+    assert o.pfsm[1] == 0  # the responder is still on its way to the depot
+
+
+def test_pedestrian_step_rotation_invariant(oracle_mod):
+    nx, ny = 6, 30
+    sc = _two_way_corridor(nx, ny)
+    rng = np.random.default_rng(17)
+    n = 14
+    p = S.empty_peds(n)
+    q = 2.0 ** -10  # dyadic positions: W - x and H - y are exact
+    p["x"] = (np.round(rng.uniform(0.3, nx - 0.3, n) / q) * q).astype(np.float32)
+    p["y"] = (np.round(rng.uniform(11.0, 17.0, n) / q) * q).astype(np.float32)
+    p["vx"] = rng.uniform(-0.5, 0.5, n).astype(np.float32)
+    p["vy"] = rng.uniform(-0.5, 0.5, n).astype(np.float32)
+    p["v0"][:] = 1.4
+    p["role"][n // 2:] = 1
+    sc.peds = p
+    r = sc.copy()
+    for f in ("z", "h", "hu", "hv", "n0", "walkable", "exit_mask"):
+        setattr(r, f, getattr(sc, f)[::-1, ::-1].copy())
+    W, H = nx * sc.dx, ny * sc.dx
+    r.depot_cells = np.array([(ny - 1 - c // nx) * nx + (nx - 1 - c % nx) for c in sc.depot_cells], np.int32)
+    r.barrier_cells = np.array([(ny - 1 - c // nx) * nx + (nx - 1 - c % nx) for c in sc.barrier_cells], np.int32)
+    r.peds = {k: v.copy() for k, v in sc.peds.items()}
+    r.peds["x"] = (np.float32(W) - sc.peds["x"]).astype(np.float32)
+    r.peds["y"] = (np.float32(H) - sc.peds["y"]).astype(np.float32)
+    r.peds["vx"] = -sc.peds["vx"]
+    r.peds["vy"] = -sc.peds["vy"]
+    a, b = oracle_mod.Oracle(sc), oracle_mod.Oracle(r)
+    assert np.array_equal(a.px, W - b.px) and np.array_equal(a.py, H - b.py)
+    moved = False
+    for _ in range(40):
+        a.step(1)
+        b.step(1)
+        assert np.allclose(a.px, W - b.px, rtol=0, atol=1e-9) and np.allclose(a.py, H - b.py, rtol=0, atol=1e-9)
+        assert np.allclose(a.pvx, -b.pvx, rtol=0, atol=1e-9) and np.allclose(a.pvy, -b.pvy, rtol=0, atol=1e-9)
+        assert np.array_equal(a.pfsm, b.pfsm) and np.array_equal(a.phr, b.phr)
+        moved |= bool(np.abs(a.pvx).max() > 0.05)
+    assert moved  # the crowd interacted sideways, not only along the corridor

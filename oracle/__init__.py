@@ -55,6 +55,14 @@ def lib():
         _lib.or_hll.restype = None
         _lib.or_hll.argtypes = [ctypes.c_double] * 7 + [ctypes.c_void_p]
         _lib.or_philox4x64.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        _lib.or_discharge.restype = ctypes.c_double
+        _lib.or_discharge.argtypes = [ctypes.c_void_p, ctypes.c_double]
+        _lib.or_discharge_volume.restype = ctypes.c_double
+        _lib.or_discharge_volume.argtypes = [ctypes.c_void_p, ctypes.c_double]
+        _lib.or_discharge_width.restype = ctypes.c_double
+        _lib.or_discharge_width.argtypes = [ctypes.c_void_p]
+        _lib.or_max_hr.restype = ctypes.c_float
+        _lib.or_max_hr.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
         _lib.or_hydro_depth.restype = ctypes.c_double
         _lib.or_hydro_depth.argtypes = [ctypes.c_void_p, ctypes.c_int64]
         _lib.or_nav_field.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
@@ -87,6 +95,7 @@ class _Params(ctypes.Structure):
         ("n_barrier", ctypes.c_int32), ("barrier_cells", _P),
         ("n_layers", ctypes.c_int32), ("coupling", ctypes.c_int32), ("evac_trigger", ctypes.c_int32),
         ("seed", ctypes.c_uint64), ("ped_noise", ctypes.c_double), ("dt_fixed_ticks", ctypes.c_int64),
+        ("n_q", ctypes.c_int32), ("q_t", _P), ("q_Q", _P), ("h_qin", ctypes.c_double),
     ]
 
 
@@ -153,6 +162,10 @@ class Oracle:
         P.seed = int(sc.seed) & ((1 << 64) - 1)
         P.ped_noise = _f32(sc.ped_noise)
         P.dt_fixed_ticks = int(getattr(sc, "dt_fixed_ticks", 0))
+        self.q_t = keep(np.asarray(getattr(sc, "q_t", np.zeros(0)), np.float64))
+        self.q_Q = keep(np.asarray(getattr(sc, "q_Q", np.zeros(0)), np.float64))
+        P.n_q, P.q_t, P.q_Q = self.q_t.size, _ptr(self.q_t), _ptr(self.q_Q)
+        P.h_qin = _f32(getattr(sc, "h_qin", 1.0))
         self.P = P
         n = nx * ny
         self.h = keep(np.asarray(sc.h, np.float64).reshape(-1).copy())
@@ -213,6 +226,19 @@ class Oracle:
 
     def mass(self) -> float:
         return float(lib().or_mass(ctypes.byref(self.P), ctypes.byref(self.S)))
+
+    def max_hr(self) -> float:
+        """Largest hazard rating over the wet cells of the current state (FP32)."""
+        return float(lib().or_max_hr(ctypes.byref(self.P), ctypes.byref(self.S)))
+
+    def discharge(self, t: float) -> float:
+        return float(lib().or_discharge(ctypes.byref(self.P), float(t)))
+
+    def discharge_volume(self, t: float) -> float:
+        return float(lib().or_discharge_volume(ctypes.byref(self.P), float(t)))
+
+    def discharge_width(self) -> float:
+        return float(lib().or_discharge_width(ctypes.byref(self.P)))
 
     def boundary_inflow(self) -> float:
         return float(self.bflux.sum())

@@ -17,7 +17,9 @@
  *     is read as a Godunov-type scheme with non-negative hydrostatic
  *     reconstruction of the face depths and the HLL Riemann solver.
  *   - Section 3 (CFL-adaptive time step when wet, 1.0 s pedestrian step when
- *     dry).
+ *     dry); Section 3.1 inflow: a depth hydrograph (ghost state) or the
+ *     paper's triangular discharge hydrograph Q(t) entering through a breach
+ *     of width B with depth h_inflow (boundary mass flux, exact volume).
  *   - Section 2.4 + Table 1: HR = (V + 0.5) h with V = max(|u|, |v|), the
  *     four flood-risk states and walking speeds; evacuee roughness coupling
  *     n_M = n_M + N_p n_M with N_p <= 20; responders' sandbag cycle (storage
@@ -50,6 +52,7 @@
 #define OR_BC_WALL 0
 #define OR_BC_TRANS 1
 #define OR_BC_INFLOW 2
+#define OR_BC_DISCHARGE 3
 /* pedestrian roles, hazard states, responder task states */
 #define OR_EVAC 0
 #define OR_RESP 1
@@ -101,6 +104,9 @@ typedef struct {
     uint64_t seed;
     double ped_noise;
     int64_t dt_fixed_ticks;   /* > 0: fixed step (a build-added mode), else the CFL step */
+    int32_t n_q;              /* discharge hydrograph points (0: none) */
+    const double *q_t, *q_Q;  /* times (s) and discharges Q (m^3/s) */
+    double h_qin;             /* depth of the inflowing water at the breach (m) */
 } or_params;
 
 typedef struct {
@@ -219,6 +225,48 @@ double or_hydro_depth(const or_params *P, int64_t t_ticks) {
     return P->hydro_h[n - 1];
 }
 
+/* ------------------------------------------------------------------------ */
+/* Discharge hydrograph (Section 3.1): Q(t) piecewise linear between its     */
+/* points, constant outside; the inflow volume V(t) = integral of Q from 0   */
+/* to t, exact for that shape (a trapezoid per piece).                       */
+/* ------------------------------------------------------------------------ */
+double or_discharge(const or_params *P, double t) {
+    int n = P->n_q;
+    if (n <= 0) return 0.0;
+    if (t <= P->q_t[0]) return P->q_Q[0];
+    if (t >= P->q_t[n - 1]) return P->q_Q[n - 1];
+    for (int k = 0; k + 1 < n; ++k) {
+        if (t < P->q_t[k + 1]) {
+            double a = (t - P->q_t[k]) / (P->q_t[k + 1] - P->q_t[k]);
+            return P->q_Q[k] + (P->q_Q[k + 1] - P->q_Q[k]) * a;
+        }
+    }
+    return P->q_Q[n - 1];
+}
+
+double or_discharge_volume(const or_params *P, double t) {
+    if (P->n_q <= 0 || t <= 0.0) return 0.0;
+    /* the breakpoints of Q in (0, t): Q is linear between consecutive ones */
+    double v = 0.0, a = 0.0;
+    for (int k = 0; k <= P->n_q; ++k) {
+        double b = k < P->n_q ? P->q_t[k] : t;
+        if (b > t) b = t;
+        if (b > a) {
+            v += 0.5 * (or_discharge(P, a) + or_discharge(P, b)) * (b - a);
+            a = b;
+        }
+    }
+    return v;
+}
+
+/* width (m) of the breach: the boundary cells coded discharge */
+double or_discharge_width(const or_params *P) {
+    int32_t cnt = 0;
+    for (int i = 0; i < P->nx; ++i) cnt += (P->bc_s[i] == OR_BC_DISCHARGE) + (P->bc_n[i] == OR_BC_DISCHARGE);
+    for (int j = 0; j < P->ny; ++j) cnt += (P->bc_w[j] == OR_BC_DISCHARGE) + (P->bc_e[j] == OR_BC_DISCHARGE);
+    return (double)cnt * P->dx;
+}
+
 static int or_has_inflow(const or_params *P) {
     for (int i = 0; i < P->nx; ++i) if (P->bc_s[i] == OR_BC_INFLOW || P->bc_n[i] == OR_BC_INFLOW) return 1;
     for (int j = 0; j < P->ny; ++j) if (P->bc_w[j] == OR_BC_INFLOW || P->bc_e[j] == OR_BC_INFLOW) return 1;
@@ -254,6 +302,16 @@ int64_t or_dt_ticks(const or_params *P, const double *h, const double *hu, const
         float hin = (float)or_hydro_depth(P, t_ticks);
         if (hin > heps) {
             float s = sqrtf(g * hin);
+            if (s > smax) smax = s;
+        }
+    }
+    /* the inflowing water at the breach: depth h_qin at velocity Q(t) / (B h_qin) */
+    const double B = or_discharge_width(P);
+    if (B > 0.0) {
+        double Q = or_discharge(P, (double)t_ticks / OR_TICKS);
+        if (Q > 0.0) {
+            float u = (float)(Q / (B * P->h_qin));
+            float s = u + sqrtf(g * (float)P->h_qin);
             if (s > smax) smax = s;
         }
     }
@@ -340,7 +398,7 @@ static or_side or_cell_side(const or_state *S, int64_t c) {
 /* ghost state outside an edge cell; normal_x selects which velocity is normal */
 static or_side or_ghost(uint8_t code, or_side in, int normal_x, double h_in) {
     or_side g = in;
-    if (code == OR_BC_WALL) {
+    if (code == OR_BC_WALL || code == OR_BC_DISCHARGE) {
         if (normal_x) g.u = -in.u; else g.v = -in.v;
     } else if (code == OR_BC_INFLOW) {
         g.h = h_in; g.u = 0.0; g.v = 0.0;
@@ -361,6 +419,18 @@ void or_flood_step(const or_params *P, or_state *S, int64_t dt_ticks, const doub
     const double dt = (double)dt_ticks / OR_TICKS;
     const double dx = P->dx, g = P->g;
     const double h_in = or_hydro_depth(P, S->t_ticks);
+    /* discharge breach (Section 3.1): over this step the mean unit discharge
+     * qb = (V(t + dt) - V(t)) / (dt B) enters through the faces coded
+     * discharge (walls otherwise), carrying momentum qb * u_in, u_in = qb / h_qin */
+    double qb = 0.0, u_in = 0.0;
+    {
+        const double B = or_discharge_width(P);
+        const double t0 = (double)S->t_ticks / OR_TICKS, t1 = (double)(S->t_ticks + dt_ticks) / OR_TICKS;
+        if (B > 0.0 && dt > 0.0) {
+            qb = (or_discharge_volume(P, t1) - or_discharge_volume(P, t0)) / (dt * B);
+            u_in = qb / P->h_qin;
+        }
+    }
     double *FE = (double *)calloc((size_t)n * 3, sizeof(double));
     double *FW = (double *)calloc((size_t)n * 3, sizeof(double));
     double *GN = (double *)calloc((size_t)n * 3, sizeof(double));
@@ -378,6 +448,8 @@ void or_flood_step(const or_params *P, or_state *S, int64_t dt_ticks, const doub
             double hLs = L.h + L.z - zf; if (hLs < 0.0) hLs = 0.0;
             double hRs = R.h + R.z - zf; if (hRs < 0.0) hRs = 0.0;
             or_hll(g, hLs, L.u, L.v, hRs, R.u, R.v, f);
+            if (i == 0 && P->bc_w[j] == OR_BC_DISCHARGE) { f[0] += qb; f[1] += qb * u_in; }
+            if (i == nx && P->bc_e[j] == OR_BC_DISCHARGE) { f[0] -= qb; f[1] += qb * u_in; }
             if (i > 0) {
                 int64_t c = (int64_t)j * nx + i - 1;
                 FE[3 * c] = f[0]; FE[3 * c + 1] = f[1] - or_press(g, hLs); FE[3 * c + 2] = f[2];
@@ -402,6 +474,8 @@ void or_flood_step(const or_params *P, or_state *S, int64_t dt_ticks, const doub
             double hLs = L.h + L.z - zf; if (hLs < 0.0) hLs = 0.0;
             double hRs = R.h + R.z - zf; if (hRs < 0.0) hRs = 0.0;
             or_hll(g, hLs, L.v, L.u, hRs, R.v, R.u, f);   /* f = (mass, hv-flux, hu-flux) */
+            if (j == 0 && P->bc_s[i] == OR_BC_DISCHARGE) { f[0] += qb; f[1] += qb * u_in; }
+            if (j == ny && P->bc_n[i] == OR_BC_DISCHARGE) { f[0] -= qb; f[1] += qb * u_in; }
             if (j > 0) {
                 int64_t c = (int64_t)(j - 1) * nx + i;
                 GN[3 * c] = f[0]; GN[3 * c + 1] = f[2]; GN[3 * c + 2] = f[1] - or_press(g, hLs);
@@ -685,6 +759,22 @@ int64_t or_run(const or_params *P, or_state *S, int64_t n_steps) {
         if (or_step(P, S) == 0) break;
     }
     return k;
+}
+
+/* Largest hazard rating HR = (max(|u|,|v|) + 0.5) h over the cells holding
+ * water (h > h_eps), in FP32 from the FP32-rounded state (Section 2.4; the
+ * time history of this maximum is Fig. 5(b)'s severity measure). */
+float or_max_hr(const or_params *P, const or_state *S) {
+    float m = 0.0f;
+    int64_t n = (int64_t)P->nx * P->ny;
+    for (int64_t c = 0; c < n; ++c) {
+        float h = (float)S->h[c];
+        if (!(h > (float)OR_H_EPS)) continue;
+        float u = (float)S->hu[c] / h, v = (float)S->hv[c] / h;
+        float hr = (fmaxf(fabsf(u), fabsf(v)) + 0.5f) * h;
+        if (hr > m) m = hr;
+    }
+    return m;
 }
 
 double or_mass(const or_params *P, const or_state *S) {

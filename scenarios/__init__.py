@@ -23,7 +23,8 @@ Workloads (all seeded, all synthetic):
 Encodings shared with both implementations (an interface, not arithmetic):
 
 * boundary codes per edge cell: 0 wall, 1 transmissive, 2 inflow (depth
-  hydrograph);
+  hydrograph), 3 discharge inflow (a wall through which the discharge
+  hydrograph enters);
 * pedestrian role: 0 evacuee, 1 responder; responder task state: 0 to depot,
   1 picking up, 2 to barrier, 3 dropping, 4 done; timers in ticks of 2**-20 s.
 """
@@ -34,7 +35,7 @@ from typing import Optional
 
 import numpy as np
 
-BC_WALL, BC_TRANSMISSIVE, BC_INFLOW = 0, 1, 2
+BC_WALL, BC_TRANSMISSIVE, BC_INFLOW, BC_DISCHARGE = 0, 1, 2, 3
 ROLE_EVACUEE, ROLE_RESPONDER = 0, 1
 TICKS_PER_SECOND = 1 << 20
 
@@ -74,6 +75,11 @@ class Scenario:
     step0: int = 0           # step index at the start (random-generator counter)
     bags0: int = 0           # sandbags already dropped
     applied0: int = 0        # barrier cell-layers already built into z
+    # discharge hydrograph through the boundary cells coded BC_DISCHARGE:
+    # times (s), discharges Q (m^3/s), depth of the inflowing water (m)
+    q_t: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros(0))
+    q_Q: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros(0))
+    h_qin: float = 1.0
 
     @property
     def n_cells(self) -> int:
@@ -207,19 +213,26 @@ def _shop_layout(rng, n, dx):
 def shopping_centre(n: int = 512, dx: float = 0.5, n_evac: int = 10_000, n_resp: int = 0,
                     seed: int = 2, t_end: float = 1800.0, peak_depth: float = 1.0,
                     hydro=None, n_barrier: int = 0, n_layers: int = 0,
-                    coupling: int = 1, evac_trigger: int = 1) -> Scenario:
+                    coupling: int = 1, evac_trigger: int = 1, discharge=None) -> Scenario:
     """Procedural shopping centre (stand-in for Fig. 4): see the module docstring."""
     rng = np.random.default_rng(seed)
     s = _base("shopping_centre_%d" % n, n, n, dx, t_end, seed)
     z, shop, (b0, bw), (e0, ew), (c0, c1), n_shops = _shop_layout(rng, n, dx)
     s.n_shops = n_shops
+    s.breach = (b0, bw)
     ring = z >= 1.5
     noise = rng.uniform(-0.02, 0.02, size=(n, n)).astype(np.float32)
     s.z = (z + noise).astype(np.float32)
     s.walkable = (~ring).astype(np.uint8)
     s.exit_mask[n - 1, e0:e0 + ew] = 1
-    s.bc_s[b0:b0 + bw] = BC_INFLOW
     s.bc_n[:] = BC_TRANSMISSIVE
+    if discharge is None:
+        s.bc_s[b0:b0 + bw] = BC_INFLOW
+    else:
+        # the paper's form (Section 3.1): a discharge hydrograph (q_peak, t_inflow)
+        # through the breach, inflow depth 1 m; no depth hydrograph
+        hydro = ([0.0], [0.0])
+        with_discharge_breach(s, "south", b0, bw, discharge[0], discharge[1])
     if hydro is None:
         s.hydro_t = np.array([0.0, 300.0, 900.0])
         s.hydro_h = np.array([0.0, peak_depth, 0.0])
@@ -248,6 +261,37 @@ def shopping_centre(n: int = 512, dx: float = 0.5, n_evac: int = 10_000, n_resp:
     return s
 
 
+def triangular_discharge(q_peak: float, t_inflow: float, t_start: float = 0.0):
+    """A triangular discharge hydrograph (Section 3.1): 0 at t_start, q_peak
+    (m^3/s) at t_start + t_inflow / 2, 0 from t_start + t_inflow on; returns the
+    (times, discharges) points."""
+    return (np.array([t_start, t_start + 0.5 * t_inflow, t_start + t_inflow], np.float64),
+            np.array([0.0, q_peak, 0.0], np.float64))
+
+
+def with_discharge_breach(s: Scenario, edge: str, first: int, width: int, q_peak: float, t_inflow: float,
+                          h_inflow: float = 1.0, t_start: float = 0.0) -> Scenario:
+    """Code ``width`` boundary cells of an edge ('south', 'north', 'west',
+    'east') from index ``first`` as the discharge breach and give the scenario a
+    triangular discharge hydrograph."""
+    codes = {"south": s.bc_s, "north": s.bc_n, "west": s.bc_w, "east": s.bc_e}[edge]
+    codes[first:first + width] = BC_DISCHARGE
+    s.q_t, s.q_Q = triangular_discharge(q_peak, t_inflow, t_start)
+    s.h_qin = float(h_inflow)
+    return s
+
+
+def breach_basin(n: int = 64, dx: float = 5.0, breach_cells: int = 20, q_peak: float = 160.0,
+                 t_inflow: float = 450.0, t_end: float = 1e9, seed: int = 0) -> Scenario:
+    """A flat, dry, walled square whose south edge has a discharge breach of
+    ``breach_cells`` cells in its middle (100 m at the defaults), fed by a
+    triangular hydrograph; the water has nowhere to leave."""
+    s = _base("breach_basin", n, n, dx, t_end, seed)
+    s.n0[:] = 0.01
+    s.coupling = 0
+    return with_discharge_breach(s, "south", n // 2 - breach_cells // 2, breach_cells, q_peak, t_inflow)
+
+
 def config_plain(seed=1):
     """Plain coupled step, 128x128, 256 evacuees, 600 s."""
     return plain_coupled_128(seed)
@@ -264,6 +308,54 @@ def config_barrier(seed=3):
     return shopping_centre(2048, 0.5, 99_500, 500, seed, 3600.0,
                            hydro=([0.0, 900.0, 1500.0, 2700.0], [0.0, 0.0, 1.0, 0.0]),
                            n_barrier=200, n_layers=2)
+
+
+def config_barrier_midflood(seed=3, t0=1500.0, reach_m=300.0, depth_m=1.0, speed_m_s=0.6, bags=600):
+    """The pre-flood barrier deployment workload (``config_barrier``) taken up
+    mid-flood, as a synthetic state: at t0 (the inflow hydrograph's peak) the
+    water surface falls linearly from ``depth_m`` above the breach centre to
+    nothing ``reach_m`` away (so raised shop blocks stay dry), flowing radially
+    away from the breach at up to ``speed_m_s``; the crowd stands where it was
+    seeded; the responders are mid-deployment, each in a seeded task with a
+    seeded wait, ``bags`` sandbags already dropped and the completed cell-layers
+    already built into the bed.  Only input arrays are built here -- the flood
+    and the crowd evolve from this state under the method itself."""
+    s = config_barrier(seed)
+    rng = np.random.default_rng(seed + 104729)
+    n = s.nx
+    b0, bw = s.breach
+    xc = (b0 + 0.5 * bw) * s.dx
+    yy, xx = np.mgrid[0:n, 0:n]
+    x = (xx + 0.5) * s.dx
+    y = (yy + 0.5) * s.dx
+    d = np.hypot(x - xc, y)
+    eta = depth_m * np.clip(1.0 - d / reach_m, 0.0, None)
+    h = np.maximum(eta - s.z.astype(np.float64), 0.0)
+    h[s.z >= 1.0] = 0.0          # walls and shop blocks
+    sp = speed_m_s * np.clip(1.0 - d / reach_m, 0.0, None)
+    ux = np.where(d > 0, (x - xc) / np.maximum(d, 1e-9), 0.0) * sp
+    uy = np.where(d > 0, y / np.maximum(d, 1e-9), 0.0) * sp
+    s.h = h.astype(np.float32)
+    s.hu = (s.h * ux).astype(np.float32)
+    s.hv = (s.h * uy).astype(np.float32)
+    s.h[s.h < 1e-4] = 0.0
+    s.hu[s.h == 0] = 0.0
+    s.hv[s.h == 0] = 0.0
+    # responders mid-deployment
+    resp = np.nonzero(s.peds["role"] == ROLE_RESPONDER)[0]
+    s.peds["fsm"][resp] = rng.integers(0, 4, resp.size).astype(np.uint8)
+    waiting = (s.peds["fsm"][resp] == 1) | (s.peds["fsm"][resp] == 3)
+    s.peds["timer"][resp] = np.where(waiting, rng.integers(1, 30 * TICKS_PER_SECOND, resp.size), 0).astype(np.int32)
+    bpc = int(np.ceil(float(np.float32(s.dx)) ** 2 / (0.40 * 0.30)))
+    s.bags0 = int(bags)
+    s.applied0 = min(int(bags) // bpc, s.barrier_cells.size * s.n_layers)
+    for k in range(s.applied0):
+        c = s.barrier_cells[k % s.barrier_cells.size]
+        s.z.flat[c] += np.float32(0.25)
+    s.t0_ticks = int(round(t0 * TICKS_PER_SECOND))
+    s.step0 = 12_000
+    s.name = "barrier_2048_midflood"
+    return s
 
 
 # ---------------------------------------------------------------------------

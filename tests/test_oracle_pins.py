@@ -566,3 +566,97 @@ def test_pedestrian_step_rotation_invariant(oracle_mod):
         assert np.array_equal(a.pfsm, b.pfsm) and np.array_equal(a.phr, b.phr)
         moved |= bool(np.abs(a.pvx).max() > 0.05)
     assert moved  # the crowd interacted sideways, not only along the corridor
+
+
+# --------------------------------------------------------------------------
+# Discharge hydrograph through the breach (Section 3.1): the four paper pairs
+# release the same volume 1/2 Q_peak t_inflow = 36,000 m^3, the inflow volume
+# function is the triangle's closed form, and a walled basin fed through the
+# breach holds exactly that volume once the hydrograph has passed
+# --------------------------------------------------------------------------
+def _paper_pairs():
+    return [tuple(float(v) for v in r) for r in read_golden("paper_hydrographs.txt")]
+
+
+@pytest.mark.parametrize("pair", range(4))
+def test_discharge_hydrograph_closed_form(oracle_mod, pair):
+    q_peak, T, v_in, h_in, B, vol = _paper_pairs()[pair]
+    assert math.isclose(q_peak, v_in * h_in * B, rel_tol=1e-12)
+    assert math.isclose(0.5 * q_peak * T, vol, rel_tol=1e-12)
+    sc = S.breach_basin(n=40, dx=B / 20, breach_cells=20, q_peak=q_peak, t_inflow=T)
+    o = oracle_mod.Oracle(sc)
+    assert math.isclose(o.discharge_width(), B, rel_tol=1e-12)
+    assert math.isclose(o.discharge(0.5 * T), q_peak, rel_tol=1e-12)
+    assert o.discharge(0.0) == 0.0 and o.discharge(T) == 0.0 and o.discharge(3 * T) == 0.0
+    for f in (0.1, 0.25, 0.5, 0.7, 0.9, 1.0, 2.0):
+        t = f * T
+        want = q_peak * t * t / T if f <= 0.5 else vol - q_peak * (T - min(t, T)) ** 2 / T
+        assert math.isclose(o.discharge_volume(t), want, rel_tol=1e-12), (f, o.discharge_volume(t), want)
+
+
+@pytest.mark.parametrize("pair", [0, 3])
+def test_discharge_breach_mass_closed_form(oracle_mod, pair):
+    q_peak, T, _, _, B, vol = _paper_pairs()[pair]
+    sc = S.breach_basin(n=64, dx=5.0, breach_cells=int(B / 5.0), q_peak=q_peak, t_inflow=T)
+    o = oracle_mod.Oracle(sc)
+    while o.t < T + 20.0:
+        o.step(50)
+    assert o.counters()["neg_depth"] == 0
+    assert math.isclose(o.mass(), vol, rel_tol=1e-10), o.mass()
+    assert math.isclose(o.boundary_inflow(), vol, rel_tol=1e-10)
+
+
+def test_discharge_breach_without_flow_is_a_wall(oracle_mod):
+    """Q = 0: the breach faces are exactly walls."""
+    a = S.random_wet_state(30, 22, dx=1.0, seed=4, bc=(0, 1, 0, 0))
+    b = a.copy()
+    S.with_discharge_breach(b, "south", 5, 12, 0.0, 100.0)
+    b.q_Q[:] = 0.0
+    oa, ob = oracle_mod.Oracle(a), oracle_mod.Oracle(b)
+    oa.step(60)
+    ob.step(60)
+    assert oa.t_ticks == ob.t_ticks
+    for f in ("h", "hu", "hv"):
+        assert np.array_equal(getattr(oa, f), getattr(ob, f)), f
+
+
+def test_discharge_one_step_into_a_still_lake(oracle_mod):
+    """A constant Q into a frictionless still lake of depth h0: after one step
+    the breach cells hold h0 + dt/dx q and momentum dt/dx q^2 / h_in (the wall
+    part of the face balances the lake's pressure exactly); nothing else moves."""
+    n, dx, h0, Q, B, h_in = 20, 5.0, 0.8, 50.0, 50.0, 1.0
+    sc = S.closed_basin(n, n, dx=dx, wet=False, bumps=False)
+    sc.h[:] = h0
+    sc.n0[:] = 0.0
+    S.with_discharge_breach(sc, "south", 5, int(B / dx), Q, 1.0, h_inflow=h_in)
+    sc.q_t, sc.q_Q = np.array([0.0, 1e6]), np.array([Q, Q])
+    o = oracle_mod.Oracle(sc)
+    o.step(1)
+    dt = o.t
+    q = Q / B
+    h, hu, hv = o.field("h"), o.field("hu"), o.field("hv")
+    hf = float(np.float32(h0))
+    assert np.allclose(h[0, 5:15], hf + dt / dx * q, rtol=0, atol=1e-13)
+    assert np.allclose(hv[0, 5:15], dt / dx * q * q / h_in, rtol=0, atol=1e-13)
+    assert np.all(hu == 0.0)
+    rest = np.ones_like(h, bool)
+    rest[0, 5:15] = False
+    assert np.all(h[rest] == hf) and np.all(hv[rest] == 0.0)
+    # the CFL step includes the inflowing water's speed q / h_in + sqrt(g h_in)
+    g = float(np.float32(9.81))
+    assert abs(dt - 0.5 * dx / (q / h_in + math.sqrt(g * h_in))) <= 2 * TICK
+
+
+def test_max_hazard_rating(oracle_mod):
+    """The largest HR = (max(|u|,|v|) + 0.5) h over the wet cells (Section 2.4)."""
+    sc = S.closed_basin(9, 7, wet=False, bumps=False)
+    sc.h[:] = 0.2
+    sc.h[3, 4], sc.hu[3, 4] = 1.0, 0.8          # HR 1.3
+    sc.h[5, 1], sc.hv[5, 1] = 0.5, -0.6         # |v| = 1.2: HR 0.85
+    sc.h[1, 7], sc.hu[1, 7] = 0.0, 5.0          # dry: no HR
+    o = oracle_mod.Oracle(sc)
+    assert math.isclose(o.max_hr(), 1.3, rel_tol=1e-6)
+    sc.h[3, 4] = 0.2
+    sc.hu[3, 4] = 0.0
+    o = oracle_mod.Oracle(sc)
+    assert math.isclose(o.max_hr(), 0.85, rel_tol=1e-6)

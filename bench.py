@@ -1,25 +1,37 @@
 #!/usr/bin/env python3
 """Benchmark of the coupled flood-pedestrian step on B300.
 
-Workload (default): the synthetic shopping centre, 512 x 512 cells of 0.5 m,
-10,000 evacuees, evacuee roughness coupling on, triangular depth hydrograph
-peaking at 1.0 m.  The simulation is first advanced 1024 steps (flood inside,
-evacuation under way) and that state is kept as a snapshot.  One benchmark
-step = restore the snapshot (untimed), flush L2, then 256 coupled simulation
-steps through the C ABI (``fp_step``), timed with CUDA events on the
-simulation's stream.
+Workload (default): the pre-flood barrier deployment at scale taken up
+mid-flood -- 2048 x 2048 cells of 0.5 m, 100,000 pedestrians of which 500
+responders building a 200-cell, 2-layer sandbag barrier, evacuee roughness
+coupling on, the triangular depth hydrograph at its 1.0 m peak (t = 1500 s),
+the synthetic mid-flood state of ``scenarios.config_barrier_midflood`` (about
+15 % of the cells wet, the responders mid-deployment).  One benchmark step =
+restore that snapshot (untimed), flush L2, then 512 coupled simulation steps
+through the C ABI (``fp_step``), timed with CUDA events on the simulation's
+stream.
 
 metric  coupled cell-updates/s + ped-updates/s (cells x steps + pedestrians
-        advanced, over the timed region).
-e2e     the same through the C ABI with host buffers: pinned-host state and
-        pedestrian upload, 256 steps, read-back of h, hu, hv, pedestrians and
-        counters, all inside the timed region.
+        advanced, over the timed region); ``breakdown`` gives the cell updates
+        the flood kernel computed (it skips tiles that stay dry) beside all.
+e2e     the same through the C ABI with host buffers: pinned-host state, bed
+        and pedestrian upload, 512 steps, read-back of h, hu, hv, pedestrians
+        and counters, all inside the timed region.
 roofline the flood kernel (HBM-bound stencil), 34 algorithmic bytes per cell
-        update of the tiles it computed (it skips tiles that stay dry), its
-        launch duration from CUDA events in a profiled pass.
-cpu_baseline the FP64 C oracle on a bounded sample of the same workload.
+        update of the tiles it computed, its launch duration from CUDA events
+        on its own stream in a profiled pass of the same steps;
+        ``roofline_peds`` the pedestrian kernel, 96 algorithmic bytes per
+        pedestrian update; ``roofline_wet2048`` the flood kernel alone on a
+        2048 x 2048 grid holding water almost everywhere.
+cpu_baseline the FP64 C oracle on one coupled step of the same snapshot.
+batched  a seeded ensemble of shopping centres stepped together by the batched
+        kernels against the same simulations stepped one by one
+        (scenario-seconds/s).
+surrogate the learned surrogate's windows against the plain update from the
+        same snapshot at a fixed step (scenario-seconds/s), with the largest
+        depth difference from the plain run at the end.
 
-``--impl reference`` times the oracle itself (host cores) on the same workload.
+``--impl reference`` times the oracle itself (host cores) on the same snapshot.
 Multi-GPU (torchrun): every rank runs an independent replica (weak scaling).
 """
 import argparse
@@ -27,6 +39,7 @@ import ctypes
 import hashlib
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -37,16 +50,22 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-CHUNK = 256            # simulation steps per benchmark step
-PRE_STEPS = 1024       # steps before the snapshot
+CHUNK = 512            # simulation steps per benchmark step
 FLOOD_BYTES_PER_CELL = 34  # read h,hu,hv,z,n0 (20 B) + occupancy (2 B); write h,hu,hv (12 B)
+# pedestrian update: read its record (32 B) and position copy (8 B), its cell's
+# h, hu, hv (12 B), navigation code, arrival and cell flags (3 B); write its
+# record (32 B), hash key and slot (8 B), its evacuee count (1 B amortised)
+PED_BYTES = 96
 METRIC = "coupled cell-updates/s + ped-updates/s"
 UNIT = "updates/s"
+WORKLOAD = "barrier_2048_midflood"
+WORKLOAD_TEXT = ("2048x2048 cells of 0.5 m, 100,000 pedestrians (500 responders, 200-cell 2-layer sandbag "
+                 "barrier), synthetic mid-flood state at t = 1500 s")
 
 
 def workload(seed):
     import scenarios
-    return scenarios.shopping_centre(512, 0.5, 10_000, 0, seed, 1800.0)
+    return scenarios.config_barrier_midflood(seed)
 
 
 def launches_per_chunk(sc, hash_ahead):
@@ -99,6 +118,19 @@ def peaks():
     return 6400.0, "fallback"
 
 
+def host_cpu():
+    model = platform.processor() or "unknown"
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "model": model}
+
+
 class ClockSampler:
     FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.hw_slowdown",
               "clocks_event_reasons.hw_thermal_slowdown", "clocks_event_reasons.sw_thermal_slowdown",
@@ -140,11 +172,9 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# DRAM bytes per flood-kernel launch from ncu captures (dram__bytes_read.sum +
-# dram__bytes_write.sum; profiles/flood_kernel_traffic.md), valid only for the
-# kernel sources they were taken on.
-FLOOD_TRAFFIC = {"sources_sha256": "028ecc7b75e77bf0790eaa4ca4ae2bb0da2c316059374eb0e4a48152c3d8ce79",
-                 "shopping_centre_512": 4.52e6, "wet_2048": 93.01e6 + 15.92e6}
+# DRAM bytes per launch from ncu captures (dram__bytes_read.sum +
+# dram__bytes_write.sum), valid only for the kernel sources they were taken on.
+FLOOD_TRAFFIC = {"sources_sha256": None}
 FLOOD_SOURCES = ("flood.cu", "flood_dev.cuh", "fp_common.cuh")
 
 
@@ -162,19 +192,22 @@ def flood_traffic(workload_name):
 # --------------------------------------------------------------------------
 # oracle (CPU) timing
 # --------------------------------------------------------------------------
-def oracle_rate(n_steps, seed=2):
-    import oracle
-    sc = workload(seed)
-    o = oracle.Oracle(sc)
-    t0 = time.perf_counter()
-    upd = 0
+def oracle_steps(o, sc, n_steps, budget_s=None):
+    """Coupled oracle steps; returns (updates, seconds, steps taken), stopping
+    early once budget_s seconds have been spent."""
+    t_total, upd, k = 0.0, 0, 0
     for _ in range(n_steps):
         active = int((o.pexit == 0).sum())
-        if o.step_dt() == 0:
+        t0 = time.perf_counter()
+        dt = o.step_dt()
+        t_total += time.perf_counter() - t0
+        if dt == 0:
             break
         upd += sc.n_cells + active
-    el = time.perf_counter() - t0
-    return upd / el, el
+        k += 1
+        if budget_s is not None and t_total >= budget_s:
+            break
+    return upd, t_total, k
 
 
 def run_reference(args):
@@ -183,28 +216,27 @@ def run_reference(args):
         return 0
     import oracle
     oracle.build()
-    sc = workload(2)
+    sc = workload(3)
     o = oracle.Oracle(sc)
-    per = args.ref_sample_steps
-    for _ in range(args.warmup):
-        o.step(per)
-    t_total, upd = 0.0, 0
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        for _ in range(per):
-            active = int((o.pexit == 0).sum())
-            if o.step_dt() == 0:
-                break
-            upd += sc.n_cells + active
-        t_total += time.perf_counter() - t0
+    # one oracle coupled step stands for one benchmark step of the GPU arm (a
+    # bounded sample of its 512); warm-up is one untimed step, and the timed
+    # steps stop once the budget is spent
+    for _ in range(min(args.warmup, 1)):
+        o.step(1)
+    upd, t_total, k = oracle_steps(o, sc, args.steps, budget_s=args.ref_budget_s)
     value = upd / t_total
-    sample = "%d oracle steps per benchmark step of the 512x512 / 10k-evacuee shopping centre" % per
+    cpu = host_cpu()
+    sample = ("%d coupled oracle steps (FP64 C, single thread, %.1f s) of the %s snapshot, after %d untimed; "
+              "each stands for one %d-step benchmark step; host %s, %d cores"
+              % (k, t_total, WORKLOAD, min(args.warmup, 1), CHUNK, cpu["model"], cpu["nproc"]))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
+            "steps": k, "warmup": min(args.warmup, 1), "ms_per_step": 1e3 * t_total / max(k, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": "shopping_centre_512", "nx": 512, "ny": 512, "dx": 0.5, "n_peds": 10000},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "config": {"workload": WORKLOAD, "description": WORKLOAD_TEXT, "nx": sc.nx, "ny": sc.ny, "dx": sc.dx,
+                       "n_peds": sc.n_peds, "t0_s": sc.t0_ticks / float(1 << 20)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                             "nproc": cpu["nproc"], "cpu_model": cpu["model"]},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -213,6 +245,120 @@ def run_reference(args):
 # --------------------------------------------------------------------------
 # our arm
 # --------------------------------------------------------------------------
+class Snapshot:
+    """A simulation's start state kept on the device and restored through the
+    C ABI before every benchmark step (untimed)."""
+
+    def __init__(self, P, N, sim, sc, dev):
+        import torch
+        self.N, self.sim, self.sc = N, sim, sc
+        c = np.ascontiguousarray
+        self.fields = [torch.from_numpy(c(a, np.float32)).to(dev) for a in (sc.h, sc.hu, sc.hv, sc.z)]
+        recs = P.ped_records(sc.peds)
+        self.n_peds = int(recs.shape[0])
+        self.peds = torch.from_numpy(recs.view(np.uint8).copy()).to(dev)
+
+    def restore(self, fields=None, peds=None):
+        N, h = self.N, self.sim.h
+        f = self.fields if fields is None else fields
+        p = self.peds if peds is None else peds
+        N.fp_set_state(h, f[0], f[1], f[2])
+        N.fp_set_bed(h, f[3])
+        N.fp_clear_pedestrians(h)
+        N._check(N.lib().fp_add_pedestrians(h, N._VP(p.data_ptr()), self.n_peds), h)
+        self.sim.n_total = self.n_peds
+        N.fp_set_time(h, self.sc.t0_ticks, self.sc.step0)
+        N.fp_set_barrier_progress(h, self.sc.bags0, self.sc.applied0)
+
+
+def batched_figures(P, args, dev):
+    """A seeded ensemble of shopping centres (grid side 128-1024, 1k-50k
+    pedestrians, 50-1000 responders, 1-3 sandbag layers, inflow peak 0.3-1.5
+    m) stepped together by the batched kernels against the same simulations
+    stepped one by one, each arm's step graphs captured before its timing."""
+    import torch
+    import scenarios
+    t0 = time.perf_counter()
+    scs = scenarios.ensemble(args.ensemble_size)
+    sims = [P.from_scenario(sc) for sc in scs]
+    setup = time.perf_counter() - t0
+    chunk, reps = 64, args.ensemble_steps
+
+    def sim_seconds():
+        return sum(s.counters()["t_ticks"] for s in sims) / float(1 << 20)
+
+    batch = P.Batch(sims)
+    batch.step(chunk)
+    batch.synchronize()
+    s0 = sim_seconds()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        batch.step(chunk)
+    batch.synchronize()
+    t_batch = time.perf_counter() - t0
+    s1 = sim_seconds()
+    batch.close()
+    for sim in sims:  # the members' own step graphs (hashing and hashed-ahead openings)
+        sim.step(2 * chunk)
+        sim.synchronize()
+    s1w = sim_seconds()
+    t0 = time.perf_counter()
+    for sim in sims:
+        sim.step(chunk * reps)
+        sim.synchronize()
+    t_single = time.perf_counter() - t0
+    s2 = sim_seconds()
+    for sim in sims:
+        sim.close()
+    rate_b, rate_1 = (s1 - s0) / t_batch, (s2 - s1w) / t_single
+    return {"value": rate_b, "unit": "scenario-s/s", "one_by_one": rate_1, "speedup_vs_one_by_one": rate_b / rate_1,
+            "scenarios": len(scs), "cells": int(sum(sc.nx * sc.ny for sc in scs)),
+            "pedestrians": int(sum(sc.n_peds for sc in scs)), "steps_timed": chunk * reps,
+            "seconds": {"batched": t_batch, "one_by_one": t_single, "setup": setup},
+            "workload": "ensemble(%d): shopping centres of side 128-1024 cells (0.5 m), 1k-50k pedestrians"
+                        % len(scs)}
+
+
+def surrogate_figures(P, N, sc, args):
+    """The learned surrogate's windows (8 fixed steps of 2^-5 s each, default
+    guard) against the plain update, both from the benchmark snapshot."""
+    import torch
+    dt = 2.0 ** -5
+    sur = P.Surrogate.pretrained()
+    sims = [P.from_scenario(sc) for _ in range(2)]
+    for s in sims:
+        s.set_fixed_dt(dt)
+    plain, surr = sims
+    windows = args.surrogate_windows
+    plain.step(8)
+    plain.synchronize()
+    surr.surrogate_advance(sur, 1)
+    torch.cuda.synchronize()
+    ta = plain.counters()["t_ticks"]
+    t0 = time.perf_counter()
+    plain.step(8 * windows)
+    plain.synchronize()
+    t_plain = time.perf_counter() - t0
+    tb = plain.counters()["t_ticks"]
+    ts0 = surr.counters()["t_ticks"]
+    t0 = time.perf_counter()
+    st = surr.surrogate_advance(sur, windows)
+    t_sur = time.perf_counter() - t0
+    tc = surr.counters()["t_ticks"]
+    hp, hs = plain.field(N.FP_FIELD_H), surr.field(N.FP_FIELD_H)
+    err = float(np.abs(hp - hs).max())
+    rate_p, rate_s = (tb - ta) / N.TICKS / t_plain, (tc - ts0) / N.TICKS / t_sur
+    out = {"value": rate_s, "unit": "scenario-s/s", "plain": rate_p, "speedup_vs_plain": rate_s / rate_p,
+           "max_depth_error_m": err, "meets_1cm": err <= 0.01, "windows": windows, "dt_s": dt,
+           "seconds": {"surrogate": t_sur, "plain": t_plain},
+           "guard": {k: getattr(st, k) for k, _ in st._fields_}}
+    for s in sims:
+        s.close()
+    sur.close()
+    return out
+
+
 def run_ours(args):
     import torch
     ws, rank, local = dist_env()
@@ -223,36 +369,22 @@ def run_ours(args):
     import paper_1908_05232_b300 as P
     from paper_1908_05232_b300 import _native as N
     P.build.build()
-    sc = workload(2 + rank)
+    sc = workload(3 + rank)
+    dev = torch.device("cuda", local)
     stream = torch.cuda.Stream()
     sim = P.from_scenario(sc, tile_rows=args.tile_rows)
     N.fp_set_stream(sim.h, stream.cuda_stream)
-    sim.step(PRE_STEPS)
-    sim.synchronize()
-    # device snapshot
-    dev = torch.device("cuda", local)
-    snap = [torch.empty((sc.ny, sc.nx), dtype=torch.float32, device=dev) for _ in range(3)]
-    for k, t in zip((N.FP_FIELD_H, N.FP_FIELD_HU, N.FP_FIELD_HV), snap):
-        N.fp_read_state(sim.h, k, t)
-    c0 = sim.counters()
-    peds_all = sim.peds()
-    active = peds_all[peds_all["exited"] == 0].copy()
-    peds_dev = torch.from_numpy(active.view(np.uint8).copy()).to(dev)
-    n_act = int(active.shape[0])
+    snap = Snapshot(P, N, sim, sc, dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > 126 MB L2
 
     def restore():
-        N.fp_set_state(sim.h, snap[0], snap[1], snap[2])
-        N.fp_clear_pedestrians(sim.h)
-        N._check(N.lib().fp_add_pedestrians(sim.h, N._VP(peds_dev.data_ptr()), n_act), sim.h)
-        sim.n_total = n_act
-        N.fp_set_time(sim.h, c0["t_ticks"], c0["step"])
+        snap.restore()
         sim.counters()  # runs the post-restore preparation outside the timed region
         with torch.cuda.stream(stream):
             flush.zero_()
         stream.synchronize()
 
-    def one(timed):
+    def one():
         restore()
         a = sim.counters()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -263,8 +395,9 @@ def run_ours(args):
         b = sim.counters()
         if b["error_flags"]:
             raise RuntimeError("device error flags %#x" % b["error_flags"])
-        upd = (b["step"] - a["step"]) * sc.n_cells + (b["ped_updates"] - a["ped_updates"])
-        return e0.elapsed_time(e1), upd, b["step"] - a["step"]
+        st = b["step"] - a["step"]
+        upd = st * sc.n_cells + (b["ped_updates"] - a["ped_updates"])
+        return e0.elapsed_time(e1), upd, st, b["ped_updates"] - a["ped_updates"]
 
     # launch shape: the autotuner's candidates timed on this snapshot (the
     # results never depend on the shape); --tile-rows pins the flood tile height
@@ -276,7 +409,7 @@ def run_ours(args):
                 for ha in (True, False):
                     N.fp_set_tuning(sim.h, tr, pl)
                     N.fp_set_hash_ahead(sim.h, ha)
-                    t = min(one(False)[0] for _ in range(2))
+                    t = min(one()[0] for _ in range(2))
                     if best is None or t < best[0]:
                         best = (t, tr, pl, ha)
         tuned = {"tile_rows": best[1], "ped_lanes": best[2], "hash_ahead": best[3]}
@@ -284,18 +417,19 @@ def run_ours(args):
     N.fp_set_hash_ahead(sim.h, tuned["hash_ahead"])
 
     for _ in range(args.warmup):
-        one(False)
+        one()
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     sampler = ClockSampler(local)
     sampler.start()
-    ms_list, upd_total, steps_total = [], 0, 0
+    ms_list, upd_total, steps_total, ped_total = [], 0, 0, 0
     for _ in range(args.steps):
-        ms, upd, st = one(True)
+        ms, upd, st, pu = one()
         ms_list.append(ms)
         upd_total += upd
         steps_total += st
+        ped_total += pu
     torch.cuda.synchronize()
     clocks = sampler.stop()
     t_sec = sum(ms_list) / 1e3
@@ -304,56 +438,55 @@ def run_ours(args):
     else:
         upd_all = float(upd_total)
     value = upd_all / t_sec
+    ms_step = statistics.mean(ms_list)
 
-    # profiled pass: CUDA events around each kernel group, same workload
+    # profiled pass: the same steps captured with CUDA events between the
+    # kernels (on the stream each kernel runs on) and replayed
     restore()
     N.fp_set_profiling(sim.h, 1)
     sim.step(CHUNK)
     prof = sim.profile()
     N.fp_set_profiling(sim.h, 0)
-    flood_ms = prof["flood_ms"] / max(prof["steps"], 1)
+    nprof = max(prof["steps"], 1)
+    flood_ms = prof["flood_ms"] / nprof
+    ped_ms = prof["ped_ms"] / nprof
     hbm, peak_kind = peaks()
-    # algorithmic bytes: the cells of the tiles the kernel computed (dry tiles
-    # it skips move no bytes)
-    flood_cells = prof["flood_cells"] / max(prof["steps"], 1)
+    flood_cells = prof["flood_cells"] / nprof  # cells of the tiles computed (dry tiles are skipped)
     achieved = flood_cells * FLOOD_BYTES_PER_CELL / (flood_ms * 1e-3) / 1e9
-    traffic = flood_traffic("shopping_centre_512")
+    peds_per_step = ped_total / max(steps_total, 1)
+    ped_achieved = peds_per_step * PED_BYTES / (ped_ms * 1e-3) / 1e9 if ped_ms > 0 else None
 
     # end to end through the C ABI with pinned host buffers
-    host_state = [t.cpu().pin_memory() for t in snap]
-    host_peds = torch.from_numpy(active.view(np.uint8).copy()).pin_memory()
+    host_fields = [t.cpu().pin_memory() for t in snap.fields]
+    host_peds = snap.peds.cpu().pin_memory()
+    n_act = snap.n_peds
     out_state = [torch.empty((sc.ny, sc.nx), dtype=torch.float32).pin_memory() for _ in range(3)]
     out_peds = torch.empty(n_act * 32, dtype=torch.uint8).pin_memory()
-    e2e_t = 0.0
+    e2e_t, e2e_upd = 0.0, 0
     for it in range(args.warmup + args.steps):
         with torch.cuda.stream(stream):
             flush.zero_()
         stream.synchronize()
         t0 = time.perf_counter()
-        N.fp_set_state(sim.h, host_state[0], host_state[1], host_state[2])
-        N.fp_clear_pedestrians(sim.h)
-        N._check(N.lib().fp_add_pedestrians(sim.h, N._VP(host_peds.data_ptr()), n_act), sim.h)
-        sim.n_total = n_act
-        N.fp_set_time(sim.h, c0["t_ticks"], c0["step"])
+        snap.restore(host_fields, host_peds)
+        a = sim.counters()
         sim.step(CHUNK)
         for k, t in zip((N.FP_FIELD_H, N.FP_FIELD_HU, N.FP_FIELD_HV), out_state):
             N.fp_read_state(sim.h, k, t)
         N._check(N.lib().fp_read_state(sim.h, N.FP_FIELD_PEDS, N._VP(out_peds.data_ptr()), n_act * 32), sim.h)
-        sim.counters()
+        b = sim.counters()
         el = time.perf_counter() - t0
         if it >= args.warmup:
             e2e_t += el
-    # every iteration replays the same 256 steps from the snapshot (deterministic),
-    # so it performs the same updates as a device-timed iteration
-    e2e_value = (upd_total / args.steps) * args.steps / e2e_t
-    h2d = 3 * sc.n_cells * 4 + n_act * 32
-    d2h = 3 * sc.n_cells * 4 + n_act * 32 + ctypes.sizeof(N.FpCounters)
+            e2e_upd += (b["step"] - a["step"]) * sc.n_cells + (b["ped_updates"] - a["ped_updates"])
+    e2e_value = e2e_upd / e2e_t
+    h2d = 4 * sc.n_cells * 4 + n_act * 32
+    d2h = 3 * sc.n_cells * 4 + n_act * 32 + 2 * ctypes.sizeof(N.FpCounters)
 
     # the same kernel where it is HBM-bound: a 2048x2048 grid holding water
-    # almost everywhere (no pedestrians, so the kernel runs alone), CUDA events
-    # around the flood kernel in a profiled pass
-    roof2048 = None
-    if rank == 0 and not args.no_2048:
+    # almost everywhere (no pedestrians, so the kernel runs alone)
+    roof_wet = None
+    if rank == 0 and not args.no_wet2048:
         big = wet2048()
         bsim = P.from_scenario(big, peds=False)
         N.fp_set_stream(bsim.h, stream.cuda_stream)
@@ -366,48 +499,75 @@ def run_ours(args):
         bflood = bprof["flood_ms"] / max(bprof["steps"], 1)
         bcells = bprof["flood_cells"] / max(bprof["steps"], 1)
         bach = bcells * FLOOD_BYTES_PER_CELL / (bflood * 1e-3) / 1e9
-        roof2048 = {"kernel": "flood_kernel<16>", "workload": "wet_2048 (2048x2048 cells of 0.5 m, 70 % wet, every boundary type)",
-                    "bound": "hbm", "achieved": bach, "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s",
-                    "frac": bach / hbm, "us_per_launch": bflood * 1e3, "bytes_per_cell_update": FLOOD_BYTES_PER_CELL,
-                    "computed_cells_per_launch": bcells,
-                    "traffic": flood_traffic("wet_2048"), "note": "profiled pass, no pedestrians: the kernel timed alone"}
+        roof_wet = {"kernel": "flood_kernel<16>", "workload": "wet_2048 (2048x2048 cells of 0.5 m, 70 % wet, "
+                    "every boundary type)", "bound": "hbm", "achieved": bach, "peak": hbm, "peak_kind": peak_kind,
+                    "unit": "GB/s", "frac": bach / hbm, "us_per_launch": bflood * 1e3,
+                    "bytes_per_cell_update": FLOOD_BYTES_PER_CELL, "computed_cells_per_launch": bcells,
+                    "traffic": flood_traffic("wet_2048"), "note": "profiled pass, no pedestrians: the kernel alone"}
         bsim.close()
+
+    sim.close()
+    batched = surrogate = None
+    if rank == 0 and not args.no_batched:
+        batched = batched_figures(P, args, dev)
+    if rank == 0 and not args.no_surrogate:
+        surrogate = surrogate_figures(P, N, sc, args)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        rate, el = oracle_rate(args.cpu_sample_steps)
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "first %d coupled steps of the same 512x512 / 10k-evacuee workload, FP64 C oracle, "
-                         "single thread (%.1f s)" % (args.cpu_sample_steps, el)}
+        import oracle
+        oracle.build()
+        o = oracle.Oracle(sc)
+        upd, el, k = oracle_steps(o, sc, args.cpu_sample_steps)
+        hc = host_cpu()
+        cpu = {"value": upd / el, "unit": UNIT, "cores": 1, "kind": "oracle", "nproc": hc["nproc"],
+               "cpu_model": hc["model"],
+               "sample": "%d coupled step(s) of the same %s snapshot, FP64 C oracle, single thread (%.1f s)"
+                         % (k, WORKLOAD, el)}
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": statistics.mean(ms_list), "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "shopping_centre_512", "nx": sc.nx, "ny": sc.ny, "dx": sc.dx,
-                       "n_peds": sc.n_peds, "n_peds_active_at_snapshot": n_act,
-                       "sim_steps_per_bench_step": CHUNK, "snapshot_after_steps": PRE_STEPS,
+            "config": {"workload": WORKLOAD, "description": WORKLOAD_TEXT, "nx": sc.nx, "ny": sc.ny, "dx": sc.dx,
+                       "n_peds": sc.n_peds, "n_responders": int((sc.peds["role"] == 1).sum()),
+                       "barrier_cells": int(sc.barrier_cells.size), "barrier_layers": int(sc.n_layers),
+                       "t0_s": sc.t0_ticks / float(1 << 20), "wet_fraction_at_start": float((sc.h > 0).mean()),
+                       "sim_steps_per_bench_step": CHUNK,
                        "parallelism": "replicas" if ws > 1 else "single",
-                       "l2": "flushed between timed iterations (256 MB write); the 512x512 working set "
-                             "(~10 MB) is L2-resident within an iteration",
+                       "l2": "flushed between timed iterations (256 MB write); the working set (~0.5 GB) "
+                             "exceeds L2",
                        "tile_rows": tuned["tile_rows"], "ped_lanes": tuned["ped_lanes"],
                        "hash_ahead": tuned["hash_ahead"],
                        "launch_shape": "default" if args.no_tune else "fastest autotuner candidate on the snapshot"},
-            "breakdown": {"cell_updates_per_s": steps_total * sc.n_cells / (sum(ms_list) / 1e3),
-                          "ped_updates_per_s": (upd_total - steps_total * sc.n_cells) / (sum(ms_list) / 1e3),
-                          "profiled_ms_per_step": {k: prof[k] / max(prof["steps"], 1)
-                                                   for k in ("hash_ms", "flood_ms", "ped_chain_ms", "step_ms")}},
+            "breakdown": {"cell_updates_per_s": steps_total * sc.n_cells / t_sec,
+                          "computed_cell_updates_per_s": steps_total * flood_cells / t_sec,
+                          "computed_cells_per_step": flood_cells, "cells_per_step": sc.n_cells,
+                          "ped_updates_per_s": ped_total / t_sec,
+                          "us_per_sim_step": 1e3 * ms_step / CHUNK,
+                          "profiled_us_per_step": {k[:-3]: 1e3 * prof[k] / nprof
+                                                   for k in ("hash_ms", "flood_ms", "ped_chain_ms", "ped_ms",
+                                                             "step_ms")}},
             "roofline": {"kernel": "flood_kernel<%d>" % tuned["tile_rows"], "bound": "hbm", "achieved": achieved,
-                         "peak": hbm,
-                         "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
-                         "bytes_per_cell_update": FLOOD_BYTES_PER_CELL,
+                         "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm,
+                         "traffic": flood_traffic(WORKLOAD), "bytes_per_cell_update": FLOOD_BYTES_PER_CELL,
                          "computed_cells_per_launch": flood_cells, "cells_per_launch": sc.n_cells,
-                         "note": "512x512 fits in L2; frac is against HBM; bytes counted for the cells of "
-                                 "the tiles computed (dry tiles are skipped)"},
-            "roofline_2048": roof2048,
+                         "us_per_launch": flood_ms * 1e3,
+                         "note": "launch duration from CUDA events on the flood kernel's own stream in a profiled "
+                                 "pass of the same 512 steps; bytes counted for the cells of the tiles computed"},
+            "roofline_peds": {"kernel": "ped_step_kernel<%d>" % tuned["ped_lanes"], "bound": "hbm",
+                              "achieved": ped_achieved, "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s",
+                              "frac": ped_achieved / hbm if ped_achieved else None, "traffic": None,
+                              "bytes_per_ped_update": PED_BYTES, "peds_per_launch": peds_per_step,
+                              "us_per_launch": ped_ms * 1e3,
+                              "note": "issue- and latency-bound (neighbour scans out of L1/L2); HBM fraction of "
+                                      "its algorithmic bytes for reference"},
+            "roofline_wet2048": roof_wet,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "batched": batched,
+            "surrogate": surrogate,
             "clocks": clocks,
             "gpu_launches": launches_per_chunk(sc, tuned["hash_ahead"]) * args.steps,
         }
@@ -420,149 +580,36 @@ def run_ours(args):
 
 
 def run_surrogate(args):
-    """Learned surrogate against the plain update on the 2048x2048 shopping
-    centre with 100,000 coupled pedestrians (500 responders building a 2-layer
-    barrier; flood from t = 900 s): two identical simulations are brought to
-    mid-flood (CFL step), then the same simulated interval is run with the plain
-    update at a fixed 2^-5 s step and with surrogate windows of 8 such steps
-    (default guard: per-tile mass bound 1e-4, plain check every 64 steps,
-    suspension above 1 cm).  Metric: simulated seconds per wall second;
-    accuracy: the largest depth difference between the two runs at the end."""
+    """Learned surrogate against the plain update on the benchmark snapshot
+    (2048x2048 shopping centre mid-flood, 100,000 coupled pedestrians), over
+    --steps x 8 windows."""
     import torch
-    import scenarios
     import paper_1908_05232_b300 as P
     from paper_1908_05232_b300 import _native as N
     torch.cuda.set_device(0)
     P.build.build()
-    dt = 2.0 ** -5
-    sc = scenarios.config_barrier()
-    t_start = args.surrogate_start
-    sur = P.Surrogate.pretrained()
-    t0 = time.perf_counter()
-    sims = []
-    for _ in range(2):
-        sim = P.from_scenario(sc)
-        c = sim.counters()
-        while c["t_ticks"] < int(t_start * N.TICKS):
-            sim.step(256)
-            c = sim.counters()
-        sim.set_fixed_dt(dt)
-        sims.append(sim)
-    setup = time.perf_counter() - t0
-    plain, surr = sims
-    assert plain.counters()["t_ticks"] == surr.counters()["t_ticks"]
-    windows = args.steps * 8
-    # warm-up: one window each (graphs, scratch buffers), on both simulations
-    plain.step(8)
-    plain.synchronize()
-    st_w = surr.surrogate_advance(sur, 1, fix_tol=args.surrogate_fix_tol)
-    torch.cuda.synchronize()
-    ta = plain.counters()["t_ticks"]
-    t0 = time.perf_counter()
-    plain.step(8 * windows)
-    plain.synchronize()
-    t_plain = time.perf_counter() - t0
-    tb = plain.counters()["t_ticks"]
-    ts0 = surr.counters()["t_ticks"]
-    t0 = time.perf_counter()
-    st = surr.surrogate_advance(sur, windows, fix_tol=args.surrogate_fix_tol)
-    t_sur = time.perf_counter() - t0
-    tc = surr.counters()["t_ticks"]
-    sim_s = (tb - ta) / N.TICKS
-    sim_s_sur = (tc - ts0) / N.TICKS
-    err = float(np.abs(plain.field(N.FP_FIELD_H) - surr.field(N.FP_FIELD_H)).max())
-    wet_frac = float((plain.field(N.FP_FIELD_H) > 0).mean())
-    rate_p, rate_s = sim_s / t_plain, sim_s_sur / t_sur
-    line = {"metric": "scenario-seconds/s (learned surrogate windows vs plain update)", "value": rate_s,
-            "unit": "scenario-s/s", "n_gpus": 1, "steps": args.steps, "warmup": 1,
-            "ms_per_step": 1e3 * t_sur / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "bf16 net (FP32 accumulate), f32 plain update", "data": "synthetic",
-            "config": {"workload": "surrogate_2048 (2048x2048 shopping centre, 100,000 pedestrians, barrier, "
-                                   "flood from 900 s)", "start_s": t_start, "dt_s": dt,
-                       "windows": windows, "steps_per_window": 8, "wet_fraction_at_end": wet_frac,
-                       "guard": {"mass_tol": 1e-4, "fix_tol": args.surrogate_fix_tol, "check_tol_m": 0.01,
-                                 "check_every_windows": 8, "suspend_windows": 8},
-                       "setup_s": setup},
-            "plain": {"value": rate_p, "unit": "scenario-s/s", "seconds": t_plain},
-            "speedup_vs_plain": rate_s / rate_p,
-            "max_depth_error_m": err,
-            "guard": {k: getattr(st, k) for k, _ in st._fields_}}
+    args.surrogate_windows = args.steps * 8
+    out = surrogate_figures(P, N, workload(3), args)
+    line = {"metric": "scenario-seconds/s (learned surrogate windows vs plain update)", "value": out["value"],
+            "unit": "scenario-s/s", "n_gpus": 1, "steps": args.steps, "warmup": 1, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16 net (FP32 accumulate), f32 plain update",
+            "data": "synthetic", "config": {"workload": WORKLOAD + " (fixed 2^-5 s step)"}, "surrogate": out}
     print(json.dumps(line), flush=True)
     return 0
 
 
 def run_ensemble(args):
-    """Batched ensemble: 256 seeded shopping-centre scenarios (grid side 128-1024,
-    1k-50k pedestrians, 50-1000 responders, 1-3 sandbag layers, inflow peak
-    0.3-1.5 m) stepped together by the batched kernels, against the same
-    simulations stepped one by one.  Metric: simulated scenario-seconds per
-    wall second."""
+    """Batched ensemble (--ensemble-size scenarios) against one by one."""
     import torch
-    import scenarios
     import paper_1908_05232_b300 as P
     torch.cuda.set_device(0)
     P.build.build()
-    scs = scenarios.ensemble(args.ensemble_size)
-    t0 = time.perf_counter()
-    sims = [P.from_scenario(sc) for sc in scs]
-    setup = time.perf_counter() - t0
-    batch = P.Batch(sims)
-    chunk = 64
-    for _ in range(args.warmup):
-        batch.step(chunk)
-    batch.synchronize()
-
-    def sim_seconds():
-        return sum(s.counters()["t_ticks"] for s in sims) / float(1 << 20)
-
-    def cell_steps():
-        return sum(s.counters()["step"] * s.nx * s.ny for s in sims)
-
-    s0, c0 = sim_seconds(), cell_steps()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        batch.step(chunk)
-    batch.synchronize()
-    t_batch = time.perf_counter() - t0
-    s1, c1 = sim_seconds(), cell_steps()
-    batch.close()
-    # the simulations' own step graphs (a step whose records are not yet hashed
-    # ahead, then one whose are) captured before the timed arms, as the batch's
-    # were in its warm-up
-    for sim in sims:
-        sim.step(2 * chunk)
-        sim.synchronize()
-    s1w, c1w = sim_seconds(), cell_steps()
-    # one by one: each simulation's steps run to completion before the next starts
-    t0 = time.perf_counter()
-    for sim in sims:
-        sim.step(chunk * args.steps)
-        sim.synchronize()
-    t_single = time.perf_counter() - t0
-    s2, c2 = sim_seconds(), cell_steps()
-    # independent: every simulation on its own stream, all enqueued at once
-    t0 = time.perf_counter()
-    for sim in sims:
-        sim.step(chunk * args.steps)
-    for sim in sims:
-        sim.synchronize()
-    t_streams = time.perf_counter() - t0
-    s3 = sim_seconds()
-    rate_b = (s1 - s0) / t_batch
-    rate_1 = (s2 - s1w) / t_single
-    rate_s = (s3 - s2) / t_streams
-    line = {"metric": "scenario-seconds/s (batched ensemble)", "value": rate_b, "unit": "scenario-s/s",
-            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_batch / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "ensemble_%d" % len(scs), "scenarios": len(scs),
-                       "cells": int(sum(sc.nx * sc.ny for sc in scs)), "pedestrians": int(sum(sc.n_peds for sc in scs)),
-                       "sim_steps_per_bench_step": chunk, "setup_s": setup},
-            "one_by_one": {"value": rate_1, "unit": "scenario-s/s", "seconds": t_single},
-            "independent_streams": {"value": rate_s, "unit": "scenario-s/s", "seconds": t_streams},
-            "speedup_vs_one_by_one": rate_b / rate_1,
-            "speedup_vs_independent_streams": rate_b / rate_s,
-            "cell_updates_per_s_batched": (c1 - c0) / t_batch, "cell_updates_per_s_one_by_one": (c2 - c1w) / t_single}
+    args.ensemble_steps = args.steps
+    out = batched_figures(P, args, torch.device("cuda", 0))
+    line = {"metric": "scenario-seconds/s (batched ensemble)", "value": out["value"], "unit": "scenario-s/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": 1, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "ensemble_%d" % out["scenarios"]}, "batched": out}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -579,10 +626,14 @@ def run_case(args):
     P.build.build()
     if args.ncu_case == "barrier2048":
         sc = scenarios.config_barrier()
+    elif args.ncu_case == "barrier2048mid":
+        sc = workload(3)
     elif args.ncu_case == "wet2048":
         sc = wet2048()
+    elif args.ncu_case == "wet1024":
+        sc = scenarios.random_wet_state(1024, 1024, dx=0.5, seed=5)
     else:
-        sc = workload(2)
+        sc = scenarios.config_shopping()
     from paper_1908_05232_b300 import _native as N
     sim = P.from_scenario(sc, tile_rows=args.tile_rows)
     stream = torch.cuda.Stream()
@@ -614,27 +665,29 @@ def run_case(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--tile-rows", type=int, default=0)
-    ap.add_argument("--no-2048", action="store_true", help="skip the 2048x2048 flood-kernel roofline pass")
+    ap.add_argument("--no-wet2048", action="store_true", help="skip the wet 2048x2048 flood-kernel roofline pass")
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch shape (16-row tiles, 8 lanes)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sample-steps", type=int, default=100)
-    ap.add_argument("--ref-sample-steps", type=int, default=8)
-    ap.add_argument("--ncu-case", choices=["barrier2048", "wet2048", "shopping512"], default=None,
-                    help="short untimed run of one workload, for profiler captures")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-ensemble figures")
+    ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate figures")
+    ap.add_argument("--cpu-sample-steps", type=int, default=1)
+    ap.add_argument("--ref-budget-s", type=float, default=150.0,
+                    help="reference arm: stop timing oracle steps once this many seconds are spent")
+    ap.add_argument("--ensemble-size", type=int, default=48)
+    ap.add_argument("--ensemble-steps", type=int, default=4, help="64-step chunks timed per ensemble arm")
+    ap.add_argument("--surrogate-windows", type=int, default=160)
+    ap.add_argument("--ncu-case", choices=["barrier2048", "barrier2048mid", "wet2048", "wet1024", "shopping512"],
+                    default=None, help="short untimed run of one workload, for profiler captures")
     ap.add_argument("--case-steps", type=int, default=4)
     ap.add_argument("--case-lanes", type=int, default=8, choices=[4, 8, 16], help="lanes per pedestrian in the case")
     ap.add_argument("--case-hash-ahead", type=int, default=1, choices=[0, 1], help="hash-ahead in the case")
     ap.add_argument("--case-time", type=float, default=0.0,
                     help="simulated seconds to run before the case's steps (profiler range opened after them)")
-    ap.add_argument("--workload", choices=["shopping512", "ensemble", "surrogate"], default="shopping512")
-    ap.add_argument("--surrogate-start", type=float, default=1500.0, help="simulated time (s) the surrogate run starts at")
-    ap.add_argument("--surrogate-fix-tol", type=float, default=0.0,
-                    help="accept net tiles up to this mass residual and close their balance (0: the 1e-4 bound)")
-    ap.add_argument("--ensemble-size", type=int, default=256)
+    ap.add_argument("--workload", choices=["barrier2048", "ensemble", "surrogate"], default="barrier2048")
     args = ap.parse_args()
     if args.ncu_case:
         return run_case(args)

@@ -48,6 +48,7 @@ extern "C" {
 #define FP_BC_WALL 0         /* reflective wall */
 #define FP_BC_TRANSMISSIVE 1 /* zero-gradient ("slip" outflow) */
 #define FP_BC_INFLOW 2       /* ghost at rest with the hydrograph depth */
+#define FP_BC_DISCHARGE 3    /* breach: a wall through which the discharge hydrograph enters */
 
 #define FP_EDGE_SOUTH 0 /* row j = 0, nx codes */
 #define FP_EDGE_NORTH 1 /* row j = ny-1, nx codes */
@@ -77,10 +78,15 @@ extern "C" {
 #define FP_FIELD_COUNTERS 5 /* one fp_counters */
 #define FP_FIELD_NAV 6      /* uint8[3*ny*nx]: exit, storage, barrier direction codes */
 #define FP_FIELD_MASS 7     /* double[2]: water volume sum h dx^2 (m^3), net boundary inflow volume (m^3) */
-#define FP_FIELD_PROFILE 8  /* double[6]: profiled steps, then total ms of: the hashing/scan part,
+#define FP_FIELD_PROFILE 8  /* double[7]: profiled steps, then total ms of: the hashing/scan part,
                                the flood update, the gather + pedestrian part, whole steps;
                                then the cell updates the flood kernel computed (cells of
-                               tiles not skipped as dry, see fp_step) (see fp_set_profiling) */
+                               tiles not skipped as dry, see fp_step); then total ms of
+                               the pedestrian kernel alone (0 in FP_MODE_PERSISTENT)
+                               (see fp_set_profiling) */
+#define FP_FIELD_HR_MAX 9   /* float[1]: largest hazard rating HR = (max(|u|,|v|) + 0.5) h over
+                               the cells holding water (Section 2.4; sampled over time it is the
+                               maximum-HR history of Fig. 5(b)) */
 
 /* Simulation set-up.  Sizes: nx, ny >= 1; max_peds >= 0. */
 typedef struct fp_config {
@@ -146,6 +152,12 @@ int fp_set_stream(fp_sim *sim, void *cuda_stream);
 int fp_set_terrain(fp_sim *sim, const float *z, const float *n0, const uint8_t *walkable,
                    const uint8_t *exit_mask);
 
+/* Bed elevation only (Section 2.1 flood agent z), float[ny*nx]: replaces z,
+ * barrier raises included, leaving walkability and the navigation fields as
+ * they are (e.g. to restore a run taken mid-deployment together with
+ * fp_set_barrier_progress).  The next two steps compute every flood tile. */
+int fp_set_bed(fp_sim *sim, const float *z);
+
 /* Boundary codes of one edge (FP_EDGE_*): uint8[nx] for south/north, uint8[ny]
  * for west/east, each FP_BC_*. */
 int fp_set_boundary(fp_sim *sim, int32_t edge, const uint8_t *codes);
@@ -153,6 +165,20 @@ int fp_set_boundary(fp_sim *sim, int32_t edge, const uint8_t *codes);
 /* Inflow depth hydrograph (Section 3.1, depth form): n >= 1 points (t_k, h_k),
  * t increasing (s), h >= 0 (m); linear between points, constant outside. */
 int fp_set_hydrograph(fp_sim *sim, const double *t, const double *h, int32_t n);
+
+/* Discharge hydrograph (Section 3.1, the paper's form): n >= 1 points (t_k,
+ * Q_k), t increasing (s), Q >= 0 (m^3/s); linear between points, constant
+ * outside (a triangle (0, 0), (t_inflow / 2, Q_peak), (t_inflow, 0) is the
+ * paper's).  The water enters through the boundary cells coded
+ * FP_BC_DISCHARGE, spread evenly over their total width B = count x dx, at
+ * depth h_inflow (m, > 0; the paper's 1 m): over a step [t, t + dt] each
+ * breach face carries the mass flux q = (V(t + dt) - V(t)) / (dt B), V the
+ * exact volume the hydrograph has released since t = 0, and the momentum
+ * q^2 / h_inflow, added to the flux of a wall (so the domain gains exactly
+ * V(t + dt) - V(t); with Q = 0 the breach is a wall).  The CFL step includes
+ * the inflowing water's speed Q(t) / (B h_inflow) + sqrt(g h_inflow).
+ * FP_EINVAL for bad points or depth.  Not taken by fp_surrogate_advance. */
+int fp_set_discharge(fp_sim *sim, const double *t, const double *q, int32_t n, double h_inflow);
 
 /* Sandbag storage cells and the ordered barrier cells (Section 2.4, Fig. 3-right),
  * flat cell indices; n_layers = N_L layers of one bag thickness (0.25 m). */
@@ -337,8 +363,23 @@ int fp_surrogate_advance(fp_sim *sim, fp_surrogate *sur, int32_t n_windows, cons
                          fp_surrogate_stats *stats);
 
 /* Wait for enqueued work; returns FP_ETIMEOUT / FP_EOVERFLOW / FP_ENAN when the
- * device raised the corresponding error bit. */
+ * device raised the corresponding error bit (a non-finite depth or discharge
+ * written by the flood update: FP_ENAN; a grid-barrier wait that gave up:
+ * FP_ETIMEOUT).  An error is reported once: the call then clears the device
+ * error word and the per-step hash and evacuee counts, so the handle stays
+ * usable, but the water and pedestrian state reached by the failed steps is
+ * undefined -- set it again (fp_set_state, fp_clear_pedestrians +
+ * fp_add_pedestrians, fp_set_time) before stepping on. */
 int fp_synchronize(fp_sim *sim);
+
+/* Bound of every grid-barrier wait of the persistent step kernel
+ * (FP_MODE_PERSISTENT), in polls of the barrier word (default 4,194,304, a
+ * few seconds).  A CTA whose wait runs out sets the timeout error bit and
+ * leaves the kernel (no copy of it is in flight at a barrier); the others
+ * follow at their next barrier, and fp_synchronize returns FP_ETIMEOUT.  A
+ * small limit makes a wait run out on purpose (failure-detection tests);
+ * polls >= 0, else FP_EINVAL. */
+int fp_set_barrier_wait_limit(fp_sim *sim, int32_t polls);
 
 /* Copy one FP_FIELD_* into dst (host or device), bytes >= the field's size.
  * Synchronises the stream. */

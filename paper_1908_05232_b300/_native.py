@@ -17,6 +17,8 @@ from . import build as _build
 FP_OK, FP_EINVAL, FP_ENOMEM, FP_ECUDA, FP_ETIMEOUT, FP_ENAN, FP_EOVERFLOW = 0, -1, -2, -3, -4, -5, -6
 FP_FIELD_H, FP_FIELD_HU, FP_FIELD_HV, FP_FIELD_Z = 0, 1, 2, 3
 FP_FIELD_PEDS, FP_FIELD_COUNTERS, FP_FIELD_NAV, FP_FIELD_MASS, FP_FIELD_PROFILE = 4, 5, 6, 7, 8
+FP_FIELD_HR_MAX = 9
+FP_BC_WALL, FP_BC_TRANSMISSIVE, FP_BC_INFLOW, FP_BC_DISCHARGE = 0, 1, 2, 3
 FP_EDGE_SOUTH, FP_EDGE_NORTH, FP_EDGE_WEST, FP_EDGE_EAST = 0, 1, 2, 3
 TICKS = 1 << 20
 FP_MODE_KERNELS, FP_MODE_PERSISTENT = 0, 1
@@ -75,8 +77,9 @@ def lib():
         L = ctypes.CDLL(_build.LIB)
         sigs = {
             "fp_sim_create": [_VP, _VP], "fp_set_stream": [_VP, _VP],
-            "fp_set_terrain": [_VP] * 5, "fp_set_boundary": [_VP, ctypes.c_int32, _VP],
+            "fp_set_terrain": [_VP] * 5, "fp_set_bed": [_VP, _VP], "fp_set_boundary": [_VP, ctypes.c_int32, _VP],
             "fp_set_hydrograph": [_VP, _VP, _VP, ctypes.c_int32],
+            "fp_set_discharge": [_VP, _VP, _VP, ctypes.c_int32, ctypes.c_double],
             "fp_set_goals": [_VP, _VP, ctypes.c_int32, _VP, ctypes.c_int32, ctypes.c_int32],
             "fp_set_state": [_VP] * 4, "fp_set_time": [_VP, ctypes.c_int64, ctypes.c_int64],
             "fp_set_barrier_progress": [_VP, ctypes.c_int64, ctypes.c_int64],
@@ -86,7 +89,7 @@ def lib():
             "fp_batch_create": [_VP, ctypes.c_int32, _VP], "fp_batch_step": [_VP, ctypes.c_int32],
             "fp_batch_synchronize": [_VP], "fp_batch_destroy": [_VP], "fp_set_profiling": [_VP, ctypes.c_int32],
             "fp_read_state": [_VP, ctypes.c_int32, _VP, ctypes.c_size_t], "fp_destroy": [_VP],
-            "fp_set_fixed_dt": [_VP, ctypes.c_double], "fp_surrogate_advance": [_VP, _VP, ctypes.c_int32, _VP, _VP],
+            "fp_set_fixed_dt": [_VP, ctypes.c_double], "fp_set_barrier_wait_limit": [_VP, ctypes.c_int32], "fp_surrogate_advance": [_VP, _VP, ctypes.c_int32, _VP, _VP],
         }
         for name, args in sigs.items():
             f = getattr(L, name)
@@ -144,6 +147,10 @@ def fp_set_terrain(h, z, n0, walkable, exit_mask):
     _check(lib().fp_set_terrain(h, _ptr(z), _ptr(n0), _ptr(walkable), _ptr(exit_mask)), h)
 
 
+def fp_set_bed(h, z):
+    _check(lib().fp_set_bed(h, _ptr(z)), h)
+
+
 def fp_set_boundary(h, edge, codes):
     _check(lib().fp_set_boundary(h, edge, _ptr(codes)), h)
 
@@ -152,6 +159,12 @@ def fp_set_hydrograph(h, t, depth):
     t = np.ascontiguousarray(t, np.float64)
     depth = np.ascontiguousarray(depth, np.float64)
     _check(lib().fp_set_hydrograph(h, _ptr(t), _ptr(depth), int(t.size)), h)
+
+
+def fp_set_discharge(h, t, q, h_inflow):
+    t = np.ascontiguousarray(t, np.float64)
+    q = np.ascontiguousarray(q, np.float64)
+    _check(lib().fp_set_discharge(h, _ptr(t), _ptr(q), int(t.size), float(h_inflow)), h)
 
 
 def fp_set_goals(h, depot, barrier, n_layers):
@@ -203,6 +216,10 @@ def fp_set_profiling(h, on):
 
 def fp_synchronize(h):
     _check(lib().fp_synchronize(h), h)
+
+
+def fp_set_barrier_wait_limit(h, polls):
+    _check(lib().fp_set_barrier_wait_limit(h, int(polls)), h)
 
 
 def fp_read_state(h, which, dst):
@@ -294,14 +311,20 @@ class Simulation:
         return st
 
     def profile(self) -> dict:
-        out = np.zeros(6, np.float64)
+        out = np.zeros(7, np.float64)
         fp_read_state(self.h, FP_FIELD_PROFILE, out)
         return dict(steps=out[0], hash_ms=out[1], flood_ms=out[2], ped_chain_ms=out[3], step_ms=out[4],
-                    flood_cells=out[5])
+                    flood_cells=out[5], ped_ms=out[6])
 
     def nav(self):
         out = np.empty((3, self.ny, self.nx), np.uint8)
         return fp_read_state(self.h, FP_FIELD_NAV, out)
+
+    def max_hr(self) -> float:
+        """Largest hazard rating over the cells holding water (FP_FIELD_HR_MAX)."""
+        out = np.zeros(1, np.float32)
+        fp_read_state(self.h, FP_FIELD_HR_MAX, out)
+        return float(out[0])
 
     def mass(self):
         out = np.zeros(2, np.float64)
@@ -357,6 +380,8 @@ def from_scenario(sc, max_peds=None, tile_rows=0, peds=True, mode=None) -> Simul
                         (FP_EDGE_EAST, sc.bc_e)):
         fp_set_boundary(sim.h, edge, c(codes, np.uint8))
     fp_set_hydrograph(sim.h, sc.hydro_t, sc.hydro_h)
+    if getattr(sc, "q_t", None) is not None and len(sc.q_t):
+        fp_set_discharge(sim.h, sc.q_t, sc.q_Q, sc.h_qin)
     fp_set_goals(sim.h, sc.depot_cells, sc.barrier_cells, sc.n_layers)
     fp_set_state(sim.h, c(sc.h, np.float32), c(sc.hu, np.float32), c(sc.hv, np.float32))
     if getattr(sc, "t0_ticks", 0) or getattr(sc, "step0", 0):

@@ -70,7 +70,10 @@ __global__ void init_clock_kernel(const __grid_constant__ FpSim S, int par, int 
         if (smax > 0.0f) atomicMax(&S.clock[slot].smax_bits, __float_as_uint(smax));
         if (wet) atomicOr(&S.clock[slot].wet, 1);
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) S.clock[slot].h_in = (float)fp_hydro_depth(S, S.clock[slot].t);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        S.clock[slot].h_in = (float)fp_hydro_depth(S, S.clock[slot].t);
+        S.clock[slot].q_speed = fp_discharge_speed(S, S.clock[slot].t);
+    }
 }
 
 // Water volume sum h dx^2 in FP64: per-CTA partials, then the last CTA adds
@@ -109,7 +112,32 @@ __global__ void mass_kernel(const __grid_constant__ FpSim S, int par) {
     }
 }
 
+// Largest hazard rating HR = (max(|u|,|v|) + 0.5) h over the cells holding
+// water (h > h_eps), FP32 with correctly rounded division (Section 2.4;
+// Fig. 5(b) follows its time history).  Non-negative floats order as their
+// bit patterns: one integer max per warp.
+__global__ void hr_max_kernel(const __grid_constant__ FpSim S, int par) {
+    unsigned best = 0u;
+    const long long n = (long long)S.nx * S.ny;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(c % S.nx), j = (int)(c / S.nx);
+        const size_t o = fp_pidx(S, i, j);
+        const float h = S.h[par][o];
+        if (!(h > FP_H_EPS_F)) continue;
+        const float V = __fdiv_rn(fmaxf(fabsf(S.hu[par][o]), fabsf(S.hv[par][o])), h);
+        const float hr = __fmul_rn(__fadd_rn(V, 0.5f), h);
+        best = max(best, __float_as_uint(hr));
+    }
+    best = __reduce_max_sync(0xffffffffu, best);
+    if ((threadIdx.x & 31) == 0 && best) atomicMax(&S.cnt->hr_max_bits, best);
+}
+
 }  // namespace
+
+void fp_launch_hr_max(const FpSim &S, int par, cudaStream_t st) {
+    cudaMemsetAsync(&S.cnt->hr_max_bits, 0, sizeof(unsigned), st);
+    hr_max_kernel<<<148 * 4, 256, 0, st>>>(S, par);
+}
 
 int fp_flood_smem_bytes(int tile_rows) {
     if (tile_rows == 8) return smem_bytes<8>();

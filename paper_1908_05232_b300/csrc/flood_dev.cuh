@@ -106,9 +106,13 @@ struct Side {
     float h, u, v, z;
 };
 
+// Ghost state outside a boundary cell: a wall (code 0) and a discharge breach
+// (code 3, whose inflow is added to the face flux) reflect the normal velocity,
+// a transmissive edge (1) copies the cell, a depth inflow (2) is water at rest
+// at the hydrograph depth.
 __device__ __forceinline__ Side ghost(unsigned char code, Side in, bool normal_x, float h_in) {
     Side g = in;
-    if (code == 0) {
+    if (code == 0 || code == 3) {
         if (normal_x) g.u = -in.u; else g.v = -in.v;
     } else if (code == 2) {
         g.h = h_in; g.u = 0.0f; g.v = 0.0f;
@@ -176,16 +180,34 @@ __device__ __forceinline__ float4 shfl_down_f4(float4 f) {
                        __shfl_down_sync(0xffffffffu, f.z, 1), __shfl_down_sync(0xffffffffu, f.w, 1));
 }
 
+// Inflow of a discharge breach over one step: qd.x = mean unit discharge q
+// (m^2/s) entering through each breach face, qd.y = the momentum it carries,
+// q u_in with u_in = q / h_qin.  Added to the wall flux of a breach face, in
+// the direction into the domain.
+__device__ __forceinline__ void add_discharge(float dir, float2 qd, float &fm, float &fn) {
+    fm = __fadd_rn(fm, dir * qd.x);
+    fn = __fadd_rn(fn, qd.y);
+}
+
 // x face between cells i-1 (L) and i (R) of row j: (mass, normal momentum minus
 // the L pressure, minus the R pressure, tangential momentum); ghosts on the
 // domain's west / east edges; zero past the east edge.  edge (the same for the
 // whole tile) is false when the tile touches no domain edge: no checks then.
-__device__ __forceinline__ float4 x_face(const FpSim &S, float g, float hg, float h_in, Side L, Side R, int i,
-                                         int j, bool edge) {
+__device__ __forceinline__ float4 x_face(const FpSim &S, float g, float hg, float h_in, float2 qd, Side L, Side R,
+                                         int i, int j, bool edge) {
+    float dir = 0.0f;  // +1 / -1: a discharge breach face on the west / east edge
     if (edge) {
         if (i > S.nx) return make_float4(0.f, 0.f, 0.f, 0.f);
-        if (i == 0) L = ghost(S.bc[2][j], R, true, h_in);
-        if (i == S.nx) R = ghost(S.bc[3][j], L, true, h_in);
+        if (i == 0) {
+            const unsigned char c = S.bc[2][j];
+            L = ghost(c, R, true, h_in);
+            if (c == 3) dir = 1.0f;
+        }
+        if (i == S.nx) {
+            const unsigned char c = S.bc[3][j];
+            R = ghost(c, L, true, h_in);
+            if (c == 3) dir = -1.0f;
+        }
     }
     const float zf = fmaxf(L.z, R.z);
     const float hLs = fmaxf(0.0f, (L.h + L.z) - zf);
@@ -193,18 +215,28 @@ __device__ __forceinline__ float4 x_face(const FpSim &S, float g, float hg, floa
     const float pL = press(hg, hLs), pR = press(hg, hRs);
     float fm, fn, ft;
     hll(g, hLs, L.u, L.v, pL, hRs, R.u, R.v, pR, fm, fn, ft);
+    if (dir != 0.0f) add_discharge(dir, qd, fm, fn);
     return make_float4(fm, fn - pL, fn - pR, ft);
 }
 
 // y face between rows j-1 (B) and j (A) of column i: (mass, tangential momentum,
 // normal momentum minus the B pressure, minus the A pressure); ghosts on the
 // domain's south / north edges; zero past the east edge.
-__device__ __forceinline__ float4 y_face(const FpSim &S, float g, float hg, float h_in, Side B, Side A, int i,
-                                         int j, bool edge) {
+__device__ __forceinline__ float4 y_face(const FpSim &S, float g, float hg, float h_in, float2 qd, Side B, Side A,
+                                         int i, int j, bool edge) {
+    float dir = 0.0f;  // +1 / -1: a discharge breach face on the south / north edge
     if (edge) {
         if (i >= S.nx) return make_float4(0.f, 0.f, 0.f, 0.f);
-        if (j == 0) B = ghost(S.bc[0][i], A, false, h_in);
-        if (j == S.ny) A = ghost(S.bc[1][i], B, false, h_in);
+        if (j == 0) {
+            const unsigned char c = S.bc[0][i];
+            B = ghost(c, A, false, h_in);
+            if (c == 3) dir = 1.0f;
+        }
+        if (j == S.ny) {
+            const unsigned char c = S.bc[1][i];
+            A = ghost(c, B, false, h_in);
+            if (c == 3) dir = -1.0f;
+        }
     }
     const float zf = fmaxf(B.z, A.z);
     const float hBs = fmaxf(0.0f, (B.h + B.z) - zf);
@@ -212,6 +244,7 @@ __device__ __forceinline__ float4 y_face(const FpSim &S, float g, float hg, floa
     const float pB = press(hg, hBs), pA = press(hg, hAs);
     float fm, fn, ft;
     hll(g, hBs, B.v, B.u, pB, hAs, A.v, A.u, pA, fm, fn, ft);
+    if (dir != 0.0f) add_discharge(dir, qd, fm, fn);
     return make_float4(fm, ft, fn - pB, fn - pA);
 }
 
@@ -331,6 +364,7 @@ __device__ bool flood_tiles(const FpTmaSet &tm, const FpSim &S, int par, int slo
     __shared__ unsigned char s_mode[kModeChunk];
     __shared__ long long s_dt, s_t, s_step;
     __shared__ float s_hin, s_dtf, s_lx, s_accm;
+    __shared__ float2 s_qd;
     __shared__ unsigned s_smax0;
     __shared__ int s_ok[2], s_accf, s_accn;
     __shared__ int2 s_xy[2];
@@ -349,12 +383,24 @@ __device__ bool flood_tiles(const FpTmaSet &tm, const FpSim &S, int par, int slo
     constexpr int CTL = NT - 32;
     const int nx = S.nx, ny = S.ny, tiles_x = (nx + FP_TX - 1) / FP_TX;
 
-    // the step's clock, the same for every tile
-    const bool inflow_on = S.has_inflow && S.clock[slot].h_in > FP_H_EPS_F;
+    // the step's clock, the same for every tile; an inflow is active while the
+    // depth hydrograph is above h_eps or the discharge hydrograph has not ended
+    const bool inflow_on = (S.has_inflow && S.clock[slot].h_in > FP_H_EPS_F) ||
+                           (S.has_discharge && S.clock[slot].t < S.q_end_ticks);
     if (tid == 0) {
         const FpClock c = S.clock[slot];
         const long long dt = fp_dt_ticks(S, c, c.h_in);
         const float dtf = (float)dt * (1.0f / FP_TICKS_F);
+        // the discharge breach: mean unit discharge over [t, t + dt] from the
+        // exact volume of the hydrograph, and the momentum it carries
+        float2 qd = make_float2(0.0f, 0.0f);
+        if (S.has_discharge && dt > 0) {
+            const double t0 = __ddiv_rn((double)c.t, 1048576.0), t1 = __ddiv_rn((double)(c.t + dt), 1048576.0);
+            const double dV = __dsub_rn(fp_discharge_volume(S, t1), fp_discharge_volume(S, t0));
+            const double q = __ddiv_rn(dV, __dmul_rn(__ddiv_rn((double)dt, 1048576.0), S.q_width));
+            qd = make_float2((float)q, (float)__dmul_rn(q, __ddiv_rn(q, S.h_qin)));
+        }
+        s_qd = qd;
         s_hin = c.h_in;
         s_dt = dt;
         s_dtf = dtf;
@@ -435,6 +481,7 @@ __device__ bool flood_tiles(const FpTmaSet &tm, const FpSim &S, int par, int slo
 
         const float g = S.g, hg = 0.5f * g;
         const float h_in = s_hin;
+        const float2 qd = s_qd;
 
         const int oA = (row + 1) * ROWW + lane + 4, oB = oA + 32;
         const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -454,8 +501,8 @@ __device__ bool flood_tiles(const FpTmaSet &tm, const FpSim &S, int par, int slo
                 wB = c31;
             }
             if (cj < ny) {
-                fwA = x_face(S, g, hg, h_in, wA, cA, iA, cj, edge);
-                fwB = x_face(S, g, hg, h_in, wB, cB, iB, cj, edge);
+                fwA = x_face(S, g, hg, h_in, qd, wA, cA, iA, cj, edge);
+                fwB = x_face(S, g, hg, h_in, qd, wB, cB, iB, cj, edge);
                 if (iA == 0) s_bx[0][row] = fwA.x;
                 if (iA == nx) s_bx[1][row] = fwA.x;
                 if (iB == nx) s_bx[1][row] = fwB.x;
@@ -463,8 +510,8 @@ __device__ bool flood_tiles(const FpTmaSet &tm, const FpSim &S, int par, int slo
             if (cj <= ny) {
                 const Side bA = staged_side(s_h, s_hu, s_hv, s_z, oA - ROWW);
                 const Side bB = staged_side(s_h, s_hu, s_hv, s_z, oB - ROWW);
-                const float4 gA = y_face(S, g, hg, h_in, bA, cA, iA, cj, edge);
-                const float4 gB = y_face(S, g, hg, h_in, bB, cB, iB, cj, edge);
+                const float4 gA = y_face(S, g, hg, h_in, qd, bA, cA, iA, cj, edge);
+                const float4 gB = y_face(S, g, hg, h_in, qd, bB, cB, iB, cj, edge);
                 s_yf[row * FP_TX + lane] = gA;
                 s_yf[row * FP_TX + lane + 32] = gB;
                 if (cj == 0) { s_by[0][lane] = gA.x; s_by[0][lane + 32] = gB.x; }
@@ -480,7 +527,7 @@ __device__ bool flood_tiles(const FpTmaSet &tm, const FpSim &S, int par, int slo
                 float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (j < ny && i <= nx) {
                     const int o = (r + 1) * ROWW + FP_TX + 4;
-                    f = x_face(S, g, hg, h_in, staged_side(s_h, s_hu, s_hv, s_z, o - 1),
+                    f = x_face(S, g, hg, h_in, qd, staged_side(s_h, s_hu, s_hv, s_z, o - 1),
                                staged_side(s_h, s_hu, s_hv, s_z, o), i, j, edge);
                     if (i == nx) s_bx[1][r] = f.x;
                 }
@@ -490,7 +537,7 @@ __device__ bool flood_tiles(const FpTmaSet &tm, const FpSim &S, int par, int slo
                 float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (j <= ny) {
                     const int o = (TY + 1) * ROWW + c + 4;
-                    f = y_face(S, g, hg, h_in, staged_side(s_h, s_hu, s_hv, s_z, o - ROWW),
+                    f = y_face(S, g, hg, h_in, qd, staged_side(s_h, s_hu, s_hv, s_z, o - ROWW),
                                staged_side(s_h, s_hu, s_hv, s_z, o), i, j, edge);
                     if (j == ny && i < nx) s_by[1][c] = f.x;
                 }
@@ -625,6 +672,7 @@ __device__ bool flood_tiles(const FpTmaSet &tm, const FpSim &S, int par, int slo
                     nxt->t = t1;
                     nxt->step = s_step + (dt_ticks > 0 ? 1 : 0);
                     nxt->h_in = (float)fp_hydro_depth(S, t1);
+                    nxt->q_speed = fp_discharge_speed(S, t1);
                     if (S.clock[slot].wet) atomicOr(&nxt->wet, 1);
                     FpClock *old = &S.clock[(slot + 2) & 3];
                     old->smax_bits = 0u;

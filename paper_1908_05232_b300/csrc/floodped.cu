@@ -18,6 +18,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -30,6 +31,7 @@
 namespace {
 
 constexpr int kGraphSteps = 64;
+constexpr int kProfEvents = 6;  // CUDA events per profiled step
 std::string g_create_error;
 
 // 4-connected breadth-first distance over walkable cells from the goal set;
@@ -122,7 +124,7 @@ struct fp_sim {
     int mode = FP_MODE_KERNELS;
     int persist_ctas = 0, persist_smem = 0;
     unsigned *grid_bar = nullptr;
-    std::vector<cudaEvent_t> prof_ev;  // 5 per profiled step
+    std::vector<cudaEvent_t> prof_ev;  // kProfEvents per profiled step
     // surrogate window buffers (allocated by the first fp_surrogate_advance)
     struct Window {
         bool ready = false;
@@ -144,8 +146,9 @@ struct fp_sim {
         long long done = 0;                 // windows advanced (check cadence)
         int suspend = 0;                    // windows left on the plain update
     } win;
-    // steps, hash ms, flood ms, pedestrian chain ms, step ms, cell updates the flood kernel computed
-    double prof[6] = {0, 0, 0, 0, 0, 0};
+    // steps, hash ms, flood ms, pedestrian chain ms, step ms, cell updates the flood kernel computed,
+    // pedestrian kernel ms
+    double prof[7] = {0, 0, 0, 0, 0, 0, 0};
     unsigned *blk_runs = nullptr;  // profiling: flood updates computed per 64 x 8 block
 
     // Every copy of the library is stream-ordered on the simulation's stream and
@@ -260,10 +263,16 @@ static int upload_nav(fp_sim *s) {
 }
 
 static void update_inflow_flag(fp_sim *s) {
-    int f = 0;
+    int f = 0, nd = 0;
     for (int e = 0; e < 4; ++e)
-        for (uint8_t c : s->bc_h[e]) f |= (c == FP_BC_INFLOW);
+        for (uint8_t c : s->bc_h[e]) {
+            f |= (c == FP_BC_INFLOW);
+            nd += (c == FP_BC_DISCHARGE);
+        }
     s->S.has_inflow = f;
+    // the breach width B: the discharge cells' total length, from the FP32 cell side
+    s->S.q_width = (double)nd * (double)s->S.dx;
+    s->S.has_discharge = (nd > 0 && s->S.n_q > 0) ? 1 : 0;
 }
 
 // copy a caller grid (host or device) into a padded device plane
@@ -322,9 +331,10 @@ static int prepare(fp_sim *s) {
     return FP_OK;
 }
 
-// One coupled step.  ev (profiling only): 5 events -- before hash_count (or
-// step_begin), after it, after the flood kernel (stream 2), after the
-// pedestrian chain (stream 1), before the flood kernel (stream 2).  The pedestrian kernel hashes its output records
+// One coupled step.  ev (profiling only): kProfEvents events -- before
+// hash_count (or step_begin), after it, after the flood kernel (stream 2),
+// after the pedestrian chain (stream 1), before the flood kernel (stream 2),
+// before the pedestrian kernel (stream 1).  The pedestrian kernel hashes its output records
 // for the next step, which then opens with step_begin alone.
 static void launch_step(fp_sim *s, int par, int slot, cudaEvent_t *ev = nullptr) {
     const FpSim &S = s->S;
@@ -347,6 +357,7 @@ static void launch_step(fp_sim *s, int par, int slot, cudaEvent_t *ev = nullptr)
     if (ev) cudaEventRecordWithFlags(ev[2], s->stream2, cudaEventRecordExternal);
     fp_launch_scan(S, s->stream, pdl);
     fp_launch_gather(S, s->stream, pdl);
+    if (ev) cudaEventRecordWithFlags(ev[5], s->stream, cudaEventRecordExternal);
     fp_launch_ped_step(S, par, slot, s->ped_lanes, s->stream, pdl, s->hash_ahead);
     if (ev) cudaEventRecordWithFlags(ev[3], s->stream, cudaEventRecordExternal);
     cudaEventRecord(s->ev_join, s->stream2);
@@ -486,8 +497,8 @@ static int step_profiled(fp_sim *s, int n) {
 }
 
 static int step_profiled_kernels(fp_sim *s, int n) {
-    if ((int)s->prof_ev.size() < 5 * n) {
-        for (int k = (int)s->prof_ev.size(); k < 5 * n; ++k) {
+    if ((int)s->prof_ev.size() < kProfEvents * n) {
+        for (int k = (int)s->prof_ev.size(); k < kProfEvents * n; ++k) {
             cudaEvent_t e;
             if (cudaEventCreate(&e) != cudaSuccess) return s->fail(FP_ECUDA, "event create");
             s->prof_ev.push_back(e);
@@ -501,7 +512,7 @@ static int step_profiled_kernels(fp_sim *s, int n) {
     cudaError_t e = cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return s->cuda_fail(e, "profiled capture");
     for (int k = 0; k < n; ++k) {
-        launch_step(s, s->par, s->slot, &s->prof_ev[5 * k]);
+        launch_step(s, s->par, s->slot, &s->prof_ev[kProfEvents * k]);
         s->par ^= 1;
         s->slot = (s->slot + 1) & 3;
     }
@@ -513,12 +524,14 @@ static int step_profiled_kernels(fp_sim *s, int n) {
     if (exec) cudaGraphExecDestroy(exec);
     if (e != cudaSuccess) return s->cuda_fail(e, "profiled steps");
     for (int k = 0; k < n; ++k) {
-        cudaEvent_t *ev = &s->prof_ev[5 * k];
-        float a = 0, b = 0, c = 0, d = 0;
+        cudaEvent_t *ev = &s->prof_ev[kProfEvents * k];
+        float a = 0, b = 0, c = 0, d = 0, f = 0;
         cudaEventElapsedTime(&a, ev[0], ev[1]);
         cudaEventElapsedTime(&b, ev[4], ev[2]);  // the flood kernel, on its own stream
         cudaEventElapsedTime(&c, ev[1], ev[3]);
         cudaEventElapsedTime(&d, ev[0], ev[2]);
+        cudaEventElapsedTime(&f, ev[5], ev[3]);  // the pedestrian kernel
+        s->prof[6] += f;
         s->prof[0] += 1;
         s->prof[1] += a;
         s->prof[2] += b;
@@ -562,6 +575,7 @@ int fp_sim_create(const fp_config *cfg, fp_sim **out) {
     S.nby = (c.ny + S.hk - 1) / S.hk;
     S.nbins = S.nbx * S.nby;
     S.bpc = (int)std::ceil(((double)c.dx * (double)c.dx) / (0.40 * 0.30));
+    S.barrier_polls = FP_BARRIER_POLLS_DEFAULT;
     s->tile_rows = c.tile_rows ? c.tile_rows : 16;
     const size_t pe = s->plane_elems(), n = (size_t)c.nx * c.ny;
     bool ok = true;
@@ -588,9 +602,13 @@ int fp_sim_create(const fp_config *cfg, fp_sim **out) {
     S.arrive = arrive;
     for (int g = 0; g < 3; ++g) ok &= (S.nav[g] = s->dalloc<unsigned char>(n)) != nullptr;
     double *ht = s->dalloc<double>(FP_MAX_HYDRO), *hh = s->dalloc<double>(FP_MAX_HYDRO);
-    ok &= ht && hh;
+    double *qt = s->dalloc<double>(FP_MAX_HYDRO), *qq = s->dalloc<double>(FP_MAX_HYDRO);
+    ok &= ht && hh && qt && qq;
     S.hydro_t = ht;
     S.hydro_h = hh;
+    S.q_t = qt;
+    S.q_Q = qq;
+    S.h_qin = 1.0;
     ok &= (S.clock = s->dalloc<FpClock>(4)) != nullptr;
     ok &= (S.cnt = s->dalloc<FpCounters>(1)) != nullptr;
     const size_t cap = (size_t)std::max(1, c.max_peds);
@@ -683,6 +701,16 @@ int fp_set_terrain(fp_sim *s, const float *z, const float *n0, const uint8_t *wa
     return upload_nav(s);
 }
 
+int fp_set_bed(fp_sim *s, const float *z) {
+    if (!s) return FP_EINVAL;
+    if (!z) return s->fail(FP_EINVAL, "null bed array");
+    cudaError_t e = put_plane(s, s->S.z, z);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return s->cuda_fail(e, "z upload");
+    s->need_prepare = true;
+    return FP_OK;
+}
+
 int fp_set_boundary(fp_sim *s, int32_t edge, const uint8_t *codes) {
     if (!s) return FP_EINVAL;
     if (edge < 0 || edge > 3 || !codes) return s->fail(FP_EINVAL, "bad edge or codes");
@@ -691,12 +719,49 @@ int fp_set_boundary(fp_sim *s, int32_t edge, const uint8_t *codes) {
     cudaError_t e = s->copy(h.data(), codes, len);
     if (e != cudaSuccess) return s->cuda_fail(e, "boundary copy");
     for (uint8_t c : h)
-        if (c > FP_BC_INFLOW) return s->fail(FP_EINVAL, "boundary code out of range");
+        if (c > FP_BC_DISCHARGE) return s->fail(FP_EINVAL, "boundary code out of range");
     s->bc_h[edge] = h;
     e = s->copy(const_cast<unsigned char *>(s->S.bc[edge]), h.data(), len);
     if (e != cudaSuccess) return s->cuda_fail(e, "boundary upload");
     update_inflow_flag(s);
     s->drop_graphs();
+    s->need_prepare = true;  // the clock's inflow speeds
+    return FP_OK;
+}
+
+int fp_set_discharge(fp_sim *s, const double *t, const double *q, int32_t n, double h_inflow) {
+    if (!s) return FP_EINVAL;
+    if (!t || !q || n < 1 || n > FP_MAX_HYDRO) return s->fail(FP_EINVAL, "discharge hydrograph needs 1..64 points");
+    if (!(h_inflow > 0.0) || !std::isfinite(h_inflow)) return s->fail(FP_EINVAL, "inflow depth must be > 0");
+    std::vector<double> th(n), qh(n);
+    cudaError_t e = s->copy(th.data(), t, n * sizeof(double));
+    if (e == cudaSuccess) e = s->copy(qh.data(), q, n * sizeof(double));
+    if (e != cudaSuccess) return s->cuda_fail(e, "discharge copy");
+    for (int k = 0; k < n; ++k) {
+        if (!(qh[k] >= 0.0) || !std::isfinite(qh[k]) || !std::isfinite(th[k]))
+            return s->fail(FP_EINVAL, "discharge values");
+        if (k && !(th[k] > th[k - 1])) return s->fail(FP_EINVAL, "discharge times must increase");
+    }
+    s->copy(const_cast<double *>(s->S.q_t), th.data(), n * sizeof(double));
+    e = s->copy(const_cast<double *>(s->S.q_Q), qh.data(), n * sizeof(double));
+    if (e != cudaSuccess) return s->cuda_fail(e, "discharge upload");
+    s->S.n_q = n;
+    s->S.h_qin = (double)(float)h_inflow;
+    // Q = 0 from the point after the last positive one on (never, if the table ends positive)
+    long long end = 0;
+    if (qh[n - 1] > 0.0) {
+        end = LLONG_MAX;
+    } else {
+        for (int k = n - 2; k >= 0; --k)
+            if (qh[k] > 0.0) {
+                end = (long long)std::ceil(th[k + 1] * 1048576.0);
+                break;
+            }
+    }
+    s->S.q_end_ticks = end;
+    update_inflow_flag(s);
+    s->drop_graphs();
+    s->need_prepare = true;
     return FP_OK;
 }
 
@@ -951,6 +1016,7 @@ int fp_surrogate_advance(fp_sim *s, fp_surrogate *sur, int32_t n_windows, const 
     if (!s) return FP_EINVAL;
     if (!sur || !guard || !st || n_windows < 0) return s->fail(FP_EINVAL, "null surrogate, guard or stats");
     if (s->S.dt_fixed <= 0) return s->fail(FP_EINVAL, "the surrogate window needs a fixed time step (fp_set_fixed_dt)");
+    if (s->S.has_discharge) return s->fail(FP_EINVAL, "the surrogate window does not take a discharge breach");
     if (!(guard->mass_tol >= 0.0f) || !(guard->check_tol >= 0.0f) || !(guard->fix_tol >= 0.0f) ||
         guard->check_every < 0 ||
         guard->suspend_windows < 0)
@@ -1145,6 +1211,21 @@ int fp_set_profiling(fp_sim *s, int32_t on) {
     return FP_OK;
 }
 
+// After a device error: the error word and the transient per-step structures
+// (bin counts, evacuee counts, the hash made ahead) back to their between-step
+// values, so that the handle takes new state and steps again.
+static cudaError_t clear_device_error(fp_sim *s) {
+    const FpSim &S = s->S;
+    s->hashed = false;
+    cudaError_t e = cudaMemsetAsync(S.bin_count, 0, ((size_t)S.nbins + 1) * sizeof(int), s->stream);
+    for (int p = 0; p < 2 && e == cudaSuccess; ++p)
+        e = cudaMemsetAsync(S.occ[p], 0, s->plane_elems() * sizeof(unsigned short), s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(&S.cnt->err, 0, sizeof(unsigned), s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    s->need_prepare = true;
+    return e;
+}
+
 int fp_synchronize(fp_sim *s) {
     if (!s) return FP_EINVAL;
     cudaError_t e = cudaStreamSynchronize(s->stream);
@@ -1152,9 +1233,22 @@ int fp_synchronize(fp_sim *s) {
     unsigned err = 0;
     e = s->copy(&err, &s->S.cnt->err, sizeof(err));
     if (e != cudaSuccess) return s->cuda_fail(e, "error word");
+    if (err == 0) return FP_OK;
+    e = clear_device_error(s);
+    if (e != cudaSuccess) return s->cuda_fail(e, "error reset");
     if (err & FP_ERR_TIMEOUT) return s->fail(FP_ETIMEOUT, "a bounded device wait timed out");
     if (err & FP_ERR_OCC_OVERFLOW) return s->fail(FP_EOVERFLOW, "more than 65535 evacuees in one cell");
     if (err & FP_ERR_NAN) return s->fail(FP_ENAN, "non-finite water state");
+    return s->fail(FP_ECUDA, "device error bits set");
+}
+
+int fp_set_barrier_wait_limit(fp_sim *s, int32_t polls) {
+    if (!s) return FP_EINVAL;
+    if (polls < 0) return s->fail(FP_EINVAL, "negative poll limit");
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return s->cuda_fail(e, "wait limit switch");
+    s->S.barrier_polls = polls;
+    s->drop_graphs();
     return FP_OK;
 }
 
@@ -1223,6 +1317,15 @@ int fp_read_state(fp_sim *s, int32_t which, void *dst, size_t bytes) {
             e = cudaMemcpyAsync(tmp, &S.cnt->mass, 2 * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
             if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
             if (e == cudaSuccess) e = s->copy(dst, tmp, sizeof(tmp));
+            break;
+        }
+        case FP_FIELD_HR_MAX: {
+            if (bytes < sizeof(float)) return s->fail(FP_EINVAL, "destination too small");
+            fp_launch_hr_max(S, s->par, s->stream);
+            unsigned bits = 0;
+            e = cudaMemcpyAsync(&bits, &S.cnt->hr_max_bits, sizeof(bits), cudaMemcpyDeviceToHost, s->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+            if (e == cudaSuccess) e = s->copy(dst, &bits, sizeof(float));
             break;
         }
         case FP_FIELD_PROFILE: {

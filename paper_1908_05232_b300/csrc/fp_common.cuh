@@ -33,6 +33,7 @@
 #define FP_H_DRY_F 1e-3f         // dry pedestrian below 1 mm (m)
 #define FP_NP_CAP 20             // evacuees counted per cell (Section 2.4)
 #define FP_MAX_HYDRO 64
+#define FP_BARRIER_POLLS_DEFAULT (1 << 22)
 
 // error bits
 #define FP_ERR_TIMEOUT 1u
@@ -56,7 +57,7 @@ struct __align__(16) FpClock {
     unsigned int smax_bits; // max over wet cells of max(|u|,|v|) + sqrt(g h), float bits
     int wet;                // sticky: some cell held >= 1 mm
     float h_in;             // inflow hydrograph depth at t, rounded to FP32 (evaluated once per step)
-    int pad;
+    float q_speed;          // wave speed of the water entering through the discharge breach at t (0: none)
 };
 
 struct FpCounters {
@@ -77,6 +78,7 @@ struct FpCounters {
     unsigned int mass_done;           // blocks finished in the mass reduction
     unsigned int cfl_over;            // fixed-dt steps whose CFL number exceeded the limit
     unsigned long long ped_updates;   // sum over steps with dt > 0 of pedestrians advanced
+    unsigned int hr_max_bits;         // largest hazard rating of the last FP_FIELD_HR_MAX read, float bits
 };
 
 struct FpSim {
@@ -112,6 +114,14 @@ struct FpSim {
     unsigned long long *phase_ts;  // optional: global timer at each persistent-kernel phase end
     int phase_ts_steps;            // steps recorded in phase_ts (4 stamps per step + 1)
     long long dt_fixed;            // fixed time step in ticks (0: CFL step)
+    int barrier_polls;             // polls of a persistent-kernel grid barrier before it gives up
+    // discharge breach (Section 3.1): boundary cells coded FP_BC_DISCHARGE take
+    // the hydrograph Q(t) (points q_t, q_Q) spread over their width q_width
+    int has_discharge, n_q;
+    const double *q_t, *q_Q;
+    double q_width;                // breach width B (m): discharge cells x dx
+    double h_qin;                  // depth of the inflowing water (m), an FP32 value
+    long long q_end_ticks;         // Q = 0 from this time on (the breach is a wall)
     const unsigned char *tile_mask;  // per flood tile: 0 = skip (nullptr: every tile runs)
     // Water flags of 64 x 8-cell blocks, by the parity of the state plane they
     // describe: 0 = the block holds h = hu = hv = 0 there (written by the flood
@@ -146,8 +156,54 @@ __device__ __forceinline__ double fp_hydro_depth(const FpSim &S, long long t_tic
     return S.hydro_h[n - 1];
 }
 
+// Discharge hydrograph Q(t) (m^3/s, t in s): piecewise linear between its
+// points, constant outside; FP64 with explicit round-to-nearest operations.
+__device__ __forceinline__ double fp_discharge(const FpSim &S, double t) {
+    const int n = S.n_q;
+    if (n <= 0) return 0.0;
+    if (t <= S.q_t[0]) return S.q_Q[0];
+    if (t >= S.q_t[n - 1]) return S.q_Q[n - 1];
+    for (int k = 0; k + 1 < n; ++k) {
+        const double t1 = S.q_t[k + 1];
+        if (t < t1) {
+            const double t0 = S.q_t[k];
+            const double a = __ddiv_rn(__dsub_rn(t, t0), __dsub_rn(t1, t0));
+            return __dadd_rn(S.q_Q[k], __dmul_rn(__dsub_rn(S.q_Q[k + 1], S.q_Q[k]), a));
+        }
+    }
+    return S.q_Q[n - 1];
+}
+
+// Volume released by the hydrograph from t = 0 to t (m^3): the integral of the
+// piecewise-linear Q, one trapezoid per piece between its breakpoints.
+__device__ __forceinline__ double fp_discharge_volume(const FpSim &S, double t) {
+    if (S.n_q <= 0 || !(t > 0.0)) return 0.0;
+    double v = 0.0, a = 0.0;
+    for (int k = 0; k <= S.n_q; ++k) {
+        double b = k < S.n_q ? S.q_t[k] : t;
+        if (b > t) b = t;
+        if (b > a) {
+            const double qa = fp_discharge(S, a), qb = fp_discharge(S, b);
+            v = __dadd_rn(v, __dmul_rn(__dmul_rn(0.5, __dadd_rn(qa, qb)), __dsub_rn(b, a)));
+            a = b;
+        }
+    }
+    return v;
+}
+
+// Wave speed of the inflowing water at t (ticks): depth h_qin moving at
+// Q(t) / (B h_qin), so Q / (B h_qin) + sqrt(g h_qin) in FP32; 0 when Q(t) = 0.
+__device__ __forceinline__ float fp_discharge_speed(const FpSim &S, long long t_ticks) {
+    if (!S.has_discharge) return 0.0f;
+    const double Q = fp_discharge(S, __ddiv_rn((double)t_ticks, 1048576.0));
+    if (!(Q > 0.0)) return 0.0f;
+    const float u = (float)__ddiv_rn(Q, __dmul_rn(S.q_width, S.h_qin));
+    return __fadd_rn(u, __fsqrt_rn(__fmul_rn(S.g, (float)S.h_qin)));
+}
+
 // The step's dt in ticks: min(1 s, CFL dx / max wave speed, t_end - t), the
-// max over wet cells of the state it reads and the inflow ghost state.
+// max over wet cells of the state it reads, the inflow ghost state and the
+// water entering through a discharge breach.
 // Taken in FP32 with correctly rounded division and square root.
 __device__ __forceinline__ long long fp_dt_ticks(const FpSim &S, const FpClock &c, float h_in) {
     if (S.dt_fixed > 0) {
@@ -160,6 +216,7 @@ __device__ __forceinline__ long long fp_dt_ticks(const FpSim &S, const FpClock &
         const float s = __fsqrt_rn(__fmul_rn(S.g, h_in));
         smax = fmaxf(smax, s);
     }
+    if (c.q_speed > 0.0f) smax = fmaxf(smax, c.q_speed);
     long long ticks = FP_DT_MAX_TICKS;
     if (smax > 0.0f) {
         const float dtf = __fdiv_rn(__fmul_rn(S.cfl, S.dx), smax);
@@ -219,6 +276,7 @@ void fp_launch_flood(const FpSim &S, const void *tma_set, int par, int slot, int
                      bool pdl = false);
 void fp_launch_init_clock(const FpSim &S, int par, int slot, cudaStream_t st);
 void fp_launch_mass(const FpSim &S, int par, cudaStream_t st);
+void fp_launch_hr_max(const FpSim &S, int par, cudaStream_t st);
 int fp_flood_smem_bytes(int tile_rows);
 cudaError_t fp_flood_init_attributes();
 void fp_launch_hash_count(const FpSim &S, int par, cudaStream_t st);

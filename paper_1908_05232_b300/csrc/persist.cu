@@ -20,6 +20,10 @@
 //                --- grid barrier ---
 // The last step does not hash its output, so a launch ends with the same
 // invariants as the per-step kernels (bin counts and evacuee counts zero).
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
 #include "flood_dev.cuh"
 #include "peds_dev.cuh"
 
@@ -37,10 +41,11 @@ struct PersistTma {
 // Grid barrier on one word: every CTA adds 1 except CTA 0, which adds
 // 2^31 - (gridDim.x - 1), so the word's top bit flips exactly when the last
 // CTA has arrived (and the low bits are back to zero); each CTA spins until
-// the top bit differs from the value it saw on arrival.  The spin is bounded;
-// past 2^10 polls it also watches the error word, so that CTAs leave soon
-// after another CTA failed; on timeout the error flag is set and the CTA
-// returns (those still waiting time out in turn).
+// the top bit differs from the value it saw on arrival.  The spin is bounded
+// by S.barrier_polls polls; past 2^10 polls it also watches the error word, so
+// that CTAs leave soon after another CTA failed; on timeout the error flag is
+// set and the CTA returns (those still waiting time out in turn).  No
+// asynchronous copy of the CTA is in flight at a barrier.
 __device__ __forceinline__ bool grid_sync(unsigned *bar, const FpSim &S) {
     __shared__ int s_fail;
     // generic-proxy stores of this phase become visible to later TMA reads
@@ -52,9 +57,14 @@ __device__ __forceinline__ bool grid_sync(unsigned *bar, const FpSim &S) {
         const unsigned old = atomicAdd(bar, add);
         volatile unsigned *vb = bar;
         int fail = 0;
+        const int limit = S.barrier_polls;
         for (int it = 0; ((*vb ^ old) & 0x80000000u) == 0u; ++it) {
+            if (it >= limit) {
+                fail = 1;
+                break;
+            }
             if (it >= (1 << 10)) {
-                if (it >= (1 << 22) || (*(volatile unsigned *)&S.cnt->err & FP_ERR_TIMEOUT) != 0u) {
+                if ((*(volatile unsigned *)&S.cnt->err & FP_ERR_TIMEOUT) != 0u) {
                     fail = 1;
                     break;
                 }
@@ -245,22 +255,30 @@ __global__ void __launch_bounds__(kPT, 2) persistent_kernel(const __grid_constan
 
 }  // namespace
 
+// CTAs of the cooperative launch on the current device for a dynamic shared
+// memory size (0: no cooperative launch); the attribute is set and the count
+// cached per (device, size).
 int fp_persistent_ctas(int smem_dynamic) {
-    static int cached = -1;
-    if (cached >= 0) return cached;
+    struct Entry {
+        int dev, smem, ctas;
+    };
+    static std::mutex mu;
+    static std::vector<Entry> cache;
     int dev = 0, sms = 0, per_sm = 0, coop = 0;
-    cudaGetDevice(&dev);
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    std::lock_guard<std::mutex> lock(mu);
+    for (const Entry &e : cache)
+        if (e.dev == dev && e.smem == smem_dynamic) return e.ctas;
+    int g = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
-    if (!coop) return cached = 0;
-    if (cudaFuncSetAttribute(persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_dynamic) !=
-        cudaSuccess)
-        return cached = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_kernel, kPT, smem_dynamic) != cudaSuccess)
-        return cached = 0;
-    int g = sms * per_sm;
-    if (g > kMaxCTAs) g = kMaxCTAs;
-    return cached = g;
+    if (coop &&
+        cudaFuncSetAttribute(persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_dynamic) ==
+            cudaSuccess &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_kernel, kPT, smem_dynamic) == cudaSuccess)
+        g = std::min(sms * per_sm, kMaxCTAs);
+    cache.push_back(Entry{dev, smem_dynamic, g});
+    return g;
 }
 
 cudaError_t fp_launch_persistent(const FpSim &S, const FpTmaSet tma[2], int par, int slot, int nsteps,

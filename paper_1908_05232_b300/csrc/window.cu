@@ -29,6 +29,7 @@ __global__ void clock_advance_kernel(const __grid_constant__ FpSim S, int slot) 
     nxt->t = t1;
     nxt->step = c.step + (dt > 0 ? 1 : 0);
     nxt->h_in = (float)fp_hydro_depth(S, t1);
+    nxt->q_speed = fp_discharge_speed(S, t1);
     nxt->smax_bits = c.smax_bits;
     nxt->wet = c.wet;
     FpClock *old = &S.clock[(slot + 2) & 3];

@@ -56,7 +56,7 @@ def test_reference_arm_other_ranks_exit(monkeypatch, capsys):
     monkeypatch.setenv("RANK", "1")
 
     class Args:
-        steps, warmup, ref_sample_steps = 1, 0, 1
+        steps, warmup, ref_budget_s = 1, 0, 1.0
     assert bench.run_reference(Args()) == 0
     assert capsys.readouterr().out == ""
 
@@ -68,7 +68,7 @@ def test_launch_count_follows_the_step_structure():
     sys.path.insert(0, ROOT)
     import bench
     import scenarios
-    plain = bench.workload(2)
+    plain = scenarios.config_shopping()
     assert bench.launches_per_chunk(plain, True) == 5 + (bench.CHUNK - 1) * 4
     assert bench.launches_per_chunk(plain, False) == 5 * bench.CHUNK
     barrier = scenarios.shopping_centre(128, 0.5, 100, 10, 1, 600.0, n_barrier=8, n_layers=2)

@@ -363,6 +363,41 @@ def test_shopping_centre_full_size_parity(P, O):
     assert_flood_close(sim, o, atol=1e-4)
 
 
+@pytest.mark.parametrize("shape", [(16, 8, True), (32, 16, False)])
+def test_barrier_midflood_full_size_parity(P, O, shape):
+    """The benchmark workload at full size -- 2048 x 2048 cells, 100,000
+    pedestrians (500 responders mid-deployment), the synthetic mid-flood state --
+    restored the way bench.py restores it (state, bed, pedestrians, clock and
+    barrier progress through the C ABI, on a simulation that already ran) and
+    stepped once in two launch shapes: every cell within 2e-5 m (+2e-6
+    relative) of the oracle, every pedestrian's integers identical and its
+    position within 1e-4 m, the counters identical."""
+    import torch
+    import bench
+    from paper_1908_05232_b300 import _native as N
+    rows, lanes, ahead = shape
+    sc = bench.workload(3)
+    o = O.Oracle(sc)
+    o.step(1)
+    sim = P.from_scenario(sc)
+    N.fp_set_tuning(sim.h, rows, lanes)
+    N.fp_set_hash_ahead(sim.h, ahead)
+    sim.step(70)
+    sim.synchronize()
+    snap = bench.Snapshot(P, N, sim, sc, torch.device("cuda", 0))
+    snap.restore()
+    sim.step(1)
+    sim.synchronize()
+    c = sim.counters()
+    assert c["t_ticks"] == o.t_ticks and c["error_flags"] == 0
+    assert_flood_close(sim, o, atol=2e-5, rtol=2e-6)
+    assert np.array_equal(sim.field(Z).astype(np.float64), o.field("z"))
+    assert_peds_match(sim, o, pos_tol=1e-4, vel_tol=2e-4, dx=sc.dx)
+    oc = o.counters()
+    for k in ("n_exited", "total_bags", "applied_layers", "hist", "wet"):
+        assert c[k] == oc[k], k
+
+
 def test_barrier_config_full_size_properties(P):
     """2048 x 2048 cells, 100,000 pedestrians incl. 500 responders: properties
     that hold at any size (the oracle is too slow here)."""

@@ -1,52 +1,50 @@
 // flood.cu -- per-step kernels of the hydrodynamic update (Section 2.2): the
-// flood kernel (CTAs resident on every SM, each taking a strided list of 64 x TY
-// tiles, see flood_dev.cuh), its batched-ensemble form, the clock
-// initialisation after a state change, and the FP64 water-volume reduction.
+// flood kernel (one warp per run of 64 columns x TY rows, see flood_dev.cuh),
+// its batched-ensemble form, the clock initialisation after a state change,
+// the FP64 water-volume reduction and the largest hazard rating.
 #include "flood_dev.cuh"
 
 namespace {
 using namespace fpdev;
 
-// Batched ensemble: flat tile space, member s owns tiles [tile_off[s], tile_off[s+1]);
-// one tile per CTA.
-__global__ void __launch_bounds__(512, 2) flood_batch_kernel(const FpSim *__restrict__ sims,
-                                                          const FpTmaSet *__restrict__ maps,
-                                                          const int *__restrict__ tile_off, int n, int par,
-                                                          int slot) {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ __align__(8) unsigned long long mbar[2];
-    if (threadIdx.x == 0) {
-        mbar_init(&mbar[0]);
-        mbar_init(&mbar[1]);
-    }
-    __syncthreads();
-    const int t = blockIdx.x;
+constexpr int kFloodWarps = 8;  // warps per CTA of the flood kernels
+
+// Batched ensemble: flat run space (64 x 16 runs), member s owns runs
+// [run_off[s], run_off[s + 1]); one warp per run, each warp folding its own
+// tallies into its member's clock.
+__global__ void __launch_bounds__(32 * kFloodWarps, 2) flood_batch_kernel(const FpSim *__restrict__ sims,
+                                                                       const int *__restrict__ run_off, int n,
+                                                                       int total_runs, int par, int slot) {
+    const int r = blockIdx.x * kFloodWarps + (threadIdx.x >> 5);
+    if (r >= total_runs) return;  // whole warps
     int lo = 0, hi = n - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (tile_off[mid] <= t) lo = mid; else hi = mid - 1;
+        if (run_off[mid] <= r) lo = mid; else hi = mid - 1;
     }
     const FpSim &S = sims[lo];
-    const int ntiles = tile_off[lo + 1] - tile_off[lo];
-    unsigned phase = 0u;
-    flood_tiles<16>(maps[2 * lo + par], S, par, slot, t - tile_off[lo], ntiles, ntiles, smem_raw, mbar, phase, false);
+    const int lr = r - run_off[lo];
+    const FloodStep st = flood_step_consts(S, slot);
+    if (lr == 0 && (threadIdx.x & 31) == 0) flood_clock_advance(S, slot, st);
+    FloodAcc acc = flood_acc_init();
+    flood_run<16>(S, par, st, lr, acc);
+    flood_acc_fold_warp(S, slot, acc);
 }
 
-// One CTA per SM slot, each taking every gridDim.x-th tile.
+// One warp per run of TY rows, each warp reading the step's constants and
+// folding its own tallies (no barrier: warps of a CTA finish apart); the
+// first warp advances the clock.
 template <int TY>
-__global__ void __launch_bounds__(32 * TY, 32 / TY) flood_kernel(const __grid_constant__ FpTmaSet tm,
-                                                                 const __grid_constant__ FpSim S, int par, int slot) {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ __align__(8) unsigned long long mbar[2];
+__global__ void __launch_bounds__(32 * kFloodWarps, 2) flood_kernel(const __grid_constant__ FpSim S, int par,
+                                                                 int slot) {
     fp_pdl_wait();
-    if (threadIdx.x == 0) {
-        mbar_init(&mbar[0]);
-        mbar_init(&mbar[1]);
-    }
-    __syncthreads();
-    const int ntiles = ((S.nx + FP_TX - 1) / FP_TX) * ((S.ny + TY - 1) / TY);
-    unsigned phase = 0u;
-    flood_tiles<TY>(tm, S, par, slot, blockIdx.x, gridDim.x, ntiles, smem_raw, mbar, phase, true);
+    const FloodStep st = flood_step_consts(S, slot);
+    const int w = blockIdx.x * kFloodWarps + (threadIdx.x >> 5);
+    if (w == 0 && threadIdx.x == 0) flood_clock_advance(S, slot, st);
+    const int nruns = ((S.nx + FP_TX - 1) / FP_TX) * ((S.ny + TY - 1) / TY);
+    FloodAcc acc = flood_acc_init();
+    for (int r = w; r < nruns; r += gridDim.x * kFloodWarps) flood_run<TY>(S, par, st, r, acc);
+    flood_acc_fold_warp(S, slot, acc);
 }
 
 // U^0 wave-speed max and wet flag into clock slot `slot` (after a state change).
@@ -139,68 +137,27 @@ void fp_launch_hr_max(const FpSim &S, int par, cudaStream_t st) {
     hr_max_kernel<<<148 * 4, 256, 0, st>>>(S, par);
 }
 
-int fp_flood_smem_bytes(int tile_rows) {
-    if (tile_rows == 8) return smem_bytes<8>();
-    if (tile_rows == 32) return smem_bytes<32>();
-    return smem_bytes<16>();
+void fp_launch_flood_batch(const FpSim *d_sims, const int *d_run_off, int n, int total_runs, int par, int slot,
+                           cudaStream_t st) {
+    const int grid = (total_runs + kFloodWarps - 1) / kFloodWarps;
+    flood_batch_kernel<<<grid, 32 * kFloodWarps, 0, st>>>(d_sims, d_run_off, n, total_runs, par, slot);
 }
 
-void fp_launch_flood_batch(const FpSim *d_sims, const FpTmaSet *d_maps, const int *d_tile_off, int n,
-                           int total_tiles, int par, int slot, cudaStream_t st) {
-    flood_batch_kernel<<<total_tiles, 512, smem_bytes<16>(), st>>>(d_sims, d_maps, d_tile_off, n, par, slot);
-}
+cudaError_t fp_flood_init_attributes() { return cudaSuccess; }
 
-// resident flood CTAs of each tile height on the whole GPU (set with the
-// attributes), and the SM count
-static int g_flood_ctas[3] = {0, 0, 0};
-static int g_sms = 0;
-
+// One warp per run: the block scheduler hands runs to SMs as warps finish
+// (runs cost very different amounts: dry groups are skipped).
 template <int TY>
-static cudaError_t init_flood_t(int sms) {
-    cudaError_t e = cudaFuncSetAttribute(flood_kernel<TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<TY>());
-    int per_sm = 0;
-    if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, flood_kernel<TY>, 32 * TY, smem_bytes<TY>());
-    g_flood_ctas[TY == 8 ? 0 : TY == 16 ? 1 : 2] = (per_sm > 0 ? per_sm : 1) * sms;
-    return e;
+static void launch_flood_t(const FpSim &S, int par, int slot, cudaStream_t st, bool pdl) {
+    const int nruns = ((S.nx + FP_TX - 1) / FP_TX) * ((S.ny + TY - 1) / TY);
+    const int grid = (nruns + kFloodWarps - 1) / kFloodWarps;
+    fp_launch(pdl, flood_kernel<TY>, dim3(grid), dim3(32 * kFloodWarps), 0, st, S, par, slot);
 }
 
-cudaError_t fp_flood_init_attributes() {
-    int dev = 0, sms = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    g_sms = sms;
-    if (e == cudaSuccess) e = init_flood_t<8>(sms);
-    if (e == cudaSuccess) e = init_flood_t<16>(sms);
-    if (e == cudaSuccess) e = init_flood_t<32>(sms);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(flood_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<16>());
-    return e;
-}
-
-template <int TY>
-static void launch_flood_t(const FpSim &S, const FpTmaSet &tm, int par, int slot, cudaStream_t st, bool pdl) {
-    constexpr int smem = smem_bytes<TY>();
-    const int ntiles = ((S.nx + FP_TX - 1) / FP_TX) * ((S.ny + TY - 1) / TY);
-    const int resident = g_flood_ctas[TY == 8 ? 0 : TY == 16 ? 1 : 2];
-    int grid = resident > 0 && resident < ntiles ? resident : ntiles;
-    // When every tile fits in one resident wave, at most half the resident CTAs
-    // (never fewer than one per SM), each taking up to two tiles in turn: the
-    // rest of each SM stays free for the pedestrian kernels that run beside
-    // this one (a 512 x 512 step: 3 % faster; larger grids keep every CTA).
-    if (resident > 0 && ntiles <= resident) {
-        const int half = resident / 2 > g_sms ? resident / 2 : g_sms;
-        if (grid > half) grid = half;
-    }
-    fp_launch(pdl, flood_kernel<TY>, dim3(grid), dim3(32 * TY), smem, st, tm, S, par, slot);
-}
-
-void fp_launch_flood(const FpSim &S, const void *tma_set, int par, int slot, int tile_rows, cudaStream_t st,
-                     bool pdl) {
-    const FpTmaSet &tm = *static_cast<const FpTmaSet *>(tma_set);
-    if (tile_rows == 8) launch_flood_t<8>(S, tm, par, slot, st, pdl);
-    else if (tile_rows == 32) launch_flood_t<32>(S, tm, par, slot, st, pdl);
-    else launch_flood_t<16>(S, tm, par, slot, st, pdl);
+void fp_launch_flood(const FpSim &S, int par, int slot, int tile_rows, cudaStream_t st, bool pdl) {
+    if (tile_rows == 8) launch_flood_t<8>(S, par, slot, st, pdl);
+    else if (tile_rows == 32) launch_flood_t<32>(S, par, slot, st, pdl);
+    else launch_flood_t<16>(S, par, slot, st, pdl);
 }
 
 void fp_launch_init_clock(const FpSim &S, int par, int slot, cudaStream_t st) {

@@ -2,8 +2,8 @@
 //
 // Owns the device memory of one simulation, builds the navigation fields
 // (Section 2.1: navigation agents pointing pedestrians toward the exit, the
-// sandbag storage and the barrier) with a breadth-first search, encodes the
-// TMA descriptors of the flood kernel, and enqueues coupled steps.  A step is
+// sandbag storage and the barrier) with a breadth-first search, and enqueues
+// coupled steps.  A step is
 // five kernels on two streams:
 //     hash_count --+--> scan -> gather -> ped_step (stream 1) --+--> next step
 //                  +--> flood (stream 2)                      --+
@@ -77,19 +77,6 @@ void build_nav(int nx, int ny, const std::vector<uint8_t> &walk, const std::vect
     }
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    if (!fn) {
-        cudaDriverEntryPointQueryResult q;
-        void *p = nullptr;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-    }
-    return fn;
-}
-
 }  // namespace
 
 struct fp_sim {
@@ -109,8 +96,6 @@ struct fp_sim {
     long long pend_t = 0, pend_step = 0;
     int tile_rows = 16;
     int ped_lanes = 8;   // lanes per pedestrian in the per-step kernel (4, 8, 16)
-    FpTmaSet tma[2];
-    FpTmaSet tma16[2];  // 16-row tiles, for the persistent kernel
     // graphs of 64 steps by starting clock slot, whose first step hashes the
     // records of B itself ([0]) or finds them hashed ([1])
     cudaGraphExec_t graphs[2][4] = {};
@@ -122,7 +107,7 @@ struct fp_sim {
     uint4 *read_buf = nullptr;
     bool profiling = false;
     int mode = FP_MODE_KERNELS;
-    int persist_ctas = 0, persist_smem = 0;
+    int persist_ctas = 0;
     unsigned *grid_bar = nullptr;
     std::vector<cudaEvent_t> prof_ev;  // kProfEvents per profiled step
     // surrogate window buffers (allocated by the first fp_surrogate_advance)
@@ -140,7 +125,6 @@ struct fp_sim {
         unsigned *maxdiff = nullptr;
         void *x16 = nullptr;                // net input: tiles of 266 x 266 pixels, 16 BF16 channels
         float *dU = nullptr;                // net output [tiles][256][256][3]
-        FpTmaSet tma[2];
         cudaStream_t net_stream = nullptr;  // the net runs here, beside the window's pedestrian steps
         cudaEvent_t ev_start = nullptr, ev_input = nullptr, ev_net = nullptr;
         long long done = 0;                 // windows advanced (check cadence)
@@ -192,46 +176,6 @@ struct fp_sim {
         return e;
     }
 };
-
-static int encode_tma_rows(fp_sim *s, int rows, FpTmaSet out[2], const FpSim *planes = nullptr) {
-    auto enc = get_encode();
-    if (!enc) return s->fail(FP_ECUDA, "cuTensorMapEncodeTiled entry point unavailable");
-    const FpSim &S = planes ? *planes : s->S;
-    cuuint64_t dims[2] = {(cuuint64_t)S.px, (cuuint64_t)(S.ny + 2)};
-    cuuint64_t strides[1] = {(cuuint64_t)S.px * 4};
-    cuuint32_t box[2] = {(cuuint32_t)(FP_TX + 8), (cuuint32_t)(rows + 2)};
-    cuuint32_t es[2] = {1, 1};
-    // n0 and the evacuee counts: the tile's rows only; the uint16 box starts
-    // at the tile's first cell - 4 too (16-byte aligned), the pitch px is a
-    // multiple of 8 cells
-    cuuint32_t box_c[2] = {(cuuint32_t)(FP_TX + 8), (cuuint32_t)rows};
-    cuuint64_t strides16[1] = {(cuuint64_t)S.px * 2};
-    for (int p = 0; p < 2; ++p) {
-        float *ptrs[4] = {S.h[p], S.hu[p], S.hv[p], S.z};
-        CUtensorMap *maps[4] = {&out[p].h, &out[p].hu, &out[p].hv, &out[p].z};
-        for (int k = 0; k < 4; ++k) {
-            CUresult r = enc(maps[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, ptrs[k], dims, strides, box, es,
-                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-            if (r != CUDA_SUCCESS) return s->fail(FP_ECUDA, "cuTensorMapEncodeTiled failed");
-        }
-        CUresult r = enc(&out[p].n0, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(S.n0), dims, strides,
-                         box_c, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (r == CUDA_SUCCESS)
-            r = enc(&out[p].occ, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, S.occ[p], dims, strides16, box_c, es,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (r != CUDA_SUCCESS) return s->fail(FP_ECUDA, "cuTensorMapEncodeTiled failed");
-    }
-    return FP_OK;
-}
-
-static int encode_tma(fp_sim *s) {
-    int rc = encode_tma_rows(s, s->tile_rows, s->tma);
-    if (rc == FP_OK) rc = encode_tma_rows(s, 16, s->tma16);
-    return rc;
-}
 
 static int upload_nav(fp_sim *s) {
     const int nx = s->S.nx, ny = s->S.ny;
@@ -353,7 +297,7 @@ static void launch_step(fp_sim *s, int par, int slot, cudaEvent_t *ev = nullptr)
     // edges (not in profiling mode, whose events sit between the kernels)
     const bool pdl = ev == nullptr;
     if (ev) cudaEventRecordWithFlags(ev[4], s->stream2, cudaEventRecordExternal);
-    fp_launch_flood(S, &s->tma[par], par, slot, s->tile_rows, s->stream2);
+    fp_launch_flood(S, par, slot, s->tile_rows, s->stream2);
     if (ev) cudaEventRecordWithFlags(ev[2], s->stream2, cudaEventRecordExternal);
     fp_launch_scan(S, s->stream, pdl);
     fp_launch_gather(S, s->stream, pdl);
@@ -423,8 +367,6 @@ static int ensure_window(fp_sim *s) {
         F.hv[p] = W.fb[p][2];
         F.blk_wet[p] = nullptr;
     }
-    const int rc = encode_tma_rows(s, s->tile_rows, W.tma, &F);
-    if (rc != FP_OK) return rc;
     if (cudaStreamCreateWithFlags(&W.net_stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&W.ev_start, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&W.ev_input, cudaEventDisableTiming) != cudaSuccess ||
@@ -447,8 +389,7 @@ static int step_profiled_persistent(fp_sim *s, int n) {
         FpSim S = s->S;
         S.phase_ts = ts;
         S.phase_ts_steps = m;
-        cudaError_t e = fp_launch_persistent(S, s->tma16, s->par, s->slot, m, s->grid_bar, s->persist_ctas,
-                                             s->persist_smem, s->stream);
+        cudaError_t e = fp_launch_persistent(S, s->par, s->slot, m, s->grid_bar, s->persist_ctas, s->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
         std::vector<unsigned long long> h(cnt);
         if (e == cudaSuccess) e = s->copy(h.data(), ts, cnt * sizeof(unsigned long long));
@@ -643,14 +584,12 @@ int fp_sim_create(const fp_config *cfg, fp_sim **out) {
     cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming);
     cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming);
     int rc = upload_nav(s);
-    if (rc == FP_OK) rc = encode_tma(s);
     if (rc == FP_OK) {
         cudaError_t ea = fp_flood_init_attributes();
         if (ea != cudaSuccess) rc = s->cuda_fail(ea, "flood kernel attributes");
     }
     if (rc == FP_OK) {
-        s->persist_smem = fp_flood_smem_bytes(16);
-        s->persist_ctas = fp_persistent_ctas(s->persist_smem);
+        s->persist_ctas = fp_persistent_ctas();
         cudaGetLastError();
         s->mode = FP_MODE_KERNELS;
     }
@@ -915,8 +854,7 @@ int fp_step(fp_sim *s, int32_t n_steps) {
         int left = n_steps;
         while (left > 0) {
             const int n = left < 256 ? left : 256;
-            cudaError_t e = fp_launch_persistent(s->S, s->tma16, s->par, s->slot, n, s->grid_bar, s->persist_ctas,
-                                                 s->persist_smem, s->stream);
+            cudaError_t e = fp_launch_persistent(s->S, s->par, s->slot, n, s->grid_bar, s->persist_ctas, s->stream);
             if (e != cudaSuccess) return s->cuda_fail(e, "persistent launch");
             if (n & 1) s->par ^= 1;
             s->slot = (s->slot + n) & 3;
@@ -966,11 +904,7 @@ int fp_set_tuning(fp_sim *s, int32_t tile_rows, int32_t ped_lanes) {
         return s->fail(FP_EINVAL, "tile_rows must be 8, 16 or 32 and ped_lanes 4, 8 or 16");
     cudaError_t e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return s->cuda_fail(e, "tuning switch");
-    if (tile_rows != s->tile_rows) {
-        s->tile_rows = tile_rows;
-        const int rc = encode_tma_rows(s, tile_rows, s->tma);
-        if (rc != FP_OK) return rc;
-    }
+    s->tile_rows = tile_rows;
     s->ped_lanes = ped_lanes;
     s->drop_graphs();
     return FP_OK;
@@ -1128,7 +1062,6 @@ int fp_surrogate_advance(fp_sim *s, fp_surrogate *sur, int32_t n_windows, const 
                     for (int fy = ya / s->tile_rows; fy <= (yb - 1) / s->tile_rows && fy < fty; ++fy)
                         for (int fx = xa / FP_TX; fx <= (xb - 1) / FP_TX && fx < ftx; ++fx) mask[fy * ftx + fx] = 1;
                 }
-                mask[0] = 1;  // tile (0, 0) advances the fallback clock
                 e = s->copy(W.mask, mask.data(), W.ftiles);
                 if (e != cudaSuccess) return s->cuda_fail(e, "fallback mask");
                 dmask = W.mask;
@@ -1151,7 +1084,7 @@ int fp_surrogate_advance(fp_sim *s, fp_surrogate *sur, int32_t n_windows, const 
             for (int k = 0; k < FP_SUR_WINDOW; ++k) {
                 cudaMemsetAsync(W.fb_occ, 0, s->plane_elems() * sizeof(unsigned short), s->stream);
                 if (S.coupling) fp_launch_sur_occupancy(F, W.fb_occ, s->stream);
-                fp_launch_flood(F, &W.tma[p], p, sl, s->tile_rows, s->stream);
+                fp_launch_flood(F, p, sl, s->tile_rows, s->stream);
                 p ^= 1;
                 sl = (sl + 1) & 3;
             }
@@ -1345,12 +1278,10 @@ int fp_read_state(fp_sim *s, int32_t which, void *dst, size_t bytes) {
 
 struct fp_batch {
     std::vector<fp_sim *> sims;
-    int n = 0, total_tiles = 0, total_rec = 0, max_scan_tiles = 0;
+    int n = 0, total_runs = 0, total_rec = 0, max_scan_tiles = 0;
     FpSim *d_sims = nullptr;
-    FpTmaSet *d_maps = nullptr;
-    int *d_tile_off = nullptr, *d_rec_off = nullptr;
+    int *d_run_off = nullptr, *d_rec_off = nullptr;  // flood runs (64 x 16) and record slots of each member
     std::vector<FpSim> h_sims;
-    std::vector<FpTmaSet> h_maps;
     cudaStream_t stream = nullptr, stream2 = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaGraphExec_t graphs[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -1361,7 +1292,7 @@ static void batch_launch_step(fp_batch *b, int par, int slot) {
     fp_launch_batch_peds(b->d_sims, b->d_rec_off, b->n, b->total_rec, b->max_scan_tiles, par, slot, b->stream,
                          b->stream2, b->ev_fork, true);
     cudaStreamWaitEvent(b->stream2, b->ev_fork, 0);
-    fp_launch_flood_batch(b->d_sims, b->d_maps, b->d_tile_off, b->n, b->total_tiles, par, slot, b->stream);
+    fp_launch_flood_batch(b->d_sims, b->d_run_off, b->n, b->total_runs, par, slot, b->stream);
     fp_launch_batch_peds(b->d_sims, b->d_rec_off, b->n, b->total_rec, b->max_scan_tiles, par, slot, b->stream,
                          b->stream2, b->ev_fork, false);
     cudaEventRecord(b->ev_join, b->stream2);
@@ -1378,18 +1309,18 @@ int fp_batch_create(fp_sim *const *sims, int32_t n, fp_batch **out) {
     *out = nullptr;
     fp_batch *b = new fp_batch();
     b->n = n;
-    std::vector<int> tile_off(n + 1, 0), rec_off(n + 1, 0);
+    std::vector<int> run_off(n + 1, 0), rec_off(n + 1, 0);
     for (int k = 0; k < n; ++k) {
         fp_sim *m = sims[k];
         if (!m) { delete b; g_create_error = "fp_batch_create: null member"; return FP_EINVAL; }
         b->sims.push_back(m);
-        const int tiles = ((m->S.nx + FP_TX - 1) / FP_TX) * ((m->S.ny + 15) / 16);
-        tile_off[k + 1] = tile_off[k] + tiles;
+        const int runs = ((m->S.nx + FP_TX - 1) / FP_TX) * ((m->S.ny + 15) / 16);
+        run_off[k + 1] = run_off[k] + runs;
         const int cap = std::max(1, m->S.cap);
         rec_off[k + 1] = rec_off[k] + ((cap + 255) / 256) * 256;
         b->max_scan_tiles = std::max(b->max_scan_tiles, fp_scan_tiles(m->S.nbins));
     }
-    b->total_tiles = tile_off[n];
+    b->total_runs = run_off[n];
     b->total_rec = rec_off[n];
     auto alloc = [&](size_t bytes) -> void * {
         void *p = nullptr;
@@ -1398,18 +1329,16 @@ int fp_batch_create(fp_sim *const *sims, int32_t n, fp_batch **out) {
         return p;
     };
     b->d_sims = static_cast<FpSim *>(alloc(sizeof(FpSim) * n));
-    b->d_maps = static_cast<FpTmaSet *>(alloc(sizeof(FpTmaSet) * 2 * n));
-    b->d_tile_off = static_cast<int *>(alloc(sizeof(int) * (n + 1)));
+    b->d_run_off = static_cast<int *>(alloc(sizeof(int) * (n + 1)));
     b->d_rec_off = static_cast<int *>(alloc(sizeof(int) * (n + 1)));
-    if (!b->d_sims || !b->d_maps || !b->d_tile_off || !b->d_rec_off) {
+    if (!b->d_sims || !b->d_run_off || !b->d_rec_off) {
         fp_batch_destroy(b);
         g_create_error = "fp_batch_create: device allocation failed";
         return FP_ENOMEM;
     }
-    cudaMemcpy(b->d_tile_off, tile_off.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice);
+    cudaMemcpy(b->d_run_off, run_off.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice);
     cudaMemcpy(b->d_rec_off, rec_off.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice);
     b->h_sims.resize(n);
-    b->h_maps.resize(2 * n);
     cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
     cudaStreamCreateWithFlags(&b->stream2, cudaStreamNonBlocking);
     cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
@@ -1443,14 +1372,9 @@ int fp_batch_step(fp_batch *b, int32_t n_steps) {
         }
         b->h_sims[k] = m->S;
         b->h_sims[k].blk_runs = nullptr;
-        b->h_maps[2 * k] = m->tma16[0];
-        b->h_maps[2 * k + 1] = m->tma16[1];
     }
     cudaError_t e = cudaMemcpyAsync(b->d_sims, b->h_sims.data(), sizeof(FpSim) * b->n, cudaMemcpyHostToDevice,
                                     b->stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(b->d_maps, b->h_maps.data(), sizeof(FpTmaSet) * 2 * b->n, cudaMemcpyHostToDevice,
-                            b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);  // host vectors may change at the next call
     if (e != cudaSuccess) {
         g_create_error = "fp_batch_step: descriptor upload failed";

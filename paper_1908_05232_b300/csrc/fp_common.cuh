@@ -265,19 +265,11 @@ __device__ __forceinline__ void fp_philox4x64(unsigned long long c[4], unsigned 
 
 __device__ __forceinline__ void fp_set_err(const FpSim &S, unsigned int bit) { atomicOr(&S.cnt->err, bit); }
 
-// TMA descriptors of the four staged planes for one step parity
-struct FpTmaSet {
-    CUtensorMap h, hu, hv, z;  // FP32 planes, box (FP_TX + 8) x (rows + 2): a tile and its one-cell halo
-    CUtensorMap n0, occ;       // FP32 / uint16 planes, box (FP_TX + 8) x rows
-};
-
 // launchers (defined in flood.cu / peds.cu)
-void fp_launch_flood(const FpSim &S, const void *tma_set, int par, int slot, int tile_rows, cudaStream_t st,
-                     bool pdl = false);
+void fp_launch_flood(const FpSim &S, int par, int slot, int tile_rows, cudaStream_t st, bool pdl = false);
 void fp_launch_init_clock(const FpSim &S, int par, int slot, cudaStream_t st);
 void fp_launch_mass(const FpSim &S, int par, cudaStream_t st);
 void fp_launch_hr_max(const FpSim &S, int par, cudaStream_t st);
-int fp_flood_smem_bytes(int tile_rows);
 cudaError_t fp_flood_init_attributes();
 void fp_launch_hash_count(const FpSim &S, int par, cudaStream_t st);
 void fp_launch_scan(const FpSim &S, cudaStream_t st, bool pdl = false);
@@ -290,14 +282,14 @@ void fp_launch_clear_peds(const FpSim &S, cudaStream_t st);
 void fp_launch_read_peds(const FpSim &S, uint4 *out, int n_total, cudaStream_t st);
 int fp_scan_tiles(int nbins);
 void fp_note_error(const char *msg);  // message for fp_last_error(NULL)
-int fp_persistent_ctas(int smem_dynamic);
+int fp_persistent_ctas();
 void fp_launch_batch_peds(const FpSim *d_sims, const int *d_rec_off, int n, int total_rec, int max_scan_tiles,
                           int par, int slot, cudaStream_t st_hash, cudaStream_t st_chain, cudaEvent_t fork,
                           bool hash_part);
-void fp_launch_flood_batch(const FpSim *d_sims, const FpTmaSet *d_maps, const int *d_tile_off, int n,
-                           int total_tiles, int par, int slot, cudaStream_t st);
-cudaError_t fp_launch_persistent(const FpSim &S, const FpTmaSet tma[2], int par, int slot, int nsteps,
-                                 unsigned *bar, int ctas, int smem_dynamic, cudaStream_t st);
+void fp_launch_flood_batch(const FpSim *d_sims, const int *d_run_off, int n, int total_runs, int par, int slot,
+                           cudaStream_t st);
+cudaError_t fp_launch_persistent(const FpSim &S, int par, int slot, int nsteps, unsigned *bar, int ctas,
+                                 cudaStream_t st);
 
 // Programmatic dependent launch: the kernel may be scheduled while the previous
 // kernel of its stream is finishing; it must execute fp_pdl_wait() before it

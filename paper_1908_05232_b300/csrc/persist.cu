@@ -12,9 +12,9 @@
 //                    memory (bin start = chunk prefix + local start) and
 //                    gathers its share of B into bin order A;
 //                --- grid barrier ---
-//                FP  flood tiles (flood_dev.cuh) from the first CTA up and
+//                FP  flood runs (flood_dev.cuh), one warp per run, then
 //                    pedestrian chunks of eight lanes per pedestrian
-//                    (peds_dev.cuh) from the last CTA down, concurrently; each
+//                    (peds_dev.cuh) taken by whichever CTAs are free; each
 //                    output record is hashed at once for the next step into
 //                    the other parity's evacuee-count plane;
 //                --- grid barrier ---
@@ -34,9 +34,6 @@ constexpr int kPT = 512;       // threads per CTA = 32 x TY with TY = 16
 constexpr int kPTY = 16;
 constexpr int kMaxCTAs = 2048;
 
-struct PersistTma {
-    FpTmaSet p[2];
-};
 
 // Grid barrier on one word: every CTA adds 1 except CTA 0, which adds
 // 2^31 - (gridDim.x - 1), so the word's top bit flips exactly when the last
@@ -45,11 +42,9 @@ struct PersistTma {
 // by S.barrier_polls polls; past 2^10 polls it also watches the error word, so
 // that CTAs leave soon after another CTA failed; on timeout the error flag is
 // set and the CTA returns (those still waiting time out in turn).  No
-// asynchronous copy of the CTA is in flight at a barrier.
+// asynchronous copy is in flight at a barrier: the kernel makes none.
 __device__ __forceinline__ bool grid_sync(unsigned *bar, const FpSim &S) {
     __shared__ int s_fail;
-    // generic-proxy stores of this phase become visible to later TMA reads
-    asm volatile("fence.proxy.async.global;" ::: "memory");
     __syncthreads();
     if (threadIdx.x == 0) {
         const unsigned add = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1u) : 1u;
@@ -71,8 +66,7 @@ __device__ __forceinline__ bool grid_sync(unsigned *bar, const FpSim &S) {
                 __nanosleep(64);
             }
         }
-        __threadfence();
-        asm volatile("fence.proxy.async.global;" ::: "memory");
+        __threadfence();  // the other CTAs' writes of the phase are seen by this CTA's loads after it
         if (fail) fp_set_err(S, FP_ERR_TIMEOUT);
         s_fail = fail;
     }
@@ -123,24 +117,17 @@ struct ChunkLookup {
     __device__ int operator()(int key) const { return base[key / chunk] + local[key]; }
 };
 
-__global__ void __launch_bounds__(kPT, 2) persistent_kernel(const __grid_constant__ PersistTma tm,
-                                                            const __grid_constant__ FpSim S, int par0, int slot0,
+__global__ void __launch_bounds__(kPT, 1) persistent_kernel(const __grid_constant__ FpSim S, int par0, int slot0,
                                                             int nsteps, unsigned *bar) {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ __align__(8) unsigned long long mbar[2];
     __shared__ int s_base[kMaxCTAs];
+    __shared__ FloodStep s_fst;
     __shared__ StepCtl s_ctl;
     __shared__ int s_pcx;
     FpCounters *C = S.cnt;
     const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x;
     const int nbin1 = S.nbins + 1;
     const int chunk = (nbin1 + G - 1) / G;
-    const int ntiles = ((S.nx + FP_TX - 1) / FP_TX) * ((S.ny + kPTY - 1) / kPTY);
-    if (tid == 0) {
-        mbar_init(&mbar[0]);
-        mbar_init(&mbar[1]);
-    }
-    unsigned phase = 0u;
+    const int nruns = ((S.nx + FP_TX - 1) / FP_TX) * ((S.ny + kPTY - 1) / kPTY);
 
     // H: hash the current records of B
     {
@@ -221,21 +208,30 @@ __global__ void __launch_bounds__(kPT, 2) persistent_kernel(const __grid_constan
         }
         if (!grid_sync(bar, S)) return;
         stamp(S, 4 * s + 2);
-        // FP: flood tiles (a strided list per CTA), then pedestrian chunks taken
-        // from a ticket counter by whichever CTAs are free (those whose tiles
-        // were skipped as dry come first) -- both read the state at step n;
-        // pedestrian outputs are hashed for the next step (not after the last),
-        // into the other parity's evacuee-count plane.
+        // FP: flood runs (warp w of CTA c takes runs c * 16 + w, + 16 G, ...),
+        // then pedestrian chunks taken from a ticket counter by whichever CTAs
+        // are free (those whose runs were skipped as dry come first) -- both
+        // read the state at step n; pedestrian outputs are hashed for the next
+        // step (not after the last), into the other parity's evacuee-count plane.
         if (tid == 0) {
             load_step_ctl(S, slot, nA, s_ctl);
+            const FloodStep fst = flood_step_consts(S, slot);
+            s_fst = fst;
             if (cta == 0) {
                 C->nA = nA;
                 C->nB = nA;
                 if (s_ctl.dt_ticks > 0) C->ped_updates += (unsigned long long)nA;
+                flood_clock_advance(S, slot, fst);
             }
         }
-        if (!flood_tiles<kPTY>(tm.p[par], S, par, slot, cta, G, ntiles, smem_raw, mbar, phase, true)) return;
         __syncthreads();
+        {
+            const FloodStep fst = s_fst;
+            FloodAcc acc = flood_acc_init();
+            for (int r = cta * (kPT / 32) + (tid >> 5); r < nruns; r += G * (kPT / 32))
+                flood_run<kPTY>(S, par, fst, r, acc);
+            flood_acc_fold_cta<kPT / 32>(S, slot, acc);
+        }
         const StepCtl ctl = s_ctl;
         const bool hash_next = s + 1 < nsteps;
         constexpr int kPedPerCTA = kPT / kGroup;
@@ -255,12 +251,11 @@ __global__ void __launch_bounds__(kPT, 2) persistent_kernel(const __grid_constan
 
 }  // namespace
 
-// CTAs of the cooperative launch on the current device for a dynamic shared
-// memory size (0: no cooperative launch); the attribute is set and the count
-// cached per (device, size).
-int fp_persistent_ctas(int smem_dynamic) {
+// CTAs of the cooperative launch on the current device (0: no cooperative
+// launch), cached per device.
+int fp_persistent_ctas() {
     struct Entry {
-        int dev, smem, ctas;
+        int dev, ctas;
     };
     static std::mutex mu;
     static std::vector<Entry> cache;
@@ -268,30 +263,23 @@ int fp_persistent_ctas(int smem_dynamic) {
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     std::lock_guard<std::mutex> lock(mu);
     for (const Entry &e : cache)
-        if (e.dev == dev && e.smem == smem_dynamic) return e.ctas;
+        if (e.dev == dev) return e.ctas;
     int g = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
-    if (coop &&
-        cudaFuncSetAttribute(persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_dynamic) ==
-            cudaSuccess &&
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_kernel, kPT, smem_dynamic) == cudaSuccess)
+    if (coop && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_kernel, kPT, 0) == cudaSuccess)
         g = std::min(sms * per_sm, kMaxCTAs);
-    cache.push_back(Entry{dev, smem_dynamic, g});
+    cache.push_back(Entry{dev, g});
     return g;
 }
 
-cudaError_t fp_launch_persistent(const FpSim &S, const FpTmaSet tma[2], int par, int slot, int nsteps,
-                                 unsigned *bar, int ctas, int smem_dynamic, cudaStream_t st) {
-    PersistTma tm;
-    tm.p[0] = tma[0];
-    tm.p[1] = tma[1];
+cudaError_t fp_launch_persistent(const FpSim &S, int par, int slot, int nsteps, unsigned *bar, int ctas,
+                                 cudaStream_t st) {
     FpSim s = S;
-    void *args[] = {(void *)&tm, (void *)&s, (void *)&par, (void *)&slot, (void *)&nsteps, (void *)&bar};
+    void *args[] = {(void *)&s, (void *)&par, (void *)&slot, (void *)&nsteps, (void *)&bar};
     // the barrier word and the pedestrian tickets start at zero (a barrier that
     // timed out leaves its word partly counted)
     const cudaError_t e = cudaMemsetAsync(bar, 0, 4 * sizeof(unsigned), st);
     if (e != cudaSuccess) return e;
-    return cudaLaunchCooperativeKernel((const void *)persistent_kernel, dim3(ctas), dim3(kPT), args,
-                                       (size_t)smem_dynamic, st);
+    return cudaLaunchCooperativeKernel((const void *)persistent_kernel, dim3(ctas), dim3(kPT), args, 0, st);
 }

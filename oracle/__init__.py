@@ -61,6 +61,9 @@ def lib():
         _lib.or_discharge_volume.argtypes = [ctypes.c_void_p, ctypes.c_double]
         _lib.or_discharge_width.restype = ctypes.c_double
         _lib.or_discharge_width.argtypes = [ctypes.c_void_p]
+        _lib.or_guard_residual.restype = ctypes.c_double
+        _lib.or_guard_residual.argtypes = [ctypes.c_void_p] + [ctypes.c_void_p] * 7 + [ctypes.c_int32] * 4 + \
+            [ctypes.c_int64] * 2
         _lib.or_max_hr.restype = ctypes.c_float
         _lib.or_max_hr.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
         _lib.or_hydro_depth.restype = ctypes.c_double
@@ -239,6 +242,14 @@ class Oracle:
 
     def discharge_width(self) -> float:
         return float(lib().or_discharge_width(ctypes.byref(self.P)))
+
+    def guard_residual(self, start, end, x0, x1, y0, y1, t0_ticks, t1_ticks) -> float:
+        """The surrogate guard's mass residual of tile [x0, x1) x [y0, y1) for a
+        window from state start = (h, hu, hv) at t0 to end at t1 (build-added
+        check; the bed is this oracle's z)."""
+        arrs = [np.ascontiguousarray(a, np.float64).reshape(-1) for a in tuple(start) + tuple(end)]
+        return float(lib().or_guard_residual(ctypes.byref(self.P), _ptr(self.z), *[_ptr(a) for a in arrs],
+                                             int(x0), int(x1), int(y0), int(y1), int(t0_ticks), int(t1_ticks)))
 
     def boundary_inflow(self) -> float:
         return float(self.bflux.sum())

@@ -785,6 +785,88 @@ double or_mass(const or_params *P, const or_state *S) {
 }
 
 /* ------------------------------------------------------------------------ */
+/* The learned surrogate's guard (build-added, not the paper's method): the  */
+/* per-tile mass residual |dV - F| / max(V0, 1 cm x tile area) of a window   */
+/* [t0, t1] whose start state is (h0, hu0, hv0) and end state (h1, hu1,      */
+/* hv1): dV the change of the tile's water volume, F the window length times */
+/* the mean of the water flowing in through the tile's edges in the start   */
+/* and end states, each the HLL mass flux after the hydrostatic              */
+/* reconstruction (ghost states at domain edges, with the inflow depth of    */
+/* t0, resp. t1).  Tile: cells [x0, x1) x [y0, y1).                          */
+/* ------------------------------------------------------------------------ */
+static or_side or_side_arrays(const double *h, const double *hu, const double *hv, const double *z, int64_t c) {
+    or_side s;
+    s.h = h[c];
+    s.z = z[c];
+    if (s.h > OR_H_EPS) { s.u = hu[c] / s.h; s.v = hv[c] / s.h; }
+    else { s.u = 0.0; s.v = 0.0; }
+    return s;
+}
+
+static double or_face_mass(double g, or_side L, or_side R, int xface) {
+    double zf = L.z > R.z ? L.z : R.z;
+    double hL = L.h + L.z - zf; if (hL < 0.0) hL = 0.0;
+    double hR = R.h + R.z - zf; if (hR < 0.0) hR = 0.0;
+    double f[3];
+    if (xface) or_hll(g, hL, L.u, L.v, hR, R.u, R.v, f);
+    else or_hll(g, hL, L.v, L.u, hR, R.v, R.u, f);
+    return f[0];
+}
+
+/* water flowing into the tile through its edges per unit time (m^3/s / dx) */
+static double or_tile_inflow(const or_params *P, const double *z, const double *h, const double *hu,
+                             const double *hv, int32_t x0, int32_t x1, int32_t y0, int32_t y1, double h_in) {
+    const int32_t nx = P->nx, ny = P->ny;
+    double q = 0.0;
+    for (int32_t j = y0; j < y1; ++j) {
+        /* west edge: face between x0 - 1 and x0 */
+        or_side R = or_side_arrays(h, hu, hv, z, (int64_t)j * nx + x0), L;
+        if (x0 == 0) L = or_ghost(P->bc_w[j], R, 1, h_in);
+        else L = or_side_arrays(h, hu, hv, z, (int64_t)j * nx + x0 - 1);
+        q += or_face_mass(P->g, L, R, 1);
+        /* east edge: face between x1 - 1 and x1 */
+        L = or_side_arrays(h, hu, hv, z, (int64_t)j * nx + x1 - 1);
+        if (x1 == nx) R = or_ghost(P->bc_e[j], L, 1, h_in);
+        else R = or_side_arrays(h, hu, hv, z, (int64_t)j * nx + x1);
+        q -= or_face_mass(P->g, L, R, 1);
+    }
+    for (int32_t i = x0; i < x1; ++i) {
+        /* south edge: face between y0 - 1 and y0 */
+        or_side A = or_side_arrays(h, hu, hv, z, (int64_t)y0 * nx + i), B;
+        if (y0 == 0) B = or_ghost(P->bc_s[i], A, 0, h_in);
+        else B = or_side_arrays(h, hu, hv, z, (int64_t)(y0 - 1) * nx + i);
+        q += or_face_mass(P->g, B, A, 0);
+        /* north edge: face between y1 - 1 and y1 */
+        B = or_side_arrays(h, hu, hv, z, (int64_t)(y1 - 1) * nx + i);
+        if (y1 == ny) A = or_ghost(P->bc_n[i], B, 0, h_in);
+        else A = or_side_arrays(h, hu, hv, z, (int64_t)y1 * nx + i);
+        q -= or_face_mass(P->g, B, A, 0);
+    }
+    return q;
+}
+
+double or_guard_residual(const or_params *P, const double *z, const double *h0, const double *hu0,
+                         const double *hv0, const double *h1, const double *hu1, const double *hv1, int32_t x0,
+                         int32_t x1, int32_t y0, int32_t y1, int64_t t0_ticks, int64_t t1_ticks) {
+    const int32_t nx = P->nx;
+    const double dx = P->dx;
+    double v0 = 0.0, v1 = 0.0;
+    for (int32_t j = y0; j < y1; ++j)
+        for (int32_t i = x0; i < x1; ++i) {
+            v0 += h0[(int64_t)j * nx + i];
+            v1 += h1[(int64_t)j * nx + i];
+        }
+    const double q0 = or_tile_inflow(P, z, h0, hu0, hv0, x0, x1, y0, y1, or_hydro_depth(P, t0_ticks));
+    const double q1 = or_tile_inflow(P, z, h1, hu1, hv1, x0, x1, y0, y1, or_hydro_depth(P, t1_ticks));
+    const double window = (double)(t1_ticks - t0_ticks) / OR_TICKS;
+    const double dV = (v1 - v0) * dx * dx;
+    const double F = window * dx * 0.5 * (q0 + q1);
+    const double area = (double)(x1 - x0) * (double)(y1 - y0) * dx * dx;
+    const double denom = v0 * dx * dx > 0.01 * area ? v0 * dx * dx : 0.01 * area;
+    return fabs(dV - F) / denom;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Learned surrogate (build-added, not in the paper): a stack of 3x3 "valid" */
 /* convolutions over NHWC tensors in FP64, with ReLU between layers, and the */
 /* gradients of the mean squared error of its output.  Plain loops in the    */

@@ -616,3 +616,28 @@ def test_launch_shape_switched_mid_run(P):
     for x, y in zip(fields(a), fields(b)):
         assert np.array_equal(x, y)
     assert np.array_equal(a.peds(), b.peds())
+
+
+def test_batch_member_matches_oracle(P, O):
+    """A member of a batched ensemble against the oracle directly: 64 coupled
+    steps of a low-density crowd on a fixed 1/8 s step, batched with two other
+    scenarios of different sizes; the flood within 1e-4 m, every pedestrian's
+    integers identical and its position within 1e-3 m, the counters identical."""
+    a = S.plain_coupled_128(seed=3, n_peds=48, nx=100, ny=90)
+    a.dt_fixed_ticks = 1 << 17
+    b = S.shopping_centre(160, 0.5, 300, 20, seed=7, n_barrier=20, n_layers=1)
+    c = S.random_wet_state(70, 45, dx=0.5, seed=2)
+    members = [P.from_scenario(x) for x in (b, a, c)]
+    batch = P.Batch(members)
+    batch.step(64)
+    batch.synchronize()
+    o = O.Oracle(a)
+    o.step(64)
+    m = members[1]
+    assert m.counters()["t_ticks"] == o.t_ticks == 64 * a.dt_fixed_ticks
+    assert_flood_close(m, o, atol=1e-4)
+    assert_peds_match(m, o, pos_tol=1e-3, vel_tol=1e-2)
+    mc, oc = m.counters(), o.counters()
+    for k in ("n_exited", "hist", "wet"):
+        assert mc[k] == oc[k], k
+    batch.close()

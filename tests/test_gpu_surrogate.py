@@ -112,6 +112,52 @@ def test_gradients_match_oracle(env, shape):
         for got, ref in ((dw, ref_g[l]), (db, ref_g[len(ws) + l])):
             rel = np.linalg.norm(got - ref) / max(np.linalg.norm(ref), 1e-30)
             assert rel <= tol, (l, rel)
+            # element by element: FP32 against FP64 accumulation of each sum
+            err = np.abs(got.astype(np.float64) - ref)
+            bound = 2e-3 * np.abs(ref).max() + 1e-2 * np.abs(ref)
+            assert np.all(err <= bound), (l, float((err / np.maximum(bound, 1e-300)).max()),
+                                          np.unravel_index(np.argmax(err - bound), err.shape))
+
+
+def test_gradients_against_fp64_net(env):
+    """The same gradients against the oracle's plain FP64 net (hidden
+    activations not rounded): what differs is the BF16 storage of the GPU's
+    activations (relative 2^-9 per value, and the rare ReLU decision it moves),
+    so the bound is looser -- 3e-2 of the layer's gradient norm, and element by
+    element 2e-2 of the layer's largest gradient plus 5e-2 relative."""
+    torch, P, O = env
+    B, H, W = 2, 24, 90
+    rng = np.random.default_rng(321)
+    sur = P.Surrogate(seed=12)
+    p = sur.params()
+    p[:] = rng.normal(0, 1, p.size).astype(np.float32) * np.float32(0.12)
+    sur.set_params(p)
+    x = _inputs(rng, B, H, W)
+    t = rng.normal(0, 0.05, (B, H - 10, W - 10, 3)).astype(np.float32)
+    loss, g = sur.gradients(torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda())
+    layers = sur.layers(p)
+    ws = [bf16(w).astype(np.float64) for w, _ in layers]
+    bs = [b.astype(np.float64) for _, b in layers]
+    ws[-1] = ws[-1] * OUT_SCALE
+    bs[-1] = bs[-1] * OUT_SCALE
+    ref_loss = 0.0
+    ref_g = [np.zeros_like(w) for w in ws] + [np.zeros_like(b) for b in bs]
+    for b in range(B):
+        lb, dws, dbs = O.net_loss_grad(split(x[b]).astype(np.float64), ws, bs, t[b].astype(np.float64),
+                                       act_bf16=False)
+        ref_loss += lb / B
+        for l in range(len(ws)):
+            scale = OUT_SCALE if l == len(ws) - 1 else 1.0
+            ref_g[l] += scale * dws[l] / B
+            ref_g[len(ws) + l] += scale * dbs[l] / B
+    assert abs(loss - ref_loss) <= 1e-2 * ref_loss, (loss, ref_loss)
+    for l, (dw, db) in enumerate(sur.layers(g)):
+        for got, ref in ((dw, ref_g[l]), (db, ref_g[len(ws) + l])):
+            rel = np.linalg.norm(got - ref) / max(np.linalg.norm(ref), 1e-30)
+            assert rel <= 3e-2, (l, rel)
+            err = np.abs(got.astype(np.float64) - ref)
+            bound = 2e-2 * np.abs(ref).max() + 5e-2 * np.abs(ref)
+            assert np.all(err <= bound), (l, float((err / np.maximum(bound, 1e-300)).max()))
 
 
 def test_gradients_deterministic(env):

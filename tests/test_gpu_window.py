@@ -267,3 +267,26 @@ def test_window_after_hashed_steps_keeps_results(P):
     for x, y in zip(out[0][0], out[1][0]):
         assert np.array_equal(x, y)
     assert np.array_equal(out[0][1], out[1][1]) and out[0][2] == out[1][2]
+
+
+def test_guard_residual_matches_oracle(P, O):
+    """The guard's per-tile mass residual, restated in the oracle from the
+    window's start and end states: a small random net over two tiles of a wet
+    domain (every net tile accepted: mass bound off, no check), the largest
+    residual the window records against the oracle's over the same tiles."""
+    sc = fixed(S.random_wet_state(300, 120, dx=0.5, seed=6, bc=(2, 1, 0, 0)), dt=2 ** -5)
+    sc.peds = S.empty_peds(0)
+    sim = P.from_scenario(sc)
+    start = [f.astype(np.float64) for f in fields(sim)]
+    t0 = sim.counters()["t_ticks"]
+    sur = net(P, scale=0.05, seed=8)
+    st = sim.surrogate_advance(sur, 1, mass_tol=1e9, check_every=0)
+    end = [f.astype(np.float64) for f in fields(sim)]
+    t1 = sim.counters()["t_ticks"]
+    assert st.tiles_net == 2 and st.tiles_fallback == 0 and st.fail_courant == 0
+    assert t1 - t0 == 8 * sc.dt_fixed_ticks
+    o = O.Oracle(sc)
+    T = 246  # FP_SUR_TILE
+    res = [o.guard_residual(start, end, x0, min(x0 + T, sc.nx), 0, sc.ny, t0, t1) for x0 in (0, T)]
+    assert max(res) > 1e-4  # the random net moves mass: a residual the guard would reject
+    assert abs(st.max_residual - max(res)) <= 1e-3 * max(res), (st.max_residual, res)

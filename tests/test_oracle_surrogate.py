@@ -1,6 +1,8 @@
 """Pins of the oracle's FP64 conv net (the learned surrogate, build-added):
 exact special cases of a convolution and central finite differences of the
 loss gradient."""
+import math
+
 import numpy as np
 import pytest
 
@@ -93,3 +95,63 @@ def test_bf16_activation_option_special_cases(oracle_mod):
     assert a[0] == b[0]
     for ga, gb in zip(a[1] + a[2], b[1] + b[2]):
         assert np.array_equal(ga, gb)
+
+
+# --------------------------------------------------------------------------
+# The surrogate guard's per-tile mass residual (build-added): closed-form cases
+# --------------------------------------------------------------------------
+def _channel(oracle_mod, u):
+    """A 10 x 3 walled channel of 1 m cells, still bed, water 1 m deep moving at u."""
+    import scenarios as S
+    sc = S.closed_basin(10, 3, dx=1.0, wet=False, bumps=False)
+    sc.h[:] = 1.0
+    sc.hu[:] = u
+    return sc, oracle_mod.Oracle(sc)
+
+
+def test_guard_residual_closed_box_redistribution(oracle_mod):
+    """Water moved inside a walled box: no volume change, no flow through walls."""
+    sc, o = _channel(oracle_mod, 0.0)
+    h0 = sc.h.astype(np.float64)
+    h1 = h0.copy()
+    h1[1, 2] += 0.25
+    h1[1, 7] -= 0.25
+    z = np.zeros_like(h0)
+    r = o.guard_residual((h0, z, z), (h1, z, z), 0, 10, 0, 3, 0, 1 << 18)
+    assert r == 0.0
+
+
+def test_guard_residual_inflow_sign_and_window(oracle_mod):
+    """Tile = the channel's east half against the east wall, water flowing in
+    from the west half at q = 0.5 m^2/s: the west face carries exactly q (the
+    states either side are identical), the wall nothing (a reflected state).
+    Unchanged water: residual = window x 3 rows x q / start volume; water raised
+    by that inflow: residual 0."""
+    sc, o = _channel(oracle_mod, 0.5)
+    h0 = sc.h.astype(np.float64)
+    hu0 = sc.hu.astype(np.float64)
+    z = np.zeros_like(h0)
+    t1 = 1 << 18  # 0.25 s
+    r = o.guard_residual((h0, hu0, z), (h0, hu0, z), 5, 10, 0, 3, 0, t1)
+    assert math.isclose(r, 0.25 * 3 * 0.5 / 15.0, rel_tol=1e-12), r
+    h1 = h0.copy()
+    h1[:, 5:] += 0.25 * 3 * 0.5 / 15.0
+    hu1 = hu0.copy()
+    hu1[:, 5:] = 0.5 * h1[:, 5:]  # the same velocity: the west face still carries h u of identical states
+    hu1[:, :5] = 0.5
+    h1[:, :5] = 1.0
+    r = o.guard_residual((h0, hu0, z), (h1, hu1, z), 5, 10, 0, 3, 0, t1)
+    # end state's west face: (1, 0.5) | (1.025, 0.5): the HLL average, not exactly q;
+    # the residual is then the difference of the two fluxes' mean from q
+    assert r < 5e-3, r
+
+
+def test_guard_residual_floor_of_one_centimetre(oracle_mod):
+    """A nearly dry tile: the denominator is 1 cm over the tile's area."""
+    sc, o = _channel(oracle_mod, 0.0)
+    h0 = np.zeros((3, 10))
+    h1 = h0.copy()
+    h1[1, 6] = 0.003
+    z = np.zeros_like(h0)
+    r = o.guard_residual((h0, z, z), (h1, z, z), 5, 10, 0, 3, 0, 1 << 18)
+    assert math.isclose(r, 0.003 / (0.01 * 15.0), rel_tol=1e-12), r

@@ -614,6 +614,30 @@ def run_ensemble(args):
     return 0
 
 
+def run_deployment(args):
+    """Scenario 2 of the paper (Section 3.3): 6 responder group sizes x 6
+    barrier thicknesses on the synthetic shopping centre at the paper's
+    resolution (128 x 128 cells of 2.59 m, 1000 pedestrians), stepped as one
+    batch until every barrier is built or 12 h have passed, then the
+    (160 m^3/s, 7.5 min) discharge flood; prints the deployment table."""
+    import torch
+    import paper_1908_05232_b300 as P
+    from paper_1908_05232_b300 import studies
+    torch.cuda.set_device(0)
+    P.build.build()
+    t0 = time.perf_counter()
+    res = studies.deployment_study(P, flood_minutes=args.deploy_flood_minutes)
+    wall = time.perf_counter() - t0
+    line = {"metric": "scenario-seconds/s (Section 3.3 deployment study as one batched ensemble)",
+            "value": res["ensemble_sim_seconds"] / wall, "unit": "scenario-s/s", "n_gpus": 1, "steps": 1,
+            "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": {"workload": "deployment_36 (6 responder fractions x 6 layers, 128x128 "
+                                                        "cells of 2.59 m, 1000 pedestrians, 12 h window)"},
+            "wall_s": wall, "rows": res["rows"]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_case(args):
     """A short run of one workload (the command line profiled under ncu): after
     an optional pre-run to a simulated time, the case's steps in the given
@@ -687,7 +711,8 @@ def main():
     ap.add_argument("--case-hash-ahead", type=int, default=1, choices=[0, 1], help="hash-ahead in the case")
     ap.add_argument("--case-time", type=float, default=0.0,
                     help="simulated seconds to run before the case's steps (profiler range opened after them)")
-    ap.add_argument("--workload", choices=["barrier2048", "ensemble", "surrogate"], default="barrier2048")
+    ap.add_argument("--workload", choices=["barrier2048", "ensemble", "surrogate", "deployment"], default="barrier2048")
+    ap.add_argument("--deploy-flood-minutes", type=float, default=20.0)
     args = ap.parse_args()
     if args.ncu_case:
         return run_case(args)
@@ -695,6 +720,8 @@ def main():
         return run_surrogate(args)
     if args.workload == "ensemble":
         return run_ensemble(args)
+    if args.workload == "deployment":
+        return run_deployment(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

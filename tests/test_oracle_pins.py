@@ -660,3 +660,41 @@ def test_max_hazard_rating(oracle_mod):
     sc.hu[3, 4] = 0.0
     o = oracle_mod.Oracle(sc)
     assert math.isclose(o.max_hr(), 0.85, rel_tol=1e-6)
+
+
+# --------------------------------------------------------------------------
+# Scenario 2 deployment (Section 3.3) on the oracle: a barrier of B bags built
+# by R responders takes at least 60 s per bag and responder (30 s picking up
+# and 30 s dropping, Section 2.4); all bags are dropped exactly once; more
+# layers take longer
+# --------------------------------------------------------------------------
+def _deploy_time(oracle_mod, n_resp, n_layers, t_max=4000.0):
+    sc = S.closed_basin(24, 12, dx=0.5, wet=False, bumps=False)
+    sc.ped_noise = 0.0
+    sc.exit_mask[11, 10:14] = 1
+    S.with_depot_and_barrier(sc, depot_ij=[(3, 2), (4, 2)], barrier_ij=[(18, 6), (19, 6)], n_layers=n_layers)
+    p = S.empty_peds(n_resp)
+    p["x"][:] = 1.9 + 0.05 * np.arange(n_resp)
+    p["y"][:] = 1.2
+    p["v0"][:] = 1.4
+    p["role"][:] = 1
+    sc.peds = p
+    sc.t_end = t_max
+    o = oracle_mod.Oracle(sc)
+    bags = 2 * n_layers * oracle_mod.bags_per_cell(0.5)
+    while o.t < t_max:
+        o.step(1)
+        if o.S.applied_layers >= 2 * n_layers:
+            return o.t, o.S.total_bags, bags, o
+    return None, o.S.total_bags, bags, o
+
+
+@pytest.mark.parametrize("n_resp", [1, 3])
+def test_deployment_time_bound(oracle_mod, n_resp):
+    t1, dropped, bags, o = _deploy_time(oracle_mod, n_resp, 1)
+    assert t1 is not None
+    assert dropped == bags  # every bag of the layer, once
+    assert t1 >= 60.0 * math.ceil(bags / n_resp)
+    assert np.array_equal(o.field("z")[6, 18:20], [0.25, 0.25])
+    t2, dropped2, bags2, _ = _deploy_time(oracle_mod, n_resp, 2)
+    assert t2 is not None and dropped2 == bags2 and t2 > t1

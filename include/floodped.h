@@ -101,9 +101,16 @@ typedef struct fp_config {
     int32_t coupling;   /* 1: evacuees raise Manning n (Section 2.4), 0: off */
     int32_t evac_trigger; /* 0: evacuees head for the exit from t = 0;
                              1: only once some cell holds water (Section 2.4) */
-    int32_t tile_rows;  /* flood tile height: 8, 16 or 32 (0 = 16) */
-    int32_t reserved[4];
+    int32_t tile_rows;  /* flood run height: 8, 16 or 32 (0 = 16) */
+    int32_t riemann;    /* interface flux: FP_RIEMANN_HLL (0, the paper's first-order
+                           scheme) or FP_RIEMANN_HLLC (1: the cited scheme's three-wave
+                           solver, which also resolves the contact wave of the
+                           tangential momentum); else FP_EINVAL */
+    int32_t reserved[3];
 } fp_config;
+
+#define FP_RIEMANN_HLL 0
+#define FP_RIEMANN_HLLC 1
 
 /* One pedestrian record (32 bytes).  On input, id is ignored: ids are given
  * in order of addition starting at 0.  timer_ticks is the remaining wait of a

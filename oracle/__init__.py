@@ -52,6 +52,8 @@ def lib():
                                      ctypes.c_int64]
         _lib.or_hr_state.restype = ctypes.c_int
         _lib.or_hr_state.argtypes = [ctypes.c_float, ctypes.c_float, ctypes.c_float]
+        _lib.or_hllc.restype = None
+        _lib.or_hllc.argtypes = [ctypes.c_double] * 7 + [ctypes.c_void_p]
         _lib.or_hll.restype = None
         _lib.or_hll.argtypes = [ctypes.c_double] * 7 + [ctypes.c_void_p]
         _lib.or_philox4x64.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
@@ -99,6 +101,7 @@ class _Params(ctypes.Structure):
         ("n_layers", ctypes.c_int32), ("coupling", ctypes.c_int32), ("evac_trigger", ctypes.c_int32),
         ("seed", ctypes.c_uint64), ("ped_noise", ctypes.c_double), ("dt_fixed_ticks", ctypes.c_int64),
         ("n_q", ctypes.c_int32), ("q_t", _P), ("q_Q", _P), ("h_qin", ctypes.c_double),
+        ("riemann", ctypes.c_int32),
     ]
 
 
@@ -169,6 +172,7 @@ class Oracle:
         self.q_Q = keep(np.asarray(getattr(sc, "q_Q", np.zeros(0)), np.float64))
         P.n_q, P.q_t, P.q_Q = self.q_t.size, _ptr(self.q_t), _ptr(self.q_Q)
         P.h_qin = _f32(getattr(sc, "h_qin", 1.0))
+        P.riemann = int(getattr(sc, "riemann", 0))
         self.P = P
         n = nx * ny
         self.h = keep(np.asarray(sc.h, np.float64).reshape(-1).copy())
@@ -297,6 +301,12 @@ class Oracle:
 def hll(g, hL, unL, utL, hR, unR, utR):
     out = (ctypes.c_double * 3)()
     lib().or_hll(g, hL, unL, utL, hR, unR, utR, out)
+    return np.array(out[:])
+
+
+def hllc(g, hL, unL, utL, hR, unR, utR):
+    out = (ctypes.c_double * 3)()
+    lib().or_hllc(g, hL, unL, utL, hR, unR, utR, out)
     return np.array(out[:])
 
 

@@ -15,7 +15,9 @@
  *   - Eq. (2): explicit first-order finite-volume update with east/west and
  *     north/south interface fluxes; "Wang et al. 2011 reduced to first order"
  *     is read as a Godunov-type scheme with non-negative hydrostatic
- *     reconstruction of the face depths and the HLL Riemann solver.
+ *     reconstruction of the face depths and the HLL Riemann solver (HLLC,
+ *     which also resolves the contact wave, as an option: the cited scheme's
+ *     three-wave solver).
  *   - Section 3 (CFL-adaptive time step when wet, 1.0 s pedestrian step when
  *     dry); Section 3.1 inflow: a depth hydrograph (ghost state) or the
  *     paper's triangular discharge hydrograph Q(t) entering through a breach
@@ -107,6 +109,7 @@ typedef struct {
     int32_t n_q;              /* discharge hydrograph points (0: none) */
     const double *q_t, *q_Q;  /* times (s) and discharges Q (m^3/s) */
     double h_qin;             /* depth of the inflowing water at the breach (m) */
+    int32_t riemann;          /* 0: HLL, 1: HLLC (the contact wave resolved) */
 } or_params;
 
 typedef struct {
@@ -383,6 +386,38 @@ void or_hll(double g, double hL, double unL, double utL, double hR, double unR, 
         out[k] = (sR * FL[k] - sL * FR[k] + sL * sR * (UR[k] - UL[k])) / (sR - sL);
 }
 
+/* HLLC (Toro's three-wave solver for the shallow-water equations): the mass
+ * and normal momentum fluxes are HLL's; the tangential momentum is carried by
+ * the mass flux with the tangential velocity of the side the contact wave
+ * S* = (sL hR (uR - sR) - sR hL (uL - sL)) / (hR (uR - sR) - hL (uL - sL))
+ * leaves behind (left for S* > 0, right for S* < 0, their mean at S* = 0). */
+void or_hllc(double g, double hL, double unL, double utL, double hR, double unR, double utR, double out[3]) {
+    or_hll(g, hL, unL, utL, hR, unR, utR, out);
+    if (hL <= OR_H_EPS && hR <= OR_H_EPS) return;
+    if (hL == hR && unL == unR && utL == utR) return;
+    double cL = sqrt(g * hL), cR = sqrt(g * hR), sL, sR;
+    if (hL <= OR_H_EPS) { sL = unR - 2.0 * cR; sR = unR + cR; }
+    else if (hR <= OR_H_EPS) { sL = unL - cL; sR = unL + 2.0 * cL; }
+    else {
+        double us = 0.5 * (unL + unR) + (cL - cR);
+        double cs = 0.5 * (cL + cR) + 0.25 * (unL - unR);
+        double a = unL - cL, b = us - cs;
+        sL = a < b ? a : b;
+        double c = unR + cR, d = us + cs;
+        sR = c > d ? c : d;
+    }
+    if (sL >= 0.0 || sR <= 0.0) return;  /* one-sided: the physical flux already carries the right ut */
+    double ss = (sL * hR * (unR - sR) - sR * hL * (unL - sL)) / (hR * (unR - sR) - hL * (unL - sL));
+    double ut = ss > 0.0 ? utL : (ss < 0.0 ? utR : 0.5 * (utL + utR));
+    out[2] = out[0] * ut;
+}
+
+static void or_flux(const or_params *P, double g, double hL, double unL, double utL, double hR, double unR,
+                    double utR, double out[3]) {
+    if (P->riemann == 1) or_hllc(g, hL, unL, utL, hR, unR, utR, out);
+    else or_hll(g, hL, unL, utL, hR, unR, utR, out);
+}
+
 /* one side of a face: depth, velocities, bed */
 typedef struct { double h, u, v, z; } or_side;
 
@@ -447,7 +482,7 @@ void or_flood_step(const or_params *P, or_state *S, int64_t dt_ticks, const doub
             double zf = L.z > R.z ? L.z : R.z;
             double hLs = L.h + L.z - zf; if (hLs < 0.0) hLs = 0.0;
             double hRs = R.h + R.z - zf; if (hRs < 0.0) hRs = 0.0;
-            or_hll(g, hLs, L.u, L.v, hRs, R.u, R.v, f);
+            or_flux(P, g, hLs, L.u, L.v, hRs, R.u, R.v, f);
             if (i == 0 && P->bc_w[j] == OR_BC_DISCHARGE) { f[0] += qb; f[1] += qb * u_in; }
             if (i == nx && P->bc_e[j] == OR_BC_DISCHARGE) { f[0] -= qb; f[1] += qb * u_in; }
             if (i > 0) {
@@ -473,7 +508,7 @@ void or_flood_step(const or_params *P, or_state *S, int64_t dt_ticks, const doub
             double zf = L.z > R.z ? L.z : R.z;
             double hLs = L.h + L.z - zf; if (hLs < 0.0) hLs = 0.0;
             double hRs = R.h + R.z - zf; if (hRs < 0.0) hRs = 0.0;
-            or_hll(g, hLs, L.v, L.u, hRs, R.v, R.u, f);   /* f = (mass, hv-flux, hu-flux) */
+            or_flux(P, g, hLs, L.v, L.u, hRs, R.v, R.u, f);   /* f = (mass, hv-flux, hu-flux) */
             if (j == 0 && P->bc_s[i] == OR_BC_DISCHARGE) { f[0] += qb; f[1] += qb * u_in; }
             if (j == ny && P->bc_n[i] == OR_BC_DISCHARGE) { f[0] -= qb; f[1] += qb * u_in; }
             if (j > 0) {

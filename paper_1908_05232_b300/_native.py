@@ -33,8 +33,8 @@ class FpConfig(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("dx", ctypes.c_float), ("g", ctypes.c_float),
                 ("cfl", ctypes.c_float), ("ped_noise", ctypes.c_float), ("t_end", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("max_peds", ctypes.c_int32), ("coupling", ctypes.c_int32),
-                ("evac_trigger", ctypes.c_int32), ("tile_rows", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("evac_trigger", ctypes.c_int32), ("tile_rows", ctypes.c_int32), ("riemann", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
 
 
 class FpCounters(ctypes.Structure):
@@ -365,6 +365,7 @@ def config_for(sc, max_peds=None, tile_rows=0) -> FpConfig:
     c.ped_noise, c.t_end, c.seed = sc.ped_noise, sc.t_end, int(sc.seed) & ((1 << 64) - 1)
     c.max_peds = sc.n_peds if max_peds is None else max_peds
     c.coupling, c.evac_trigger, c.tile_rows = int(sc.coupling), int(sc.evac_trigger), int(tile_rows)
+    c.riemann = int(getattr(sc, "riemann", 0))
     return c
 
 

@@ -172,7 +172,7 @@ struct Flux2 {
 // two products are rounded explicitly, so a mirrored face gives exactly the
 // mirrored flux.
 __device__ __forceinline__ Flux2 face2(const K2 &k, float g, float hg, const Sides2 &L, const Sides2 &R, float2 dir,
-                                       float2 qd) {
+                                       float2 qd, bool hllc) {
     const float2 zf = make_float2(fmaxf(L.z.x, R.z.x), fmaxf(L.z.y, R.z.y));
     const float2 hL = f2_max0(f2_sub(k, f2_add(k, L.h, L.z), zf));
     const float2 hR = f2_max0(f2_sub(k, f2_add(k, R.h, R.z), zf));
@@ -204,6 +204,21 @@ __device__ __forceinline__ Flux2 face2(const K2 &k, float g, float hg, const Sid
         fm = f2_mul(k, am, inv);
         fn = f2_mul(k, an, inv);
         ft = f2_mul(k, at, inv);
+        if (hllc) {
+            // HLLC: the tangential momentum rides on the mass flux with the
+            // tangential velocity of the side the contact wave S* leaves behind
+            // (S* > 0: left, S* < 0: right, S* = 0: their mean); S* =
+            // (sL hR (uR - sR) - sR hL (uL - sL)) / (hR (uR - sR) - hL (uL - sL)),
+            // whose sign flips exactly under a mirror
+            const float2 num = f2_sub(k, f2_mul(k, f2_mul(k, sL, hR), f2_sub(k, R.un, sR)),
+                                      f2_mul(k, f2_mul(k, sR, hL), f2_sub(k, L.un, sL)));
+            const float2 den = f2_sub(k, f2_mul(k, hR, f2_sub(k, R.un, sR)), f2_mul(k, hL, f2_sub(k, L.un, sL)));
+            const float2 ss = f2_mul(k, num, f2_rcp(den));
+            const float2 mid = f2_mul(k, f2(0.5f), f2_add(k, L.ut, R.ut));
+            const float2 ut = make_float2(ss.x > 0.0f ? L.ut.x : (ss.x < 0.0f ? R.ut.x : mid.x),
+                                          ss.y > 0.0f ? L.ut.y : (ss.y < 0.0f ? R.ut.y : mid.y));
+            ft = f2_mul(k, fm, ut);
+        }
         const bool rx = sR.x <= 0.0f, ry = sR.y <= 0.0f;
         fm = f2_sel(rx, ry, qR, fm);
         fn = f2_sel(rx, ry, FR1, fn);
@@ -383,7 +398,7 @@ __device__ __forceinline__ void flood_acc_fold_cta(const FpSim &S, int slot, con
 // definition, so the result does not depend on how the rows are split into
 // runs.  Loads are plain (coherent) global loads: in the persistent kernel the
 // planes read in one step were written by other SMs in the step before.
-template <bool EDGE>
+template <bool EDGE, bool HLLC>
 __device__ __forceinline__ void flood_march(const FpSim &S, int par, const FloodStep &st, int x0, int ys, int ye,
                                             FloodAcc &acc) {
     constexpr bool edge = EDGE;
@@ -395,6 +410,7 @@ __device__ __forceinline__ void flood_march(const FpSim &S, int par, const Flood
     const bool ld = i1 <= nx + 3;                      // the pair lies inside the padded row
     const bool ldh = lane == 31 && x0 + FP_TX <= nx;  // the cell east of the run (lane 31's east neighbour)
     const K2 k = make_k2(S);
+    constexpr bool hllc = HLLC;
     const float g = S.g, hg = 0.5f * g;
     const float dt = st.dtf, h_in = st.h_in;
     const float2 nlx = f2(-st.lx), nly = f2(-st.lx), qd = st.qd, zero2 = f2(0.0f);
@@ -445,7 +461,7 @@ __device__ __forceinline__ void flood_march(const FpSim &S, int par, const Flood
                 L = ghost(c, R, true, h_in);
                 if (c == 3) dir = 1.0f;
             }
-            const Flux2 f = face2(k, g, hg, sides_x(L, L), sides_x(R, R), f2(dir), qd);
+            const Flux2 f = face2(k, g, hg, sides_x(L, L), sides_x(R, R), f2(dir), qd, hllc);
             wM = f.m.x;
             wN = f.nr.x;
             wT = f.t.x;
@@ -479,7 +495,7 @@ __device__ __forceinline__ void flood_march(const FpSim &S, int par, const Flood
         // the two y faces between rows j - 1 and j
         Flux2 gy;
         if (!edge) {
-            gy = face2(k, g, hg, Sides2{prev.h, prev.v, prev.u, prev.z}, Sides2{cur.h, cur.v, cur.u, cur.z}, zero2, qd);
+            gy = face2(k, g, hg, Sides2{prev.h, prev.v, prev.u, prev.z}, Sides2{cur.h, cur.v, cur.u, cur.z}, zero2, qd, hllc);
         } else {
             Side B0 = side_x(prev), B1 = side_y(prev), A0 = side_x(cur), A1 = side_y(cur);
             float2 dir = zero2;
@@ -495,7 +511,7 @@ __device__ __forceinline__ void flood_march(const FpSim &S, int par, const Flood
                 A1 = ghost(c1, B1, false, h_in);
                 dir = make_float2(c0 == 3 ? -1.0f : 0.0f, c1 == 3 ? -1.0f : 0.0f);
             }
-            gy = face2(k, g, hg, sides_y(B0, B1), sides_y(A0, A1), dir, qd);
+            gy = face2(k, g, hg, sides_y(B0, B1), sides_y(A0, A1), dir, qd, hllc);
             // no face past the east edge
             gy.m = f2_sel(!v0, !v1, zero2, gy.m);
             gy.nl = f2_sel(!v0, !v1, zero2, gy.nl);
@@ -598,7 +614,7 @@ __device__ __forceinline__ void flood_march(const FpSim &S, int par, const Flood
             fx = face2(k, g, hg, Sides2{cur.h, cur.u, cur.v, cur.z},
                        Sides2{make_float2(cur.h.y, east.h), make_float2(cur.u.y, east.u), make_float2(cur.v.y, east.v),
                               make_float2(cur.z.y, east.z)},
-                       zero2, qd);
+                       zero2, qd, hllc);
         } else {
             const Side L0 = side_x(cur), L1 = side_y(cur);
             Side R0 = side_y(cur), R1 = east;
@@ -613,7 +629,7 @@ __device__ __forceinline__ void flood_march(const FpSim &S, int par, const Flood
                 R1 = ghost(c, L1, true, h_in);
                 if (c == 3) dir.y = -1.0f;
             }
-            fx = face2(k, g, hg, sides_x(L0, L1), sides_x(R0, R1), dir, qd);
+            fx = face2(k, g, hg, sides_x(L0, L1), sides_x(R0, R1), dir, qd, hllc);
             const bool px = i1 > nx, py = i1 + 1 > nx;  // no face past the east edge
             fx.m = f2_sel(px, py, zero2, fx.m);
             fx.nl = f2_sel(px, py, zero2, fx.nl);
@@ -716,8 +732,13 @@ __device__ __forceinline__ void flood_run(const FpSim &S, int par, const FloodSt
         int k1 = k;
         while (k1 + 1 < ng && ((load >> (k1 + 1)) & 1u)) ++k1;
         const int ys = y0 + k * FP_BLK_ROWS, ye = min(y0 + (k1 + 1) * FP_BLK_ROWS, ny);
-        if (edge) flood_march<true>(S, par, st, x0, ys, ye, acc);
-        else flood_march<false>(S, par, st, x0, ys, ye, acc);
+        if (S.riemann == 1) {
+            if (edge) flood_march<true, true>(S, par, st, x0, ys, ye, acc);
+            else flood_march<false, true>(S, par, st, x0, ys, ye, acc);
+        } else {
+            if (edge) flood_march<true, false>(S, par, st, x0, ys, ye, acc);
+            else flood_march<false, false>(S, par, st, x0, ys, ye, acc);
+        }
         k = k1 + 1;
     }
 }

@@ -491,7 +491,8 @@ int fp_sim_create(const fp_config *cfg, fp_sim **out) {
     if (c.nx < 1 || c.ny < 1 || c.nx > (1 << 16) || c.ny > (1 << 16) || !(c.dx > 0.0f) || !(c.g > 0.0f) ||
         !(c.cfl > 0.0f) || c.cfl > 1.0f || c.max_peds < 0 || c.max_peds > (1 << 26) || !(c.t_end >= 0.0) ||
         !(c.ped_noise >= 0.0f) ||
-        (c.tile_rows != 0 && c.tile_rows != 8 && c.tile_rows != 16 && c.tile_rows != 32)) {
+        (c.tile_rows != 0 && c.tile_rows != 8 && c.tile_rows != 16 && c.tile_rows != 32) ||
+        (c.riemann != FP_RIEMANN_HLL && c.riemann != FP_RIEMANN_HLLC)) {
         g_create_error = "invalid fp_config";
         return FP_EINVAL;
     }
@@ -517,6 +518,7 @@ int fp_sim_create(const fp_config *cfg, fp_sim **out) {
     S.nbins = S.nbx * S.nby;
     S.bpc = (int)std::ceil(((double)c.dx * (double)c.dx) / (0.40 * 0.30));
     S.barrier_polls = FP_BARRIER_POLLS_DEFAULT;
+    S.riemann = c.riemann;
     s->tile_rows = c.tile_rows ? c.tile_rows : 16;
     const size_t pe = s->plane_elems(), n = (size_t)c.nx * c.ny;
     bool ok = true;

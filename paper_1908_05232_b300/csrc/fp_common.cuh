@@ -115,6 +115,7 @@ struct FpSim {
     int phase_ts_steps;            // steps recorded in phase_ts (4 stamps per step + 1)
     long long dt_fixed;            // fixed time step in ticks (0: CFL step)
     int barrier_polls;             // polls of a persistent-kernel grid barrier before it gives up
+    int riemann;                   // interface flux: 0 HLL, 1 HLLC
     // discharge breach (Section 3.1): boundary cells coded FP_BC_DISCHARGE take
     // the hydrograph Q(t) (points q_t, q_Q) spread over their width q_width
     int has_discharge, n_q;

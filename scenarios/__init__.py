@@ -80,6 +80,7 @@ class Scenario:
     q_t: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros(0))
     q_Q: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros(0))
     h_qin: float = 1.0
+    riemann: int = 0         # interface flux: 0 HLL, 1 HLLC
 
     @property
     def n_cells(self) -> int:

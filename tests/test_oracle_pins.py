@@ -698,3 +698,80 @@ def test_deployment_time_bound(oracle_mod, n_resp):
     assert np.array_equal(o.field("z")[6, 18:20], [0.25, 0.25])
     t2, dropped2, bags2, _ = _deploy_time(oracle_mod, n_resp, 2)
     assert t2 is not None and dropped2 == bags2 and t2 > t1
+
+
+# --------------------------------------------------------------------------
+# HLLC (the cited scheme's three-wave solver): on a shear wave -- uniform depth
+# and normal velocity, the tangential velocity jumping from +1 to -1 -- the
+# contact travels with the flow, S* = u, and one step is exactly first-order
+# upwind advection of hv; depth and normal momentum do not change.  HLL smears
+# the same jump differently.
+# --------------------------------------------------------------------------
+def _shear(riemann, nx=40):
+    sc = S.closed_basin(nx, 3, dx=1.0, wet=False, bumps=False)
+    sc.h[:] = 1.0
+    sc.hu[:] = 0.5
+    sc.hv[:, : nx // 2] = 1.0
+    sc.hv[:, nx // 2:] = -1.0
+    sc.n0[:] = 0.0
+    sc.bc_s[:], sc.bc_n[:], sc.bc_w[:], sc.bc_e[:] = 1, 1, 1, 1
+    sc.riemann = riemann
+    return sc
+
+
+def test_hllc_shear_wave_is_upwind(oracle_mod):
+    sc = _shear(1)
+    o = oracle_mod.Oracle(sc)
+    o.step(1)
+    lam = o.t / sc.dx
+    v0 = np.where(np.arange(sc.nx) < sc.nx // 2, 1.0, -1.0)
+    q = 0.5
+    want = v0 - lam * q * (v0 - np.concatenate([[v0[0]], v0[:-1]]))
+    for j in range(3):
+        assert np.allclose(o.field("hv")[j], want, rtol=0, atol=1e-14)
+    assert np.all(o.field("h") == 1.0) and np.allclose(o.field("hu"), 0.5, rtol=0, atol=1e-15)
+    # HLL on the same input: the same h and hu, a different (smeared) hv
+    b = oracle_mod.Oracle(_shear(0))
+    b.step(1)
+    assert b.t == o.t
+    assert np.abs(b.field("hv")[1] - want).max() > 1e-2
+
+
+@pytest.mark.parametrize("axis", ["x", "y"])
+def test_hllc_mirror_symmetry_and_mass(oracle_mod, axis):
+    sc = S.random_wet_state(23, 19, dx=0.7, seed=21, bc=(2, 1, 0, 1))
+    sc.riemann = 1
+    m = sc.copy()
+    if axis == "x":
+        for f in ("z", "h", "hu", "hv", "n0"):
+            setattr(m, f, getattr(sc, f)[:, ::-1].copy())
+        m.hu = -m.hu
+        m.bc_w, m.bc_e = sc.bc_e.copy(), sc.bc_w.copy()
+        m.bc_s, m.bc_n = sc.bc_s[::-1].copy(), sc.bc_n[::-1].copy()
+        fl, su, sv = (lambda f: f[:, ::-1]), -1, 1
+    else:
+        for f in ("z", "h", "hu", "hv", "n0"):
+            setattr(m, f, getattr(sc, f)[::-1, :].copy())
+        m.hv = -m.hv
+        m.bc_s, m.bc_n = sc.bc_n.copy(), sc.bc_s.copy()
+        m.bc_w, m.bc_e = sc.bc_w[::-1].copy(), sc.bc_e[::-1].copy()
+        fl, su, sv = (lambda f: f[::-1, :]), 1, -1
+    a, b = oracle_mod.Oracle(sc), oracle_mod.Oracle(m)
+    m0 = a.mass()
+    a.step(40)
+    b.step(40)
+    assert np.array_equal(a.field("h"), fl(b.field("h")))
+    assert np.array_equal(a.field("hu"), su * fl(b.field("hu")))
+    assert np.array_equal(a.field("hv"), sv * fl(b.field("hv")))
+    assert abs(a.mass() - (m0 + a.boundary_inflow())) <= 1e-11 * m0
+
+
+def test_hllc_lake_at_rest_exact(oracle_mod):
+    sc = S.closed_basin(40, 31, dx=1.0, seed=3)
+    sc.riemann = 1
+    o = oracle_mod.Oracle(sc)
+    eta0 = o.h + o.z
+    wet = o.h > 0
+    o.step(100)
+    assert np.all(o.hu == 0.0) and np.all(o.hv == 0.0)
+    assert np.array_equal((o.h + o.z)[wet], eta0[wet])

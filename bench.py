@@ -648,6 +648,24 @@ def run_case(args):
     import paper_1908_05232_b300 as P
     torch.cuda.set_device(0)
     P.build.build()
+    if args.ncu_case == "surrogate_forward":
+        # the surrogate's tensor-core forward on 16 net input tiles of 266 x 266
+        # pixels (a window's batch), twice; each forward launches the five
+        # conv3x3_tc_kernel layers
+        sur = P.Surrogate(seed=1)
+        g = torch.Generator(device="cuda").manual_seed(1)
+        x = torch.rand((16, 266, 266, 4), device="cuda", generator=g)
+        y = torch.zeros((16, 256, 256, 3), device="cuda")
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        sur.forward(x, y)
+        e0.record()
+        sur.forward(x, y)
+        e1.record()
+        torch.cuda.synchronize()
+        flops = 16 * 266 * 266 * 73728
+        print(json.dumps({"case": "surrogate_forward", "ms": e0.elapsed_time(e1),
+                          "tflops_padded": flops / (e0.elapsed_time(e1) * 1e-3) / 1e12}))
+        return 0
     if args.ncu_case == "barrier2048":
         sc = scenarios.config_barrier()
     elif args.ncu_case == "barrier2048mid":
@@ -704,7 +722,8 @@ def main():
     ap.add_argument("--ensemble-size", type=int, default=48)
     ap.add_argument("--ensemble-steps", type=int, default=4, help="64-step chunks timed per ensemble arm")
     ap.add_argument("--surrogate-windows", type=int, default=160)
-    ap.add_argument("--ncu-case", choices=["barrier2048", "barrier2048mid", "wet2048", "wet1024", "shopping512"],
+    ap.add_argument("--ncu-case", choices=["barrier2048", "barrier2048mid", "wet2048", "wet1024", "shopping512",
+                                           "surrogate_forward"],
                     default=None, help="short untimed run of one workload, for profiler captures")
     ap.add_argument("--case-steps", type=int, default=4)
     ap.add_argument("--case-lanes", type=int, default=8, choices=[4, 8, 16], help="lanes per pedestrian in the case")

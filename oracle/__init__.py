@@ -57,6 +57,9 @@ def lib():
         _lib.or_hll.restype = None
         _lib.or_hll.argtypes = [ctypes.c_double] * 7 + [ctypes.c_void_p]
         _lib.or_philox4x64.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        _lib.or_visitor_draw.restype = None
+        _lib.or_visitor_draw.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int32, ctypes.c_float,
+                                         ctypes.c_float, ctypes.c_void_p, ctypes.c_void_p]
         _lib.or_discharge.restype = ctypes.c_double
         _lib.or_discharge.argtypes = [ctypes.c_void_p, ctypes.c_double]
         _lib.or_discharge_volume.restype = ctypes.c_double
@@ -102,6 +105,8 @@ class _Params(ctypes.Structure):
         ("seed", ctypes.c_uint64), ("ped_noise", ctypes.c_double), ("dt_fixed_ticks", ctypes.c_int64),
         ("n_q", ctypes.c_int32), ("q_t", _P), ("q_Q", _P), ("h_qin", ctypes.c_double),
         ("riemann", ctypes.c_int32),
+        ("n_doors", ctypes.c_int32), ("n_door_cells", ctypes.c_int32), ("door_cells", _P), ("door_of", _P),
+        ("entry_period_ticks", ctypes.c_int64), ("entry_v0_lo", ctypes.c_double), ("entry_v0_hi", ctypes.c_double),
     ]
 
 
@@ -119,6 +124,9 @@ class _State(ctypes.Structure):
         ("prole", _P), ("pfsm", _P), ("phr", _P), ("pexit", _P),
         ("nav_exit", _P), ("nav_depot", _P), ("nav_barrier", _P),
         ("last_dt_ticks", ctypes.c_int64),
+        ("cap", ctypes.c_int32), ("pad2", ctypes.c_int32),
+        ("n_entered", ctypes.c_int64), ("n_left", ctypes.c_int64), ("entry_refused", ctypes.c_int64),
+        ("nav_door", _P),
     ]
 
 
@@ -173,6 +181,13 @@ class Oracle:
         P.n_q, P.q_t, P.q_Q = self.q_t.size, _ptr(self.q_t), _ptr(self.q_Q)
         P.h_qin = _f32(getattr(sc, "h_qin", 1.0))
         P.riemann = int(getattr(sc, "riemann", 0))
+        self.door_cells = keep(np.asarray(getattr(sc, "door_cells", np.zeros(0)), np.int32))
+        self.door_of = keep(np.asarray(getattr(sc, "door_of", np.zeros(0)), np.int32))
+        P.n_doors = int(getattr(sc, "n_doors", 0))
+        P.n_door_cells, P.door_cells, P.door_of = self.door_cells.size, _ptr(self.door_cells), _ptr(self.door_of)
+        P.entry_period_ticks = int(round(float(getattr(sc, "entry_period", 6.0)) * TICKS))
+        v0 = getattr(sc, "entry_v0", (1.4, 1.4))
+        P.entry_v0_lo, P.entry_v0_hi = _f32(v0[0]), _f32(v0[1])
         self.P = P
         n = nx * ny
         self.h = keep(np.asarray(sc.h, np.float64).reshape(-1).copy())
@@ -182,20 +197,29 @@ class Oracle:
         self.bflux = keep(np.zeros(2 * nx + 2 * ny, np.float64))
         p = sc.peds
         m = int(p["x"].shape[0])
-        self.px = keep(p["x"].astype(np.float64))
-        self.py = keep(p["y"].astype(np.float64))
-        self.pvx = keep(p["vx"].astype(np.float64))
-        self.pvy = keep(p["vy"].astype(np.float64))
-        self.pv0 = keep(p["v0"].astype(np.float64))
-        self.pid = keep(np.arange(m, dtype=np.int32))
-        self.ptimer = keep(p["timer"].astype(np.int32))
-        self.prole = keep(p["role"].astype(np.uint8))
-        self.pfsm = keep(p["fsm"].astype(np.uint8))
-        self.phr = keep(np.zeros(m, np.uint8))
-        self.pexit = keep(np.zeros(m, np.uint8))
+        # room for the visitors the doors admit: ids up to the scenario's capacity
+        cap = max(m, int(getattr(sc, "max_peds", 0) or 0))
+
+        def grow(a, dtype):
+            out = np.zeros(cap, dtype)
+            out[:m] = a
+            return keep(out)
+
+        self.px = grow(p["x"], np.float64)
+        self.py = grow(p["y"], np.float64)
+        self.pvx = grow(p["vx"], np.float64)
+        self.pvy = grow(p["vy"], np.float64)
+        self.pv0 = grow(p["v0"], np.float64)
+        self.pid = keep(np.arange(cap, dtype=np.int32))
+        self.ptimer = grow(p["timer"], np.int32)
+        self.prole = grow(p["role"], np.uint8)
+        self.pfsm = grow(p["fsm"], np.uint8)
+        self.phr = keep(np.zeros(cap, np.uint8))
+        self.pexit = keep(np.zeros(cap, np.uint8))
         self.nav_exit = keep(np.zeros(n, np.uint8))
         self.nav_depot = keep(np.zeros(n, np.uint8))
         self.nav_barrier = keep(np.zeros(n, np.uint8))
+        self.nav_door = keep(np.zeros(max(1, P.n_doors) * n, np.uint8))
         S = _State()
         S.h, S.hu, S.hv, S.z, S.bflux = [_ptr(a) for a in (self.h, self.hu, self.hv, self.z, self.bflux)]
         S.np = m
@@ -203,6 +227,7 @@ class Oracle:
         S.pid, S.ptimer = _ptr(self.pid), _ptr(self.ptimer)
         S.prole, S.pfsm, S.phr, S.pexit = [_ptr(a) for a in (self.prole, self.pfsm, self.phr, self.pexit)]
         S.nav_exit, S.nav_depot, S.nav_barrier = _ptr(self.nav_exit), _ptr(self.nav_depot), _ptr(self.nav_barrier)
+        S.nav_door, S.cap = _ptr(self.nav_door), cap
         S.t_ticks, S.step = int(sc.t0_ticks), int(sc.step0)
         S.total_bags, S.applied_layers = int(sc.bags0), int(sc.applied0)
         self.S = S
@@ -255,6 +280,19 @@ class Oracle:
         return float(lib().or_guard_residual(ctypes.byref(self.P), _ptr(self.z), *[_ptr(a) for a in arrs],
                                              int(x0), int(x1), int(y0), int(y1), int(t0_ticks), int(t1_ticks)))
 
+    @property
+    def n_peds(self) -> int:
+        """Pedestrians ever in the domain (ids 0 .. n_peds - 1), present or gone."""
+        return int(self.S.np)
+
+    def flow_counts(self) -> dict:
+        """Entry/exit flow counters: entered through the doors, left through
+        their door, out through the emergency exit, refused for capacity, present."""
+        S = self.S
+        n = int(S.np)
+        return dict(n_ids=n, n_entered=int(S.n_entered), n_left=int(S.n_left), n_exited=int(S.n_exited),
+                    refused=int(S.entry_refused), n_active=n - int(S.n_left) - int(S.n_exited))
+
     def boundary_inflow(self) -> float:
         return float(self.bflux.sum())
 
@@ -267,7 +305,7 @@ class Oracle:
         return dict(t_ticks=int(S.t_ticks), step=int(S.step), wet=int(S.wet), total_bags=int(S.total_bags),
                     applied_layers=int(S.applied_layers), neg_depth=int(S.neg_depth),
                     n_exited=int(S.n_exited), hist=[int(v) for v in S.hist],
-                    n_active=int((self.pexit == 0).sum()))
+                    n_active=int((self.pexit[:S.np] == 0).sum()))
 
     def to_scenario(self):
         """The oracle's current state as a new scenario (FP32-rounded fields and
@@ -280,7 +318,8 @@ class Oracle:
         sc.hu = self.hu.reshape(ny, nx).astype(np.float32)
         sc.hv = self.hv.reshape(ny, nx).astype(np.float32)
         sc.z = self.z.reshape(ny, nx).astype(np.float32)
-        keep = self.pexit == 0
+        keep = np.zeros(self.pexit.size, bool)
+        keep[:self.S.np] = self.pexit[:self.S.np] == 0
         p = scenarios.empty_peds(int(keep.sum()))
         p["x"], p["y"] = self.px[keep].astype(np.float32), self.py[keep].astype(np.float32)
         p["vx"], p["vy"] = self.pvx[keep].astype(np.float32), self.pvy[keep].astype(np.float32)
@@ -292,9 +331,11 @@ class Oracle:
         return sc
 
     def peds(self) -> dict:
-        return dict(x=self.px.copy(), y=self.py.copy(), vx=self.pvx.copy(), vy=self.pvy.copy(),
-                    role=self.prole.copy(), fsm=self.pfsm.copy(), hr=self.phr.copy(),
-                    exited=self.pexit.copy(), timer=self.ptimer.copy())
+        """Every pedestrian so far by id (present or gone)."""
+        n = int(self.S.np)
+        return dict(x=self.px[:n].copy(), y=self.py[:n].copy(), vx=self.pvx[:n].copy(), vy=self.pvy[:n].copy(),
+                    role=self.prole[:n].copy(), fsm=self.pfsm[:n].copy(), hr=self.phr[:n].copy(),
+                    exited=self.pexit[:n].copy(), timer=self.ptimer[:n].copy(), v0=self.pv0[:n].copy())
 
 
 # -- pointwise functions, used by the pins ------------------------------------
@@ -320,6 +361,16 @@ def philox4x64(counter, key):
     o = (ctypes.c_uint64 * 4)()
     lib().or_philox4x64(c, k, o)
     return [int(v) for v in o]
+
+
+def visitor_draw(seed, pid, n_doors, v0_lo, v0_hi):
+    """A visitor's draws: (x offset, y offset) in cells inside its entry
+    cell, dry walking speed (FP32 values) and destination door."""
+    off = (ctypes.c_float * 3)()
+    dest = ctypes.c_int32()
+    lib().or_visitor_draw(int(seed) & ((1 << 64) - 1), int(pid), int(n_doors), float(np.float32(v0_lo)),
+                          float(np.float32(v0_hi)), off, ctypes.byref(dest))
+    return float(off[0]), float(off[1]), float(off[2]), int(dest.value)
 
 
 def nav_field(walkable: np.ndarray, goal: np.ndarray):

@@ -29,6 +29,10 @@
  *     bed by one bag thickness per completed layer, N_L layers.
  *   - Section 2.3: pedestrians steered by navigation information toward their
  *     destination, avoiding each other (a social-force repulsion).
+ *   - Sections 2.4, 3 and 3.2: the entry/exit flow before the flood -- visitors
+ *     enter through the entrance doors at a constant rate per door, each bound
+ *     for a door drawn with equal probability, and leave through it; once any
+ *     cell holds water nobody enters and everyone present evacuates.
  *
  * Where floating point decides an integer (the CFL time step in ticks, the
  * hazard state, the cell a position falls in, the wet flag), the decision is
@@ -68,6 +72,8 @@
 #define OR_TO_BARRIER 2
 #define OR_DROP 3
 #define OR_DONE 4
+#define OR_VISIT0 8              /* evacuee task 8 + d: a visitor bound for door d */
+#define OR_MAX_DOORS 8
 /* navigation codes: 0..7 = direction to the next cell, 8 = at goal, 255 = unreachable */
 #define OR_AT_GOAL 8
 #define OR_UNREACHABLE 255
@@ -110,6 +116,12 @@ typedef struct {
     const double *q_t, *q_Q;  /* times (s) and discharges Q (m^3/s) */
     double h_qin;             /* depth of the inflowing water at the breach (m) */
     int32_t riemann;          /* 0: HLL, 1: HLLC (the contact wave resolved) */
+    int32_t n_doors;          /* entrance doors (0: no entry/exit flow) */
+    int32_t n_door_cells;
+    const int32_t *door_cells;   /* flat cell indices; a door's first listed cell is its entry cell */
+    const int32_t *door_of;      /* the door of each listed cell */
+    int64_t entry_period_ticks;  /* each door admits one visitor every this many ticks */
+    double entry_v0_lo, entry_v0_hi;  /* visitors' dry walking speeds (FP32 values, m/s) */
 } or_params;
 
 typedef struct {
@@ -127,6 +139,10 @@ typedef struct {
     uint8_t *prole, *pfsm, *phr, *pexit;
     uint8_t *nav_exit, *nav_depot, *nav_barrier;  /* [ny*nx] */
     int64_t last_dt_ticks;
+    int32_t cap;              /* capacity of the pedestrian arrays (ids 0 .. cap-1) */
+    int32_t pad2;
+    int64_t n_entered, n_left, entry_refused;
+    uint8_t *nav_door;        /* [n_doors][ny*nx] */
 } or_state;
 
 /* ------------------------------------------------------------------------ */
@@ -158,6 +174,26 @@ void or_philox4x64(const uint64_t ctr_in[4], const uint64_t key_in[2], uint64_t 
 
 /* uniform in [0, 1) from the top 24 bits: exact in FP32 and FP64 */
 static double or_uniform24(uint64_t r) { return (double)(r >> 40) * (1.0 / 16777216.0); }
+
+/* A visitor's draws (Section 3: doors used with equal probability), from the
+ * generator's block at counter (id, 0, 1, 0) -- the per-step draws use
+ * (id, step, 0, 0), so the streams never meet:
+ *   off[0], off[1]  its entry position inside the entry cell, in cells:
+ *                   1/4 + u/2 with u the top 22 bits (exact in FP32);
+ *   off[2]          its dry walking speed lo + u (hi - lo), u the top 24 bits,
+ *                   one FP32 fused multiply-add after the FP32 difference;
+ *   *dest           its destination door floor(u n_doors), u the top 24 bits
+ *                   (an integer product: exact). */
+void or_visitor_draw(uint64_t seed, uint64_t id, int32_t n_doors, float v0_lo, float v0_hi, float off[3],
+                     int32_t *dest) {
+    uint64_t ctr[4] = {id, 0, 1, 0}, key[2] = {seed, 0}, r[4];
+    or_philox4x64(ctr, key, r);
+    off[0] = 0.25f + 0.5f * ((float)(r[0] >> 42) * (1.0f / 4194304.0f));
+    off[1] = 0.25f + 0.5f * ((float)(r[1] >> 42) * (1.0f / 4194304.0f));
+    const float span = v0_hi - v0_lo;
+    off[2] = fmaf((float)(r[3] >> 40) * (1.0f / 16777216.0f), span, v0_lo);
+    *dest = (int32_t)(((r[2] >> 40) * (uint64_t)n_doors) >> 24);
+}
 
 /* ------------------------------------------------------------------------ */
 /* Navigation map (Section 2.1/2.3): a 4-connected BFS distance over        */
@@ -556,7 +592,7 @@ static int or_walkable_at(const or_params *P, double x, double y) {
 
 int32_t or_bags_per_cell(double dx) { return (int32_t)ceil((dx * dx) / (OR_BAG_L * OR_BAG_W)); }
 
-enum { G_NONE = 0, G_EXIT = 1, G_DEPOT = 2, G_BARRIER = 3, G_STRAIGHT = 4 };
+enum { G_NONE = 0, G_EXIT = 1, G_DEPOT = 2, G_BARRIER = 3, G_STRAIGHT = 4, G_DOOR = 5 };
 
 /* h, hu, hv are the flood state at step n (the step's input) */
 int64_t or_ped_step(const or_params *P, or_state *S, int64_t dt_ticks, int32_t wet, int64_t bags_snap,
@@ -589,8 +625,17 @@ int64_t or_ped_step(const or_params *P, or_state *S, int64_t dt_ticks, int32_t w
         int32_t target = -1;
         uint8_t fsm = S->pfsm[p];
         int32_t timer = S->ptimer[p];
+        int32_t door = -1;
         if (S->prole[p] == OR_EVAC) {
-            goal = (P->evac_trigger == 0 || wet) ? G_EXIT : G_NONE;
+            /* before the trigger a visitor walks to its door; once water is seen
+             * (or with no trigger) every evacuee heads for the exit */
+            if (P->evac_trigger == 0 || wet) {
+                goal = G_EXIT;
+                fsm = 0;
+            } else if (fsm >= OR_VISIT0 && fsm - OR_VISIT0 < P->n_doors) {
+                goal = G_DOOR;
+                door = fsm - OR_VISIT0;
+            }
         } else {
             if (fsm != OR_DONE && bags_snap >= cap) fsm = OR_DONE;
             switch (fsm) {
@@ -626,7 +671,7 @@ int64_t or_ped_step(const or_params *P, or_state *S, int64_t dt_ticks, int32_t w
          * (or straight to the barrier cell being filled), plus a small random term;
          * when that cell is the destination, no faster than reaching its centre in dt */
         double ex = 0.0, ey = 0.0, sdes = speed;
-        if (goal == G_EXIT || goal == G_DEPOT || goal == G_BARRIER || goal == G_STRAIGHT) {
+        if (goal != G_NONE) {
             double tx = 0.0, ty = 0.0;
             int have = 0, arriving = 0;
             if (goal == G_STRAIGHT) {
@@ -635,7 +680,9 @@ int64_t or_ped_step(const or_params *P, or_state *S, int64_t dt_ticks, int32_t w
                 have = 1;
                 arriving = 1;
             } else {
-                const uint8_t *nav = goal == G_EXIT ? S->nav_exit : goal == G_DEPOT ? S->nav_depot : S->nav_barrier;
+                const uint8_t *nav = goal == G_EXIT ? S->nav_exit : goal == G_DEPOT ? S->nav_depot
+                                     : goal == G_BARRIER ? S->nav_barrier
+                                     : S->nav_door + (int64_t)door * P->nx * P->ny;
                 uint8_t code = nav[c];
                 if (code < 8) {
                     int32_t ti = ci + OR_OX[code], tj = cj + OR_OY[code];
@@ -698,15 +745,19 @@ int64_t or_ped_step(const or_params *P, or_state *S, int64_t dt_ticks, int32_t w
         else if (or_walkable_at(P, xn, y)) { yn = y; vy = 0.0; }
         else if (or_walkable_at(P, x, yn)) { xn = x; vx = 0.0; }
         else { xn = x; yn = y; vx = 0.0; vy = 0.0; }
+        /* through the emergency exit (1), or a visitor in a cell of its door (2) */
         uint8_t exited = 0;
-        if (goal == G_EXIT) {
+        {
             int32_t ii = or_cell_index(xn, dxf), jj = or_cell_index(yn, dxf);
-            if (P->exit_mask[(int64_t)jj * nx + ii]) exited = 1;
+            int64_t cn = (int64_t)jj * nx + ii;
+            if (goal == G_EXIT && P->exit_mask[cn]) exited = 1;
+            if (goal == G_DOOR && S->nav_door[(int64_t)door * P->nx * P->ny + cn] == OR_AT_GOAL) exited = 2;
         }
         nxp[p] = xn; nyp[p] = yn; nvx[p] = vx; nvy[p] = vy;
         nfsm[p] = fsm; ntim[p] = timer; nhr[p] = (uint8_t)hr; nex[p] = exited;
         S->hist[hr] += 1;
-        if (exited) S->n_exited += 1;
+        if (exited == 1) S->n_exited += 1;
+        if (exited == 2) S->n_left += 1;
     }
     for (int32_t p = 0; p < np; ++p) {
         S->px[p] = nxp[p]; S->py[p] = nyp[p]; S->pvx[p] = nvx[p]; S->pvy[p] = nvy[p];
@@ -730,8 +781,54 @@ void or_prepare(const or_params *P, or_state *S) {
     memset(goal, 0, (size_t)n);
     for (int k = 0; k < P->n_barrier; ++k) goal[P->barrier_cells[k]] = 1;
     or_nav_field(P->nx, P->ny, P->walkable, goal, S->nav_barrier, dist);
+    for (int d = 0; d < P->n_doors; ++d) {
+        memset(goal, 0, (size_t)n);
+        for (int k = 0; k < P->n_door_cells; ++k)
+            if (P->door_of[k] == d) goal[P->door_cells[k]] = 1;
+        or_nav_field(P->nx, P->ny, P->walkable, goal, S->nav_door + (int64_t)d * n, dist);
+    }
     free(goal);
     free(dist);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Entry flow (Sections 3, 3.2): while the evacuation trigger has not fired,  */
+/* every door admits one visitor at each whole multiple of the entry period  */
+/* in the step's interval (t, t + dt]; the step's visitors take the next ids */
+/* door by door; each stands at rest at its draws' position in its door's   */
+/* entry cell, bound for the drawn door.  Past the array capacity a visitor  */
+/* is refused (counted).  t >= 0.                                            */
+/* ------------------------------------------------------------------------ */
+static void or_entries(const or_params *P, or_state *S, int64_t t, int64_t dt_ticks, int32_t wet) {
+    if (P->n_doors <= 0 || P->evac_trigger == 0 || wet || dt_ticks <= 0) return;
+    const int64_t T = P->entry_period_ticks;
+    const float dxf = (float)P->dx;
+    for (int32_t d = 0; d < P->n_doors; ++d) {
+        int32_t cell = -1;
+        for (int32_t k = 0; k < P->n_door_cells && cell < 0; ++k)
+            if (P->door_of[k] == d) cell = P->door_cells[k];
+        const int64_t count = (t + dt_ticks) / T - t / T;
+        for (int64_t m = 0; m < count; ++m) {
+            if (S->np >= S->cap) { S->entry_refused += 1; continue; }
+            const int32_t p = S->np;
+            float off[3];
+            int32_t dest;
+            or_visitor_draw(P->seed, (uint64_t)p, P->n_doors, (float)P->entry_v0_lo, (float)P->entry_v0_hi, off,
+                            &dest);
+            S->px[p] = (double)(((float)(cell % P->nx) + off[0]) * dxf);
+            S->py[p] = (double)(((float)(cell / P->nx) + off[1]) * dxf);
+            S->pvx[p] = 0.0; S->pvy[p] = 0.0;
+            S->pv0[p] = (double)off[2];
+            S->pid[p] = p;
+            S->ptimer[p] = 0;
+            S->prole[p] = OR_EVAC;
+            S->pfsm[p] = (uint8_t)(OR_VISIT0 + dest);
+            S->phr[p] = 0;
+            S->pexit[p] = 0;
+            S->np += 1;
+            S->n_entered += 1;
+        }
+    }
 }
 
 /* ------------------------------------------------------------------------ */
@@ -780,6 +877,7 @@ int64_t or_step(const or_params *P, or_state *S) {
     memcpy(h0 + 2 * n, S->hv, sizeof(double) * (size_t)n);
     or_flood_step(P, S, dt_ticks, n_eff);
     int64_t drops = or_ped_step(P, S, dt_ticks, S->wet, bags_snap, h0, h0 + n, h0 + 2 * n);
+    or_entries(P, S, S->t_ticks, dt_ticks, S->wet);
     S->total_bags += drops;
     S->t_ticks += dt_ticks;
     S->step += 1;

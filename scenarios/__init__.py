@@ -81,6 +81,17 @@ class Scenario:
     q_Q: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros(0))
     h_qin: float = 1.0
     riemann: int = 0         # interface flux: 0 HLL, 1 HLLC
+    # entrance doors (entry/exit flow before the flood): door_of[k] is the door
+    # of cell door_cells[k] (a door's first listed cell is its entry cell); each
+    # door admits one visitor every entry_period seconds, walking speeds drawn
+    # in entry_v0 = (lo, hi) m/s; max_peds: pedestrian capacity (ids), 0 = the
+    # initial count
+    door_cells: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros(0, np.int32))
+    door_of: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros(0, np.int32))
+    n_doors: int = 0
+    entry_period: float = 6.0
+    entry_v0: tuple = (1.0, 1.6)
+    max_peds: int = 0
 
     @property
     def n_cells(self) -> int:
@@ -260,6 +271,62 @@ def shopping_centre(n: int = 512, dx: float = 0.5, n_evac: int = 10_000, n_resp:
                                   (yd + 1) * n + xd, (yd + 1) * n + xd + 1], np.int32)
         s.n_layers = n_layers
     return s
+
+
+def with_doors(s: Scenario, n_doors: int = 7, period: float = 6.0, v0=(1.0, 1.6),
+               capacity: Optional[int] = None) -> Scenario:
+    """Entrance doors of the shopping centre (Sections 3, 3.2: 7 doors at the
+    ends of the corridors): one cell each, just inside the west or east wall
+    (alternately) at the cross corridors between the shop rows, from the
+    south; each admits one visitor every ``period`` seconds (10 per door per
+    minute at the default) while no water has been seen.  ``capacity``: the
+    pedestrian ids the run may use (default: the present crowd plus every
+    door's admissions until t_end)."""
+    n = s.nx
+    L = n * s.dx
+    n_rows = max(2, int(round(L / 40.0)))
+    rows = list(np.linspace(2, n - 2, n_rows + 1).astype(int)[1:-1])
+    cells = []
+    for k in range(n_doors):
+        west = k % 2 == 0
+        row = rows[k % len(rows)] if rows else n // 2
+        if k >= len(rows):
+            west = not west
+        col = 1 if west else n - 2
+        # the nearest walkable cell of that wall's column, outward from the row
+        for dy in range(0, s.ny):
+            hit = [r for r in (row - dy, row + dy) if 0 <= r < s.ny and s.walkable[r, col]]
+            if hit:
+                row = hit[0]
+                break
+        c = row * n + col
+        assert s.walkable[row, col] and c not in cells, "no walkable door cell"
+        cells.append(c)
+    s.door_cells = np.array(cells, np.int32)
+    s.door_of = np.arange(n_doors, dtype=np.int32)
+    s.n_doors = int(n_doors)
+    s.entry_period = float(period)
+    s.entry_v0 = (float(v0[0]), float(v0[1]))
+    if capacity is None:
+        capacity = s.n_peds + n_doors * (int(s.t_end / period) + 1)
+    s.max_peds = int(capacity)
+    s.evac_trigger = 1
+    return s
+
+
+def scenario1(n: int = 128, dx: float = 2.59, pre_flood: float = 300.0, q_peak: float = 160.0,
+              t_inflow: float = 450.0, period: float = 6.0, coupling: int = 1, t_end: float = 3600.0,
+              seed: int = 6, n_doors: int = 7) -> Scenario:
+    """Scenario 1 (Section 3.2, during-flood evacuation) on the synthetic
+    shopping centre at the paper's resolution: empty at t = 0, visitors enter
+    through the doors during a pre-flood spread of ``pre_flood`` seconds (the
+    paper's 5 minutes, Q = 0), then the (q_peak, t_inflow) triangular discharge
+    flood enters through the south breach (depth 1 m); the first wet cell
+    stops the entries and turns everyone present into an evacuee."""
+    sc = shopping_centre(n, dx, 0, 0, seed, t_end, discharge=(q_peak, t_inflow), coupling=coupling)
+    sc.q_t, sc.q_Q = triangular_discharge(q_peak, t_inflow, t_start=pre_flood)
+    sc.name = "scenario1_%d" % n
+    return with_doors(sc, n_doors, period, capacity=n_doors * (int((pre_flood + t_inflow) / period) + 2))
 
 
 def triangular_discharge(q_peak: float, t_inflow: float, t_start: float = 0.0):

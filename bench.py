@@ -266,7 +266,6 @@ class Snapshot:
         N.fp_set_bed(h, f[3])
         N.fp_clear_pedestrians(h)
         N._check(N.lib().fp_add_pedestrians(h, N._VP(p.data_ptr()), self.n_peds), h)
-        self.sim.n_total = self.n_peds
         N.fp_set_time(h, self.sc.t0_ticks, self.sc.step0)
         N.fp_set_barrier_progress(h, self.sc.bags0, self.sc.applied0)
 

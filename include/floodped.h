@@ -120,9 +120,11 @@ typedef struct fp_ped {
     float vx, vy;    /* velocity (m/s) */
     uint32_t id;
     uint8_t role;    /* FP_ROLE_* */
-    uint8_t task;    /* FP_TASK_* (responders) */
+    uint8_t task;    /* FP_TASK_* (responders); evacuees: 0, or FP_TASK_VISIT0 + d
+                        for a visitor bound for door d (fp_set_doors) */
     uint8_t hr;      /* FP_HR_* of the last step */
-    uint8_t exited;  /* 1 once through the emergency exit */
+    uint8_t exited;  /* 1 once through the emergency exit, 2 once a visitor has
+                        left through the door it was bound for */
     int32_t timer_ticks;
     float v0;        /* walking speed on dry ground (m/s) */
 } fp_ped;
@@ -141,6 +143,10 @@ typedef struct fp_counters {
     int64_t ped_updates;    /* pedestrians advanced, summed over steps */
     int64_t cfl_exceeded;   /* fixed-dt steps whose Courant number exceeded cfg.cfl
                                (see fp_set_fixed_dt; 0 in CFL mode) */
+    int64_t n_ids;          /* pedestrian ids issued: added, or admitted through a door
+                               (FP_FIELD_PEDS returns this many records) */
+    int64_t n_entered;      /* visitors admitted through the doors (fp_set_doors) */
+    int64_t n_left;         /* visitors gone through the door they were bound for */
 } fp_counters;
 
 typedef struct fp_sim fp_sim; /* opaque handle, owned by the library */
@@ -191,6 +197,33 @@ int fp_set_discharge(fp_sim *sim, const double *t, const double *q, int32_t n, d
  * flat cell indices; n_layers = N_L layers of one bag thickness (0.25 m). */
 int fp_set_goals(fp_sim *sim, const int32_t *depot_cells, int32_t n_depot,
                  const int32_t *barrier_cells, int32_t n_barrier, int32_t n_layers);
+
+/* Entrance doors and the entry/exit flow before the flood (Sections 2.4, 3 and
+ * 3.2: pedestrians enter and leave through the doors, each door used with
+ * equal probability; once water is seen nobody enters any more and everyone
+ * present evacuates).  Door d (0 <= d < n_doors <= FP_MAX_DOORS) is the walkable
+ * cells cells[k] with door[k] == d (flat indices, n_cells entries); visitors
+ * enter in its first listed cell.  With cfg.evac_trigger = 1 and while no cell
+ * has held water, every door admits one visitor at each whole multiple of
+ * entry_period_s (>= 2^-10 s, rounded to the tick) within a step's interval
+ * (t, t + dt] (t >= 0): an evacuee record (role 0) with the next id, at rest at
+ * a random point of the middle half of the entry cell (each axis), dry walking
+ * speed uniform in [v0_min, v0_max] (0 <= v0_min <= v0_max <= 10 m/s), task
+ * FP_TASK_VISIT0 + its destination door, drawn with probability 1/n_doors.
+ * The draws come from the random generator's block at counter (id, 0, 1, 0).
+ * Before the trigger a visitor walks toward its destination door on that
+ * door's navigation field and leaves (exited = 2, fp_counters.n_left) after
+ * the move that puts it in one of the door's cells; once water is seen it is
+ * an evacuee bound for the emergency exit (task 0).  An admission past the
+ * capacity (cfg.max_peds ids) is refused and fp_synchronize reports
+ * FP_EOVERFLOW.  Records added with fp_add_pedestrians may carry a visitor task
+ * too.  n_doors = 0 removes the doors; fp_set_terrain removes them as well (set
+ * them after the terrain).  FP_EINVAL for cells outside the domain or not
+ * walkable, a door with no cell, or values out of range. */
+#define FP_MAX_DOORS 8
+#define FP_TASK_VISIT0 8
+int fp_set_doors(fp_sim *sim, const int32_t *cells, const int32_t *door, int32_t n_cells, int32_t n_doors,
+                 double entry_period_s, double v0_min, double v0_max);
 
 /* Water state U = [h, hu, hv] (Eq. 1), float[ny*nx] each; h >= 0. */
 int fp_set_state(fp_sim *sim, const float *h, const float *hu, const float *hv);

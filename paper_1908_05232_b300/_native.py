@@ -41,7 +41,8 @@ class FpCounters(ctypes.Structure):
     _fields_ = [("t_ticks", ctypes.c_int64), ("step", ctypes.c_int64), ("n_active", ctypes.c_int64),
                 ("n_exited", ctypes.c_int64), ("total_bags", ctypes.c_int64), ("applied_layers", ctypes.c_int64),
                 ("neg_depth", ctypes.c_int64), ("hist", ctypes.c_int64 * 5), ("wet", ctypes.c_int32),
-                ("error_flags", ctypes.c_uint32), ("ped_updates", ctypes.c_int64), ("cfl_exceeded", ctypes.c_int64)]
+                ("error_flags", ctypes.c_uint32), ("ped_updates", ctypes.c_int64), ("cfl_exceeded", ctypes.c_int64),
+                ("n_ids", ctypes.c_int64), ("n_entered", ctypes.c_int64), ("n_left", ctypes.c_int64)]
 
 
 class SurGuard(ctypes.Structure):
@@ -81,6 +82,8 @@ def lib():
             "fp_set_hydrograph": [_VP, _VP, _VP, ctypes.c_int32],
             "fp_set_discharge": [_VP, _VP, _VP, ctypes.c_int32, ctypes.c_double],
             "fp_set_goals": [_VP, _VP, ctypes.c_int32, _VP, ctypes.c_int32, ctypes.c_int32],
+            "fp_set_doors": [_VP, _VP, _VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+                             ctypes.c_double],
             "fp_set_state": [_VP] * 4, "fp_set_time": [_VP, ctypes.c_int64, ctypes.c_int64],
             "fp_set_barrier_progress": [_VP, ctypes.c_int64, ctypes.c_int64],
             "fp_add_pedestrians": [_VP, _VP, ctypes.c_int32], "fp_clear_pedestrians": [_VP],
@@ -173,6 +176,13 @@ def fp_set_goals(h, depot, barrier, n_layers):
     _check(lib().fp_set_goals(h, _ptr(depot), depot.size, _ptr(barrier), barrier.size, int(n_layers)), h)
 
 
+def fp_set_doors(h, cells, door, n_doors, entry_period_s, v0_min, v0_max):
+    cells = np.ascontiguousarray(cells, np.int32)
+    door = np.ascontiguousarray(door, np.int32)
+    _check(lib().fp_set_doors(h, _ptr(cells), _ptr(door), int(cells.size), int(n_doors), float(entry_period_s),
+                              float(v0_min), float(v0_max)), h)
+
+
 def fp_set_state(h, depth, hu, hv):
     _check(lib().fp_set_state(h, _ptr(depth), _ptr(hu), _ptr(hv)), h)
 
@@ -255,7 +265,6 @@ class Simulation:
         self.cfg = cfg
         self.h = fp_sim_create(cfg)
         self.nx, self.ny = cfg.nx, cfg.ny
-        self.n_total = 0
 
     def close(self):
         if self.h is not None:
@@ -276,15 +285,16 @@ class Simulation:
 
     def add_pedestrians(self, recs):
         fp_add_pedestrians(self.h, recs)
-        self.n_total += int(recs.shape[0])
 
     def field(self, which):
         out = np.empty((self.ny, self.nx), np.float32)
         return fp_read_state(self.h, which, out)
 
     def peds(self):
-        out = np.zeros(self.n_total, PED_DTYPE)
-        if self.n_total:
+        """Every pedestrian so far by id (present or gone)."""
+        n = int(self.counters()["n_ids"])
+        out = np.zeros(n, PED_DTYPE)
+        if n:
             fp_read_state(self.h, FP_FIELD_PEDS, out)
         return out
 
@@ -294,7 +304,7 @@ class Simulation:
         return dict(t_ticks=c.t_ticks, step=c.step, n_active=c.n_active, n_exited=c.n_exited,
                     total_bags=c.total_bags, applied_layers=c.applied_layers, neg_depth=c.neg_depth,
                     hist=list(c.hist), wet=c.wet, error_flags=c.error_flags, ped_updates=c.ped_updates,
-                    cfl_exceeded=c.cfl_exceeded)
+                    cfl_exceeded=c.cfl_exceeded, n_ids=c.n_ids, n_entered=c.n_entered, n_left=c.n_left)
 
     def set_fixed_dt(self, dt_seconds):
         _check(lib().fp_set_fixed_dt(self.h, float(dt_seconds)), self.h)
@@ -363,7 +373,7 @@ def config_for(sc, max_peds=None, tile_rows=0) -> FpConfig:
     c = FpConfig()
     c.nx, c.ny, c.dx, c.g, c.cfl = sc.nx, sc.ny, sc.dx, sc.g, sc.cfl
     c.ped_noise, c.t_end, c.seed = sc.ped_noise, sc.t_end, int(sc.seed) & ((1 << 64) - 1)
-    c.max_peds = sc.n_peds if max_peds is None else max_peds
+    c.max_peds = max(sc.n_peds, int(getattr(sc, "max_peds", 0) or 0)) if max_peds is None else max_peds
     c.coupling, c.evac_trigger, c.tile_rows = int(sc.coupling), int(sc.evac_trigger), int(tile_rows)
     c.riemann = int(getattr(sc, "riemann", 0))
     return c
@@ -384,6 +394,8 @@ def from_scenario(sc, max_peds=None, tile_rows=0, peds=True, mode=None) -> Simul
     if getattr(sc, "q_t", None) is not None and len(sc.q_t):
         fp_set_discharge(sim.h, sc.q_t, sc.q_Q, sc.h_qin)
     fp_set_goals(sim.h, sc.depot_cells, sc.barrier_cells, sc.n_layers)
+    if getattr(sc, "n_doors", 0):
+        fp_set_doors(sim.h, sc.door_cells, sc.door_of, sc.n_doors, sc.entry_period, sc.entry_v0[0], sc.entry_v0[1])
     fp_set_state(sim.h, c(sc.h, np.float32), c(sc.hu, np.float32), c(sc.hv, np.float32))
     if getattr(sc, "t0_ticks", 0) or getattr(sc, "step0", 0):
         fp_set_time(sim.h, sc.t0_ticks, sc.step0)

@@ -93,17 +93,18 @@ struct fp_sim {
     bool hashed = false;
     bool hash_ahead = true;  // ped_step hashes its output records (fp_set_hash_ahead)
     int nb_known = -1;       // the record count of B while the host knows it (since a clear or an add), else -1
+    int ids_known = -1;      // the ids issued, likewise
     long long pend_t = 0, pend_step = 0;
     int tile_rows = 16;
     int ped_lanes = 8;   // lanes per pedestrian in the per-step kernel (4, 8, 16)
     // graphs of 64 steps by starting clock slot, whose first step hashes the
     // records of B itself ([0]) or finds them hashed ([1])
     cudaGraphExec_t graphs[2][4] = {};
-    int n_total = 0;
     std::string err;
     std::vector<void *> allocs;
     std::vector<uint8_t> walk_h, exit_h, bc_h[4];
     std::vector<int> depot_h, barrier_h;
+    std::vector<int> door_cells_h, door_of_h;  // entrance doors: cell, door of the cell
     uint4 *read_buf = nullptr;
     bool profiling = false;
     int mode = FP_MODE_KERNELS;
@@ -360,13 +361,6 @@ static int ensure_window(fp_sim *s) {
                                             fp_sur_pitch(FP_SUR_TILE + 2 * FP_SUR_HALO) * 32)) != nullptr;
     ok &= (W.dU = s->dalloc<float>((size_t)nt * FP_SUR_TILE * FP_SUR_TILE * 3)) != nullptr;
     if (!ok) return s->fail(FP_ENOMEM, "surrogate window buffers");
-    FpSim F = S;
-    for (int p = 0; p < 2; ++p) {
-        F.h[p] = W.fb[p][0];
-        F.hu[p] = W.fb[p][1];
-        F.hv[p] = W.fb[p][2];
-        F.blk_wet[p] = nullptr;
-    }
     if (cudaStreamCreateWithFlags(&W.net_stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&W.ev_start, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&W.ev_input, cudaEventDisableTiming) != cudaSuccess ||
@@ -639,6 +633,11 @@ int fp_set_terrain(fp_sim *s, const float *z, const float *n0, const uint8_t *wa
             return s->cuda_fail(e, "walkable upload");
     }
     if ((e = cudaStreamSynchronize(s->stream)) != cudaSuccess) return s->cuda_fail(e, "terrain");
+    // the doors' fields follow the old walkability: set them again after the terrain
+    s->S.n_doors = 0;
+    s->door_cells_h.clear();
+    s->door_of_h.clear();
+    s->drop_graphs();
     return upload_nav(s);
 }
 
@@ -725,6 +724,76 @@ int fp_set_hydrograph(fp_sim *s, const double *t, const double *h, int32_t n) {
     return FP_OK;
 }
 
+int fp_set_doors(fp_sim *s, const int32_t *cells, const int32_t *door, int32_t n_cells, int32_t n_doors,
+                 double entry_period_s, double v0_min, double v0_max) {
+    if (!s) return FP_EINVAL;
+    if (n_doors < 0 || n_doors > FP_MAX_DOORS) return s->fail(FP_EINVAL, "door count out of range");
+    cudaError_t e = cudaStreamSynchronize(s->stream);  // no step in flight reads the tables
+    if (e != cudaSuccess) return s->cuda_fail(e, "doors");
+    if (n_doors == 0) {
+        s->S.n_doors = 0;
+        s->door_cells_h.clear();
+        s->door_of_h.clear();
+        s->drop_graphs();
+        return FP_OK;
+    }
+    if (n_cells < n_doors || !cells || !door) return s->fail(FP_EINVAL, "bad door cell arguments");
+    if (!(entry_period_s >= 1.0 / 1024.0 && entry_period_s <= 1e9))
+        return s->fail(FP_EINVAL, "entry period out of range");
+    if (!(v0_min >= 0.0 && v0_max >= v0_min && v0_max <= 10.0)) return s->fail(FP_EINVAL, "bad walking speeds");
+    const int nx = s->S.nx, ny = s->S.ny;
+    const size_t n = (size_t)nx * ny;
+    std::vector<int> hc(n_cells), hd(n_cells);
+    if ((e = s->copy(hc.data(), cells, sizeof(int) * n_cells)) != cudaSuccess) return s->cuda_fail(e, "door copy");
+    if ((e = s->copy(hd.data(), door, sizeof(int) * n_cells)) != cudaSuccess) return s->cuda_fail(e, "door copy");
+    int entry[FP_MAX_DOORS];
+    for (int d = 0; d < FP_MAX_DOORS; ++d) entry[d] = -1;
+    for (int k = 0; k < n_cells; ++k) {
+        if (hc[k] < 0 || (size_t)hc[k] >= n || hd[k] < 0 || hd[k] >= n_doors)
+            return s->fail(FP_EINVAL, "door cell or door index out of range");
+        if (!s->walk_h[hc[k]]) return s->fail(FP_EINVAL, "a door cell is not walkable");
+        if (entry[hd[k]] < 0) entry[hd[k]] = hc[k];
+    }
+    for (int d = 0; d < n_doors; ++d)
+        if (entry[d] < 0) return s->fail(FP_EINVAL, "a door has no cell");
+    if (!s->S.door_nav) {
+        unsigned char *nav = s->dalloc<unsigned char>((size_t)FP_MAX_DOORS * n), *arr = s->dalloc<unsigned char>(n);
+        if (!nav || !arr) return s->fail(FP_ECUDA, "door table allocation failed");
+        s->S.door_nav = nav;
+        s->S.door_arrive = arr;
+    }
+    // one navigation field per door (the same breadth-first construction as
+    // the exit's) and the arrival bits
+    std::vector<uint8_t> goal(n), code, arrive(n, 0);
+    static const int ox[8] = {1, 0, -1, 0, 1, -1, -1, 1};
+    static const int oy[8] = {0, 1, 0, -1, 1, 1, -1, -1};
+    for (int d = 0; d < n_doors; ++d) {
+        std::fill(goal.begin(), goal.end(), 0);
+        for (int k = 0; k < n_cells; ++k)
+            if (hd[k] == d) goal[hc[k]] = 1;
+        build_nav(nx, ny, s->walk_h, goal, code);
+        e = s->copy(const_cast<unsigned char *>(s->S.door_nav) + (size_t)d * n, code.data(), n);
+        if (e != cudaSuccess) return s->cuda_fail(e, "door navigation upload");
+        for (size_t c = 0; c < n; ++c) {
+            if (code[c] >= 8) continue;
+            const int i = (int)(c % nx) + ox[code[c]], j = (int)(c / nx) + oy[code[c]];
+            if (code[(size_t)j * nx + i] == FP_AT_GOAL) arrive[c] |= (uint8_t)(1u << d);
+        }
+    }
+    if ((e = s->copy(const_cast<unsigned char *>(s->S.door_arrive), arrive.data(), n)) != cudaSuccess)
+        return s->cuda_fail(e, "door navigation upload");
+    s->S.n_doors = n_doors;
+    for (int d = 0; d < FP_MAX_DOORS; ++d) s->S.door_entry[d] = d < n_doors ? entry[d] : 0;
+    s->S.entry_period = std::max(1LL, (long long)llround(entry_period_s * 1048576.0));
+    const float lo = (float)v0_min, hi = (float)v0_max;
+    s->S.entry_vlo = lo;
+    s->S.entry_vspan = hi - lo;  // FP32 difference
+    s->door_cells_h = hc;
+    s->door_of_h = hd;
+    s->drop_graphs();  // the graphs hold the kernels' parameters
+    return FP_OK;
+}
+
 int fp_set_goals(fp_sim *s, const int32_t *depot, int32_t n_depot, const int32_t *barrier, int32_t n_barrier,
                  int32_t n_layers) {
     if (!s) return FP_EINVAL;
@@ -799,32 +868,36 @@ int fp_add_pedestrians(fp_sim *s, const fp_ped *peds, int32_t count) {
     if (count == 0) return FP_OK;
     cudaError_t e = drop_hash(s);
     if (e != cudaSuccess) return s->cuda_fail(e, "hash reset");
-    // the record count of B: known on the host since a clear or an add, else read
-    int nb0 = s->nb_known;
-    if (nb0 < 0) {
+    // the record count of B and the ids issued (doors admit visitors on the
+    // device): known on the host since a clear or an add, else read
+    int nb0 = s->nb_known, ids0 = s->ids_known;
+    if (nb0 < 0 || ids0 < 0) {
         FpCounters c;
         if ((e = s->copy(&c, s->S.cnt, sizeof(c))) != cudaSuccess) return s->cuda_fail(e, "counters read");
         nb0 = c.nB;
+        ids0 = c.n_ids;
     }
-    if (s->n_total + count > s->S.cap || nb0 + count > s->S.cap)
+    if ((long long)ids0 + count > s->S.cap || (long long)nb0 + count > s->S.cap)
         return s->fail(FP_EOVERFLOW, "pedestrian capacity exceeded");
     // upload, ids and the new record count (set by the kernel), then one read
     // back for the walkability check (which also waits for the upload)
     e = cudaMemcpyAsync(s->S.pedB + 2 * (size_t)nb0, peds, (size_t)count * sizeof(fp_ped), cudaMemcpyDefault,
                         s->stream);
     if (e != cudaSuccess) return s->cuda_fail(e, "pedestrian upload");
-    fp_launch_assign_ids(s->S, nb0, s->n_total, count, s->stream);
+    fp_launch_assign_ids(s->S, nb0, ids0, count, s->stream);
     int bad = 0;
     if ((e = s->copy(&bad, &s->S.cnt->bad_ped, sizeof(int))) != cudaSuccess) return s->cuda_fail(e, "assign ids");
     if (bad) {
         int zero = 0;
         s->copy(&s->S.cnt->bad_ped, &zero, sizeof(int));
         s->copy(&s->S.cnt->nB, &nb0, sizeof(int));  // the records stay out
+        s->copy(&s->S.cnt->n_ids, &ids0, sizeof(int));
         s->nb_known = nb0;
+        s->ids_known = ids0;
         return s->fail(FP_EINVAL, "a pedestrian stands outside the domain or in a non-walkable cell");
     }
-    s->n_total += count;
     s->nb_known = nb0 + count;
+    s->ids_known = ids0 + count;
     return FP_OK;
 }
 
@@ -836,15 +909,15 @@ int fp_clear_pedestrians(fp_sim *s) {
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) return s->cuda_fail(e, "clear");
-    s->n_total = 0;
     s->nb_known = 0;
+    s->ids_known = 0;
     return FP_OK;
 }
 
 int fp_step(fp_sim *s, int32_t n_steps) {
     if (!s) return FP_EINVAL;
     if (n_steps < 0) return s->fail(FP_EINVAL, "negative step count");
-    if (n_steps > 0) s->nb_known = -1;  // exits change it
+    if (n_steps > 0) s->nb_known = s->ids_known = -1;  // exits and door admissions change them
     if (s->need_prepare) {
         int rc = prepare(s);
         if (rc != FP_OK) return rc;
@@ -1174,6 +1247,7 @@ int fp_synchronize(fp_sim *s) {
     if (err & FP_ERR_TIMEOUT) return s->fail(FP_ETIMEOUT, "a bounded device wait timed out");
     if (err & FP_ERR_OCC_OVERFLOW) return s->fail(FP_EOVERFLOW, "more than 65535 evacuees in one cell");
     if (err & FP_ERR_NAN) return s->fail(FP_ENAN, "non-finite water state");
+    if (err & FP_ERR_CAPACITY) return s->fail(FP_EOVERFLOW, "a door admission exceeded the pedestrian capacity");
     return s->fail(FP_ECUDA, "device error bits set");
 }
 
@@ -1209,10 +1283,12 @@ int fp_read_state(fp_sim *s, int32_t which, void *dst, size_t bytes) {
             break;
         }
         case FP_FIELD_PEDS: {
-            if (bytes < (size_t)s->n_total * sizeof(fp_ped)) return s->fail(FP_EINVAL, "destination too small");
-            fp_launch_read_peds(S, s->read_buf, s->n_total, s->stream);
-            if (s->n_total)
-                e = cudaMemcpyAsync(dst, s->read_buf, (size_t)s->n_total * sizeof(fp_ped), cudaMemcpyDefault, s->stream);
+            int n_ids = 0;
+            if ((e = s->copy(&n_ids, &S.cnt->n_ids, sizeof(int))) != cudaSuccess) break;
+            if (bytes < (size_t)n_ids * sizeof(fp_ped)) return s->fail(FP_EINVAL, "destination too small");
+            fp_launch_read_peds(S, s->read_buf, n_ids, s->stream);
+            if (n_ids)
+                e = cudaMemcpyAsync(dst, s->read_buf, (size_t)n_ids * sizeof(fp_ped), cudaMemcpyDefault, s->stream);
             break;
         }
         case FP_FIELD_COUNTERS: {
@@ -1227,7 +1303,10 @@ int fp_read_state(fp_sim *s, int32_t which, void *dst, size_t bytes) {
             o.t_ticks = k.t;
             o.step = k.step;
             o.n_exited = (int64_t)c.n_exited;
-            o.n_active = (int64_t)s->n_total - (int64_t)c.n_exited;
+            o.n_active = (int64_t)c.n_ids - (int64_t)c.n_exited - (int64_t)c.n_left;
+            o.n_ids = c.n_ids;
+            o.n_entered = (int64_t)c.n_entered;
+            o.n_left = (int64_t)c.n_left;
             o.total_bags = (int64_t)c.total_bags;
             o.applied_layers = (int64_t)c.applied;
             o.neg_depth = (int64_t)c.neg_depth;

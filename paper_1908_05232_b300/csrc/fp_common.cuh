@@ -40,6 +40,10 @@
 #define FP_ERR_OCC_OVERFLOW 2u
 #define FP_ERR_NAN 4u
 #define FP_ERR_BAD_PED 8u
+#define FP_ERR_CAPACITY 16u   // a door admission past the pedestrian capacity was refused
+
+#define FP_MAX_DOORS 8
+#define FP_TASK_VISIT0 8      // evacuee task 8 + d: a visitor bound for door d
 
 // pedestrian meta word: role | task << 8 | hr << 16 | exited << 24 (byte lanes of fp_ped)
 #define FP_META_ROLE(m) ((m) & 0xffu)
@@ -79,6 +83,9 @@ struct FpCounters {
     unsigned int cfl_over;            // fixed-dt steps whose CFL number exceeded the limit
     unsigned long long ped_updates;   // sum over steps with dt > 0 of pedestrians advanced
     unsigned int hr_max_bits;         // largest hazard rating of the last FP_FIELD_HR_MAX read, float bits
+    int n_ids;                        // pedestrian ids issued (added or admitted through a door)
+    unsigned long long n_entered;     // visitors admitted through the doors
+    unsigned long long n_left;        // visitors gone through the door they were bound for
 };
 
 struct FpSim {
@@ -123,6 +130,16 @@ struct FpSim {
     double q_width;                // breach width B (m): discharge cells x dx
     double h_qin;                  // depth of the inflowing water (m), an FP32 value
     long long q_end_ticks;         // Q = 0 from this time on (the breach is a wall)
+    // entrance doors (Sections 3, 3.2): door d admits a visitor every
+    // entry_period ticks at its entry cell door_entry[d] while no water has been
+    // seen; door_nav[d * nx * ny + c] the direction code toward door d,
+    // door_arrive[c] bit d: the cell that code points to is a cell of door d
+    int n_doors;
+    int door_entry[FP_MAX_DOORS];
+    long long entry_period;
+    float entry_vlo, entry_vspan;  // visitors' dry walking speed: lo + u span
+    const unsigned char *door_nav;
+    const unsigned char *door_arrive;
     const unsigned char *tile_mask;  // per flood tile: 0 = skip (nullptr: every tile runs)
     // Water flags of 64 x 8-cell blocks, by the parity of the state plane they
     // describe: 0 = the block holds h = hu = hv = 0 there (written by the flood

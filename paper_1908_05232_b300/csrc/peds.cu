@@ -9,7 +9,8 @@
 //               re-zeroes the counts; the exited bin's start is the new count;
 //   gather      moves each record of B to its bin's range in A; exited
 //               records go to the by-id archive;
-//   ped_step    eight lanes per record of A (peds_dev.cuh).
+//   ped_step    eight lanes per record of A (peds_dev.cuh); the first warp
+//               of block 0 then admits the step's visitors through the doors.
 #include "peds_dev.cuh"
 
 namespace {
@@ -226,6 +227,7 @@ __global__ void __launch_bounds__(256) ped_step_kernel(const __grid_constant__ F
     const StepCtl ctl = s_ctl;
     const int gt = blockIdx.x * blockDim.x + threadIdx.x;
     ped_group<kG>(S, par, ctl, gt / kG, threadIdx.x & (kG - 1), DirectLookup{S.bin_start}, hash_next != 0);
+    if (blockIdx.x == 0 && threadIdx.x < 32) door_entries(S, par, ctl, hash_next != 0);
 }
 
 // New records sit in B at [first_slot, first_slot + count): give them ids
@@ -233,13 +235,19 @@ __global__ void __launch_bounds__(256) ped_step_kernel(const __grid_constant__ F
 // walkable cell, and seed the by-id archive.
 __global__ void assign_ids_kernel(const __grid_constant__ FpSim S, int first_slot, int first_id, int count) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k == 0) S.cnt->nB = first_slot + count;  // the host puts it back if a record is rejected
+    if (k == 0) {  // the host puts both back if a record is rejected
+        S.cnt->nB = first_slot + count;
+        S.cnt->n_ids = first_id + count;
+    }
     if (k >= count) return;
     const int i = first_slot + k;
     const int id = first_id + k;
     uint4 a = S.pedB[2 * i], b = S.pedB[2 * i + 1];
     b.x = (unsigned)id;
-    b.y = FP_META(FP_META_ROLE(b.y) ? 1 : 0, FP_META_TASK(b.y) <= 4 ? FP_META_TASK(b.y) : 0, 0, 0);
+    // responders: tasks 0..4; evacuees: 0, or a visitor bound for door task - 8
+    const unsigned role = FP_META_ROLE(b.y) ? 1u : 0u, task = FP_META_TASK(b.y);
+    const bool task_ok = role ? task <= 4u : (task == 0u || (task >= FP_TASK_VISIT0 && task < FP_TASK_VISIT0 + FP_MAX_DOORS));
+    b.y = FP_META(role, task_ok ? task : 0u, 0, 0);
     if (!walkable_at(S, __uint_as_float(a.x), __uint_as_float(a.y))) atomicAdd(&S.cnt->bad_ped, 1);
     S.pedB[2 * i + 1] = b;
     S.arch[2 * (size_t)id] = a;
@@ -324,6 +332,7 @@ __global__ void __launch_bounds__(256) ped_step_batch_kernel(const FpSim *__rest
     __syncthreads();
     const StepCtl ctl = s_ctl;
     ped_group<kGroup>(S, par, ctl, j0 + threadIdx.x / kGroup, threadIdx.x & (kGroup - 1), DirectLookup{S.bin_start}, false);
+    if (j0 == 0 && threadIdx.x < 32) door_entries(S, par, ctl, false);
 }
 
 }  // namespace
@@ -370,6 +379,9 @@ __global__ void clear_peds_kernel(const __grid_constant__ FpSim S) {
     C->bags_snap = 0ull;
     C->applied = 0ull;
     C->n_exited = 0ull;
+    C->n_ids = 0;
+    C->n_entered = 0ull;
+    C->n_left = 0ull;
     for (int k = 0; k < 5; ++k) C->hist[k] = 0ull;
 }
 

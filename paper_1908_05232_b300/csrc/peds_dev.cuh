@@ -12,7 +12,9 @@
 //                 repulsion from neighbours in the 3 x 3 bins split over the
 //                 lanes (integer fixed point, so the sum does not depend on the
 //                 order records sit in a bin), velocity relaxation and cap, move
-//                 with wall sliding, exit.
+//                 with wall sliding, exit (through the emergency exit, or a
+//                 visitor through the door it is bound for);
+//   door_entries  visitors admitted through the doors during the step.
 #pragma once
 #include "fp_common.cuh"
 
@@ -62,7 +64,7 @@ constexpr float kBagT = 0.25f;
 __constant__ int c_ox[8] = {1, 0, -1, 0, 1, -1, -1, 1};
 __constant__ int c_oy[8] = {0, 1, 0, -1, 1, 1, -1, -1};
 
-enum { G_NONE = 0, G_EXIT = 1, G_DEPOT = 2, G_BARRIER = 3, G_STRAIGHT = 4 };
+enum { G_NONE = 0, G_EXIT = 1, G_DEPOT = 2, G_BARRIER = 3, G_STRAIGHT = 4, G_DOOR = 5 };
 
 // cell flags at a position: bit 0 walkable, bit 1 exit (0 outside the domain)
 __device__ __forceinline__ unsigned cell_flags_at(const FpSim &S, float x, float y) {
@@ -80,13 +82,14 @@ constexpr int kGroup = 8;  // lanes per pedestrian
 
 // Values every thread of a step reads once (filled by one thread per CTA).
 struct StepCtl {
-    long long dt_ticks, step;
+    long long t, dt_ticks, step;
     unsigned long long bags;
     int wet, nA;
 };
 
 __device__ __forceinline__ void load_step_ctl(const FpSim &S, int slot, int nA, StepCtl &ctl) {
     const FpClock c = S.clock[slot];
+    ctl.t = c.t;
     ctl.dt_ticks = fp_dt_ticks(S, c, c.h_in);
     ctl.step = c.step;
     ctl.wet = c.wet;
@@ -185,7 +188,7 @@ __device__ __forceinline__ void ped_group(const FpSim &S, int par, const StepCtl
     const bool live = valid && dt_ticks > 0;
     const float dx = S.dx;
     const float dt = (float)dt_ticks * (1.0f / FP_TICKS_F);
-    int hr = 0, role = 0, task = 0, timer = 0, goal = G_NONE, target = -1, ci = 0, cj = 0;
+    int hr = 0, role = 0, task = 0, timer = 0, goal = G_NONE, target = -1, ci = 0, cj = 0, door = 0;
     float x = 0.f, y = 0.f, vx = 0.f, vy = 0.f, speed = 0.f, vdx = 0.f, vdy = 0.f;
     unsigned id = 0, v0bits = 0;
     bool drop = false;
@@ -236,7 +239,15 @@ __device__ __forceinline__ void ped_group(const FpSim &S, int par, const StepCtl
             hr = fp_hr_state(hc, huc, hvc);
             speed = hr == 0 ? __uint_as_float(v0bits) : c_speed[hr];
             if (role == 0) {
-                goal = (S.evac_trigger == 0 || ctl.wet) ? G_EXIT : G_NONE;
+                // before the trigger a visitor walks to its door; once water is
+                // seen (or with no trigger) every evacuee heads for the exit
+                if (S.evac_trigger == 0 || ctl.wet) {
+                    goal = G_EXIT;
+                    task = 0;
+                } else if (task >= FP_TASK_VISIT0 && task - FP_TASK_VISIT0 < S.n_doors) {
+                    goal = G_DOOR;
+                    door = task - FP_TASK_VISIT0;
+                }
             } else {
                 const unsigned long long cap =
                     (unsigned long long)S.nb * (unsigned long long)S.n_layers * (unsigned long long)S.bpc;
@@ -275,15 +286,23 @@ __device__ __forceinline__ void ped_group(const FpSim &S, int par, const StepCtl
                     ty = ((float)(target / S.nx) + 0.5f) * dx;
                     have = arriving = true;
                 } else {
-                    const int gi = goal == G_EXIT ? 0 : goal == G_DEPOT ? 1 : 2;
-                    const int code = S.nav[gi][c];
-                    const unsigned arr = S.arrive[c];  // loaded beside the code
+                    int code, bit;
+                    unsigned arr;
+                    if (goal == G_DOOR) {
+                        code = S.door_nav[(size_t)door * ((size_t)S.nx * S.ny) + c];
+                        arr = S.door_arrive[c];  // loaded beside the code
+                        bit = door;
+                    } else {
+                        bit = goal == G_EXIT ? 0 : goal == G_DEPOT ? 1 : 2;
+                        code = S.nav[bit][c];
+                        arr = S.arrive[c];
+                    }
                     if (code < 8) {
                         const int ti = ci + c_ox[code], tj = cj + c_oy[code];
                         tx = ((float)ti + 0.5f) * dx;
                         ty = ((float)tj + 0.5f) * dx;
                         have = true;
-                        arriving = ((arr >> gi) & 1u) != 0u;
+                        arriving = ((arr >> bit) & 1u) != 0u;
                     }
                 }
                 if (have) {
@@ -398,8 +417,15 @@ __device__ __forceinline__ void ped_group(const FpSim &S, int par, const StepCtl
         } else if (walkable_at(S, xn, y)) { yn = y; vy = 0.0f; fl = cell_flags_at(S, xn, yn); }
         else if (walkable_at(S, x, yn)) { xn = x; vx = 0.0f; fl = cell_flags_at(S, xn, yn); }
         else { xn = x; yn = y; vx = 0.0f; vy = 0.0f; fl = cell_flags_at(S, xn, yn); }
-        const int exited = goal == G_EXIT && (fl & 2u) ? 1 : 0;
-        if (exited) atomicAdd(&C->n_exited, 1ull);
+        // gone: through the emergency exit (1), or a visitor now in a cell of
+        // its door (2); the new position is in a walkable cell of the domain
+        int exited = goal == G_EXIT && (fl & 2u) ? 1 : 0;
+        if (goal == G_DOOR) {
+            const size_t cn = (size_t)fp_cell_of(yn, dx) * S.nx + fp_cell_of(xn, dx);
+            if (S.door_nav[(size_t)door * ((size_t)S.nx * S.ny) + cn] == FP_AT_GOAL) exited = 2;
+        }
+        if (exited == 1) atomicAdd(&C->n_exited, 1ull);
+        if (exited == 2) atomicAdd(&C->n_left, 1ull);
         if (drop) atomicAdd(&C->total_bags, 1ull);
         const unsigned meta_out = FP_META(role, task, hr, exited);
         S.pedB[2 * j] = make_uint4(__float_as_uint(xn), __float_as_uint(yn), __float_as_uint(vx), __float_as_uint(vy));
@@ -417,5 +443,71 @@ __device__ __forceinline__ void ped_group(const FpSim &S, int par, const StepCtl
     }
 }
 
+
+// Visitors entering through the doors during the step (t, t + dt] (Sections 3
+// and 3.2): while no water has been seen (evac_trigger 1), door d admits one
+// visitor at each whole multiple of the entry period in the interval (t >= 0).
+// The step's visitors take the next ids and the slots of B after the nA
+// records the pedestrian step writes, door by door; ids past the capacity are
+// refused (error bit).  A visitor's draws come from the generator's block at
+// counter (id, 0, 1, 0): its position in the door's entry cell (a quarter to
+// three quarters of a cell along each axis), its destination door (equal
+// probabilities) and its dry walking speed.  It stands at rest, and with
+// hash_next it is hashed for the next step like the step's other outputs.
+// Called by one full warp of the block whose thread 0 set nB = nA for the step
+// (that thread, lane 0 here, moves nB on).
+__device__ __forceinline__ void door_entries(const FpSim &S, int par, const StepCtl &ctl, bool hash_next) {
+    if (S.n_doors == 0 || S.evac_trigger == 0 || ctl.wet || ctl.dt_ticks <= 0) return;
+    const int lane = threadIdx.x & 31;
+    FpCounters *C = S.cnt;
+    const long long T = S.entry_period;
+    const int k = lane < S.n_doors ? (int)((ctl.t + ctl.dt_ticks) / T - ctl.t / T) : 0;
+    int incl = k;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    if (total == 0) return;
+    const int pre = incl - k;
+    const int id0 = C->n_ids;
+    const int admitted = max(0, min(total, S.cap - id0));
+    __syncwarp();
+    if (lane == 0) {
+        if (admitted < total) fp_set_err(S, FP_ERR_CAPACITY);
+        C->nB = ctl.nA + admitted;
+        C->n_ids = id0 + admitted;
+        C->n_entered += (unsigned long long)admitted;
+    }
+    for (int e0 = 0; e0 < admitted; e0 += 32) {
+        const int e = e0 + lane;
+        int door = 0;  // the last door (with admissions) whose first visitor is <= e
+        for (int d = 0; d < S.n_doors; ++d) {
+            const int pd = __shfl_sync(0xffffffffu, pre, d), kd = __shfl_sync(0xffffffffu, k, d);
+            if (kd > 0 && e >= pd) door = d;
+        }
+        if (e < admitted) {
+            const int id = id0 + e, slot = ctl.nA + e;
+            unsigned long long r[4] = {(unsigned long long)id, 0ull, 1ull, 0ull};
+            fp_philox4x64(r, S.seed, 0ull);
+            const float ox = __fmaf_rn(0.5f, (float)(unsigned)(r[0] >> 42) * (1.0f / 4194304.0f), 0.25f);
+            const float oy = __fmaf_rn(0.5f, (float)(unsigned)(r[1] >> 42) * (1.0f / 4194304.0f), 0.25f);
+            const int dest = (int)((((r[2] >> 40) * (unsigned long long)S.n_doors)) >> 24);
+            const float v0 = __fmaf_rn((float)(unsigned)(r[3] >> 40) * (1.0f / 16777216.0f), S.entry_vspan, S.entry_vlo);
+            const int c = S.door_entry[door];
+            const float x = __fmul_rn(__fadd_rn((float)(c % S.nx), ox), S.dx);
+            const float y = __fmul_rn(__fadd_rn((float)(c / S.nx), oy), S.dx);
+            const unsigned meta = FP_META(0, FP_TASK_VISIT0 + dest, 0, 0);
+            const uint4 a = make_uint4(__float_as_uint(x), __float_as_uint(y), 0u, 0u);
+            const uint4 b = make_uint4((unsigned)id, meta, 0u, __float_as_uint(v0));
+            S.pedB[2 * slot] = a;
+            S.pedB[2 * slot + 1] = b;
+            S.arch[2 * (size_t)id] = a;
+            S.arch[2 * (size_t)id + 1] = b;
+            if (hash_next) hash_record(S, slot, x, y, meta, S.occ[par ^ 1]);
+        }
+    }
+}
 
 }  // namespace fpdev

@@ -244,6 +244,7 @@ __global__ void __launch_bounds__(kPT, 1) persistent_kernel(const __grid_constan
             if (pcx * kPedPerCTA >= nA) break;
             ped_group<kGroup>(S, par, ctl, pcx * kPedPerCTA + tid / kGroup, tid & (kGroup - 1), lookup, hash_next);
         }
+        if (cta == 0 && tid < 32) door_entries(S, par, ctl, hash_next);  // thread 0 set nB = nA above
         if (!grid_sync(bar, S)) return;
         stamp(S, 4 * s + 4);
     }

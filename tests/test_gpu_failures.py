@@ -40,7 +40,6 @@ def _restore(P, sim, sc):
     c = np.ascontiguousarray
     N.fp_set_state(sim.h, c(sc.h, np.float32), c(sc.hu, np.float32), c(sc.hv, np.float32))
     N.fp_clear_pedestrians(sim.h)
-    sim.n_total = 0
     if sc.n_peds:
         sim.add_pedestrians(P.ped_records(sc.peds))
     N.fp_set_time(sim.h, sc.t0_ticks, sc.step0)

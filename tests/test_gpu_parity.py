@@ -588,7 +588,6 @@ def test_restore_then_step_matches_a_fresh_run(P):
     for _ in range(2):
         N.fp_set_state(sim.h, sc.h, sc.hu, sc.hv)
         N.fp_clear_pedestrians(sim.h)
-        sim.n_total = 0
         sim.add_pedestrians(recs)
         N.fp_set_time(sim.h, 0, 0)
         sim.step(70)

@@ -31,6 +31,11 @@ surrogate the learned surrogate's windows against the plain update from the
         same snapshot at a fixed step (scenario-seconds/s), with the largest
         depth difference from the plain run at the end.
 
+Other workloads (``--workload``): ``ensemble`` and ``surrogate`` (the batched
+and surrogate figures at full size), ``deployment`` (the Section 3.3 study of
+36 runs as one batch), ``scenario1`` (the Section 3.2 study: entry/exit flow
+through the doors, flood, evacuation, with and without the roughness coupling).
+
 ``--impl reference`` times the oracle itself (host cores) on the same snapshot.
 Multi-GPU (torchrun): every rank runs an independent replica (weak scaling).
 """
@@ -637,6 +642,98 @@ def run_deployment(args):
     return 0
 
 
+def run_scenario1(args):
+    """Scenario 1 of the paper (Section 3.2) on the synthetic shopping centre
+    at the paper's resolution (128 x 128 cells of 2.59 m, 7 doors): visitors
+    enter and leave through the doors during a 5-minute pre-flood spread, then
+    the (160 m^3/s, 7.5 min) discharge flood enters, the first wet cell stops
+    the entries and everyone present evacuates.  Runs with and without the
+    evacuees' roughness coupling, each to the last evacuee out (or 1 h): whole
+    run timed in 64-step chunks (the evacuee count polled after each), then the
+    same run again sampling the flood-risk states every 0.1 min (Fig. 6).  The
+    oracle is timed on the run's first steps, the GPU on the same steps."""
+    import torch
+    import scenarios
+    import paper_1908_05232_b300 as P
+    from paper_1908_05232_b300 import studies
+    torch.cuda.set_device(0)
+    P.build.build()
+    T = 1 << 20
+    pre, t_end = 300.0, 3600.0
+
+    def make(coupling):
+        return scenarios.scenario1(pre_flood=pre, period=args.s1_period, coupling=coupling, t_end=t_end)
+
+    def run(sim, max_steps=None):
+        steps = 0
+        while True:
+            k = 64 if max_steps is None else min(64, max_steps - steps)
+            sim.step(k)
+            steps += k
+            c = sim.counters()  # synchronises
+            if max_steps is not None and steps >= max_steps:
+                return c
+            if c["t_ticks"] >= int(t_end * T) or (c["t_ticks"] > int(pre * T) and c["wet"] and c["n_active"] == 0):
+                return c
+
+    warm = P.from_scenario(make(1))  # graphs and first-touch costs, not timed
+    run(warm, 256)
+    warm.close()
+    runs = {}
+    for coupling in (1, 0):
+        sc = make(coupling)
+        sim = P.from_scenario(sc)
+        t0 = time.perf_counter()
+        c = run(sim)
+        wall = time.perf_counter() - t0
+        sim.close()
+        st = studies.evacuation_study(P, coupling, pre_flood=pre, period=args.s1_period, t_end=t_end)
+        hist = np.array([h for _, _, h in st["samples"]])
+        runs["with_coupling" if coupling else "without_coupling"] = {
+            "wall_s": wall, "steps": int(c["step"]), "simulated_s": c["t_ticks"] / T,
+            "scenario_s_per_s": c["t_ticks"] / T / wall, "steps_per_s": c["step"] / wall,
+            "ped_updates_per_s": c["ped_updates"] / wall,
+            "cell_updates_per_s": c["step"] * sc.nx * sc.ny / wall,
+            "visitors_admitted": int(c["n_entered"]), "left_through_doors": int(c["n_left"]),
+            "evacuated": int(c["n_exited"]), "population_at_flood": st["population_at_flood"],
+            "evacuation_done_after_flood_s": st["evacuated_after_s"],
+            "peak_per_state": {k: int(hist[:, i].max()) if hist.size else 0
+                               for i, k in enumerate(("dry", "low", "medium", "high", "highest"))},
+            "per_minute": [(round(t / 60.0, 2), n, h) for t, n, h in st["samples"][::10]]}
+    # the oracle on the run's first steps (bounded), the GPU on the same steps
+    import oracle
+    oracle.build()
+    o = oracle.Oracle(make(1))
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < args.s1_cpu_seconds:
+        if o.step(8) < 8:
+            break
+        oc = o.flow_counts()
+        if o.t_ticks > int(pre * T) and o.counters()["wet"] and oc["n_active"] == 0:
+            break
+    cpu_wall = time.perf_counter() - t0
+    k = o.nstep
+    sim = P.from_scenario(make(1))
+    t0 = time.perf_counter()
+    run(sim, k)
+    gpu_wall = time.perf_counter() - t0
+    sim.close()
+    w = runs["with_coupling"]
+    line = {"metric": "scenario-seconds/s (Section 3.2 Scenario 1: entry/exit flow, flood, evacuation)",
+            "value": w["scenario_s_per_s"], "unit": "scenario-s/s", "n_gpus": 1, "steps": w["steps"],
+            "warmup": 256, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "scenario1_128 (128x128 cells of 2.59 m, 7 doors, one visitor per door every "
+                                   "%g s, 300 s pre-flood spread, (160 m^3/s, 7.5 min) discharge flood, to the last "
+                                   "evacuee out or 1 h)" % args.s1_period},
+            "runs": runs,
+            "cpu_baseline": {"value": o.t_ticks / T / cpu_wall, "unit": "scenario-s/s", "cores": 1, "kind": "oracle",
+                             "sample": "the run's first %d steps (t = 0 .. %.0f s)" % (k, o.t_ticks / T),
+                             "gpu_same_steps_s": gpu_wall, "cpu_s": cpu_wall}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_case(args):
     """A short run of one workload (the command line profiled under ncu): after
     an optional pre-run to a simulated time, the case's steps in the given
@@ -729,7 +826,11 @@ def main():
     ap.add_argument("--case-hash-ahead", type=int, default=1, choices=[0, 1], help="hash-ahead in the case")
     ap.add_argument("--case-time", type=float, default=0.0,
                     help="simulated seconds to run before the case's steps (profiler range opened after them)")
-    ap.add_argument("--workload", choices=["barrier2048", "ensemble", "surrogate", "deployment"], default="barrier2048")
+    ap.add_argument("--workload", choices=["barrier2048", "ensemble", "surrogate", "deployment", "scenario1"],
+                    default="barrier2048")
+    ap.add_argument("--s1-period", type=float, default=1.25,
+                    help="scenario1: seconds between admissions per door (1.25 s holds about 1000 visitors)")
+    ap.add_argument("--s1-cpu-seconds", type=float, default=15.0, help="scenario1: oracle sample length (s)")
     ap.add_argument("--deploy-flood-minutes", type=float, default=20.0)
     args = ap.parse_args()
     if args.ncu_case:
@@ -740,6 +841,8 @@ def main():
         return run_ensemble(args)
     if args.workload == "deployment":
         return run_deployment(args)
+    if args.workload == "scenario1":
+        return run_scenario1(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -315,14 +315,17 @@ def with_doors(s: Scenario, n_doors: int = 7, period: float = 6.0, v0=(1.0, 1.6)
 
 
 def scenario1(n: int = 128, dx: float = 2.59, pre_flood: float = 300.0, q_peak: float = 160.0,
-              t_inflow: float = 450.0, period: float = 6.0, coupling: int = 1, t_end: float = 3600.0,
+              t_inflow: float = 450.0, period: float = 1.25, coupling: int = 1, t_end: float = 3600.0,
               seed: int = 6, n_doors: int = 7) -> Scenario:
     """Scenario 1 (Section 3.2, during-flood evacuation) on the synthetic
     shopping centre at the paper's resolution: empty at t = 0, visitors enter
     through the doors during a pre-flood spread of ``pre_flood`` seconds (the
     paper's 5 minutes, Q = 0), then the (q_peak, t_inflow) triangular discharge
     flood enters through the south breach (depth 1 m); the first wet cell
-    stops the entries and turns everyone present into an evacuee."""
+    stops the entries and turns everyone present into an evacuee.  One visitor
+    per door every 1.25 s holds about the paper's 1000 pedestrians in this
+    layout by the flood's start (a visitor stays about 3 minutes; one every
+    6 s, 10 per door per minute, holds about 220)."""
     sc = shopping_centre(n, dx, 0, 0, seed, t_end, discharge=(q_peak, t_inflow), coupling=coupling)
     sc.q_t, sc.q_Q = triangular_discharge(q_peak, t_inflow, t_start=pre_flood)
     sc.name = "scenario1_%d" % n

@@ -76,11 +76,12 @@ def workload(seed):
 def launches_per_chunk(sc, hash_ahead):
     """Kernel launches of one benchmark step (CHUNK coupled steps after a
     restore): the first step opens with a hashing pass over all records
-    (hash_count, flood, scan, gather, pedestrian update: 5 launches); with the
-    records hashed ahead and no barrier to build, every later step is the
-    flood, scan, gather and pedestrian kernels alone (4), else 5."""
+    (hash_count, flood, the scan's two launches, gather, pedestrian update: 6
+    launches); with the records hashed ahead and no barrier to build, every
+    later step is the flood, scan, gather and pedestrian kernels alone (5),
+    else 6."""
     opening = (not hash_ahead) or (len(sc.barrier_cells) > 0 and sc.n_layers > 0)
-    return 5 + (CHUNK - 1) * (5 if opening else 4)
+    return 6 + (CHUNK - 1) * (6 if opening else 5)
 
 
 def combine_ranks(t_sec, updates, device):
@@ -179,7 +180,11 @@ class ClockSampler:
 
 # DRAM bytes per launch from ncu captures (dram__bytes_read.sum +
 # dram__bytes_write.sum), valid only for the kernel sources they were taken on.
-FLOOD_TRAFFIC = {"sources_sha256": None}
+# DRAM bytes (read + write) per flood-kernel launch from ncu captures of the
+# current kernel sources (profiles/flood_kernel_barrier2048mid_traffic.md,
+# profiles/flood_kernel_wet2048_ncu.md)
+FLOOD_TRAFFIC = {"sources_sha256": "db32320d73da4c08820bd24cd452f92987b5623b29567df7325e7b15229b95d6",
+                 "barrier_2048_midflood": 21724800, "wet_2048": 115236864}
 FLOOD_SOURCES = ("flood.cu", "flood_dev.cuh", "fp_common.cuh")
 
 
@@ -202,7 +207,7 @@ def oracle_steps(o, sc, n_steps, budget_s=None):
     early once budget_s seconds have been spent."""
     t_total, upd, k = 0.0, 0, 0
     for _ in range(n_steps):
-        active = int((o.pexit == 0).sum())
+        active = int(o.counters()["n_active"])
         t0 = time.perf_counter()
         dt = o.step_dt()
         t_total += time.perf_counter() - t0

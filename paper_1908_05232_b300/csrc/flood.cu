@@ -4,6 +4,11 @@
 // the FP64 water-volume reduction and the largest hazard rating.
 #include "flood_dev.cuh"
 
+#include <algorithm>
+#include <mutex>
+#include <utility>
+#include <vector>
+
 namespace {
 using namespace fpdev;
 
@@ -31,19 +36,37 @@ __global__ void __launch_bounds__(32 * kFloodWarps, 2) flood_batch_kernel(const 
     flood_acc_fold_warp(S, slot, acc);
 }
 
-// One warp per run of TY rows, each warp reading the step's constants and
-// folding its own tallies (no barrier: warps of a CTA finish apart); the
-// first warp advances the clock.
+// Runs of TY rows handed out one at a time from a ticket to whichever warp is
+// free (at most two CTAs per SM are launched, each warp looping): a run whose
+// groups stay dry costs a ticket and a flag test, a wet run a march of TY
+// rows, so where only part of the grid holds water every wet run still
+// starts at once, spread over all resident warps, instead of waiting behind
+// a static share of dry ones.  Each warp reads the step's constants and folds
+// its own tallies (no barrier: warps of a CTA finish apart); the first warp
+// advances the clock.  Every warp takes exactly one ticket past the last run;
+// the warp that takes the very last one resets the counter for the next
+// launch (no other warp touches it after that).
 template <int TY>
 __global__ void __launch_bounds__(32 * kFloodWarps, 2) flood_kernel(const __grid_constant__ FpSim S, int par,
                                                                  int slot) {
     fp_pdl_wait();
     const FloodStep st = flood_step_consts(S, slot);
-    const int w = blockIdx.x * kFloodWarps + (threadIdx.x >> 5);
-    if (w == 0 && threadIdx.x == 0) flood_clock_advance(S, slot, st);
-    const int nruns = ((S.nx + FP_TX - 1) / FP_TX) * ((S.ny + TY - 1) / TY);
+    const int lane = threadIdx.x & 31;
+    if (blockIdx.x == 0 && threadIdx.x == 0) flood_clock_advance(S, slot, st);
+    const unsigned nruns = (unsigned)(((S.nx + FP_TX - 1) / FP_TX) * ((S.ny + TY - 1) / TY));
+    const unsigned last = nruns + gridDim.x * kFloodWarps - 1u;
+    unsigned *ticket = &S.cnt->flood_ticket;
     FloodAcc acc = flood_acc_init();
-    for (int r = w; r < nruns; r += gridDim.x * kFloodWarps) flood_run<TY>(S, par, st, r, acc);
+    for (;;) {
+        unsigned r = 0u;
+        if (lane == 0) r = atomicAdd(ticket, 1u);
+        r = __shfl_sync(0xffffffffu, r, 0);
+        if (r >= nruns) {
+            if (lane == 0 && r == last) *ticket = 0u;
+            break;
+        }
+        flood_run<TY>(S, par, st, (int)r, acc);
+    }
     flood_acc_fold_warp(S, slot, acc);
 }
 
@@ -145,12 +168,26 @@ void fp_launch_flood_batch(const FpSim *d_sims, const int *d_run_off, int n, int
 
 cudaError_t fp_flood_init_attributes() { return cudaSuccess; }
 
-// One warp per run: the block scheduler hands runs to SMs as warps finish
-// (runs cost very different amounts: dry groups are skipped).
+// SMs of the current device, cached per device.
+static int device_sms() {
+    static std::mutex mu;
+    static std::vector<std::pair<int, int>> cache;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 148;
+    std::lock_guard<std::mutex> lock(mu);
+    for (const auto &e : cache)
+        if (e.first == dev) return e.second;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 148;
+    cache.emplace_back(dev, sms);
+    return sms;
+}
+
+// At most two CTAs per SM (the kernel's register budget), fewer for small grids.
 template <int TY>
 static void launch_flood_t(const FpSim &S, int par, int slot, cudaStream_t st, bool pdl) {
     const int nruns = ((S.nx + FP_TX - 1) / FP_TX) * ((S.ny + TY - 1) / TY);
-    const int grid = (nruns + kFloodWarps - 1) / kFloodWarps;
+    const int grid = std::min((nruns + kFloodWarps - 1) / kFloodWarps, 2 * device_sms());
     fp_launch(pdl, flood_kernel<TY>, dim3(grid), dim3(32 * kFloodWarps), 0, st, S, par, slot);
 }
 

@@ -268,6 +268,7 @@ static int prepare(fp_sim *s) {
     e = cudaMemcpyAsync(s->S.clock, ring, sizeof(ring), cudaMemcpyHostToDevice, s->stream);
     if (e != cudaSuccess) return s->cuda_fail(e, "clock write");
     e = s->reset_water_flags();
+    if (e == cudaSuccess) e = cudaMemsetAsync(&s->S.cnt->flood_ticket, 0, sizeof(unsigned), s->stream);
     if (e != cudaSuccess) return s->cuda_fail(e, "water flags");
     fp_launch_init_clock(s->S, s->par, s->slot, s->stream);
     e = cudaGetLastError();
@@ -558,7 +559,7 @@ int fp_sim_create(const fp_config *cfg, fp_sim **out) {
     ok &= (S.bin_start = s->dalloc<int>((size_t)S.nbins + 2)) != nullptr;
     ok &= (S.pkey = s->dalloc<int>(cap)) != nullptr;
     ok &= (S.pslot = s->dalloc<int>(cap)) != nullptr;
-    ok &= (S.scan_flags = s->dalloc<unsigned long long>((size_t)fp_scan_tiles(S.nbins))) != nullptr;
+    ok &= (S.tile_sum = s->dalloc<int>((size_t)fp_scan_tiles(S.nbins))) != nullptr;
     ok &= (S.bflux = s->dalloc<double>(2 * (size_t)c.nx + 2 * (size_t)c.ny)) != nullptr;
     ok &= (S.partials = s->dalloc<double>(148 * 4)) != nullptr;
     ok &= (S.scan_part = s->dalloc<int>(2048)) != nullptr;
@@ -1229,6 +1230,7 @@ static cudaError_t clear_device_error(fp_sim *s) {
     for (int p = 0; p < 2 && e == cudaSuccess; ++p)
         e = cudaMemsetAsync(S.occ[p], 0, s->plane_elems() * sizeof(unsigned short), s->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(&S.cnt->err, 0, sizeof(unsigned), s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(&S.cnt->flood_ticket, 0, sizeof(unsigned), s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     s->need_prepare = true;
     return e;

@@ -73,8 +73,6 @@ struct FpCounters {
     unsigned long long n_exited;
     unsigned long long neg_depth;
     unsigned int err;
-    unsigned int scan_epoch;          // increments once per hash build
-    unsigned int scan_ticket;         // dynamic tile order of the scan
     int bad_ped;
     unsigned long long hist[5];
     double mass;                      // last mass reduction (m^3)
@@ -86,6 +84,7 @@ struct FpCounters {
     int n_ids;                        // pedestrian ids issued (added or admitted through a door)
     unsigned long long n_entered;     // visitors admitted through the doors
     unsigned long long n_left;        // visitors gone through the door they were bound for
+    unsigned int flood_ticket;        // next run of the flood kernel in flight (0 between launches)
 };
 
 struct FpSim {
@@ -114,7 +113,7 @@ struct FpSim {
     int *bin_count;            // nbins + 1 (last = exited)
     int *bin_start;            // nbins + 2
     int *pkey, *pslot;         // per record of B
-    unsigned long long *scan_flags;  // per scan tile: epoch<<34 | status<<32 | value
+    int *tile_sum;             // per scan tile of 2048 bins: the sum of its counts
     double *bflux;             // 2 nx + 2 ny inflow volume per boundary face (S, N, W, E)
     double *partials;          // mass reduction partial sums
     int *scan_part;            // persistent kernel: bin-count total of each CTA's chunk

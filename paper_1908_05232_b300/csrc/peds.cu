@@ -4,9 +4,11 @@
 //   step_begin  the sandbag layers and bag snapshot alone, for a step whose
 //               records the previous pedestrian step already hashed (only
 //               where a barrier can be built);
-//   scan        single-pass exclusive scan of the bin counts (decoupled
-//               look-back, tiles in ticket order, bounded waits) -> bin starts;
-//               re-zeroes the counts; the exited bin's start is the new count;
+//   scan        exclusive scan of the bin counts in two launches: the sum
+//               of every tile of 2048 bins, then per tile the sum of the tiles
+//               before it and the tile's own scan -> bin starts (no atomics,
+//               no waits); re-zeroes the counts; the exited bin's start is the
+//               new count;
 //   gather      moves each record of B to its bin's range in A; exited
 //               records go to the by-id archive;
 //   ped_step    eight lanes per record of A (peds_dev.cuh); the first warp
@@ -17,15 +19,12 @@ namespace {
 using namespace fpdev;
 
 constexpr int kScanItems = 8, kScanThreads = 256, kScanTile = kScanItems * kScanThreads;
+static_assert(kScanItems == 8, "scan_load and scan_tile move a thread's bins as two int4");
 
 __global__ void hash_count_kernel(const __grid_constant__ FpSim S, int par) {
     fp_pdl_trigger();  // the scan may be scheduled now; it waits for this grid's end
     FpCounters *C = S.cnt;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        barrier_and_snapshot(S);
-        C->scan_epoch += 1u;
-        C->scan_ticket = 0u;
-    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) barrier_and_snapshot(S);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= S.cap) return;
     const uint4 pa = S.pedB[2 * i], pb = S.pedB[2 * i + 1];  // loaded beside the count
@@ -34,40 +33,71 @@ __global__ void hash_count_kernel(const __grid_constant__ FpSim S, int par) {
 }
 
 // The opening of a step whose records of B the previous pedestrian step hashed
-// as it wrote them: completed sandbag layers, the bag snapshot, a new scan epoch.
+// as it wrote them: completed sandbag layers and the bag snapshot.
 __global__ void step_begin_kernel(const __grid_constant__ FpSim S) {
     fp_pdl_trigger();  // the scan may be scheduled now; it waits for this grid's end
-    FpCounters *C = S.cnt;
-    const unsigned epoch = C->scan_epoch;  // loaded beside the bag counters
     barrier_and_snapshot(S);
-    C->scan_epoch = epoch + 1u;
-    C->scan_ticket = 0u;
 }
 
-// status word: epoch (30 bits) << 34 | status (1 aggregate, 2 inclusive prefix) << 32 | value
-__device__ __forceinline__ void scan_tile(const FpSim &S) {
-    __shared__ int s_tile, s_prefix;
+// The counts of this thread's kScanItems consecutive bins of tile `tile`
+// (0 past the last bin), two 16-byte loads where the tile is whole.
+__device__ __forceinline__ void scan_load(const FpSim &S, int base, int n, int v[kScanItems]) {
+    if (base + kScanItems <= n) {
+        const int4 a = *reinterpret_cast<const int4 *>(S.bin_count + base);
+        const int4 b = *reinterpret_cast<const int4 *>(S.bin_count + base + 4);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+        v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    } else {
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) v[k] = base + k < n ? S.bin_count[base + k] : 0;
+    }
+}
+
+// Block sum of one int per thread (every thread gets it).
+__device__ __forceinline__ int block_sum(int x) {
+    __shared__ int s_red[kScanThreads / 32];
+    __shared__ int s_tot;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = 0;
+        for (int w = 0; w < kScanThreads / 32; ++w) t += s_red[w];
+        s_tot = t;
+    }
+    __syncthreads();
+    return s_tot;
+}
+
+// First launch: the sum of the counts of tile `tile`.
+__device__ __forceinline__ void scan_sum_tile(const FpSim &S, int tile) {
+    int v[kScanItems];
+    scan_load(S, tile * kScanTile + threadIdx.x * kScanItems, S.nbins + 1, v);
+    int sum = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) sum += v[k];
+    const int total = block_sum(sum);
+    if (threadIdx.x == 0) S.tile_sum[tile] = total;
+}
+
+// Second launch: the tile's exclusive prefix is the sum of the tiles before
+// it (all written by the first launch); then the tile's own exclusive scan.
+__device__ __forceinline__ void scan_tile(const FpSim &S, int tile) {
     __shared__ int s_warp[kScanThreads / 32];
     const int tid = threadIdx.x;
     FpCounters *C = S.cnt;
-    if (tid == 0) s_tile = (int)atomicAdd(&C->scan_ticket, 1u);
-    __syncthreads();
-    const int tile = s_tile;
     if (tile == 0 && tid < 5) C->hist[tid] = 0ull;  // the step's state histogram (the pedestrian kernel fills it)
     const int n = S.nbins + 1;
-    const unsigned long long epoch = (unsigned long long)(C->scan_epoch & 0x3fffffffu);
     const int base = tile * kScanTile + tid * kScanItems;
+    int part = 0;
+    for (int t = tid; t < tile; t += kScanThreads) part += S.tile_sum[t];
     int v[kScanItems];
+    scan_load(S, base, n, v);
+    const int prefix = block_sum(part);
     int sum = 0;
 #pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-        const int idx = base + k;
-        v[k] = idx < n ? S.bin_count[idx] : 0;
-        sum += v[k];
-    }
-#pragma unroll
-    for (int k = 0; k < kScanItems; ++k)
-        if (base + k < n) S.bin_count[base + k] = 0;
+    for (int k = 0; k < kScanItems; ++k) sum += v[k];
     // block exclusive scan of the per-thread sums
     const int lane = tid & 31, wid = tid >> 5;
     int incl = sum;
@@ -78,76 +108,48 @@ __device__ __forceinline__ void scan_tile(const FpSim &S) {
     }
     if (lane == 31) s_warp[wid] = incl;
     __syncthreads();
-    int wpre = 0, total = 0;
-    for (int w = 0; w < kScanThreads / 32; ++w) {
-        if (w < wid) wpre += s_warp[w];
-        total += s_warp[w];
-    }
-    // warp-parallel decoupled look-back: lane l inspects predecessor tile - 1 - l
-    // (and the window moves back by 32 while none of them has its inclusive prefix)
-    if (wid == 0) {
-        volatile unsigned long long *flags = S.scan_flags;
-        int excl = 0;
-        if (tile == 0) {
-            if (lane == 0) flags[0] = (epoch << 34) | (2ull << 32) | (unsigned)total;
-        } else {
-            if (lane == 0) {
-                flags[tile] = (epoch << 34) | (1ull << 32) | (unsigned)total;
-                __threadfence();
-            }
-            __syncwarp();
-            int t = tile - 1 - lane;
-            bool timed_out = false;
-            while (true) {
-                unsigned long long w = 0;
-                unsigned st = 2u;  // tiles before 0: an inclusive prefix of 0
-                if (t >= 0) {
-                    int it = 0;
-                    for (; it < (1 << 22); ++it) {
-                        w = flags[t];
-                        st = (unsigned)(w >> 32) & 3u;
-                        if ((w >> 34) == epoch && st != 0u) break;
-                    }
-                    if (it == (1 << 22)) { timed_out = true; w = 0; st = 2u; }
-                }
-                const int val = t >= 0 ? (int)(unsigned)(w & 0xffffffffull) : 0;
-                const unsigned pmask = __ballot_sync(0xffffffffu, st == 2u);
-                const int last = pmask ? __ffs(pmask) - 1 : 31;  // nearest predecessor with a prefix
-                int part = lane <= last ? val : 0;
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-                excl += part;
-                if (pmask) break;
-                t -= 32;
-            }
-            if (__any_sync(0xffffffffu, timed_out) && lane == 0) fp_set_err(S, FP_ERR_TIMEOUT);
-            if (lane == 0) {
-                __threadfence();
-                flags[tile] = (epoch << 34) | (2ull << 32) | (unsigned)(excl + total);
-            }
-        }
-        if (lane == 0) s_prefix = excl;
-    }
-    __syncthreads();
-    int run = s_prefix + wpre + incl - sum;
+    int wpre = 0;
+    for (int w = 0; w < wid; ++w) wpre += s_warp[w];
+    int run = prefix + wpre + incl - sum;
+    int out[kScanItems];
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
-        const int idx = base + k;
-        if (idx < n) {
-            S.bin_start[idx] = run;
-            if (idx == n - 1) {
-                S.bin_start[n] = run + v[k];
-                C->nA = run;  // records before the exited bin
-            }
-        }
+        out[k] = run;
         run += v[k];
     }
+    if (base + kScanItems <= n) {
+        const int4 z = make_int4(0, 0, 0, 0);
+        *reinterpret_cast<int4 *>(S.bin_count + base) = z;
+        *reinterpret_cast<int4 *>(S.bin_count + base + 4) = z;
+        *reinterpret_cast<int4 *>(S.bin_start + base) = make_int4(out[0], out[1], out[2], out[3]);
+        *reinterpret_cast<int4 *>(S.bin_start + base + 4) = make_int4(out[4], out[5], out[6], out[7]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k)
+            if (base + k < n) {
+                S.bin_count[base + k] = 0;
+                S.bin_start[base + k] = out[k];
+            }
+    }
+    // the exited bin (the last) starts where the records still present end
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k)
+        if (base + k == n - 1) {
+            S.bin_start[n] = out[k] + v[k];
+            C->nA = out[k];
+        }
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_sum_kernel(const __grid_constant__ FpSim S) {
+    fp_pdl_wait();     // the step's opening kernel (the counts)
+    fp_pdl_trigger();  // the scan may be scheduled now; it waits for this grid's end
+    scan_sum_tile(S, blockIdx.x);
 }
 
 __global__ void __launch_bounds__(kScanThreads) scan_kernel(const __grid_constant__ FpSim S) {
-    fp_pdl_wait();     // the step's opening kernel (counts, scan epoch and ticket)
+    fp_pdl_wait();     // the tile sums
     fp_pdl_trigger();  // the gather may be scheduled now; it waits for this grid's end
-    scan_tile(S);
+    scan_tile(S, blockIdx.x);
 }
 
 __device__ __forceinline__ void gather_record(const FpSim &S, int i) {
@@ -216,9 +218,6 @@ __global__ void __launch_bounds__(256) ped_step_kernel(const __grid_constant__ F
         ctl0.nA = C->nA;
         s_ctl = ctl0;
         if (blockIdx.x == 0) {
-            // this step's scan is over: a new epoch and ticket for the next one
-            C->scan_epoch += 1u;
-            C->scan_ticket = 0u;
             C->nB = ctl0.nA;
             if (ctl0.dt_ticks > 0) C->ped_updates += (unsigned long long)ctl0.nA;
         }
@@ -290,20 +289,22 @@ __global__ void hash_count_batch_kernel(const FpSim *__restrict__ sims, const in
     const FpSim &S = sims[s];
     FpCounters *C = S.cnt;
     const int i = blockIdx.x * blockDim.x + threadIdx.x - rec_off[s];
-    if (i == 0) {
-        barrier_and_snapshot(S);
-        C->scan_epoch += 1u;
-        C->scan_ticket = 0u;
-    }
+    if (i == 0) barrier_and_snapshot(S);
     if (i >= C->nB) return;
     const uint4 pa = S.pedB[2 * i], pb = S.pedB[2 * i + 1];
     hash_record(S, i, __uint_as_float(pa.x), __uint_as_float(pa.y), pb.y, S.occ[par]);
 }
 
+__global__ void __launch_bounds__(kScanThreads) scan_sum_batch_kernel(const FpSim *__restrict__ sims) {
+    const FpSim &S = sims[blockIdx.y];
+    if ((int)blockIdx.x >= (S.nbins + 1 + kScanTile - 1) / kScanTile) return;
+    scan_sum_tile(S, blockIdx.x);
+}
+
 __global__ void __launch_bounds__(kScanThreads) scan_batch_kernel(const FpSim *__restrict__ sims) {
     const FpSim &S = sims[blockIdx.y];
     if ((int)blockIdx.x >= (S.nbins + 1 + kScanTile - 1) / kScanTile) return;
-    scan_tile(S);
+    scan_tile(S, blockIdx.x);
 }
 
 __global__ void gather_batch_kernel(const FpSim *__restrict__ sims, const int *__restrict__ rec_off, int n) {
@@ -345,6 +346,7 @@ void fp_launch_batch_peds(const FpSim *d_sims, const int *d_rec_off, int n, int 
         cudaEventRecord(fork, st_hash);
         return;
     }
+    scan_sum_batch_kernel<<<dim3(max_scan_tiles, n), kScanThreads, 0, st_chain>>>(d_sims);
     scan_batch_kernel<<<dim3(max_scan_tiles, n), kScanThreads, 0, st_chain>>>(d_sims);
     gather_batch_kernel<<<total_rec / 256, 256, 0, st_chain>>>(d_sims, d_rec_off, n);
     ped_step_batch_kernel<<<total_rec * kGroup / 256, 256, 0, st_chain>>>(d_sims, d_rec_off, n, par, slot);
@@ -356,6 +358,7 @@ void fp_launch_hash_count(const FpSim &S, int par, cudaStream_t st) {
     hash_count_kernel<<<blocks_for(S.cap, 256), 256, 0, st>>>(S, par);
 }
 void fp_launch_scan(const FpSim &S, cudaStream_t st, bool pdl) {
+    fp_launch(pdl, scan_sum_kernel, dim3(fp_scan_tiles(S.nbins)), dim3(kScanThreads), 0, st, S);
     fp_launch(pdl, scan_kernel, dim3(fp_scan_tiles(S.nbins)), dim3(kScanThreads), 0, st, S);
 }
 void fp_launch_gather(const FpSim &S, cudaStream_t st, bool pdl) {

@@ -403,6 +403,7 @@ def config_barrier_midflood(seed=3, t0=1500.0, reach_m=300.0, depth_m=1.0, speed
     eta = depth_m * np.clip(1.0 - d / reach_m, 0.0, None)
     h = np.maximum(eta - s.z.astype(np.float64), 0.0)
     h[s.z >= 1.0] = 0.0          # walls and shop blocks
+    h[d >= reach_m] = 0.0        # beyond the front the floor is dry (no water in the bed noise's hollows)
     sp = speed_m_s * np.clip(1.0 - d / reach_m, 0.0, None)
     ux = np.where(d > 0, (x - xc) / np.maximum(d, 1e-9), 0.0) * sp
     uy = np.where(d > 0, y / np.maximum(d, 1e-9), 0.0) * sp

@@ -286,8 +286,8 @@ static void launch_step(fp_sim *s, int par, int slot, cudaEvent_t *ev = nullptr)
     const FpSim &S = s->S;
     if (ev) cudaEventRecordWithFlags(ev[0], s->stream, cudaEventRecordExternal);
     // With the records hashed ahead, a step opens with step_begin only where a
-    // barrier can be built (sandbag layers, bag snapshot); the pedestrian
-    // kernel starts the next scan's epoch and the scan clears the histogram.
+    // barrier can be built (sandbag layers, bag snapshot); the scan clears the
+    // histogram.
     const bool opening = !s->hashed || (S.nb > 0 && S.n_layers > 0);
     if (!s->hashed) fp_launch_hash_count(S, par, s->stream);
     else if (opening) fp_launch_step_begin(S, s->stream);
@@ -302,7 +302,7 @@ static void launch_step(fp_sim *s, int par, int slot, cudaEvent_t *ev = nullptr)
     fp_launch_flood(S, par, slot, s->tile_rows, s->stream2);
     if (ev) cudaEventRecordWithFlags(ev[2], s->stream2, cudaEventRecordExternal);
     fp_launch_scan(S, s->stream, pdl);
-    fp_launch_gather(S, s->stream, pdl);
+    fp_launch_gather(S, slot, s->stream, pdl);
     if (ev) cudaEventRecordWithFlags(ev[5], s->stream, cudaEventRecordExternal);
     fp_launch_ped_step(S, par, slot, s->ped_lanes, s->stream, pdl, s->hash_ahead);
     if (ev) cudaEventRecordWithFlags(ev[3], s->stream, cudaEventRecordExternal);
@@ -324,7 +324,7 @@ static void launch_window_step(fp_sim *s, int par, int slot) {
     fp_launch_clock_advance(S, slot, s->stream);
     cudaMemsetAsync(S.occ[par], 0, s->plane_elems() * sizeof(unsigned short), s->stream);
     fp_launch_scan(S, s->stream2);
-    fp_launch_gather(S, s->stream2);
+    fp_launch_gather(S, slot, s->stream2);
     fp_launch_ped_step(S, par, slot, s->ped_lanes, s->stream2);
     cudaEventRecord(s->ev_join, s->stream2);
     cudaStreamWaitEvent(s->stream, s->ev_join, 0);
@@ -552,6 +552,7 @@ int fp_sim_create(const fp_config *cfg, fp_sim **out) {
     const size_t cap = (size_t)std::max(1, c.max_peds);
     ok &= (S.pedA = s->dalloc<uint4>(2 * cap)) != nullptr;
     ok &= (S.posA = s->dalloc<float2>(cap)) != nullptr;
+    ok &= (S.xiA = s->dalloc<float2>(cap)) != nullptr;
     ok &= (S.pedB = s->dalloc<uint4>(2 * cap)) != nullptr;
     ok &= (S.arch = s->dalloc<uint4>(2 * cap)) != nullptr;
     ok &= (s->read_buf = s->dalloc<uint4>(2 * cap)) != nullptr;

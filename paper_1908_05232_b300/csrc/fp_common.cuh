@@ -109,6 +109,7 @@ struct FpSim {
     FpCounters *cnt;
     uint4 *pedA, *pedB;        // 2 x uint4 per record
     float2 *posA;              // positions of the records of A (the neighbour scans read these)
+    float2 *xiA;               // the step's two uniform draws of each record of A (written by the gather)
     uint4 *arch;               // records by id (exited ones)
     int *bin_count;            // nbins + 1 (last = exited)
     int *bin_start;            // nbins + 2
@@ -280,6 +281,16 @@ __device__ __forceinline__ void fp_philox4x64(unsigned long long c[4], unsigned 
     }
 }
 
+// A pedestrian's two uniform draws of a step (the random term of its desired
+// velocity): the top 24 bits of the first two words of the generator's block
+// at counter (id, step, 0, 0), exact in FP32.
+__device__ __forceinline__ float2 fp_step_draws(const FpSim &S, unsigned id, long long step) {
+    unsigned long long ctr[4] = {(unsigned long long)id, (unsigned long long)step, 0ull, 0ull};
+    fp_philox4x64(ctr, S.seed, 0ull);
+    return make_float2((float)(unsigned)(ctr[0] >> 40) * (1.0f / 16777216.0f),
+                       (float)(unsigned)(ctr[1] >> 40) * (1.0f / 16777216.0f));
+}
+
 __device__ __forceinline__ void fp_set_err(const FpSim &S, unsigned int bit) { atomicOr(&S.cnt->err, bit); }
 
 // launchers (defined in flood.cu / peds.cu)
@@ -290,7 +301,7 @@ void fp_launch_hr_max(const FpSim &S, int par, cudaStream_t st);
 cudaError_t fp_flood_init_attributes();
 void fp_launch_hash_count(const FpSim &S, int par, cudaStream_t st);
 void fp_launch_scan(const FpSim &S, cudaStream_t st, bool pdl = false);
-void fp_launch_gather(const FpSim &S, cudaStream_t st, bool pdl = false);
+void fp_launch_gather(const FpSim &S, int slot, cudaStream_t st, bool pdl = false);
 void fp_launch_ped_step(const FpSim &S, int par, int slot, int lanes, cudaStream_t st, bool pdl = false,
                         bool hash_next = false);
 void fp_launch_step_begin(const FpSim &S, cudaStream_t st);

@@ -152,47 +152,50 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(const __grid_constan
     scan_tile(S, blockIdx.x);
 }
 
-__device__ __forceinline__ void gather_record(const FpSim &S, int i) {
-    const int key = S.pkey[i];
-    const uint4 a = S.pedB[2 * i], b = S.pedB[2 * i + 1];
+// Record i of B to its place in A (or, gone, to the by-id archive), with the
+// step's two uniform draws the pedestrian kernel reads beside it.
+__device__ __forceinline__ void gather_place(const FpSim &S, int key, int bslot, const uint4 &a, const uint4 &b,
+                                             float2 xi) {
     if (key == S.nbins) {
         S.arch[2 * (size_t)b.x] = a;
         S.arch[2 * (size_t)b.x + 1] = b;
     } else {
-        const int dst = S.bin_start[key] + S.pslot[i];
+        const int dst = S.bin_start[key] + bslot;
         S.pedA[2 * dst] = a;
         S.pedA[2 * dst + 1] = b;
         S.posA[dst] = make_float2(__uint_as_float(a.x), __uint_as_float(a.y));
+        S.xiA[dst] = xi;
     }
 }
 
-__global__ void gather_kernel(const __grid_constant__ FpSim S) {
-    // The record, its key and slot and the record count come from kernels
-    // that finished before the scan began: loaded before waiting for the
-    // scan (the arrays hold cap entries; the count is checked after).
+__device__ __forceinline__ void gather_record(const FpSim &S, int i, long long step) {
+    const int key = S.pkey[i];
+    const uint4 a = S.pedB[2 * i], b = S.pedB[2 * i + 1];
+    gather_place(S, key, S.pslot[i], a, b, fp_step_draws(S, b.x, step));
+}
+
+__global__ void gather_kernel(const __grid_constant__ FpSim S, int slot) {
+    // The record, its key and slot, the record count and the step index come
+    // from kernels that finished before the scan began: loaded, and the
+    // record's draws computed, before waiting for the scan (the arrays hold
+    // cap entries; the count is checked after).
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const bool in = i < S.cap;
     const int nB = S.cnt->nB;
-    int key = 0, slot = 0;
+    const long long step = S.clock[slot].step;
+    int key = 0, bslot = 0;
     uint4 a = make_uint4(0u, 0u, 0u, 0u), b = a;
     if (in) {
         key = S.pkey[i];
-        slot = S.pslot[i];
+        bslot = S.pslot[i];
         a = S.pedB[2 * i];
         b = S.pedB[2 * i + 1];
     }
+    const float2 xi = fp_step_draws(S, b.x, step);
     fp_pdl_wait();
     fp_pdl_trigger();
     if (!in || i >= nB) return;
-    if (key == S.nbins) {
-        S.arch[2 * (size_t)b.x] = a;
-        S.arch[2 * (size_t)b.x + 1] = b;
-    } else {
-        const int dst = S.bin_start[key] + slot;
-        S.pedA[2 * dst] = a;
-        S.pedA[2 * dst + 1] = b;
-        S.posA[dst] = make_float2(__uint_as_float(a.x), __uint_as_float(a.y));
-    }
+    gather_place(S, key, bslot, a, b, xi);
 }
 
 struct DirectLookup {
@@ -205,25 +208,20 @@ struct DirectLookup {
 template <int kG>
 __global__ void __launch_bounds__(256) ped_step_kernel(const __grid_constant__ FpSim S, int par, int slot,
                                                        int hash_next) {
-    __shared__ StepCtl s_ctl;
     FpCounters *C = S.cnt;
     // the clock and the bag snapshot come from kernels that finished before
-    // the scan began: read (and the time step computed) before waiting for the
-    // gather; the record count is the scan's
-    StepCtl ctl0;
-    if (threadIdx.x == 0) load_step_ctl(S, slot, 0, ctl0);
+    // the scan began: read (and the time step computed) by every thread before
+    // waiting for the gather -- the same addresses, so one transaction per warp
+    // and no block barrier; the record count is the scan's
+    StepCtl ctl;
+    load_step_ctl(S, slot, 0, ctl);
     fp_pdl_wait();
     fp_pdl_trigger();  // the next step's scan may be scheduled; it waits for this grid's end
-    if (threadIdx.x == 0) {
-        ctl0.nA = C->nA;
-        s_ctl = ctl0;
-        if (blockIdx.x == 0) {
-            C->nB = ctl0.nA;
-            if (ctl0.dt_ticks > 0) C->ped_updates += (unsigned long long)ctl0.nA;
-        }
+    ctl.nA = C->nA;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        C->nB = ctl.nA;
+        if (ctl.dt_ticks > 0) C->ped_updates += (unsigned long long)ctl.nA;
     }
-    __syncthreads();
-    const StepCtl ctl = s_ctl;
     const int gt = blockIdx.x * blockDim.x + threadIdx.x;
     ped_group<kG>(S, par, ctl, gt / kG, threadIdx.x & (kG - 1), DirectLookup{S.bin_start}, hash_next != 0);
     if (blockIdx.x == 0 && threadIdx.x < 32) door_entries(S, par, ctl, hash_next != 0);
@@ -307,11 +305,12 @@ __global__ void __launch_bounds__(kScanThreads) scan_batch_kernel(const FpSim *_
     scan_tile(S, blockIdx.x);
 }
 
-__global__ void gather_batch_kernel(const FpSim *__restrict__ sims, const int *__restrict__ rec_off, int n) {
+__global__ void gather_batch_kernel(const FpSim *__restrict__ sims, const int *__restrict__ rec_off, int n,
+                                    int slot) {
     const int s = batch_member(rec_off, n, blockIdx.x * blockDim.x);
     const FpSim &S = sims[s];
     const int i = blockIdx.x * blockDim.x + threadIdx.x - rec_off[s];
-    if (i < S.cnt->nB) gather_record(S, i);
+    if (i < S.cnt->nB) gather_record(S, i, S.clock[slot].step);
 }
 
 __global__ void __launch_bounds__(256) ped_step_batch_kernel(const FpSim *__restrict__ sims,
@@ -348,7 +347,7 @@ void fp_launch_batch_peds(const FpSim *d_sims, const int *d_rec_off, int n, int 
     }
     scan_sum_batch_kernel<<<dim3(max_scan_tiles, n), kScanThreads, 0, st_chain>>>(d_sims);
     scan_batch_kernel<<<dim3(max_scan_tiles, n), kScanThreads, 0, st_chain>>>(d_sims);
-    gather_batch_kernel<<<total_rec / 256, 256, 0, st_chain>>>(d_sims, d_rec_off, n);
+    gather_batch_kernel<<<total_rec / 256, 256, 0, st_chain>>>(d_sims, d_rec_off, n, slot);
     ped_step_batch_kernel<<<total_rec * kGroup / 256, 256, 0, st_chain>>>(d_sims, d_rec_off, n, par, slot);
 }
 
@@ -361,8 +360,8 @@ void fp_launch_scan(const FpSim &S, cudaStream_t st, bool pdl) {
     fp_launch(pdl, scan_sum_kernel, dim3(fp_scan_tiles(S.nbins)), dim3(kScanThreads), 0, st, S);
     fp_launch(pdl, scan_kernel, dim3(fp_scan_tiles(S.nbins)), dim3(kScanThreads), 0, st, S);
 }
-void fp_launch_gather(const FpSim &S, cudaStream_t st, bool pdl) {
-    fp_launch(pdl, gather_kernel, dim3(blocks_for(S.cap, 256)), dim3(256), 0, st, S);
+void fp_launch_gather(const FpSim &S, int slot, cudaStream_t st, bool pdl) {
+    fp_launch(pdl, gather_kernel, dim3(blocks_for(S.cap, 256)), dim3(256), 0, st, S, slot);
 }
 void fp_launch_step_begin(const FpSim &S, cudaStream_t st) { step_begin_kernel<<<1, 1, 0, st>>>(S); }
 void fp_launch_ped_step(const FpSim &S, int par, int slot, int lanes, cudaStream_t st, bool pdl, bool hash_next) {

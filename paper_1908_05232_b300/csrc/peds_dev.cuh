@@ -214,17 +214,12 @@ __device__ __forceinline__ void ped_group(const FpSim &S, int par, const StepCtl
             cj = fp_cell_of(y, dx);
             const int c = cj * S.nx + ci;
             const size_t pc = fp_pidx(S, ci, cj);
-            // independent loads issued together: the cell's water, the 3 x 3 bin ranges
+            // independent loads issued together: the cell's water, the step's
+            // two uniform draws (fp_step_draws on id and step, computed by the
+            // gather that placed the record), the 3 x 3 bin ranges
             const float hc = S.h[par][pc], huc = S.hu[par][pc], hvc = S.hv[par][pc];
-            // the step's two uniform draws for this pedestrian (Philox4x64 on id
-            // and step), computed while the loads above are in flight
-            float xi1, xi2;
-            {
-                unsigned long long ctr[4] = {(unsigned long long)id, (unsigned long long)ctl.step, 0ull, 0ull};
-                fp_philox4x64(ctr, S.seed, 0ull);
-                xi1 = (float)(unsigned)(ctr[0] >> 40) * (1.0f / 16777216.0f);
-                xi2 = (float)(unsigned)(ctr[1] >> 40) * (1.0f / 16777216.0f);
-            }
+            const float2 xi = S.xiA[j];
+            const float xi1 = xi.x, xi2 = xi.y;
             {
                 const int bx = ci / S.hk, by = cj / S.hk;
                 const int bx0 = bx > 0 ? bx - 1 : 0, bx1 = bx + 1 < S.nbx ? bx + 1 : S.nbx - 1;

@@ -203,6 +203,7 @@ __global__ void __launch_bounds__(kPT, 1) persistent_kernel(const __grid_constan
                     S.pedA[2 * dst] = a;
                     S.pedA[2 * dst + 1] = b;
                     S.posA[dst] = make_float2(__uint_as_float(a.x), __uint_as_float(a.y));
+                    S.xiA[dst] = fp_step_draws(S, b.x, S.clock[slot].step);
                 }
             }
         }

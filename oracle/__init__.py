@@ -107,6 +107,7 @@ class _Params(ctypes.Structure):
         ("riemann", ctypes.c_int32),
         ("n_doors", ctypes.c_int32), ("n_door_cells", ctypes.c_int32), ("door_cells", _P), ("door_of", _P),
         ("entry_period_ticks", ctypes.c_int64), ("entry_v0_lo", ctypes.c_double), ("entry_v0_hi", ctypes.c_double),
+        ("order", ctypes.c_int32),
     ]
 
 
@@ -188,6 +189,7 @@ class Oracle:
         P.entry_period_ticks = int(round(float(getattr(sc, "entry_period", 6.0)) * TICKS))
         v0 = getattr(sc, "entry_v0", (1.4, 1.4))
         P.entry_v0_lo, P.entry_v0_hi = _f32(v0[0]), _f32(v0[1])
+        P.order = int(getattr(sc, "order", 1))
         self.P = P
         n = nx * ny
         self.h = keep(np.asarray(sc.h, np.float64).reshape(-1).copy())

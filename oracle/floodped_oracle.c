@@ -17,7 +17,11 @@
  *     is read as a Godunov-type scheme with non-negative hydrostatic
  *     reconstruction of the face depths and the HLL Riemann solver (HLLC,
  *     which also resolves the contact wave, as an option: the cited scheme's
- *     three-wave solver).
+ *     three-wave solver).  The cited scheme at full order, as an option: MUSCL
+ *     reconstruction of the surface, the depth and the velocities (minmod
+ *     slopes, first order next to dry cells and on the domain edge), the
+ *     hydrostatic reconstruction at the faces with the centred bed-slope term
+ *     that keeps a lake at rest, and two-stage Runge-Kutta time stepping.
  *   - Section 3 (CFL-adaptive time step when wet, 1.0 s pedestrian step when
  *     dry); Section 3.1 inflow: a depth hydrograph (ghost state) or the
  *     paper's triangular discharge hydrograph Q(t) entering through a breach
@@ -122,6 +126,7 @@ typedef struct {
     const int32_t *door_of;      /* the door of each listed cell */
     int64_t entry_period_ticks;  /* each door admits one visitor every this many ticks */
     double entry_v0_lo, entry_v0_hi;  /* visitors' dry walking speeds (FP32 values, m/s) */
+    int32_t order;            /* 2: the second-order (MUSCL, two-stage) scheme; else first order */
 } or_params;
 
 typedef struct {
@@ -581,6 +586,202 @@ void or_flood_step(const or_params *P, or_state *S, int64_t dt_ticks, const doub
 }
 
 /* ------------------------------------------------------------------------ */
+/* Second order (the cited scheme at full order; a build-added option).      */
+/* Per direction and cell: minmod slopes of the surface eta = h + z, of h    */
+/* and of the velocities u, v -- zero on the domain edge and where the cell  */
+/* or a neighbour along that direction is dry -- give face values            */
+/* eta_f = eta +- s_eta/2, h_f = h +- s_h/2, z_f = eta_f - h_f, u_f, v_f.    */
+/* At a face z* = max(z_L, z_R), h*_{L,R} = max(0, eta_{L,R} - z*), the same */
+/* Riemann flux, and each cell takes it minus the pressure 1/2 g h*^2 of its */
+/* own side (as at first order); the cell adds the centred bed-slope term    */
+/* -g/2 (h_+ + h_-)(eta_+ - eta_-), in which the reconstructed pressure      */
+/* difference and the bed slope between the cell's two faces combine (so a  */
+/* lake at rest, eta constant, stays exactly at rest).  Time: two Euler       */
+/* stages, each followed by the point-implicit friction, and the mean of the */
+/* start state and the second stage's result (SSP-RK2); the second stage    */
+/* takes the inflow depth of t + dt; each stage adds half its boundary      */
+/* volumes.  With all slopes zero a stage is exactly the first-order step.  */
+/* ------------------------------------------------------------------------ */
+static double or_minmod(double a, double b) {
+    if (a > 0.0 && b > 0.0) return a < b ? a : b;
+    if (a < 0.0 && b < 0.0) return a > b ? a : b;
+    return 0.0;
+}
+
+/* face values of one cell along one direction: minus side [0], plus side [1] */
+typedef struct { double eta[2], h[2], u[2], v[2]; } or_faces;
+
+static void or_cell_faces(const double *z, const double *h, const double *hu, const double *hv, int64_t c,
+                          int64_t cm, int64_t cp, int slope, or_faces *F) {
+    double hc = h[c], uc = 0.0, vc = 0.0;
+    if (hc > OR_H_EPS) { uc = hu[c] / hc; vc = hv[c] / hc; }
+    double eta = hc + z[c];
+    double se = 0.0, sh = 0.0, su = 0.0, sv = 0.0;
+    if (slope && hc > OR_H_EPS && h[cm] > OR_H_EPS && h[cp] > OR_H_EPS) {
+        double um = hu[cm] / h[cm], vm = hv[cm] / h[cm], up = hu[cp] / h[cp], vp = hv[cp] / h[cp];
+        se = or_minmod((h[cp] + z[cp]) - eta, eta - (h[cm] + z[cm]));
+        sh = or_minmod(h[cp] - hc, hc - h[cm]);
+        su = or_minmod(up - uc, uc - um);
+        sv = or_minmod(vp - vc, vc - vm);
+    }
+    F->eta[0] = eta - 0.5 * se; F->eta[1] = eta + 0.5 * se;
+    F->h[0] = hc - 0.5 * sh;    F->h[1] = hc + 0.5 * sh;
+    F->u[0] = uc - 0.5 * su;    F->u[1] = uc + 0.5 * su;
+    F->v[0] = vc - 0.5 * sv;    F->v[1] = vc + 0.5 * sv;
+}
+
+/* one stage: (ho, huo, hvo) = friction(U + dt L(U)) */
+static void or_muscl_stage(const or_params *P, const double *z, const double *h, const double *hu, const double *hv,
+                           double *ho, double *huo, double *hvo, double dt, double h_in, double qb, double u_in,
+                           const double *n_eff, double *bflux, int64_t *neg) {
+    const int32_t nx = P->nx, ny = P->ny;
+    const int64_t n = (int64_t)nx * ny;
+    const double dx = P->dx, g = P->g;
+    or_faces *FX = (or_faces *)malloc(sizeof(or_faces) * (size_t)n);
+    or_faces *FY = (or_faces *)malloc(sizeof(or_faces) * (size_t)n);
+    for (int32_t j = 0; j < ny; ++j)
+        for (int32_t i = 0; i < nx; ++i) {
+            int64_t c = (int64_t)j * nx + i;
+            or_cell_faces(z, h, hu, hv, c, i > 0 ? c - 1 : c, i < nx - 1 ? c + 1 : c, i > 0 && i < nx - 1, &FX[c]);
+            or_cell_faces(z, h, hu, hv, c, j > 0 ? c - nx : c, j < ny - 1 ? c + nx : c, j > 0 && j < ny - 1, &FY[c]);
+        }
+    double *FE = (double *)calloc((size_t)n * 3, sizeof(double));
+    double *FW = (double *)calloc((size_t)n * 3, sizeof(double));
+    double *GN = (double *)calloc((size_t)n * 3, sizeof(double));
+    double *GS = (double *)calloc((size_t)n * 3, sizeof(double));
+    double f[3];
+    /* x faces: face i between cell i-1 (its plus side) and cell i (its minus side) */
+    for (int32_t j = 0; j < ny; ++j) {
+        for (int32_t i = 0; i <= nx; ++i) {
+            double eL, hL, uL, vL, eR, hR, uR, vR;
+            if (i > 0) {
+                const or_faces *A = &FX[(int64_t)j * nx + i - 1];
+                eL = A->eta[1]; hL = A->h[1]; uL = A->u[1]; vL = A->v[1];
+            }
+            if (i < nx) {
+                const or_faces *B = &FX[(int64_t)j * nx + i];
+                eR = B->eta[0]; hR = B->h[0]; uR = B->u[0]; vR = B->v[0];
+            }
+            if (i == 0 || i == nx) {  /* edge cells have no slope: the ghost of the cell state */
+                or_side in;
+                if (i == 0) { in.h = hR; in.u = uR; in.v = vR; in.z = z[(int64_t)j * nx]; }
+                else { in.h = hL; in.u = uL; in.v = vL; in.z = z[(int64_t)j * nx + nx - 1]; }
+                or_side gs = or_ghost(i == 0 ? P->bc_w[j] : P->bc_e[j], in, 1, h_in);
+                double ge = gs.h + gs.z;
+                if (i == 0) { eL = ge; hL = gs.h; uL = gs.u; vL = gs.v; }
+                else { eR = ge; hR = gs.h; uR = gs.u; vR = gs.v; }
+            }
+            double zL = eL - hL, zR = eR - hR;
+            double zf = zL > zR ? zL : zR;
+            double hLs = eL - zf; if (hLs < 0.0) hLs = 0.0;
+            double hRs = eR - zf; if (hRs < 0.0) hRs = 0.0;
+            or_flux(P, g, hLs, uL, vL, hRs, uR, vR, f);
+            if (i == 0 && P->bc_w[j] == OR_BC_DISCHARGE) { f[0] += qb; f[1] += qb * u_in; }
+            if (i == nx && P->bc_e[j] == OR_BC_DISCHARGE) { f[0] -= qb; f[1] += qb * u_in; }
+            if (i > 0) {
+                int64_t c = (int64_t)j * nx + i - 1;
+                FE[3 * c] = f[0]; FE[3 * c + 1] = f[1] - or_press(g, hLs); FE[3 * c + 2] = f[2];
+            }
+            if (i < nx) {
+                int64_t c = (int64_t)j * nx + i;
+                FW[3 * c] = f[0]; FW[3 * c + 1] = f[1] - or_press(g, hRs); FW[3 * c + 2] = f[2];
+            }
+            if (i == 0) bflux[2 * nx + j] += 0.5 * f[0] * dt * dx;
+            if (i == nx) bflux[2 * nx + ny + j] -= 0.5 * f[0] * dt * dx;
+        }
+    }
+    /* y faces: face j between row j-1 (plus side) and row j (minus side); normal velocity v */
+    for (int32_t j = 0; j <= ny; ++j) {
+        for (int32_t i = 0; i < nx; ++i) {
+            double eL, hL, uL, vL, eR, hR, uR, vR;
+            if (j > 0) {
+                const or_faces *A = &FY[(int64_t)(j - 1) * nx + i];
+                eL = A->eta[1]; hL = A->h[1]; uL = A->u[1]; vL = A->v[1];
+            }
+            if (j < ny) {
+                const or_faces *B = &FY[(int64_t)j * nx + i];
+                eR = B->eta[0]; hR = B->h[0]; uR = B->u[0]; vR = B->v[0];
+            }
+            if (j == 0 || j == ny) {
+                or_side in;
+                if (j == 0) { in.h = hR; in.u = uR; in.v = vR; in.z = z[i]; }
+                else { in.h = hL; in.u = uL; in.v = vL; in.z = z[(int64_t)(ny - 1) * nx + i]; }
+                or_side gs = or_ghost(j == 0 ? P->bc_s[i] : P->bc_n[i], in, 0, h_in);
+                double ge = gs.h + gs.z;
+                if (j == 0) { eL = ge; hL = gs.h; uL = gs.u; vL = gs.v; }
+                else { eR = ge; hR = gs.h; uR = gs.u; vR = gs.v; }
+            }
+            double zL = eL - hL, zR = eR - hR;
+            double zf = zL > zR ? zL : zR;
+            double hLs = eL - zf; if (hLs < 0.0) hLs = 0.0;
+            double hRs = eR - zf; if (hRs < 0.0) hRs = 0.0;
+            or_flux(P, g, hLs, vL, uL, hRs, vR, uR, f);   /* f = (mass, hv-flux, hu-flux) */
+            if (j == 0 && P->bc_s[i] == OR_BC_DISCHARGE) { f[0] += qb; f[1] += qb * u_in; }
+            if (j == ny && P->bc_n[i] == OR_BC_DISCHARGE) { f[0] -= qb; f[1] += qb * u_in; }
+            if (j > 0) {
+                int64_t c = (int64_t)(j - 1) * nx + i;
+                GN[3 * c] = f[0]; GN[3 * c + 1] = f[2]; GN[3 * c + 2] = f[1] - or_press(g, hLs);
+            }
+            if (j < ny) {
+                int64_t c = (int64_t)j * nx + i;
+                GS[3 * c] = f[0]; GS[3 * c + 1] = f[2]; GS[3 * c + 2] = f[1] - or_press(g, hRs);
+            }
+            if (j == 0) bflux[i] += 0.5 * f[0] * dt * dx;
+            if (j == ny) bflux[nx + i] -= 0.5 * f[0] * dt * dx;
+        }
+    }
+    const double l = dt / dx;
+    for (int64_t c = 0; c < n; ++c) {
+        /* centred bed-slope term of each direction */
+        double sx = 0.5 * g * (FX[c].h[0] + FX[c].h[1]) * (FX[c].eta[1] - FX[c].eta[0]);
+        double sy = 0.5 * g * (FY[c].h[0] + FY[c].h[1]) * (FY[c].eta[1] - FY[c].eta[0]);
+        double hh = h[c] - l * (FE[3 * c] - FW[3 * c]) - l * (GN[3 * c] - GS[3 * c]);
+        double qx = hu[c] - l * (FE[3 * c + 1] - FW[3 * c + 1]) - l * (GN[3 * c + 1] - GS[3 * c + 1]) - l * sx;
+        double qy = hv[c] - l * (FE[3 * c + 2] - FW[3 * c + 2]) - l * (GN[3 * c + 2] - GS[3 * c + 2]) - l * sy;
+        if (hh < 0.0) { *neg += 1; hh = 0.0; }
+        if (hh <= OR_H_EPS) {
+            qx = 0.0; qy = 0.0;
+        } else {
+            double u = qx / hh, v = qy / hh;
+            double speed = sqrt(u * u + v * v);
+            double nm = n_eff[c];
+            double denom = 1.0 + dt * g * nm * nm * speed / (hh * cbrt(hh));
+            qx = qx / denom;
+            qy = qy / denom;
+        }
+        ho[c] = hh; huo[c] = qx; hvo[c] = qy;
+    }
+    free(FE); free(FW); free(GN); free(GS); free(FX); free(FY);
+}
+
+void or_flood_step2(const or_params *P, or_state *S, int64_t dt_ticks, const double *n_eff) {
+    const int64_t n = (int64_t)P->nx * P->ny;
+    const double dt = (double)dt_ticks / OR_TICKS;
+    double qb = 0.0, u_in = 0.0;
+    {
+        const double B = or_discharge_width(P);
+        const double t0 = (double)S->t_ticks / OR_TICKS, t1 = (double)(S->t_ticks + dt_ticks) / OR_TICKS;
+        if (B > 0.0 && dt > 0.0) {
+            qb = (or_discharge_volume(P, t1) - or_discharge_volume(P, t0)) / (dt * B);
+            u_in = qb / P->h_qin;
+        }
+    }
+    double *b1 = (double *)malloc(sizeof(double) * (size_t)n * 6);
+    double *h1 = b1, *hu1 = b1 + n, *hv1 = b1 + 2 * n, *h2 = b1 + 3 * n, *hu2 = b1 + 4 * n, *hv2 = b1 + 5 * n;
+    or_muscl_stage(P, S->z, S->h, S->hu, S->hv, h1, hu1, hv1, dt, or_hydro_depth(P, S->t_ticks), qb, u_in, n_eff,
+                   S->bflux, &S->neg_depth);
+    or_muscl_stage(P, S->z, h1, hu1, hv1, h2, hu2, hv2, dt, or_hydro_depth(P, S->t_ticks + dt_ticks), qb, u_in,
+                   n_eff, S->bflux, &S->neg_depth);
+    for (int64_t c = 0; c < n; ++c) {
+        double h = 0.5 * (S->h[c] + h2[c]);
+        double hu = 0.5 * (S->hu[c] + hu2[c]), hv = 0.5 * (S->hv[c] + hv2[c]);
+        if (h <= OR_H_EPS) { hu = 0.0; hv = 0.0; }
+        S->h[c] = h; S->hu[c] = hu; S->hv[c] = hv;
+    }
+    free(b1);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Pedestrian step (Sections 2.3-2.4) from the state at step n.             */
 /* ------------------------------------------------------------------------ */
 static int or_walkable_at(const or_params *P, double x, double y) {
@@ -875,7 +1076,8 @@ int64_t or_step(const or_params *P, or_state *S) {
     memcpy(h0, S->h, sizeof(double) * (size_t)n);
     memcpy(h0 + n, S->hu, sizeof(double) * (size_t)n);
     memcpy(h0 + 2 * n, S->hv, sizeof(double) * (size_t)n);
-    or_flood_step(P, S, dt_ticks, n_eff);
+    if (P->order == 2) or_flood_step2(P, S, dt_ticks, n_eff);
+    else or_flood_step(P, S, dt_ticks, n_eff);
     int64_t drops = or_ped_step(P, S, dt_ticks, S->wet, bags_snap, h0, h0 + n, h0 + 2 * n);
     or_entries(P, S, S->t_ticks, dt_ticks, S->wet);
     S->total_bags += drops;

@@ -81,6 +81,7 @@ class Scenario:
     q_Q: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros(0))
     h_qin: float = 1.0
     riemann: int = 0         # interface flux: 0 HLL, 1 HLLC
+    order: int = 1           # 2: the second-order (MUSCL, two-stage) scheme
     # entrance doors (entry/exit flow before the flood): door_of[k] is the door
     # of cell door_cells[k] (a door's first listed cell is its entry cell); each
     # door admits one visitor every entry_period seconds, walking speeds drawn

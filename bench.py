@@ -21,7 +21,9 @@ roofline the flood kernel (HBM-bound stencil), 34 algorithmic bytes per cell
         update of the tiles it computed, its launch duration from CUDA events
         on its own stream in a profiled pass of the same steps;
         ``roofline_peds`` the pedestrian kernel, 96 algorithmic bytes per
-        pedestrian update; ``roofline_wet2048`` the flood kernel alone on a
+        pedestrian update; ``roofline_muscl_wet2048`` the second-order
+        update's two stage kernels on the wet grid (74 B per cell and step);
+        ``roofline_wet2048`` the flood kernel alone on a
         2048 x 2048 grid holding water almost everywhere.
 cpu_baseline the FP64 C oracle on one coupled step of the same snapshot.
 batched  a seeded ensemble of shopping centres stepped together by the batched
@@ -57,6 +59,10 @@ sys.path.insert(0, ROOT)
 
 CHUNK = 512            # simulation steps per benchmark step
 FLOOD_BYTES_PER_CELL = 34  # read h,hu,hv,z,n0 (20 B) + occupancy (2 B); write h,hu,hv (12 B)
+# second order, per cell and step: stage 1 reads h,hu,hv,z (16 B) and writes the
+# stage state (12 B); stage 2 reads it (12 B), z, n0 (8 B), the occupancy (2 B)
+# and the step's start state (12 B) and writes h,hu,hv (12 B)
+MUSCL_BYTES_PER_CELL = 74
 # pedestrian update: read its record (32 B) and position copy (8 B), its cell's
 # h, hu, hv (12 B), navigation code, arrival and cell flags (3 B); write its
 # record (32 B), hash key and slot (8 B), its evacuee count (1 B amortised)
@@ -494,7 +500,7 @@ def run_ours(args):
 
     # the same kernel where it is HBM-bound: a 2048x2048 grid holding water
     # almost everywhere (no pedestrians, so the kernel runs alone)
-    roof_wet = None
+    roof_wet = roof_muscl = None
     if rank == 0 and not args.no_wet2048:
         big = wet2048()
         bsim = P.from_scenario(big, peds=False)
@@ -514,6 +520,24 @@ def run_ours(args):
                     "bytes_per_cell_update": FLOOD_BYTES_PER_CELL, "computed_cells_per_launch": bcells,
                     "traffic": flood_traffic("wet_2048"), "note": "profiled pass, no pedestrians: the kernel alone"}
         bsim.close()
+        # the second-order update (the cited scheme at full order) on the same grid
+        big.order = 2
+        msim = P.from_scenario(big, peds=False)
+        N.fp_set_stream(msim.h, stream.cuda_stream)
+        msim.step(4)
+        msim.synchronize()
+        N.fp_set_profiling(msim.h, 1)
+        msim.step(32)
+        mprof = msim.profile()
+        N.fp_set_profiling(msim.h, 0)
+        mflood = mprof["flood_ms"] / max(mprof["steps"], 1)
+        mach = big.n_cells * MUSCL_BYTES_PER_CELL / (mflood * 1e-3) / 1e9
+        roof_muscl = {"kernel": "muscl_stage_kernel<1>+<2>", "workload": "wet_2048, fp_config.order = 2",
+                      "bound": "hbm", "achieved": mach, "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s",
+                      "frac": mach / hbm, "us_per_step": mflood * 1e3, "bytes_per_cell_step": MUSCL_BYTES_PER_CELL,
+                      "cells_per_step": big.n_cells, "traffic": None,
+                      "note": "profiled pass, no pedestrians: the two stage kernels of a step, every cell computed"}
+        msim.close()
 
     sim.close()
     batched = surrogate = None
@@ -573,6 +597,7 @@ def run_ours(args):
                               "note": "issue- and latency-bound (neighbour scans out of L1/L2); HBM fraction of "
                                       "its algorithmic bytes for reference"},
             "roofline_wet2048": roof_wet,
+            "roofline_muscl_wet2048": roof_muscl,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "batched": batched,
@@ -778,6 +803,7 @@ def run_case(args):
     else:
         sc = scenarios.config_shopping()
     from paper_1908_05232_b300 import _native as N
+    sc.order = args.case_order
     sim = P.from_scenario(sc, tile_rows=args.tile_rows)
     stream = torch.cuda.Stream()
     N.fp_set_stream(sim.h, stream.cuda_stream)
@@ -829,6 +855,8 @@ def main():
     ap.add_argument("--case-steps", type=int, default=4)
     ap.add_argument("--case-lanes", type=int, default=8, choices=[4, 8, 16], help="lanes per pedestrian in the case")
     ap.add_argument("--case-hash-ahead", type=int, default=1, choices=[0, 1], help="hash-ahead in the case")
+    ap.add_argument("--case-order", type=int, default=1, choices=[1, 2],
+                    help="flood update of the case: 1 first order, 2 the second-order option")
     ap.add_argument("--case-time", type=float, default=0.0,
                     help="simulated seconds to run before the case's steps (profiler range opened after them)")
     ap.add_argument("--workload", choices=["barrier2048", "ensemble", "surrogate", "deployment", "scenario1"],

@@ -106,7 +106,15 @@ typedef struct fp_config {
                            scheme) or FP_RIEMANN_HLLC (1: the cited scheme's three-wave
                            solver, which also resolves the contact wave of the
                            tangential momentum); else FP_EINVAL */
-    int32_t reserved[3];
+    int32_t order;      /* 0 or 1: the paper's first-order update (Eq. 2); 2: the cited
+                           scheme at full order -- MUSCL minmod reconstruction of the
+                           surface, the depth and the velocities (first order on the
+                           domain edge and next to dry cells), the hydrostatic
+                           reconstruction with the centred bed-slope term (a lake at
+                           rest stays at rest), two-stage Runge-Kutta; every cell is
+                           computed every step; FP_MODE_KERNELS only (no persistent
+                           mode, batch or surrogate window); else FP_EINVAL */
+    int32_t reserved[2];
 } fp_config;
 
 #define FP_RIEMANN_HLL 0

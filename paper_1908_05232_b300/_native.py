@@ -34,7 +34,7 @@ class FpConfig(ctypes.Structure):
                 ("cfl", ctypes.c_float), ("ped_noise", ctypes.c_float), ("t_end", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("max_peds", ctypes.c_int32), ("coupling", ctypes.c_int32),
                 ("evac_trigger", ctypes.c_int32), ("tile_rows", ctypes.c_int32), ("riemann", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 3)]
+                ("order", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 class FpCounters(ctypes.Structure):
@@ -376,6 +376,7 @@ def config_for(sc, max_peds=None, tile_rows=0) -> FpConfig:
     c.max_peds = max(sc.n_peds, int(getattr(sc, "max_peds", 0) or 0)) if max_peds is None else max_peds
     c.coupling, c.evac_trigger, c.tile_rows = int(sc.coupling), int(sc.evac_trigger), int(tile_rows)
     c.riemann = int(getattr(sc, "riemann", 0))
+    c.order = int(getattr(sc, "order", 1))
     return c
 
 

@@ -299,7 +299,8 @@ static void launch_step(fp_sim *s, int par, int slot, cudaEvent_t *ev = nullptr)
     // edges (not in profiling mode, whose events sit between the kernels)
     const bool pdl = ev == nullptr;
     if (ev) cudaEventRecordWithFlags(ev[4], s->stream2, cudaEventRecordExternal);
-    fp_launch_flood(S, par, slot, s->tile_rows, s->stream2);
+    if (S.order == 2) fp_launch_muscl(S, par, slot, s->stream2);
+    else fp_launch_flood(S, par, slot, s->tile_rows, s->stream2);
     if (ev) cudaEventRecordWithFlags(ev[2], s->stream2, cudaEventRecordExternal);
     fp_launch_scan(S, s->stream, pdl);
     fp_launch_gather(S, slot, s->stream, pdl);
@@ -487,7 +488,7 @@ int fp_sim_create(const fp_config *cfg, fp_sim **out) {
         !(c.cfl > 0.0f) || c.cfl > 1.0f || c.max_peds < 0 || c.max_peds > (1 << 26) || !(c.t_end >= 0.0) ||
         !(c.ped_noise >= 0.0f) ||
         (c.tile_rows != 0 && c.tile_rows != 8 && c.tile_rows != 16 && c.tile_rows != 32) ||
-        (c.riemann != FP_RIEMANN_HLL && c.riemann != FP_RIEMANN_HLLC)) {
+        (c.riemann != FP_RIEMANN_HLL && c.riemann != FP_RIEMANN_HLLC) || c.order < 0 || c.order > 2) {
         g_create_error = "invalid fp_config";
         return FP_EINVAL;
     }
@@ -514,6 +515,7 @@ int fp_sim_create(const fp_config *cfg, fp_sim **out) {
     S.bpc = (int)std::ceil(((double)c.dx * (double)c.dx) / (0.40 * 0.30));
     S.barrier_polls = FP_BARRIER_POLLS_DEFAULT;
     S.riemann = c.riemann;
+    S.order = c.order == 2 ? 2 : 1;
     s->tile_rows = c.tile_rows ? c.tile_rows : 16;
     const size_t pe = s->plane_elems(), n = (size_t)c.nx * c.ny;
     bool ok = true;
@@ -523,6 +525,11 @@ int fp_sim_create(const fp_config *cfg, fp_sim **out) {
         ok &= (S.hv[p] = s->dalloc<float>(pe)) != nullptr;
     }
     ok &= (S.z = s->dalloc<float>(pe)) != nullptr;
+    if (S.order == 2) {
+        ok &= (S.mh = s->dalloc<float>(pe)) != nullptr;
+        ok &= (S.mhu = s->dalloc<float>(pe)) != nullptr;
+        ok &= (S.mhv = s->dalloc<float>(pe)) != nullptr;
+    }
     ok &= (S.n0 = s->dalloc<float>(pe)) != nullptr;
     ok &= (S.occ[0] = s->dalloc<unsigned short>(pe + 2)) != nullptr;
     ok &= (S.occ[1] = s->dalloc<unsigned short>(pe + 2)) != nullptr;
@@ -1004,6 +1011,8 @@ int fp_set_step_mode(fp_sim *s, int32_t mode) {
     if (mode != FP_MODE_KERNELS && mode != FP_MODE_PERSISTENT) return s->fail(FP_EINVAL, "unknown step mode");
     if (mode == FP_MODE_PERSISTENT && s->persist_ctas <= 0)
         return s->fail(FP_EINVAL, "cooperative launch unavailable on this device");
+    if (mode == FP_MODE_PERSISTENT && s->S.order == 2)
+        return s->fail(FP_EINVAL, "the second-order update runs in FP_MODE_KERNELS only");
     cudaError_t e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return s->cuda_fail(e, "mode switch");
     s->mode = mode;
@@ -1028,6 +1037,7 @@ int fp_surrogate_advance(fp_sim *s, fp_surrogate *sur, int32_t n_windows, const 
     if (!sur || !guard || !st || n_windows < 0) return s->fail(FP_EINVAL, "null surrogate, guard or stats");
     if (s->S.dt_fixed <= 0) return s->fail(FP_EINVAL, "the surrogate window needs a fixed time step (fp_set_fixed_dt)");
     if (s->S.has_discharge) return s->fail(FP_EINVAL, "the surrogate window does not take a discharge breach");
+    if (s->S.order == 2) return s->fail(FP_EINVAL, "the surrogate window stands in for the first-order update");
     if (!(guard->mass_tol >= 0.0f) || !(guard->check_tol >= 0.0f) || !(guard->fix_tol >= 0.0f) ||
         guard->check_every < 0 ||
         guard->suspend_windows < 0)
@@ -1397,6 +1407,11 @@ int fp_batch_create(fp_sim *const *sims, int32_t n, fp_batch **out) {
     for (int k = 0; k < n; ++k) {
         fp_sim *m = sims[k];
         if (!m) { delete b; g_create_error = "fp_batch_create: null member"; return FP_EINVAL; }
+        if (m->S.order == 2) {
+            delete b;
+            g_create_error = "fp_batch_create: a member uses the second-order update (per-step kernels only)";
+            return FP_EINVAL;
+        }
         b->sims.push_back(m);
         const int runs = ((m->S.nx + FP_TX - 1) / FP_TX) * ((m->S.ny + 15) / 16);
         run_off[k + 1] = run_off[k] + runs;

@@ -123,6 +123,8 @@ struct FpSim {
     long long dt_fixed;            // fixed time step in ticks (0: CFL step)
     int barrier_polls;             // polls of a persistent-kernel grid barrier before it gives up
     int riemann;                   // interface flux: 0 HLL, 1 HLLC
+    int order;                     // 1: first order (the paper's); 2: MUSCL + two-stage Runge-Kutta
+    float *mh, *mhu, *mhv;         // second order: the first stage's state (padded planes)
     // discharge breach (Section 3.1): boundary cells coded FP_BC_DISCHARGE take
     // the hydrograph Q(t) (points q_t, q_Q) spread over their width q_width
     int has_discharge, n_q;
@@ -296,6 +298,7 @@ __device__ __forceinline__ void fp_set_err(const FpSim &S, unsigned int bit) { a
 // launchers (defined in flood.cu / peds.cu)
 void fp_launch_flood(const FpSim &S, int par, int slot, int tile_rows, cudaStream_t st, bool pdl = false);
 void fp_launch_init_clock(const FpSim &S, int par, int slot, cudaStream_t st);
+void fp_launch_muscl(const FpSim &S, int par, int slot, cudaStream_t st);
 void fp_launch_mass(const FpSim &S, int par, cudaStream_t st);
 void fp_launch_hr_max(const FpSim &S, int par, cudaStream_t st);
 cudaError_t fp_flood_init_attributes();

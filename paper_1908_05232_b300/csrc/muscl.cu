@@ -18,13 +18,14 @@
 //                   evacuee roughness, every cell computed (no dry skipping).
 //
 // One thread per cell, CTAs of 32 x 8 cells; the CTA loads its cells with a
-// two-cell halo into shared memory, forms the face values of its cells and a
-// one-cell ring, then each thread forms its cell's four faces (a face between
-// two CTAs is formed by both) and updates its cell.  Stage 1 advances the
+// two-cell halo into shared memory (velocities formed once per cell), forms
+// the face values of its cells and a one-cell ring, then every face of its
+// cells once (a face between two CTAs is formed by both), then each thread
+// updates its cell.  Stage 1 advances the
 // clock; stage 2 takes the inflow depth of t + dt, averages, clears the
 // evacuee counts it used and folds the wave-speed maximum, wet flag and
 // tallies into the next step's clock.  Each stage adds half its boundary
-// volumes.  A correctness-first path: no run ticket, no paired arithmetic.
+// volumes.  No run ticket, no paired arithmetic, no dry skipping.
 #include "flood_dev.cuh"
 #include "floodped.h"
 
@@ -45,29 +46,30 @@ __device__ __forceinline__ float minmod(float a, float b) {
     return 0.0f;
 }
 
-__device__ __forceinline__ float vel(float q, float h) { return h > FP_H_EPS_F ? __fdiv_rn(q, h) : 0.0f; }
+// a velocity q / h (0 where dry), sign-symmetric in q
+__device__ __forceinline__ float vel(float q, float h) { return h > FP_H_EPS_F ? div_fast(q, h) : 0.0f; }
 
-// face values of the cell at region (rx, ry) along x (dx = 1) or y (dy = 1);
+// The loaded region: depth, velocities, surface and bed per cell.
+struct Region {
+    float h[kRy][kRx], u[kRy][kRx], v[kRy][kRx], eta[kRy][kRx], z[kRy][kRx];
+};
+
+// face values of the cell at region (rx, ry) along x (ddx = 1) or y (ddy = 1);
 // slope only if the flag allows it and the cell and both neighbours are wet
-__device__ __forceinline__ FaceVals faces_of(const float (*sh)[kRx], const float (*shu)[kRx], const float (*shv)[kRx],
-                                             const float (*sz)[kRx], int rx, int ry, int ddx, int ddy, bool slope) {
-    const float hc = sh[ry][rx], z = sz[ry][rx];
-    const float uc = vel(shu[ry][rx], hc), vc = vel(shv[ry][rx], hc);
-    const float eta = __fadd_rn(hc, z);
-    float se = 0.0f, sh_ = 0.0f, su = 0.0f, sv = 0.0f;
-    const float hm = sh[ry - ddy][rx - ddx], hp = sh[ry + ddy][rx + ddx];
+__device__ __forceinline__ FaceVals faces_of(const Region &R, int rx, int ry, int ddx, int ddy, bool slope) {
+    const float hc = R.h[ry][rx], uc = R.u[ry][rx], vc = R.v[ry][rx], eta = R.eta[ry][rx];
+    float se = 0.0f, sh = 0.0f, su = 0.0f, sv = 0.0f;
+    const int xm = rx - ddx, ym = ry - ddy, xp = rx + ddx, yp = ry + ddy;
+    const float hm = R.h[ym][xm], hp = R.h[yp][xp];
     if (slope && hc > FP_H_EPS_F && hm > FP_H_EPS_F && hp > FP_H_EPS_F) {
-        const float em = __fadd_rn(hm, sz[ry - ddy][rx - ddx]), ep = __fadd_rn(hp, sz[ry + ddy][rx + ddx]);
-        const float um = vel(shu[ry - ddy][rx - ddx], hm), up = vel(shu[ry + ddy][rx + ddx], hp);
-        const float vm = vel(shv[ry - ddy][rx - ddx], hm), vp = vel(shv[ry + ddy][rx + ddx], hp);
-        se = minmod(__fsub_rn(ep, eta), __fsub_rn(eta, em));
-        sh_ = minmod(__fsub_rn(hp, hc), __fsub_rn(hc, hm));
-        su = minmod(__fsub_rn(up, uc), __fsub_rn(uc, um));
-        sv = minmod(__fsub_rn(vp, vc), __fsub_rn(vc, vm));
+        se = minmod(__fsub_rn(R.eta[yp][xp], eta), __fsub_rn(eta, R.eta[ym][xm]));
+        sh = minmod(__fsub_rn(hp, hc), __fsub_rn(hc, hm));
+        su = minmod(__fsub_rn(R.u[yp][xp], uc), __fsub_rn(uc, R.u[ym][xm]));
+        sv = minmod(__fsub_rn(R.v[yp][xp], vc), __fsub_rn(vc, R.v[ym][xm]));
     }
     FaceVals f;
     f.eta[0] = __fsub_rn(eta, 0.5f * se); f.eta[1] = __fadd_rn(eta, 0.5f * se);
-    f.h[0] = __fsub_rn(hc, 0.5f * sh_);   f.h[1] = __fadd_rn(hc, 0.5f * sh_);
+    f.h[0] = __fsub_rn(hc, 0.5f * sh);    f.h[1] = __fadd_rn(hc, 0.5f * sh);
     f.u[0] = __fsub_rn(uc, 0.5f * su);    f.u[1] = __fadd_rn(uc, 0.5f * su);
     f.v[0] = __fsub_rn(vc, 0.5f * sv);    f.v[1] = __fadd_rn(vc, 0.5f * sv);
     return f;
@@ -118,129 +120,119 @@ __device__ __forceinline__ FaceFlux face_flux(const FpSim &S, float eL, float hL
 // U^{n+1} = (U + U2) / 2 into the other parity's planes
 template <int STAGE>
 __global__ void __launch_bounds__(kMx * kMy) muscl_stage_kernel(const __grid_constant__ FpSim S, int par, int slot) {
-    __shared__ float sh[kRy][kRx], shu[kRy][kRx], shv[kRy][kRx], sz[kRy][kRx];
+    __shared__ Region R;
     __shared__ FaceVals fx[kFy][kFx], fy[kFy][kFx];
+    __shared__ FaceFlux xf[kMy][kMx + 1], yf[kMy + 1][kMx];
     const int nx = S.nx, ny = S.ny;
     const int x0 = blockIdx.x * kMx, y0 = blockIdx.y * kMy;
     const int tid = threadIdx.x;
     const FloodStep st = flood_step_consts(S, slot);
     if (STAGE == 1 && blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) flood_clock_advance(S, slot, st);
+    const float h_in = STAGE == 1 ? st.h_in : S.clock[(slot + 1) & 3].h_in;
+    const double half_dtdx = 0.5 * (double)st.dtf * (double)S.dx;
     const float *ih = STAGE == 1 ? S.h[par] : S.mh, *ihu = STAGE == 1 ? S.hu[par] : S.mhu,
                 *ihv = STAGE == 1 ? S.hv[par] : S.mhv;
+    // the region with its two-cell halo (zeros outside the domain, never used)
     for (int k = tid; k < kRx * kRy; k += kMx * kMy) {
         const int rx = k % kRx, ry = k / kRx, gi = x0 + rx - 2, gj = y0 + ry - 2;
-        float a = 0.0f, b = 0.0f, c = 0.0f, d = 0.0f;
+        float h = 0.0f, q = 0.0f, r = 0.0f, z = 0.0f;
         if (gi >= 0 && gi < nx && gj >= 0 && gj < ny) {
             const size_t o = fp_pidx(S, gi, gj);
-            a = ih[o]; b = ihu[o]; c = ihv[o]; d = S.z[o];
+            h = ih[o]; q = ihu[o]; r = ihv[o]; z = S.z[o];
         }
-        sh[ry][rx] = a; shu[ry][rx] = b; shv[ry][rx] = c; sz[ry][rx] = d;
+        R.h[ry][rx] = h; R.u[ry][rx] = vel(q, h); R.v[ry][rx] = vel(r, h);
+        R.eta[ry][rx] = __fadd_rn(h, z); R.z[ry][rx] = z;
     }
     __syncthreads();
+    // face values of the cells and a one-cell ring
     for (int k = tid; k < kFx * kFy; k += kMx * kMy) {
         const int fxi = k % kFx, fyi = k / kFx, gi = x0 + fxi - 1, gj = y0 + fyi - 1;
         if (gi < 0 || gi >= nx || gj < 0 || gj >= ny) continue;
-        fx[fyi][fxi] = faces_of(sh, shu, shv, sz, fxi + 1, fyi + 1, 1, 0, gi > 0 && gi < nx - 1);
-        fy[fyi][fxi] = faces_of(sh, shu, shv, sz, fxi + 1, fyi + 1, 0, 1, gj > 0 && gj < ny - 1);
+        fx[fyi][fxi] = faces_of(R, fxi + 1, fyi + 1, 1, 0, gi > 0 && gi < nx - 1);
+        fy[fyi][fxi] = faces_of(R, fxi + 1, fyi + 1, 0, 1, gj > 0 && gj < ny - 1);
+    }
+    __syncthreads();
+    // every face of the CTA's cells once: x faces (kMx + 1 per row), then y
+    // faces (kMy + 1 per column); a domain-edge face takes the ghost of its
+    // edge cell, the breach's flux and the boundary volume
+    for (int k = tid; k < kMy * (kMx + 1) + (kMy + 1) * kMx; k += kMx * kMy) {
+        const bool xface = k < kMy * (kMx + 1);
+        const int kk = xface ? k : k - kMy * (kMx + 1);
+        const int a = xface ? kk % (kMx + 1) : kk % kMx, b = xface ? kk / (kMx + 1) : kk / kMx;
+        // x face a of row b lies west of local cell a; y face b of column a south of local cell row b
+        const int gi = x0 + a, gj = y0 + b;
+        if (xface ? (gj >= ny || gi > nx) : (gi >= nx || gj > ny)) continue;
+        const int n_ = xface ? nx : ny, gf = xface ? gi : gj;
+        const unsigned char *bc = xface ? S.bc[gf == 0 ? 2 : 3] : S.bc[gf == 0 ? 0 : 1];
+        const int along = xface ? gj : gi;
+        float eL, hL, unL, utL, eR, hR, unR, utR;
+        // own-side cells: local (a - 1, b) / (a, b) for x faces, (a, b - 1) / (a, b) for y faces
+        const FaceVals *Lf = nullptr, *Rf = nullptr;
+        if (gf > 0) Lf = xface ? &fx[b + 1][a] : &fy[b][a + 1];
+        if (gf < n_) Rf = xface ? &fx[b + 1][a + 1] : &fy[b + 1][a + 1];
+        if (Lf) { eL = Lf->eta[1]; hL = Lf->h[1]; unL = xface ? Lf->u[1] : Lf->v[1]; utL = xface ? Lf->v[1] : Lf->u[1]; }
+        if (Rf) { eR = Rf->eta[0]; hR = Rf->h[0]; unR = xface ? Rf->u[0] : Rf->v[0]; utR = xface ? Rf->v[0] : Rf->u[0]; }
+        if (gf == 0 || gf == n_) {
+            // the edge cell's own state (no slope across the edge)
+            const int rx = xface ? (gf == 0 ? a + 2 : a + 1) : a + 2, ry = xface ? b + 2 : (gf == 0 ? b + 2 : b + 1);
+            const Side cell{R.h[ry][rx], R.u[ry][rx], R.v[ry][rx], R.z[ry][rx]};
+            const Side gs = ghost(bc[along], cell, xface, h_in);
+            const float ge = __fadd_rn(gs.h, gs.z);
+            const float gn = xface ? gs.u : gs.v, gt = xface ? gs.v : gs.u;
+            if (gf == 0) { eL = ge; hL = gs.h; unL = gn; utL = gt; }
+            else { eR = ge; hR = gs.h; unR = gn; utR = gt; }
+        }
+        FaceFlux f = face_flux(S, eL, hL, unL, utL, eR, hR, unR, utR);
+        if ((gf == 0 || gf == n_) && bc[along] == FP_BC_DISCHARGE) {
+            f.m = gf == 0 ? __fadd_rn(f.m, st.qd.x) : __fsub_rn(f.m, st.qd.x);
+            f.n = __fadd_rn(f.n, st.qd.y);
+        }
+        if (gf == 0) S.bflux[(xface ? 2 * nx : 0) + along] += (double)f.m * half_dtdx;
+        if (gf == n_) S.bflux[(xface ? 2 * nx + ny : nx) + along] -= (double)f.m * half_dtdx;
+        if (xface) xf[b][a] = f;
+        else yf[b][a] = f;
     }
     __syncthreads();
     const int tx = tid % kMx, ty = tid / kMx, gi = x0 + tx, gj = y0 + ty;
-    const bool in = gi < nx && gj < ny;
     FloodAcc acc = flood_acc_init();
-    if (in) {
-        const float h_in = STAGE == 1 ? st.h_in : S.clock[(slot + 1) & 3].h_in;
-        const double half_dtdx = 0.5 * (double)st.dtf * (double)S.dx;
-        const int rx = tx + 2, ry = ty + 2, cx = tx + 1, cy = ty + 1;
-        const float hc = sh[ry][rx], zc = sz[ry][rx];
-        const Side cell{hc, vel(shu[ry][rx], hc), vel(shv[ry][rx], hc), zc};
-        // x faces: west (own side R) and east (own side L)
-        float mW, nW, tW, mE, nE, tE;
-        {
-            const FaceVals &c = fx[cy][cx];
-            float eL, hL, uL, vL;
-            if (gi == 0) {
-                const Side gs = ghost(S.bc[2][gj], cell, true, h_in);
-                eL = __fadd_rn(gs.h, gs.z); hL = gs.h; uL = gs.u; vL = gs.v;
-            } else {
-                const FaceVals &a = fx[cy][cx - 1];
-                eL = a.eta[1]; hL = a.h[1]; uL = a.u[1]; vL = a.v[1];
-            }
-            FaceFlux f = face_flux(S, eL, hL, uL, vL, c.eta[0], c.h[0], c.u[0], c.v[0]);
-            if (gi == 0 && S.bc[2][gj] == FP_BC_DISCHARGE) { f.m = __fadd_rn(f.m, st.qd.x); f.n = __fadd_rn(f.n, st.qd.y); }
-            if (gi == 0) S.bflux[2 * nx + gj] += (double)f.m * half_dtdx;
-            mW = f.m; nW = __fsub_rn(f.n, f.pR); tW = f.t;
-            float eR, hR, uR, vR;
-            if (gi == nx - 1) {
-                const Side gs = ghost(S.bc[3][gj], cell, true, h_in);
-                eR = __fadd_rn(gs.h, gs.z); hR = gs.h; uR = gs.u; vR = gs.v;
-            } else {
-                const FaceVals &b = fx[cy][cx + 1];
-                eR = b.eta[0]; hR = b.h[0]; uR = b.u[0]; vR = b.v[0];
-            }
-            f = face_flux(S, c.eta[1], c.h[1], c.u[1], c.v[1], eR, hR, uR, vR);
-            if (gi == nx - 1 && S.bc[3][gj] == FP_BC_DISCHARGE) { f.m = __fsub_rn(f.m, st.qd.x); f.n = __fadd_rn(f.n, st.qd.y); }
-            if (gi == nx - 1) S.bflux[2 * nx + ny + gj] -= (double)f.m * half_dtdx;
-            mE = f.m; nE = __fsub_rn(f.n, f.pL); tE = f.t;
-        }
-        // y faces: normal velocity v, tangential u
-        float mS, nS, tS, mN, nN, tN;
-        {
-            const FaceVals &c = fy[cy][cx];
-            float eL, hL, uL, vL;
-            if (gj == 0) {
-                const Side gs = ghost(S.bc[0][gi], cell, false, h_in);
-                eL = __fadd_rn(gs.h, gs.z); hL = gs.h; uL = gs.u; vL = gs.v;
-            } else {
-                const FaceVals &a = fy[cy - 1][cx];
-                eL = a.eta[1]; hL = a.h[1]; uL = a.u[1]; vL = a.v[1];
-            }
-            FaceFlux f = face_flux(S, eL, hL, vL, uL, c.eta[0], c.h[0], c.v[0], c.u[0]);
-            if (gj == 0 && S.bc[0][gi] == FP_BC_DISCHARGE) { f.m = __fadd_rn(f.m, st.qd.x); f.n = __fadd_rn(f.n, st.qd.y); }
-            if (gj == 0) S.bflux[gi] += (double)f.m * half_dtdx;
-            mS = f.m; nS = __fsub_rn(f.n, f.pR); tS = f.t;
-            float eR, hR, uR, vR;
-            if (gj == ny - 1) {
-                const Side gs = ghost(S.bc[1][gi], cell, false, h_in);
-                eR = __fadd_rn(gs.h, gs.z); hR = gs.h; uR = gs.u; vR = gs.v;
-            } else {
-                const FaceVals &b = fy[cy + 1][cx];
-                eR = b.eta[0]; hR = b.h[0]; uR = b.u[0]; vR = b.v[0];
-            }
-            f = face_flux(S, c.eta[1], c.h[1], c.v[1], c.u[1], eR, hR, vR, uR);
-            if (gj == ny - 1 && S.bc[1][gi] == FP_BC_DISCHARGE) { f.m = __fsub_rn(f.m, st.qd.x); f.n = __fadd_rn(f.n, st.qd.y); }
-            if (gj == ny - 1) S.bflux[nx + gi] -= (double)f.m * half_dtdx;
-            mN = f.m; nN = __fsub_rn(f.n, f.pL); tN = f.t;
-        }
+    if (gi < nx && gj < ny) {
+        const FaceFlux &W = xf[ty][tx], &E = xf[ty][tx + 1], &So = yf[ty][tx], &No = yf[ty + 1][tx];
+        // x faces: (mass, u-momentum, v-momentum); y faces: (mass, v-momentum, u-momentum);
+        // each cell's own side: R of its west / south face, L of its east / north face
         const float g = S.g, l = st.lx;
-        const FaceVals &ax = fx[cy][cx], &ay = fy[cy][cx];
+        const FaceVals &ax = fx[ty + 1][tx + 1], &ay = fy[ty + 1][tx + 1];
         const float sx = __fmul_rn(__fmul_rn(0.5f * g, __fadd_rn(ax.h[0], ax.h[1])), __fsub_rn(ax.eta[1], ax.eta[0]));
         const float sy = __fmul_rn(__fmul_rn(0.5f * g, __fadd_rn(ay.h[0], ay.h[1])), __fsub_rn(ay.eta[1], ay.eta[0]));
-        float hh = __fsub_rn(__fsub_rn(hc, __fmul_rn(l, __fsub_rn(mE, mW))), __fmul_rn(l, __fsub_rn(mN, mS)));
-        float qu = __fsub_rn(__fsub_rn(__fsub_rn(shu[ry][rx], __fmul_rn(l, __fsub_rn(nE, nW))),
-                                       __fmul_rn(l, __fsub_rn(tN, tS))), __fmul_rn(l, sx));
-        float qv = __fsub_rn(__fsub_rn(__fsub_rn(shv[ry][rx], __fmul_rn(l, __fsub_rn(tE, tW))),
-                                       __fmul_rn(l, __fsub_rn(nN, nS))), __fmul_rn(l, sy));
-        if (hh < 0.0f) { acc.neg += 1; hh = 0.0f; }
+        const int rx = tx + 2, ry = ty + 2;
+        const float hc = R.h[ry][rx];
         const size_t o = fp_pidx(S, gi, gj);
+        const float quc = ihu[o], qvc = ihv[o];
+        float hh = __fsub_rn(__fsub_rn(hc, __fmul_rn(l, __fsub_rn(E.m, W.m))), __fmul_rn(l, __fsub_rn(No.m, So.m)));
+        float qu = __fsub_rn(__fsub_rn(__fsub_rn(quc, __fmul_rn(l, __fsub_rn(__fsub_rn(E.n, E.pL), __fsub_rn(W.n, W.pR)))),
+                                       __fmul_rn(l, __fsub_rn(No.t, So.t))), __fmul_rn(l, sx));
+        float qv = __fsub_rn(__fsub_rn(__fsub_rn(qvc, __fmul_rn(l, __fsub_rn(E.t, W.t))),
+                                       __fmul_rn(l, __fsub_rn(__fsub_rn(No.n, No.pL), __fsub_rn(So.n, So.pR)))),
+                             __fmul_rn(l, sy));
+        if (hh < 0.0f) { acc.neg += 1; hh = 0.0f; }
         if (hh <= FP_H_EPS_F) {
             qu = 0.0f; qv = 0.0f;
         } else {
             // point-implicit Manning friction, n = n0 + N_p n0 (N_p <= 20)
-            const float u = __fdiv_rn(qu, hh), v = __fdiv_rn(qv, hh);
-            const float sp = __fsqrt_rn(__fadd_rn(__fmul_rn(u, u), __fmul_rn(v, v)));
+            const float rh = rcp_fast(hh);
+            const float u = __fmul_rn(qu, rh), v = __fmul_rn(qv, rh);
+            const float sp = sqrt_fast(__fadd_rn(__fmul_rn(u, u), __fmul_rn(v, v)));
             const unsigned oc = S.occ[par][o];
             const float n0 = S.n0[o];
             const float nm = S.coupling ? __fadd_rn(n0, __fmul_rn((float)(oc < FP_NP_CAP ? oc : FP_NP_CAP), n0)) : n0;
             const float c = __fmul_rn(__fmul_rn(__fmul_rn(__fmul_rn(st.dtf, g), nm), nm), sp);
-            const float denom = __fadd_rn(__fmul_rn(c, pow_m43(hh)), 1.0f);
-            qu = __fdiv_rn(qu, denom);
-            qv = __fdiv_rn(qv, denom);
+            const float rd = rcp_fast(__fadd_rn(__fmul_rn(c, pow_m43(hh)), 1.0f));
+            qu = __fmul_rn(qu, rd);
+            qv = __fmul_rn(qv, rd);
         }
         if (STAGE == 1) {
             S.mh[o] = hh; S.mhu[o] = qu; S.mhv[o] = qv;
         } else {
-            const float h0 = S.h[par][o];
-            hh = 0.5f * __fadd_rn(h0, hh);
+            hh = 0.5f * __fadd_rn(S.h[par][o], hh);
             qu = 0.5f * __fadd_rn(S.hu[par][o], qu);
             qv = 0.5f * __fadd_rn(S.hv[par][o], qv);
             if (hh <= FP_H_EPS_F) { qu = 0.0f; qv = 0.0f; }

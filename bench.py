@@ -82,12 +82,11 @@ def workload(seed):
 def launches_per_chunk(sc, hash_ahead):
     """Kernel launches of one benchmark step (CHUNK coupled steps after a
     restore): the first step opens with a hashing pass over all records
-    (hash_count, flood, the scan's two launches, gather, pedestrian update: 6
-    launches); with the records hashed ahead and no barrier to build, every
-    later step is the flood, scan, gather and pedestrian kernels alone (5),
-    else 6."""
+    (hash_count, flood, scan, gather, pedestrian update: 5 launches); with the
+    records hashed ahead and no barrier to build, every later step is the
+    flood, scan, gather and pedestrian kernels alone (4), else 5."""
     opening = (not hash_ahead) or (len(sc.barrier_cells) > 0 and sc.n_layers > 0)
-    return 6 + (CHUNK - 1) * (6 if opening else 5)
+    return 5 + (CHUNK - 1) * (5 if opening else 4)
 
 
 def combine_ranks(t_sec, updates, device):

@@ -241,6 +241,8 @@ static cudaError_t drop_hash(fp_sim *s) {
     s->hashed = false;
     cudaError_t e = cudaMemsetAsync(s->S.bin_count, 0, ((size_t)s->S.nbins + 1) * sizeof(int), s->stream);
     if (e == cudaSuccess)
+        e = cudaMemsetAsync(s->S.tile_sum, 0, (size_t)fp_scan_tiles(s->S.nbins) * sizeof(int), s->stream);
+    if (e == cudaSuccess)
         e = cudaMemsetAsync(s->S.occ[s->par], 0, s->plane_elems() * sizeof(unsigned short), s->stream);
     return e;
 }
@@ -1238,6 +1240,7 @@ static cudaError_t clear_device_error(fp_sim *s) {
     const FpSim &S = s->S;
     s->hashed = false;
     cudaError_t e = cudaMemsetAsync(S.bin_count, 0, ((size_t)S.nbins + 1) * sizeof(int), s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(S.tile_sum, 0, (size_t)fp_scan_tiles(S.nbins) * sizeof(int), s->stream);
     for (int p = 0; p < 2 && e == cudaSuccess; ++p)
         e = cudaMemsetAsync(S.occ[p], 0, s->plane_elems() * sizeof(unsigned short), s->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(&S.cnt->err, 0, sizeof(unsigned), s->stream);

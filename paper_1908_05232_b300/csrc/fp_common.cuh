@@ -42,6 +42,7 @@
 #define FP_ERR_BAD_PED 8u
 #define FP_ERR_CAPACITY 16u   // a door admission past the pedestrian capacity was refused
 
+#define FP_SCAN_TILE 2048      // bins per tile of the bin-count scan
 #define FP_MAX_DOORS 8
 #define FP_TASK_VISIT0 8      // evacuee task 8 + d: a visitor bound for door d
 
@@ -114,7 +115,7 @@ struct FpSim {
     int *bin_count;            // nbins + 1 (last = exited)
     int *bin_start;            // nbins + 2
     int *pkey, *pslot;         // per record of B
-    int *tile_sum;             // per scan tile of 2048 bins: the sum of its counts
+    int *tile_sum;             // per scan tile of FP_SCAN_TILE bins: the records hashed into it (zeroed by the gather)
     double *bflux;             // 2 nx + 2 ny inflow volume per boundary face (S, N, W, E)
     double *partials;          // mass reduction partial sums
     int *scan_part;            // persistent kernel: bin-count total of each CTA's chunk
@@ -294,6 +295,9 @@ __device__ __forceinline__ float2 fp_step_draws(const FpSim &S, unsigned id, lon
 }
 
 __device__ __forceinline__ void fp_set_err(const FpSim &S, unsigned int bit) { atomicOr(&S.cnt->err, bit); }
+
+// tiles of the bin-count scan (the bins and the exited bin)
+__device__ __forceinline__ int fp_scan_tiles_dev(int nbins) { return (nbins + 1 + FP_SCAN_TILE - 1) / FP_SCAN_TILE; }
 
 // launchers (defined in flood.cu / peds.cu)
 void fp_launch_flood(const FpSim &S, int par, int slot, int tile_rows, cudaStream_t st, bool pdl = false);

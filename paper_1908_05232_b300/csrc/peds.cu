@@ -4,13 +4,13 @@
 //   step_begin  the sandbag layers and bag snapshot alone, for a step whose
 //               records the previous pedestrian step already hashed (only
 //               where a barrier can be built);
-//   scan        exclusive scan of the bin counts in two launches: the sum
-//               of every tile of 2048 bins, then per tile the sum of the tiles
-//               before it and the tile's own scan -> bin starts (no atomics,
-//               no waits); re-zeroes the counts; the exited bin's start is the
-//               new count;
+//   scan        exclusive scan of the bin counts: per tile of 2048 bins the
+//               sum of the tile counts before it (the hashing counted the
+//               records of every tile) and the tile's own scan -> bin starts
+//               (no waits); re-zeroes the bin counts; the exited bin's start
+//               is the new count;
 //   gather      moves each record of B to its bin's range in A; exited
-//               records go to the by-id archive;
+//               records go to the by-id archive; re-zeroes the tile counts;
 //   ped_step    eight lanes per record of A (peds_dev.cuh); the first warp
 //               of block 0 then admits the step's visitors through the doors.
 #include "peds_dev.cuh"
@@ -19,6 +19,7 @@ namespace {
 using namespace fpdev;
 
 constexpr int kScanItems = 8, kScanThreads = 256, kScanTile = kScanItems * kScanThreads;
+static_assert(kScanTile == FP_SCAN_TILE, "the hashing counts records per scan tile");
 static_assert(kScanItems == 8, "scan_load and scan_tile move a thread's bins as two int4");
 
 __global__ void hash_count_kernel(const __grid_constant__ FpSim S, int par) {
@@ -70,19 +71,8 @@ __device__ __forceinline__ int block_sum(int x) {
     return s_tot;
 }
 
-// First launch: the sum of the counts of tile `tile`.
-__device__ __forceinline__ void scan_sum_tile(const FpSim &S, int tile) {
-    int v[kScanItems];
-    scan_load(S, tile * kScanTile + threadIdx.x * kScanItems, S.nbins + 1, v);
-    int sum = 0;
-#pragma unroll
-    for (int k = 0; k < kScanItems; ++k) sum += v[k];
-    const int total = block_sum(sum);
-    if (threadIdx.x == 0) S.tile_sum[tile] = total;
-}
-
-// Second launch: the tile's exclusive prefix is the sum of the tiles before
-// it (all written by the first launch); then the tile's own exclusive scan.
+// The tile's exclusive prefix is the sum of the records the hashing counted
+// in the tiles before it; then the tile's own exclusive scan.
 __device__ __forceinline__ void scan_tile(const FpSim &S, int tile) {
     __shared__ int s_warp[kScanThreads / 32];
     const int tid = threadIdx.x;
@@ -140,14 +130,8 @@ __device__ __forceinline__ void scan_tile(const FpSim &S, int tile) {
         }
 }
 
-__global__ void __launch_bounds__(kScanThreads) scan_sum_kernel(const __grid_constant__ FpSim S) {
-    fp_pdl_wait();     // the step's opening kernel (the counts)
-    fp_pdl_trigger();  // the scan may be scheduled now; it waits for this grid's end
-    scan_sum_tile(S, blockIdx.x);
-}
-
 __global__ void __launch_bounds__(kScanThreads) scan_kernel(const __grid_constant__ FpSim S) {
-    fp_pdl_wait();     // the tile sums
+    fp_pdl_wait();     // the step's opening kernel (the counts)
     fp_pdl_trigger();  // the gather may be scheduled now; it waits for this grid's end
     scan_tile(S, blockIdx.x);
 }
@@ -194,6 +178,8 @@ __global__ void gather_kernel(const __grid_constant__ FpSim S, int slot) {
     const float2 xi = fp_step_draws(S, b.x, step);
     fp_pdl_wait();
     fp_pdl_trigger();
+    // the scan has read the tile counts: clear them for the next hashing
+    for (int t = i; t < fp_scan_tiles_dev(S.nbins); t += gridDim.x * blockDim.x) S.tile_sum[t] = 0;
     if (!in || i >= nB) return;
     gather_place(S, key, bslot, a, b, xi);
 }
@@ -293,12 +279,6 @@ __global__ void hash_count_batch_kernel(const FpSim *__restrict__ sims, const in
     hash_record(S, i, __uint_as_float(pa.x), __uint_as_float(pa.y), pb.y, S.occ[par]);
 }
 
-__global__ void __launch_bounds__(kScanThreads) scan_sum_batch_kernel(const FpSim *__restrict__ sims) {
-    const FpSim &S = sims[blockIdx.y];
-    if ((int)blockIdx.x >= (S.nbins + 1 + kScanTile - 1) / kScanTile) return;
-    scan_sum_tile(S, blockIdx.x);
-}
-
 __global__ void __launch_bounds__(kScanThreads) scan_batch_kernel(const FpSim *__restrict__ sims) {
     const FpSim &S = sims[blockIdx.y];
     if ((int)blockIdx.x >= (S.nbins + 1 + kScanTile - 1) / kScanTile) return;
@@ -310,6 +290,7 @@ __global__ void gather_batch_kernel(const FpSim *__restrict__ sims, const int *_
     const int s = batch_member(rec_off, n, blockIdx.x * blockDim.x);
     const FpSim &S = sims[s];
     const int i = blockIdx.x * blockDim.x + threadIdx.x - rec_off[s];
+    for (int t = i; t < fp_scan_tiles_dev(S.nbins); t += rec_off[s + 1] - rec_off[s]) S.tile_sum[t] = 0;
     if (i < S.cnt->nB) gather_record(S, i, S.clock[slot].step);
 }
 
@@ -345,7 +326,6 @@ void fp_launch_batch_peds(const FpSim *d_sims, const int *d_rec_off, int n, int 
         cudaEventRecord(fork, st_hash);
         return;
     }
-    scan_sum_batch_kernel<<<dim3(max_scan_tiles, n), kScanThreads, 0, st_chain>>>(d_sims);
     scan_batch_kernel<<<dim3(max_scan_tiles, n), kScanThreads, 0, st_chain>>>(d_sims);
     gather_batch_kernel<<<total_rec / 256, 256, 0, st_chain>>>(d_sims, d_rec_off, n, slot);
     ped_step_batch_kernel<<<total_rec * kGroup / 256, 256, 0, st_chain>>>(d_sims, d_rec_off, n, par, slot);
@@ -357,7 +337,6 @@ void fp_launch_hash_count(const FpSim &S, int par, cudaStream_t st) {
     hash_count_kernel<<<blocks_for(S.cap, 256), 256, 0, st>>>(S, par);
 }
 void fp_launch_scan(const FpSim &S, cudaStream_t st, bool pdl) {
-    fp_launch(pdl, scan_sum_kernel, dim3(fp_scan_tiles(S.nbins)), dim3(kScanThreads), 0, st, S);
     fp_launch(pdl, scan_kernel, dim3(fp_scan_tiles(S.nbins)), dim3(kScanThreads), 0, st, S);
 }
 void fp_launch_gather(const FpSim &S, int slot, cudaStream_t st, bool pdl) {

@@ -4,8 +4,9 @@
 //
 //   hash_record   a record's hash bin (hk x hk cells, bin side >= the 1 m
 //                 neighbour radius) or the "exited" bin, its slot in the bin
-//                 (integer atomic) and the evacuee count of its cell (uint16
-//                 lanes of the occupancy plane, N_p of Section 2.4);
+//                 (integer atomic), its scan tile's record count and the
+//                 evacuee count of its cell (uint16 lanes of the occupancy
+//                 plane, N_p of Section 2.4);
 //   barrier_and_snapshot   completed sandbag layers raise z;
 //   ped_group     eight lanes per pedestrian: Table 1 state from the cell's
 //                 h, u, v at step n, responder task, navigation direction,
@@ -140,6 +141,9 @@ __device__ __forceinline__ void hash_record(const FpSim &S, int i, float x, floa
     const int bfirst = first;
     int base = 0;
     if (lane == first) base = atomicAdd(&S.bin_count[key], n);
+    // the scan's tile sums: a run of lanes in one tile adds its records with one atomic
+    lane_run(act, (unsigned long long)(key / FP_SCAN_TILE), &first, &n);
+    if (lane == first) atomicAdd(&S.tile_sum[key / FP_SCAN_TILE], n);
     // evacuee counts: runs of evacuees on one cell (other lanes are runs of one);
     // both atomics are in flight before either result is used
     lane_run(act, evac ? (unsigned long long)o : ~0ull - (unsigned long long)lane, &first, &n);

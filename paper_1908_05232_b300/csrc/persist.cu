@@ -190,6 +190,9 @@ __global__ void __launch_bounds__(kPT, 1) persistent_kernel(const __grid_constan
         }
         const ChunkLookup lookup{S.bin_start, s_base, chunk};
         const int nA = lookup(S.nbins);
+        // this kernel's scan does not read the hashing's tile counts: keep them
+        // at zero for the per-step kernels' scan of a later step
+        for (int t = cta * kPT + tid; t < fp_scan_tiles_dev(S.nbins); t += G * kPT) S.tile_sum[t] = 0;
         {
             const int nB = C->nB;
             for (int i = cta * kPT + tid; i < nB; i += G * kPT) {

@@ -63,15 +63,15 @@ def test_reference_arm_other_ranks_exit(monkeypatch, capsys):
 
 def test_launch_count_follows_the_step_structure():
     """gpu_launches: after a restore the first step hashes in a pass of its
-    own (6 launches: hash, flood, the scan's two, gather, pedestrian update);
-    then 5 per step with hash-ahead and no barrier, else 6 -- the per-kernel
-    launch counts of the ncu launch list of 64 steps."""
+    own (5 launches: hash, flood, scan, gather, pedestrian update); then 4 per
+    step with hash-ahead and no barrier, else 5 -- the per-kernel launch
+    counts of the ncu launch list of 64 steps."""
     import sys
     sys.path.insert(0, ROOT)
     import bench
     import scenarios
     plain = scenarios.config_shopping()
-    assert bench.launches_per_chunk(plain, True) == 6 + (bench.CHUNK - 1) * 5
-    assert bench.launches_per_chunk(plain, False) == 6 * bench.CHUNK
+    assert bench.launches_per_chunk(plain, True) == 5 + (bench.CHUNK - 1) * 4
+    assert bench.launches_per_chunk(plain, False) == 5 * bench.CHUNK
     barrier = scenarios.shopping_centre(128, 0.5, 100, 10, 1, 600.0, n_barrier=8, n_layers=2)
-    assert bench.launches_per_chunk(barrier, True) == 6 * bench.CHUNK
+    assert bench.launches_per_chunk(barrier, True) == 5 * bench.CHUNK

@@ -5,8 +5,9 @@ Workload (default): the pre-flood barrier deployment at scale taken up
 mid-flood -- 2048 x 2048 cells of 0.5 m, 100,000 pedestrians of which 500
 responders building a 200-cell, 2-layer sandbag barrier, evacuee roughness
 coupling on, the triangular depth hydrograph at its 1.0 m peak (t = 1500 s),
-the synthetic mid-flood state of ``scenarios.config_barrier_midflood`` (about
-15 % of the cells wet, the responders mid-deployment).  One benchmark step =
+the synthetic mid-flood state of ``scenarios.config_barrier_midflood`` (9 %
+of the cells wet, the water within 300 m of the breach, the responders
+mid-deployment).  One benchmark step =
 restore that snapshot (untimed), flush L2, then 512 coupled simulation steps
 through the C ABI (``fp_step``), timed with CUDA events on the simulation's
 stream.
@@ -26,8 +27,9 @@ roofline the flood kernel (HBM-bound stencil), 34 algorithmic bytes per cell
         ``roofline_wet2048`` the flood kernel alone on a
         2048 x 2048 grid holding water almost everywhere.
 cpu_baseline the FP64 C oracle on one coupled step of the same snapshot.
-batched  a seeded ensemble of shopping centres stepped together by the batched
-        kernels against the same simulations stepped one by one
+batched  a seeded ensemble of shopping centres stepped together (per-step
+        batch kernels in graphs, and one persistent launch per 256 steps: the
+        faster is ``value``) against the same simulations stepped one by one
         (scenario-seconds/s).
 surrogate the learned surrogate's windows against the plain update from the
         same snapshot at a fixed step (scenario-seconds/s), with the largest
@@ -288,8 +290,9 @@ class Snapshot:
 def batched_figures(P, args, dev):
     """A seeded ensemble of shopping centres (grid side 128-1024, 1k-50k
     pedestrians, 50-1000 responders, 1-3 sandbag layers, inflow peak 0.3-1.5
-    m) stepped together by the batched kernels against the same simulations
-    stepped one by one, each arm's step graphs captured before its timing."""
+    m) stepped together -- by the per-step batch kernels (64-step graphs) and
+    by one persistent launch per 256 steps -- against the same simulations
+    stepped one by one, each arm warmed (graphs captured) before its timing."""
     import torch
     import scenarios
     t0 = time.perf_counter()
@@ -312,6 +315,19 @@ def batched_figures(P, args, dev):
     batch.synchronize()
     t_batch = time.perf_counter() - t0
     s1 = sim_seconds()
+    # the same ensemble in one persistent launch per 256 steps
+    from paper_1908_05232_b300 import _native as N
+    t_pers = None
+    if N.lib().fp_batch_set_step_mode(batch.h, N.FP_MODE_PERSISTENT) == N.FP_OK:
+        batch.step(chunk)
+        batch.synchronize()
+        sp0 = sim_seconds()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        batch.step(chunk * reps)
+        batch.synchronize()
+        t_pers = time.perf_counter() - t0
+        sp1 = sim_seconds()
     batch.close()
     for sim in sims:  # the members' own step graphs (hashing and hashed-ahead openings)
         sim.step(2 * chunk)
@@ -326,10 +342,14 @@ def batched_figures(P, args, dev):
     for sim in sims:
         sim.close()
     rate_b, rate_1 = (s1 - s0) / t_batch, (s2 - s1w) / t_single
-    return {"value": rate_b, "unit": "scenario-s/s", "one_by_one": rate_1, "speedup_vs_one_by_one": rate_b / rate_1,
+    rate_p = (sp1 - sp0) / t_pers if t_pers else None
+    best = max(rate_b, rate_p or 0.0)
+    return {"value": best, "unit": "scenario-s/s", "one_by_one": rate_1, "speedup_vs_one_by_one": best / rate_1,
+            "kernels_graphs": rate_b, "persistent": rate_p,
+            "mode": "persistent" if rate_p and rate_p > rate_b else "kernels_graphs",
             "scenarios": len(scs), "cells": int(sum(sc.nx * sc.ny for sc in scs)),
             "pedestrians": int(sum(sc.n_peds for sc in scs)), "steps_timed": chunk * reps,
-            "seconds": {"batched": t_batch, "one_by_one": t_single, "setup": setup},
+            "seconds": {"batched": t_batch, "persistent": t_pers, "one_by_one": t_single, "setup": setup},
             "workload": "ensemble(%d): shopping centres of side 128-1024 cells (0.5 m), 1k-50k pedestrians"
                         % len(scs)}
 

@@ -321,6 +321,15 @@ int fp_set_profiling(fp_sim *sim, int32_t on);
 typedef struct fp_batch fp_batch;
 int fp_batch_create(fp_sim *const *sims, int32_t n, fp_batch **out);
 int fp_batch_step(fp_batch *batch, int32_t n_steps);
+/* How fp_batch_step runs (both give every member the bytes of stepping it alone):
+ * FP_MODE_KERNELS (default): per step one set of batch kernels, 64-step CUDA
+ *   graphs; FP_MODE_PERSISTENT (devices with cooperative launch): up to 256
+ *   steps of every member per launch of one persistent kernel (every CTA
+ *   resident), the phases of a step separated by grid barriers with bounded
+ *   waits (member 0's fp_set_barrier_wait_limit; a wait that gives up is
+ *   reported by fp_batch_synchronize as FP_ETIMEOUT).  FP_EINVAL for another
+ *   mode or no cooperative launch. */
+int fp_batch_set_step_mode(fp_batch *batch, int32_t mode);
 int fp_batch_synchronize(fp_batch *batch);
 int fp_batch_destroy(fp_batch *batch);
 

@@ -91,6 +91,7 @@ def lib():
             "fp_set_tuning": [_VP, ctypes.c_int32, ctypes.c_int32], "fp_set_hash_ahead": [_VP, ctypes.c_int32],
             "fp_batch_create": [_VP, ctypes.c_int32, _VP], "fp_batch_step": [_VP, ctypes.c_int32],
             "fp_batch_synchronize": [_VP], "fp_batch_destroy": [_VP], "fp_set_profiling": [_VP, ctypes.c_int32],
+            "fp_batch_set_step_mode": [_VP, ctypes.c_int32],
             "fp_read_state": [_VP, ctypes.c_int32, _VP, ctypes.c_size_t], "fp_destroy": [_VP],
             "fp_set_fixed_dt": [_VP, ctypes.c_double], "fp_set_barrier_wait_limit": [_VP, ctypes.c_int32], "fp_surrogate_advance": [_VP, _VP, ctypes.c_int32, _VP, _VP],
         }
@@ -343,13 +344,19 @@ class Simulation:
 
 
 class Batch:
-    """Members (``Simulation`` objects) stepped together by the batched kernels."""
+    """Members (``Simulation`` objects) stepped together by the batched kernels
+    (mode FP_MODE_KERNELS) or one persistent kernel (FP_MODE_PERSISTENT)."""
 
-    def __init__(self, sims):
+    def __init__(self, sims, mode=None):
         self.sims = list(sims)
         arr = (_VP * len(self.sims))(*[s.h for s in self.sims])
         self.h = _VP()
         _check(lib().fp_batch_create(arr, len(self.sims), ctypes.byref(self.h)))
+        if mode is not None:
+            self.set_mode(mode)
+
+    def set_mode(self, mode):
+        _check(lib().fp_batch_set_step_mode(self.h, int(mode)))
 
     def step(self, n=1):
         _check(lib().fp_batch_step(self.h, int(n)))

@@ -15,7 +15,7 @@ LIB = os.path.join(HERE, "libfloodped.so")
 OBJ = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC", "-I", INC, "-I", CSRC]
-SOURCES = [("flood.cu", []), ("peds.cu", []), ("floodped.cu", []), ("noalloc.cu", []), ("persist.cu", []), ("surrogate.cu", []), ("window.cu", []), ("muscl.cu", [])]
+SOURCES = [("flood.cu", []), ("peds.cu", []), ("floodped.cu", []), ("noalloc.cu", []), ("persist.cu", []), ("surrogate.cu", []), ("window.cu", []), ("muscl.cu", []), ("batch.cu", [])]
 
 
 def _inputs():

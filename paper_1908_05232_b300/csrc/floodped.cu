@@ -31,6 +31,7 @@
 namespace {
 
 constexpr int kGraphSteps = 64;
+constexpr int kPersistSteps = 256;  // steps per launch of a persistent kernel
 constexpr int kProfEvents = 6;  // CUDA events per profiled step
 std::string g_create_error;
 
@@ -939,7 +940,7 @@ int fp_step(fp_sim *s, int32_t n_steps) {
         if (eh != cudaSuccess) return s->cuda_fail(eh, "hash reset");
         int left = n_steps;
         while (left > 0) {
-            const int n = left < 256 ? left : 256;
+            const int n = left < kPersistSteps ? left : kPersistSteps;
             cudaError_t e = fp_launch_persistent(s->S, s->par, s->slot, n, s->grid_bar, s->persist_ctas, s->stream);
             if (e != cudaSuccess) return s->cuda_fail(e, "persistent launch");
             if (n & 1) s->par ^= 1;
@@ -1383,6 +1384,9 @@ struct fp_batch {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaGraphExec_t graphs[4] = {nullptr, nullptr, nullptr, nullptr};
     std::vector<void *> allocs;
+    int mode = FP_MODE_KERNELS;
+    int ctas = 0;            // CTAs of the persistent launch
+    unsigned *bar = nullptr;  // grid barrier word + pedestrian tickets (4 words)
 };
 
 static void batch_launch_step(fp_batch *b, int par, int slot) {
@@ -1433,7 +1437,8 @@ int fp_batch_create(fp_sim *const *sims, int32_t n, fp_batch **out) {
     b->d_sims = static_cast<FpSim *>(alloc(sizeof(FpSim) * n));
     b->d_run_off = static_cast<int *>(alloc(sizeof(int) * (n + 1)));
     b->d_rec_off = static_cast<int *>(alloc(sizeof(int) * (n + 1)));
-    if (!b->d_sims || !b->d_run_off || !b->d_rec_off) {
+    b->bar = static_cast<unsigned *>(alloc(4 * sizeof(unsigned)));
+    if (!b->d_sims || !b->d_run_off || !b->d_rec_off || !b->bar) {
         fp_batch_destroy(b);
         g_create_error = "fp_batch_create: device allocation failed";
         return FP_ENOMEM;
@@ -1483,6 +1488,15 @@ int fp_batch_step(fp_batch *b, int32_t n_steps) {
         return FP_ECUDA;
     }
     int p = par, sl = slot, left = n_steps;
+    while (left > 0 && b->mode == FP_MODE_PERSISTENT) {
+        const int k = std::min(left, kPersistSteps);
+        e = fp_launch_batch_persistent(b->d_sims, b->d_run_off, b->d_rec_off, b->n, b->total_runs, b->total_rec,
+                                       b->max_scan_tiles, p, sl, k, b->bar, b->ctas, b->stream);
+        if (e != cudaSuccess) break;
+        p ^= k & 1;
+        sl = (sl + k) & 3;
+        left -= k;
+    }
     while (left > 0) {
         if (left >= kGraphSteps) {
             cudaGraphExec_t &g = b->graphs[sl];
@@ -1524,6 +1538,28 @@ int fp_batch_step(fp_batch *b, int32_t n_steps) {
     return FP_OK;
 }
 
+int fp_batch_set_step_mode(fp_batch *b, int32_t mode) {
+    if (!b) return FP_EINVAL;
+    if (mode != FP_MODE_KERNELS && mode != FP_MODE_PERSISTENT) {
+        g_create_error = "fp_batch_set_step_mode: unknown step mode";
+        return FP_EINVAL;
+    }
+    if (mode == FP_MODE_PERSISTENT) {
+        if (b->ctas <= 0) b->ctas = fp_batch_persistent_ctas();
+        if (b->ctas <= 0) {
+            g_create_error = "fp_batch_set_step_mode: cooperative launch unavailable on this device";
+            return FP_EINVAL;
+        }
+    }
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) {
+        g_create_error = std::string("fp_batch_set_step_mode: ") + cudaGetErrorString(e);
+        return FP_ECUDA;
+    }
+    b->mode = mode;
+    return FP_OK;
+}
+
 int fp_batch_synchronize(fp_batch *b) {
     if (!b) return FP_EINVAL;
     cudaError_t e = cudaStreamSynchronize(b->stream);
@@ -1531,14 +1567,27 @@ int fp_batch_synchronize(fp_batch *b) {
         g_create_error = std::string("fp_batch_synchronize: ") + cudaGetErrorString(e);
         return FP_ECUDA;
     }
+    // every member's error is read (each is reported once); after any error the
+    // hashing state of every member is reset: a persistent launch that gave up
+    // leaves all members part-way through a step
+    int first = FP_OK;
     for (fp_sim *m : b->sims) {
         const int rc = fp_synchronize(m);
-        if (rc != FP_OK) {
+        if (rc != FP_OK && first == FP_OK) {
+            first = rc;
             g_create_error = m->err;
-            return rc;
         }
     }
-    return FP_OK;
+    if (first != FP_OK) {
+        for (fp_sim *m : b->sims) {
+            e = clear_device_error(m);
+            if (e != cudaSuccess) {
+                g_create_error = std::string("fp_batch_synchronize: ") + cudaGetErrorString(e);
+                return FP_ECUDA;
+            }
+        }
+    }
+    return first;
 }
 
 int fp_batch_destroy(fp_batch *b) {

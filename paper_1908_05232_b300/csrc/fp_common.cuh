@@ -318,6 +318,10 @@ void fp_launch_read_peds(const FpSim &S, uint4 *out, int n_total, cudaStream_t s
 int fp_scan_tiles(int nbins);
 void fp_note_error(const char *msg);  // message for fp_last_error(NULL)
 int fp_persistent_ctas();
+int fp_batch_persistent_ctas();
+cudaError_t fp_launch_batch_persistent(const FpSim *d_sims, const int *d_run_off, const int *d_rec_off, int n,
+                                       int total_runs, int total_rec, int max_tiles, int par, int slot, int nsteps,
+                                       unsigned *bar, int ctas, cudaStream_t st);
 void fp_launch_batch_peds(const FpSim *d_sims, const int *d_rec_off, int n, int total_rec, int max_scan_tiles,
                           int par, int slot, cudaStream_t st_hash, cudaStream_t st_chain, cudaEvent_t fork,
                           bool hash_part);

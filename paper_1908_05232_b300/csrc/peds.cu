@@ -18,9 +18,6 @@
 namespace {
 using namespace fpdev;
 
-constexpr int kScanItems = 8, kScanThreads = 256, kScanTile = kScanItems * kScanThreads;
-static_assert(kScanTile == FP_SCAN_TILE, "the hashing counts records per scan tile");
-static_assert(kScanItems == 8, "scan_load and scan_tile move a thread's bins as two int4");
 
 __global__ void hash_count_kernel(const __grid_constant__ FpSim S, int par) {
     fp_pdl_trigger();  // the scan may be scheduled now; it waits for this grid's end
@@ -40,122 +37,10 @@ __global__ void step_begin_kernel(const __grid_constant__ FpSim S) {
     barrier_and_snapshot(S);
 }
 
-// The counts of this thread's kScanItems consecutive bins of tile `tile`
-// (0 past the last bin), two 16-byte loads where the tile is whole.
-__device__ __forceinline__ void scan_load(const FpSim &S, int base, int n, int v[kScanItems]) {
-    if (base + kScanItems <= n) {
-        const int4 a = *reinterpret_cast<const int4 *>(S.bin_count + base);
-        const int4 b = *reinterpret_cast<const int4 *>(S.bin_count + base + 4);
-        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-        v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
-    } else {
-#pragma unroll
-        for (int k = 0; k < kScanItems; ++k) v[k] = base + k < n ? S.bin_count[base + k] : 0;
-    }
-}
-
-// Block sum of one int per thread (every thread gets it).
-__device__ __forceinline__ int block_sum(int x) {
-    __shared__ int s_red[kScanThreads / 32];
-    __shared__ int s_tot;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = x;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int t = 0;
-        for (int w = 0; w < kScanThreads / 32; ++w) t += s_red[w];
-        s_tot = t;
-    }
-    __syncthreads();
-    return s_tot;
-}
-
-// The tile's exclusive prefix is the sum of the records the hashing counted
-// in the tiles before it; then the tile's own exclusive scan.
-__device__ __forceinline__ void scan_tile(const FpSim &S, int tile) {
-    __shared__ int s_warp[kScanThreads / 32];
-    const int tid = threadIdx.x;
-    FpCounters *C = S.cnt;
-    if (tile == 0 && tid < 5) C->hist[tid] = 0ull;  // the step's state histogram (the pedestrian kernel fills it)
-    const int n = S.nbins + 1;
-    const int base = tile * kScanTile + tid * kScanItems;
-    int part = 0;
-    for (int t = tid; t < tile; t += kScanThreads) part += S.tile_sum[t];
-    int v[kScanItems];
-    scan_load(S, base, n, v);
-    const int prefix = block_sum(part);
-    int sum = 0;
-#pragma unroll
-    for (int k = 0; k < kScanItems; ++k) sum += v[k];
-    // block exclusive scan of the per-thread sums
-    const int lane = tid & 31, wid = tid >> 5;
-    int incl = sum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += t;
-    }
-    if (lane == 31) s_warp[wid] = incl;
-    __syncthreads();
-    int wpre = 0;
-    for (int w = 0; w < wid; ++w) wpre += s_warp[w];
-    int run = prefix + wpre + incl - sum;
-    int out[kScanItems];
-#pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-        out[k] = run;
-        run += v[k];
-    }
-    if (base + kScanItems <= n) {
-        const int4 z = make_int4(0, 0, 0, 0);
-        *reinterpret_cast<int4 *>(S.bin_count + base) = z;
-        *reinterpret_cast<int4 *>(S.bin_count + base + 4) = z;
-        *reinterpret_cast<int4 *>(S.bin_start + base) = make_int4(out[0], out[1], out[2], out[3]);
-        *reinterpret_cast<int4 *>(S.bin_start + base + 4) = make_int4(out[4], out[5], out[6], out[7]);
-    } else {
-#pragma unroll
-        for (int k = 0; k < kScanItems; ++k)
-            if (base + k < n) {
-                S.bin_count[base + k] = 0;
-                S.bin_start[base + k] = out[k];
-            }
-    }
-    // the exited bin (the last) starts where the records still present end
-#pragma unroll
-    for (int k = 0; k < kScanItems; ++k)
-        if (base + k == n - 1) {
-            S.bin_start[n] = out[k] + v[k];
-            C->nA = out[k];
-        }
-}
-
 __global__ void __launch_bounds__(kScanThreads) scan_kernel(const __grid_constant__ FpSim S) {
     fp_pdl_wait();     // the step's opening kernel (the counts)
     fp_pdl_trigger();  // the gather may be scheduled now; it waits for this grid's end
     scan_tile(S, blockIdx.x);
-}
-
-// Record i of B to its place in A (or, gone, to the by-id archive), with the
-// step's two uniform draws the pedestrian kernel reads beside it.
-__device__ __forceinline__ void gather_place(const FpSim &S, int key, int bslot, const uint4 &a, const uint4 &b,
-                                             float2 xi) {
-    if (key == S.nbins) {
-        S.arch[2 * (size_t)b.x] = a;
-        S.arch[2 * (size_t)b.x + 1] = b;
-    } else {
-        const int dst = S.bin_start[key] + bslot;
-        S.pedA[2 * dst] = a;
-        S.pedA[2 * dst + 1] = b;
-        S.posA[dst] = make_float2(__uint_as_float(a.x), __uint_as_float(a.y));
-        S.xiA[dst] = xi;
-    }
-}
-
-__device__ __forceinline__ void gather_record(const FpSim &S, int i, long long step) {
-    const int key = S.pkey[i];
-    const uint4 a = S.pedB[2 * i], b = S.pedB[2 * i + 1];
-    gather_place(S, key, S.pslot[i], a, b, fp_step_draws(S, b.x, step));
 }
 
 __global__ void gather_kernel(const __grid_constant__ FpSim S, int slot) {
@@ -203,7 +88,7 @@ __global__ void __launch_bounds__(256) ped_step_kernel(const __grid_constant__ F
     load_step_ctl(S, slot, 0, ctl);
     fp_pdl_wait();
     fp_pdl_trigger();  // the next step's scan may be scheduled; it waits for this grid's end
-    ctl.nA = C->nA;
+    ctl.nA = min(C->nA, S.cap);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         C->nB = ctl.nA;
         if (ctl.dt_ticks > 0) C->ped_updates += (unsigned long long)ctl.nA;
@@ -258,14 +143,6 @@ inline int blocks_for(int n, int t) { return n <= 0 ? 1 : (n + t - 1) / t; }
 // Flat record space: member s owns [rec_off[s], rec_off[s+1]), a multiple of 256
 // records long, so every CTA belongs to one member.
 
-__device__ __forceinline__ int batch_member(const int *off, int n, int x) {
-    int lo = 0, hi = n - 1;  // largest s with off[s] <= x
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (off[mid] <= x) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
 
 __global__ void hash_count_batch_kernel(const FpSim *__restrict__ sims, const int *__restrict__ rec_off, int n,
                                         int par) {

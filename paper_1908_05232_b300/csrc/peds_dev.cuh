@@ -95,7 +95,7 @@ __device__ __forceinline__ void load_step_ctl(const FpSim &S, int slot, int nA, 
     ctl.step = c.step;
     ctl.wet = c.wet;
     ctl.bags = S.cnt->bags_snap;
-    ctl.nA = nA;
+    ctl.nA = min(nA, S.cap);  // the records of A never exceed the capacity
 }
 
 // Hash one record of B (index i) for the next step: its bin (or the exited bin),
@@ -232,7 +232,7 @@ __device__ __forceinline__ void ped_group(const FpSim &S, int par, const StepCtl
                     const int yy = by - 1 + r;
                     if (yy < 0 || yy >= S.nby) { rk0[r] = 0; rk1[r] = 0; continue; }
                     rk0[r] = lookup(yy * S.nbx + bx0);
-                    rk1[r] = lookup(yy * S.nbx + bx1 + 1);
+                    rk1[r] = min(lookup(yy * S.nbx + bx1 + 1), ctl.nA);  // never read past the records of A
                 }
             }
             hr = fp_hr_state(hc, huc, hvc);
@@ -508,5 +508,138 @@ __device__ __forceinline__ void door_entries(const FpSim &S, int par, const Step
         }
     }
 }
+
+// ---- the bin scan, the gather and the batch's member lookup (shared by the
+// per-step, batch and persistent kernels) ------------------------------------
+constexpr int kScanItems = 8, kScanThreads = 256, kScanTile = kScanItems * kScanThreads;
+static_assert(kScanTile == FP_SCAN_TILE, "the hashing counts records per scan tile");
+static_assert(kScanItems == 8, "scan_load and scan_tile move a thread's bins as two int4");
+
+// The counts of this thread's kScanItems consecutive bins of tile `tile`
+// (0 past the last bin), two 16-byte loads where the tile is whole.
+__device__ __forceinline__ void scan_load(const FpSim &S, int base, int n, int v[kScanItems]) {
+    if (base + kScanItems <= n) {
+        const int4 a = *reinterpret_cast<const int4 *>(S.bin_count + base);
+        const int4 b = *reinterpret_cast<const int4 *>(S.bin_count + base + 4);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+        v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    } else {
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) v[k] = base + k < n ? S.bin_count[base + k] : 0;
+    }
+}
+
+// Block sum of one int per thread (every thread gets it).
+__device__ __forceinline__ int block_sum(int x) {
+    __shared__ int s_red[kScanThreads / 32];
+    __shared__ int s_tot;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = 0;
+        for (int w = 0; w < kScanThreads / 32; ++w) t += s_red[w];
+        s_tot = t;
+    }
+    __syncthreads();
+    return s_tot;
+}
+
+// The tile's exclusive prefix is the sum of the records the hashing counted
+// in the tiles before it; then the tile's own exclusive scan.
+__device__ __forceinline__ void scan_tile(const FpSim &S, int tile) {
+    __shared__ int s_warp[kScanThreads / 32];
+    const int tid = threadIdx.x;
+    FpCounters *C = S.cnt;
+    if (tile == 0 && tid < 5) C->hist[tid] = 0ull;  // the step's state histogram (the pedestrian kernel fills it)
+    const int n = S.nbins + 1;
+    const int base = tile * kScanTile + tid * kScanItems;
+    int part = 0;
+    for (int t = tid; t < tile; t += kScanThreads) part += S.tile_sum[t];
+    int v[kScanItems];
+    scan_load(S, base, n, v);
+    const int prefix = block_sum(part);
+    int sum = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) sum += v[k];
+    // block exclusive scan of the per-thread sums
+    const int lane = tid & 31, wid = tid >> 5;
+    int incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) s_warp[wid] = incl;
+    __syncthreads();
+    int wpre = 0;
+    for (int w = 0; w < wid; ++w) wpre += s_warp[w];
+    int run = prefix + wpre + incl - sum;
+    int out[kScanItems];
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        out[k] = run;
+        run += v[k];
+    }
+    if (base + kScanItems <= n) {
+        const int4 z = make_int4(0, 0, 0, 0);
+        *reinterpret_cast<int4 *>(S.bin_count + base) = z;
+        *reinterpret_cast<int4 *>(S.bin_count + base + 4) = z;
+        *reinterpret_cast<int4 *>(S.bin_start + base) = make_int4(out[0], out[1], out[2], out[3]);
+        *reinterpret_cast<int4 *>(S.bin_start + base + 4) = make_int4(out[4], out[5], out[6], out[7]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k)
+            if (base + k < n) {
+                S.bin_count[base + k] = 0;
+                S.bin_start[base + k] = out[k];
+            }
+    }
+    // the exited bin (the last) starts where the records still present end
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k)
+        if (base + k == n - 1) {
+            S.bin_start[n] = out[k] + v[k];
+            C->nA = out[k];
+        }
+}
+
+// Record i of B to its place in A (or, gone, to the by-id archive), with the
+// step's two uniform draws the pedestrian kernel reads beside it.
+__device__ __forceinline__ void gather_place(const FpSim &S, int key, int bslot, const uint4 &a, const uint4 &b,
+                                             float2 xi) {
+    if (key == S.nbins) {
+        S.arch[2 * (size_t)b.x] = a;
+        S.arch[2 * (size_t)b.x + 1] = b;
+    } else {
+        const int dst = S.bin_start[key] + bslot;
+        if ((unsigned)dst >= (unsigned)S.cap) {  // counts out of step with the records: never write past A
+            fp_set_err(S, FP_ERR_BAD_PED);
+            return;
+        }
+        S.pedA[2 * dst] = a;
+        S.pedA[2 * dst + 1] = b;
+        S.posA[dst] = make_float2(__uint_as_float(a.x), __uint_as_float(a.y));
+        S.xiA[dst] = xi;
+    }
+}
+
+__device__ __forceinline__ void gather_record(const FpSim &S, int i, long long step) {
+    const int key = S.pkey[i];
+    const uint4 a = S.pedB[2 * i], b = S.pedB[2 * i + 1];
+    gather_place(S, key, S.pslot[i], a, b, fp_step_draws(S, b.x, step));
+}
+
+// The member owning flat index x: the largest s with off[s] <= x.
+__device__ __forceinline__ int batch_member(const int *off, int n, int x) {
+    int lo = 0, hi = n - 1;  // largest s with off[s] <= x
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= x) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
 
 }  // namespace fpdev

@@ -25,6 +25,7 @@
 #include <vector>
 
 #include "flood_dev.cuh"
+#include "grid_sync.cuh"
 #include "peds_dev.cuh"
 
 namespace {
@@ -34,45 +35,6 @@ constexpr int kPT = 512;       // threads per CTA = 32 x TY with TY = 16
 constexpr int kPTY = 16;
 constexpr int kMaxCTAs = 2048;
 
-
-// Grid barrier on one word: every CTA adds 1 except CTA 0, which adds
-// 2^31 - (gridDim.x - 1), so the word's top bit flips exactly when the last
-// CTA has arrived (and the low bits are back to zero); each CTA spins until
-// the top bit differs from the value it saw on arrival.  The spin is bounded
-// by S.barrier_polls polls; past 2^10 polls it also watches the error word, so
-// that CTAs leave soon after another CTA failed; on timeout the error flag is
-// set and the CTA returns (those still waiting time out in turn).  No
-// asynchronous copy is in flight at a barrier: the kernel makes none.
-__device__ __forceinline__ bool grid_sync(unsigned *bar, const FpSim &S) {
-    __shared__ int s_fail;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const unsigned add = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1u) : 1u;
-        __threadfence();
-        const unsigned old = atomicAdd(bar, add);
-        volatile unsigned *vb = bar;
-        int fail = 0;
-        const int limit = S.barrier_polls;
-        for (int it = 0; ((*vb ^ old) & 0x80000000u) == 0u; ++it) {
-            if (it >= limit) {
-                fail = 1;
-                break;
-            }
-            if (it >= (1 << 10)) {
-                if ((*(volatile unsigned *)&S.cnt->err & FP_ERR_TIMEOUT) != 0u) {
-                    fail = 1;
-                    break;
-                }
-                __nanosleep(64);
-            }
-        }
-        __threadfence();  // the other CTAs' writes of the phase are seen by this CTA's loads after it
-        if (fail) fp_set_err(S, FP_ERR_TIMEOUT);
-        s_fail = fail;
-    }
-    __syncthreads();
-    return !s_fail;
-}
 
 // exclusive scan of one value per thread over the CTA (kPT threads); returns
 // the thread's prefix, total in *total
@@ -203,6 +165,10 @@ __global__ void __launch_bounds__(kPT, 1) persistent_kernel(const __grid_constan
                     S.arch[2 * (size_t)b.x + 1] = b;
                 } else {
                     const int dst = lookup(key) + S.pslot[i];
+                    if ((unsigned)dst >= (unsigned)S.cap) {  // counts out of step with the records
+                        fp_set_err(S, FP_ERR_BAD_PED);
+                        continue;
+                    }
                     S.pedA[2 * dst] = a;
                     S.pedA[2 * dst + 1] = b;
                     S.posA[dst] = make_float2(__uint_as_float(a.x), __uint_as_float(a.y));

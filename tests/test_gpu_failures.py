@@ -103,6 +103,32 @@ def test_grid_barrier_wait_runs_out_reports_etimeout_and_recovers(P):
     sim.close()
 
 
+def test_batch_persistent_barrier_wait_runs_out(P):
+    """The batch's persistent kernel with member 0's barrier wait limit at 0
+    polls: every wait gives up at once (no spin), fp_batch_synchronize reports
+    FP_ETIMEOUT once, and the batch steps again afterwards."""
+    from paper_1908_05232_b300 import _native as N
+    scs = [S.plain_coupled_128(seed=4, n_peds=100, nx=80 + 16 * k, ny=64) for k in range(2)]
+    sims = [P.from_scenario(sc) for sc in scs]
+    b = P.Batch(sims, mode=N.FP_MODE_PERSISTENT)
+    b.step(8)
+    b.synchronize()
+    N.fp_set_barrier_wait_limit(sims[0].h, 0)
+    b.step(4)
+    assert N.lib().fp_batch_synchronize(b.h) == N.FP_ETIMEOUT
+    assert N.lib().fp_batch_synchronize(b.h) == N.FP_OK
+    N.fp_set_barrier_wait_limit(sims[0].h, 1 << 22)
+    b.set_mode(N.FP_MODE_KERNELS)
+    b.step(8)
+    b.synchronize()
+    b.set_mode(N.FP_MODE_PERSISTENT)
+    b.step(8)
+    b.synchronize()
+    b.close()
+    for s in sims:
+        s.close()
+
+
 def test_batch_reports_member_error(P):
     """A member's non-finite state surfaces from the batch's synchronisation."""
     from paper_1908_05232_b300 import _native as N

@@ -430,13 +430,17 @@ def _batch_members():
     return [a, b, c, d, e]
 
 
-def test_batch_matches_members_alone(P):
-    """Scenarios of different grids and crowds stepped as one batch give the
-    bytes each gives stepped alone (graph-replayed 64-step runs included)."""
+@pytest.mark.parametrize("mode", ["kernels", "persistent"])
+def test_batch_matches_members_alone(P, mode):
+    """Scenarios of different grids and crowds stepped as one batch -- per-step
+    batch kernels (graph-replayed 64-step runs included) or one persistent
+    launch for the whole ensemble (two launches here: 256 steps, then 44) --
+    give the bytes each gives stepped alone."""
+    from paper_1908_05232_b300 import _native as N
     scs = _batch_members()
-    n = 200
+    n = 300
     members = [P.from_scenario(sc) for sc in scs]
-    batch = P.Batch(members)
+    batch = P.Batch(members, mode=N.FP_MODE_PERSISTENT if mode == "persistent" else None)
     batch.step(n)
     batch.synchronize()
     for sc, m in zip(scs, members):
@@ -451,13 +455,15 @@ def test_batch_matches_members_alone(P):
     batch.close()
 
 
-def test_batch_then_alone_continues(P):
+@pytest.mark.parametrize("mode", ["kernels", "persistent"])
+def test_batch_then_alone_continues(P, mode):
     """A member stepped alone (leaving its records hashed ahead), then in a
     batch, then alone again gives the bytes of a run stepped alone."""
+    from paper_1908_05232_b300 import _native as N
     sc = S.plain_coupled_128(seed=3)
     m = P.from_scenario(sc)
     m.step(20)
-    b = P.Batch([m])
+    b = P.Batch([m], mode=N.FP_MODE_PERSISTENT if mode == "persistent" else None)
     b.step(70)
     b.synchronize()
     b.close()

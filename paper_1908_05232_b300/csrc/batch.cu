@@ -13,8 +13,9 @@
 //             G   every member's records gathered into bin order A with the
 //                 step's draws; the tile counts cleared;
 //             --- grid barrier ---
-//             FP  the flood runs of all members (one warp per run; the warp of
-//                 a member's first run advances its clock), then pedestrian
+//             FP  the flood runs of all members (one warp per run, from a
+//                 ticket; the warp of a member's first run advances its
+//                 clock), then pedestrian
 //                 chunks of all members taken from a ticket by whichever CTAs
 //                 are free (the chunk of a member's first record also admits
 //                 its visitors through the doors);
@@ -55,7 +56,10 @@ __global__ void __launch_bounds__(kBT, 2) batch_persistent_kernel(const FpSim *_
     for (int s = 0; s < nsteps; ++s) {
         const int par = par0 ^ (s & 1), slot = (slot0 + s) & 3;
         // H: hash every member's records of B
-        if (cta == 0 && tid == 0) bar[2 + (s & 1)] = 0u;  // this step's pedestrian ticket (last used two steps ago)
+        if (cta == 0 && tid == 0) {  // this step's tickets (last used two steps ago)
+            bar[2 + (s & 1)] = 0u;
+            bar[4 + (s & 1)] = 0u;
+        }
         for (int x0 = cta * kBT; x0 < total_rec; x0 += G * kBT) {
             const int m = batch_member(rec_off, n, x0);
             const FpSim &S = sims[m];
@@ -83,8 +87,14 @@ __global__ void __launch_bounds__(kBT, 2) batch_persistent_kernel(const FpSim *_
             if (i < S.cnt->nB) gather_record(S, i, S.clock[slot].step);
         }
         if (!grid_sync(bar, S0)) return;
-        // FP: flood runs, one warp per run
-        for (int r = cta * (kBT / 32) + (tid >> 5); r < total_runs; r += G * (kBT / 32)) {
+        // FP: flood runs, one warp per run, taken from a ticket (members' runs
+        // cost very different amounts: dry groups are skipped)
+        unsigned *fticket = bar + 4 + (s & 1);
+        for (;;) {
+            unsigned rr = 0u;
+            if (lane == 0) rr = atomicAdd(fticket, 1u);
+            const int r = (int)__shfl_sync(0xffffffffu, rr, 0);
+            if (r >= total_runs) break;
             const int m = batch_member(run_off, n, r);
             const FpSim &S = sims[m];
             const int lr = r - run_off[m];
@@ -152,9 +162,9 @@ cudaError_t fp_launch_batch_persistent(const FpSim *d_sims, const int *d_run_off
     void *args[] = {(void *)&d_sims, (void *)&d_run_off, (void *)&d_rec_off, (void *)&n, (void *)&total_runs,
                     (void *)&total_rec, (void *)&max_tiles, (void *)&par, (void *)&slot, (void *)&nsteps,
                     (void *)&bar};
-    // the barrier word and the pedestrian tickets start at zero (a barrier that
-    // timed out leaves its word partly counted)
-    const cudaError_t e = cudaMemsetAsync(bar, 0, 4 * sizeof(unsigned), st);
+    // the barrier word and the tickets start at zero (a barrier that timed out
+    // leaves its word partly counted)
+    const cudaError_t e = cudaMemsetAsync(bar, 0, 8 * sizeof(unsigned), st);
     if (e != cudaSuccess) return e;
     return cudaLaunchCooperativeKernel((const void *)batch_persistent_kernel, dim3(ctas), dim3(kBT), args, 0, st);
 }

@@ -1386,7 +1386,7 @@ struct fp_batch {
     std::vector<void *> allocs;
     int mode = FP_MODE_KERNELS;
     int ctas = 0;            // CTAs of the persistent launch
-    unsigned *bar = nullptr;  // grid barrier word + pedestrian tickets (4 words)
+    unsigned *bar = nullptr;  // grid barrier word + pedestrian and flood tickets (8 words)
 };
 
 static void batch_launch_step(fp_batch *b, int par, int slot) {
@@ -1437,7 +1437,7 @@ int fp_batch_create(fp_sim *const *sims, int32_t n, fp_batch **out) {
     b->d_sims = static_cast<FpSim *>(alloc(sizeof(FpSim) * n));
     b->d_run_off = static_cast<int *>(alloc(sizeof(int) * (n + 1)));
     b->d_rec_off = static_cast<int *>(alloc(sizeof(int) * (n + 1)));
-    b->bar = static_cast<unsigned *>(alloc(4 * sizeof(unsigned)));
+    b->bar = static_cast<unsigned *>(alloc(8 * sizeof(unsigned)));
     if (!b->d_sims || !b->d_run_off || !b->d_rec_off || !b->bar) {
         fp_batch_destroy(b);
         g_create_error = "fp_batch_create: device allocation failed";

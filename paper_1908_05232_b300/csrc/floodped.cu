@@ -545,8 +545,10 @@ int fp_sim_create(const fp_config *cfg, fp_sim **out) {
         s->bc_h[e].assign(len, FP_BC_WALL);
     }
     unsigned char *walk = s->dalloc<unsigned char>(n), *arrive = s->dalloc<unsigned char>(n);
-    ok &= walk && arrive;
+    unsigned *nbr = s->dalloc<unsigned>(n);
+    ok &= walk && arrive && nbr;
     S.walk = walk;
+    S.nbr = nbr;
     S.arrive = arrive;
     for (int g = 0; g < 3; ++g) ok &= (S.nav[g] = s->dalloc<unsigned char>(n)) != nullptr;
     double *ht = s->dalloc<double>(FP_MAX_HYDRO), *hh = s->dalloc<double>(FP_MAX_HYDRO);
@@ -642,6 +644,23 @@ int fp_set_terrain(fp_sim *s, const float *z, const float *n0, const uint8_t *wa
         std::vector<uint8_t> flags(n);
         for (size_t c = 0; c < n; ++c) flags[c] = (uint8_t)(s->walk_h[c] | (s->exit_h[c] ? 2 : 0));
         if ((e = s->copy(const_cast<unsigned char *>(s->S.walk), flags.data(), n)) != cudaSuccess)
+            return s->cuda_fail(e, "walkable upload");
+        // the flags of every cell's 3 x 3 neighbourhood in one word (a
+        // pedestrian's move mostly ends next to its cell)
+        const int nx = s->S.nx, ny = s->S.ny;
+        std::vector<unsigned> nb(n, 0u);
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                unsigned f = 0u;
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        const int a = i + dx, b = j + dy;
+                        if (a >= 0 && b >= 0 && a < nx && b < ny)
+                            f |= (unsigned)(flags[(size_t)b * nx + a] & 3u) << (2 * ((dy + 1) * 3 + dx + 1));
+                    }
+                nb[(size_t)j * nx + i] = f;
+            }
+        if ((e = s->copy(const_cast<unsigned *>(s->S.nbr), nb.data(), n * sizeof(unsigned))) != cudaSuccess)
             return s->cuda_fail(e, "walkable upload");
     }
     if ((e = cudaStreamSynchronize(s->stream)) != cudaSuccess) return s->cuda_fail(e, "terrain");

@@ -102,6 +102,8 @@ struct FpSim {
     unsigned short *occ[2];    // evacuees per cell, by the parity of the step that uses them
     const unsigned char *bc[4];
     const unsigned char *walk;    // per cell: bit 0 walkable, bit 1 exit
+    const unsigned *nbr;          // per cell: the walk flags of the 3 x 3 cells centred on it, 2 bits each,
+                                  // row by row from the south-west (0 outside the domain)
     const unsigned char *nav[3];  // per goal (exit, depot, barrier): direction code 0..7, FP_AT_GOAL, 255
     const unsigned char *arrive;  // per cell: bit g set if the cell nav[g] points to is a goal cell of g
     const int *barrier;

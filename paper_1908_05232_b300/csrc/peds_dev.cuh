@@ -193,6 +193,7 @@ __device__ __forceinline__ void ped_group(const FpSim &S, int par, const StepCtl
     const float dx = S.dx;
     const float dt = (float)dt_ticks * (1.0f / FP_TICKS_F);
     int hr = 0, role = 0, task = 0, timer = 0, goal = G_NONE, target = -1, ci = 0, cj = 0, door = 0;
+    unsigned nbr = 0u;  // walk flags of the 3 x 3 cells around the pedestrian
     float x = 0.f, y = 0.f, vx = 0.f, vy = 0.f, speed = 0.f, vdx = 0.f, vdy = 0.f;
     unsigned id = 0, v0bits = 0;
     bool drop = false;
@@ -222,6 +223,7 @@ __device__ __forceinline__ void ped_group(const FpSim &S, int par, const StepCtl
             // two uniform draws (fp_step_draws on id and step, computed by the
             // gather that placed the record), the 3 x 3 bin ranges
             const float hc = S.h[par][pc], huc = S.hu[par][pc], hvc = S.hv[par][pc];
+            nbr = S.nbr[c];
             const float2 xi = S.xiA[j];
             const float xi1 = xi.x, xi2 = xi.y;
             {
@@ -411,11 +413,18 @@ __device__ __forceinline__ void ped_group(const FpSim &S, int par, const StepCtl
             if (sp > speed) { vx = vx * (speed / sp); vy = vy * (speed / sp); }
         }
         float xn = __fmaf_rn(dt, vx, x), yn = __fmaf_rn(dt, vy, y);
-        unsigned fl = cell_flags_at(S, xn, yn);  // one load gives the exit bit of the usual move too
+        // the flags of a cell next to the pedestrian's come from its
+        // neighbourhood word; a move past the neighbouring cells loads them
+        auto flags = [&](float px, float py) -> unsigned {
+            const int ddx = fp_cell_of(px, dx) - ci, ddy = fp_cell_of(py, dx) - cj;
+            if (ddx >= -1 && ddx <= 1 && ddy >= -1 && ddy <= 1) return (nbr >> (2 * ((ddy + 1) * 3 + ddx + 1))) & 3u;
+            return cell_flags_at(S, px, py);
+        };
+        unsigned fl = flags(xn, yn);  // the exit bit of the usual move too
         if (fl & 1u) {
-        } else if (walkable_at(S, xn, y)) { yn = y; vy = 0.0f; fl = cell_flags_at(S, xn, yn); }
-        else if (walkable_at(S, x, yn)) { xn = x; vx = 0.0f; fl = cell_flags_at(S, xn, yn); }
-        else { xn = x; yn = y; vx = 0.0f; vy = 0.0f; fl = cell_flags_at(S, xn, yn); }
+        } else if (flags(xn, y) & 1u) { yn = y; vy = 0.0f; fl = flags(xn, yn); }
+        else if (flags(x, yn) & 1u) { xn = x; vx = 0.0f; fl = flags(xn, yn); }
+        else { xn = x; yn = y; vx = 0.0f; vy = 0.0f; fl = flags(xn, yn); }
         // gone: through the emergency exit (1), or a visitor now in a cell of
         // its door (2); the new position is in a walkable cell of the domain
         int exited = goal == G_EXIT && (fl & 2u) ? 1 : 0;

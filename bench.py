@@ -439,7 +439,7 @@ def run_ours(args):
     if not args.no_tune:
         best = None
         for tr in ((args.tile_rows,) if args.tile_rows else (8, 16, 32)):
-            for pl in (4, 8, 16):
+            for pl in (1, 2, 4, 8, 16):
                 for ha in (True, False):
                     N.fp_set_tuning(sim.h, tr, pl)
                     N.fp_set_hash_ahead(sim.h, ha)
@@ -872,7 +872,7 @@ def main():
                                            "surrogate_forward"],
                     default=None, help="short untimed run of one workload, for profiler captures")
     ap.add_argument("--case-steps", type=int, default=4)
-    ap.add_argument("--case-lanes", type=int, default=8, choices=[4, 8, 16], help="lanes per pedestrian in the case")
+    ap.add_argument("--case-lanes", type=int, default=8, choices=[1, 2, 4, 8, 16], help="lanes per pedestrian in the case")
     ap.add_argument("--case-hash-ahead", type=int, default=1, choices=[0, 1], help="hash-ahead in the case")
     ap.add_argument("--case-order", type=int, default=1, choices=[1, 2],
                     help="flood update of the case: 1 first order, 2 the second-order option")

@@ -265,7 +265,7 @@ int fp_step(fp_sim *sim, int32_t n_steps);
  *   barriers with bounded waits (FP_ETIMEOUT if one gives up). */
 /* Launch shape of the per-step kernels (results do not depend on it): flood
  * tile height tile_rows (8, 16, 32 cells; 64 wide) and lanes per pedestrian in
- * the pedestrian step (4, 8, 16).  Chosen by the package's autotuner. */
+ * the pedestrian step (1, 2, 4, 8, 16).  Chosen by the package's autotuner. */
 int fp_set_tuning(fp_sim *sim, int32_t tile_rows, int32_t ped_lanes);
 
 /* Hash-ahead in FP_MODE_KERNELS (results do not depend on it): with on = 1

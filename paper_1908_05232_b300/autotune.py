@@ -1,7 +1,7 @@
 """Autotuner for the launch shape of a simulation.
 
 Times every candidate (flood tile height 8/16/32, lanes per pedestrian
-4/8/16, hashing of the next step's records in the pedestrian kernel or in a
+1/2/4/8/16, hashing of the next step's records in the pedestrian kernel or in a
 pass of its own, per-step kernels or the persistent kernel) for a few dozen
 steps on a
 scratch copy of the scenario, picks the fastest and caches the choice in a JSON
@@ -17,7 +17,7 @@ from . import _native as N
 
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "floodped_autotune.json")
 TILE_ROWS = (8, 16, 32)
-PED_LANES = (4, 8, 16)
+PED_LANES = (1, 2, 4, 8, 16)
 HASH_AHEAD = (True, False)
 
 

@@ -97,7 +97,7 @@ struct fp_sim {
     int ids_known = -1;      // the ids issued, likewise
     long long pend_t = 0, pend_step = 0;
     int tile_rows = 16;
-    int ped_lanes = 8;   // lanes per pedestrian in the per-step kernel (4, 8, 16)
+    int ped_lanes = 8;   // lanes per pedestrian in the per-step kernel (1, 2, 4, 8, 16)
     // graphs of 64 steps by starting clock slot, whose first step hashes the
     // records of B itself ([0]) or finds them hashed ([1])
     cudaGraphExec_t graphs[2][4] = {};
@@ -1006,8 +1006,9 @@ int fp_step(fp_sim *s, int32_t n_steps) {
 
 int fp_set_tuning(fp_sim *s, int32_t tile_rows, int32_t ped_lanes) {
     if (!s) return FP_EINVAL;
-    if ((tile_rows != 8 && tile_rows != 16 && tile_rows != 32) || (ped_lanes != 4 && ped_lanes != 8 && ped_lanes != 16))
-        return s->fail(FP_EINVAL, "tile_rows must be 8, 16 or 32 and ped_lanes 4, 8 or 16");
+    if ((tile_rows != 8 && tile_rows != 16 && tile_rows != 32) ||
+        (ped_lanes != 1 && ped_lanes != 2 && ped_lanes != 4 && ped_lanes != 8 && ped_lanes != 16))
+        return s->fail(FP_EINVAL, "tile_rows must be 8, 16 or 32 and ped_lanes 1, 2, 4, 8 or 16");
     cudaError_t e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return s->cuda_fail(e, "tuning switch");
     s->tile_rows = tile_rows;

@@ -222,7 +222,11 @@ void fp_launch_gather(const FpSim &S, int slot, cudaStream_t st, bool pdl) {
 void fp_launch_step_begin(const FpSim &S, cudaStream_t st) { step_begin_kernel<<<1, 1, 0, st>>>(S); }
 void fp_launch_ped_step(const FpSim &S, int par, int slot, int lanes, cudaStream_t st, bool pdl, bool hash_next) {
     const int hn = hash_next ? 1 : 0;
-    if (lanes == 4)
+    if (lanes == 1)
+        fp_launch(pdl, ped_step_kernel<1>, dim3(blocks_for(S.cap, 256)), dim3(256), 0, st, S, par, slot, hn);
+    else if (lanes == 2)
+        fp_launch(pdl, ped_step_kernel<2>, dim3(blocks_for(S.cap * 2, 256)), dim3(256), 0, st, S, par, slot, hn);
+    else if (lanes == 4)
         fp_launch(pdl, ped_step_kernel<4>, dim3(blocks_for(S.cap * 4, 256)), dim3(256), 0, st, S, par, slot, hn);
     else if (lanes == 16)
         fp_launch(pdl, ped_step_kernel<16>, dim3(blocks_for(S.cap * 16, 256)), dim3(256), 0, st, S, par, slot, hn);

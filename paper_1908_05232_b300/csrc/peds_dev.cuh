@@ -179,7 +179,7 @@ __device__ __forceinline__ void barrier_and_snapshot(const FpSim &S) {
 }
 
 // One pedestrian (record j of A) by a group of kG lanes (sub = lane in the
-// group; kG = 4, 8 or 16).  lookup(key) gives the first record of hash bin key in A.  With
+// group; kG = 1, 2, 4, 8 or 16).  lookup(key) gives the first record of hash bin key in A.  With
 // hash_next the group's first lane also hashes its output record for the next
 // step.  Every lane of the warp must call this (shuffles over the full warp).
 template <int kG, class Lookup>

@@ -185,13 +185,12 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# DRAM bytes per launch from ncu captures (dram__bytes_read.sum +
-# dram__bytes_write.sum), valid only for the kernel sources they were taken on.
-# DRAM bytes (read + write) per flood-kernel launch from ncu captures of the
-# current kernel sources (profiles/flood_kernel_barrier2048mid_traffic.md,
-# profiles/flood_kernel_wet2048_ncu.md)
-FLOOD_TRAFFIC = {"sources_sha256": "db32320d73da4c08820bd24cd452f92987b5623b29567df7325e7b15229b95d6",
-                 "barrier_2048_midflood": 21724800, "wet_2048": 115236864}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per flood-kernel
+# launch from ncu captures of the kernel sources with this hash: the mid-flood
+# barrier case in the benchmark's tuned shape (8-row runs) and the wet grid
+# (16-row runs)
+FLOOD_TRAFFIC = {"sources_sha256": "67fa21ef59b81f1b949777225090368a77a6e4fa1d170e5d1daa46673838fe8f",
+                 "barrier_2048_midflood": 21733888, "wet_2048": 115023360}
 FLOOD_SOURCES = ("flood.cu", "flood_dev.cuh", "fp_common.cuh")
 
 

@@ -20,9 +20,21 @@
 // read their TMEM lanes with tcgen05.ld for the bias / ReLU / BF16 epilogue.
 // Every wait is bounded; TMEM is freed on every exit path.
 //
-// Training: the backward pass (data and weight gradients of every
-// layer, FP32 on the CUDA cores, deterministic reductions), the loss and Adam
-// with FP32 master weights.
+// Training: the loss, the backward pass on the same tensor cores and Adam with
+// FP32 master weights.  A layer's output gradient is carried as two BF16
+// numbers per value (the rounded value and the rounded remainder, FP32-level
+// precision) in a zero-padded image:
+//   data gradient   = the same implicit-GEMM convolution of the padded output
+//                     gradient (both halves as input channels) with the
+//                     flipped, transposed BF16 weights; its epilogue applies
+//                     the previous ReLU, splits the result for the next layer
+//                     and keeps the bias-gradient partial sums;
+//   weight gradient = per tap sum over pixels of input x output gradient:
+//                     tcgen05.mma with both operands MN-major (pixels are K),
+//                     M = 128 = the input channels of four (eight) stacked
+//                     input rows, N = the split gradient channels, one TMEM
+//                     accumulator per horizontal tap; per-CTA partials summed
+//                     in a fixed order.
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
@@ -74,6 +86,11 @@ constexpr int kRing = 4;        // staged input rows in the ring
 constexpr int kEpiWarps = 8;    // epilogue warps: TMEM lane quarter w % 4, column half w / 4
 constexpr int kConvWarps = kEpiWarps + 2;  // + one TMA producer warp + one MMA issuer warp
 constexpr int kBlk = 4;         // TMEM accumulator blocks (COUT columns each), one per output row in flight
+
+// epilogues of the implicit-GEMM convolution
+constexpr int kHidden = 0;   // bias + ReLU, BF16 activations
+constexpr int kLast = 1;     // bias, times kOutScale, FP32 changes of (h, hu, hv)
+constexpr int kBwdData = 2;  // data gradient: ReLU mask, BF16 split into a padded image, bias-gradient partials
 
 template <int CIN, int COUT>
 struct ConvGeom {
@@ -170,9 +187,14 @@ __device__ __forceinline__ void tmem_zero<16>(unsigned taddr) {
 
 // One 3x3 valid convolution of B images (BF16, CIN channels in groups of 8) with the
 // packed weights (3 horizontal taps x CIN/16 chunks of [2 k-cores][3 COUT
-// rows][8] BF16, the rows ordered vertical tap 2, 1, 0).  Hidden layers: bias
-// + ReLU, BF16 output with COUT channels.  Last layer (LAST): bias, FP32
-// output with 3 channels, times kOutScale.
+// rows][8] BF16, the rows ordered vertical tap 2, 1, 0).  Hidden layers
+// (kHidden): bias + ReLU, BF16 output with COUT channels.  Last layer (kLast):
+// bias, FP32 output with 3 channels, times kOutScale.  Data gradient
+// (kBwdData): the input is a padded, split output gradient and the weights
+// are flipped and transposed; the output is masked by the ReLU of act (the
+// activation the forward layer read, Ho x Wo x COUT) and written split into
+// a zero-padded (Ho + 4) x (Wo + 4) image of 2 COUT channels; each lane
+// quarter of each CTA leaves its bias-gradient sums in dbpart.
 //
 // Work item: one column segment (128 output pixels) of up to kStripRows
 // consecutive output rows of one image.  Input row i feeds output rows i - 2,
@@ -196,13 +218,16 @@ __device__ __forceinline__ void tmem_zero<16>(unsigned taddr) {
 //   epilogue warps (8): wait acc_full, read their TMEM lane quarter and
 //     column half (tcgen05.ld), clear it (tcgen05.st), free the block
 //     (empty[]), then bias / ReLU / BF16 and the stores.
-template <int CIN, int COUT, bool LAST>
+template <int CIN, int COUT, int MODE>
 __global__ void __launch_bounds__(kConvWarps * 32) conv3x3_tc_kernel(const __grid_constant__ CUtensorMap tmap, int B,
                                                                      int H, int W,
                                                                      const __nv_bfloat16 *__restrict__ wpack,
                                                                      const float *__restrict__ bias,
-                                                                     void *__restrict__ y, unsigned *err) {
+                                                                     void *__restrict__ y,
+                                                                     const __nv_bfloat16 *__restrict__ act,
+                                                                     float *__restrict__ dbpart, unsigned *err) {
     using G = ConvGeom<CIN, COUT>;
+    constexpr bool LAST = MODE == kLast;
     constexpr int HALF = COUT / 2;
     extern __shared__ __align__(1024) unsigned char sm[];
     unsigned char *s_w = sm;
@@ -216,7 +241,7 @@ __global__ void __launch_bounds__(kConvWarps * 32) conv3x3_tc_kernel(const __gri
     const int segs = (Wo + kSeg - 1) / kSeg;
     const int chunks = (Ho + kStripRows - 1) / kStripRows;
     const int items = B * segs * chunks;
-    if (tid < COUT) s_bias[tid] = bias[tid];
+    if (MODE != kBwdData && tid < COUT) s_bias[tid] = bias[tid];
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sm_addr(&s_taddr)),
@@ -361,6 +386,9 @@ __global__ void __launch_bounds__(kConvWarps * 32) conv3x3_tc_kernel(const __gri
         const int quarter = warp & 3, half = warp >> 2;
         unsigned g = 0;
         bool ok = true;
+        float dbacc[HALF];  // data gradient: this thread's bias-gradient sums
+#pragma unroll
+        for (int c = 0; c < HALF; ++c) dbacc[c] = 0.0f;
         for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
             const int img = item / (segs * chunks), rem = item % (segs * chunks);
             const int ox0 = (rem / chunks) * kSeg, oy0 = (rem % chunks) * kStripRows;
@@ -390,6 +418,35 @@ __global__ void __launch_bounds__(kConvWarps * 32) conv3x3_tc_kernel(const __gri
                         float *yo = static_cast<float *>(y) + pix * 3;
 #pragma unroll
                         for (int co = 0; co < 3; ++co) yo[co] = (__uint_as_float(v[co]) + s_bias[co]) * kOutScale;
+                    } else if constexpr (MODE == kBwdData) {
+                        // the gradient of the previous pre-activation: masked by
+                        // its ReLU (the activation this layer read), split into
+                        // the BF16 rounded value (groups 0-3) and remainder
+                        // (groups 4-7) at (oy + 2, ox + 2) of the zero-padded image
+                        const int Pa = fp_sur_pitch(Wo), Pp = fp_sur_pitch(Wo + 4);
+#pragma unroll
+                        for (int qd = 0; qd < HALF / 8; ++qd) {
+                            const int grp = half * (HALF / 8) + qd;
+                            const uint4 araw = *reinterpret_cast<const uint4 *>(
+                                act + ((((size_t)img * Ho + oy) * (COUT / 8) + grp) * Pa + ox) * 8);
+                            const __nv_bfloat162 *a2 = reinterpret_cast<const __nv_bfloat162 *>(&araw);
+                            __nv_bfloat162 hi[4], lo[4];
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                const float2 a = __bfloat1622float2(a2[e]);
+                                const float d0 = a.x > 0.0f ? __uint_as_float(v[8 * qd + 2 * e]) : 0.0f;
+                                const float d1 = a.y > 0.0f ? __uint_as_float(v[8 * qd + 2 * e + 1]) : 0.0f;
+                                dbacc[8 * qd + 2 * e] += d0;
+                                dbacc[8 * qd + 2 * e + 1] += d1;
+                                hi[e] = __floats2bfloat162_rn(d0, d1);
+                                const float2 hf = __bfloat1622float2(hi[e]);
+                                lo[e] = __floats2bfloat162_rn(d0 - hf.x, d1 - hf.y);
+                            }
+                            __nv_bfloat16 *yo = static_cast<__nv_bfloat16 *>(y) +
+                                                ((((size_t)img * (Ho + 4) + oy + 2) * 8 + grp) * Pp + ox + 2) * 8;
+                            *reinterpret_cast<uint4 *>(yo) = *reinterpret_cast<const uint4 *>(hi);
+                            *reinterpret_cast<uint4 *>(yo + (size_t)4 * Pp * 8) = *reinterpret_cast<const uint4 *>(lo);
+                        }
                     } else {
                         // channel groups of 8: group half * HALF / 8 + qd of the pixel
                         __nv_bfloat16 *yo = static_cast<__nv_bfloat16 *>(y) +
@@ -409,6 +466,22 @@ __global__ void __launch_bounds__(kConvWarps * 32) conv3x3_tc_kernel(const __gri
                         }
                     }
                 }
+            }
+        }
+        if constexpr (MODE == kBwdData) {
+            // this warp's bias-gradient partials (lanes summed in a fixed
+            // butterfly): slot (CTA, lane quarter), channels of its half
+#pragma unroll
+            for (int c = 0; c < HALF; ++c) {
+                float x = dbacc[c];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+                dbacc[c] = x;
+            }
+            if (lane == 0) {
+#pragma unroll
+                for (int c = 0; c < HALF; ++c)
+                    dbpart[((size_t)blockIdx.x * 4 + quarter) * 32 + half * HALF + c] = dbacc[c];
             }
         }
     }
@@ -431,29 +504,68 @@ __global__ void pack_input_kernel(const float *__restrict__ x4, int B, int H, in
 }
 
 
-// ---- training: FP32 backward on the CUDA cores --------------------------------
+// ---- training: loss, backward on the tensor cores ----------------------------
 
-// g = d loss / d (last layer pre-activation): loss = mean (s z - t)^2 over
-// B x Ho x Wo x 3 with s = kOutScale, so dz = 2 s (s z - t) / n = 2 s (y - t) / n with y the
-// scaled output.  Per-block FP64 partial losses, summed in block order later.
-__global__ void loss_grad_kernel(const float *__restrict__ y, const float *__restrict__ t, size_t n,
-                                 float *__restrict__ g, double *__restrict__ partial) {
+// BF16 rounded value and rounded remainder of an FP32 number
+__device__ __forceinline__ void split_bf16(float d, __nv_bfloat16 &hi, __nv_bfloat16 &lo) {
+    hi = __float2bfloat16_rn(d);
+    lo = __float2bfloat16_rn(d - __bfloat162float(hi));
+}
+
+// loss = mean (s z - t)^2 over B x Ho x Wo x 3 (s = kOutScale, z the last
+// pre-activation) and its gradient dz = 2 s (y - t) / n with y = s z the
+// scaled output.  One thread per pixel: dz goes split into channels 0-2
+// (rounded values) and 3-5 (remainders) of group 0 of the zero-padded
+// (Ho + 4) x (Wo + 4) gradient image (16 channels; cleared beforehand).
+// Per-block FP64 partial losses and FP32 partial bias gradients (slot = block),
+// summed in block order later.
+__global__ void __launch_bounds__(256) loss_grad_kernel(const float *__restrict__ y, const float *__restrict__ t,
+                                                        int B, int Ho, int Wo, size_t n,
+                                                        __nv_bfloat16 *__restrict__ dpad,
+                                                        double *__restrict__ partial, float *__restrict__ dbpart) {
     __shared__ double red[256 / 32];
+    __shared__ float redb[256 / 32][3];
+    const size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     double acc = 0.0;
-    const size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-    if (k < n) {
-        const float d = y[k] - t[k];
-        acc = (double)d * (double)d;
-        g[k] = 2.0f * kOutScale * d / (float)n;
+    float gb[3] = {0.0f, 0.0f, 0.0f};
+    if (p < (size_t)B * Ho * Wo) {
+        const int img = (int)(p / ((size_t)Ho * Wo));
+        const int r = (int)(p % ((size_t)Ho * Wo));
+        const int oy = r / Wo, ox = r % Wo;
+        __align__(16) __nv_bfloat16 o[8];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float d = y[p * 3 + c] - t[p * 3 + c];
+            acc += (double)d * (double)d;
+            gb[c] = 2.0f * kOutScale * d / (float)n;
+            split_bf16(gb[c], o[c], o[3 + c]);
+        }
+        o[6] = o[7] = __float2bfloat16_rn(0.0f);
+        const int Pp = fp_sur_pitch(Wo + 4);
+        *reinterpret_cast<uint4 *>(dpad + ((((size_t)img * (Ho + 4) + oy + 2) * 2) * Pp + ox + 2) * 8) =
+            *reinterpret_cast<const uint4 *>(o);
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    for (int o = 16; o > 0; o >>= 1) {
+        acc += __shfl_xor_sync(0xffffffffu, acc, o);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) gb[c] += __shfl_xor_sync(0xffffffffu, gb[c], o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[threadIdx.x >> 5] = acc;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) redb[threadIdx.x >> 5][c] = gb[c];
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         double s2 = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s2 += red[w];
+        float b3[3] = {0.0f, 0.0f, 0.0f};
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            s2 += red[w];
+            for (int c = 0; c < 3; ++c) b3[c] += redb[w][c];
+        }
         partial[blockIdx.x] = s2;
+        for (int c = 0; c < 3; ++c) dbpart[(size_t)blockIdx.x * 32 + c] = b3[c];
     }
 }
 
@@ -465,96 +577,195 @@ __global__ void sum_partials_kernel(const double *__restrict__ partial, int n, d
     }
 }
 
-// activation (image b, row y, column x, channel c) of an H x W x C image, by channel groups of 8
-__device__ __forceinline__ float act_at(const __nv_bfloat16 *a, int b, int y, int x, int c, int H, int W, int C) {
-    return __bfloat162float(a[((((size_t)b * H + y) * (C / 8) + c / 8) * fp_sur_pitch(W) + x) * 8 + (c & 7)]);
-}
+// weight gradient of one layer: dW[ky][kx][ci][co] = sum over output pixels p of
+// X[p + (ky, kx)][ci] dZ[p][co], dZ the layer's output gradient (split).
+// Work item: kWgR output rows x kWgSK output pixels of one image.  All threads
+// stage the item's input rows (kWgR + ROWS - 1 of them, kWgNPA pixels) and
+// gradient rows (kWgR, kWgSK pixels) in their natural [row][channel group]
+// [pixel][8 channels] form -- MN-major operands, pixels being K; one thread
+// then issues per output row r, horizontal tap kx and 16-pixel chunk j one
+// MMA: A = the input channels of input rows r .. r + ROWS - 1 (M = 128; the
+// first three are vertical taps 0-2, the rest discarded), shifted by kx
+// pixels (16 bytes), B = the gradient channels of output row r; accumulator
+// kx (NB TMEM columns).  Two stages: an item is staged while the MMAs of the
+// one before run.  Items are taken in a fixed order per CTA and each CTA
+// writes its sums (hi + lo) as part[cta][tap][CA][32]: the result is
+// deterministic.  Every wait is bounded; TMEM is freed on every exit path.
+constexpr int kWgR = 4;        // output rows per work item
+constexpr int kWgSK = 64;      // output pixels per work item (four 16-pixel K chunks)
+constexpr int kWgNPA = 72;     // staged input pixels per row (64 + 2 taps, whole core matrices)
+constexpr int kWgThreads = 256;
 
-// dW[t][ci][co] += sum_p X[p + off_t][ci] dY[p][co] and db[co] += sum_p dY[p][co],
-// one CTA per (tap, input channel); threads stride over output pixels; fixed-order
-// tree reduction.  X: BF16 H x W images with CX >= CIN channels (groups of 8).
-template <int COUT>
-__global__ void __launch_bounds__(256) conv_bwd_weight_kernel(const __nv_bfloat16 *__restrict__ X, int CX, int CIN,
-                                                              const float *__restrict__ dY, int B, int H, int W,
-                                                              float *__restrict__ dw, float *__restrict__ db) {
-    const int t = blockIdx.x / CIN, ci = blockIdx.x % CIN;
-    const int ky = t / 3, kx = t % 3;
+template <int CA, int NB>
+struct WgGeom {
+    static constexpr int ROWS = 128 / CA;                // input rows stacked in M
+    static constexpr int AROWS = kWgR + ROWS - 1;        // staged input rows per item
+    static constexpr int AROW = (CA / 8) * kWgNPA * 16;  // bytes of one staged input row
+    static constexpr int ABYTES = AROWS * AROW;
+    static constexpr int BROW = (NB / 8) * kWgSK * 16;   // bytes of one staged gradient row
+    static constexpr int STAGE = ABYTES + kWgR * BROW;
+    static constexpr int SMEM = 2 * STAGE + 1024;
+    static constexpr int TCOLS = 3 * NB <= 64 ? 64 : 3 * NB <= 128 ? 128 : 256;
+    static_assert(CA * ROWS == 128 && STAGE % 16 == 0 && 3 * NB <= TCOLS, "weight-gradient geometry");
+};
+
+// X: the layer's input, B x H x W, CA channels (groups of 8, row pitch
+// fp_sur_pitch(W)).  D: its output gradient split into NB channels, in the
+// zero-padded (H - 2 + 4) x (W - 2 + 4) image: NB = 64, a hidden layer (32
+// rounded values, then 32 remainders); NB = 16, the last layer (3 rounded
+// values, 3 remainders, zeros).  Column co of the result is accumulator
+// column co plus column co + LO.
+template <int CA, int NB>
+__global__ void __launch_bounds__(kWgThreads) conv_wgrad_tc_kernel(const __nv_bfloat16 *__restrict__ X,
+                                                                   const __nv_bfloat16 *__restrict__ D, int B,
+                                                                   int H, int W, float *__restrict__ part,
+                                                                   unsigned *err) {
+    using G = WgGeom<CA, NB>;
+    constexpr int LO = NB == 64 ? 32 : 3;  // column of the remainder of channel 0
+    extern __shared__ __align__(1024) unsigned char sm[];
+    __shared__ __align__(8) unsigned long long bar_mma[2];
+    __shared__ unsigned s_taddr;
+    __shared__ int s_fail;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int Ho = H - 2, Wo = W - 2;
-    const size_t npix = (size_t)B * Ho * Wo;
-    float acc[COUT], accb[COUT];
-#pragma unroll
-    for (int c = 0; c < COUT; ++c) { acc[c] = 0.0f; accb[c] = 0.0f; }
-    const bool do_b = blockIdx.x == 0;
-    for (size_t p = threadIdx.x; p < npix; p += blockDim.x) {
-        const int b = (int)(p / ((size_t)Ho * Wo));
-        const int r = (int)(p % ((size_t)Ho * Wo));
-        const int oy = r / Wo, ox = r % Wo;
-        const float xv = act_at(X, b, oy + ky, ox + kx, ci, H, W, CX);
-        const float *g = dY + p * COUT;
-#pragma unroll
-        for (int c = 0; c < COUT; ++c) {
-            acc[c] = fmaf(xv, g[c], acc[c]);
-            if (do_b) accb[c] += g[c];
-        }
+    const int Px = fp_sur_pitch(W), Pd = fp_sur_pitch(Wo + 4);
+    const int strips = (Ho + kWgR - 1) / kWgR, segs = (Wo + kWgSK - 1) / kWgSK;
+    const int items = B * strips * segs;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sm_addr(&s_taddr)),
+                     "n"(G::TCOLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
-    __shared__ float red[256][COUT + 1];
-#pragma unroll
-    for (int c = 0; c < COUT; ++c) red[threadIdx.x][c] = acc[c];
+    if (tid == 0) {
+        mbar_init_n(sm_addr(&bar_mma[0]), 1);
+        mbar_init_n(sm_addr(&bar_mma[1]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_fail = 0;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    for (int sz = 128; sz > 0; sz >>= 1) {
-        if ((int)threadIdx.x < sz)
-            for (int c = 0; c < COUT; ++c) red[threadIdx.x][c] += red[threadIdx.x + sz][c];
-        __syncthreads();
-    }
-    if ((int)threadIdx.x < COUT) dw[((size_t)t * CIN + ci) * COUT + threadIdx.x] = red[0][threadIdx.x];
-    if (do_b) {
-        __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const unsigned taddr = s_taddr;
+    // warps 0-3 clear the three accumulators in their lane quarters
+    if (warp < 4) {
 #pragma unroll
-        for (int c = 0; c < COUT; ++c) red[threadIdx.x][c] = accb[c];
-        __syncthreads();
-        for (int sz = 128; sz > 0; sz >>= 1) {
-            if ((int)threadIdx.x < sz)
-                for (int c = 0; c < COUT; ++c) red[threadIdx.x][c] += red[threadIdx.x + sz][c];
-            __syncthreads();
-        }
-        if ((int)threadIdx.x < COUT) db[threadIdx.x] = red[0][threadIdx.x];
+        for (int c = 0; c < 3 * NB; c += 16) tmem_zero<16>(taddr + ((unsigned)(32 * warp) << 16) + c);
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
     }
-}
-
-// dX[q][ci] = sum_{t, co} dY[q - off_t][co] W[t][ci][co] over valid output
-// positions, masked by the ReLU of X (the previous layer's output): the
-// gradient of the previous layer's pre-activation.  W is taken rounded to BF16,
-// the weights the forward multiplied by.  One thread per (q, ci).
-template <int CIN, int COUT>
-__global__ void conv_bwd_data_kernel(const float *__restrict__ dY, const float *__restrict__ w,
-                                     const __nv_bfloat16 *__restrict__ X, int B, int H, int W,
-                                     float *__restrict__ dXm) {
-    const size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-    const size_t n = (size_t)B * H * W * CIN;
-    if (k >= n) return;
-    const int ci = (int)(k % CIN);
-    const size_t q = k / CIN;
-    const int b = (int)(q / ((size_t)H * W));
-    const int r = (int)(q % ((size_t)H * W));
-    const int iy = r / W, ix = r % W;
-    const int Ho = H - 2, Wo = W - 2;
-    float acc = 0.0f;
-    if (act_at(X, b, iy, ix, ci, H, W, CIN) > 0.0f) {
-        for (int ky = 0; ky < 3; ++ky) {
-            const int oy = iy - ky;
-            if (oy < 0 || oy >= Ho) continue;
-            for (int kx = 0; kx < 3; ++kx) {
-                const int ox = ix - kx;
-                if (ox < 0 || ox >= Wo) continue;
-                const float *g = dY + (((size_t)b * Ho + oy) * Wo + ox) * COUT;
-                const float *wr = w + ((size_t)(ky * 3 + kx) * CIN + ci) * COUT;
-#pragma unroll 8
-                for (int co = 0; co < COUT; ++co)
-                    acc = fmaf(g[co], __bfloat162float(__float2bfloat16(wr[co])), acc);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const unsigned smb = sm_addr(sm);
+    const unsigned idesc = umma_idesc(128, NB) | (1u << 15) | (1u << 16);  // A and B MN-major
+    const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
+    int it = 0;  // items issued
+    for (int item = blockIdx.x; item < items; item += gridDim.x, ++it) {
+        const int st = it & 1;
+        // the MMAs of the item two back read this stage
+        if (tid == 0 && it >= 2 && !mbar_wait_bounded(sm_addr(&bar_mma[st]), ((it - 2) >> 1) & 1)) s_fail = 1;
+        __syncthreads();
+        if (s_fail) break;
+        const int img = item / (strips * segs), rem = item % (strips * segs);
+        const int oy0 = (rem / segs) * kWgR, ox0 = (rem % segs) * kWgSK;
+        unsigned char *sa = sm + st * G::STAGE, *sb = sa + G::ABYTES;
+        for (int q = tid; q < G::AROWS * (CA / 8) * kWgNPA; q += kWgThreads) {
+            const int px = q % kWgNPA, gr = (q / kWgNPA) % (CA / 8), r = q / (kWgNPA * (CA / 8));
+            const int yy = oy0 + r, xx = ox0 + px;
+            uint4 v = zero4;
+            if (yy < H && xx < W)
+                v = *reinterpret_cast<const uint4 *>(X + ((((size_t)img * H + yy) * (CA / 8) + gr) * Px + xx) * 8);
+            *reinterpret_cast<uint4 *>(sa + (size_t)q * 16) = v;
+        }
+        for (int q = tid; q < kWgR * (NB / 8) * kWgSK; q += kWgThreads) {
+            const int px = q % kWgSK, gr = (q / kWgSK) % (NB / 8), r = q / (kWgSK * (NB / 8));
+            const int yy = oy0 + r, xx = ox0 + px;
+            uint4 v = zero4;
+            if (yy < Ho && xx < Wo)
+                v = *reinterpret_cast<const uint4 *>(
+                    D + ((((size_t)img * (Ho + 4) + yy + 2) * (NB / 8) + gr) * Pd + xx + 2) * 8);
+            *reinterpret_cast<uint4 *>(sb + (size_t)q * 16) = v;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const unsigned a0 = smb + st * G::STAGE, b0 = a0 + G::ABYTES;
+            for (int r = 0; r < kWgR; ++r)
+#pragma unroll
+                for (int kx = 0; kx < 3; ++kx)
+#pragma unroll
+                    for (int j = 0; j < kWgSK / 16; ++j) {
+                        // LBO = K-direction core stride (8 pixels), SBO = channel-group stride
+                        const unsigned long long ad =
+                            umma_desc(a0 + r * G::AROW + (16 * j + kx) * 16, 128, kWgNPA * 16);
+                        const unsigned long long bd = umma_desc(b0 + r * G::BROW + 16 * j * 16, 128, kWgSK * 16);
+                        mma_acc(taddr + kx * NB, ad, bd, idesc);
+                    }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             sm_addr(&bar_mma[st]))
+                         : "memory");
+        }
+    }
+    // the last two items' MMAs (all earlier ones were waited for)
+    if (tid == 0)
+        for (int k = it >= 2 ? it - 2 : 0; k < it; ++k)
+            if (!mbar_wait_bounded(sm_addr(&bar_mma[k & 1]), (k >> 1) & 1)) s_fail = 1;
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (s_fail) {
+        if (tid == 0) atomicOr(err, FP_ERR_TIMEOUT);
+    } else {
+        // warp w reads TMEM lanes 32 (w % 4) ..: lane m = stacked row m / CA,
+        // channel m % CA; warps 4-7 take output channels 16 .. 31
+        const int quarter = warp & 3, half = warp >> 2;
+        const int m = 32 * quarter + lane, rr = m / CA, ca = m % CA;
+        float *pc = part + (size_t)blockIdx.x * 9 * CA * 32;
+        const unsigned tl = taddr + ((unsigned)(32 * quarter) << 16);
+#pragma unroll
+        for (int kx = 0; kx < 3; ++kx) {
+            if constexpr (NB == 64) {
+                unsigned hi[16], lo[16];
+                tmem_load<16>(tl + kx * NB + 16 * half, hi);
+                tmem_load<16>(tl + kx * NB + LO + 16 * half, lo);
+                if (rr < 3)
+#pragma unroll
+                    for (int c = 0; c < 16; ++c)
+                        pc[((rr * 3 + kx) * CA + ca) * 32 + 16 * half + c] =
+                            __uint_as_float(hi[c]) + __uint_as_float(lo[c]);
+            } else if (half == 0) {
+                unsigned v[16];
+                tmem_load<16>(tl + kx * NB, v);
+                if (rr < 3)
+#pragma unroll
+                    for (int c = 0; c < LO; ++c)
+                        pc[((rr * 3 + kx) * CA + ca) * 32 + c] = __uint_as_float(v[c]) + __uint_as_float(v[c + LO]);
             }
         }
     }
-    dXm[k] = acc;
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "n"(G::TCOLS));
+}
+
+// dW (master layout [tap][ci][co]) and db of one layer: the per-CTA weight
+// partials part[cta][tap][CA][32] and the bias partials dbpart[slot][32]
+// summed in index order (deterministic).  One thread per output value.
+__global__ void grad_reduce_kernel(const float *__restrict__ part, int ctas, int CA, int ci_real, int co_real,
+                                   const float *__restrict__ dbpart, int slots, float *__restrict__ dw,
+                                   float *__restrict__ db) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nw = 9 * ci_real * co_real;
+    if (k < nw) {
+        const int co = k % co_real, ci = (k / co_real) % ci_real, t = k / (co_real * ci_real);
+        float acc = 0.0f;
+        for (int c = 0; c < ctas; ++c) acc += part[(((size_t)c * 9 + t) * CA + ci) * 32 + co];
+        dw[k] = acc;
+    } else if (k < nw + co_real) {
+        const int co = k - nw;
+        float acc = 0.0f;
+        for (int q = 0; q < slots; ++q) acc += dbpart[(size_t)q * 32 + co];
+        db[co] = acc;
+    }
 }
 
 // Adam on the FP32 master parameters
@@ -589,6 +800,29 @@ __global__ void pack_layer_kernel(const float *__restrict__ w, const float *__re
     pk[k] = __float2bfloat16(v);
 }
 
+// FP32 master (one layer, ci_real x co_real) -> the packed BF16 operand of its
+// data gradient, in the forward kernel's block format with kWidth output
+// channels: input channel k is a channel of the split output gradient (k <
+// co_real the rounded value of channel k, co_real <= k < 2 co_real the
+// remainder of channel k - co_real, zero beyond), output channel n the
+// layer's input channel n, tap (ky, kx) the layer's tap (2 - ky, 2 - kx).
+__global__ void pack_layer_bwd_kernel(const float *__restrict__ w, int ci_real, int co_real, int cin_b,
+                                      __nv_bfloat16 *__restrict__ pk) {
+    const int kc = cin_b / 16, rows = 3 * kWidth;
+    const int total = 3 * kc * 2 * rows * 8;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= total) return;
+    const int e = k % 8, n3 = (k / 8) % rows, j = (k / (8 * rows)) % 2;
+    const int c = (k / (16 * rows)) % kc, kx = k / (16 * rows * kc);
+    const int ky = 2 - n3 / kWidth, n = n3 % kWidth;
+    const int kin = 16 * c + 8 * j + e;
+    const int co = kin < co_real ? kin : kin < 2 * co_real ? kin - co_real : -1;
+    const int t = 3 * (2 - ky) + (2 - kx);
+    float v = 0.0f;
+    if (co >= 0 && n < ci_real) v = w[((size_t)t * ci_real + n) * co_real + co];
+    pk[k] = __float2bfloat16(v);
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -599,14 +833,21 @@ struct fp_surrogate {
     std::vector<size_t> w_off, b_off;             // offsets of each layer's w and b
     float *d_master = nullptr, *d_m = nullptr, *d_v = nullptr, *d_grad = nullptr;
     __nv_bfloat16 *d_wpack[kLayers] = {};         // packed BF16 weights per layer
+    __nv_bfloat16 *d_wpack_bwd[kLayers] = {};     // packed data-gradient weights (layers 1-4)
     float *d_bias[kLayers] = {};                  // padded FP32 biases per layer
     unsigned *d_err = nullptr;
     double *d_loss = nullptr, *d_partial = nullptr;
     long long adam_t = 0;
-    // cached scratch: activations (BF16), output and gradients (FP32)
+    // cached scratch: activations (BF16) and output (FP32)
     size_t cap_pix = 0, cap_partial = 0;
     __nv_bfloat16 *d_a[kLayers] = {};             // inputs of every layer (a[0] packed input)
-    float *d_out = nullptr, *d_g0 = nullptr, *d_g1 = nullptr;
+    float *d_out = nullptr;
+    // backward scratch: two padded split-gradient images, the weight-gradient
+    // partials of up to part_ctas CTAs, the bias-gradient partials
+    size_t cap_dpad = 0, cap_slots = 0;
+    __nv_bfloat16 *d_dpad[2] = {};
+    float *d_part = nullptr, *d_dbpart = nullptr;
+    int part_ctas = 0;
     std::vector<void *> allocs;
     int sms = 148;
 };
@@ -646,28 +887,58 @@ cudaError_t encode_act_map(CUtensorMap *m, const __nv_bfloat16 *x, int B, int H,
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-template <int CIN, int COUT, bool LAST>
-cudaError_t launch_conv(const fp_surrogate *s, int layer, const __nv_bfloat16 *x, int B, int H, int W, void *y,
-                        cudaStream_t st) {
+constexpr int kConvMaxPerSM = 3;  // resident convolution CTAs per SM at most
+
+// one implicit-GEMM convolution of B x H x W images x (CIN channels) into y
+// (act, dbpart: the data-gradient epilogue's mask and partials; grid_out: the
+// CTAs launched, each leaving 4 bias-gradient slots in that epilogue)
+template <int CIN, int COUT, int MODE>
+cudaError_t launch_conv(const fp_surrogate *s, const __nv_bfloat16 *wpack, const float *bias,
+                        const __nv_bfloat16 *x, int B, int H, int W, void *y, const __nv_bfloat16 *act,
+                        float *dbpart, int *grid_out, cudaStream_t st) {
     using G = ConvGeom<CIN, COUT>;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(conv3x3_tc_kernel<CIN, COUT, LAST>,
+    static int per_sm = 0;  // resident CTAs per SM: shared memory, TMEM (512 / TCOLS), at most three
+    if (!per_sm) {
+        cudaError_t e = cudaFuncSetAttribute(conv3x3_tc_kernel<CIN, COUT, MODE>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
         if (e != cudaSuccess) return e;
-        attr = true;
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, conv3x3_tc_kernel<CIN, COUT, MODE>, kConvWarps * 32,
+                                                          G::SMEM) != cudaSuccess || n < 1)
+            n = 1;
+        per_sm = std::min(std::min(kConvMaxPerSM, n), 512 / G::TCOLS);
     }
     CUtensorMap m;
     cudaError_t e = encode_act_map<CIN>(&m, x, B, H, W);
     if (e != cudaSuccess) return e;
     const long long items =
         (long long)B * (((W - 2) + kSeg - 1) / kSeg) * (((H - 2) + kStripRows - 1) / kStripRows);
-    // resident CTAs per SM: three (shared memory allows three), at most 512 / TCOLS (TMEM)
-    const int per_sm = std::min(3, 512 / G::TCOLS);
     int grid = (int)std::min<long long>(items, (long long)s->sms * per_sm);
     if (grid < 1) grid = 1;
-    conv3x3_tc_kernel<CIN, COUT, LAST><<<grid, kConvWarps * 32, G::SMEM, st>>>(m, B, H, W, s->d_wpack[layer],
-                                                                              s->d_bias[layer], y, s->d_err);
+    if (grid_out) *grid_out = grid;
+    conv3x3_tc_kernel<CIN, COUT, MODE><<<grid, kConvWarps * 32, G::SMEM, st>>>(m, B, H, W, wpack, bias, y, act,
+                                                                              dbpart, s->d_err);
+    return cudaGetLastError();
+}
+
+// the weight gradient of a layer with input X (B x H x W, CA channels) and
+// split output gradient D (NB channels, padded); partials of *ctas CTAs in d_part
+template <int CA, int NB>
+cudaError_t launch_wgrad(const fp_surrogate *s, const __nv_bfloat16 *X, const __nv_bfloat16 *D, int B, int H, int W,
+                         int *ctas, cudaStream_t st) {
+    using G = WgGeom<CA, NB>;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(conv_wgrad_tc_kernel<CA, NB>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const long long items = (long long)B * ((H - 2 + kWgR - 1) / kWgR) * ((W - 2 + kWgSK - 1) / kWgSK);
+    int grid = (int)std::min<long long>(items, (long long)s->part_ctas);
+    if (grid < 1) grid = 1;
+    *ctas = grid;
+    conv_wgrad_tc_kernel<CA, NB><<<grid, kWgThreads, G::SMEM, st>>>(X, D, B, H, W, s->d_part, s->d_err);
     return cudaGetLastError();
 }
 
@@ -686,6 +957,12 @@ cudaError_t repack(fp_surrogate *s, cudaStream_t st) {
                                                               kCh[l], kCh[l + 1], ci_pad, co_pad, s->d_wpack[l],
                                                               s->d_bias[l]);
     }
+    for (int l = 1; l < kLayers; ++l) {
+        const int cin_b = l == kLayers - 1 ? 16 : 2 * kWidth;
+        const int total = 3 * (cin_b / 16) * 2 * 3 * kWidth * 8;
+        pack_layer_bwd_kernel<<<(total + 255) / 256, 256, 0, st>>>(s->d_master + s->w_off[l], kCh[l], kCh[l + 1],
+                                                                  cin_b, s->d_wpack_bwd[l]);
+    }
     return cudaGetLastError();
 }
 
@@ -693,13 +970,11 @@ cudaError_t repack(fp_surrogate *s, cudaStream_t st) {
 bool ensure_scratch(fp_surrogate *s, size_t pix) {
     if (pix <= s->cap_pix) return true;
     for (int l = 0; l < kLayers; ++l) cudaFree(s->d_a[l]);
-    cudaFree(s->d_out); cudaFree(s->d_g0); cudaFree(s->d_g1); cudaFree(s->d_partial);
+    cudaFree(s->d_out); cudaFree(s->d_partial);
     s->cap_pix = 0;
     bool ok = cudaMalloc(&s->d_a[0], pix * kCin0 * sizeof(__nv_bfloat16)) == cudaSuccess;
     for (int l = 1; l < kLayers; ++l) ok &= cudaMalloc(&s->d_a[l], pix * kWidth * sizeof(__nv_bfloat16)) == cudaSuccess;
     ok &= cudaMalloc(&s->d_out, pix * 3 * sizeof(float)) == cudaSuccess;
-    ok &= cudaMalloc(&s->d_g0, pix * kWidth * sizeof(float)) == cudaSuccess;
-    ok &= cudaMalloc(&s->d_g1, pix * kWidth * sizeof(float)) == cudaSuccess;
     s->cap_partial = (pix * 3 + 255) / 256 + 1;
     ok &= cudaMalloc(&s->d_partial, s->cap_partial * sizeof(double)) == cudaSuccess;
     // activation rows are padded to 32 pixels: keep the padding finite
@@ -709,17 +984,41 @@ bool ensure_scratch(fp_surrogate *s, size_t pix) {
     return ok;
 }
 
+// backward scratch for B x H x W inputs: padded split gradients up to
+// (H + 2) x (W + 2) x 64 channels; bias-gradient slots for the loss blocks or
+// four per convolution CTA
+bool ensure_bwd(fp_surrogate *s, int B, int H, int W) {
+    const size_t dpad = (size_t)B * (H + 2) * fp_sur_pitch(W + 2) * 2 * kWidth;
+    const size_t slots = std::max<size_t>(((size_t)B * H * W + 255) / 256 + 1,
+                                          (size_t)4 * kConvMaxPerSM * s->sms);
+    if (dpad <= s->cap_dpad && slots <= s->cap_slots) return true;
+    cudaFree(s->d_dpad[0]); cudaFree(s->d_dpad[1]); cudaFree(s->d_dbpart);
+    s->cap_dpad = s->cap_slots = 0;
+    bool ok = cudaMalloc(&s->d_dpad[0], dpad * sizeof(__nv_bfloat16)) == cudaSuccess;
+    ok &= cudaMalloc(&s->d_dpad[1], dpad * sizeof(__nv_bfloat16)) == cudaSuccess;
+    ok &= cudaMalloc(&s->d_dbpart, slots * 32 * sizeof(float)) == cudaSuccess;
+    if (ok) {
+        s->cap_dpad = dpad;
+        s->cap_slots = slots;
+    }
+    return ok;
+}
+
 // the five layers from a packed BF16 input in0 [B][H][W][16]; every later
 // layer's input stays in d_a; output to out
 cudaError_t forward_layers(fp_surrogate *s, const __nv_bfloat16 *in0, int B, int H, int W, float *out,
                            cudaStream_t st) {
-    cudaError_t e = launch_conv<kCin0, kWidth, false>(s, 0, in0, B, H, W, s->d_a[1], st);
+    cudaError_t e = launch_conv<kCin0, kWidth, kHidden>(s, s->d_wpack[0], s->d_bias[0], in0, B, H, W, s->d_a[1],
+                                                        nullptr, nullptr, nullptr, st);
     int h = H - 2, w = W - 2;
     for (int l = 1; l < kLayers - 1 && e == cudaSuccess; ++l) {
-        e = launch_conv<kWidth, kWidth, false>(s, l, s->d_a[l], B, h, w, s->d_a[l + 1], st);
+        e = launch_conv<kWidth, kWidth, kHidden>(s, s->d_wpack[l], s->d_bias[l], s->d_a[l], B, h, w, s->d_a[l + 1],
+                                                 nullptr, nullptr, nullptr, st);
         h -= 2; w -= 2;
     }
-    if (e == cudaSuccess) e = launch_conv<kWidth, kCout4, true>(s, kLayers - 1, s->d_a[kLayers - 1], B, h, w, out, st);
+    if (e == cudaSuccess)
+        e = launch_conv<kWidth, kCout4, kLast>(s, s->d_wpack[kLayers - 1], s->d_bias[kLayers - 1],
+                                               s->d_a[kLayers - 1], B, h, w, out, nullptr, nullptr, nullptr, st);
     return e;
 }
 
@@ -730,33 +1029,51 @@ cudaError_t forward_keep(fp_surrogate *s, const float *x, int B, int H, int W, f
     return forward_layers(s, s->d_a[0], B, H, W, out, st);
 }
 
-// loss and gradients (into d_grad, master layout) of the last forward_keep
+// loss and gradients (into d_grad, master layout) of the last forward_keep.
+// Layer l (input H - 2l x W - 2l): weight gradient from its input and split
+// output gradient, reduced with the bias partials its producer left; then
+// (l > 0) the data gradient into the other padded image.
 cudaError_t backward(fp_surrogate *s, const float *target, int B, int H, int W, cudaStream_t st) {
     const int H5 = H - 2 * kLayers, W5 = W - 2 * kLayers;
-    const size_t n_out = (size_t)B * H5 * W5 * 3;
-    const unsigned nb = (unsigned)((n_out + 255) / 256);
-    loss_grad_kernel<<<nb, 256, 0, st>>>(s->d_out, target, n_out, s->d_g0, s->d_partial);
+    const size_t npix = (size_t)B * H5 * W5, n_out = npix * 3;
+    const unsigned nb = (unsigned)((npix + 255) / 256);
+    __nv_bfloat16 *cur = s->d_dpad[0], *nxt = s->d_dpad[1];
+    cudaError_t e = cudaMemsetAsync(cur, 0, (size_t)B * (H5 + 4) * fp_sur_pitch(W5 + 4) * 16 * sizeof(__nv_bfloat16),
+                                    st);
+    if (e != cudaSuccess) return e;
+    loss_grad_kernel<<<nb, 256, 0, st>>>(s->d_out, target, B, H5, W5, n_out, cur, s->d_partial, s->d_dbpart);
     sum_partials_kernel<<<1, 32, 0, st>>>(s->d_partial, (int)nb, 1.0 / (double)n_out, s->d_loss);
-    float *g = s->d_g0, *gprev = s->d_g1;
-    for (int l = kLayers - 1; l >= 0; --l) {
-        const int Hl = H - 2 * l, Wl = W - 2 * l;  // input size of layer l
-        float *dw = s->d_grad + s->w_off[l], *db = s->d_grad + s->b_off[l];
-        if (l == kLayers - 1) {
-            conv_bwd_weight_kernel<3><<<9 * kWidth, 256, 0, st>>>(s->d_a[l], kWidth, kWidth, g, B, Hl, Wl, dw, db);
-            const size_t n = (size_t)B * Hl * Wl * kWidth;
-            conv_bwd_data_kernel<kWidth, 3><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
-                g, s->d_master + s->w_off[l], s->d_a[l], B, Hl, Wl, gprev);
-        } else if (l > 0) {
-            conv_bwd_weight_kernel<kWidth><<<9 * kWidth, 256, 0, st>>>(s->d_a[l], kWidth, kWidth, g, B, Hl, Wl, dw, db);
-            const size_t n = (size_t)B * Hl * Wl * kWidth;
-            conv_bwd_data_kernel<kWidth, kWidth><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
-                g, s->d_master + s->w_off[l], s->d_a[l], B, Hl, Wl, gprev);
-        } else {
-            conv_bwd_weight_kernel<kWidth><<<9 * kCh[0], 256, 0, st>>>(s->d_a[0], kCin0, kCh[0], g, B, Hl, Wl, dw, db);
-        }
-        std::swap(g, gprev);
+    int slots = (int)nb;
+    for (int l = kLayers - 1; l >= 0 && e == cudaSuccess; --l) {
+        const int Hl = H - 2 * l, Wl = W - 2 * l;
+        int ctas = 0;
+        if (l == kLayers - 1)
+            e = launch_wgrad<kWidth, 16>(s, s->d_a[l], cur, B, Hl, Wl, &ctas, st);
+        else if (l > 0)
+            e = launch_wgrad<kWidth, 2 * kWidth>(s, s->d_a[l], cur, B, Hl, Wl, &ctas, st);
+        else
+            e = launch_wgrad<kCin0, 2 * kWidth>(s, s->d_a[0], cur, B, Hl, Wl, &ctas, st);
+        if (e != cudaSuccess) break;
+        const int nred = 9 * kCh[l] * kCh[l + 1] + kCh[l + 1];
+        grad_reduce_kernel<<<(nred + 255) / 256, 256, 0, st>>>(s->d_part, ctas, l == 0 ? kCin0 : kWidth, kCh[l],
+                                                               kCh[l + 1], s->d_dbpart, slots,
+                                                               s->d_grad + s->w_off[l], s->d_grad + s->b_off[l]);
+        if (l == 0) break;
+        e = cudaMemsetAsync(nxt, 0, (size_t)B * (Hl + 4) * fp_sur_pitch(Wl + 4) * 2 * kWidth * sizeof(__nv_bfloat16),
+                            st);
+        if (e != cudaSuccess) break;
+        int grid = 0;
+        if (l == kLayers - 1)
+            e = launch_conv<16, kWidth, kBwdData>(s, s->d_wpack_bwd[l], nullptr, cur, B, Hl + 2, Wl + 2, nxt,
+                                                  s->d_a[l], s->d_dbpart, &grid, st);
+        else
+            e = launch_conv<2 * kWidth, kWidth, kBwdData>(s, s->d_wpack_bwd[l], nullptr, cur, B, Hl + 2, Wl + 2, nxt,
+                                                          s->d_a[l], s->d_dbpart, &grid, st);
+        slots = 4 * grid;
+        std::swap(cur, nxt);
     }
-    return cudaGetLastError();
+    if (e == cudaSuccess) e = cudaGetLastError();
+    return e;
 }
 
 int check_err(fp_surrogate *s, cudaError_t e, const char *what) {
@@ -829,7 +1146,14 @@ int fp_surrogate_create(uint64_t seed, fp_surrogate **out) {
         const int ci_pad = l == 0 ? kCin0 : kWidth, co_pad = l == kLayers - 1 ? kCout4 : kWidth;
         ok &= (s->d_wpack[l] = static_cast<__nv_bfloat16 *>(alloc((size_t)9 * ci_pad * co_pad * 2))) != nullptr;
         ok &= (s->d_bias[l] = static_cast<float *>(alloc((size_t)co_pad * sizeof(float)))) != nullptr;
+        if (l > 0) {
+            const size_t cin_b = l == kLayers - 1 ? 16 : 2 * kWidth;
+            ok &= (s->d_wpack_bwd[l] = static_cast<__nv_bfloat16 *>(alloc(9 * cin_b * kWidth * 2))) != nullptr;
+        }
     }
+    s->part_ctas = s->sms;  // one weight-gradient CTA per SM
+    ok &= (s->d_part = static_cast<float *>(alloc((size_t)s->part_ctas * 9 * kWidth * 32 * sizeof(float)))) !=
+          nullptr;
     ok &= (s->d_err = static_cast<unsigned *>(alloc(sizeof(unsigned)))) != nullptr;
     ok &= (s->d_loss = static_cast<double *>(alloc(sizeof(double)))) != nullptr;
     if (ok) ok = cudaMemcpy(s->d_master, init.data(), o * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess;
@@ -848,7 +1172,8 @@ int fp_surrogate_destroy(fp_surrogate *s) {
     if (!s) return FP_EINVAL;
     cudaDeviceSynchronize();
     for (int l = 0; l < kLayers; ++l) cudaFree(s->d_a[l]);
-    cudaFree(s->d_out); cudaFree(s->d_g0); cudaFree(s->d_g1); cudaFree(s->d_partial);
+    cudaFree(s->d_out); cudaFree(s->d_partial);
+    cudaFree(s->d_dpad[0]); cudaFree(s->d_dpad[1]); cudaFree(s->d_dbpart);
     for (void *p : s->allocs) cudaFree(p);
     delete s;
     return FP_OK;
@@ -879,7 +1204,7 @@ int fp_surrogate_forward(fp_surrogate *s, const float *x, int32_t B, int32_t H, 
 int fp_surrogate_gradients(fp_surrogate *s, const float *x, const float *target, int32_t B, int32_t H, int32_t W,
                            float *grads, double *loss) {
     if (!s || !x || !target || B < 1 || H < 11 || W < 11) return FP_EINVAL;
-    if (!ensure_scratch(s, (size_t)B * H * fp_sur_pitch(W))) {
+    if (!ensure_scratch(s, (size_t)B * H * fp_sur_pitch(W)) || !ensure_bwd(s, B, H, W)) {
         fp_note_error("fp_surrogate_gradients: allocation failed");
         return FP_ENOMEM;
     }

@@ -810,6 +810,25 @@ def run_case(args):
         print(json.dumps({"case": "surrogate_forward", "ms": e0.elapsed_time(e1),
                           "tflops_padded": flops / (e0.elapsed_time(e1) * 1e-3) / 1e12}))
         return 0
+    if args.ncu_case == "surrogate_train":
+        # Adam steps of the surrogate on a batch of 64 crops of 42 x 42 cells (the
+        # training sampler's shape): forward, loss, the tensor-core backward
+        # (weight and data gradients of the five layers), Adam, repacking;
+        # --case-steps of them after two untimed
+        sur = P.Surrogate(seed=1)
+        g = torch.Generator(device="cuda").manual_seed(1)
+        x = torch.rand((64, 42, 42, 4), device="cuda", generator=g)
+        t = 0.05 * torch.randn((64, 32, 32, 3), device="cuda", generator=g)
+        for _ in range(2):
+            sur.train_step(x, t, 1e-4)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.case_steps):
+            loss = sur.train_step(x, t, 1e-4)
+        torch.cuda.synchronize()
+        print(json.dumps({"case": "surrogate_train", "steps": args.case_steps, "loss": loss,
+                          "ms_per_step": (time.perf_counter() - t0) * 1e3 / max(args.case_steps, 1)}))
+        return 0
     if args.ncu_case == "barrier2048":
         sc = scenarios.config_barrier()
     elif args.ncu_case == "barrier2048mid":
@@ -868,7 +887,7 @@ def main():
     ap.add_argument("--ensemble-steps", type=int, default=4, help="64-step chunks timed per ensemble arm")
     ap.add_argument("--surrogate-windows", type=int, default=160)
     ap.add_argument("--ncu-case", choices=["barrier2048", "barrier2048mid", "wet2048", "wet1024", "shopping512",
-                                           "surrogate_forward"],
+                                           "surrogate_forward", "surrogate_train"],
                     default=None, help="short untimed run of one workload, for profiler captures")
     ap.add_argument("--case-steps", type=int, default=4)
     ap.add_argument("--case-lanes", type=int, default=8, choices=[1, 2, 4, 8, 16], help="lanes per pedestrian in the case")

@@ -81,7 +81,7 @@ __host__ __device__ constexpr unsigned umma_idesc(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(N >> 3) << 17) | ((unsigned)(M >> 4) << 24);
 }
 
-constexpr int kStripRows = 32;  // output rows per work item (one column segment of one image)
+constexpr int kStripRows = 32;  // output rows per work item at most (one column segment of one image)
 constexpr int kRing = 4;        // staged input rows in the ring
 constexpr int kEpiWarps = 8;    // epilogue warps: TMEM lane quarter w % 4, column half w / 4
 constexpr int kConvWarps = kEpiWarps + 2;  // + one TMA producer warp + one MMA issuer warp
@@ -196,7 +196,7 @@ __device__ __forceinline__ void tmem_zero<16>(unsigned taddr) {
 // a zero-padded (Ho + 4) x (Wo + 4) image of 2 COUT channels; each lane
 // quarter of each CTA leaves its bias-gradient sums in dbpart.
 //
-// Work item: one column segment (128 output pixels) of up to kStripRows
+// Work item: one column segment (128 output pixels) of up to strip (<= kStripRows)
 // consecutive output rows of one image.  Input row i feeds output rows i - 2,
 // i - 1, i through its vertical taps 2, 1, 0: one MMA per (horizontal tap,
 // chunk) with N = 3 COUT covers all three, writing three consecutive COUT-column
@@ -220,7 +220,7 @@ __device__ __forceinline__ void tmem_zero<16>(unsigned taddr) {
 //     (empty[]), then bias / ReLU / BF16 and the stores.
 template <int CIN, int COUT, int MODE>
 __global__ void __launch_bounds__(kConvWarps * 32) conv3x3_tc_kernel(const __grid_constant__ CUtensorMap tmap, int B,
-                                                                     int H, int W,
+                                                                     int H, int W, int strip,
                                                                      const __nv_bfloat16 *__restrict__ wpack,
                                                                      const float *__restrict__ bias,
                                                                      void *__restrict__ y,
@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(kConvWarps * 32) conv3x3_tc_kernel(const __gri
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int Ho = H - 2, Wo = W - 2, Pout = fp_sur_pitch(Wo);
     const int segs = (Wo + kSeg - 1) / kSeg;
-    const int chunks = (Ho + kStripRows - 1) / kStripRows;
+    const int chunks = (Ho + strip - 1) / strip;
     const int items = B * segs * chunks;
     if (MODE != kBwdData && tid < COUT) s_bias[tid] = bias[tid];
 
@@ -289,8 +289,8 @@ __global__ void __launch_bounds__(kConvWarps * 32) conv3x3_tc_kernel(const __gri
             unsigned q = 0;  // input rows issued by this CTA
             for (int item = blockIdx.x; item < items && !s_abort; item += gridDim.x) {
                 const int img = item / (segs * chunks), rem = item % (segs * chunks);
-                const int ox0 = (rem / chunks) * kSeg, oy0 = (rem % chunks) * kStripRows;
-                const int nrow = min(kStripRows, Ho - oy0);
+                const int ox0 = (rem / chunks) * kSeg, oy0 = (rem % chunks) * strip;
+                const int nrow = min(strip, Ho - oy0);
                 bool ok = true;
                 for (int i = 0; i < nrow + 2; ++i, ++q) {
                     const unsigned slot = q % kRing, use = q / kRing;
@@ -336,8 +336,8 @@ __global__ void __launch_bounds__(kConvWarps * 32) conv3x3_tc_kernel(const __gri
             bool ok = true;
             for (int item = blockIdx.x; item < items && ok && !s_abort; item += gridDim.x) {
                 const int rem = item % (segs * chunks);
-                const int oy0 = (rem % chunks) * kStripRows;
-                const int nrow = min(kStripRows, Ho - oy0);
+                const int oy0 = (rem % chunks) * strip;
+                const int nrow = min(strip, Ho - oy0);
                 for (int i = 0; i < nrow + 2 && ok; ++i, ++q) {
                     // output rows i - kyhi .. i - kylo of the item take this row
                     const int kylo = max(0, i - (nrow - 1)), kyhi = min(2, i);
@@ -391,8 +391,8 @@ __global__ void __launch_bounds__(kConvWarps * 32) conv3x3_tc_kernel(const __gri
         for (int c = 0; c < HALF; ++c) dbacc[c] = 0.0f;
         for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
             const int img = item / (segs * chunks), rem = item % (segs * chunks);
-            const int ox0 = (rem / chunks) * kSeg, oy0 = (rem % chunks) * kStripRows;
-            const int nrow = min(kStripRows, Ho - oy0);
+            const int ox0 = (rem / chunks) * kSeg, oy0 = (rem % chunks) * strip;
+            const int nrow = min(strip, Ho - oy0);
             for (int r = 0; r < nrow; ++r, ++g) {
                 const unsigned a = g % kBlk;
                 ok = mbar_wait_or_abort(sm_addr(&bar_accf[a]), (g / kBlk) & 1u, &s_abort);
@@ -569,12 +569,20 @@ __global__ void __launch_bounds__(256) loss_grad_kernel(const float *__restrict_
     }
 }
 
-__global__ void sum_partials_kernel(const double *__restrict__ partial, int n, double scale, double *out) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        double s2 = 0.0;
-        for (int k = 0; k < n; ++k) s2 += partial[k];
-        *out = s2 * scale;
+// the loss: the block partials summed by 256 threads (thread i: partials i,
+// i + 256, ...) and a fixed-order tree, times scale
+__global__ void __launch_bounds__(256) sum_partials_kernel(const double *__restrict__ partial, int n, double scale,
+                                                           double *out) {
+    __shared__ double red[256];
+    double s2 = 0.0;
+    for (int k = threadIdx.x; k < n; k += 256) s2 += partial[k];
+    red[threadIdx.x] = s2;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
     }
+    if (threadIdx.x == 0) *out = red[0] * scale;
 }
 
 // weight gradient of one layer: dW[ky][kx][ci][co] = sum over output pixels p of
@@ -748,23 +756,37 @@ __global__ void __launch_bounds__(kWgThreads) conv_wgrad_tc_kernel(const __nv_bf
 }
 
 // dW (master layout [tap][ci][co]) and db of one layer: the per-CTA weight
-// partials part[cta][tap][CA][32] and the bias partials dbpart[slot][32]
-// summed in index order (deterministic).  One thread per output value.
-__global__ void grad_reduce_kernel(const float *__restrict__ part, int ctas, int CA, int ci_real, int co_real,
-                                   const float *__restrict__ dbpart, int slots, float *__restrict__ dw,
-                                   float *__restrict__ db) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+// partials part[cta][tap][CA][32] and the bias partials dbpart[slot][32].
+// A block takes 32 consecutive outputs; thread (g, o) sums partials g, g + 32,
+// ... of output o, then the 32 sums are added in order (deterministic).
+__global__ void __launch_bounds__(1024) grad_reduce_kernel(const float *__restrict__ part, int ctas, int CA,
+                                                           int ci_real, int co_real,
+                                                           const float *__restrict__ dbpart, int slots,
+                                                           float *__restrict__ dw, float *__restrict__ db) {
+    __shared__ float red[32][33];
+    const int o = threadIdx.x & 31, g = threadIdx.x >> 5;
+    const int k = blockIdx.x * 32 + o;
     const int nw = 9 * ci_real * co_real;
+    float acc = 0.0f;
     if (k < nw) {
         const int co = k % co_real, ci = (k / co_real) % ci_real, t = k / (co_real * ci_real);
-        float acc = 0.0f;
-        for (int c = 0; c < ctas; ++c) acc += part[(((size_t)c * 9 + t) * CA + ci) * 32 + co];
-        dw[k] = acc;
+        const float *p = part + ((size_t)t * CA + ci) * 32 + co;
+        const size_t stride = (size_t)9 * CA * 32;
+#pragma unroll 4
+        for (int c = g; c < ctas; c += 32) acc += p[c * stride];
     } else if (k < nw + co_real) {
-        const int co = k - nw;
-        float acc = 0.0f;
-        for (int q = 0; q < slots; ++q) acc += dbpart[(size_t)q * 32 + co];
-        db[co] = acc;
+#pragma unroll 4
+        for (int q = g; q < slots; q += 32) acc += dbpart[(size_t)q * 32 + (k - nw)];
+    }
+    red[g][o] = acc;
+    __syncthreads();
+    if (g == 0 && k < nw + co_real) {
+        float sum = 0.0f;
+        for (int j = 0; j < 32; ++j) sum += red[j][o];
+        if (k < nw)
+            dw[k] = sum;
+        else
+            db[k - nw] = sum;
     }
 }
 
@@ -784,11 +806,11 @@ __global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ g, 
 // FP32 master (one layer) -> packed BF16 operand blocks and padded bias: per
 // (horizontal tap kx, chunk c) a block [2 k-cores][3 co_pad rows][8], row
 // (2 - ky) co_pad + n holding output channel n of vertical tap ky
-__global__ void pack_layer_kernel(const float *__restrict__ w, const float *__restrict__ b, int ci_real, int co_real,
-                                  int ci_pad, int co_pad, __nv_bfloat16 *__restrict__ pk, float *__restrict__ bias) {
+__device__ void pack_layer_at(int k, const float *__restrict__ w, const float *__restrict__ b, int ci_real,
+                              int co_real, int ci_pad, int co_pad, __nv_bfloat16 *__restrict__ pk,
+                              float *__restrict__ bias) {
     const int kc = ci_pad / 16, rows = 3 * co_pad;
     const int total = 3 * kc * 2 * rows * 8;
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k < co_pad) bias[k] = k < co_real ? b[k] : 0.0f;
     if (k >= total) return;
     const int e = k % 8, n3 = (k / 8) % rows, j = (k / (8 * rows)) % 2;
@@ -806,11 +828,10 @@ __global__ void pack_layer_kernel(const float *__restrict__ w, const float *__re
 // co_real the rounded value of channel k, co_real <= k < 2 co_real the
 // remainder of channel k - co_real, zero beyond), output channel n the
 // layer's input channel n, tap (ky, kx) the layer's tap (2 - ky, 2 - kx).
-__global__ void pack_layer_bwd_kernel(const float *__restrict__ w, int ci_real, int co_real, int cin_b,
-                                      __nv_bfloat16 *__restrict__ pk) {
+__device__ void pack_layer_bwd_at(int k, const float *__restrict__ w, int ci_real, int co_real, int cin_b,
+                                  __nv_bfloat16 *__restrict__ pk) {
     const int kc = cin_b / 16, rows = 3 * kWidth;
     const int total = 3 * kc * 2 * rows * 8;
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= total) return;
     const int e = k % 8, n3 = (k / 8) % rows, j = (k / (8 * rows)) % 2;
     const int c = (k / (16 * rows)) % kc, kx = k / (16 * rows * kc);
@@ -821,6 +842,24 @@ __global__ void pack_layer_bwd_kernel(const float *__restrict__ w, int ci_real, 
     float v = 0.0f;
     if (co >= 0 && n < ci_real) v = w[((size_t)t * ci_real + n) * co_real + co];
     pk[k] = __float2bfloat16(v);
+}
+
+// every packing of the master weights in one launch: job j < kLayers the
+// forward operand and bias of layer j, job kLayers - 1 + l the data-gradient
+// operand of layer l (1 <= l < kLayers); one thread per packed value
+struct PackJobs {
+    const float *w[2 * kLayers - 1], *b[2 * kLayers - 1];
+    __nv_bfloat16 *pk[2 * kLayers - 1];
+    float *bias[2 * kLayers - 1];
+    int ci_real[2 * kLayers - 1], co_real[2 * kLayers - 1], ci_pad[2 * kLayers - 1], co_pad[2 * kLayers - 1];
+};
+
+__global__ void pack_all_kernel(const __grid_constant__ PackJobs J) {
+    const int j = blockIdx.y, k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < kLayers)
+        pack_layer_at(k, J.w[j], J.b[j], J.ci_real[j], J.co_real[j], J.ci_pad[j], J.co_pad[j], J.pk[j], J.bias[j]);
+    else
+        pack_layer_bwd_at(k, J.w[j], J.ci_real[j], J.co_real[j], J.ci_pad[j], J.pk[j]);
 }
 
 }  // namespace
@@ -848,6 +887,7 @@ struct fp_surrogate {
     __nv_bfloat16 *d_dpad[2] = {};
     float *d_part = nullptr, *d_dbpart = nullptr;
     int part_ctas = 0;
+    int smem_per_sm = 233472;  // shared memory per SM (bytes)
     std::vector<void *> allocs;
     int sms = 148;
 };
@@ -897,27 +937,41 @@ cudaError_t launch_conv(const fp_surrogate *s, const __nv_bfloat16 *wpack, const
                         const __nv_bfloat16 *x, int B, int H, int W, void *y, const __nv_bfloat16 *act,
                         float *dbpart, int *grid_out, cudaStream_t st) {
     using G = ConvGeom<CIN, COUT>;
-    static int per_sm = 0;  // resident CTAs per SM: shared memory, TMEM (512 / TCOLS), at most three
-    if (!per_sm) {
+    static bool attr = false;
+    if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(conv3x3_tc_kernel<CIN, COUT, MODE>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
         if (e != cudaSuccess) return e;
-        int n = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, conv3x3_tc_kernel<CIN, COUT, MODE>, kConvWarps * 32,
-                                                          G::SMEM) != cudaSuccess || n < 1)
-            n = 1;
-        per_sm = std::min(std::min(kConvMaxPerSM, n), 512 / G::TCOLS);
+        attr = true;
     }
+    // resident CTAs per SM: shared memory (the dynamic part plus 2 KB of static
+    // and reserved per CTA), TMEM (512 / TCOLS columns), at most three
+    const int per_sm =
+        std::max(1, std::min(std::min(kConvMaxPerSM, s->smem_per_sm / (G::SMEM + 2048)), 512 / G::TCOLS));
     CUtensorMap m;
     cudaError_t e = encode_act_map<CIN>(&m, x, B, H, W);
     if (e != cudaSuccess) return e;
-    const long long items =
-        (long long)B * (((W - 2) + kSeg - 1) / kSeg) * (((H - 2) + kStripRows - 1) / kStripRows);
-    int grid = (int)std::min<long long>(items, (long long)s->sms * per_sm);
+    // strip height 32, 16 or 8 output rows: a CTA's time ~ its items x
+    // (strip + the two halo rows staged per item), so the fewest waves of
+    // items x (strip + 2), the taller strip on ties (small images get short
+    // strips and use more SMs)
+    const long long segs = ((W - 2) + kSeg - 1) / kSeg, resident = (long long)s->sms * per_sm;
+    int strip = kStripRows;
+    long long best = -1;
+    for (int sr = kStripRows; sr >= 8; sr /= 2) {
+        const long long n = (long long)B * segs * (((H - 2) + sr - 1) / sr);
+        const long long cost = (n + resident - 1) / resident * (sr + 2);
+        if (best < 0 || cost < best) {
+            best = cost;
+            strip = sr;
+        }
+    }
+    const long long items = (long long)B * segs * (((H - 2) + strip - 1) / strip);
+    int grid = (int)std::min<long long>(items, resident);
     if (grid < 1) grid = 1;
     if (grid_out) *grid_out = grid;
-    conv3x3_tc_kernel<CIN, COUT, MODE><<<grid, kConvWarps * 32, G::SMEM, st>>>(m, B, H, W, wpack, bias, y, act,
-                                                                              dbpart, s->d_err);
+    conv3x3_tc_kernel<CIN, COUT, MODE><<<grid, kConvWarps * 32, G::SMEM, st>>>(m, B, H, W, strip, wpack, bias, y,
+                                                                              act, dbpart, s->d_err);
     return cudaGetLastError();
 }
 
@@ -948,21 +1002,32 @@ size_t param_count() {
     return n;
 }
 
-// FP32 master -> packed BF16 operand blocks and padded biases (on the device)
+// FP32 master -> packed BF16 operand blocks and padded biases, and the
+// data-gradient operands (on the device, one launch)
 cudaError_t repack(fp_surrogate *s, cudaStream_t st) {
-    for (int l = 0; l < kLayers; ++l) {
-        const int ci_pad = l == 0 ? kCin0 : kWidth, co_pad = l == kLayers - 1 ? kCout4 : kWidth;
-        const int total = 9 * (ci_pad / 16) * 2 * co_pad * 8;
-        pack_layer_kernel<<<(total + 255) / 256, 256, 0, st>>>(s->d_master + s->w_off[l], s->d_master + s->b_off[l],
-                                                              kCh[l], kCh[l + 1], ci_pad, co_pad, s->d_wpack[l],
-                                                              s->d_bias[l]);
+    PackJobs J{};
+    int most = 0;
+    for (int j = 0; j < 2 * kLayers - 1; ++j) {
+        const int l = j < kLayers ? j : j - kLayers + 1;
+        J.w[j] = s->d_master + s->w_off[l];
+        J.b[j] = s->d_master + s->b_off[l];
+        J.ci_real[j] = kCh[l];
+        J.co_real[j] = kCh[l + 1];
+        int total;
+        if (j < kLayers) {
+            J.ci_pad[j] = l == 0 ? kCin0 : kWidth;  // input channels of the operand
+            J.co_pad[j] = l == kLayers - 1 ? kCout4 : kWidth;
+            J.pk[j] = s->d_wpack[l];
+            J.bias[j] = s->d_bias[l];
+            total = 9 * (J.ci_pad[j] / 16) * 2 * J.co_pad[j] * 8;
+        } else {
+            J.ci_pad[j] = l == kLayers - 1 ? 16 : 2 * kWidth;  // split gradient channels
+            J.pk[j] = s->d_wpack_bwd[l];
+            total = 3 * (J.ci_pad[j] / 16) * 2 * 3 * kWidth * 8;
+        }
+        most = std::max(most, total);
     }
-    for (int l = 1; l < kLayers; ++l) {
-        const int cin_b = l == kLayers - 1 ? 16 : 2 * kWidth;
-        const int total = 3 * (cin_b / 16) * 2 * 3 * kWidth * 8;
-        pack_layer_bwd_kernel<<<(total + 255) / 256, 256, 0, st>>>(s->d_master + s->w_off[l], kCh[l], kCh[l + 1],
-                                                                  cin_b, s->d_wpack_bwd[l]);
-    }
+    pack_all_kernel<<<dim3((most + 255) / 256, 2 * kLayers - 1), 256, 0, st>>>(J);
     return cudaGetLastError();
 }
 
@@ -1042,7 +1107,7 @@ cudaError_t backward(fp_surrogate *s, const float *target, int B, int H, int W, 
                                     st);
     if (e != cudaSuccess) return e;
     loss_grad_kernel<<<nb, 256, 0, st>>>(s->d_out, target, B, H5, W5, n_out, cur, s->d_partial, s->d_dbpart);
-    sum_partials_kernel<<<1, 32, 0, st>>>(s->d_partial, (int)nb, 1.0 / (double)n_out, s->d_loss);
+    sum_partials_kernel<<<1, 256, 0, st>>>(s->d_partial, (int)nb, 1.0 / (double)n_out, s->d_loss);
     int slots = (int)nb;
     for (int l = kLayers - 1; l >= 0 && e == cudaSuccess; --l) {
         const int Hl = H - 2 * l, Wl = W - 2 * l;
@@ -1055,7 +1120,7 @@ cudaError_t backward(fp_surrogate *s, const float *target, int B, int H, int W, 
             e = launch_wgrad<kCin0, 2 * kWidth>(s, s->d_a[0], cur, B, Hl, Wl, &ctas, st);
         if (e != cudaSuccess) break;
         const int nred = 9 * kCh[l] * kCh[l + 1] + kCh[l + 1];
-        grad_reduce_kernel<<<(nred + 255) / 256, 256, 0, st>>>(s->d_part, ctas, l == 0 ? kCin0 : kWidth, kCh[l],
+        grad_reduce_kernel<<<(nred + 31) / 32, 1024, 0, st>>>(s->d_part, ctas, l == 0 ? kCin0 : kWidth, kCh[l],
                                                                kCh[l + 1], s->d_dbpart, slots,
                                                                s->d_grad + s->w_off[l], s->d_grad + s->b_off[l]);
         if (l == 0) break;
@@ -1130,6 +1195,7 @@ int fp_surrogate_create(uint64_t seed, fp_surrogate **out) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&s->smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
     auto alloc = [&](size_t bytes) -> void * {
         void *p = nullptr;
         if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;

@@ -364,6 +364,11 @@ int fp_surrogate_gradients(fp_surrogate *sur, const float *x, const float *targe
 /* One Adam step (beta1 0.9, beta2 0.999) of learning rate lr on that loss. */
 int fp_surrogate_train_step(fp_surrogate *sur, const float *x, const float *target, int32_t B, int32_t H, int32_t W,
                             float lr, double *loss);
+/* At most ctas CTAs for each of the net's kernels (0: as many as the GPU
+ * holds), e.g. to leave SMs to a simulation stepping beside it.  Results are
+ * the same up to the order of the weight-gradient partial sums.  Returns
+ * FP_EINVAL for ctas < 0. */
+int fp_surrogate_set_max_ctas(fp_surrogate *sur, int32_t ctas);
 
 /* Advance a simulation by n_windows windows of FP_SUR_WINDOW fixed steps with
  * the surrogate standing in for the flood update (requires fp_set_fixed_dt;

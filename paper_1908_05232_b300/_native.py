@@ -110,7 +110,8 @@ def lib():
                            "fp_surrogate_gradients": [_VP, _VP, _VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                                       _VP, _VP],
                            "fp_surrogate_train_step": [_VP, _VP, _VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
-                                                       ctypes.c_float, _VP]}.items():
+                                                       ctypes.c_float, _VP],
+                           "fp_surrogate_set_max_ctas": [_VP, ctypes.c_int32]}.items():
             f = getattr(L, name)
             f.argtypes = args
             f.restype = ctypes.c_int
@@ -468,6 +469,10 @@ class Surrogate:
         loss = ctypes.c_double()
         _check(lib().fp_surrogate_train_step(self.h, _ptr(x), _ptr(target), B, H, W, float(lr), ctypes.byref(loss)))
         return float(loss.value)
+
+    def set_max_ctas(self, ctas):
+        """At most ctas CTAs per kernel of the net (0: no limit)."""
+        _check(lib().fp_surrogate_set_max_ctas(self.h, int(ctas)))
 
     @classmethod
     def pretrained(cls, name="shopping_dt1_32"):

@@ -24,8 +24,9 @@ std::mutex g_mutex;
 double *g_scratch_ptr[kMaxDevices] = {};
 
 // One CTA per row (grid-stride over rows): row sums in FP64 in a fixed tree
-// order, then the last CTA to finish adds the rows in index order, writes the
-// volume and re-arms the counter for the next call.
+// order, then the last CTA to finish adds the rows (thread t rows t, t + 256,
+// ... in index order, then the same fixed tree), writes the volume and
+// re-arms the counter for the next call.
 __global__ void __launch_bounds__(256) volume_rows_kernel(const float *__restrict__ h, int nx, int ny,
                                                           long long pitch, double dx2, double *out,
                                                           double *scratch) {
@@ -52,14 +53,22 @@ __global__ void __launch_bounds__(256) volume_rows_kernel(const float *__restric
         last = atomicAdd(counter, 1ull) == (unsigned long long)(gridDim.x - 1);
     }
     __syncthreads();
-    if (last && threadIdx.x == 0) {
+    if (last) {
         __threadfence();
         const volatile double *rows = scratch + kRowBase;
-        double s = 0.0;
-        for (int r = 0; r < ny; ++r) s += rows[r];
-        *out = s * dx2;
-        *reinterpret_cast<unsigned long long *>(scratch) = 0ull;
-        __threadfence();
+        double acc = 0.0;
+        for (int r = threadIdx.x; r < ny; r += blockDim.x) acc += rows[r];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s = 0.0;
+            for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += red[k];
+            *out = s * dx2;
+            *reinterpret_cast<unsigned long long *>(scratch) = 0ull;
+            __threadfence();
+        }
     }
 }
 

@@ -887,6 +887,7 @@ struct fp_surrogate {
     __nv_bfloat16 *d_dpad[2] = {};
     float *d_part = nullptr, *d_dbpart = nullptr;
     int part_ctas = 0;
+    int max_ctas = 0;          // CTAs per kernel at most (0: no limit)
     int smem_per_sm = 233472;  // shared memory per SM (bytes)
     std::vector<void *> allocs;
     int sms = 148;
@@ -955,7 +956,9 @@ cudaError_t launch_conv(const fp_surrogate *s, const __nv_bfloat16 *wpack, const
     // (strip + the two halo rows staged per item), so the fewest waves of
     // items x (strip + 2), the taller strip on ties (small images get short
     // strips and use more SMs)
-    const long long segs = ((W - 2) + kSeg - 1) / kSeg, resident = (long long)s->sms * per_sm;
+    const long long segs = ((W - 2) + kSeg - 1) / kSeg;
+    const long long resident = s->max_ctas > 0 ? std::min<long long>(s->max_ctas, (long long)s->sms * per_sm)
+                                               : (long long)s->sms * per_sm;
     int strip = kStripRows;
     long long best = -1;
     for (int sr = kStripRows; sr >= 8; sr /= 2) {
@@ -989,7 +992,8 @@ cudaError_t launch_wgrad(const fp_surrogate *s, const __nv_bfloat16 *X, const __
         attr = true;
     }
     const long long items = (long long)B * ((H - 2 + kWgR - 1) / kWgR) * ((W - 2 + kWgSK - 1) / kWgSK);
-    int grid = (int)std::min<long long>(items, (long long)s->part_ctas);
+    const int cap = s->max_ctas > 0 ? std::min(s->max_ctas, s->part_ctas) : s->part_ctas;
+    int grid = (int)std::min<long long>(items, (long long)cap);
     if (grid < 1) grid = 1;
     *ctas = grid;
     conv_wgrad_tc_kernel<CA, NB><<<grid, kWgThreads, G::SMEM, st>>>(X, D, B, H, W, s->d_part, s->d_err);
@@ -1281,6 +1285,12 @@ int fp_surrogate_gradients(fp_surrogate *s, const float *x, const float *target,
     if (grads && cudaMemcpy(grads, s->d_grad, s->n_params * sizeof(float), cudaMemcpyDefault) != cudaSuccess)
         return FP_ECUDA;
     if (loss && cudaMemcpy(loss, s->d_loss, sizeof(double), cudaMemcpyDefault) != cudaSuccess) return FP_ECUDA;
+    return FP_OK;
+}
+
+int fp_surrogate_set_max_ctas(fp_surrogate *s, int32_t ctas) {
+    if (!s || ctas < 0) return FP_EINVAL;
+    s->max_ctas = ctas;
     return FP_OK;
 }
 

@@ -73,17 +73,23 @@ def _inputs(rng, B, H, W):
                      rng.uniform(-1, 1, (B, H, W)), rng.uniform(0, 0.6, (B, H, W))], axis=-1).astype(np.float32)
 
 
-@pytest.mark.parametrize("shape", [(1, 14, 19), (2, 24, 150)])
-def test_gradients_match_oracle(env, shape):
+@pytest.mark.parametrize("shape,ctas", [((1, 14, 19), 0), ((2, 24, 150), 0), ((2, 24, 150), 4)])
+def test_gradients_match_oracle(env, shape, ctas):
     """Loss and every parameter gradient of the CUDA backward against the FP64
     oracle backward, the oracle given the BF16-rounded weights and split inputs
     the tensor cores see, the last layer scaled by the output factor 2^-10, and
-    its hidden activations stored in BF16 as on the GPU (same ReLU decisions).
-    What remains is FP32 against FP64 accumulation: 2e-3 relative."""
+    its hidden activations stored in BF16 as on the GPU (the same rounding).
+    What remains is FP32 against FP64 accumulation, and hidden values whose
+    FP32 and FP64 pre-activations round to different BF16 numbers (or fall on
+    either side of zero): 2e-3 relative on these inputs.  With ctas = 4 each
+    kernel runs on four CTAs: the weight-gradient kernel then takes 9 work
+    items per CTA (36 items of 4 rows x 64 pixels in layer 0), reusing both of
+    its staging buffers, and the data-gradient convolution several strips."""
     torch, P, O = env
     B, H, W = shape
     rng = np.random.default_rng(B * H * W)
     sur = P.Surrogate(seed=11)
+    sur.set_max_ctas(ctas)
     p = sur.params()
     p[:] = rng.normal(0, 1, p.size).astype(np.float32) * np.float32(0.12)
     sur.set_params(p)

@@ -289,15 +289,21 @@ class Snapshot:
 def batched_figures(P, args, dev):
     """A seeded ensemble of shopping centres (grid side 128-1024, 1k-50k
     pedestrians, 50-1000 responders, 1-3 sandbag layers, inflow peak 0.3-1.5
-    m) stepped together -- by the per-step batch kernels (64-step graphs) and
-    by one persistent launch per 256 steps -- against the same simulations
-    stepped one by one, each arm warmed (graphs captured) before its timing."""
+    m) stepped together -- by the per-step batch kernels (64-step graphs, the
+    members' launch shapes autotuned on a scratch batch) and by one persistent
+    launch per 256 steps -- against the same simulations stepped one by one in
+    the default shape, each arm warmed (graphs captured) before its timing."""
     import torch
     import scenarios
+    from paper_1908_05232_b300 import autotune
     t0 = time.perf_counter()
     scs = scenarios.ensemble(args.ensemble_size)
+    # members' launch shapes tuned on a scratch batch of the same scenarios
+    tuned = autotune.tune_batch(scs)
+    t_tune = time.perf_counter() - t0
     sims = [P.from_scenario(sc) for sc in scs]
-    setup = time.perf_counter() - t0
+    autotune.apply_batch(sims, tuned["shapes"])
+    setup = time.perf_counter() - t0 - t_tune
     chunk, reps = 64, args.ensemble_steps
 
     def sim_seconds():
@@ -328,6 +334,7 @@ def batched_figures(P, args, dev):
         t_pers = time.perf_counter() - t0
         sp1 = sim_seconds()
     batch.close()
+    autotune.apply_batch(sims, [(16, 8)] * len(sims))  # one by one: the default shape
     for sim in sims:  # the members' own step graphs (hashing and hashed-ahead openings)
         sim.step(2 * chunk)
         sim.synchronize()
@@ -348,7 +355,10 @@ def batched_figures(P, args, dev):
             "mode": "persistent" if rate_p and rate_p > rate_b else "kernels_graphs",
             "scenarios": len(scs), "cells": int(sum(sc.nx * sc.ny for sc in scs)),
             "pedestrians": int(sum(sc.n_peds for sc in scs)), "steps_timed": chunk * reps,
-            "seconds": {"batched": t_batch, "persistent": t_pers, "one_by_one": t_single, "setup": setup},
+            "seconds": {"batched": t_batch, "persistent": t_pers, "one_by_one": t_single, "setup": setup,
+                        "tuning": t_tune},
+            "tuned_shapes": {"%dx%d" % sh: tuned["shapes"].count(sh) for sh in sorted(set(tuned["shapes"]))},
+            "uniform_shape_us_per_step": tuned["uniform"],
             "workload": "ensemble(%d): shopping centres of side 128-1024 cells (0.5 m), 1k-50k pedestrians"
                         % len(scs)}
 

@@ -314,7 +314,11 @@ int fp_set_profiling(fp_sim *sim, int32_t on);
  *   calls above, on the current device, at the same step parity (e.g. all
  *   fresh, or all stepped the same number of times); they must outlive the
  *   batch and must not be stepped on their own while batched.  The batch
- *   re-reads their configuration at every fp_batch_step.
+ *   re-reads their configuration at every fp_batch_step.  Launch shapes: in
+ *   the per-step-kernel mode each member runs with the flood run height and
+ *   lanes per pedestrian set on it by fp_set_tuning when the batch is created
+ *   (one flood and one pedestrian launch per distinct value; results never
+ *   depend on the shape); the persistent mode runs 16-row runs and 8 lanes.
  * fp_batch_step: n_steps coupled steps of every member (asynchronous on the
  *   batch's stream).  fp_batch_synchronize waits for it and reports device
  *   error bits of any member; read members with fp_read_state afterwards. */

@@ -1,12 +1,18 @@
-"""Autotuner for the launch shape of a simulation.
+"""Autotuner for the launch shape of a simulation and of a batched ensemble.
 
-Times every candidate (flood tile height 8/16/32, lanes per pedestrian
-1/2/4/8/16, hashing of the next step's records in the pedestrian kernel or in a
-pass of its own, per-step kernels or the persistent kernel) for a few dozen
-steps on a
-scratch copy of the scenario, picks the fastest and caches the choice in a JSON
-file keyed by device, grid size and crowd size.  The launch shape never changes
-the results (the same arithmetic runs in every shape), only the time.
+tune / choose: times every candidate (flood tile height 8/16/32, lanes per
+pedestrian 1/2/4/8/16, hashing of the next step's records in the pedestrian
+kernel or in a pass of its own, per-step kernels or the persistent kernel) for
+a few dozen steps on a scratch copy of the scenario, picks the fastest and
+caches the choice in a JSON file keyed by device, grid size and crowd size.
+
+tune_batch: the shapes of a batch's members, timed on a scratch batch of the
+same scenarios -- first one shape for all members, then, member size class by
+size class, the shape of that class with the others held (coordinate
+descent), keeping any change that makes the batch step faster.
+
+The launch shape never changes the results (the same arithmetic runs in every
+shape), only the time.
 """
 from __future__ import annotations
 
@@ -91,3 +97,71 @@ def apply(sim, best: dict) -> None:
     N.fp_set_step_mode(sim.h, best["mode"])
     N.fp_set_tuning(sim.h, best["tile_rows"], best["ped_lanes"])
     N.fp_set_hash_ahead(sim.h, best.get("hash_ahead", True))
+
+
+def _time_batch(members, shapes, steps, chunk=64):
+    """Microseconds per step of a batch of ``members`` with per-member
+    (tile_rows, ped_lanes) ``shapes``: one untimed chunk (graph capture), then
+    ``steps`` timed steps."""
+    import torch
+    for m, (rows, lanes) in zip(members, shapes):
+        N.fp_set_tuning(m.h, rows, lanes)
+    batch = N.Batch(members)
+    try:
+        batch.step(chunk)
+        batch.synchronize()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        batch.step(steps)
+        batch.synchronize()
+        e1.record()
+        e1.synchronize()
+        return 1e3 * e0.elapsed_time(e1) / steps
+    finally:
+        batch.close()
+
+
+def tune_batch(scs, steps: int = 128, classes: int = 2) -> dict:
+    """Launch shapes for a batch of the scenarios ``scs`` (per-step-kernel mode),
+    timed on a scratch batch: the best shape for all members, then coordinate
+    descent over ``classes`` member size classes (by cell count).  Returns
+    {"shapes": [(tile_rows, ped_lanes) per scenario], "us_per_step", "uniform":
+    {shape: us}, "classes": [class of each scenario]}."""
+    members = [N.from_scenario(sc) for sc in scs]
+    try:
+        n = len(scs)
+        order = sorted(range(n), key=lambda k: scs[k].nx * scs[k].ny)
+        cls = [0] * n
+        for rank, k in enumerate(order):
+            cls[k] = min(classes - 1, rank * classes // max(n, 1))
+        _time_batch(members, [(16, 8)] * n, steps)  # warm: the ensemble past its first steps
+        uniform = {}
+        for rows in TILE_ROWS:
+            for lanes in PED_LANES:
+                uniform[(rows, lanes)] = _time_batch(members, [(rows, lanes)] * n, steps)
+        class_shape = [min(uniform, key=uniform.get)] * classes
+        for c in range(classes):
+            # the incumbent timed again first: the scratch members advance
+            # while they are timed, so each sweep compares like with like
+            best = _time_batch(members, [class_shape[cls[k]] for k in range(n)], steps)
+            for cand in ((r, l) for r in TILE_ROWS for l in PED_LANES):
+                if cand == class_shape[c]:
+                    continue
+                trial = list(class_shape)
+                trial[c] = cand
+                t = _time_batch(members, [trial[cls[k]] for k in range(n)], steps)
+                if t < best:
+                    best, class_shape = t, trial
+        return {"shapes": [class_shape[cls[k]] for k in range(n)], "us_per_step": best,
+                "uniform": {"%dx%d" % k: v for k, v in uniform.items()}, "classes": cls}
+    finally:
+        for m in members:
+            m.close()
+
+
+def apply_batch(members, shapes) -> None:
+    """Set each member's (tile_rows, ped_lanes) before the batch is made."""
+    for m, (rows, lanes) in zip(members, shapes):
+        N.fp_set_tuning(m.h, rows, lanes)

@@ -14,25 +14,27 @@ using namespace fpdev;
 
 constexpr int kFloodWarps = 8;  // warps per CTA of the flood kernels
 
-// Batched ensemble: flat run space (64 x 16 runs), member s owns runs
-// [run_off[s], run_off[s + 1]); one warp per run, each warp folding its own
-// tallies into its member's clock.
+// Batched ensemble, the members of one run-height group: a flat space of
+// 64 x TY runs, member k of the group owning runs [run_off[k], run_off[k + 1]);
+// one warp per run, each warp folding its own tallies into its member's clock.
+template <int TY>
 __global__ void __launch_bounds__(32 * kFloodWarps, 2) flood_batch_kernel(const FpSim *__restrict__ sims,
-                                                                       const int *__restrict__ run_off, int n,
+                                                                       const int *__restrict__ members,
+                                                                       const int *__restrict__ run_off, int ng,
                                                                        int total_runs, int par, int slot) {
     const int r = blockIdx.x * kFloodWarps + (threadIdx.x >> 5);
     if (r >= total_runs) return;  // whole warps
-    int lo = 0, hi = n - 1;
+    int lo = 0, hi = ng - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
         if (run_off[mid] <= r) lo = mid; else hi = mid - 1;
     }
-    const FpSim &S = sims[lo];
+    const FpSim &S = sims[members[lo]];
     const int lr = r - run_off[lo];
     const FloodStep st = flood_step_consts(S, slot);
     if (lr == 0 && (threadIdx.x & 31) == 0) flood_clock_advance(S, slot, st);
     FloodAcc acc = flood_acc_init();
-    flood_run<16>(S, par, st, lr, acc);
+    flood_run<TY>(S, par, st, lr, acc);
     flood_acc_fold_warp(S, slot, acc);
 }
 
@@ -160,10 +162,17 @@ void fp_launch_hr_max(const FpSim &S, int par, cudaStream_t st) {
     hr_max_kernel<<<148 * 4, 256, 0, st>>>(S, par);
 }
 
-void fp_launch_flood_batch(const FpSim *d_sims, const int *d_run_off, int n, int total_runs, int par, int slot,
-                           cudaStream_t st) {
-    const int grid = (total_runs + kFloodWarps - 1) / kFloodWarps;
-    flood_batch_kernel<<<grid, 32 * kFloodWarps, 0, st>>>(d_sims, d_run_off, n, total_runs, par, slot);
+void fp_launch_flood_batch(const FpSim *d_sims, const FpBatchGroups &fg, int par, int slot, cudaStream_t st) {
+    // one launch per run-height group that has members (disjoint members)
+    for (int g = 0; g < 3; ++g) {
+        if (fg.n[g] == 0) continue;
+        const int grid = (fg.total[g] + kFloodWarps - 1) / kFloodWarps;
+        switch (kBatchFloodRows[g]) {
+            case 8: flood_batch_kernel<8><<<grid, 32 * kFloodWarps, 0, st>>>(d_sims, fg.members[g], fg.off[g], fg.n[g], fg.total[g], par, slot); break;
+            case 32: flood_batch_kernel<32><<<grid, 32 * kFloodWarps, 0, st>>>(d_sims, fg.members[g], fg.off[g], fg.n[g], fg.total[g], par, slot); break;
+            default: flood_batch_kernel<16><<<grid, 32 * kFloodWarps, 0, st>>>(d_sims, fg.members[g], fg.off[g], fg.n[g], fg.total[g], par, slot); break;
+        }
+    }
 }
 
 cudaError_t fp_flood_init_attributes() { return cudaSuccess; }

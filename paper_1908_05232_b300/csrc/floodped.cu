@@ -1399,6 +1399,9 @@ struct fp_batch {
     int n = 0, total_runs = 0, total_rec = 0, max_scan_tiles = 0;
     FpSim *d_sims = nullptr;
     int *d_run_off = nullptr, *d_rec_off = nullptr;  // flood runs (64 x 16) and record slots of each member
+    // per-step kernels: members grouped by their launch shapes when the batch
+    // was made (flood run height, lanes per pedestrian), device lists
+    FpBatchGroups fg{}, pg{};
     std::vector<FpSim> h_sims;
     cudaStream_t stream = nullptr, stream2 = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -1410,12 +1413,12 @@ struct fp_batch {
 };
 
 static void batch_launch_step(fp_batch *b, int par, int slot) {
-    fp_launch_batch_peds(b->d_sims, b->d_rec_off, b->n, b->total_rec, b->max_scan_tiles, par, slot, b->stream,
-                         b->stream2, b->ev_fork, true);
+    fp_launch_batch_peds(b->d_sims, b->d_rec_off, b->n, b->total_rec, b->max_scan_tiles, b->pg, par, slot,
+                         b->stream, b->stream2, b->ev_fork, true);
     cudaStreamWaitEvent(b->stream2, b->ev_fork, 0);
-    fp_launch_flood_batch(b->d_sims, b->d_run_off, b->n, b->total_runs, par, slot, b->stream);
-    fp_launch_batch_peds(b->d_sims, b->d_rec_off, b->n, b->total_rec, b->max_scan_tiles, par, slot, b->stream,
-                         b->stream2, b->ev_fork, false);
+    fp_launch_flood_batch(b->d_sims, b->fg, par, slot, b->stream);
+    fp_launch_batch_peds(b->d_sims, b->d_rec_off, b->n, b->total_rec, b->max_scan_tiles, b->pg, par, slot,
+                         b->stream, b->stream2, b->ev_fork, false);
     cudaEventRecord(b->ev_join, b->stream2);
     cudaStreamWaitEvent(b->stream, b->ev_join, 0);
 }
@@ -1465,6 +1468,37 @@ int fp_batch_create(fp_sim *const *sims, int32_t n, fp_batch **out) {
     }
     cudaMemcpy(b->d_run_off, run_off.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice);
     cudaMemcpy(b->d_rec_off, rec_off.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice);
+    // shape groups: member lists and work-item offsets per flood run height
+    // and per lane count (each member's fp_set_tuning shape)
+    auto build_groups = [&](FpBatchGroups &G, const int *values, int nvals, bool flood) -> bool {
+        for (int g = 0; g < nvals; ++g) {
+            std::vector<int> mem, off(1, 0);
+            for (int k = 0; k < n; ++k) {
+                const fp_sim *m = b->sims[k];
+                if ((flood ? m->tile_rows : m->ped_lanes) != values[g]) continue;
+                mem.push_back(k);
+                const int items = flood ? ((m->S.nx + FP_TX - 1) / FP_TX) * ((m->S.ny + values[g] - 1) / values[g])
+                                        : (rec_off[k + 1] - rec_off[k]) * values[g] / 256;
+                off.push_back(off.back() + items);
+            }
+            G.n[g] = (int)mem.size();
+            G.total[g] = off.back();
+            if (mem.empty()) continue;
+            int *dm = static_cast<int *>(alloc(sizeof(int) * mem.size()));
+            int *dof = static_cast<int *>(alloc(sizeof(int) * off.size()));
+            if (!dm || !dof) return false;
+            cudaMemcpy(dm, mem.data(), sizeof(int) * mem.size(), cudaMemcpyHostToDevice);
+            cudaMemcpy(dof, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice);
+            G.members[g] = dm;
+            G.off[g] = dof;
+        }
+        return true;
+    };
+    if (!build_groups(b->fg, kBatchFloodRows, 3, true) || !build_groups(b->pg, kBatchPedLanes, 5, false)) {
+        fp_batch_destroy(b);
+        g_create_error = "fp_batch_create: device allocation failed";
+        return FP_ENOMEM;
+    }
     b->h_sims.resize(n);
     cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
     cudaStreamCreateWithFlags(&b->stream2, cudaStreamNonBlocking);

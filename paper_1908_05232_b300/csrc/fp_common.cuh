@@ -324,10 +324,26 @@ int fp_batch_persistent_ctas();
 cudaError_t fp_launch_batch_persistent(const FpSim *d_sims, const int *d_run_off, const int *d_rec_off, int n,
                                        int total_runs, int total_rec, int max_tiles, int par, int slot, int nsteps,
                                        unsigned *bar, int ctas, cudaStream_t st);
+// Members of a batch grouped by launch shape (their own fp_set_tuning): group
+// g holds n[g] members (device indices members[g][k]) whose work items --
+// flood runs of the group's height, or pedestrian blocks of 256 threads at
+// the group's lanes per pedestrian -- are [off[g][k], off[g][k + 1]) of the
+// group's flat space of total[g] items.  Flood groups: 8, 16, 32 rows;
+// pedestrian groups: 1, 2, 4, 8, 16 lanes.
+struct FpBatchGroups {
+    static constexpr int kMax = 5;
+    const int *members[kMax];
+    const int *off[kMax];
+    int n[kMax];
+    int total[kMax];
+};
+constexpr int kBatchFloodRows[3] = {8, 16, 32};
+constexpr int kBatchPedLanes[5] = {1, 2, 4, 8, 16};
+
 void fp_launch_batch_peds(const FpSim *d_sims, const int *d_rec_off, int n, int total_rec, int max_scan_tiles,
-                          int par, int slot, cudaStream_t st_hash, cudaStream_t st_chain, cudaEvent_t fork,
-                          bool hash_part);
-void fp_launch_flood_batch(const FpSim *d_sims, const int *d_run_off, int n, int total_runs, int par, int slot,
+                          const FpBatchGroups &ped_groups, int par, int slot, cudaStream_t st_hash,
+                          cudaStream_t st_chain, cudaEvent_t fork, bool hash_part);
+void fp_launch_flood_batch(const FpSim *d_sims, const FpBatchGroups &flood_groups, int par, int slot,
                            cudaStream_t st);
 cudaError_t fp_launch_persistent(const FpSim &S, int par, int slot, int nsteps, unsigned *bar, int ctas,
                                  cudaStream_t st);

@@ -171,14 +171,19 @@ __global__ void gather_batch_kernel(const FpSim *__restrict__ sims, const int *_
     if (i < S.cnt->nB) gather_record(S, i, S.clock[slot].step);
 }
 
+// The pedestrian update of the members of one lane group: G lanes per
+// pedestrian, 256 / G pedestrians per block; member k of the group owns blocks
+// [blk_off[k], blk_off[k + 1]).
+template <int G>
 __global__ void __launch_bounds__(256) ped_step_batch_kernel(const FpSim *__restrict__ sims,
-                                                             const int *__restrict__ rec_off, int n, int par,
+                                                             const int *__restrict__ members,
+                                                             const int *__restrict__ blk_off, int ng, int par,
                                                              int slot) {
     __shared__ StepCtl s_ctl;
-    constexpr int kRecPerBlock = 256 / kGroup;
-    const int s = batch_member(rec_off, n, blockIdx.x * kRecPerBlock);
-    const FpSim &S = sims[s];
-    const int j0 = blockIdx.x * kRecPerBlock - rec_off[s];
+    constexpr int kRecPerBlock = 256 / G;
+    const int k = batch_member(blk_off, ng, blockIdx.x);
+    const FpSim &S = sims[members[k]];
+    const int j0 = ((int)blockIdx.x - blk_off[k]) * kRecPerBlock;
     if (threadIdx.x == 0) {
         FpCounters *C = S.cnt;
         load_step_ctl(S, slot, C->nA, s_ctl);
@@ -189,15 +194,15 @@ __global__ void __launch_bounds__(256) ped_step_batch_kernel(const FpSim *__rest
     }
     __syncthreads();
     const StepCtl ctl = s_ctl;
-    ped_group<kGroup>(S, par, ctl, j0 + threadIdx.x / kGroup, threadIdx.x & (kGroup - 1), DirectLookup{S.bin_start}, false);
+    ped_group<G>(S, par, ctl, j0 + threadIdx.x / G, threadIdx.x & (G - 1), DirectLookup{S.bin_start}, false);
     if (j0 == 0 && threadIdx.x < 32) door_entries(S, par, ctl, false);
 }
 
 }  // namespace
 
 void fp_launch_batch_peds(const FpSim *d_sims, const int *d_rec_off, int n, int total_rec, int max_scan_tiles,
-                          int par, int slot, cudaStream_t st_hash, cudaStream_t st_chain, cudaEvent_t fork,
-                          bool hash_part) {
+                          const FpBatchGroups &pg, int par, int slot, cudaStream_t st_hash, cudaStream_t st_chain,
+                          cudaEvent_t fork, bool hash_part) {
     if (hash_part) {
         hash_count_batch_kernel<<<total_rec / 256, 256, 0, st_hash>>>(d_sims, d_rec_off, n, par);
         cudaEventRecord(fork, st_hash);
@@ -205,7 +210,18 @@ void fp_launch_batch_peds(const FpSim *d_sims, const int *d_rec_off, int n, int 
     }
     scan_batch_kernel<<<dim3(max_scan_tiles, n), kScanThreads, 0, st_chain>>>(d_sims);
     gather_batch_kernel<<<total_rec / 256, 256, 0, st_chain>>>(d_sims, d_rec_off, n, slot);
-    ped_step_batch_kernel<<<total_rec * kGroup / 256, 256, 0, st_chain>>>(d_sims, d_rec_off, n, par, slot);
+    // one launch per lane group that has members (the groups touch disjoint members)
+    for (int g = 0; g < 5; ++g) {
+        if (pg.n[g] == 0) continue;
+        const dim3 grid(pg.total[g]);
+        switch (kBatchPedLanes[g]) {
+            case 1: ped_step_batch_kernel<1><<<grid, 256, 0, st_chain>>>(d_sims, pg.members[g], pg.off[g], pg.n[g], par, slot); break;
+            case 2: ped_step_batch_kernel<2><<<grid, 256, 0, st_chain>>>(d_sims, pg.members[g], pg.off[g], pg.n[g], par, slot); break;
+            case 4: ped_step_batch_kernel<4><<<grid, 256, 0, st_chain>>>(d_sims, pg.members[g], pg.off[g], pg.n[g], par, slot); break;
+            case 8: ped_step_batch_kernel<8><<<grid, 256, 0, st_chain>>>(d_sims, pg.members[g], pg.off[g], pg.n[g], par, slot); break;
+            default: ped_step_batch_kernel<16><<<grid, 256, 0, st_chain>>>(d_sims, pg.members[g], pg.off[g], pg.n[g], par, slot); break;
+        }
+    }
 }
 
 int fp_scan_tiles(int nbins) { return (nbins + 1 + kScanTile - 1) / kScanTile; }

@@ -430,16 +430,21 @@ def _batch_members():
     return [a, b, c, d, e]
 
 
-@pytest.mark.parametrize("mode", ["kernels", "persistent"])
+@pytest.mark.parametrize("mode", ["kernels", "persistent", "mixed_shapes"])
 def test_batch_matches_members_alone(P, mode):
     """Scenarios of different grids and crowds stepped as one batch -- per-step
-    batch kernels (graph-replayed 64-step runs included) or one persistent
-    launch for the whole ensemble (two launches here: 256 steps, then 44) --
-    give the bytes each gives stepped alone."""
+    batch kernels (graph-replayed 64-step runs included), the same with every
+    member in a launch shape of its own (flood run heights 8/16/32 and 1-16
+    lanes per pedestrian: one flood and one pedestrian launch per shape group),
+    or one persistent launch for the whole ensemble (two launches here: 256
+    steps, then 44) -- give the bytes each gives stepped alone."""
     from paper_1908_05232_b300 import _native as N
     scs = _batch_members()
     n = 300
     members = [P.from_scenario(sc) for sc in scs]
+    if mode == "mixed_shapes":
+        for m, (rows, lanes) in zip(members, [(8, 1), (32, 16), (8, 4), (16, 2), (32, 1)]):
+            N.fp_set_tuning(m.h, rows, lanes)
     batch = P.Batch(members, mode=N.FP_MODE_PERSISTENT if mode == "persistent" else None)
     batch.step(n)
     batch.synchronize()
@@ -514,6 +519,25 @@ def test_autotuner_picks_a_valid_shape(P, tmp_path):
     autotune.apply(sim, best)
     sim.step(10)
     sim.synchronize()
+
+
+def test_batch_tuner_picks_valid_shapes(P):
+    """The batch tuner's per-member shapes (one shape for all, then per size
+    class) are valid candidates; a batch made with them steps."""
+    from paper_1908_05232_b300 import autotune
+    scs = _batch_members()
+    tuned = autotune.tune_batch(scs, steps=16)
+    assert len(tuned["shapes"]) == len(scs) and len(tuned["uniform"]) == 15
+    for rows, lanes in tuned["shapes"]:
+        assert rows in autotune.TILE_ROWS and lanes in autotune.PED_LANES
+    assert sorted(set(tuned["classes"])) == [0, 1] and tuned["us_per_step"] > 0
+    members = [P.from_scenario(sc) for sc in scs]
+    autotune.apply_batch(members, tuned["shapes"])
+    batch = P.Batch(members)
+    batch.step(70)
+    batch.synchronize()
+    assert all(m.counters()["step"] == 70 for m in members)
+    batch.close()
 
 
 @pytest.mark.parametrize("tile_rows", [8, 16, 32])

@@ -318,7 +318,7 @@ int fp_set_profiling(fp_sim *sim, int32_t on);
  *   the per-step-kernel mode each member runs with the flood run height and
  *   lanes per pedestrian set on it by fp_set_tuning when the batch is created
  *   (one flood and one pedestrian launch per distinct value; results never
- *   depend on the shape); the persistent mode runs 16-row runs and 8 lanes.
+ *   depend on the shape); the persistent mode runs 8-row runs and 1 lane.
  * fp_batch_step: n_steps coupled steps of every member (asynchronous on the
  *   batch's stream).  fp_batch_synchronize waits for it and reports device
  *   error bits of any member; read members with fp_read_state afterwards. */

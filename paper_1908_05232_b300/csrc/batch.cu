@@ -101,15 +101,15 @@ __global__ void __launch_bounds__(kBT, 2) batch_persistent_kernel(const FpSim *_
             const FloodStep st = flood_step_consts(S, slot);
             if (lr == 0 && lane == 0) flood_clock_advance(S, slot, st);
             FloodAcc acc = flood_acc_init();
-            flood_run<16>(S, par, st, lr, acc);
+            flood_run<kBatchPersistRows>(S, par, st, lr, acc);
             flood_acc_fold_warp(S, slot, acc);
         }
-        // then pedestrian chunks (kBT / kGroup records each) from the ticket
+        // then pedestrian chunks (kBT / kBatchPersistLanes records each) from the ticket
         unsigned *ticket = bar + 2 + (s & 1);
         for (;;) {
             if (tid == 0) s_pcx = (int)atomicAdd(ticket, 1u);
             __syncthreads();
-            const int x = s_pcx * (kBT / kGroup);
+            const int x = s_pcx * (kBT / kBatchPersistLanes);
             if (x >= total_rec) break;  // block-uniform
             const int m = batch_member(rec_off, n, x);
             const FpSim &S = sims[m];
@@ -124,7 +124,8 @@ __global__ void __launch_bounds__(kBT, 2) batch_persistent_kernel(const FpSim *_
             }
             __syncthreads();
             const StepCtl ctl = s_ctl;
-            ped_group<kGroup>(S, par, ctl, j0 + tid / kGroup, tid & (kGroup - 1), DirectLookup{S.bin_start}, false);
+            ped_group<kBatchPersistLanes>(S, par, ctl, j0 + tid / kBatchPersistLanes, tid & (kBatchPersistLanes - 1),
+                                          DirectLookup{S.bin_start}, false);
             if (j0 == 0 && tid < 32) door_entries(S, par, ctl, false);  // thread 0 set nB = nA above
             __syncthreads();  // s_ctl and s_pcx are taken again
         }

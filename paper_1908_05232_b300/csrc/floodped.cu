@@ -1398,7 +1398,8 @@ struct fp_batch {
     std::vector<fp_sim *> sims;
     int n = 0, total_runs = 0, total_rec = 0, max_scan_tiles = 0;
     FpSim *d_sims = nullptr;
-    int *d_run_off = nullptr, *d_rec_off = nullptr;  // flood runs (64 x 16) and record slots of each member
+    // flood runs of the persistent kernel (64 x kBatchPersistRows) and record slots of each member
+    int *d_run_off = nullptr, *d_rec_off = nullptr;
     // per-step kernels: members grouped by their launch shapes when the batch
     // was made (flood run height, lanes per pedestrian), device lists
     FpBatchGroups fg{}, pg{};
@@ -1443,7 +1444,7 @@ int fp_batch_create(fp_sim *const *sims, int32_t n, fp_batch **out) {
             return FP_EINVAL;
         }
         b->sims.push_back(m);
-        const int runs = ((m->S.nx + FP_TX - 1) / FP_TX) * ((m->S.ny + 15) / 16);
+        const int runs = ((m->S.nx + FP_TX - 1) / FP_TX) * ((m->S.ny + kBatchPersistRows - 1) / kBatchPersistRows);
         run_off[k + 1] = run_off[k] + runs;
         const int cap = std::max(1, m->S.cap);
         rec_off[k + 1] = rec_off[k] + ((cap + 255) / 256) * 256;

@@ -320,6 +320,10 @@ void fp_launch_read_peds(const FpSim &S, uint4 *out, int n_total, cudaStream_t s
 int fp_scan_tiles(int nbins);
 void fp_note_error(const char *msg);  // message for fp_last_error(NULL)
 int fp_persistent_ctas();
+// launch shape of the batch's persistent kernel: flood run height and lanes
+// per pedestrian
+constexpr int kBatchPersistRows = 8;
+constexpr int kBatchPersistLanes = 1;
 int fp_batch_persistent_ctas();
 cudaError_t fp_launch_batch_persistent(const FpSim *d_sims, const int *d_run_off, const int *d_rec_off, int n,
                                        int total_runs, int total_rec, int max_tiles, int par, int slot, int nsteps,

@@ -99,6 +99,18 @@ def apply(sim, best: dict) -> None:
     N.fp_set_hash_ahead(sim.h, best.get("hash_ahead", True))
 
 
+def size_classes(cells, classes: int = 2):
+    """Class of each member (0 = smallest grids): members ranked by cell count
+    (ties in input order), the member of rank r in class floor(r classes / n)
+    -- groups of nearly equal size, the smaller grids taking any remainder."""
+    n = len(cells)
+    order = sorted(range(n), key=lambda k: cells[k])
+    cls = [0] * n
+    for rank, k in enumerate(order):
+        cls[k] = min(classes - 1, rank * classes // max(n, 1))
+    return cls
+
+
 def _time_batch(members, shapes, steps, chunk=64):
     """Microseconds per step of a batch of ``members`` with per-member
     (tile_rows, ped_lanes) ``shapes``: one untimed chunk (graph capture), then
@@ -132,10 +144,7 @@ def tune_batch(scs, steps: int = 128, classes: int = 2) -> dict:
     members = [N.from_scenario(sc) for sc in scs]
     try:
         n = len(scs)
-        order = sorted(range(n), key=lambda k: scs[k].nx * scs[k].ny)
-        cls = [0] * n
-        for rank, k in enumerate(order):
-            cls[k] = min(classes - 1, rank * classes // max(n, 1))
+        cls = size_classes([sc.nx * sc.ny for sc in scs], classes)
         _time_batch(members, [(16, 8)] * n, steps)  # warm: the ensemble past its first steps
         uniform = {}
         for rows in TILE_ROWS:

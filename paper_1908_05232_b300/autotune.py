@@ -6,10 +6,11 @@ kernel or in a pass of its own, per-step kernels or the persistent kernel) for
 a few dozen steps on a scratch copy of the scenario, picks the fastest and
 caches the choice in a JSON file keyed by device, grid size and crowd size.
 
-tune_batch: the shapes of a batch's members, timed on a scratch batch of the
+tune_batch: the shapes of a batch's members, raced on a scratch batch of the
 same scenarios -- first one shape for all members, then, member size class by
 size class, the shape of that class with the others held (coordinate
-descent), keeping any change that makes the batch step faster.
+descent).  The candidates of a race are batches over the same members that
+take turns, so all of them are timed on the same range of states.
 
 The launch shape never changes the results (the same arithmetic runs in every
 shape), only the time.
@@ -111,58 +112,65 @@ def size_classes(cells, classes: int = 2):
     return cls
 
 
-def _time_batch(members, shapes, steps, chunk=64):
-    """Microseconds per step of a batch of ``members`` with per-member
-    (tile_rows, ped_lanes) ``shapes``: one untimed chunk (graph capture), then
-    ``steps`` timed steps."""
+def _race(members, shape_lists, rounds: int = 2, chunk: int = 64):
+    """Milliseconds per step of one batch per entry of ``shape_lists`` (per-member
+    (tile_rows, ped_lanes)), all over the same ``members``: every batch is made
+    and warmed (its step graph captured), then the batches take turns, ``rounds``
+    chunks of ``chunk`` steps each, so that every candidate is timed on the
+    same range of states of the advancing members."""
     import torch
-    for m, (rows, lanes) in zip(members, shapes):
-        N.fp_set_tuning(m.h, rows, lanes)
-    batch = N.Batch(members)
+    batches = []
     try:
-        batch.step(chunk)
-        batch.synchronize()
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        batch.step(steps)
-        batch.synchronize()
-        e1.record()
-        e1.synchronize()
-        return 1e3 * e0.elapsed_time(e1) / steps
+        for shapes in shape_lists:
+            for m, (rows, lanes) in zip(members, shapes):
+                N.fp_set_tuning(m.h, rows, lanes)
+            batches.append(N.Batch(members))
+        for b in batches:
+            b.step(chunk)
+            b.synchronize()
+        total = [0.0] * len(batches)
+        for _ in range(rounds):
+            for k, b in enumerate(batches):
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                b.step(chunk)
+                b.synchronize()
+                e1.record()
+                e1.synchronize()
+                total[k] += e0.elapsed_time(e1)
+        return [t / (rounds * chunk) for t in total]
     finally:
-        batch.close()
+        for b in batches:
+            b.close()
 
 
-def tune_batch(scs, steps: int = 128, classes: int = 2) -> dict:
+def tune_batch(scs, rounds: int = 2, classes: int = 2) -> dict:
     """Launch shapes for a batch of the scenarios ``scs`` (per-step-kernel mode),
-    timed on a scratch batch: the best shape for all members, then coordinate
-    descent over ``classes`` member size classes (by cell count).  Returns
-    {"shapes": [(tile_rows, ped_lanes) per scenario], "us_per_step", "uniform":
-    {shape: us}, "classes": [class of each scenario]}."""
+    raced on a scratch batch: the 15 uniform shapes, then for each of
+    ``classes`` member size classes (by cell count) the 15 shapes of that class
+    with the others held, the incumbent among them (coordinate descent).
+    Returns {"shapes": [(tile_rows, ped_lanes) per scenario], "us_per_step",
+    "uniform": {shape: us}, "classes": [class of each scenario]}."""
     members = [N.from_scenario(sc) for sc in scs]
     try:
         n = len(scs)
         cls = size_classes([sc.nx * sc.ny for sc in scs], classes)
-        _time_batch(members, [(16, 8)] * n, steps)  # warm: the ensemble past its first steps
-        uniform = {}
-        for rows in TILE_ROWS:
-            for lanes in PED_LANES:
-                uniform[(rows, lanes)] = _time_batch(members, [(rows, lanes)] * n, steps)
+        cands = [(r, l) for r in TILE_ROWS for l in PED_LANES]
+        ms = _race(members, [[c] * n for c in cands], rounds)
+        uniform = {c: 1e3 * t for c, t in zip(cands, ms)}
         class_shape = [min(uniform, key=uniform.get)] * classes
+        best = uniform[class_shape[0]]
         for c in range(classes):
-            # the incumbent timed again first: the scratch members advance
-            # while they are timed, so each sweep compares like with like
-            best = _time_batch(members, [class_shape[cls[k]] for k in range(n)], steps)
-            for cand in ((r, l) for r in TILE_ROWS for l in PED_LANES):
-                if cand == class_shape[c]:
-                    continue
-                trial = list(class_shape)
-                trial[c] = cand
-                t = _time_batch(members, [trial[cls[k]] for k in range(n)], steps)
-                if t < best:
-                    best, class_shape = t, trial
+            trials = []
+            for cand in cands:
+                t = list(class_shape)
+                t[c] = cand
+                trials.append(t)
+            ms = _race(members, [[t[cls[k]] for k in range(n)] for t in trials], rounds)
+            k_best = min(range(len(trials)), key=lambda k: ms[k])
+            class_shape, best = trials[k_best], 1e3 * ms[k_best]
         return {"shapes": [class_shape[cls[k]] for k in range(n)], "us_per_step": best,
                 "uniform": {"%dx%d" % k: v for k, v in uniform.items()}, "classes": cls}
     finally:

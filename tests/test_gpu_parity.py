@@ -526,7 +526,7 @@ def test_batch_tuner_picks_valid_shapes(P):
     class) are valid candidates; a batch made with them steps."""
     from paper_1908_05232_b300 import autotune
     scs = _batch_members()
-    tuned = autotune.tune_batch(scs, steps=16)
+    tuned = autotune.tune_batch(scs, rounds=1)
     assert len(tuned["shapes"]) == len(scs) and len(tuned["uniform"]) == 15
     for rows, lanes in tuned["shapes"]:
         assert rows in autotune.TILE_ROWS and lanes in autotune.PED_LANES

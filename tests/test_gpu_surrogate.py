@@ -200,3 +200,22 @@ def test_training_reduces_loss(env):
     losses = [sur.train_step(xd, td, 2e-3) for _ in range(100)]
     assert np.isfinite(losses).all()
     assert min(losses[-10:]) < 0.1 * losses[0], (losses[0], losses[-10:])
+
+
+def test_max_ctas_rejects_negative_and_keeps_results(env):
+    """fp_surrogate_set_max_ctas: a negative limit is refused; the forward on
+    one CTA per kernel gives the same bytes as on all (the forward's sums do
+    not depend on how work items are spread over CTAs)."""
+    torch, P, O = env
+    rng = np.random.default_rng(4)
+    sur = P.Surrogate(seed=5)
+    with pytest.raises(P.FloodPedError):
+        sur.set_max_ctas(-1)
+    x = torch.from_numpy(_inputs(rng, 2, 40, 150)).cuda()
+    y_all = torch.zeros((2, 30, 140, 3), device="cuda")
+    y_one = torch.zeros_like(y_all)
+    sur.forward(x, y_all)
+    sur.set_max_ctas(1)
+    sur.forward(x, y_one)
+    torch.cuda.synchronize()
+    assert torch.equal(y_all, y_one)

@@ -20,10 +20,10 @@
 //                 are free (the chunk of a member's first record also admits
 //                 its visitors through the doors);
 //             --- grid barrier ---
-// Flat spaces as in the per-step batch kernels: member m owns runs
-// [run_off[m], run_off[m+1]) and records [rec_off[m], rec_off[m+1]), the
+// Flat spaces over all members: member m owns runs [run_off[m], run_off[m+1])
+// (64 x kBatchPersistRows each) and records [rec_off[m], rec_off[m+1]), the
 // latter a multiple of 256 long, so every 256 consecutive records (and every
-// pedestrian chunk) belong to one member.  Barrier bookkeeping (poll limit,
+// pedestrian chunk of 256 / kBatchPersistLanes) belong to one member.  Barrier bookkeeping (poll limit,
 // error word) is member 0's.
 #include <algorithm>
 #include <mutex>

@@ -587,160 +587,194 @@ __global__ void __launch_bounds__(256) sum_partials_kernel(const double *__restr
 
 // weight gradient of one layer: dW[ky][kx][ci][co] = sum over output pixels p of
 // X[p + (ky, kx)][ci] dZ[p][co], dZ the layer's output gradient (split).
-// Work item: kWgR output rows x kWgSK output pixels of one image.  All threads
-// stage the item's input rows (kWgR + ROWS - 1 of them, kWgNPA pixels) and
-// gradient rows (kWgR, kWgSK pixels) in their natural [row][channel group]
-// [pixel][8 channels] form -- MN-major operands, pixels being K; one thread
-// then issues per output row r, horizontal tap kx and 16-pixel chunk j one
-// MMA: A = the input channels of input rows r .. r + ROWS - 1 (M = 128; the
-// first three are vertical taps 0-2, the rest discarded), shifted by kx
-// pixels (16 bytes), B = the gradient channels of output row r; accumulator
-// kx (NB TMEM columns).  Two stages: an item is staged while the MMAs of the
-// one before run.  Items are taken in a fixed order per CTA and each CTA
-// writes its sums (hi + lo) as part[cta][tap][CA][32]: the result is
-// deterministic.  Every wait is bounded; TMEM is freed on every exit path.
-constexpr int kWgR = 4;        // output rows per work item
-constexpr int kWgSK = 64;      // output pixels per work item (four 16-pixel K chunks)
-constexpr int kWgNPA = 72;     // staged input pixels per row (64 + 2 taps, whole core matrices)
-constexpr int kWgThreads = 256;
+// Work item: kWgR output rows x kWgSK output pixels of one image.  Per item the
+// TMA producer (warp 0, one thread) copies the item's input rows (kWgR + ROWS
+// - 1 of them) and gradient rows (kWgR), kWgNP pixels each from the item's
+// first 32-pixel block, in their natural [row][channel group][pixel][8
+// channels] form -- MN-major operands, pixels being K -- into one of two
+// stages; the MMA issuer (warp 1, one thread) then issues per output row r,
+// horizontal tap kx and 16-pixel chunk j one MMA: A = the input channels of
+// input rows r .. r + ROWS - 1 (M = 128; the first three are vertical taps
+// 0-2, the rest discarded), shifted by kx pixels (16 bytes), B = the gradient
+// channels of output row r (shifted by the image's 2-pixel padding);
+// accumulator kx (NB TMEM columns), and commits the stage back to the
+// producer.  Pixels and rows past the data come in as zeros (the copies' fill
+// and the padded image's zero border), so no masking is needed.  Items are
+// taken in a fixed order per CTA and each CTA writes its sums (value +
+// remainder) as part[cta][tap][CA][32]: the result is deterministic.  Every
+// wait is bounded; a CTA that gives up waits for its copies in flight and
+// frees its TMEM.
+constexpr int kWgR = 4;                 // output rows per work item
+constexpr int kWgSK = 64;               // output pixels per work item (four 16-pixel K chunks)
+constexpr int kWgBlocks = 3;            // 32-pixel blocks copied per row (64 + the 2 taps, rounded up)
+constexpr int kWgNP = 32 * kWgBlocks;   // staged pixels per row
+constexpr int kWgThreads = 128;         // warp 0 producer, warp 1 issuer; all four the epilogue
 
 template <int CA, int NB>
 struct WgGeom {
     static constexpr int ROWS = 128 / CA;                // input rows stacked in M
     static constexpr int AROWS = kWgR + ROWS - 1;        // staged input rows per item
-    static constexpr int AROW = (CA / 8) * kWgNPA * 16;  // bytes of one staged input row
+    static constexpr int AROW = (CA / 8) * kWgNP * 16;   // bytes of one staged input row
     static constexpr int ABYTES = AROWS * AROW;
-    static constexpr int BROW = (NB / 8) * kWgSK * 16;   // bytes of one staged gradient row
-    static constexpr int STAGE = ABYTES + kWgR * BROW;
+    static constexpr int BROW = (NB / 8) * kWgNP * 16;   // bytes of one staged gradient row
+    static constexpr int BBYTES = kWgR * BROW;
+    static constexpr int STAGE = ABYTES + BBYTES;        // bytes one item's two copies bring
     static constexpr int SMEM = 2 * STAGE + 1024;
     static constexpr int TCOLS = 3 * NB <= 64 ? 64 : 3 * NB <= 128 ? 128 : 256;
-    static_assert(CA * ROWS == 128 && STAGE % 16 == 0 && 3 * NB <= TCOLS, "weight-gradient geometry");
+    static_assert(CA * ROWS == 128 && ABYTES % 1024 == 0 && STAGE % 1024 == 0 && 3 * NB <= TCOLS,
+                  "weight-gradient geometry");
 };
 
-// X: the layer's input, B x H x W, CA channels (groups of 8, row pitch
-// fp_sur_pitch(W)).  D: its output gradient split into NB channels, in the
-// zero-padded (H - 2 + 4) x (W - 2 + 4) image: NB = 64, a hidden layer (32
-// rounded values, then 32 remainders); NB = 16, the last layer (3 rounded
-// values, 3 remainders, zeros).  Column co of the result is accumulator
-// column co plus column co + LO.
+// X (the layer's input, B x H x W, CA channels) through tmX, boxes of (256,
+// kWgBlocks, CA / 8, AROWS, 1); its output gradient split into NB channels,
+// in the zero-padded (H - 2 + 4) x (W - 2 + 4) image, through tmD, boxes of
+// (256, kWgBlocks, NB / 8, kWgR, 1).  NB = 64: a hidden layer (32 rounded
+// values, then 32 remainders); NB = 16: the last layer (3 rounded values, 3
+// remainders, zeros).  Column co of the result is accumulator column co plus
+// column co + LO.
 template <int CA, int NB>
-__global__ void __launch_bounds__(kWgThreads) conv_wgrad_tc_kernel(const __nv_bfloat16 *__restrict__ X,
-                                                                   const __nv_bfloat16 *__restrict__ D, int B,
+__global__ void __launch_bounds__(kWgThreads) conv_wgrad_tc_kernel(const __grid_constant__ CUtensorMap tmX,
+                                                                   const __grid_constant__ CUtensorMap tmD, int B,
                                                                    int H, int W, float *__restrict__ part,
                                                                    unsigned *err) {
     using G = WgGeom<CA, NB>;
     constexpr int LO = NB == 64 ? 32 : 3;  // column of the remainder of channel 0
     extern __shared__ __align__(1024) unsigned char sm[];
-    __shared__ __align__(8) unsigned long long bar_mma[2];
+    __shared__ __align__(8) unsigned long long bar_full[2], bar_empty[2], bar_done;
     __shared__ unsigned s_taddr;
-    __shared__ int s_fail;
+    __shared__ volatile int s_abort;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int Ho = H - 2, Wo = W - 2;
-    const int Px = fp_sur_pitch(W), Pd = fp_sur_pitch(Wo + 4);
     const int strips = (Ho + kWgR - 1) / kWgR, segs = (Wo + kWgSK - 1) / kWgSK;
     const int items = B * strips * segs;
+    // stages from the first 1024-byte boundary of the dynamic buffer
+    const unsigned sm0 = sm_addr(sm), base = (sm0 + 1023u) & ~1023u;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sm_addr(&s_taddr)),
                      "n"(G::TCOLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        mbar_init_n(sm_addr(&bar_mma[0]), 1);
-        mbar_init_n(sm_addr(&bar_mma[1]), 1);
+        for (int k = 0; k < 2; ++k) {
+            mbar_init_n(sm_addr(&bar_full[k]), 1);
+            mbar_init_n(sm_addr(&bar_empty[k]), 1);
+        }
+        mbar_init_n(sm_addr(&bar_done), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        s_fail = 0;
+        s_abort = 0;
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const unsigned taddr = s_taddr;
-    // warps 0-3 clear the three accumulators in their lane quarters
-    if (warp < 4) {
+    // the four warps clear the three accumulators in their lane quarters
 #pragma unroll
-        for (int c = 0; c < 3 * NB; c += 16) tmem_zero<16>(taddr + ((unsigned)(32 * warp) << 16) + c);
-        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-    }
+    for (int c = 0; c < 3 * NB; c += 16) tmem_zero<16>(taddr + ((unsigned)(32 * warp) << 16) + c);
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const unsigned smb = sm_addr(sm);
-    const unsigned idesc = umma_idesc(128, NB) | (1u << 15) | (1u << 16);  // A and B MN-major
-    const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
-    int it = 0;  // items issued
-    for (int item = blockIdx.x; item < items; item += gridDim.x, ++it) {
-        const int st = it & 1;
-        // the MMAs of the item two back read this stage
-        if (tid == 0 && it >= 2 && !mbar_wait_bounded(sm_addr(&bar_mma[st]), ((it - 2) >> 1) & 1)) s_fail = 1;
-        __syncthreads();
-        if (s_fail) break;
-        const int img = item / (strips * segs), rem = item % (strips * segs);
-        const int oy0 = (rem / segs) * kWgR, ox0 = (rem % segs) * kWgSK;
-        unsigned char *sa = sm + st * G::STAGE, *sb = sa + G::ABYTES;
-        for (int q = tid; q < G::AROWS * (CA / 8) * kWgNPA; q += kWgThreads) {
-            const int px = q % kWgNPA, gr = (q / kWgNPA) % (CA / 8), r = q / (kWgNPA * (CA / 8));
-            const int yy = oy0 + r, xx = ox0 + px;
-            uint4 v = zero4;
-            if (yy < H && xx < W)
-                v = *reinterpret_cast<const uint4 *>(X + ((((size_t)img * H + yy) * (CA / 8) + gr) * Px + xx) * 8);
-            *reinterpret_cast<uint4 *>(sa + (size_t)q * 16) = v;
+    auto fail = [&]() {
+        atomicOr(err, FP_ERR_TIMEOUT);
+        s_abort = 1;
+    };
+
+    if (warp == 0) {
+        // ---- TMA producer: both copies of an item into its stage
+        if (lane == 0) {
+            int it = 0;
+            for (int item = blockIdx.x; item < items && !s_abort; item += gridDim.x, ++it) {
+                const int st = it & 1;
+                if (it >= 2 && !mbar_wait_or_abort(sm_addr(&bar_empty[st]), ((it - 2) >> 1) & 1, &s_abort)) {
+                    fail();
+                    break;
+                }
+                const int img = item / (strips * segs), rem = item % (strips * segs);
+                const int oy0 = (rem / segs) * kWgR, blk = (rem % segs) * (kWgSK / 32);
+                const unsigned sa = base + st * G::STAGE, sb = sa + G::ABYTES, fb = sm_addr(&bar_full[st]);
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(G::STAGE)
+                             : "memory");
+                asm volatile(
+                    "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+                    "%4, %5, %6}], [%7];" ::"r"(sa),
+                    "l"(reinterpret_cast<unsigned long long>(&tmX)), "r"(0), "r"(blk), "r"(0), "r"(oy0), "r"(img),
+                    "r"(fb)
+                    : "memory");
+                asm volatile(
+                    "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+                    "%4, %5, %6}], [%7];" ::"r"(sb),
+                    "l"(reinterpret_cast<unsigned long long>(&tmD)), "r"(0), "r"(blk), "r"(0), "r"(oy0 + 2),
+                    "r"(img), "r"(fb)
+                    : "memory");
+            }
+            // no copy of this CTA may still be landing when it exits
+            const int n = it < 2 ? it : 2;
+            for (int k = 0; k < n; ++k) {
+                const int q = it - 1 - k;
+                mbar_wait_bounded(sm_addr(&bar_full[q & 1]), (q >> 1) & 1);
+            }
         }
-        for (int q = tid; q < kWgR * (NB / 8) * kWgSK; q += kWgThreads) {
-            const int px = q % kWgSK, gr = (q / kWgSK) % (NB / 8), r = q / (kWgSK * (NB / 8));
-            const int yy = oy0 + r, xx = ox0 + px;
-            uint4 v = zero4;
-            if (yy < Ho && xx < Wo)
-                v = *reinterpret_cast<const uint4 *>(
-                    D + ((((size_t)img * (Ho + 4) + yy + 2) * (NB / 8) + gr) * Pd + xx + 2) * 8);
-            *reinterpret_cast<uint4 *>(sb + (size_t)q * 16) = v;
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const unsigned a0 = smb + st * G::STAGE, b0 = a0 + G::ABYTES;
-            for (int r = 0; r < kWgR; ++r)
+    } else if (warp == 1) {
+        // ---- MMA issuer
+        if (lane == 0) {
+            const unsigned idesc = umma_idesc(128, NB) | (1u << 15) | (1u << 16);  // A and B MN-major
+            int it = 0;
+            for (int item = blockIdx.x; item < items; item += gridDim.x, ++it) {
+                const int st = it & 1;
+                if (!mbar_wait_or_abort(sm_addr(&bar_full[st]), (it >> 1) & 1, &s_abort)) {
+                    fail();
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const unsigned a0 = base + st * G::STAGE, b0 = a0 + G::ABYTES;
+                for (int r = 0; r < kWgR; ++r)
 #pragma unroll
-                for (int kx = 0; kx < 3; ++kx)
+                    for (int kx = 0; kx < 3; ++kx)
 #pragma unroll
-                    for (int j = 0; j < kWgSK / 16; ++j) {
-                        // LBO = K-direction core stride (8 pixels), SBO = channel-group stride
-                        const unsigned long long ad =
-                            umma_desc(a0 + r * G::AROW + (16 * j + kx) * 16, 128, kWgNPA * 16);
-                        const unsigned long long bd = umma_desc(b0 + r * G::BROW + 16 * j * 16, 128, kWgSK * 16);
-                        mma_acc(taddr + kx * NB, ad, bd, idesc);
-                    }
+                        for (int j = 0; j < kWgSK / 16; ++j) {
+                            // LBO = K-direction core stride (8 pixels), SBO = channel-group stride
+                            const unsigned long long ad =
+                                umma_desc(a0 + r * G::AROW + (16 * j + kx) * 16, 128, kWgNP * 16);
+                            const unsigned long long bd =
+                                umma_desc(b0 + r * G::BROW + (16 * j + 2) * 16, 128, kWgNP * 16);
+                            mma_acc(taddr + kx * NB, ad, bd, idesc);
+                        }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 sm_addr(&bar_empty[st]))
+                             : "memory");
+            }
+            // every MMA issued above has completed once this arrives
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             sm_addr(&bar_mma[st]))
+                             sm_addr(&bar_done))
                          : "memory");
         }
     }
-    // the last two items' MMAs (all earlier ones were waited for)
-    if (tid == 0)
-        for (int k = it >= 2 ? it - 2 : 0; k < it; ++k)
-            if (!mbar_wait_bounded(sm_addr(&bar_mma[k & 1]), (k >> 1) & 1)) s_fail = 1;
+    // ---- epilogue (all four warps, once the roles are done): warp w reads
+    // TMEM lanes 32 w ..: lane m = stacked row m / CA, channel m % CA
     __syncthreads();
+    const bool done = mbar_wait_bounded(sm_addr(&bar_done), 0u);
+    if (!__all_sync(0xffffffffu, done) && lane == 0) fail();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (s_fail) {
-        if (tid == 0) atomicOr(err, FP_ERR_TIMEOUT);
-    } else {
-        // warp w reads TMEM lanes 32 (w % 4) ..: lane m = stacked row m / CA,
-        // channel m % CA; warps 4-7 take output channels 16 .. 31
-        const int quarter = warp & 3, half = warp >> 2;
-        const int m = 32 * quarter + lane, rr = m / CA, ca = m % CA;
+    __syncthreads();
+    if (!s_abort) {
+        const int m = 32 * warp + lane, rr = m / CA, ca = m % CA;
         float *pc = part + (size_t)blockIdx.x * 9 * CA * 32;
-        const unsigned tl = taddr + ((unsigned)(32 * quarter) << 16);
+        const unsigned tl = taddr + ((unsigned)(32 * warp) << 16);
 #pragma unroll
         for (int kx = 0; kx < 3; ++kx) {
             if constexpr (NB == 64) {
-                unsigned hi[16], lo[16];
-                tmem_load<16>(tl + kx * NB + 16 * half, hi);
-                tmem_load<16>(tl + kx * NB + LO + 16 * half, lo);
-                if (rr < 3)
 #pragma unroll
-                    for (int c = 0; c < 16; ++c)
-                        pc[((rr * 3 + kx) * CA + ca) * 32 + 16 * half + c] =
-                            __uint_as_float(hi[c]) + __uint_as_float(lo[c]);
-            } else if (half == 0) {
+                for (int half = 0; half < 2; ++half) {
+                    unsigned hi[16], lo[16];
+                    tmem_load<16>(tl + kx * NB + 16 * half, hi);
+                    tmem_load<16>(tl + kx * NB + LO + 16 * half, lo);
+                    if (rr < 3)
+#pragma unroll
+                        for (int c = 0; c < 16; ++c)
+                            pc[((rr * 3 + kx) * CA + ca) * 32 + 16 * half + c] =
+                                __uint_as_float(hi[c]) + __uint_as_float(lo[c]);
+                }
+            } else {
                 unsigned v[16];
                 tmem_load<16>(tl + kx * NB, v);
                 if (rr < 3)
@@ -978,6 +1012,23 @@ cudaError_t launch_conv(const fp_surrogate *s, const __nv_bfloat16 *wpack, const
     return cudaGetLastError();
 }
 
+// 5-D view (256 elements = 32 pixels x 8 channels, 32-pixel block, channel
+// group, row, image) of a BF16 image batch of `rows` rows, row pitch P pixels
+// and C channels in groups of 8, with boxes of (256, blocks, C / 8, box_rows, 1)
+cudaError_t encode_rows_map(CUtensorMap *m, const __nv_bfloat16 *x, int B, int rows, int P, int C, int blocks,
+                            int box_rows) {
+    auto enc = tmap_encoder();
+    if (!enc) return cudaErrorNotSupported;
+    const cuuint64_t dims[5] = {256, (cuuint64_t)(P / 32), (cuuint64_t)(C / 8), (cuuint64_t)rows, (cuuint64_t)B};
+    const cuuint64_t strides[4] = {512, (cuuint64_t)P * 16, (cuuint64_t)P * C * 2, (cuuint64_t)rows * P * C * 2};
+    const cuuint32_t box[5] = {256, (cuuint32_t)blocks, (cuuint32_t)(C / 8), (cuuint32_t)box_rows, 1};
+    const cuuint32_t es[5] = {1, 1, 1, 1, 1};
+    const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<__nv_bfloat16 *>(x), dims, strides,
+                           box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 // the weight gradient of a layer with input X (B x H x W, CA channels) and
 // split output gradient D (NB channels, padded); partials of *ctas CTAs in d_part
 template <int CA, int NB>
@@ -991,12 +1042,16 @@ cudaError_t launch_wgrad(const fp_surrogate *s, const __nv_bfloat16 *X, const __
         if (e != cudaSuccess) return e;
         attr = true;
     }
+    CUtensorMap mx, md;
+    cudaError_t e = encode_rows_map(&mx, X, B, H, fp_sur_pitch(W), CA, kWgBlocks, G::AROWS);
+    if (e == cudaSuccess) e = encode_rows_map(&md, D, B, H - 2 + 4, fp_sur_pitch(W - 2 + 4), NB, kWgBlocks, kWgR);
+    if (e != cudaSuccess) return e;
     const long long items = (long long)B * ((H - 2 + kWgR - 1) / kWgR) * ((W - 2 + kWgSK - 1) / kWgSK);
     const int cap = s->max_ctas > 0 ? std::min(s->max_ctas, s->part_ctas) : s->part_ctas;
     int grid = (int)std::min<long long>(items, (long long)cap);
     if (grid < 1) grid = 1;
     *ctas = grid;
-    conv_wgrad_tc_kernel<CA, NB><<<grid, kWgThreads, G::SMEM, st>>>(X, D, B, H, W, s->d_part, s->d_err);
+    conv_wgrad_tc_kernel<CA, NB><<<grid, kWgThreads, G::SMEM, st>>>(mx, md, B, H, W, s->d_part, s->d_err);
     return cudaGetLastError();
 }
 

@@ -30,7 +30,8 @@
 //                     the previous ReLU, splits the result for the next layer
 //                     and keeps the bias-gradient partial sums;
 //   weight gradient = per tap sum over pixels of input x output gradient:
-//                     tcgen05.mma with both operands MN-major (pixels are K),
+//                     tcgen05.mma with both operands MN-major (pixels are K)
+//                     as TMA lands whole rows of them,
 //                     M = 128 = the input channels of four (eight) stacked
 //                     input rows, N = the split gradient channels, one TMEM
 //                     accumulator per horizontal tap; per-CTA partials summed

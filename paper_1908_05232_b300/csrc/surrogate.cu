@@ -105,7 +105,9 @@ struct ConvGeom {
     static constexpr int TCOLS = kBlk * COUT;       // TMEM columns (a power of two, >= 32)
     static_assert((TCOLS & (TCOLS - 1)) == 0 && TCOLS >= 32 && TCOLS <= 512, "TMEM allocation");
     // guard region after the operands (a descriptor-field error reads garbage inside the allocation)
-    static constexpr int SMEM = ((WB + kRing * SLOT + 2048) + 1023) / 1024 * 1024;
+    // ring slots: four, two for 64 input channels (two CTAs then fit on an SM)
+    static constexpr int RING = CIN >= 64 ? 2 : kRing;
+    static constexpr int SMEM = ((WB + RING * SLOT + 2048) + 1023) / 1024 * 1024;
 };
 
 __device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity) {
@@ -206,7 +208,7 @@ __device__ __forceinline__ void tmem_zero<16>(unsigned taddr) {
 // starts: the epilogue clears a block after reading it, so every MMA
 // accumulates.  Warp-specialised pipeline, hand-offs by mbarriers only (every
 // wait bounded):
-//   producer warp (one thread): one TMA per input row into a ring of kRing slots --
+//   producer warp (one thread): one TMA per input row into a ring of G::RING slots --
 //     the 5-D tensor map (8 channels, pixel, k-core, row, image) lands the row
 //     as [k-core][pixel][8 channels], the MMA's canonical K-major layout;
 //     a slot is refilled once the MMAs that read it completed (free[slot]);
@@ -250,7 +252,7 @@ __global__ void __launch_bounds__(kConvWarps * 32) conv3x3_tc_kernel(const __gri
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        for (int k = 0; k < kRing; ++k) {
+        for (int k = 0; k < G::RING; ++k) {
             mbar_init_n(sm_addr(&bar_full[k]), 1);
             mbar_init_n(sm_addr(&bar_free[k]), 1);
         }
@@ -294,7 +296,7 @@ __global__ void __launch_bounds__(kConvWarps * 32) conv3x3_tc_kernel(const __gri
                 const int nrow = min(strip, Ho - oy0);
                 bool ok = true;
                 for (int i = 0; i < nrow + 2; ++i, ++q) {
-                    const unsigned slot = q % kRing, use = q / kRing;
+                    const unsigned slot = q % G::RING, use = q / G::RING;
                     if (use > 0 && !mbar_wait_or_abort(sm_addr(&bar_free[slot]), (use - 1) & 1u, &s_abort)) {
                         fail();
                         ok = false;
@@ -313,10 +315,10 @@ __global__ void __launch_bounds__(kConvWarps * 32) conv3x3_tc_kernel(const __gri
                 if (!ok) break;
             }
             // no copy of this CTA may still be landing when it exits
-            const unsigned n = q < (unsigned)kRing ? q : (unsigned)kRing;
+            const unsigned n = q < (unsigned)G::RING ? q : (unsigned)G::RING;
             for (unsigned k = 0; k < n; ++k) {
                 const unsigned qq = q - 1 - k;
-                mbar_wait_bounded(sm_addr(&bar_full[qq % kRing]), (qq / kRing) & 1u);
+                mbar_wait_bounded(sm_addr(&bar_full[qq % G::RING]), (qq / G::RING) & 1u);
             }
         }
     } else if (warp == kEpiWarps + 1) {
@@ -342,7 +344,7 @@ __global__ void __launch_bounds__(kConvWarps * 32) conv3x3_tc_kernel(const __gri
                 for (int i = 0; i < nrow + 2 && ok; ++i, ++q) {
                     // output rows i - kyhi .. i - kylo of the item take this row
                     const int kylo = max(0, i - (nrow - 1)), kyhi = min(2, i);
-                    ok = mbar_wait_or_abort(sm_addr(&bar_full[q % kRing]), (q / kRing) & 1u, &s_abort);
+                    ok = mbar_wait_or_abort(sm_addr(&bar_full[q % G::RING]), (q / G::RING) & 1u, &s_abort);
                     const unsigned gnew = g0 + (unsigned)i;  // the output row this input row starts
                     if (ok && kylo == 0 && gnew >= (unsigned)kBlk)
                         ok = mbar_wait_or_abort(sm_addr(&bar_acce[gnew % kBlk]), (gnew / kBlk - 1) & 1u, &s_abort);
@@ -354,7 +356,7 @@ __global__ void __launch_bounds__(kConvWarps * 32) conv3x3_tc_kernel(const __gri
                     const int nb = kyhi - kylo + 1;
                     const unsigned b0 = (g0 + (unsigned)(i - kyhi)) % kBlk;
                     const int n1 = min(nb, kBlk - (int)b0), n2 = nb - n1;
-                    const unsigned slot_off = (q % kRing) * (G::SLOT / 16);
+                    const unsigned slot_off = (q % G::RING) * (G::SLOT / 16);
                     const unsigned brow = (unsigned)((2 - kyhi) * COUT);
 #pragma unroll
                     for (int kx = 0; kx < 3; ++kx) {
@@ -369,7 +371,7 @@ __global__ void __launch_bounds__(kConvWarps * 32) conv3x3_tc_kernel(const __gri
                     }
                     // the input row is read by no later MMA
                     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                                     sm_addr(&bar_free[q % kRing]))
+                                     sm_addr(&bar_free[q % G::RING]))
                                  : "memory");
                     if (kyhi == 2)  // output row i - 2 is complete
                         asm volatile(

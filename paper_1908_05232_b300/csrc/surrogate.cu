@@ -43,6 +43,7 @@
 #include <cmath>
 #include <utility>
 #include <cstring>
+#include <mutex>
 #include <random>
 #include <string>
 #include <vector>
@@ -967,6 +968,23 @@ cudaError_t encode_act_map(CUtensorMap *m, const __nv_bfloat16 *x, int B, int H,
 
 constexpr int kConvMaxPerSM = 3;  // resident convolution CTAs per SM at most
 
+// The dynamic shared-memory limit of a kernel raised to bytes on the current
+// device, once per (kernel, device): the kernel's address keys the record.
+template <typename K>
+cudaError_t set_smem_once(K *kernel, int bytes) {
+    static std::mutex mu;
+    static std::vector<std::pair<const void *, int>> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    for (const auto &d : done)
+        if (d.first == (const void *)kernel && d.second == dev) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) done.emplace_back((const void *)kernel, dev);
+    return e;
+}
+
 // one implicit-GEMM convolution of B x H x W images x (CIN channels) into y
 // (act, dbpart: the data-gradient epilogue's mask and partials; grid_out: the
 // CTAs launched, each leaving 4 bias-gradient slots in that epilogue)
@@ -975,12 +993,9 @@ cudaError_t launch_conv(const fp_surrogate *s, const __nv_bfloat16 *wpack, const
                         const __nv_bfloat16 *x, int B, int H, int W, void *y, const __nv_bfloat16 *act,
                         float *dbpart, int *grid_out, cudaStream_t st) {
     using G = ConvGeom<CIN, COUT>;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(conv3x3_tc_kernel<CIN, COUT, MODE>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
+    {
+        cudaError_t e = set_smem_once(conv3x3_tc_kernel<CIN, COUT, MODE>, G::SMEM);
         if (e != cudaSuccess) return e;
-        attr = true;
     }
     // resident CTAs per SM: shared memory (the dynamic part plus 2 KB of static
     // and reserved per CTA), TMEM (512 / TCOLS columns), at most three
@@ -1038,12 +1053,9 @@ template <int CA, int NB>
 cudaError_t launch_wgrad(const fp_surrogate *s, const __nv_bfloat16 *X, const __nv_bfloat16 *D, int B, int H, int W,
                          int *ctas, cudaStream_t st) {
     using G = WgGeom<CA, NB>;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(conv_wgrad_tc_kernel<CA, NB>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
+    {
+        cudaError_t e = set_smem_once(conv_wgrad_tc_kernel<CA, NB>, G::SMEM);
         if (e != cudaSuccess) return e;
-        attr = true;
     }
     CUtensorMap mx, md;
     cudaError_t e = encode_rows_map(&mx, X, B, H, fp_sur_pitch(W), CA, kWgBlocks, G::AROWS);

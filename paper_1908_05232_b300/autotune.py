@@ -60,8 +60,8 @@ def tune(sc, steps: int = 48, warm: int = 16, modes=(N.FP_MODE_KERNELS, N.FP_MOD
         for rows in TILE_ROWS:
             for lanes in PED_LANES:
                 for ahead in HASH_AHEAD:
-                    if mode == N.FP_MODE_PERSISTENT and (rows != 16 or lanes != 8 or not ahead):
-                        continue  # the persistent kernel has one fixed shape
+                    if mode == N.FP_MODE_PERSISTENT and (rows != 8 or lanes != 1 or not ahead):
+                        continue  # the persistent kernel has one fixed shape (8-row runs, 1 lane)
                     N.fp_set_tuning(sim.h, rows, lanes)
                     N.fp_set_hash_ahead(sim.h, ahead)
                     sim.step(8)

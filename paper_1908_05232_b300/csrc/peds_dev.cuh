@@ -79,7 +79,6 @@ __device__ __forceinline__ bool walkable_at(const FpSim &S, float x, float y) {
 }
 
 
-constexpr int kGroup = 8;  // lanes per pedestrian in the single simulation's persistent kernel
 
 // Values every thread of a step reads once (filled by one thread per CTA).
 struct StepCtl {

@@ -31,8 +31,9 @@
 namespace {
 using namespace fpdev;
 
-constexpr int kPT = 512;       // threads per CTA = 32 x TY with TY = 16
-constexpr int kPTY = 16;
+constexpr int kPT = 512;       // threads per CTA
+constexpr int kPTY = 8;        // flood run height
+constexpr int kPLanes = 1;     // lanes per pedestrian
 constexpr int kMaxCTAs = 2048;
 
 
@@ -204,7 +205,7 @@ __global__ void __launch_bounds__(kPT, 1) persistent_kernel(const __grid_constan
         }
         const StepCtl ctl = s_ctl;
         const bool hash_next = s + 1 < nsteps;
-        constexpr int kPedPerCTA = kPT / kGroup;
+        constexpr int kPedPerCTA = kPT / kPLanes;
         unsigned *ticket = bar + 2 + (s & 1);  // zeroed during the previous step (or before the launch)
         for (;;) {
             if (tid == 0) s_pcx = (int)atomicAdd(ticket, 1u);
@@ -212,7 +213,7 @@ __global__ void __launch_bounds__(kPT, 1) persistent_kernel(const __grid_constan
             const int pcx = s_pcx;
             __syncthreads();
             if (pcx * kPedPerCTA >= nA) break;
-            ped_group<kGroup>(S, par, ctl, pcx * kPedPerCTA + tid / kGroup, tid & (kGroup - 1), lookup, hash_next);
+            ped_group<kPLanes>(S, par, ctl, pcx * kPedPerCTA + tid / kPLanes, tid & (kPLanes - 1), lookup, hash_next);
         }
         if (cta == 0 && tid < 32) door_entries(S, par, ctl, hash_next);  // thread 0 set nB = nA above
         if (!grid_sync(bar, S)) return;

@@ -793,28 +793,35 @@ __global__ void __launch_bounds__(kWgThreads) conv_wgrad_tc_kernel(const __grid_
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "n"(G::TCOLS));
 }
 
-// dW (master layout [tap][ci][co]) and db of one layer: the per-CTA weight
-// partials part[cta][tap][CA][32] and the bias partials dbpart[slot][32].
-// A block takes 32 consecutive outputs; thread (g, o) sums partials g, g + 32,
-// ... of output o, then the 32 sums are added in order (deterministic).
-__global__ void __launch_bounds__(1024) grad_reduce_kernel(const float *__restrict__ part, int ctas, int CA,
-                                                           int ci_real, int co_real,
-                                                           const float *__restrict__ dbpart, int slots,
-                                                           float *__restrict__ dw, float *__restrict__ db) {
+// dW (master layout [tap][ci][co]) and db of every layer in one launch
+// (blockIdx.y = layer): the per-CTA weight partials part[cta][tap][CA][32] and
+// the bias partials dbpart[slot][32] of the layer.  A block takes 32
+// consecutive outputs; thread (g, o) sums partials g, g + 32, ... of output
+// o, then the 32 sums are added in order (deterministic).
+struct ReduceJobs {
+    const float *part[kLayers], *dbpart[kLayers];
+    float *dw[kLayers], *db[kLayers];
+    int ctas[kLayers], CA[kLayers], ci[kLayers], co[kLayers], slots[kLayers];
+};
+
+__global__ void __launch_bounds__(1024) grad_reduce_kernel(const __grid_constant__ ReduceJobs J) {
     __shared__ float red[32][33];
+    const int l = blockIdx.y;
     const int o = threadIdx.x & 31, g = threadIdx.x >> 5;
     const int k = blockIdx.x * 32 + o;
+    const int ci_real = J.ci[l], co_real = J.co[l], CA = J.CA[l];
     const int nw = 9 * ci_real * co_real;
+    if ((int)blockIdx.x * 32 >= nw + co_real) return;  // block-uniform: this layer has fewer outputs
     float acc = 0.0f;
     if (k < nw) {
         const int co = k % co_real, ci = (k / co_real) % ci_real, t = k / (co_real * ci_real);
-        const float *p = part + ((size_t)t * CA + ci) * 32 + co;
+        const float *p = J.part[l] + ((size_t)t * CA + ci) * 32 + co;
         const size_t stride = (size_t)9 * CA * 32;
 #pragma unroll 4
-        for (int c = g; c < ctas; c += 32) acc += p[c * stride];
+        for (int c = g; c < J.ctas[l]; c += 32) acc += p[c * stride];
     } else if (k < nw + co_real) {
 #pragma unroll 4
-        for (int q = g; q < slots; q += 32) acc += dbpart[(size_t)q * 32 + (k - nw)];
+        for (int q = g; q < J.slots[l]; q += 32) acc += J.dbpart[l][(size_t)q * 32 + (k - nw)];
     }
     red[g][o] = acc;
     __syncthreads();
@@ -822,9 +829,9 @@ __global__ void __launch_bounds__(1024) grad_reduce_kernel(const float *__restri
         float sum = 0.0f;
         for (int j = 0; j < 32; ++j) sum += red[j][o];
         if (k < nw)
-            dw[k] = sum;
+            J.dw[l][k] = sum;
         else
-            db[k - nw] = sum;
+            J.db[l][k - nw] = sum;
     }
 }
 
@@ -919,8 +926,9 @@ struct fp_surrogate {
     size_t cap_pix = 0, cap_partial = 0;
     __nv_bfloat16 *d_a[kLayers] = {};             // inputs of every layer (a[0] packed input)
     float *d_out = nullptr;
-    // backward scratch: two padded split-gradient images, the weight-gradient
-    // partials of up to part_ctas CTAs, the bias-gradient partials
+    // backward scratch: two padded split-gradient images, per layer the
+    // weight-gradient partials of up to part_ctas CTAs and the bias-gradient
+    // partials of up to cap_slots slots
     size_t cap_dpad = 0, cap_slots = 0;
     __nv_bfloat16 *d_dpad[2] = {};
     float *d_part = nullptr, *d_dbpart = nullptr;
@@ -1048,10 +1056,10 @@ cudaError_t encode_rows_map(CUtensorMap *m, const __nv_bfloat16 *x, int B, int r
 }
 
 // the weight gradient of a layer with input X (B x H x W, CA channels) and
-// split output gradient D (NB channels, padded); partials of *ctas CTAs in d_part
+// split output gradient D (NB channels, padded); partials of *ctas CTAs in part
 template <int CA, int NB>
 cudaError_t launch_wgrad(const fp_surrogate *s, const __nv_bfloat16 *X, const __nv_bfloat16 *D, int B, int H, int W,
-                         int *ctas, cudaStream_t st) {
+                         float *part, int *ctas, cudaStream_t st) {
     using G = WgGeom<CA, NB>;
     {
         cudaError_t e = set_smem_once(conv_wgrad_tc_kernel<CA, NB>, G::SMEM);
@@ -1066,7 +1074,7 @@ cudaError_t launch_wgrad(const fp_surrogate *s, const __nv_bfloat16 *X, const __
     int grid = (int)std::min<long long>(items, (long long)cap);
     if (grid < 1) grid = 1;
     *ctas = grid;
-    conv_wgrad_tc_kernel<CA, NB><<<grid, kWgThreads, G::SMEM, st>>>(mx, md, B, H, W, s->d_part, s->d_err);
+    conv_wgrad_tc_kernel<CA, NB><<<grid, kWgThreads, G::SMEM, st>>>(mx, md, B, H, W, part, s->d_err);
     return cudaGetLastError();
 }
 
@@ -1124,8 +1132,8 @@ bool ensure_scratch(fp_surrogate *s, size_t pix) {
 }
 
 // backward scratch for B x H x W inputs: padded split gradients up to
-// (H + 2) x (W + 2) x 64 channels; bias-gradient slots for the loss blocks or
-// four per convolution CTA
+// (H + 2) x (W + 2) x 64 channels; per layer, bias-gradient slots for the loss
+// blocks or four per convolution CTA
 bool ensure_bwd(fp_surrogate *s, int B, int H, int W) {
     const size_t dpad = (size_t)B * (H + 2) * fp_sur_pitch(W + 2) * 2 * kWidth;
     const size_t slots = std::max<size_t>(((size_t)B * H * W + 255) / 256 + 1,
@@ -1135,7 +1143,7 @@ bool ensure_bwd(fp_surrogate *s, int B, int H, int W) {
     s->cap_dpad = s->cap_slots = 0;
     bool ok = cudaMalloc(&s->d_dpad[0], dpad * sizeof(__nv_bfloat16)) == cudaSuccess;
     ok &= cudaMalloc(&s->d_dpad[1], dpad * sizeof(__nv_bfloat16)) == cudaSuccess;
-    ok &= cudaMalloc(&s->d_dbpart, slots * 32 * sizeof(float)) == cudaSuccess;
+    ok &= cudaMalloc(&s->d_dbpart, (size_t)kLayers * slots * 32 * sizeof(float)) == cudaSuccess;
     if (ok) {
         s->cap_dpad = dpad;
         s->cap_slots = slots;
@@ -1169,49 +1177,62 @@ cudaError_t forward_keep(fp_surrogate *s, const float *x, int B, int H, int W, f
 }
 
 // loss and gradients (into d_grad, master layout) of the last forward_keep.
-// Layer l (input H - 2l x W - 2l): weight gradient from its input and split
-// output gradient, reduced with the bias partials its producer left; then
-// (l > 0) the data gradient into the other padded image.
+// Layer l (input H - 2l x W - 2l): weight-gradient partials from its input and
+// split output gradient; then (l > 0) the data gradient into the other padded
+// image, whose epilogue leaves the bias partials of layer l - 1.  Every
+// layer's partials have buffers of their own, reduced in one launch at the end.
 cudaError_t backward(fp_surrogate *s, const float *target, int B, int H, int W, cudaStream_t st) {
     const int H5 = H - 2 * kLayers, W5 = W - 2 * kLayers;
     const size_t npix = (size_t)B * H5 * W5, n_out = npix * 3;
     const unsigned nb = (unsigned)((npix + 255) / 256);
+    const size_t part_stride = (size_t)s->part_ctas * 9 * kWidth * 32, slot_stride = s->cap_slots * 32;
+    ReduceJobs J{};
     __nv_bfloat16 *cur = s->d_dpad[0], *nxt = s->d_dpad[1];
     cudaError_t e = cudaMemsetAsync(cur, 0, (size_t)B * (H5 + 4) * fp_sur_pitch(W5 + 4) * 16 * sizeof(__nv_bfloat16),
                                     st);
     if (e != cudaSuccess) return e;
-    loss_grad_kernel<<<nb, 256, 0, st>>>(s->d_out, target, B, H5, W5, n_out, cur, s->d_partial, s->d_dbpart);
+    loss_grad_kernel<<<nb, 256, 0, st>>>(s->d_out, target, B, H5, W5, n_out, cur, s->d_partial,
+                                         s->d_dbpart + (kLayers - 1) * slot_stride);
     sum_partials_kernel<<<1, 256, 0, st>>>(s->d_partial, (int)nb, 1.0 / (double)n_out, s->d_loss);
-    int slots = (int)nb;
+    J.slots[kLayers - 1] = (int)nb;
+    int most = 0;  // blocks of the largest layer's reduction
     for (int l = kLayers - 1; l >= 0 && e == cudaSuccess; --l) {
         const int Hl = H - 2 * l, Wl = W - 2 * l;
-        int ctas = 0;
+        float *part = s->d_part + l * part_stride;
         if (l == kLayers - 1)
-            e = launch_wgrad<kWidth, 16>(s, s->d_a[l], cur, B, Hl, Wl, &ctas, st);
+            e = launch_wgrad<kWidth, 16>(s, s->d_a[l], cur, B, Hl, Wl, part, &J.ctas[l], st);
         else if (l > 0)
-            e = launch_wgrad<kWidth, 2 * kWidth>(s, s->d_a[l], cur, B, Hl, Wl, &ctas, st);
+            e = launch_wgrad<kWidth, 2 * kWidth>(s, s->d_a[l], cur, B, Hl, Wl, part, &J.ctas[l], st);
         else
-            e = launch_wgrad<kCin0, 2 * kWidth>(s, s->d_a[0], cur, B, Hl, Wl, &ctas, st);
+            e = launch_wgrad<kCin0, 2 * kWidth>(s, s->d_a[0], cur, B, Hl, Wl, part, &J.ctas[l], st);
         if (e != cudaSuccess) break;
-        const int nred = 9 * kCh[l] * kCh[l + 1] + kCh[l + 1];
-        grad_reduce_kernel<<<(nred + 31) / 32, 1024, 0, st>>>(s->d_part, ctas, l == 0 ? kCin0 : kWidth, kCh[l],
-                                                               kCh[l + 1], s->d_dbpart, slots,
-                                                               s->d_grad + s->w_off[l], s->d_grad + s->b_off[l]);
+        J.part[l] = part;
+        J.dbpart[l] = s->d_dbpart + l * slot_stride;
+        J.dw[l] = s->d_grad + s->w_off[l];
+        J.db[l] = s->d_grad + s->b_off[l];
+        J.CA[l] = l == 0 ? kCin0 : kWidth;
+        J.ci[l] = kCh[l];
+        J.co[l] = kCh[l + 1];
+        most = std::max(most, (9 * kCh[l] * kCh[l + 1] + kCh[l + 1] + 31) / 32);
         if (l == 0) break;
         e = cudaMemsetAsync(nxt, 0, (size_t)B * (Hl + 4) * fp_sur_pitch(Wl + 4) * 2 * kWidth * sizeof(__nv_bfloat16),
                             st);
         if (e != cudaSuccess) break;
         int grid = 0;
+        float *dbp = s->d_dbpart + (l - 1) * slot_stride;
         if (l == kLayers - 1)
             e = launch_conv<16, kWidth, kBwdData>(s, s->d_wpack_bwd[l], nullptr, cur, B, Hl + 2, Wl + 2, nxt,
-                                                  s->d_a[l], s->d_dbpart, &grid, st);
+                                                  s->d_a[l], dbp, &grid, st);
         else
             e = launch_conv<2 * kWidth, kWidth, kBwdData>(s, s->d_wpack_bwd[l], nullptr, cur, B, Hl + 2, Wl + 2, nxt,
-                                                          s->d_a[l], s->d_dbpart, &grid, st);
-        slots = 4 * grid;
+                                                          s->d_a[l], dbp, &grid, st);
+        J.slots[l - 1] = 4 * grid;
         std::swap(cur, nxt);
     }
-    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e == cudaSuccess) {
+        grad_reduce_kernel<<<dim3(most, kLayers), 1024, 0, st>>>(J);
+        e = cudaGetLastError();
+    }
     return e;
 }
 
@@ -1292,7 +1313,7 @@ int fp_surrogate_create(uint64_t seed, fp_surrogate **out) {
         }
     }
     s->part_ctas = s->sms;  // one weight-gradient CTA per SM
-    ok &= (s->d_part = static_cast<float *>(alloc((size_t)s->part_ctas * 9 * kWidth * 32 * sizeof(float)))) !=
+    ok &= (s->d_part = static_cast<float *>(alloc((size_t)kLayers * s->part_ctas * 9 * kWidth * 32 * sizeof(float)))) !=
           nullptr;
     ok &= (s->d_err = static_cast<unsigned *>(alloc(sizeof(unsigned)))) != nullptr;
     ok &= (s->d_loss = static_cast<double *>(alloc(sizeof(double)))) != nullptr;

@@ -153,6 +153,8 @@ def tune_batch(scs, rounds: int = 2, classes: int = 2) -> dict:
     with the others held, the incumbent among them (coordinate descent).
     Returns {"shapes": [(tile_rows, ped_lanes) per scenario], "us_per_step",
     "uniform": {shape: us}, "classes": [class of each scenario]}."""
+    if not scs:
+        return {"shapes": [], "us_per_step": 0.0, "uniform": {}, "classes": []}
     members = [N.from_scenario(sc) for sc in scs]
     try:
         n = len(scs)
@@ -163,6 +165,8 @@ def tune_batch(scs, rounds: int = 2, classes: int = 2) -> dict:
         class_shape = [min(uniform, key=uniform.get)] * classes
         best = uniform[class_shape[0]]
         for c in range(classes):
+            if c not in cls:
+                continue  # no member of this size class
             trials = []
             for cand in cands:
                 t = list(class_shape)

@@ -17,3 +17,7 @@ def test_batch_size_classes_split_by_cell_count():
     # ties keep the input order; every class of equal-size members is used
     assert autotune.size_classes([100] * 4, 2) == [0, 0, 1, 1]
     assert autotune.size_classes([], 2) == []
+
+
+def test_tune_batch_of_nothing_needs_no_gpu():
+    assert autotune.tune_batch([]) == {"shapes": [], "us_per_step": 0.0, "uniform": {}, "classes": []}

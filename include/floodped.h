@@ -362,7 +362,11 @@ int fp_surrogate_set_params(fp_surrogate *sur, const float *src, size_t n);
 int fp_surrogate_forward(fp_surrogate *sur, const float *x, int32_t B, int32_t H, int32_t W, float *y);
 /* Loss = mean squared error of the forward output against target (device FP32
  * [B][H-10][W-10][3]) and its gradient with respect to every parameter
- * (grads: host or device, fp_surrogate_num_params floats; may be NULL). */
+ * (grads: host or device, fp_surrogate_num_params floats; may be NULL).  The
+ * backward runs on the tensor cores as well: each layer's output gradient is
+ * carried as its BF16 rounding plus the BF16 rounding of the remainder (about
+ * FP32 precision), per-CTA partial sums are added in a fixed order, so the
+ * result does not change from call to call. */
 int fp_surrogate_gradients(fp_surrogate *sur, const float *x, const float *target, int32_t B, int32_t H, int32_t W,
                            float *grads, double *loss);
 /* One Adam step (beta1 0.9, beta2 0.999) of learning rate lr on that loss. */

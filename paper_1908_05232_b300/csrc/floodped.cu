@@ -170,11 +170,14 @@ struct fp_sim {
     size_t flag_blocks() const {
         return (size_t)((S.nx + FP_TX - 1) / FP_TX) * (size_t)((S.ny + FP_BLK_ROWS - 1) / FP_BLK_ROWS);
     }
+    size_t muscl_tiles() const { return (size_t)((S.nx + 31) / 32) * (size_t)((S.ny + 7) / 8); }
     // every block "maybe wet": after any write of the water state from outside
     // the flood update, the next two updates run every tile
     cudaError_t reset_water_flags() {
         cudaError_t e = cudaSuccess;
         for (int p = 0; p < 2 && e == cudaSuccess; ++p) e = cudaMemsetAsync(S.blk_wet[p], 1, flag_blocks(), stream);
+        for (int p = 0; p < 3 && e == cudaSuccess && S.mflag[0]; ++p)
+            e = cudaMemsetAsync(S.mflag[p], 1, muscl_tiles(), stream);
         return e;
     }
 };
@@ -532,6 +535,7 @@ int fp_sim_create(const fp_config *cfg, fp_sim **out) {
         ok &= (S.mh = s->dalloc<float>(pe)) != nullptr;
         ok &= (S.mhu = s->dalloc<float>(pe)) != nullptr;
         ok &= (S.mhv = s->dalloc<float>(pe)) != nullptr;
+        for (int p = 0; p < 3; ++p) ok &= (S.mflag[p] = s->dalloc<unsigned char>(s->muscl_tiles())) != nullptr;
     }
     ok &= (S.n0 = s->dalloc<float>(pe)) != nullptr;
     ok &= (S.occ[0] = s->dalloc<unsigned short>(pe + 2)) != nullptr;

@@ -128,6 +128,11 @@ struct FpSim {
     int riemann;                   // interface flux: 0 HLL, 1 HLLC
     int order;                     // 1: first order (the paper's); 2: MUSCL + two-stage Runge-Kutta
     float *mh, *mhu, *mhv;         // second order: the first stage's state (padded planes)
+    // second order: per tile of 32 x 8 cells (row-major over the tile grid), 0
+    // if h = hu = hv = 0 in all its cells: [0], [1] the state planes by parity,
+    // [2] the first stage's state (written by the stage that produced the
+    // plane); nullptr when the first-order update is used
+    unsigned char *mflag[3];
     // discharge breach (Section 3.1): boundary cells coded FP_BC_DISCHARGE take
     // the hydrograph Q(t) (points q_t, q_Q) spread over their width q_width
     int has_discharge, n_q;

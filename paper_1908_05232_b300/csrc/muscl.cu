@@ -128,19 +128,69 @@ __global__ void __launch_bounds__(kMx * kMy) muscl_stage_kernel(const __grid_con
     const int tid = threadIdx.x;
     const FloodStep st = flood_step_consts(S, slot);
     if (STAGE == 1 && blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) flood_clock_advance(S, slot, st);
-    const float h_in = STAGE == 1 ? st.h_in : S.clock[(slot + 1) & 3].h_in;
-    const double half_dtdx = 0.5 * (double)st.dtf * (double)S.dx;
     const float *ih = STAGE == 1 ? S.h[par] : S.mh, *ihu = STAGE == 1 ? S.hu[par] : S.mhu,
                 *ihv = STAGE == 1 ? S.hv[par] : S.mhv;
-    // the region with its two-cell halo (zeros outside the domain, never used)
-    for (int k = tid; k < kRx * kRy; k += kMx * kMy) {
+    // the region with its two-cell halo (zeros outside the domain, never used),
+    // loaded into registers first: the dry-tile test below runs beside the loads
+    constexpr int kLoads = (kRx * kRy + kMx * kMy - 1) / (kMx * kMy);
+    float lh[kLoads], lq[kLoads], lr[kLoads], lz[kLoads];
+#pragma unroll
+    for (int it = 0; it < kLoads; ++it) {
+        const int k = tid + it * kMx * kMy;
         const int rx = k % kRx, ry = k / kRx, gi = x0 + rx - 2, gj = y0 + ry - 2;
-        float h = 0.0f, q = 0.0f, r = 0.0f, z = 0.0f;
-        if (gi >= 0 && gi < nx && gj >= 0 && gj < ny) {
+        lh[it] = lq[it] = lr[it] = lz[it] = 0.0f;
+        if (k < kRx * kRy && gi >= 0 && gi < nx && gj >= 0 && gj < ny) {
             const size_t o = fp_pidx(S, gi, gj);
-            h = ih[o]; q = ihu[o]; r = ihv[o]; z = S.z[o];
+            lh[it] = ih[o]; lq[it] = ihu[o]; lr[it] = ihv[o]; lz[it] = S.z[o];
         }
-        R.h[ry][rx] = h; R.u[ry][rx] = vel(q, h); R.v[ry][rx] = vel(r, h);
+    }
+    // Dry tiles: when no cell this tile's faces reach holds water in the stage's
+    // input (its 3 x 3 tile neighbourhood, all h = hu = hv = 0; for stage 2
+    // also its own tile of the step's start state, which the average reads)
+    // and it does not touch the domain edge (inflow, boundary fluxes), every
+    // flux, slope term and friction term is zero and the output is zero: it
+    // is written only where not already known to be zero, and the evacuee
+    // counts the update would consume are cleared.  Interior tiles are full.
+    const int tnx = gridDim.x, tny = gridDim.y, bx = blockIdx.x, by = blockIdx.y, tile = by * tnx + bx;
+    const unsigned char *fin = S.mflag[0] == nullptr ? nullptr : STAGE == 1 ? S.mflag[par] : S.mflag[2];
+    unsigned char *fout = S.mflag[0] == nullptr ? nullptr : STAGE == 1 ? S.mflag[2] : S.mflag[par ^ 1];
+    if (fin != nullptr) {
+        const bool edge = bx == 0 || by == 0 || bx == tnx - 1 || by == tny - 1;
+        int wet = edge ? 1 : 0;
+        if (!edge && tid < 9) wet = fin[(by - 1 + tid / 3) * tnx + bx - 1 + tid % 3] != 0;
+        if (STAGE == 2 && !edge && tid == 9) wet = S.mflag[par][tile] != 0;
+        if (!__syncthreads_or(wet)) {
+            const bool need = fout[tile] != 0;
+            const size_t o = fp_pidx(S, x0 + tid % kMx, y0 + tid / kMx);
+            if (STAGE == 1) {
+                if (need) {
+                    S.mh[o] = 0.0f;
+                    S.mhu[o] = 0.0f;
+                    S.mhv[o] = 0.0f;
+                }
+            } else {
+                const int p2 = par ^ 1;
+                if (need) {
+                    S.h[p2][o] = 0.0f;
+                    S.hu[p2][o] = 0.0f;
+                    S.hv[p2][o] = 0.0f;
+                }
+                if (S.occ[par][o] != 0) S.occ[par][o] = 0;
+            }
+            __syncthreads();  // every thread has read the flag
+            if (need && tid == 0) fout[tile] = 0;
+            return;
+        }
+    }
+    const float h_in = STAGE == 1 ? st.h_in : S.clock[(slot + 1) & 3].h_in;
+    const double half_dtdx = 0.5 * (double)st.dtf * (double)S.dx;
+#pragma unroll
+    for (int it = 0; it < kLoads; ++it) {
+        const int k = tid + it * kMx * kMy;
+        if (k >= kRx * kRy) continue;
+        const int rx = k % kRx, ry = k / kRx;
+        const float h = lh[it], z = lz[it];
+        R.h[ry][rx] = h; R.u[ry][rx] = vel(lq[it], h); R.v[ry][rx] = vel(lr[it], h);
         R.eta[ry][rx] = __fadd_rn(h, z); R.z[ry][rx] = z;
     }
     __syncthreads();
@@ -195,6 +245,7 @@ __global__ void __launch_bounds__(kMx * kMy) muscl_stage_kernel(const __grid_con
     __syncthreads();
     const int tx = tid % kMx, ty = tid / kMx, gi = x0 + tx, gj = y0 + ty;
     FloodAcc acc = flood_acc_init();
+    int nz = 0;  // this cell's output holds water
     if (gi < nx && gj < ny) {
         const FaceFlux &W = xf[ty][tx], &E = xf[ty][tx + 1], &So = yf[ty][tx], &No = yf[ty + 1][tx];
         // x faces: (mass, u-momentum, v-momentum); y faces: (mass, v-momentum, u-momentum);
@@ -231,6 +282,7 @@ __global__ void __launch_bounds__(kMx * kMy) muscl_stage_kernel(const __grid_con
         }
         if (STAGE == 1) {
             S.mh[o] = hh; S.mhu[o] = qu; S.mhv[o] = qv;
+            nz = hh != 0.0f || qu != 0.0f || qv != 0.0f;
         } else {
             hh = 0.5f * __fadd_rn(S.h[par][o], hh);
             qu = 0.5f * __fadd_rn(S.hu[par][o], qu);
@@ -238,11 +290,16 @@ __global__ void __launch_bounds__(kMx * kMy) muscl_stage_kernel(const __grid_con
             if (hh <= FP_H_EPS_F) { qu = 0.0f; qv = 0.0f; }
             const int p2 = par ^ 1;
             S.h[p2][o] = hh; S.hu[p2][o] = qu; S.hv[p2][o] = qv;
+            nz = hh != 0.0f || qu != 0.0f || qv != 0.0f;
             if (S.occ[par][o] != 0) S.occ[par][o] = 0;
             if (!(hh == hh) || !(qu == qu) || !(qv == qv)) acc.bad = 1;
             if (hh > FP_H_EPS_F) acc.smax = fp_wave_speed(g, hh, qu, qv);
             if (hh >= FP_H_DRY_F) acc.wet = 1;
         }
+    }
+    if (fout != nullptr) {
+        const int any = __syncthreads_or(nz);
+        if (tid == 0) fout[tile] = any ? 1 : 0;
     }
     if (STAGE == 1) {
         const unsigned ng = __reduce_add_sync(0xffffffffu, (unsigned)acc.neg);

@@ -176,3 +176,56 @@ def test_refused_step_forms(P):
     with pytest.raises(N.FloodPedError):
         N.fp_sim_create(bad)
     sim.close()
+
+
+def test_mostly_dry_grid_parity(P, O):
+    """Second order with water in the west third only, inflow on the east
+    edge: tiles whose 3 x 3 tile neighbourhood holds no water are skipped
+    (their output written as zeros once), the wet front and the edge tiles
+    computed; one step and 120 steps against the oracle."""
+    sc = S.random_wet_state(300, 200, dx=0.8, seed=21)
+    sc.h[:, 100:] = 0.0
+    sc.hu[:, 100:] = 0.0
+    sc.hv[:, 100:] = 0.0
+    sc.order = 2
+    o = O.Oracle(sc)
+    o.step(1)
+    sim = P.from_scenario(sc)
+    sim.step(1)
+    sim.synchronize()
+    assert sim.counters()["t_ticks"] == o.t_ticks
+    _close(sim, o, 2e-5, 2e-6)
+    o.step(119)
+    sim.step(119)
+    sim.synchronize()
+    assert abs(sim.counters()["t_ticks"] - o.t_ticks) <= 120
+    _close(sim, o, 1e-4)
+
+
+def test_state_write_reopens_skipped_tiles(P):
+    """Second order: after the dry east part's tiles are skipped, water put
+    there by a state write from the host makes every tile run again -- the run
+    continues exactly as a fresh simulation from that state."""
+    import copy
+    sc = S.random_wet_state(300, 200, dx=0.8, seed=23, bc=(S.BC_WALL,) * 4)
+    sc.h[:, 90:] = 0.0
+    sc.hu[:, 90:] = 0.0
+    sc.hv[:, 90:] = 0.0
+    sc.order = 2
+    a = P.from_scenario(sc)
+    a.step(40)
+    a.synchronize()
+    h, hu, hv = _fields(a)
+    assert np.all(h[:, 200:] == 0.0)
+    h[60:120, 220:280] += 0.5
+    P._native.fp_set_state(a.h, h, hu, hv)
+    sc2 = copy.deepcopy(sc)
+    sc2.h, sc2.hu, sc2.hv = h.copy(), hu.copy(), hv.copy()
+    b = P.from_scenario(sc2)
+    a.step(60)
+    b.step(60)
+    a.synchronize()
+    b.synchronize()
+    for x, y in zip(_fields(a), _fields(b)):
+        assert np.array_equal(x, y)
+    assert np.any(_fields(a)[0][:, 220:280] != 0.0)

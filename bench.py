@@ -189,8 +189,8 @@ class ClockSampler:
 # launch from ncu captures of the kernel sources with this hash: the mid-flood
 # barrier case in the benchmark's tuned shape (8-row runs) and the wet grid
 # (16-row runs)
-FLOOD_TRAFFIC = {"sources_sha256": "e069ef3b80ca1729bb586e70e5f9d62f9d3c1aff257ebcf1c81fc9f0697df29b",
-                 "barrier_2048_midflood": 21733632, "wet_2048": 114549760}
+FLOOD_TRAFFIC = {"sources_sha256": "ea3c758bdcb0678f4701bed21628187c6212c4ad10392e72562a7157ca119d49",
+                 "barrier_2048_midflood": 21734784, "wet_2048": 115072256}
 FLOOD_SOURCES = ("flood.cu", "flood_dev.cuh", "fp_common.cuh")
 
 

@@ -146,11 +146,13 @@ def _race(members, shape_lists, rounds: int = 2, chunk: int = 64):
             b.close()
 
 
-def tune_batch(scs, rounds: int = 2, classes: int = 2) -> dict:
+def tune_batch(scs, rounds: int = 3, classes: int = 2, margin: float = 0.02) -> dict:
     """Launch shapes for a batch of the scenarios ``scs`` (per-step-kernel mode),
     raced on a scratch batch: the 15 uniform shapes, then for each of
     ``classes`` member size classes (by cell count) the 15 shapes of that class
-    with the others held, the incumbent among them (coordinate descent).
+    with the others held, the incumbent among them (coordinate descent; a
+    class moves only to a shape more than ``margin`` faster than its
+    incumbent in the same race, so that race-to-race noise does not move it).
     Returns {"shapes": [(tile_rows, ped_lanes) per scenario], "us_per_step",
     "uniform": {shape: us}, "classes": [class of each scenario]}."""
     if not scs:
@@ -173,8 +175,12 @@ def tune_batch(scs, rounds: int = 2, classes: int = 2) -> dict:
                 t[c] = cand
                 trials.append(t)
             ms = _race(members, [[t[cls[k]] for k in range(n)] for t in trials], rounds)
+            k_inc = cands.index(class_shape[c])
             k_best = min(range(len(trials)), key=lambda k: ms[k])
-            class_shape, best = trials[k_best], 1e3 * ms[k_best]
+            if ms[k_best] < (1.0 - margin) * ms[k_inc]:
+                class_shape, best = trials[k_best], 1e3 * ms[k_best]
+            else:
+                best = 1e3 * ms[k_inc]
         return {"shapes": [class_shape[cls[k]] for k in range(n)], "us_per_step": best,
                 "uniform": {"%dx%d" % k: v for k, v in uniform.items()}, "classes": cls}
     finally:
